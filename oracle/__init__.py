@@ -1,0 +1,157 @@
+"""FP64 CPU oracle for block-wise foveated Gaussian blur (ctypes binding).
+
+TEST INFRASTRUCTURE ONLY: the slow, plain restatement of the method that the
+CUDA library is checked against. Only ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` may import this package. It shares no
+code with the CUDA path and never imports it.
+
+What the functions compute is stated in ``fovea_oracle.c`` (paper Section 2,
+Algorithm 1, Eq. 1 and the truncation/normalisation paragraph after it, and
+the sigma law of Appendix "Choosing the Standard Deviation"). In short:
+
+    sigma_b = sigma0 + k * |centre_b - fixation|      (binary64, no FMA)
+    r_b     = ceil(3 * sigma_b)
+    out(p)  = sum_{|i|,|j| <= r_b} w_i w_j / S^2 * in(clamp(p + (i, j)))
+
+written as a direct 2D sum per output pixel, and its adjoint as a scatter.
+
+Parity status: every function here is pinned by tests under ``tests/``
+(scipy's uniform Gaussian filter, brute-force unit-vector matrices, closed
+forms and invariants); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fovea_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP, binary64, no FP contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            d, i, l, p = ctypes.c_double, ctypes.c_int, ctypes.c_long, ctypes.c_void_p
+            lib.oracle_sigma_table.argtypes = [i, i, i, d, d, d, d, p, p]
+            lib.oracle_sigma_table.restype = None
+            lib.oracle_taps.argtypes = [d, i, p]
+            lib.oracle_taps.restype = None
+            lib.oracle_forward.argtypes = [p, p, i, i, i, l, l, l, i, d, d, d, d, p, i, i]
+            lib.oracle_forward.restype = None
+            lib.oracle_adjoint.argtypes = [p, p, i, i, i, l, l, l, i, d, d, d, d, i]
+            lib.oracle_adjoint.restype = None
+            lib.oracle_quantize_u8.argtypes = [p, p, l]
+            lib.oracle_quantize_u8.restype = None
+            lib.oracle_max_threads.argtypes = []
+            lib.oracle_max_threads.restype = i
+            _lib = lib
+    return _lib
+
+
+def max_threads() -> int:
+    """Number of OpenMP threads the oracle uses by default."""
+    return int(_load().oracle_max_threads())
+
+
+def grid_shape(width: int, height: int, block: int) -> tuple[int, int]:
+    """(blocks along y, blocks along x)."""
+    return (height + block - 1) // block, (width + block - 1) // block
+
+
+def sigma_table(width, height, block, fix_x, fix_y, sigma0, k):
+    """Per-block sigma (float64) and radius (int32), shape (nby, nbx)."""
+    nby, nbx = grid_shape(width, height, block)
+    sig = np.zeros((nby, nbx), np.float64)
+    rad = np.zeros((nby, nbx), np.int32)
+    _load().oracle_sigma_table(width, height, block, float(fix_x), float(fix_y), float(sigma0),
+                               float(k), sig.ctypes.data, rad.ctypes.data)
+    return sig, rad
+
+
+def taps(sigma: float, r: int) -> np.ndarray:
+    """Normalised taps for offsets -r..r (float64, length 2r+1)."""
+    w = np.zeros(2 * max(r, 0) + 1, np.float64)
+    _load().oracle_taps(float(sigma), int(r), w.ctypes.data)
+    return w
+
+
+def _geometry(img: np.ndarray, layout: str):
+    """Return (H, W, C, sy, sx, sc) in elements for a C-contiguous array."""
+    if img.ndim == 2:
+        H, W = img.shape
+        return H, W, 1, W, 1, 0
+    if layout == "hwc":
+        H, W, C = img.shape
+        return H, W, C, W * C, C, 1
+    if layout == "chw":
+        C, H, W = img.shape
+        return H, W, C, W, 1, H * W
+    raise ValueError(f"unknown layout {layout!r}")
+
+
+def forward(img, block, fix_x, fix_y, sigma0, k, layout="hwc", blocks=None, nthreads=0):
+    """Foveated blur of one image in binary64.
+
+    ``img`` is (H, W), (H, W, C) for layout 'hwc' or (C, H, W) for 'chw'; any
+    real dtype (converted exactly to float64). ``blocks`` optionally lists
+    row-major block indices to compute; other pixels of the result are NaN.
+    """
+    x = np.ascontiguousarray(img, dtype=np.float64)
+    H, W, C, sy, sx, sc = _geometry(x, layout)
+    out = np.full_like(x, np.nan)
+    if blocks is None:
+        bl, nl = None, 0
+    else:
+        barr = np.ascontiguousarray(np.asarray(blocks, dtype=np.int32))
+        bl, nl = barr.ctypes.data, int(barr.size)
+    _load().oracle_forward(x.ctypes.data, out.ctypes.data, W, H, C, sy, sx, sc, int(block),
+                           float(fix_x), float(fix_y), float(sigma0), float(k), bl, nl, int(nthreads))
+    return out
+
+
+def adjoint(g_out, block, fix_x, fix_y, sigma0, k, layout="chw", nthreads=0):
+    """Transpose of :func:`forward` applied to ``g_out`` (binary64)."""
+    g = np.ascontiguousarray(g_out, dtype=np.float64)
+    H, W, C, sy, sx, sc = _geometry(g, layout)
+    out = np.zeros_like(g)
+    _load().oracle_adjoint(g.ctypes.data, out.ctypes.data, W, H, C, sy, sx, sc, int(block),
+                           float(fix_x), float(fix_y), float(sigma0), float(k), int(nthreads))
+    return out
+
+
+def quantize_u8(v) -> np.ndarray:
+    """Nearest integer (halves up), clamped to [0, 255], as uint8."""
+    x = np.ascontiguousarray(v, dtype=np.float64)
+    q = np.zeros(x.shape, np.uint8)
+    _load().oracle_quantize_u8(x.ctypes.data, q.ctypes.data, int(x.size))
+    return q
+
+
+def forward_u8(img_u8, block, fix_x, fix_y, sigma0, k, layout="hwc", blocks=None, nthreads=0):
+    """Foveated blur of a uint8 image, coded back to uint8.
+
+    With ``blocks`` given, pixels outside the listed blocks come back as 0.
+    """
+    v = forward(img_u8, block, fix_x, fix_y, sigma0, k, layout, blocks, nthreads)
+    return quantize_u8(np.nan_to_num(v, nan=0.0))

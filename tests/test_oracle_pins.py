@@ -1,0 +1,271 @@
+"""Pins for the FP64 oracle: checks against things other than itself.
+
+Each test ties the oracle to what the paper or the mathematics fixes:
+scipy's textbook Gaussian filter (uniform sigma, clamp-to-edge), closed forms
+of the sigma law, the paper's Eq. 7 figures, and invariants of a normalised,
+clamped, symmetric linear filter (constants, identity, mirror symmetry,
+linearity, the max principle, the adjoint identity). A plausible mistake in
+the oracle -- a dropped tap, a wrong sign or index, a transposed operand, a
+mis-centred block -- fails at least one of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+from scipy import ndimage
+from scipy.signal import windows
+
+import oracle
+from paper_2012_08655_gb300 import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- sigma law
+
+def test_sigma_at_fixation_block_is_sigma0():
+    # Fixation exactly on the centre of block (2, 1) with B = 32: e = 0.
+    sig, rad = oracle.sigma_table(200, 100, 32, 2 * 32 + 16, 1 * 32 + 16, 0.7, 0.05)
+    assert sig[1, 2] == 0.7
+    assert rad[1, 2] == 3  # ceil(2.1)
+
+
+def test_sigma_pythagorean_distance_is_exact():
+    # Block (0,0) centre (16,16); fixation (19,20): e = 5 exactly.
+    sig, rad = oracle.sigma_table(64, 64, 32, 19.0, 20.0, 0.5, 0.1)
+    assert sig[0, 0] == 1.0
+    assert rad[0, 0] == 3
+    # Block (1,0) centre (48,16): dx = 29, dy = -4 -> e = sqrt(857).
+    assert sig[0, 1] == 0.5 + 0.1 * np.sqrt(857.0)
+
+
+def test_sigma_symmetric_and_monotone():
+    sig, rad = oracle.sigma_table(256, 256, 32, 128.0, 128.0, 0.5, 0.02)
+    assert np.array_equal(sig, sig[::-1, :]) and np.array_equal(sig, sig[:, ::-1])
+    assert np.array_equal(sig, sig.T)
+    # Corner blocks are farthest, the four centre blocks nearest.
+    assert sig[0, 0] == sig.max() and sig[3, 3] == sig.min()
+    assert rad.max() == 12 and abs(sig.max() - 3.6678) < 1e-4 and abs(sig.min() - 0.95255) < 1e-4
+
+
+def test_sigma_grid_counts_partial_blocks():
+    sig, rad = oracle.sigma_table(1920, 1080, 32, 960.0, 540.0, 0.5, 0.02)
+    assert sig.shape == (34, 60)
+    # Partial last block row keeps its nominal centre (y = 33*32 + 16 = 1072).
+    assert sig[33, 0] == 0.5 + 0.02 * np.hypot(16.0 - 960.0, 1072.0 - 540.0)
+    assert rad.max() == 67
+
+
+# ---------------------------------------------------------------- taps
+
+@pytest.mark.parametrize("sigma", [0.3, 0.9, 1.0, 2.5, 7.3, 22.2])
+def test_taps_match_scipy_window(sigma):
+    r = int(np.ceil(3 * sigma))
+    w = oracle.taps(sigma, r)
+    ref = windows.gaussian(2 * r + 1, sigma, sym=True)
+    ref = ref / ref.sum()
+    np.testing.assert_allclose(w, ref, rtol=0, atol=1e-15)
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert np.array_equal(w, w[::-1])
+    assert abs(w[r + 1] / w[r] - np.exp(-1.0 / (2 * sigma * sigma))) < 1e-14
+
+
+def test_taps_degenerate():
+    assert np.array_equal(oracle.taps(0.0, 0), [1.0])
+    w = oracle.taps(1e-3, 1)
+    assert np.array_equal(w, [0.0, 1.0, 0.0])
+
+
+# ---------------------------------------------------------------- uniform sigma == scipy
+
+def _scipy_uniform(img, sigma, r, layout):
+    if img.ndim == 2:
+        return ndimage.gaussian_filter(img.astype(np.float64), sigma, mode="nearest", radius=r)
+    if layout == "hwc":
+        return ndimage.gaussian_filter(img.astype(np.float64), (sigma, sigma, 0.0), mode="nearest",
+                                       radius=(r, r, 0))
+    return ndimage.gaussian_filter(img.astype(np.float64), (0.0, sigma, sigma), mode="nearest",
+                                   radius=(0, r, r))
+
+
+@pytest.mark.parametrize("shape,layout,sigma0,B", [
+    ((64, 80), "hwc", 1.3, 32),
+    ((37, 29, 3), "hwc", 2.2, 8),
+    ((2, 45, 50), "chw", 0.8, 16),
+    ((20, 23), "hwc", 9.0, 4),       # r = 27 > W, H: clamping folds whole rows
+])
+def test_uniform_sigma_equals_scipy_gaussian_filter(shape, layout, sigma0, B):
+    img = wl.uniform_f32(shape, seed=3).astype(np.float64)
+    H, W = (shape[0], shape[1]) if layout == "hwc" else (shape[1], shape[2])
+    out = oracle.forward(img, B, 0.3 * W, 0.6 * H, sigma0, 0.0, layout)
+    r = int(np.ceil(3 * sigma0))
+    ref = _scipy_uniform(img, sigma0, r, layout)
+    np.testing.assert_allclose(out, ref, rtol=0, atol=1e-13)
+
+
+# ---------------------------------------------------------------- block-wise selection
+
+@pytest.mark.parametrize("W,H,C,layout,B,fx,fy,s0,k", [
+    (256, 256, 1, "chw", 32, 128.0, 128.0, 0.5, 0.02),     # the 256x256 plain workload
+    (100, 70, 3, "hwc", 16, 20.5, 61.25, 0.4, 0.05),       # partial edge blocks, RGB
+    (57, 41, 2, "chw", 8, -10.0, 50.0, 0.0, 0.15),         # fixation outside the frame
+])
+def test_blockwise_equals_per_block_uniform_blur(W, H, C, layout, B, fx, fy, s0, k):
+    shape = (C, H, W) if layout == "chw" else (H, W, C)
+    img = wl.uniform_f32(shape, seed=11).astype(np.float64)
+    out = oracle.forward(img, B, fx, fy, s0, k, layout)
+    sig, rad = oracle.sigma_table(W, H, B, fx, fy, s0, k)
+    for by in range(sig.shape[0]):
+        for bx in range(sig.shape[1]):
+            ref = _scipy_uniform(img, sig[by, bx], int(rad[by, bx]), layout)
+            ys, xs = slice(by * B, min(by * B + B, H)), slice(bx * B, min(bx * B + B, W))
+            if layout == "chw":
+                got, exp = out[:, ys, xs], ref[:, ys, xs]
+            else:
+                got, exp = out[ys, xs], ref[ys, xs]
+            np.testing.assert_allclose(got, exp, rtol=0, atol=1e-13)
+
+
+def test_u8_frame_blockwise_matches_scipy_after_rounding():
+    img = wl.grating_frame(96, 160, 3, seed=5)
+    q = oracle.forward_u8(img, 32, 80.0, 48.0, 0.5, 0.04, "hwc")
+    sig, rad = oracle.sigma_table(160, 96, 32, 80.0, 48.0, 0.5, 0.04)
+    ref = np.zeros(img.shape, np.float64)
+    for by in range(sig.shape[0]):
+        for bx in range(sig.shape[1]):
+            f = _scipy_uniform(img, sig[by, bx], int(rad[by, bx]), "hwc")
+            ref[by * 32:by * 32 + 32, bx * 32:bx * 32 + 32] = f[by * 32:by * 32 + 32, bx * 32:bx * 32 + 32]
+    refq = np.clip(np.floor(ref + 0.5), 0, 255).astype(np.uint8)
+    assert np.max(np.abs(q.astype(int) - refq.astype(int))) <= 1
+    assert np.mean(q == refq) > 0.999
+
+
+# ---------------------------------------------------------------- invariants
+
+def test_constant_image_stays_constant():
+    img = np.full((70, 90, 3), 0.37)
+    out = oracle.forward(img, 32, 10.0, 20.0, 0.5, 0.1, "hwc")
+    assert np.max(np.abs(out - 0.37)) < 1e-14
+    q = oracle.forward_u8(np.full((70, 90, 3), 200, np.uint8), 32, 10.0, 20.0, 0.5, 0.1)
+    assert np.all(q == 200)
+
+
+def test_sigma_zero_is_identity():
+    img = wl.uniform_f32((3, 40, 50), seed=2).astype(np.float64)
+    assert np.array_equal(oracle.forward(img, 16, 5.0, 5.0, 0.0, 0.0, "chw"), img)
+    # sigma0 = 1e-3 gives r = 1 whose outer taps underflow to zero.
+    assert np.array_equal(oracle.forward(img, 16, 5.0, 5.0, 1e-3, 0.0, "chw"), img)
+
+
+def test_mirror_about_fixation_commutes():
+    W, H, B = 128, 96, 32
+    img = wl.uniform_f32((H, W, 3), seed=4).astype(np.float64)
+    fx, fy = 40.25, 70.5
+    out = oracle.forward(img, B, fx, fy, 0.5, 0.05, "hwc")
+    flip_x = oracle.forward(img[:, ::-1], B, W - fx, fy, 0.5, 0.05, "hwc")
+    np.testing.assert_allclose(flip_x, out[:, ::-1], rtol=0, atol=1e-13)
+    flip_y = oracle.forward(img[::-1], B, fx, H - fy, 0.5, 0.05, "hwc")
+    np.testing.assert_allclose(flip_y, out[::-1], rtol=0, atol=1e-13)
+
+
+def test_transpose_commutes_on_square_image():
+    img = wl.uniform_f32((96, 96), seed=8).astype(np.float64)
+    out = oracle.forward(img, 32, 20.0, 61.0, 0.5, 0.04)
+    tr = oracle.forward(img.T, 32, 61.0, 20.0, 0.5, 0.04)
+    np.testing.assert_allclose(tr, out.T, rtol=0, atol=1e-13)
+
+
+def test_linearity_and_max_principle():
+    a = wl.uniform_f32((2, 50, 60), seed=5).astype(np.float64)
+    b = wl.uniform_f32((2, 50, 60), seed=6).astype(np.float64)
+    args = (16, 33.0, 12.0, 0.3, 0.07, "chw")
+    fa, fb = oracle.forward(a, *args), oracle.forward(b, *args)
+    fab = oracle.forward(2.5 * a - 1.5 * b, *args)
+    np.testing.assert_allclose(fab, 2.5 * fa - 1.5 * fb, rtol=0, atol=1e-12)
+    assert fa.min() >= a.min() - 1e-14 and fa.max() <= a.max() + 1e-14
+
+
+def test_adjoint_identity():
+    W, H, C, B = 23, 17, 2, 8
+    g = wl.rng(9)
+    x = g.standard_normal((C, H, W))
+    y = g.standard_normal((C, H, W))
+    for fx, fy, s0, k in [(5.0, 3.0, 0.5, 0.2), (30.0, -4.0, 1.0, 0.5), (11.5, 8.5, 0.0, 0.0)]:
+        ax = oracle.forward(x, B, fx, fy, s0, k, "chw")
+        aty = oracle.adjoint(y, B, fx, fy, s0, k, "chw")
+        lhs, rhs = float(np.sum(ax * y)), float(np.sum(x * aty))
+        assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+
+
+def test_dense_matrix_brute_force():
+    """Build A and A^T column by column from unit vectors on a tiny image."""
+    W, H, B = 12, 10, 4
+    fx, fy, s0, k = 5.5, 3.2, 0.2, 0.3
+    n = W * H
+    A = np.zeros((n, n))
+    AT = np.zeros((n, n))
+    for q in range(n):
+        e = np.zeros(n)
+        e[q] = 1.0
+        A[:, q] = oracle.forward(e.reshape(H, W), B, fx, fy, s0, k).ravel()
+        AT[:, q] = oracle.adjoint(e.reshape(1, H, W), B, fx, fy, s0, k, "chw").ravel()
+    np.testing.assert_allclose(AT, A.T, rtol=0, atol=1e-15)
+    assert A.min() >= 0.0
+    np.testing.assert_allclose(A.sum(axis=1), 1.0, rtol=0, atol=1e-14)
+    # Each output pixel's weights over the input plane form a separable
+    # (rank-one) kernel: the 2D filter is a product of two 1D filters.
+    for p in range(n):
+        s = np.linalg.svd(A[p].reshape(H, W), compute_uv=False)
+        assert s[1] <= 1e-13 * s[0]
+    # The weights of an output pixel follow its block's taps with clamping:
+    # column sums of its row-slice equal the 1D taps folded at the borders.
+    sig, rad = oracle.sigma_table(W, H, B, fx, fy, s0, k)
+    for p in [0, 17, 45, 119]:
+        py, px = divmod(p, W)
+        r = int(rad[py // B, px // B])
+        w = oracle.taps(sig[py // B, px // B], r)
+        fold = np.zeros(W)
+        for i in range(-r, r + 1):
+            fold[min(max(px + i, 0), W - 1)] += w[i + r]
+        np.testing.assert_allclose(A[p].reshape(H, W).sum(axis=0), fold, rtol=0, atol=1e-15)
+
+
+def test_sampled_blocks_match_full_frame():
+    img = wl.grating_frame(70, 100, 3, seed=1)
+    full = oracle.forward(img, 32, 50.0, 35.0, 0.5, 0.05, "hwc")
+    part = oracle.forward(img, 32, 50.0, 35.0, 0.5, 0.05, "hwc", blocks=[0, 5, 11])
+    for b in [0, 5, 11]:
+        by, bx = divmod(b, 4)
+        sl = (slice(by * 32, by * 32 + 32), slice(bx * 32, bx * 32 + 32))
+        assert np.array_equal(part[sl], full[sl])
+    assert not np.isnan(part[40, 40, 0])  # block 5 = (bx 1, by 1)
+    assert np.isnan(part[10, 40, 0])      # block 1 was not listed
+
+
+# ---------------------------------------------------------------- uint8 coding
+
+def test_quantize_u8_rounding():
+    v = np.array([-3.0, -0.2, 0.0, 0.49999, 0.5, 1.5, 2.5, 127.4999, 254.5, 255.0, 255.7, 300.0])
+    q = oracle.quantize_u8(v)
+    assert q.tolist() == [0, 0, 0, 0, 1, 2, 3, 127, 255, 255, 255, 255]
+
+
+# ---------------------------------------------------------------- paper's Eq. 7 figures
+
+def test_eq7_max_filter_sizes_pin_tile_geometry():
+    """Eq. 7 with the paper's maximum filter sizes fixes two readings: the tile
+    is the fragment padded by N-1 pixels in each dimension (radius (N-1)/2 on
+    each side), and the 'bits' of Eq. 7 are bytes against a 48,000-byte limit."""
+    with open(os.path.join(GOLDEN, "eq7_max_filter.json")) as f:
+        gold = json.load(f)
+    limit = gold["shared_memory_limit_bytes"]
+
+    def usage(frag, n):
+        tile = frag + n - 1
+        return tile * tile + 4 * frag * tile
+
+    for case in gold["cases"]:
+        frag, nmax = case["fragment"], case["max_filter"]
+        assert usage(frag, nmax) <= limit < usage(frag, nmax + 1)
+        assert usage(frag, nmax) == case["bytes_at_max"]
