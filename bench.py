@@ -1,0 +1,488 @@
+#!/usr/bin/env python3
+"""Benchmark of the foveation path on one node.
+
+Headline: foveated Mpix/s of one 1920x1080 RGB uint8 frame (sigma = 0.5 +
+0.02 e, fixation at the centre, 32x32 blocks), frames resident in HBM,
+rendered through the C ABI (fovea_render: sigma-table kernel, work-list
+order kernel, persistent blur kernel). A step is one render of one frame.
+Inputs rotate over a pool of distinct device buffers larger than L2.
+
+Also reported on the same JSON line:
+  e2e           same metric through fovea_render_host from pinned host
+                memory (copies inside the timed region);
+  roofline      the blur kernel timed alone with CUDA events on its stream,
+                algorithmic FP32 FMAs per launch against the FP32 FMA peak;
+  cpu_baseline  the FP64 oracle on a bounded sample of the frame's blocks;
+  clocks        nvidia-smi samples taken during the timed region;
+  batched       the 64-frame mixed batch in one launch vs one launch per frame;
+  served        p50/p99 latency of the served request stream (continuous
+                batching) vs the plain one-request-per-launch loop.
+
+`--impl reference` times the FP64 oracle (the reference arm of this build)
+on bounded samples of the same workload and prints the same line.
+
+Multi-GPU (torchrun, one process per GPU): replicas only; every rank renders
+its own frames, there is no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "foveated Mpix/s at 1080p RGB (% of roofline) + p50/p99 served-frame latency"
+UNIT = "Mpix/s"
+W, H, C, B = 1920, 1080, 3, 32
+SIGMA0, K_SLOPE = 0.5, 0.02
+FIX = (960.0, 540.0)
+WORKLOAD = "1920x1080 RGB uint8 frame, 32x32 blocks, sigma = 0.5 + 0.02 e px, fixation at the centre"
+L2_BYTES = 129 * 1024 * 1024
+PROFILE = os.path.join(ROOT, "profiles", "forward_1080p_u8.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2012_08655_gb300", "csrc", f)
+                  for f in ("forward.cu", "fovea_internal.cuh")]
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20000)
+    p.add_argument("--warmup", type=int, default=200)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-extras", action="store_true", help="skip the batched and served legs")
+    p.add_argument("--served-seconds", type=float, default=10.0)
+    p.add_argument("--no-autotune", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the blur kernel from the committed ncu summary,
+    or None when the summary is missing or the kernel changed since."""
+    try:
+        vals = {}
+        with open(PROFILE) as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    vals[k.strip()] = v.strip()
+        if vals.get("kernel_source_sha256_16") != kernel_source_hash():
+            return None
+        return float(vals["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def algorithmic_fmas(radius, width, height, channels, block):
+    """Block-wise separable FMAs of one frame, halo rows included, clamping not
+    folded: sum_b C (2 r_b + 1) bw (2 bh + 2 r_b)."""
+    import numpy as np
+    r = radius.astype(np.float64)
+    nby, nbx = radius.shape
+    bw = np.minimum(block, width - block * np.arange(nbx))[None, :].astype(np.float64)
+    bh = np.minimum(block, height - block * np.arange(nby))[:, None].astype(np.float64)
+    return float(np.sum(channels * (2 * r + 1) * bw * (2 * bh + 2 * r)))
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples of one GPU (by UUID)."""
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for _, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9 or (self.uuid and self.uuid not in parts[0]):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_uuid(dev) -> str:
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return ""
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle legs
+
+def cpu_oracle_sample(target_s: float = 8.0, seed: int = 0):
+    """Time the FP64 oracle on a bounded, seeded sample of the frame's blocks."""
+    import numpy as np
+
+    import oracle
+    from paper_2012_08655_gb300 import workloads as wl
+    frame = wl.frame_1080p()
+    nb = ((W + B - 1) // B) * ((H + B - 1) // B)
+    g = np.random.Generator(np.random.PCG64(seed))
+    order = g.permutation(nb)
+    threads = oracle.max_threads()
+    # calibrate on a few blocks, then size the sample for about target_s seconds
+    t0 = time.perf_counter()
+    oracle.forward(frame.image, B, FIX[0], FIX[1], SIGMA0, K_SLOPE, "hwc", blocks=order[:threads].tolist())
+    dt = max(time.perf_counter() - t0, 1e-3)
+    n = int(min(nb, max(threads, threads * target_s / dt)))
+    blocks = order[:n].tolist()
+    t0 = time.perf_counter()
+    oracle.forward(frame.image, B, FIX[0], FIX[1], SIGMA0, K_SLOPE, "hwc", blocks=blocks)
+    dt = time.perf_counter() - t0
+    px = n * B * B
+    return {"value": px / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} of {nb} blocks of the 1080p frame (seeded random), FP64 direct 2D sum, "
+                      f"{threads} OpenMP threads, {dt:.2f} s"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    from paper_2012_08655_gb300 import workloads as wl
+    frame = wl.frame_1080p()
+    nb = ((W + B - 1) // B) * ((H + B - 1) // B)
+    order = np.random.Generator(np.random.PCG64(1)).permutation(nb)
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    oracle.forward(frame.image, B, FIX[0], FIX[1], SIGMA0, K_SLOPE, "hwc", blocks=order[:threads].tolist())
+    per_block = max((time.perf_counter() - t0) / threads, 1e-4)
+    # size each step so the whole run takes about two minutes of wall time
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    n = int(max(1, min(nb, budget * threads / per_block)))
+    def step(i):
+        sel = np.roll(order, -i * n)[:n].tolist()
+        oracle.forward(frame.image, B, FIX[0], FIX[1], SIGMA0, K_SLOPE, "hwc", blocks=sel)
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(args.warmup + i)
+    dt = time.perf_counter() - t0
+    value = args.steps * n * B * B / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "block": B, "frame": f"{W}x{H}x{C}",
+                                        "step": f"{n} blocks of the frame per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{n} blocks per step, FP64 direct 2D sum, {threads} OpenMP threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU legs
+
+def batched_leg(fv, torch):
+    """64-frame mixed batch: one batched launch vs one render launch per frame."""
+    from paper_2012_08655_gb300 import workloads as wl
+    params = wl.mixed_batch_params(seed=0)
+    content = {}
+    ins, outs = [], []
+    for (w, h, fx, fy, k) in params:
+        if (w, h) not in content:
+            content[(w, h)] = torch.from_numpy(wl.grating_frame(h, w, 3, seed=w)).cuda()
+        ins.append(content[(w, h)].clone())
+        outs.append(torch.empty_like(ins[-1]))
+    frames = [fv.BatchFrame(ins[i], outs[i], p[2], p[3], 0.5, p[4]) for i, p in enumerate(params)]
+    ctxs = {}
+    px = sum(w * h for (w, h, _, _, _) in params)
+
+    def batched():
+        fv.foveate_batch(frames)
+
+    def per_frame():
+        for i, (w, h, fx, fy, k) in enumerate(params):
+            key = (w, h, k)
+            if key not in ctxs:
+                ctxs[key] = fv.Context(w, h, 3, 32, 0.5, k, fv.U8_HWC)
+            ctxs[key].render(ins[i], outs[i], fx, fy)
+
+    res = {}
+    for name, fn in (("batched", batched), ("per_frame", per_frame)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms": ms, "mpix_s": px / ms / 1e3}
+    return {"workload": "64 RGB uint8 frames: 16x640x480, 16x1280x720, 24x1920x1080, 8x3840x2160; "
+                        "uniform fixations, k ~ U[0.01, 0.04]", "mpix": px / 1e6,
+            "batched_mpix_s": res["batched"]["mpix_s"], "batched_ms": res["batched"]["ms"],
+            "per_frame_mpix_s": res["per_frame"]["mpix_s"], "per_frame_ms": res["per_frame"]["ms"],
+            "speedup": res["per_frame"]["ms"] / res["batched"]["ms"]}
+
+
+def served_leg(fv, torch, seconds: float, max_batch: int):
+    """Replay the Poisson request stream through the serving loop."""
+    import numpy as np
+
+    from paper_2012_08655_gb300 import workloads as wl
+    stream = wl.served_stream(seed=0, duration_s=seconds)
+    reqs = stream.requests
+    src, rings = {}, {}
+    for s, (w, h, c) in enumerate(stream.stream_shapes):
+        src[s] = torch.from_numpy(wl.grating_frame(h, w, c, seed=100 + s)).pin_memory()
+        n = 32 if w * h < 100000 else 12
+        rings[s] = [torch.empty_like(src[s]).pin_memory() for _ in range(n)]
+    srv = fv.Server(device_budget_bytes=2 << 30, max_batch=max_batch, block=32, max_inflight=512)
+    slot_owner = {}
+    ids = [None] * len(reqs)
+    times = [None] * len(reqs)
+    done_evt = threading.Event()
+
+    def waiter():
+        for i in range(len(reqs)):
+            while ids[i] is None:
+                time.sleep(0.0002)
+            times[i] = srv.wait(ids[i], timeout_ms=60000)
+        done_evt.set()
+
+    th = threading.Thread(target=waiter, daemon=True)
+    th.start()
+    ring_pos = {s: 0 for s in rings}
+    t0 = srv.now_us() + 200000.0
+    for i, r in enumerate(reqs):
+        s = r.stream
+        slot = ring_pos[s] % len(rings[s])
+        ring_pos[s] += 1
+        prev = slot_owner.get((s, slot))
+        if prev is not None:
+            while times[prev] is None:  # output buffer still in use
+                time.sleep(0.0001)
+        slot_owner[(s, slot)] = i
+        arrival = t0 + r.arrival_s * 1e6
+        while srv.now_us() < arrival:
+            d = (arrival - srv.now_us()) * 1e-6
+            if d > 0.0005:
+                time.sleep(d - 0.0003)
+        ids[i] = srv.submit(src[s], rings[s][slot], r.fix_x, r.fix_y, stream.sigma0, stream.k, arrival_us=arrival)
+    done_evt.wait(timeout=120)
+    srv.close()
+    lat = np.array([(t["done_us"] - t["arrival_us"]) * 1e-3 for t in times if t])
+    bs = np.array([t["batch_size"] for t in times if t])
+    span = (max(t["done_us"] for t in times) - t0) * 1e-6
+    px = sum(r.width * r.height for r in reqs)
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "mpix_s": px / span / 1e6, "requests": len(reqs),
+            "mean_batch": float(bs.mean()), "errors": int(sum(1 for t in times if t and t["status"] != 0))}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup(args)
+    from paper_2012_08655_gb300 import fovea as fv
+    from paper_2012_08655_gb300 import workloads as wl
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    frame = wl.frame_1080p(seed=rank)
+    base = torch.from_numpy(frame.image).to(dev)
+    fbytes = base.numel()
+    pool_n = max(2, int(np.ceil(2 * L2_BYTES / (2 * fbytes))) + 1)  # in + out of the pool > 2x L2
+    ins = [base.clone() for _ in range(pool_n)]
+    outs = [torch.empty_like(base) for _ in range(pool_n)]
+    ctx = fv.Context(W, H, C, B, SIGMA0, K_SLOPE, fv.U8_HWC)
+    cfg = ctx.get_config() if args.no_autotune else ctx.autotune(iters=20)
+    stream = torch.cuda.current_stream()
+
+    for i in range(args.warmup):
+        ctx.render(ins[i % pool_n], outs[i % pool_n], *FIX)
+    torch.cuda.synchronize()
+
+    ev_k = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(gpu_uuid(dev))
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(args.steps):
+        ctx.set_kernel_events(*ev_k[i])
+        ctx.render(ins[i % pool_n], outs[i % pool_n], *FIX)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ctx.set_kernel_events(None, None)
+    elapsed_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    kernel_ms = float(np.mean([a.elapsed_time(b) for a, b in ev_k]))
+    value = world * W * H * args.steps / (elapsed_ms * 1e-3) / 1e6
+
+    # roofline of the blur kernel: algorithmic FP32 FMAs against the FP32 FMA peak
+    sig, rad = ctx.sigma_table(*FIX)
+    fmas = algorithmic_fmas(rad.cpu().numpy(), W, H, C, B)
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    peak_tflops = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    achieved = 2 * fmas / (kernel_ms * 1e-3) / 1e12
+    traffic = profiled_traffic()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": traffic,
+                "kernel": "forward_kernel (persistent blur)", "kernel_ms": kernel_ms,
+                "algorithmic_fmas_per_launch": fmas,
+                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz "
+                              "(derived, not measured)",
+                "hbm_bound_ms": 2 * fbytes / 6795.1e9 * 1e3}
+
+    # end to end: pinned host frames through fovea_render_host
+    hin = [torch.from_numpy(frame.image).pin_memory() for _ in range(4)]
+    hout = [torch.empty_like(hin[0]).pin_memory() for _ in range(4)]
+    for i in range(min(args.warmup, 50)):
+        ctx.render_host(hin[i % 4], hout[i % 4], *FIX)
+    torch.cuda.synchronize()
+    ke = args.steps
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    t0 = time.perf_counter()
+    for i in range(ke):
+        ctx.render_host(hin[i % 4], hout[i % 4], *FIX)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall_ms = (time.perf_counter() - t0) * 1e3
+    barrier(world)
+    e2e_ms = max_over_ranks(max(e0.elapsed_time(e1), wall_ms), world)
+    e2e = {"value": world * W * H * ke / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": int(hin[0].numel()), "d2h_bytes_per_step": int(hout[0].numel()),
+           "ms_per_step": e2e_ms / ke}
+
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras["batched"] = batched_leg(fv, torch)
+        served = served_leg(fv, torch, args.served_seconds, max_batch=64)
+        plain = served_leg(fv, torch, args.served_seconds, max_batch=1)
+        served["plain_per_frame"] = {k: plain[k] for k in ("p50_ms", "p99_ms", "mpix_s", "mean_batch")}
+        extras["served"] = served
+
+    cpu = cpu_oracle_sample() if (rank == 0 and world == 1) else None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "block": B, "frame": f"{W}x{H}x{C}", "io": "uint8 HWC",
+                       "l2": f"inputs rotate over {pool_n} distinct frame buffers "
+                             f"({2 * pool_n * fbytes / 2**20:.0f} MiB in+out) > L2",
+                       "kernel_config": cfg, "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": 3 * args.steps, "clocks": clocks,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,228 @@
+/*
+ * fovea.h -- C ABI of libfovea, a GB300 (sm_103a) implementation of
+ * block-wise foveated Gaussian blur ("CUDA-Optimized real-time rendering of a
+ * Foveated Visual System", arXiv 2012.08655).
+ *
+ * The operation (paper Section 2 and Algorithm 1; filter of Eq. 1 and the
+ * truncation/normalisation paragraph after it):
+ *   - the image is split into square blocks of side B ("fragments");
+ *   - block b gets sigma_b = sigma0 + k * e_b, with e_b the Euclidean distance
+ *     in pixels from the block centre (B*bx + B/2, B*by + B/2) to the fixation
+ *     (fix_x, fix_y); pixel (x, y) covers [x, x+1) x [y, y+1), so the centre
+ *     of a W x H frame is (W/2, H/2). The law is evaluated in IEEE binary64
+ *     without fused multiply-add; r_b = ceil(3 * sigma_b);
+ *   - every output pixel of block b is the normalised Gaussian-weighted sum of
+ *     its (2 r_b + 1)^2 clamp-to-edge neighbourhood at sigma_b:
+ *        out(x,y,c) = sum_{|i|,|j| <= r_b} w_i w_j / S^2 * in(clamp(x+i), clamp(y+j), c)
+ *        w_i = exp(-i^2 / (2 sigma_b^2)),  S = sum_{|i| <= r_b} w_i.
+ *     Because all outputs of a block share one sigma, the library computes it
+ *     as an in-tile separable pass (vertical, then horizontal) over the halo
+ *     tile of the block, which is exact in real arithmetic.
+ *   - uint8 data is converted to float on load and coded back as
+ *     min(255, max(0, floor(v + 0.5))).
+ *
+ * Conventions for every entry point below:
+ *   - Device pointers are CUDA global-memory pointers on the current device;
+ *     host pointers are ordinary (preferably pinned) host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Calls enqueue work on it and return without synchronising;
+ *     errors raised while kernels run surface on the next synchronising CUDA
+ *     call of the caller, as usual for CUDA.
+ *   - A context is not thread-safe and its workspace is reused by every call:
+ *     calls on one context must be ordered on one stream (or otherwise
+ *     serialised by the caller). Use one context per concurrent stream.
+ *   - The caller owns all image and gradient buffers; the library owns its
+ *     workspace (per-block sigma/radius tables, work lists, descriptors,
+ *     graphs) and never frees the caller's memory.
+ *   - Every function returns FOVEA_OK (0) or a negative fovea_status; nothing
+ *     throws across the ABI.
+ *   - Layouts: FOVEA_U8_HWC is a row-major H x W x C array of bytes (channels
+ *     interleaved, the usual frame layout); FOVEA_F32_CHW is a C x H x W
+ *     float32 array (the torch layout of one image). Input and output of a
+ *     call must not overlap.
+ */
+#ifndef FOVEA_H_
+#define FOVEA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fovea_ctx fovea_ctx;
+typedef struct fovea_server fovea_server;
+
+typedef enum {
+  FOVEA_OK = 0,
+  FOVEA_EINVAL = -1,        /* bad argument (null pointer, aliasing, bad size, non-finite fixation, ...) */
+  FOVEA_ENOMEM = -2,        /* device or pinned-host allocation failed */
+  FOVEA_ECUDA = -3,         /* a CUDA runtime call failed (see fovea_last_cuda_error) */
+  FOVEA_EBUSY = -4,         /* no free slot / memory for the request right now (serving) */
+  FOVEA_ETIMEOUT = -5,      /* a bounded wait ran out */
+  FOVEA_EUNSUPPORTED = -6   /* valid request outside what this build supports */
+} fovea_status;
+
+typedef enum { FOVEA_U8_HWC = 0, FOVEA_F32_CHW = 1 } fovea_format;
+
+typedef enum { FOVEA_LAW_LINEAR = 0 } fovea_law_kind;
+
+/* Sigma law sigma_b = sigma0 + k * e_b (pixels). Both must be finite and >= 0.
+ * (Appendix "Choosing the Standard Deviation", Eqs. 2-6: the Geisler-Perry
+ * cut-off law with eccentricity proportional to pixel distance, Eq. 5, is
+ * linear in e_b and is expressed through these two numbers.) */
+typedef struct {
+  int kind;       /* FOVEA_LAW_LINEAR */
+  double sigma0;
+  double k;
+} fovea_sigma_law;
+
+/* Largest radius r = ceil(3 sigma) a block may reach; larger requests are
+ * refused with FOVEA_EUNSUPPORTED before any work is enqueued. */
+#define FOVEA_MAX_RADIUS 1023
+/* Block side B must satisfy 1 <= B <= FOVEA_MAX_BLOCK. */
+#define FOVEA_MAX_BLOCK 32
+
+/* Create a context for frames of width x height x channels (channels in
+ * {1, 2, 3, 4}) in `format`, split into block x block blocks, with sigma law
+ * `law`. width = height = 0 creates a batch-only context whose workspace is
+ * sized on first use (fovea_render_batch / fovea_backward_batch).
+ * Allocates device workspace on the current device (Algorithm 1, the
+ * once-per-setup CPU steps: fragment size and blur-grid parameters). */
+int fovea_create(int width, int height, int channels, int block, const fovea_sigma_law* law,
+                 int format, fovea_ctx** out);
+
+/* Foveate one frame that is resident on the device (Algorithm 1, the
+ * per-frame GPU steps: padded tile, horizontal and vertical convolution,
+ * write-out). `in_dev` and `out_dev` hold one frame in the context's format
+ * and shape; the fixation (fix_x, fix_y) is in pixel coordinates and may lie
+ * anywhere, inside or outside the frame (Section 2). */
+int fovea_render(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x, float fix_y,
+                 void* stream);
+
+/* One frame of a batch. Frames of one batch may differ in size, channels,
+ * format, fixation and sigma law; the block side is the context's. */
+typedef struct {
+  int width, height, channels, format;
+  const void* in;     /* device pointer */
+  void* out;          /* device pointer */
+  float fix_x, fix_y;
+  double sigma0, k;
+} fovea_frame;
+
+/* Foveate n frames in one launch sequence: a sigma-table kernel over every
+ * (frame, block), a cost-ordered work list, and one persistent kernel that
+ * pulls (frame, block) items from it, replayed from a CUDA graph. The
+ * `frames` array is read before the call returns. */
+int fovea_render_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, void* stream);
+
+/* Foveate one frame held in HOST memory: copies the input to device staging
+ * buffers the context owns, renders, and copies the result back into
+ * `out_host`, all on `stream` (Algorithm 1 steps "transfer input image from
+ * CPU pinned memory" and "transfer output image to CPU pinned memory"). Host
+ * buffers should be pinned (cudaHostAlloc) for the copies to be asynchronous.
+ * The call returns once the work is enqueued; out_host is valid after the
+ * stream is synchronised. */
+int fovea_render_host(fovea_ctx* ctx, const void* in_host, void* out_host, float fix_x,
+                      float fix_y, void* stream);
+
+/* Adjoint of fovea_render (the transpose of the linear map in -> out) for an
+ * FOVEA_F32_CHW context: grad_in = A^T grad_out, with the same fixation.
+ * grad_in is overwritten. Not in the paper; it lets the blur sit inside
+ * network training. */
+int fovea_backward(fovea_ctx* ctx, const float* grad_out_dev, float* grad_in_dev, float fix_x,
+                   float fix_y, void* stream);
+
+/* Adjoint of fovea_render_batch for FOVEA_F32_CHW frames: for each frame,
+ * `in` is grad_out and `out` (overwritten) is grad_in. */
+int fovea_backward_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, void* stream);
+
+/* Per-block sigma (float32, rounded from the binary64 value) and radius for
+ * the context's frame at the given fixation, row-major over the block grid
+ * (ceil(H/B) x ceil(W/B)), written to device arrays. This is the table the
+ * render path computes internally (Algorithm 1, "blur grid" with its per-frame
+ * offset to the fixation). */
+int fovea_sigma_table(fovea_ctx* ctx, float fix_x, float fix_y, float* sigma_dev, int* radius_dev,
+                      void* stream);
+
+/* Kernel configuration of the forward path. Chosen by the built-in
+ * autotuner (fovea_autotune) or set explicitly (fovea_set_config). */
+typedef struct {
+  int threads;        /* threads per CTA of the forward kernel: 128 or 256 */
+  int ctas_per_sm;    /* persistent CTAs per SM (0 = as many as fit) */
+  int rows_per_chunk; /* tile rows staged per chunk: 16, 32 or 64 */
+} fovea_config;
+
+int fovea_get_config(const fovea_ctx* ctx, fovea_config* cfg);
+int fovea_set_config(fovea_ctx* ctx, const fovea_config* cfg);
+
+/* Time every built-in configuration on the context's own frame shape (a
+ * synthetic frame, fixation at the centre, `iters` timed launches each),
+ * keep the fastest, and cache it under the device name, SM count, shape,
+ * format and radius bucket. Synchronises the device. If `cache_path` is not
+ * NULL the cache is read from and written to that JSON file. */
+int fovea_autotune(fovea_ctx* ctx, int iters, const char* cache_path);
+
+/* Measurement hook: when both are non-NULL, every later render call on this
+ * context records `ev_start` (a cudaEvent_t) immediately before launching its
+ * persistent blur kernel and `ev_stop` immediately after, on the call's
+ * stream, so a caller can time that kernel alone. NULL, NULL turns it off. */
+int fovea_set_kernel_events(fovea_ctx* ctx, void* ev_start, void* ev_stop);
+
+void fovea_destroy(fovea_ctx* ctx);
+
+const char* fovea_strerror(int status);
+
+/* The cudaError_t of the last failed CUDA call in this thread (0 if none). */
+int fovea_last_cuda_error(void);
+
+/* ------------------------------------------------------------------ serving
+ * Continuous-batching request loop (not in the paper; it serves frames of
+ * different resolutions and fixations as they arrive). Frames start and end
+ * in host memory. Requests are admitted while device memory for their input
+ * and output is available within `device_budget_bytes`; every scheduling tick
+ * the worker renders all admitted requests whose input copy has finished as
+ * one batch (same kernels as fovea_render_batch), while later requests copy
+ * in on a second stream. Results are copied back to the caller's host buffer.
+ */
+typedef struct {
+  size_t device_budget_bytes;  /* cap on device memory used for request buffers */
+  int max_batch;               /* most frames rendered in one tick */
+  int block;                   /* block side B */
+  int max_inflight;            /* most admitted-but-unfinished requests */
+} fovea_server_config;
+
+typedef struct {
+  double arrival_us;   /* caller-supplied arrival time (steady clock, microseconds) */
+  double admit_us;     /* admission (device memory reserved) */
+  double start_us;     /* host time its batch was launched */
+  double done_us;      /* host time its output copy was seen complete */
+  int batch_size;      /* frames in the batch it was rendered in */
+  int status;          /* FOVEA_OK or an error */
+} fovea_request_times;
+
+int fovea_server_create(const fovea_server_config* cfg, fovea_server** out);
+
+/* Submit one frame. `in_host` / `out_host` stay owned by the caller and must
+ * stay valid until the request completes. Returns a request id >= 0, or a
+ * negative status (FOVEA_EBUSY when the request can never fit the budget).
+ * Admission waits, inside the worker, for memory to free up. */
+long long fovea_server_submit(fovea_server* srv, const fovea_frame* frame_host,
+                              double arrival_us);
+
+/* Wait up to timeout_ms for request `id` to finish (0 = poll). Returns
+ * FOVEA_OK when done (times filled in), FOVEA_ETIMEOUT otherwise. */
+int fovea_server_wait(fovea_server* srv, long long id, int timeout_ms, fovea_request_times* times);
+
+/* Microseconds on the steady clock the server uses for its timestamps. */
+double fovea_server_now_us(void);
+
+/* Drain all requests and stop the worker. */
+void fovea_server_destroy(fovea_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FOVEA_H_ */

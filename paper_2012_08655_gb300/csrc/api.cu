@@ -1,0 +1,544 @@
+// C ABI of libfovea: contexts, argument checks, workspace, launches, graphs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fovea_internal.cuh"
+#include "fovea_host.h"
+
+using namespace fovea;
+
+namespace {
+
+thread_local int g_last_cuda_error = 0;
+
+int cuda_fail(cudaError_t e) {
+  g_last_cuda_error = (int)e;
+  return e == cudaErrorMemoryAllocation ? FOVEA_ENOMEM : FOVEA_ECUDA;
+}
+
+#define FOVEA_CUDA(call)                      \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
+
+constexpr int kBatchSlots = 4;
+
+// Zero the output planes of every frame of a device-resident batch (the
+// adjoint accumulates into them).
+__global__ void zero_outputs_kernel(const BatchHeader* hdr, const FrameDesc* frames) {
+  const int f = blockIdx.y;
+  if (f >= hdr->nframes) return;
+  const FrameDesc fd = frames[f];
+  const size_t n = (size_t)fd.W * fd.H * fd.C;
+  float* out = static_cast<float*>(fd.out);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = 0.0f;
+}
+
+}  // namespace
+
+struct fovea_ctx {
+  int W = 0, H = 0, C = 0, B = 32, fmt = 0;
+  double sigma0 = 0.0, k = 0.0;
+  bool batch_only = false;
+  int device = 0, num_sms = 0;
+  FwdConfig cfg{256, 0, 32};
+  bool cfg_tuned = false;
+  Workspace ws{};
+  cudaStream_t capture_stream = nullptr;
+  // device-resident batch (header + descriptors)
+  void* batch_dev = nullptr;
+  size_t batch_dev_cap = 0;
+  void* batch_host[kBatchSlots] = {};
+  cudaEvent_t batch_ev[kBatchSlots] = {};
+  size_t batch_host_cap = 0;
+  int batch_slot = 0;
+  // CUDA graphs of the batch launch sequence, keyed by (kind, radius bound)
+  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+  // optional events bracketing the persistent blur kernel (measurement)
+  cudaEvent_t kev_start = nullptr, kev_stop = nullptr;
+  // device staging for fovea_render_host
+  void* host_in_dev = nullptr;
+  void* host_out_dev = nullptr;
+  size_t host_io_bytes = 0;
+};
+
+namespace fovea {
+
+double block_centre_host(int b, int B) { return (double)B * (double)b + 0.5 * (double)B; }
+
+int radius_bound(int W, int H, int B, double fx, double fy, double sigma0, double k) {
+  // The largest eccentricity over the block grid is reached at one of its
+  // four corner blocks; every step is rounded on its own (this file is
+  // compiled without floating-point contraction), so the result equals the
+  // device's radius of that block.
+  const int nbx = (W + B - 1) / B, nby = (H + B - 1) / B;
+  const int bxs[2] = {0, nbx - 1}, bys[2] = {0, nby - 1};
+  int rmax = 0;
+  for (int bx : bxs)
+    for (int by : bys) {
+      volatile double dx = block_centre_host(bx, B) - fx;
+      volatile double dy = block_centre_host(by, B) - fy;
+      volatile double dx2 = dx * dx;
+      volatile double dy2 = dy * dy;
+      volatile double e = std::sqrt(dx2 + dy2);
+      volatile double ke = k * e;
+      volatile double s = sigma0 + ke;
+      volatile double s3 = 3.0 * s;
+      double rc = std::ceil(s3);
+      int r = rc > 1e9 ? 1000000000 : (int)rc;
+      rmax = std::max(rmax, r);
+    }
+  return rmax;
+}
+
+int check_frame(int W, int H, int C, int fmt, int B, double sigma0, double k, float fx, float fy) {
+  if (W <= 0 || H <= 0 || B <= 0) return FOVEA_EINVAL;
+  if (B > kMaxBlock) return FOVEA_EUNSUPPORTED;
+  if (C < 1 || C > 4) return FOVEA_EINVAL;
+  if (fmt != FOVEA_U8_HWC && fmt != FOVEA_F32_CHW) return FOVEA_EINVAL;
+  if (!finite_nonneg(sigma0) || !finite_nonneg(k)) return FOVEA_EINVAL;
+  if (!std::isfinite(fx) || !std::isfinite(fy)) return FOVEA_EINVAL;
+  if ((long long)W * H * C > (1ll << 31) - 1) return FOVEA_EUNSUPPORTED;
+  if (radius_bound(W, H, B, fx, fy, sigma0, k) > kMaxRadius) return FOVEA_EUNSUPPORTED;
+  return FOVEA_OK;
+}
+
+size_t frame_bytes(int W, int H, int C, int fmt) {
+  return (size_t)W * H * C * (fmt == FOVEA_U8_HWC ? 1 : 4);
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const char* pa = static_cast<const char*>(a);
+  const char* pb = static_cast<const char*>(b);
+  return pa < pb + nb && pb < pa + na;
+}
+
+FrameDesc make_desc(int W, int H, int C, int fmt, int B, const void* in, void* out, float fx,
+                    float fy, double sigma0, double k, long long item0) {
+  FrameDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.in = in;
+  d.out = out;
+  d.W = W; d.H = H; d.C = C; d.fmt = fmt;
+  d.B = B;
+  d.nbx = (W + B - 1) / B;
+  d.nby = (H + B - 1) / B;
+  d.fx = fx; d.fy = fy;
+  d.sigma0 = sigma0; d.k = k;
+  d.item0 = item0;
+  return d;
+}
+
+}  // namespace fovea
+
+namespace {
+
+int ensure_workspace(fovea_ctx* ctx, long long items) {
+  if (ctx->ws.capacity >= items && ctx->ws.counters) return FOVEA_OK;
+  long long cap = std::max<long long>(items, 1024);
+  if (ctx->ws.items) {
+    // Growing: the old buffers may still be in use by queued work.
+    FOVEA_CUDA(cudaDeviceSynchronize());
+    cudaFree(ctx->ws.items);
+    cudaFree(ctx->ws.rank);
+    cudaFree(ctx->ws.order);
+    ctx->ws.items = nullptr;
+    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    ctx->graphs.clear();
+  }
+  FOVEA_CUDA(cudaMalloc(&ctx->ws.items, cap * sizeof(ItemInfo)));
+  FOVEA_CUDA(cudaMalloc(&ctx->ws.rank, cap * sizeof(int)));
+  FOVEA_CUDA(cudaMalloc(&ctx->ws.order, cap * sizeof(int)));
+  if (!ctx->ws.counters) {
+    FOVEA_CUDA(cudaMalloc(&ctx->ws.counters, CNT_TOTAL * sizeof(unsigned int)));
+    FOVEA_CUDA(cudaMemset(ctx->ws.counters, 0, CNT_TOTAL * sizeof(unsigned int)));
+    FOVEA_CUDA(cudaDeviceSynchronize());
+  }
+  ctx->ws.capacity = cap;
+  return FOVEA_OK;
+}
+
+int sigma_grid(long long items, int num_sms) {
+  long long g = (items + 255) / 256;
+  return (int)std::max<long long>(1, std::min<long long>(g, 4ll * num_sms));
+}
+
+int forward_grid(fovea_ctx* ctx, int rmax) {
+  int per = forward_max_ctas_per_sm(ctx->cfg, rmax);
+  if (per <= 0) return 0;
+  if (ctx->cfg.ctas_per_sm > 0) per = std::min(per, ctx->cfg.ctas_per_sm);
+  return per * ctx->num_sms;
+}
+
+int adjoint_grid(fovea_ctx* ctx, int rmax) {
+  int per = adjoint_max_ctas_per_sm(rmax);
+  if (per <= 0) return 0;
+  return per * ctx->num_sms;
+}
+
+// Stage n frame descriptors into the pinned slot ring and copy them to the
+// device-resident batch buffer on `s`. Returns total items in *total.
+int upload_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint, cudaStream_t s,
+                 long long* total, int* rmax) {
+  if (n <= 0 || !frames) return FOVEA_EINVAL;
+  std::vector<FrameDesc> descs((size_t)n);
+  long long item0 = 0;
+  int rm = 0;
+  for (int i = 0; i < n; ++i) {
+    const fovea_frame& f = frames[i];
+    int st = check_frame(f.width, f.height, f.channels, f.format, ctx->B, f.sigma0, f.k, f.fix_x, f.fix_y);
+    if (st != FOVEA_OK) return st;
+    if (adjoint && f.format != FOVEA_F32_CHW) return FOVEA_EINVAL;
+    if (!f.in || !f.out) return FOVEA_EINVAL;
+    const size_t nb = frame_bytes(f.width, f.height, f.channels, f.format);
+    if (overlaps(f.in, nb, f.out, nb)) return FOVEA_EINVAL;
+    descs[(size_t)i] = make_desc(f.width, f.height, f.channels, f.format, ctx->B, f.in, f.out, f.fix_x,
+                                 f.fix_y, f.sigma0, f.k, item0);
+    item0 += (long long)descs[(size_t)i].nbx * descs[(size_t)i].nby;
+    rm = std::max(rm, radius_bound(f.width, f.height, ctx->B, f.fix_x, f.fix_y, f.sigma0, f.k));
+  }
+  if (item0 > (1ll << 31) - 1) return FOVEA_EUNSUPPORTED;
+  int st = ensure_workspace(ctx, item0);
+  if (st != FOVEA_OK) return st;
+  const size_t bytes = sizeof(BatchHeader) + (size_t)n * sizeof(FrameDesc);
+  if (bytes > ctx->batch_dev_cap) {
+    if (ctx->batch_dev) {
+      FOVEA_CUDA(cudaDeviceSynchronize());
+      cudaFree(ctx->batch_dev);
+      ctx->batch_dev = nullptr;
+      for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+      ctx->graphs.clear();
+    }
+    size_t cap = std::max<size_t>(bytes * 2, 64 * 1024);
+    FOVEA_CUDA(cudaMalloc(&ctx->batch_dev, cap));
+    ctx->batch_dev_cap = cap;
+  }
+  if (bytes > ctx->batch_host_cap) {
+    for (int i = 0; i < kBatchSlots; ++i) {
+      if (ctx->batch_ev[i]) cudaEventSynchronize(ctx->batch_ev[i]);
+      if (ctx->batch_host[i]) cudaFreeHost(ctx->batch_host[i]);
+      ctx->batch_host[i] = nullptr;
+    }
+    size_t cap = std::max<size_t>(bytes * 2, 64 * 1024);
+    for (int i = 0; i < kBatchSlots; ++i) {
+      FOVEA_CUDA(cudaHostAlloc(&ctx->batch_host[i], cap, cudaHostAllocDefault));
+      if (!ctx->batch_ev[i]) FOVEA_CUDA(cudaEventCreateWithFlags(&ctx->batch_ev[i], cudaEventDisableTiming));
+    }
+    ctx->batch_host_cap = cap;
+  }
+  const int slot = ctx->batch_slot;
+  ctx->batch_slot = (slot + 1) % kBatchSlots;
+  FOVEA_CUDA(cudaEventSynchronize(ctx->batch_ev[slot]));  // copy from this slot finished
+  BatchHeader hdr;
+  hdr.nframes = n;
+  hdr.pad = 0;
+  hdr.total_items = item0;
+  char* hbuf = static_cast<char*>(ctx->batch_host[slot]);
+  std::memcpy(hbuf, &hdr, sizeof(hdr));
+  std::memcpy(hbuf + sizeof(hdr), descs.data(), (size_t)n * sizeof(FrameDesc));
+  FOVEA_CUDA(cudaMemcpyAsync(ctx->batch_dev, hbuf, bytes, cudaMemcpyHostToDevice, s));
+  FOVEA_CUDA(cudaEventRecord(ctx->batch_ev[slot], s));
+  *total = item0;
+  *rmax = rm;
+  return FOVEA_OK;
+}
+
+FrameSource batch_source(fovea_ctx* ctx) {
+  FrameSource src;
+  std::memset(&src, 0, sizeof(src));
+  src.hdr = static_cast<const BatchHeader*>(ctx->batch_dev);
+  src.frames = reinterpret_cast<const FrameDesc*>(static_cast<const char*>(ctx->batch_dev) + sizeof(BatchHeader));
+  return src;
+}
+
+// Enqueue (or capture) the batch launch sequence for the current batch buffer.
+int enqueue_batch_kernels(fovea_ctx* ctx, bool adjoint, int rbound, cudaStream_t s) {
+  const FrameSource src = batch_source(ctx);
+  const int sg = 4 * ctx->num_sms;
+  if (adjoint) {
+    dim3 zg(64, 1);
+    // frames of a batch are at most 65535 (grid y)
+    cudaError_t e;
+    int nmax = (int)((ctx->batch_dev_cap - sizeof(BatchHeader)) / sizeof(FrameDesc));
+    zg.y = (unsigned)std::min(nmax, 65535);
+    zero_outputs_kernel<<<zg, 256, 0, s>>>(src.hdr, src.frames);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  }
+  cudaError_t e = launch_sigma_order(src, ctx->ws, sg, nullptr, nullptr, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (adjoint) {
+    int grid = adjoint_grid(ctx, rbound);
+    if (grid <= 0) return FOVEA_EUNSUPPORTED;
+    e = launch_adjoint(src, ctx->ws, rbound, grid, s);
+  } else {
+    int grid = forward_grid(ctx, rbound);
+    if (grid <= 0) return FOVEA_EUNSUPPORTED;
+    e = launch_forward(src, ctx->ws, ctx->cfg, rbound, grid, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e);
+  return FOVEA_OK;
+}
+
+int run_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint, cudaStream_t s) {
+  long long total = 0;
+  int rmax = 0;
+  int st = upload_batch(ctx, frames, n, adjoint, s, &total, &rmax);
+  if (st != FOVEA_OK) return st;
+  // Radius bound of the graph: next multiple of 64 (shared-memory size of
+  // the persistent kernel depends on it).
+  const int rbound = std::min(kMaxRadius, ((rmax + 63) / 64) * 64);
+  const auto key = std::make_pair(adjoint ? 1 : 0, rbound);
+  auto it = ctx->graphs.find(key);
+  if (it == ctx->graphs.end()) {
+    if (!ctx->capture_stream) FOVEA_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    FOVEA_CUDA(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+    st = enqueue_batch_kernels(ctx, adjoint, rbound, ctx->capture_stream);
+    cudaError_t ee = cudaStreamEndCapture(ctx->capture_stream, &g);
+    if (st != FOVEA_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (ee != cudaSuccess) return cuda_fail(ee);
+    cudaGraphExec_t ex = nullptr;
+    ee = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ee != cudaSuccess) return cuda_fail(ee);
+    it = ctx->graphs.emplace(key, ex).first;
+  }
+  FOVEA_CUDA(cudaGraphLaunch(it->second, s));
+  return FOVEA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fovea_create(int width, int height, int channels, int block, const fovea_sigma_law* law, int format,
+                 fovea_ctx** out) {
+  if (!out || !law) return FOVEA_EINVAL;
+  *out = nullptr;
+  if (law->kind != FOVEA_LAW_LINEAR) return FOVEA_EUNSUPPORTED;
+  if (!finite_nonneg(law->sigma0) || !finite_nonneg(law->k)) return FOVEA_EINVAL;
+  if (block <= 0) return FOVEA_EINVAL;
+  if (block > kMaxBlock) return FOVEA_EUNSUPPORTED;
+  if (format != FOVEA_U8_HWC && format != FOVEA_F32_CHW) return FOVEA_EINVAL;
+  const bool batch_only = width == 0 && height == 0;
+  if (!batch_only) {
+    if (width <= 0 || height <= 0) return FOVEA_EINVAL;
+    if (channels < 1 || channels > 4) return FOVEA_EINVAL;
+  }
+  fovea_ctx* ctx = new (std::nothrow) fovea_ctx();
+  if (!ctx) return FOVEA_ENOMEM;
+  ctx->W = width; ctx->H = height; ctx->C = channels; ctx->B = block; ctx->fmt = format;
+  ctx->sigma0 = law->sigma0; ctx->k = law->k;
+  ctx->batch_only = batch_only;
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return cuda_fail(e);
+  }
+  long long items = batch_only ? 1024 : (long long)((width + block - 1) / block) * ((height + block - 1) / block);
+  int st = ensure_workspace(ctx, items);
+  if (st != FOVEA_OK) {
+    fovea_destroy(ctx);
+    return st;
+  }
+  fovea_apply_cached_config(ctx);
+  *out = ctx;
+  return FOVEA_OK;
+}
+
+int fovea_render(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x, float fix_y, void* stream) {
+  if (!ctx || !in_dev || !out_dev || ctx->batch_only) return FOVEA_EINVAL;
+  int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->sigma0, ctx->k, fix_x, fix_y);
+  if (st != FOVEA_OK) return st;
+  const size_t nb = frame_bytes(ctx->W, ctx->H, ctx->C, ctx->fmt);
+  if (overlaps(in_dev, nb, out_dev, nb)) return FOVEA_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  FrameSource src;
+  std::memset(&src, 0, sizeof(src));
+  src.one = make_desc(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, in_dev, out_dev, fix_x, fix_y, ctx->sigma0, ctx->k, 0);
+  src.one_total = (long long)src.one.nbx * src.one.nby;
+  const int rmax = radius_bound(ctx->W, ctx->H, ctx->B, fix_x, fix_y, ctx->sigma0, ctx->k);
+  cudaError_t e = launch_sigma_order(src, ctx->ws, sigma_grid(src.one_total, ctx->num_sms), nullptr, nullptr, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const int grid = forward_grid(ctx, rmax);
+  if (grid <= 0) return FOVEA_EUNSUPPORTED;
+  if (ctx->kev_start) FOVEA_CUDA(cudaEventRecord(ctx->kev_start, s));
+  e = launch_forward(src, ctx->ws, ctx->cfg, rmax, grid, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (ctx->kev_stop) FOVEA_CUDA(cudaEventRecord(ctx->kev_stop, s));
+  return FOVEA_OK;
+}
+
+int fovea_render_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, void* stream) {
+  if (!ctx) return FOVEA_EINVAL;
+  return run_batch(ctx, frames, n, false, static_cast<cudaStream_t>(stream));
+}
+
+int fovea_backward_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, void* stream) {
+  if (!ctx) return FOVEA_EINVAL;
+  return run_batch(ctx, frames, n, true, static_cast<cudaStream_t>(stream));
+}
+
+int fovea_render_host(fovea_ctx* ctx, const void* in_host, void* out_host, float fix_x, float fix_y,
+                      void* stream) {
+  if (!ctx || !in_host || !out_host || ctx->batch_only) return FOVEA_EINVAL;
+  int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->sigma0, ctx->k, fix_x, fix_y);
+  if (st != FOVEA_OK) return st;
+  const size_t nb = frame_bytes(ctx->W, ctx->H, ctx->C, ctx->fmt);
+  if (overlaps(in_host, nb, out_host, nb)) return FOVEA_EINVAL;
+  if (ctx->host_io_bytes < nb) {
+    if (ctx->host_in_dev) {
+      FOVEA_CUDA(cudaDeviceSynchronize());
+      cudaFree(ctx->host_in_dev);
+      cudaFree(ctx->host_out_dev);
+      ctx->host_in_dev = ctx->host_out_dev = nullptr;
+    }
+    FOVEA_CUDA(cudaMalloc(&ctx->host_in_dev, nb));
+    FOVEA_CUDA(cudaMalloc(&ctx->host_out_dev, nb));
+    ctx->host_io_bytes = nb;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  FOVEA_CUDA(cudaMemcpyAsync(ctx->host_in_dev, in_host, nb, cudaMemcpyHostToDevice, s));
+  st = fovea_render(ctx, ctx->host_in_dev, ctx->host_out_dev, fix_x, fix_y, stream);
+  if (st != FOVEA_OK) return st;
+  FOVEA_CUDA(cudaMemcpyAsync(out_host, ctx->host_out_dev, nb, cudaMemcpyDeviceToHost, s));
+  return FOVEA_OK;
+}
+
+int fovea_backward(fovea_ctx* ctx, const float* grad_out_dev, float* grad_in_dev, float fix_x, float fix_y,
+                   void* stream) {
+  if (!ctx || !grad_out_dev || !grad_in_dev || ctx->batch_only) return FOVEA_EINVAL;
+  if (ctx->fmt != FOVEA_F32_CHW) return FOVEA_EINVAL;
+  int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->sigma0, ctx->k, fix_x, fix_y);
+  if (st != FOVEA_OK) return st;
+  const size_t nb = frame_bytes(ctx->W, ctx->H, ctx->C, ctx->fmt);
+  if (overlaps(grad_out_dev, nb, grad_in_dev, nb)) return FOVEA_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  FrameSource src;
+  std::memset(&src, 0, sizeof(src));
+  src.one = make_desc(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, grad_out_dev, grad_in_dev, fix_x, fix_y,
+                      ctx->sigma0, ctx->k, 0);
+  src.one_total = (long long)src.one.nbx * src.one.nby;
+  const int rmax = radius_bound(ctx->W, ctx->H, ctx->B, fix_x, fix_y, ctx->sigma0, ctx->k);
+  FOVEA_CUDA(cudaMemsetAsync(grad_in_dev, 0, nb, s));
+  cudaError_t e = launch_sigma_order(src, ctx->ws, sigma_grid(src.one_total, ctx->num_sms), nullptr, nullptr, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const int grid = adjoint_grid(ctx, rmax);
+  if (grid <= 0) return FOVEA_EUNSUPPORTED;
+  e = launch_adjoint(src, ctx->ws, rmax, grid, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return FOVEA_OK;
+}
+
+int fovea_sigma_table(fovea_ctx* ctx, float fix_x, float fix_y, float* sigma_dev, int* radius_dev, void* stream) {
+  if (!ctx || !sigma_dev || !radius_dev || ctx->batch_only) return FOVEA_EINVAL;
+  int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->sigma0, ctx->k, fix_x, fix_y);
+  if (st != FOVEA_OK) return st;
+  FrameSource src;
+  std::memset(&src, 0, sizeof(src));
+  src.one = make_desc(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, nullptr, nullptr, fix_x, fix_y, ctx->sigma0,
+                      ctx->k, 0);
+  src.one_total = (long long)src.one.nbx * src.one.nby;
+  cudaError_t e = launch_sigma_order(src, ctx->ws, sigma_grid(src.one_total, ctx->num_sms), sigma_dev, radius_dev,
+                                     static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e);
+  return FOVEA_OK;
+}
+
+int fovea_get_config(const fovea_ctx* ctx, fovea_config* cfg) {
+  if (!ctx || !cfg) return FOVEA_EINVAL;
+  cfg->threads = ctx->cfg.threads;
+  cfg->ctas_per_sm = ctx->cfg.ctas_per_sm;
+  cfg->rows_per_chunk = ctx->cfg.rows_per_chunk;
+  return FOVEA_OK;
+}
+
+int fovea_set_config(fovea_ctx* ctx, const fovea_config* cfg) {
+  if (!ctx || !cfg) return FOVEA_EINVAL;
+  if (cfg->threads != 256) return FOVEA_EUNSUPPORTED;
+  if (cfg->rows_per_chunk != 16 && cfg->rows_per_chunk != 32 && cfg->rows_per_chunk != 64) return FOVEA_EUNSUPPORTED;
+  if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 8) return FOVEA_EINVAL;
+  FwdConfig c{cfg->threads, cfg->ctas_per_sm, cfg->rows_per_chunk};
+  if (ctx->cfg.rows_per_chunk != c.rows_per_chunk || ctx->cfg.ctas_per_sm != c.ctas_per_sm) {
+    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    ctx->graphs.clear();
+  }
+  ctx->cfg = c;
+  return FOVEA_OK;
+}
+
+int fovea_set_kernel_events(fovea_ctx* ctx, void* ev_start, void* ev_stop) {
+  if (!ctx || (ev_start == nullptr) != (ev_stop == nullptr)) return FOVEA_EINVAL;
+  ctx->kev_start = static_cast<cudaEvent_t>(ev_start);
+  ctx->kev_stop = static_cast<cudaEvent_t>(ev_stop);
+  return FOVEA_OK;
+}
+
+void fovea_destroy(fovea_ctx* ctx) {
+  if (!ctx) return;
+  cudaDeviceSynchronize();
+  for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  cudaFree(ctx->ws.items);
+  cudaFree(ctx->ws.rank);
+  cudaFree(ctx->ws.order);
+  cudaFree(ctx->ws.counters);
+  cudaFree(ctx->batch_dev);
+  for (int i = 0; i < kBatchSlots; ++i) {
+    if (ctx->batch_host[i]) cudaFreeHost(ctx->batch_host[i]);
+    if (ctx->batch_ev[i]) cudaEventDestroy(ctx->batch_ev[i]);
+  }
+  cudaFree(ctx->host_in_dev);
+  cudaFree(ctx->host_out_dev);
+  delete ctx;
+}
+
+const char* fovea_strerror(int status) {
+  switch (status) {
+    case FOVEA_OK: return "ok";
+    case FOVEA_EINVAL: return "invalid argument";
+    case FOVEA_ENOMEM: return "out of memory";
+    case FOVEA_ECUDA: return "CUDA error";
+    case FOVEA_EBUSY: return "busy";
+    case FOVEA_ETIMEOUT: return "timed out";
+    case FOVEA_EUNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+int fovea_last_cuda_error(void) { return g_last_cuda_error; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- internals used by other units
+namespace fovea {
+
+int ctx_shape(const fovea_ctx* ctx, int* W, int* H, int* C, int* fmt, int* B) {
+  *W = ctx->W; *H = ctx->H; *C = ctx->C; *fmt = ctx->fmt; *B = ctx->B;
+  return ctx->batch_only ? FOVEA_EINVAL : FOVEA_OK;
+}
+
+int ctx_device_info(const fovea_ctx* ctx, int* device, int* num_sms) {
+  *device = ctx->device;
+  *num_sms = ctx->num_sms;
+  return FOVEA_OK;
+}
+
+}  // namespace fovea

@@ -1,0 +1,23 @@
+// Host-side helpers shared by the libfovea translation units (not exported).
+#pragma once
+
+#include <stddef.h>
+
+#include "fovea.h"
+
+namespace fovea {
+
+// Largest radius ceil(3 sigma) over the block grid of a W x H frame
+// (computed exactly as the device does for the farthest block).
+int radius_bound(int W, int H, int B, double fx, double fy, double sigma0, double k);
+// FOVEA_OK or the status a frame with these parameters is refused with.
+int check_frame(int W, int H, int C, int fmt, int B, double sigma0, double k, float fx, float fy);
+size_t frame_bytes(int W, int H, int C, int fmt);
+int ctx_shape(const fovea_ctx* ctx, int* W, int* H, int* C, int* fmt, int* B);
+int ctx_device_info(const fovea_ctx* ctx, int* device, int* num_sms);
+
+}  // namespace fovea
+
+// Applies a configuration the autotuner has already chosen for this
+// context's device and shape, if any (defined in tune.cpp).
+void fovea_apply_cached_config(fovea_ctx* ctx);

@@ -1,0 +1,187 @@
+// Internal declarations shared by the libfovea translation units.
+//
+// Work decomposition: one work ITEM is one (frame, block) pair with all of
+// its channels. A sigma-table kernel computes every item's sigma and radius,
+// a second small kernel sorts the items by radius (largest first, the
+// longest-processing-time order), and persistent kernels pull items from
+// that list through an atomic ticket counter.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "fovea.h"
+
+namespace fovea {
+
+constexpr int kMaxBlock = FOVEA_MAX_BLOCK;   // block side B <= 32
+constexpr int kMaxRadius = FOVEA_MAX_RADIUS; // r <= 1023
+constexpr int kBuckets = 1024;               // radius buckets of the work-list sort
+constexpr int kTapPad = 8;                   // zero taps stored before offset 0
+
+// One frame as the kernels see it (host fills it in; 80 bytes).
+struct FrameDesc {
+  const void* in;
+  void* out;
+  int W, H, C, fmt;        // fmt: FOVEA_U8_HWC or FOVEA_F32_CHW
+  int nbx, nby, B, pad0;   // block grid and block side
+  float fx, fy;            // fixation (pixels)
+  double sigma0, k;        // sigma law
+  long long item0;         // index of the frame's first item in a batch
+};
+
+// Device-resident batch: header followed by the frame descriptors.
+struct BatchHeader {
+  int nframes;
+  int pad;
+  long long total_items;
+};
+
+// Per-item record written by the sigma kernel.
+struct ItemInfo {
+  float sigma;             // sigma_b rounded to float
+  float neg_half_inv_s2;   // -1 / (2 sigma_b^2), rounded from binary64
+  int r;                   // ceil(3 sigma_b), clamped to kMaxRadius
+  int frame;               // frame index in the batch
+  int block;               // row-major block index within the frame
+  int pad;
+};
+
+enum {
+  CNT_TICKET = 0,     // next ticket of the persistent kernels
+  CNT_DONE_SIGMA = 1, // finished CTAs of the sigma kernel
+  CNT_DONE_ORDER = 2, // finished CTAs of the order kernel
+  CNT_NITEMS = 3,     // items of the current launch
+  CNT_ERROR = 4,      // device error flags (bit 0: radius clamped)
+  CNT_HIST = 8,       // kBuckets radius histogram
+  CNT_TOTAL = CNT_HIST + kBuckets
+};
+
+struct Workspace {
+  ItemInfo* items;         // [capacity]
+  int* rank;               // [capacity] rank of the item inside its radius bucket
+  int* order;              // [capacity] ticket -> item (radius descending)
+  unsigned int* counters;  // [CNT_TOTAL]
+  long long capacity;
+};
+
+// Where the kernels read frame descriptors from: a device-resident batch
+// (hdr != nullptr) or a single frame passed by value in the launch.
+struct FrameSource {
+  const BatchHeader* hdr;
+  const FrameDesc* frames;
+  FrameDesc one;
+  long long one_total;
+};
+
+__device__ __forceinline__ FrameDesc load_frame(const FrameSource& s, int f) {
+  return s.hdr ? s.frames[f] : s.one;
+}
+
+__device__ __forceinline__ long long source_total(const FrameSource& s) {
+  return s.hdr ? s.hdr->total_items : s.one_total;
+}
+
+// Sigma law of one block in IEEE binary64 with every operation rounded on
+// its own (no fused multiply-add), so the radius ceil(3 sigma) is reproduced
+// bit for bit by any implementation that follows the same order:
+//   centre = B*b + B/2;  e = sqrt(dx*dx + dy*dy);  sigma = sigma0 + k*e.
+__device__ __forceinline__ void block_sigma(int bx, int by, int B, double fx, double fy,
+                                            double sigma0, double k, double& sigma, int& r) {
+  double half = __dmul_rn(0.5, (double)B);
+  double cx = __dadd_rn(__dmul_rn((double)B, (double)bx), half);
+  double cy = __dadd_rn(__dmul_rn((double)B, (double)by), half);
+  double dx = __dsub_rn(cx, fx);
+  double dy = __dsub_rn(cy, fy);
+  double e = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+  sigma = __dadd_rn(sigma0, __dmul_rn(k, e));
+  r = (int)ceil(__dmul_rn(3.0, sigma));
+}
+
+// Packed two-lane FMA: d = a * b + c on both float lanes (one f32x2
+// instruction on sm_100-family GPUs).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+#if defined(FOVEA_SCALAR_FMA)
+  return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+#else
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\t"
+      "mov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+#endif
+}
+
+// Exact uint8 -> float: 2^23 + b has b in its low mantissa bits.
+__device__ __forceinline__ float u8_to_f32(unsigned int b) {
+  return __int_as_float(0x4B000000u | b) - 8388608.0f;
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Block-wide sum with warp shuffles; `red` holds >= 32 floats of shared memory.
+__device__ __forceinline__ float block_sum(float v, float* red) {
+  #pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  float s = lane < nw ? red[lane] : 0.0f;
+  #pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// Normalised taps of one item as (w, w) pairs: U[kTapPad + m] holds the tap
+// of offset m - r for m in [0, 2r]; every other entry of [0, len) is zero.
+// Eq. 1 sampled at integer offsets, truncated at r = ceil(3 sigma) and
+// normalised to unit sum. Sums with warp shuffles.
+__device__ __forceinline__ void make_taps(float2* U, int len, int r, float c, float* red) {
+  float part = 0.0f;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    int d = i - kTapPad - r;
+    float w = 0.0f;
+    if (d >= -r && d <= r) w = (d == 0) ? 1.0f : expf(c * (float)(d * d));
+    U[i].x = w;
+    part += w;
+  }
+  float S = block_sum(part, red);
+  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    float w = U[i].x / S;
+    U[i] = make_float2(w, w);
+  }
+  __syncthreads();
+}
+
+// Number of tap entries a launch needs for radius bound rmax.
+__host__ __device__ __forceinline__ int tap_len(int rmax) { return kTapPad + 2 * rmax + 24; }
+
+// ------------------------------------------------------------------ launchers
+// (defined in sigma.cu, forward.cu, adjoint.cu)
+
+struct FwdConfig {
+  int threads;        // 256
+  int ctas_per_sm;
+  int rows_per_chunk; // RB, multiple of 8
+};
+
+cudaError_t launch_sigma_order(const FrameSource& src, const Workspace& ws, int grid_ctas,
+                               float* sigma_out, int* radius_out, cudaStream_t s);
+size_t forward_smem_bytes(const FwdConfig& cfg, int rmax);
+cudaError_t launch_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg,
+                           int rmax, int grid, cudaStream_t s);
+int forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax);
+size_t adjoint_smem_bytes(int rmax);
+cudaError_t launch_adjoint(const FrameSource& src, const Workspace& ws, int rmax, int grid,
+                           cudaStream_t s);
+int adjoint_max_ctas_per_sm(int rmax);
+
+}  // namespace fovea

@@ -1,0 +1,353 @@
+// Continuous-batching request loop (serving form of the foveation path).
+//
+// Requests carry one frame in host memory. A worker thread
+//   1. admits pending requests in arrival order while their input and output
+//      buffers fit in a fixed device arena (admission by device memory) and
+//      fewer than max_inflight requests are admitted;
+//   2. copies each admitted input to the device on a copy stream;
+//   3. every tick, renders all admitted requests whose input copy has
+//      finished as ONE batch (fovea_render_batch: sigma table, cost-ordered
+//      work list, persistent kernel) on a compute stream, with at most two
+//      batches queued so requests arriving meanwhile gather into the next one;
+//   4. copies each result back to its caller's host buffer on a third stream
+//      and, once that copy is seen complete, frees the arena space.
+// The paper's per-frame loop (Algorithm 1: pinned host -> device, kernel,
+// device -> pinned host) is the special case max_batch = 1.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "fovea.h"
+#include "fovea_host.h"
+
+namespace {
+
+double now_us() {
+  using namespace std::chrono;
+  return (double)duration_cast<nanoseconds>(steady_clock::now().time_since_epoch()).count() * 1e-3;
+}
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+enum State { PENDING, ADMITTED, LAUNCHED, DONE };
+
+struct Request {
+  long long id = 0;
+  fovea_frame f{};
+  size_t bytes = 0;
+  size_t off = 0;          // arena offset of [input | output]
+  fovea_request_times t{};
+  State state = PENDING;
+  cudaEvent_t ev_in = nullptr, ev_done = nullptr;
+};
+
+// First-fit allocator over a fixed device arena (offsets only).
+class Arena {
+ public:
+  void reset(size_t size) {
+    free_.clear();
+    if (size) free_[0] = size;
+  }
+  bool alloc(size_t n, size_t* off) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        *off = it->first;
+        const size_t rest = it->second - n, start = it->first + n;
+        free_.erase(it);
+        if (rest) free_[start] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t n) {
+    auto it = free_.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+
+ private:
+  std::map<size_t, size_t> free_;
+};
+
+}  // namespace
+
+struct fovea_server {
+  fovea_server_config cfg{};
+  int device = 0;
+  char* arena_base = nullptr;
+  Arena arena;
+  fovea_ctx* ctx = nullptr;
+  cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
+  std::vector<cudaEvent_t> event_pool;
+  std::deque<cudaEvent_t> batch_events;  // renders queued on s_comp
+  std::mutex mu;
+  std::condition_variable cv_done, cv_work;
+  std::deque<Request*> pending;
+  std::vector<Request*> admitted;  // state ADMITTED
+  std::vector<Request*> launched;  // state LAUNCHED
+  std::unordered_map<long long, Request*> all;
+  long long next_id = 0;
+  bool stop = false;
+  std::thread worker;
+
+  cudaEvent_t get_event() {
+    if (!event_pool.empty()) {
+      cudaEvent_t e = event_pool.back();
+      event_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    return e;
+  }
+
+  void finish(Request* r, int status) {
+    r->t.done_us = now_us();
+    r->t.status = status;
+    if (r->state == ADMITTED || r->state == LAUNCHED) arena.release(r->off, 2 * align_up(r->bytes));
+    r->state = DONE;
+    if (r->ev_in) event_pool.push_back(r->ev_in);
+    if (r->ev_done) event_pool.push_back(r->ev_done);
+    r->ev_in = r->ev_done = nullptr;
+  }
+
+  void run();
+};
+
+void fovea_server::run() {
+  cudaSetDevice(device);
+  std::vector<Request*> fresh, ready;
+  std::vector<fovea_frame> frames;
+  for (;;) {
+    bool progressed = false;
+    fresh.clear();
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      if (stop && pending.empty() && admitted.empty() && launched.empty()) break;
+      while (!pending.empty() && (int)(admitted.size() + launched.size()) < cfg.max_inflight) {
+        Request* r = pending.front();
+        size_t off = 0;
+        if (!arena.alloc(2 * align_up(r->bytes), &off)) break;  // wait for memory to free up
+        pending.pop_front();
+        r->off = off;
+        r->state = ADMITTED;
+        r->t.admit_us = now_us();
+        r->ev_in = get_event();
+        r->ev_done = get_event();
+        admitted.push_back(r);
+        fresh.push_back(r);
+      }
+    }
+    for (Request* r : fresh) {  // input copies on the copy stream
+      cudaMemcpyAsync(arena_base + r->off, r->f.in, r->bytes, cudaMemcpyHostToDevice, s_in);
+      cudaEventRecord(r->ev_in, s_in);
+      progressed = true;
+    }
+    // retire finished renders so at most two batches queue on the compute stream
+    while (!batch_events.empty() && cudaEventQuery(batch_events.front()) == cudaSuccess) {
+      std::lock_guard<std::mutex> lk(mu);
+      event_pool.push_back(batch_events.front());
+      batch_events.pop_front();
+    }
+    if (batch_events.size() < 2) {
+      ready.clear();
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        for (size_t i = 0; i < admitted.size() && (int)ready.size() < cfg.max_batch;) {
+          Request* r = admitted[i];
+          if (cudaEventQuery(r->ev_in) == cudaSuccess) {
+            ready.push_back(r);
+            admitted.erase(admitted.begin() + (long)i);
+          } else {
+            ++i;
+          }
+        }
+      }
+      if (!ready.empty()) {
+        frames.resize(ready.size());
+        for (size_t i = 0; i < ready.size(); ++i) {
+          fovea_frame f = ready[i]->f;
+          f.in = arena_base + ready[i]->off;
+          f.out = arena_base + ready[i]->off + align_up(ready[i]->bytes);
+          frames[i] = f;
+        }
+        const double t0 = now_us();
+        const int st = fovea_render_batch(ctx, frames.data(), (int)frames.size(), s_comp);
+        cudaEvent_t eb = nullptr;
+        {
+          std::lock_guard<std::mutex> lk(mu);
+          eb = get_event();
+        }
+        cudaEventRecord(eb, s_comp);
+        batch_events.push_back(eb);
+        cudaStreamWaitEvent(s_out, eb, 0);
+        std::lock_guard<std::mutex> lk(mu);
+        for (Request* r : ready) {
+          r->t.start_us = t0;
+          r->t.batch_size = (int)ready.size();
+          if (st != FOVEA_OK) {
+            finish(r, st);
+            continue;
+          }
+          cudaMemcpyAsync(r->f.out, arena_base + r->off + align_up(r->bytes), r->bytes, cudaMemcpyDeviceToHost, s_out);
+          cudaEventRecord(r->ev_done, s_out);
+          r->state = LAUNCHED;
+          launched.push_back(r);
+        }
+        if (st != FOVEA_OK) cv_done.notify_all();
+        progressed = true;
+      }
+    }
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      bool any = false;
+      for (size_t i = 0; i < launched.size();) {
+        Request* r = launched[i];
+        if (cudaEventQuery(r->ev_done) == cudaSuccess) {
+          finish(r, FOVEA_OK);
+          launched.erase(launched.begin() + (long)i);
+          any = true;
+        } else {
+          ++i;
+        }
+      }
+      if (any) {
+        cv_done.notify_all();
+        progressed = true;
+      }
+    }
+    if (!progressed) {
+      std::unique_lock<std::mutex> lk(mu);
+      if (pending.empty() && admitted.empty() && launched.empty() && !stop)
+        cv_work.wait_for(lk, std::chrono::milliseconds(5));
+      else {
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+      }
+    }
+  }
+}
+
+extern "C" {
+
+double fovea_server_now_us(void) { return now_us(); }
+
+int fovea_server_create(const fovea_server_config* cfg, fovea_server** out) {
+  if (!cfg || !out) return FOVEA_EINVAL;
+  *out = nullptr;
+  if (cfg->device_budget_bytes < 2 * kAlign || cfg->max_batch <= 0 || cfg->max_inflight <= 0 || cfg->block <= 0)
+    return FOVEA_EINVAL;
+  fovea_server* s = new (std::nothrow) fovea_server();
+  if (!s) return FOVEA_ENOMEM;
+  s->cfg = *cfg;
+  if (cudaGetDevice(&s->device) != cudaSuccess ||
+      cudaMalloc(&s->arena_base, cfg->device_budget_bytes) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->s_in, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->s_comp, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->s_out, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    fovea_server_destroy(s);
+    return FOVEA_ENOMEM;
+  }
+  s->arena.reset(cfg->device_budget_bytes);
+  fovea_sigma_law law{FOVEA_LAW_LINEAR, 0.5, 0.02};
+  int st = fovea_create(0, 0, 3, cfg->block, &law, FOVEA_U8_HWC, &s->ctx);
+  if (st != FOVEA_OK) {
+    fovea_server_destroy(s);
+    return st;
+  }
+  s->worker = std::thread([s] { s->run(); });
+  *out = s;
+  return FOVEA_OK;
+}
+
+long long fovea_server_submit(fovea_server* s, const fovea_frame* f, double arrival_us) {
+  if (!s || !f || !f->in || !f->out) return FOVEA_EINVAL;
+  const int st = fovea::check_frame(f->width, f->height, f->channels, f->format, s->cfg.block, f->sigma0, f->k,
+                                    f->fix_x, f->fix_y);
+  if (st != FOVEA_OK) return st;
+  const size_t bytes = fovea::frame_bytes(f->width, f->height, f->channels, f->format);
+  if (2 * align_up(bytes) > s->cfg.device_budget_bytes) return FOVEA_EBUSY;
+  Request* r = new (std::nothrow) Request();
+  if (!r) return FOVEA_ENOMEM;
+  r->f = *f;
+  r->bytes = bytes;
+  r->t.arrival_us = arrival_us;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->stop) {
+    delete r;
+    return FOVEA_EINVAL;
+  }
+  r->id = s->next_id++;
+  s->all[r->id] = r;
+  s->pending.push_back(r);
+  s->cv_work.notify_one();
+  return r->id;
+}
+
+int fovea_server_wait(fovea_server* s, long long id, int timeout_ms, fovea_request_times* times) {
+  if (!s) return FOVEA_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->all.find(id);
+  if (it == s->all.end()) return FOVEA_EINVAL;
+  Request* r = it->second;
+  if (r->state != DONE) {
+    if (timeout_ms <= 0) return FOVEA_ETIMEOUT;
+    s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [r] { return r->state == DONE; });
+    if (r->state != DONE) return FOVEA_ETIMEOUT;
+  }
+  if (times) *times = r->t;
+  s->all.erase(it);
+  delete r;
+  return FOVEA_OK;
+}
+
+void fovea_server_destroy(fovea_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  if (s->s_in) cudaStreamSynchronize(s->s_in);
+  if (s->s_comp) cudaStreamSynchronize(s->s_comp);
+  if (s->s_out) cudaStreamSynchronize(s->s_out);
+  for (auto& kv : s->all) {
+    Request* r = kv.second;
+    if (r->ev_in) cudaEventDestroy(r->ev_in);
+    if (r->ev_done) cudaEventDestroy(r->ev_done);
+    delete r;
+  }
+  for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : s->batch_events) cudaEventDestroy(e);
+  if (s->ctx) fovea_destroy(s->ctx);
+  if (s->s_in) cudaStreamDestroy(s->s_in);
+  if (s->s_comp) cudaStreamDestroy(s->s_comp);
+  if (s->s_out) cudaStreamDestroy(s->s_out);
+  cudaFree(s->arena_base);
+  delete s;
+}
+
+}  // extern "C"

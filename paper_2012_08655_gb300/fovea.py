@@ -1,0 +1,392 @@
+"""Thin ctypes binding of libfovea (``include/fovea.h``) plus autograd glue.
+
+Every step of the foveation path runs in the library's CUDA kernels; this
+module only marshals arguments (device pointers of torch tensors, the
+current CUDA stream) and raises on error. There is no CPU fallback: if
+``libfovea.so`` has not been built, importing this module raises.
+
+Paper: "CUDA-Optimized real-time rendering of a Foveated Visual System"
+(arXiv 2012.08655), Section 2 and Algorithm 1 (block-wise foveation), Eq. 1
+(the Gaussian filter) and Appendix "Choosing the Standard Deviation" (sigma
+law, here sigma = sigma0 + k * eccentricity in pixels).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfovea.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"libfovea.so is missing at {LIB_PATH}; build it with "
+        "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+U8_HWC, F32_CHW = 0, 1
+MAX_RADIUS = 1023
+MAX_BLOCK = 32
+
+
+class SigmaLaw(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("sigma0", ctypes.c_double), ("k", ctypes.c_double)]
+
+
+class Frame(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("channels", ctypes.c_int),
+                ("format", ctypes.c_int), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("fix_x", ctypes.c_float), ("fix_y", ctypes.c_float),
+                ("sigma0", ctypes.c_double), ("k", ctypes.c_double)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("rows_per_chunk", ctypes.c_int)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device_budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int),
+                ("block", ctypes.c_int), ("max_inflight", ctypes.c_int)]
+
+
+class RequestTimes(ctypes.Structure):
+    _fields_ = [("arrival_us", ctypes.c_double), ("admit_us", ctypes.c_double),
+                ("start_us", ctypes.c_double), ("done_us", ctypes.c_double),
+                ("batch_size", ctypes.c_int), ("status", ctypes.c_int)]
+
+
+_vp, _i, _f, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_double
+_sig = {
+    "fovea_create": (_i, [_i, _i, _i, _i, ctypes.POINTER(SigmaLaw), _i, ctypes.POINTER(_vp)]),
+    "fovea_render": (_i, [_vp, _vp, _vp, _f, _f, _vp]),
+    "fovea_render_batch": (_i, [_vp, ctypes.POINTER(Frame), _i, _vp]),
+    "fovea_render_host": (_i, [_vp, _vp, _vp, _f, _f, _vp]),
+    "fovea_backward": (_i, [_vp, _vp, _vp, _f, _f, _vp]),
+    "fovea_backward_batch": (_i, [_vp, ctypes.POINTER(Frame), _i, _vp]),
+    "fovea_sigma_table": (_i, [_vp, _f, _f, _vp, _vp, _vp]),
+    "fovea_get_config": (_i, [_vp, ctypes.POINTER(Config)]),
+    "fovea_set_config": (_i, [_vp, ctypes.POINTER(Config)]),
+    "fovea_autotune": (_i, [_vp, _i, ctypes.c_char_p]),
+    "fovea_set_kernel_events": (_i, [_vp, _vp, _vp]),
+    "fovea_destroy": (None, [_vp]),
+    "fovea_strerror": (ctypes.c_char_p, [_i]),
+    "fovea_last_cuda_error": (_i, []),
+    "fovea_server_create": (_i, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)]),
+    "fovea_server_submit": (ctypes.c_longlong, [_vp, ctypes.POINTER(Frame), _d]),
+    "fovea_server_wait": (_i, [_vp, ctypes.c_longlong, _i, ctypes.POINTER(RequestTimes)]),
+    "fovea_server_now_us": (_d, []),
+    "fovea_server_destroy": (None, [_vp]),
+}
+for _name, (_res, _args) in _sig.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+class FoveaError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = _lib.fovea_strerror(status).decode()
+        if status == ECUDA:
+            msg += f" (cudaError {_lib.fovea_last_cuda_error()})"
+        super().__init__(f"{what}: {msg} [{status}]")
+        self.status = status
+
+
+def _check(status: int, what: str) -> int:
+    if status < 0:
+        raise FoveaError(status, what)
+    return status
+
+
+def _stream_handle(stream: Optional[torch.cuda.Stream]) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _fmt_of(t: torch.Tensor) -> int:
+    if t.dtype == torch.uint8:
+        return U8_HWC
+    if t.dtype == torch.float32:
+        return F32_CHW
+    raise TypeError(f"unsupported dtype {t.dtype}: uint8 (HWC) or float32 (CHW)")
+
+
+def _shape_of(t: torch.Tensor, fmt: int):
+    """(W, H, C) of one frame tensor: uint8 (H, W[, C]) or float32 ([C,] H, W)."""
+    if t.dim() == 2:
+        h, w = t.shape
+        return w, h, 1
+    if t.dim() != 3:
+        raise ValueError(f"one frame must be 2-D or 3-D, got shape {tuple(t.shape)}")
+    if fmt == U8_HWC:
+        h, w, c = t.shape
+    else:
+        c, h, w = t.shape
+    return w, h, c
+
+
+def _require_device_frame(t: torch.Tensor, name: str):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Context:
+    """One fovea context (``fovea_create``): frame shape, format, block side, sigma law."""
+
+    def __init__(self, width: int, height: int, channels: int, block: int = 32,
+                 sigma0: float = 0.5, k: float = 0.02, fmt: int = U8_HWC):
+        law = SigmaLaw(0, float(sigma0), float(k))
+        h = _vp()
+        _check(_lib.fovea_create(int(width), int(height), int(channels), int(block), ctypes.byref(law),
+                                 int(fmt), ctypes.byref(h)), "fovea_create")
+        self._h = h
+        self.width, self.height, self.channels, self.block = int(width), int(height), int(channels), int(block)
+        self.sigma0, self.k, self.fmt = float(sigma0), float(k), int(fmt)
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.fovea_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---------------------------------------------------------------- calls
+    def render(self, inp: torch.Tensor, out: torch.Tensor, fix_x: float, fix_y: float, stream=None):
+        _require_device_frame(inp, "input")
+        _require_device_frame(out, "output")
+        _check(_lib.fovea_render(self._h, inp.data_ptr(), out.data_ptr(), float(fix_x), float(fix_y),
+                                 _stream_handle(stream)), "fovea_render")
+        return out
+
+    def render_host(self, inp: torch.Tensor, out: torch.Tensor, fix_x: float, fix_y: float, stream=None):
+        if inp.is_cuda or out.is_cuda:
+            raise ValueError("render_host takes host (preferably pinned) tensors")
+        _check(_lib.fovea_render_host(self._h, inp.data_ptr(), out.data_ptr(), float(fix_x), float(fix_y),
+                                      _stream_handle(stream)), "fovea_render_host")
+        return out
+
+    def backward(self, grad_out: torch.Tensor, grad_in: torch.Tensor, fix_x: float, fix_y: float, stream=None):
+        _require_device_frame(grad_out, "grad_out")
+        _require_device_frame(grad_in, "grad_in")
+        _check(_lib.fovea_backward(self._h, grad_out.data_ptr(), grad_in.data_ptr(), float(fix_x), float(fix_y),
+                                   _stream_handle(stream)), "fovea_backward")
+        return grad_in
+
+    def sigma_table(self, fix_x: float, fix_y: float, stream=None):
+        nby = (self.height + self.block - 1) // self.block
+        nbx = (self.width + self.block - 1) // self.block
+        sig = torch.empty((nby, nbx), dtype=torch.float32, device="cuda")
+        rad = torch.empty((nby, nbx), dtype=torch.int32, device="cuda")
+        _check(_lib.fovea_sigma_table(self._h, float(fix_x), float(fix_y), sig.data_ptr(), rad.data_ptr(),
+                                      _stream_handle(stream)), "fovea_sigma_table")
+        return sig, rad
+
+    def render_batch(self, frames: Sequence["BatchFrame"], stream=None):
+        arr = _frames_array(frames)
+        _check(_lib.fovea_render_batch(self._h, arr, len(frames), _stream_handle(stream)), "fovea_render_batch")
+
+    def backward_batch(self, frames: Sequence["BatchFrame"], stream=None):
+        arr = _frames_array(frames)
+        _check(_lib.fovea_backward_batch(self._h, arr, len(frames), _stream_handle(stream)), "fovea_backward_batch")
+
+    def set_kernel_events(self, start: Optional[torch.cuda.Event], stop: Optional[torch.cuda.Event]):
+        """Bracket the persistent blur kernel of later renders with these events."""
+        a = start.cuda_event if start is not None else None
+        b = stop.cuda_event if stop is not None else None
+        _check(_lib.fovea_set_kernel_events(self._h, a, b), "fovea_set_kernel_events")
+
+    def get_config(self) -> dict:
+        c = Config()
+        _check(_lib.fovea_get_config(self._h, ctypes.byref(c)), "fovea_get_config")
+        return {"threads": c.threads, "ctas_per_sm": c.ctas_per_sm, "rows_per_chunk": c.rows_per_chunk}
+
+    def set_config(self, threads=256, ctas_per_sm=0, rows_per_chunk=32):
+        c = Config(int(threads), int(ctas_per_sm), int(rows_per_chunk))
+        _check(_lib.fovea_set_config(self._h, ctypes.byref(c)), "fovea_set_config")
+
+    def autotune(self, iters: int = 20, cache_path: Optional[str] = None) -> dict:
+        p = cache_path.encode() if cache_path else None
+        _check(_lib.fovea_autotune(self._h, int(iters), p), "fovea_autotune")
+        return self.get_config()
+
+
+def batch_context(block: int = 32) -> Context:
+    """A batch-only context (``fovea_create`` with width = height = 0)."""
+    return Context(0, 0, 3, block)
+
+
+@dataclass
+class BatchFrame:
+    inp: torch.Tensor
+    out: torch.Tensor
+    fix_x: float
+    fix_y: float
+    sigma0: float
+    k: float
+
+
+def _frames_array(frames: Sequence[BatchFrame]):
+    if len(frames) == 0:
+        raise ValueError("empty batch")
+    arr = (Frame * len(frames))()
+    keep = []
+    for i, fr in enumerate(frames):
+        _require_device_frame(fr.inp, f"frame {i} input")
+        _require_device_frame(fr.out, f"frame {i} output")
+        fmt = _fmt_of(fr.inp)
+        w, h, c = _shape_of(fr.inp, fmt)
+        arr[i] = Frame(w, h, c, fmt, fr.inp.data_ptr(), fr.out.data_ptr(), float(fr.fix_x), float(fr.fix_y),
+                       float(fr.sigma0), float(fr.k))
+        keep.append(fr)
+    return arr
+
+
+# ------------------------------------------------------------------ functional API
+_ctx_cache: dict = {}
+
+
+def _ctx_for(w, h, c, block, sigma0, k, fmt) -> Context:
+    key = (torch.cuda.current_device(), w, h, c, block, float(sigma0), float(k), fmt)
+    ctx = _ctx_cache.get(key)
+    if ctx is None:
+        ctx = Context(w, h, c, block, sigma0, k, fmt)
+        _ctx_cache[key] = ctx
+    return ctx
+
+
+def foveate(x: torch.Tensor, fix_x: float, fix_y: float, sigma0: float = 0.5, k: float = 0.02,
+            block: int = 32, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Foveate one frame: uint8 (H, W[, C]) or float32 ([C,] H, W), on the GPU."""
+    _require_device_frame(x, "input")
+    fmt = _fmt_of(x)
+    w, h, c = _shape_of(x, fmt)
+    ctx = _ctx_for(w, h, c, block, sigma0, k, fmt)
+    if out is None:
+        out = torch.empty_like(x)
+    return ctx.render(x, out, fix_x, fix_y)
+
+
+def sigma_table(width: int, height: int, fix_x: float, fix_y: float, sigma0: float = 0.5, k: float = 0.02,
+                block: int = 32):
+    """Per-block (sigma float32, radius int32) computed by the sigma-table kernel."""
+    return _ctx_for(width, height, 1, block, sigma0, k, F32_CHW).sigma_table(fix_x, fix_y)
+
+
+def _batch_ctx(block: int) -> Context:
+    key = ("batch", torch.cuda.current_device(), block)
+    ctx = _ctx_cache.get(key)
+    if ctx is None:
+        ctx = batch_context(block)
+        _ctx_cache[key] = ctx
+    return ctx
+
+
+def foveate_batch(frames: Sequence[BatchFrame], block: int = 32, stream=None):
+    """Render frames of mixed sizes in one batched launch sequence."""
+    _batch_ctx(block).render_batch(frames, stream)
+
+
+class FoveaFunction(torch.autograd.Function):
+    """Differentiable foveation of a float32 batch [N, C, H, W] with per-image fixations.
+
+    Forward: ``fovea_render_batch``; backward: ``fovea_backward_batch`` (the
+    adjoint kernel). Gradients flow to the images only (the fixation and the
+    sigma law are constants).
+    """
+
+    @staticmethod
+    def forward(ctx, x: torch.Tensor, fix: torch.Tensor, sigma0: float, k: float, block: int):
+        if x.dtype != torch.float32 or x.dim() != 4:
+            raise ValueError("FoveaFunction takes float32 [N, C, H, W]")
+        x = x.contiguous()
+        fixes = [(float(a), float(b)) for a, b in fix.detach().cpu().tolist()]
+        y = torch.empty_like(x)
+        frames = [BatchFrame(x[i], y[i], fx, fy, sigma0, k) for i, (fx, fy) in enumerate(fixes)]
+        _batch_ctx(block).render_batch(frames)
+        ctx.fixes, ctx.sigma0, ctx.k, ctx.block = fixes, sigma0, k, block
+        return y
+
+    @staticmethod
+    def backward(ctx, gy: torch.Tensor):
+        gy = gy.contiguous()
+        gx = torch.empty_like(gy)
+        frames = [BatchFrame(gy[i], gx[i], fx, fy, ctx.sigma0, ctx.k) for i, (fx, fy) in enumerate(ctx.fixes)]
+        _batch_ctx(ctx.block).backward_batch(frames)
+        return gx, None, None, None, None
+
+
+def foveate_train(x: torch.Tensor, fix: torch.Tensor, sigma0: float = 0.5, k: float = 0.08,
+                  block: int = 32) -> torch.Tensor:
+    """Differentiable foveation of x [N, C, H, W] float32 at fixations fix [N, 2] (x, y)."""
+    return FoveaFunction.apply(x, fix, sigma0, k, block)
+
+
+# ------------------------------------------------------------------ serving
+class Server:
+    """Continuous-batching request loop (``fovea_server_*``)."""
+
+    def __init__(self, device_budget_bytes: int = 1 << 30, max_batch: int = 64, block: int = 32,
+                 max_inflight: int = 256):
+        cfg = ServerConfig(int(device_budget_bytes), int(max_batch), int(block), int(max_inflight))
+        h = _vp()
+        _check(_lib.fovea_server_create(ctypes.byref(cfg), ctypes.byref(h)), "fovea_server_create")
+        self._h = h
+
+    @staticmethod
+    def now_us() -> float:
+        return float(_lib.fovea_server_now_us())
+
+    def submit(self, inp: torch.Tensor, out: torch.Tensor, fix_x: float, fix_y: float, sigma0: float,
+               k: float, arrival_us: Optional[float] = None) -> int:
+        if inp.is_cuda or out.is_cuda:
+            raise ValueError("the server takes host (preferably pinned) frames")
+        fmt = _fmt_of(inp)
+        w, h, c = _shape_of(inp, fmt)
+        fr = Frame(w, h, c, fmt, inp.data_ptr(), out.data_ptr(), float(fix_x), float(fix_y), float(sigma0), float(k))
+        t = self.now_us() if arrival_us is None else float(arrival_us)
+        return _check(int(_lib.fovea_server_submit(self._h, ctypes.byref(fr), t)), "fovea_server_submit")
+
+    def wait(self, rid: int, timeout_ms: int = 10000) -> dict:
+        t = RequestTimes()
+        _check(_lib.fovea_server_wait(self._h, int(rid), int(timeout_ms), ctypes.byref(t)), "fovea_server_wait")
+        return {"arrival_us": t.arrival_us, "admit_us": t.admit_us, "start_us": t.start_us,
+                "done_us": t.done_us, "batch_size": t.batch_size, "status": t.status}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.fovea_server_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,69 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+function that include/fovea.h declares. Only argument checks that return
+before touching CUDA are exercised here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fovea.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2012_08655_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w \*]*?\b(fovea_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["fovea_create", "fovea_render", "fovea_render_batch", "fovea_backward",
+                     "fovea_destroy", "fovea_strerror", "fovea_sigma_table", "fovea_render_host"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"libfovea.so lacks {missing}"
+
+
+def test_strerror_and_invalid_arguments(lib):
+    lib.fovea_strerror.restype = ctypes.c_char_p
+    assert lib.fovea_strerror(0) == b"ok"
+    assert lib.fovea_strerror(-1) == b"invalid argument"
+    assert lib.fovea_strerror(-6) == b"unsupported"
+
+    class Law(ctypes.Structure):
+        _fields_ = [("kind", ctypes.c_int), ("sigma0", ctypes.c_double), ("k", ctypes.c_double)]
+
+    h = ctypes.c_void_p()
+    create = lib.fovea_create
+    create.argtypes = [ctypes.c_int] * 4 + [ctypes.POINTER(Law), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+    good = Law(0, 0.5, 0.02)
+    assert create(64, 64, 3, 32, None, 0, ctypes.byref(h)) == -1           # null law
+    assert create(64, 64, 3, 0, ctypes.byref(good), 0, ctypes.byref(h)) == -1   # block <= 0
+    assert create(64, 64, 3, 64, ctypes.byref(good), 0, ctypes.byref(h)) == -6  # block > 32
+    assert create(64, 64, 5, 32, ctypes.byref(good), 0, ctypes.byref(h)) == -1  # channels
+    assert create(64, 64, 3, 32, ctypes.byref(good), 7, ctypes.byref(h)) == -1  # format
+    assert create(64, 64, 3, 32, ctypes.byref(Law(0, -1.0, 0.02)), 0, ctypes.byref(h)) == -1
+    assert create(64, 64, 3, 32, ctypes.byref(Law(0, 0.5, float("nan"))), 0, ctypes.byref(h)) == -1
+    assert create(64, 64, 3, 32, ctypes.byref(Law(3, 0.5, 0.02)), 0, ctypes.byref(h)) == -6
+    assert create(-4, 64, 3, 32, ctypes.byref(good), 0, ctypes.byref(h)) == -1
+    assert h.value is None
+    lib.fovea_render.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_float] * 2 + [ctypes.c_void_p]
+    assert lib.fovea_render(None, None, None, 1.0, 1.0, None) == -1
+
+
+def test_python_binding_imports_without_gpu():
+    from paper_2012_08655_gb300 import fovea
+    assert fovea.MAX_RADIUS == 1023
