@@ -60,6 +60,7 @@ def parse_args():
     p.add_argument("--no-extras", action="store_true", help="skip the batched and served legs")
     p.add_argument("--served-seconds", type=float, default=10.0)
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiling runs)")
     return p.parse_args()
 
 
@@ -391,6 +392,10 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     ev_k = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in ev_k:  # torch creates the CUDA events on first record
+        a.record(stream)
+        b.record(stream)
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(gpu_uuid(dev))
     sampler.start()
@@ -456,7 +461,7 @@ def run_ours(args):
         served["plain_per_frame"] = {k: plain[k] for k in ("p50_ms", "p99_ms", "mpix_s", "mean_batch")}
         extras["served"] = served
 
-    cpu = cpu_oracle_sample() if (rank == 0 and world == 1) else None
+    cpu = cpu_oracle_sample() if (rank == 0 and world == 1 and not args.no_cpu) else None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -8,9 +8,12 @@
 //   Z[yo][tx]  = sum_xo u[tx - xo] * g[yo][xo]      (horizontal, transposed)
 //   gT[ty][tx] = sum_yo u[ty - yo] * Z[yo][tx]      (vertical, transposed)
 //   g_in[clamp(y0-r+ty)][clamp(x0-r+tx)] += gT[ty][tx]
-// Tiles of neighbouring blocks overlap, so the last step is a global atomic
-// add (fp32; the summation order is not fixed, so results are reproducible to
-// rounding, not bit for bit). Not in the paper: it exists so the blur can sit
+// The tile is folded as in the forward kernel: only in-frame rows and columns
+// are formed, and the clamped taps of the edge row / column are summed into
+// one prefix-summed weight, so every frame pixel receives exactly one
+// contribution per block. Tiles of neighbouring blocks overlap, so that
+// contribution is a global atomic add (fp32; the summation order is not
+// fixed, so results are reproducible to rounding, not bit for bit). Not in the paper: it exists so the blur can sit
 // inside network training (a torch.autograd.Function uses it).
 #include "fovea_internal.cuh"
 
@@ -24,26 +27,28 @@ constexpr int kZPitch = kSlabPx + 4;   // float pitch of Z (multiple of 4 for fl
 constexpr int kGPitch = 33;            // float2 pitch of the row-pair gradient block (odd)
 
 struct SmemLayout {
-  size_t gg, z, taps, red, total;
+  size_t gg, z, taps, cum, red, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int ulen) {
+__host__ __device__ inline SmemLayout smem_layout(int rmax) {
   SmemLayout L;
   L.gg = 0;                                                // float2 [4][16][kGPitch]
   L.z = L.gg + (size_t)4 * 16 * kGPitch * sizeof(float2);  // float [32][kZPitch]
-  L.taps = L.z + (size_t)32 * kZPitch * sizeof(float);     // float2 [ulen]
-  L.red = L.taps + (size_t)ulen * sizeof(float2);          // float [32]
+  L.taps = L.z + (size_t)32 * kZPitch * sizeof(float);     // float2 [tap_len]
+  L.cum = L.taps + (size_t)tap_len(rmax) * sizeof(float2); // float [cum_len]
+  L.red = L.cum + (size_t)cum_len(rmax) * sizeof(float);   // float [32]
   L.total = L.red + 32 * sizeof(float);
   return L;
 }
 
 __global__ void __launch_bounds__(kThreads, 2)
-adjoint_kernel(FrameSource src, Workspace ws, int ulen_max) {
+adjoint_kernel(FrameSource src, Workspace ws, int rmax) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const SmemLayout L = smem_layout(ulen_max);
+  const SmemLayout L = smem_layout(rmax);
   float2* GG = reinterpret_cast<float2*>(smem + L.gg);
   float* Z = reinterpret_cast<float*>(smem + L.z);
   float2* U = reinterpret_cast<float2*>(smem + L.taps);
+  float* CU = reinterpret_cast<float*>(smem + L.cum);
   float* red = reinterpret_cast<float*>(smem + L.red);
   __shared__ int s_ticket;
 
@@ -64,8 +69,7 @@ adjoint_kernel(FrameSource src, Workspace ws, int ulen_max) {
     const ItemInfo inf = ws.items[item];
     const FrameDesc fd = load_frame(src, inf.frame);
     const int r = inf.r;
-    const int ulen = tap_len(r);
-    if (ulen > ulen_max || fd.fmt != FOVEA_F32_CHW || fd.C > 4) {
+    if (r > rmax || fd.fmt != FOVEA_F32_CHW || fd.C > 4) {
       if (tid == 0) atomicOr(&ws.counters[CNT_ERROR], 4u);
       continue;
     }
@@ -73,11 +77,18 @@ adjoint_kernel(FrameSource src, Workspace ws, int ulen_max) {
     const int bx = inf.block % fd.nbx, by = inf.block / fd.nbx;
     const int x0 = bx * B, y0 = by * B;
     const int bw = min(B, W - x0), bh = min(B, H - y0);
-    const int planePitch = W * H;
+    // Folded tile: frame columns gx0 .. gx0+EW-1 and rows gy0 .. gy0+EH-1; the
+    // tap index of (tile column ex, block column xo) is offx + ex - xo.
+    const int gx0 = max(0, x0 - r), EW = min(W - 1, x0 + bw - 1 + r) - gx0 + 1, offx = gx0 - (x0 - r);
+    const int gy0 = max(0, y0 - r), EH = min(H - 1, y0 + bh - 1 + r) - gy0 + 1, offy = gy0 - (y0 - r);
+    const bool foldL = x0 - r < 0, foldR = x0 + bw - 1 + r > W - 1;
+    const bool foldT = y0 - r < 0, foldB = y0 + bh - 1 + r > H - 1;
+    const size_t planePitch = (size_t)W * H;
     const float* gout = static_cast<const float*>(fd.in);
     float* gin = static_cast<float*>(fd.out);
 
-    make_taps(U, ulen, r, inf.neg_half_inv_s2, red);
+    make_taps(U, tap_len(r), r, inf.neg_half_inv_s2, red);
+    make_cumulative(U, CU, r);
 
     // Output-gradient block as row pairs, zero outside the block.
     float* GGf = reinterpret_cast<float*>(GG);
@@ -89,36 +100,48 @@ adjoint_kernel(FrameSource src, Workspace ws, int ulen_max) {
     }
     __syncthreads();
 
-    const int tileW = bw + 2 * r, tileH = bh + 2 * r;
-    const int nh = (tileH + 7) >> 3;
+    const int nh = (EH + 7) >> 3;
     for (int c = 0; c < C; ++c) {
-      for (int X0 = 0; X0 < tileW; X0 += kSlabPx) {
-        const int SWx = min(kSlabPx, tileW - X0);
-        // ---- pass A: Z[yo][tx - X0] for the slab, items (row pair p, 8-column group)
+      for (int X0 = 0; X0 < EW; X0 += kSlabPx) {
+        const int SWx = min(kSlabPx, EW - X0);
+        // ---- pass A: Z[yo][ex - X0] = sum_xo w(ex, xo) g[yo][xo]
         const int ngA = (SWx + 7) >> 3;
         for (int it = tid; it < 16 * ngA; it += kThreads) {
           const int p = it & 15, g = it >> 4;
-          const int txg = X0 + 8 * g;
-          // k = txg - xo; data needs xo in [0, bw); taps need k + j in [0, 2r].
-          const int klo = max(txg - bw + 1, -7), khi = min(txg, 2 * r);
+          const int tg = offx + X0 + 8 * g;   // tap index of (ex = X0 + 8g, xo = 0)
+          const int klo = max(tg - bw + 1, -7), khi = min(tg, 2 * r);
           float2 acc[8];
           #pragma unroll
           for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.f, 0.f);
+          const float2* grow = GG + (c * 16 + p) * kGPitch;
           if (klo <= khi) {
             const int k0 = klo >= 0 ? (klo & ~7) : -8;
             float2 w[8];
             #pragma unroll
             for (int s = 0; s < 7; ++s) w[s] = U[kTapPad + k0 + s];
-            const float2* grow = GG + (c * 16 + p) * kGPitch;
             for (int kb = k0; kb <= khi; kb += 8) {
               #pragma unroll
               for (int s = 0; s < 8; ++s) {
                 const int kk = kb + s;
                 w[(s + 7) & 7] = U[kTapPad + kk + 7];
                 float2 d = make_float2(0.f, 0.f);
-                if (kk >= klo && kk <= khi) d = grow[txg - kk];
+                if (kk >= klo && kk <= khi) d = grow[tg - kk];
                 #pragma unroll
                 for (int j = 0; j < 8; ++j) acc[j] = ffma2(w[(s + j) & 7], d, acc[j]);
+              }
+            }
+          }
+          // Folded edge columns collect the clamped taps (prefix sums).
+          #pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int ex = X0 + 8 * g + j;
+            const bool fl = foldL && ex == 0, fr = foldR && ex == EW - 1;
+            if (fl || fr) {
+              for (int xo = 0; xo < bw; ++xo) {
+                float cw = 0.f;
+                if (fl) cw += cum_at(CU, offx - xo, r);
+                if (fr) cw += cum_at(CU, 2 * r + 1 - (offx + EW - xo), r);
+                acc[j] = ffma2(make_float2(cw, cw), grow[xo], acc[j]);
               }
             }
           }
@@ -132,50 +155,63 @@ adjoint_kernel(FrameSource src, Workspace ws, int ulen_max) {
           }
         }
         __syncthreads();
-        // ---- pass B: gT rows for the slab, items (4-column quad, 8-row group)
+        // ---- pass B: g_in[gy0 + ey][gx0 + ex] += sum_yo w(ey, yo) Z[yo][ex]
         const int nq = (SWx + 3) >> 2;
         for (int it = tid; it < nq * nh; it += kThreads) {
           const int q = it % nq, h = it / nq;
-          const int tyg = 8 * h;
-          const int klo = max(tyg - bh + 1, -7), khi = min(tyg, 2 * r);
-          if (klo > khi) continue;
+          const int tg = offy + 8 * h;        // tap index of (ey = 8h, yo = 0)
+          const int klo = max(tg - bh + 1, -7), khi = min(tg, 2 * r);
           float2 acc[8][2];
           #pragma unroll
           for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = make_float2(0.f, 0.f);
-          const int k0 = klo >= 0 ? (klo & ~7) : -8;
-          float2 w[8];
-          #pragma unroll
-          for (int s = 0; s < 7; ++s) w[s] = U[kTapPad + k0 + s];
-          for (int kb = k0; kb <= khi; kb += 8) {
+          if (klo <= khi) {
+            const int k0 = klo >= 0 ? (klo & ~7) : -8;
+            float2 w[8];
             #pragma unroll
-            for (int s = 0; s < 8; ++s) {
-              const int kk = kb + s;
-              w[(s + 7) & 7] = U[kTapPad + kk + 7];
-              float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
-              if (kk >= klo && kk <= khi) d = *reinterpret_cast<const float4*>(Z + (tyg - kk) * kZPitch + 4 * q);
-              const float2 dlo = make_float2(d.x, d.y), dhi = make_float2(d.z, d.w);
+            for (int s = 0; s < 7; ++s) w[s] = U[kTapPad + k0 + s];
+            for (int kb = k0; kb <= khi; kb += 8) {
               #pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                acc[j][0] = ffma2(w[(s + j) & 7], dlo, acc[j][0]);
-                acc[j][1] = ffma2(w[(s + j) & 7], dhi, acc[j][1]);
+              for (int s = 0; s < 8; ++s) {
+                const int kk = kb + s;
+                w[(s + 7) & 7] = U[kTapPad + kk + 7];
+                float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (kk >= klo && kk <= khi) d = *reinterpret_cast<const float4*>(Z + (tg - kk) * kZPitch + 4 * q);
+                const float2 dlo = make_float2(d.x, d.y), dhi = make_float2(d.z, d.w);
+                #pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  acc[j][0] = ffma2(w[(s + j) & 7], dlo, acc[j][0]);
+                  acc[j][1] = ffma2(w[(s + j) & 7], dhi, acc[j][1]);
+                }
+              }
+            }
+          }
+          // Folded edge rows.
+          #pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int ey = 8 * h + j;
+            const bool ft = foldT && ey == 0, fb = foldB && ey == EH - 1;
+            if (ft || fb) {
+              for (int yo = 0; yo < bh; ++yo) {
+                float cw = 0.f;
+                if (ft) cw += cum_at(CU, offy - yo, r);
+                if (fb) cw += cum_at(CU, 2 * r + 1 - (offy + EH - yo), r);
+                const float4 d = *reinterpret_cast<const float4*>(Z + yo * kZPitch + 4 * q);
+                acc[j][0] = ffma2(make_float2(cw, cw), make_float2(d.x, d.y), acc[j][0]);
+                acc[j][1] = ffma2(make_float2(cw, cw), make_float2(d.z, d.w), acc[j][1]);
               }
             }
           }
           float* plane = gin + (size_t)c * planePitch;
           #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            const int ty = tyg + j;
-            if (ty >= tileH) break;
-            const int gy = clampi(y0 - r + ty, 0, H - 1);
-            float* rowp = plane + (size_t)gy * W;
+            const int ey = 8 * h + j;
+            if (ey >= EH) break;
+            float* rowp = plane + (size_t)(gy0 + ey) * W + gx0 + X0;
             const float v[4] = {acc[j][0].x, acc[j][0].y, acc[j][1].x, acc[j][1].y};
             #pragma unroll
             for (int e = 0; e < 4; ++e) {
               const int col = 4 * q + e;
-              if (col < SWx && v[e] != 0.f) {
-                const int gx = clampi(x0 - r + X0 + col, 0, W - 1);
-                atomicAdd(rowp + gx, v[e]);
-              }
+              if (col < SWx && v[e] != 0.f) atomicAdd(rowp + col, v[e]);
             }
           }
         }
@@ -187,7 +223,7 @@ adjoint_kernel(FrameSource src, Workspace ws, int ulen_max) {
 
 }  // namespace
 
-size_t adjoint_smem_bytes(int rmax) { return smem_layout(tap_len(rmax)).total; }
+size_t adjoint_smem_bytes(int rmax) { return smem_layout(rmax).total; }
 
 int adjoint_max_ctas_per_sm(int rmax) {
   const size_t smem = adjoint_smem_bytes(rmax);
@@ -205,11 +241,10 @@ int adjoint_max_ctas_per_sm(int rmax) {
 
 cudaError_t launch_adjoint(const FrameSource& src, const Workspace& ws, int rmax, int grid,
                            cudaStream_t s) {
-  const int ulen = tap_len(rmax);
   const size_t smem = adjoint_smem_bytes(rmax);
   cudaError_t e = cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  adjoint_kernel<<<grid, kThreads, smem, s>>>(src, ws, ulen);
+  adjoint_kernel<<<grid, kThreads, smem, s>>>(src, ws, rmax);
   return cudaGetLastError();
 }
 

@@ -163,6 +163,75 @@ __device__ __forceinline__ void make_taps(float2* U, int len, int r, float c, fl
 
 // Number of tap entries a launch needs for radius bound rmax.
 __host__ __device__ __forceinline__ int tap_len(int rmax) { return kTapPad + 2 * rmax + 24; }
+// Entries of the cumulative-tap table for radius bound rmax.
+__host__ __device__ __forceinline__ int cum_len(int rmax) { return 2 * rmax + 4; }
+
+// Exclusive prefix sums of the normalised taps: CU[m] = sum_{m' < m} u[m']
+// for m in [0, 2r+1] (u[m] is the tap of offset m - r). Used to fold the
+// taps that clamp-to-edge sends onto an edge row or column: the clamped taps
+// below tap index M weigh CU[M], and (taps being symmetric) those at or above
+// M weigh CU[2r + 1 - M]. One warp scans; the caller synchronises after.
+__device__ __forceinline__ void make_cumulative(const float2* U, float* CU, int r) {
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  const int n = 2 * r + 1;
+  const int seg = (n + 31) >> 5;
+  const int b = lane * seg, e = min(n, b + seg);
+  float s = 0.0f;
+  for (int m = b; m < e; ++m) s += U[kTapPad + m].x;
+  float incl = s;
+  #pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  float run = incl - s;
+  for (int m = b; m < e; ++m) {
+    CU[m] = run;
+    run += U[kTapPad + m].x;
+  }
+  if (lane == 31) CU[n] = incl;
+}
+
+// CU at tap index m, clamped to the table ([0, 2r+1]).
+__device__ __forceinline__ float cum_at(const float* CU, int m, int r) {
+  return CU[m < 0 ? 0 : (m > 2 * r + 1 ? 2 * r + 1 : m)];
+}
+
+// Packed two-lane add.
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
+#if defined(FOVEA_SCALAR_FMA)
+  return make_float2(a.x + b.x, a.y + b.y);
+#else
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+#endif
+}
+
+// Four packed bytes -> two float pairs, exactly (2^23 + b - 2^23).
+__device__ __forceinline__ void u8x4_to_f32(unsigned int w, float2& lo, float2& hi) {
+  const float2 bias = make_float2(-8388608.0f, -8388608.0f);
+  const unsigned int k = 0x4B000000u;
+  lo = fadd2(make_float2(__uint_as_float(__byte_perm(w, k, 0x7650)), __uint_as_float(__byte_perm(w, k, 0x7651))), bias);
+  hi = fadd2(make_float2(__uint_as_float(__byte_perm(w, k, 0x7652)), __uint_as_float(__byte_perm(w, k, 0x7653))), bias);
+}
+
+// 16-byte asynchronous global->shared copy; bytes past `src_bytes` are zero
+// filled (src_bytes = 0 writes zeros and reads nothing).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, int src_bytes) {
+  const unsigned int s = (unsigned int)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // ------------------------------------------------------------------ launchers
 // (defined in sigma.cu, forward.cu, adjoint.cu)
@@ -175,10 +244,10 @@ struct FwdConfig {
 
 cudaError_t launch_sigma_order(const FrameSource& src, const Workspace& ws, int grid_ctas,
                                float* sigma_out, int* radius_out, cudaStream_t s);
-size_t forward_smem_bytes(const FwdConfig& cfg, int rmax);
+size_t forward_smem_bytes(const FwdConfig& cfg, int rmax, bool any_f32);
 cudaError_t launch_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg,
-                           int rmax, int grid, cudaStream_t s);
-int forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax);
+                           int rmax, bool any_f32, int grid, cudaStream_t s);
+int forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, bool any_f32);
 size_t adjoint_smem_bytes(int rmax);
 cudaError_t launch_adjoint(const FrameSource& src, const Workspace& ws, int rmax, int grid,
                            cudaStream_t s);
