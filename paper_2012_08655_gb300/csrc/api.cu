@@ -65,7 +65,7 @@ struct fovea_ctx {
   cudaEvent_t batch_ev[kBatchSlots] = {};
   size_t batch_host_cap = 0;
   int batch_slot = 0;
-  // CUDA graphs of the batch launch sequence, keyed by (kind + 2*any_f32, radius bound)
+  // CUDA graphs of the batch launch sequence, keyed by (kind + 2*format mask, radius bound)
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
   // optional events bracketing the persistent blur kernel (measurement)
   cudaEvent_t kev_start = nullptr, kev_stop = nullptr;
@@ -176,8 +176,8 @@ int sigma_grid(long long items, int num_sms) {
   return (int)std::max<long long>(1, std::min<long long>(g, 4ll * num_sms));
 }
 
-int forward_grid(fovea_ctx* ctx, int rmax, bool any_f32) {
-  int per = forward_max_ctas_per_sm(ctx->cfg, rmax, any_f32);
+int forward_grid(fovea_ctx* ctx, int rmax, int fmt_mask) {
+  int per = forward_max_ctas_per_sm(ctx->cfg, rmax, fmt_mask);
   if (per <= 0) return 0;
   if (ctx->cfg.ctas_per_sm > 0) per = std::min(per, ctx->cfg.ctas_per_sm);
   return per * ctx->num_sms;
@@ -192,12 +192,12 @@ int adjoint_grid(fovea_ctx* ctx, int rmax) {
 // Stage n frame descriptors into the pinned slot ring and copy them to the
 // device-resident batch buffer on `s`. Returns total items in *total.
 int upload_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint, cudaStream_t s,
-                 long long* total, int* rmax, bool* any_f32) {
+                 long long* total, int* rmax, int* fmt_mask) {
   if (n <= 0 || !frames) return FOVEA_EINVAL;
   std::vector<FrameDesc> descs((size_t)n);
   long long item0 = 0;
   int rm = 0;
-  bool f32 = false;
+  int mask = 0;
   for (int i = 0; i < n; ++i) {
     const fovea_frame& f = frames[i];
     int st = check_frame(f.width, f.height, f.channels, f.format, ctx->B, f.sigma0, f.k, f.fix_x, f.fix_y);
@@ -210,7 +210,7 @@ int upload_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint,
                                  f.fix_y, f.sigma0, f.k, item0);
     item0 += (long long)descs[(size_t)i].nbx * descs[(size_t)i].nby;
     rm = std::max(rm, radius_bound(f.width, f.height, ctx->B, f.fix_x, f.fix_y, f.sigma0, f.k));
-    f32 = f32 || f.format == FOVEA_F32_CHW;
+    mask |= f.format == FOVEA_F32_CHW ? 2 : 1;
   }
   if (item0 > (1ll << 31) - 1) return FOVEA_EUNSUPPORTED;
   int st = ensure_workspace(ctx, item0);
@@ -255,7 +255,7 @@ int upload_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint,
   FOVEA_CUDA(cudaEventRecord(ctx->batch_ev[slot], s));
   *total = item0;
   *rmax = rm;
-  *any_f32 = f32;
+  *fmt_mask = mask;
   return FOVEA_OK;
 }
 
@@ -268,7 +268,7 @@ FrameSource batch_source(fovea_ctx* ctx) {
 }
 
 // Enqueue (or capture) the batch launch sequence for the current batch buffer.
-int enqueue_batch_kernels(fovea_ctx* ctx, bool adjoint, int rbound, bool any_f32, cudaStream_t s) {
+int enqueue_batch_kernels(fovea_ctx* ctx, bool adjoint, int rbound, int fmt_mask, cudaStream_t s) {
   const FrameSource src = batch_source(ctx);
   const int sg = 4 * ctx->num_sms;
   if (adjoint) {
@@ -287,9 +287,9 @@ int enqueue_batch_kernels(fovea_ctx* ctx, bool adjoint, int rbound, bool any_f32
     if (grid <= 0) return FOVEA_EUNSUPPORTED;
     e = launch_adjoint(src, ctx->ws, rbound, grid, s);
   } else {
-    int grid = forward_grid(ctx, rbound, any_f32);
+    int grid = forward_grid(ctx, rbound, fmt_mask);
     if (grid <= 0) return FOVEA_EUNSUPPORTED;
-    e = launch_forward(src, ctx->ws, ctx->cfg, rbound, any_f32, grid, s);
+    e = launch_forward(src, ctx->ws, ctx->cfg, rbound, fmt_mask, grid, s);
   }
   if (e != cudaSuccess) return cuda_fail(e);
   return FOVEA_OK;
@@ -298,19 +298,19 @@ int enqueue_batch_kernels(fovea_ctx* ctx, bool adjoint, int rbound, bool any_f32
 int run_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint, cudaStream_t s) {
   long long total = 0;
   int rmax = 0;
-  bool any_f32 = false;
-  int st = upload_batch(ctx, frames, n, adjoint, s, &total, &rmax, &any_f32);
+  int fmt_mask = 0;
+  int st = upload_batch(ctx, frames, n, adjoint, s, &total, &rmax, &fmt_mask);
   if (st != FOVEA_OK) return st;
   // Radius bound of the graph: next multiple of 64 (shared-memory size of
   // the persistent kernel depends on it).
   const int rbound = std::min(kMaxRadius, ((rmax + 63) / 64) * 64);
-  const auto key = std::make_pair((adjoint ? 1 : 0) + (any_f32 ? 2 : 0), rbound);
+  const auto key = std::make_pair((adjoint ? 1 : 0) + 2 * fmt_mask, rbound);
   auto it = ctx->graphs.find(key);
   if (it == ctx->graphs.end()) {
     if (!ctx->capture_stream) FOVEA_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
     FOVEA_CUDA(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-    st = enqueue_batch_kernels(ctx, adjoint, rbound, any_f32, ctx->capture_stream);
+    st = enqueue_batch_kernels(ctx, adjoint, rbound, fmt_mask, ctx->capture_stream);
     cudaError_t ee = cudaStreamEndCapture(ctx->capture_stream, &g);
     if (st != FOVEA_OK) {
       if (g) cudaGraphDestroy(g);
@@ -381,11 +381,11 @@ int fovea_render(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x,
   const int rmax = radius_bound(ctx->W, ctx->H, ctx->B, fix_x, fix_y, ctx->sigma0, ctx->k);
   cudaError_t e = launch_sigma_order(src, ctx->ws, sigma_grid(src.one_total, ctx->num_sms), nullptr, nullptr, s);
   if (e != cudaSuccess) return cuda_fail(e);
-  const bool f32 = ctx->fmt == FOVEA_F32_CHW;
-  const int grid = forward_grid(ctx, rmax, f32);
+  const int fmt_mask = ctx->fmt == FOVEA_F32_CHW ? 2 : 1;
+  const int grid = forward_grid(ctx, rmax, fmt_mask);
   if (grid <= 0) return FOVEA_EUNSUPPORTED;
   if (ctx->kev_start) FOVEA_CUDA(cudaEventRecord(ctx->kev_start, s));
-  e = launch_forward(src, ctx->ws, ctx->cfg, rmax, f32, grid, s);
+  e = launch_forward(src, ctx->ws, ctx->cfg, rmax, fmt_mask, grid, s);
   if (e != cudaSuccess) return cuda_fail(e);
   if (ctx->kev_stop) FOVEA_CUDA(cudaEventRecord(ctx->kev_stop, s));
   return FOVEA_OK;

@@ -20,9 +20,11 @@
 // The vertical pass runs first so the tile can stream by rows: shared memory
 // does not grow with the radius. Wide tiles are cut into column slabs and
 // pass 2 accumulates across slabs. All products are fp32 FMAs, two lanes per
-// instruction (fma.rn.f32x2); a thread keeps 8 outputs per value it loads and
-// a sliding window of 8 taps in registers (the register data reuse of the
-// paper's "Data Reuse" subsection, generalised).
+// instruction (fma.rn.f32x2). In pass 1 a thread owns 2 element columns x 16
+// output rows and keeps a sliding window of 16 taps in registers, so each
+// value it loads feeds 16 packed FMAs; in pass 2 a thread owns 8 output
+// columns x 2 rows (the register data reuse of the paper's "Data Reuse"
+// subsection, generalised).
 #include "fovea_internal.cuh"
 
 namespace fovea {
@@ -30,11 +32,13 @@ namespace fovea {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kSlabMax = 240;           // elements per slab (ring row <= 15 + 240 + pad)
-constexpr int kVVPitch = kSlabMax + 1;  // float2 pitch of the row-pair buffer (odd: conflict-free)
+constexpr int kSlabMax = 240;                 // elements per slab (ring row <= 15 + 240 + pad)
+constexpr int kVVPad = 32;                    // zero columns on each side of a VV row (8 px x 4 ch)
+constexpr int kVVPitch = kVVPad + kSlabMax + kVVPad + 1;  // odd pitch: conflict-free row pairs
 constexpr int kStages = 3;
-constexpr int kRowBytesU8 = 256;        // ring row: 64 words of 4 bytes
-constexpr int kRowBytesF32 = 1024;      // ring row: 64 quads of 4 floats
+constexpr int kRowBytesU8 = 256;              // ring row: 128 pairs of bytes
+constexpr int kRowBytesF32 = 1024;            // ring row: 128 pairs of floats
+constexpr int kN1 = 16;                       // pass-1 output rows per thread (tap window)
 
 struct SmemLayout {
   size_t ring, vv, taps, cum, red, total;
@@ -62,17 +66,16 @@ struct Item {
   const unsigned char* in;
   unsigned char* out;
   int W, H, C;
-  bool u8;
   int r, x0, y0, bw, bh;
   int gx0, EW, offx;          // folded columns: frame columns gx0 .. gx0+EW-1, tap offset
   int gy0, EH, offy;          // folded rows
   bool foldL, foldR, foldT, foldB;
   int ph;                     // virtual-row phase: virtual row v holds folded row v - ph
-  int vrows;                  // virtual rows staged (multiple of 8)
-  int steps;                  // 8-tap steps covering 2r + 8 taps
+  int vrows;                  // virtual rows staged (multiple of kN1)
   int nsl, sw, nchunks;       // slabs (per channel for f32), slab width, row chunks per slab
   size_t pitch;               // bytes per frame row (u8: W*C, f32: 4*W)
   bool fast;                  // 16-byte aligned rows: cp.async staging
+  bool isu8;                  // uint8 HWC (else float32 CHW)
 };
 
 struct Slab {
@@ -82,27 +85,29 @@ struct Slab {
   size_t src;  // byte offset of element e0 within frame row 0 (plane c for f32)
 };
 
+template <bool U8>
 __device__ __forceinline__ Slab slab_of(const Item& it, int s) {
   Slab sl;
-  const int E = it.u8 ? it.EW * it.C : it.EW;
-  const int ss = it.u8 ? s : s % it.nsl;
-  sl.c = it.u8 ? -1 : s / it.nsl;
+  const int E = U8 ? it.EW * it.C : it.EW;
+  const int ss = U8 ? s : s % it.nsl;
+  sl.c = U8 ? -1 : s / it.nsl;
   sl.e0 = ss * it.sw;
   sl.sws = min(it.sw, E - sl.e0);
-  if (it.u8) {
+  if (U8) {
     sl.src = (size_t)it.gx0 * it.C + sl.e0;
   } else {
     sl.src = ((size_t)sl.c * it.H * it.W + it.gx0 + sl.e0) * 4;
   }
-  sl.ph = it.fast ? (int)(((size_t)it.in + sl.src) & 15) / (it.u8 ? 1 : 4) : 0;
+  sl.ph = it.fast ? (int)(((size_t)it.in + sl.src) & 15) / (U8 ? 1 : 4) : 0;
   return sl;
 }
 
 // Stage rows [k*RB, (k+1)*RB) (virtual) of slab `sl` into one ring stage.
-template <int RB>
+template <bool U8, int RB>
 __device__ __forceinline__ void stage_rows(const Item& it, const Slab& sl, int k, unsigned char* ring,
-                                           int row_bytes, size_t frame_bytes) {
-  const int esz = it.u8 ? 1 : 4;
+                                           size_t frame_bytes) {
+  constexpr int esz = U8 ? 1 : 4;
+  constexpr int row_bytes = U8 ? kRowBytesU8 : kRowBytesF32;
   if (it.fast) {
     const int nch = (sl.ph * esz + sl.sws * esz + 15) >> 4;  // 16-byte copies per row
     for (int idx = threadIdx.x; idx < RB * nch; idx += kThreads) {
@@ -129,13 +134,13 @@ __device__ __forceinline__ void stage_rows(const Item& it, const Slab& sl, int k
       const bool ok = v < it.vrows && ey >= 0 && ey < it.EH;
       const size_t off = (size_t)(it.gy0 + (ok ? ey : 0)) * it.pitch + sl.src + (size_t)e * esz;
       unsigned char* dst = ring + (size_t)row * row_bytes + (size_t)e * esz;
-      if (it.u8) {
+      if (U8) {
         *dst = ok ? __ldg(it.in + off) : (unsigned char)0;
       } else {
         *reinterpret_cast<float*>(dst) = ok ? __ldg(reinterpret_cast<const float*>(it.in + off)) : 0.0f;
       }
     }
-    // zero the tail of each row so whole words/quads read as zeros
+    // zero the tail of each row so whole pairs read as zeros
     const int tail0 = sl.sws * esz, tailn = ((tail0 + 15) & ~15) - tail0;
     for (int idx = threadIdx.x; idx < RB * tailn; idx += kThreads) {
       const int row = idx / tailn, b = idx - row * tailn;
@@ -144,243 +149,295 @@ __device__ __forceinline__ void stage_rows(const Item& it, const Slab& sl, int k
   }
 }
 
-template <int RB>
+// Element pair of one staged row as floats.
+template <bool U8>
+__device__ __forceinline__ float2 load_pair(const unsigned char* row, int pi) {
+  if (U8) {
+    return u8x2_to_f32(*reinterpret_cast<const unsigned short*>(row + 2 * pi));
+  } else {
+    return *reinterpret_cast<const float2*>(row + 8 * pi);
+  }
+}
+
+struct Smem {
+  unsigned char* ring;
+  float2* VV;
+  const float2* U;
+  const float* CU;
+};
+
+// All slabs of one item; returns with acc2 holding the block's outputs.
+template <bool U8, int RB>
+__device__ __forceinline__ void process_item(const Item& it, const Smem& sm, float2 (&acc2)[8]) {
+  constexpr int row_bytes = U8 ? kRowBytesU8 : kRowBytesF32;
+  constexpr size_t stage_bytes = (size_t)RB * row_bytes;
+  const int tid = threadIdx.x;
+  const int r = it.r;
+  const int nslabs = U8 ? it.nsl : it.nsl * it.C;
+  const int Q = nslabs * it.nchunks;
+  const size_t frame_bytes = (size_t)it.H * it.pitch * (U8 ? 1 : it.C);
+  // pass-1 identity: element pair pi, row group G1 of kN1 output rows
+  const int pi = tid & 127, G1 = tid >> 7;
+  // pass-2 identity: row pair p2, channel c2, group g2 of 8 output columns
+  const int g2 = tid >> 6, c2 = (tid >> 4) & 3, p2 = tid & 15;
+
+  const int groups1 = (it.bh + kN1 - 1) / kN1, groups2 = (it.bw + 7) >> 3;
+  const int steps1 = 1 + (2 * r + kN1 - 1) / kN1;  // kN1-row steps covering 2r + kN1 taps
+  const int steps2 = 1 + ((2 * r + 7) >> 3);       // 8-column steps covering 2r + 8 taps
+  const int vs1 = kN1 * G1 - it.offy + it.ph;      // virtual row where acc[0] sees tap 0
+  const int v1lo = max(0, vs1), v1hi = min(it.vrows, vs1 + kN1 * steps1);
+  const bool grp1 = G1 < groups1;
+  const int xg = 8 * g2;
+  const bool act2base = g2 < groups2 && c2 < it.C && 2 * p2 < it.bh;
+  float2 a1[kN1];
+  float2 wv[kN1];
+
+  for (int q = 0; q < Q; ++q) {
+    cp_async_wait<kStages - 2>();
+    __syncthreads();  // chunk q landed for every thread; chunk q-1 fully consumed
+    {
+      const int qn = q + kStages - 1;
+      if (qn < Q) stage_rows<U8, RB>(it, slab_of<U8>(it, qn / it.nchunks), qn % it.nchunks,
+                                     sm.ring + (size_t)(qn % kStages) * stage_bytes, frame_bytes);
+      cp_async_commit();
+    }
+    const int s = q / it.nchunks, k = q - s * it.nchunks;
+    const Slab sl = slab_of<U8>(it, s);
+    const unsigned char* st = sm.ring + (size_t)(q % kStages) * stage_bytes;
+    const int R0 = k * RB;
+    // ring pair pi holds slab elements 2*pi - ph and 2*pi - ph + 1
+    const int e_first = 2 * pi - sl.ph;
+    const bool act1 = grp1 && e_first + 1 >= 0 && e_first < sl.sws;
+    if (k == 0) {
+      #pragma unroll
+      for (int j = 0; j < kN1; ++j) a1[j] = make_float2(0.f, 0.f);
+      // Folded top row: taps clamped onto the first frame row (applied first,
+      // so the summation order does not depend on the chunk size).
+      if (act1 && it.foldT) {
+        const float2 d = load_pair<U8>(st + (size_t)it.ph * row_bytes, pi);
+        #pragma unroll
+        for (int j = 0; j < kN1; ++j) {
+          const float cw = cum_at(sm.CU, it.offy - (kN1 * G1 + j), r);
+          a1[j] = ffma2(make_float2(cw, cw), d, a1[j]);
+        }
+      }
+    }
+    if (act1) {
+      const int lo = max(R0, v1lo), hi = min(R0 + RB, v1hi);
+      if (lo < hi && lo == v1lo) {  // first row of the group: preload the tap window
+        #pragma unroll
+        for (int u = 1; u < kN1; ++u) wv[u] = sm.U[kTapPad + (lo - vs1) - kN1 + u];
+      }
+      const unsigned char* rowp = st + (size_t)(lo - R0) * row_bytes;
+      const float2* up = sm.U + kTapPad + (lo - vs1);
+      for (int v0 = lo; v0 < hi; v0 += kN1) {
+        #pragma unroll
+        for (int u = 0; u < kN1; ++u) {
+          wv[u] = up[u];
+          const float2 d = load_pair<U8>(rowp + (size_t)u * row_bytes, pi);
+          #pragma unroll
+          for (int j = 0; j < kN1; ++j) a1[j] = ffma2(wv[(u - j) & (kN1 - 1)], d, a1[j]);
+        }
+        rowp += (size_t)kN1 * row_bytes;
+        up += kN1;
+      }
+      // Folded bottom row: taps clamped onto the last frame row.
+      const int vb = it.ph + it.EH - 1;
+      if (it.foldB && vb >= R0 && vb < R0 + RB) {
+        const float2 d = load_pair<U8>(st + (size_t)(vb - R0) * row_bytes, pi);
+        #pragma unroll
+        for (int j = 0; j < kN1; ++j) {
+          const float cw = cum_at(sm.CU, 2 * r + 1 - (it.offy + it.EH - (kN1 * G1 + j)), r);
+          a1[j] = ffma2(make_float2(cw, cw), d, a1[j]);
+        }
+      }
+    }
+    if (k != it.nchunks - 1) continue;
+
+    // ---- slab complete: V rows -> row-pair buffer, then pass 2 over the slab
+    if (act1) {
+      #pragma unroll
+      for (int pp = 0; pp < kN1 / 2; ++pp) {
+        float2* dst = sm.VV + (kN1 / 2 * G1 + pp) * kVVPitch + kVVPad;
+        if (e_first >= 0) dst[e_first] = make_float2(a1[2 * pp].x, a1[2 * pp + 1].x);
+        if (e_first + 1 < sl.sws) dst[e_first + 1] = make_float2(a1[2 * pp].y, a1[2 * pp + 1].y);
+      }
+    }
+    // zero the columns right of the slab (pass 2 reads up to 7 pixels past it)
+    for (int idx = tid; idx < 16 * kVVPad; idx += kThreads) {
+      const int row = idx / kVVPad, col = idx - row * kVVPad;
+      sm.VV[row * kVVPitch + kVVPad + sl.sws + col] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const bool act2 = act2base && (U8 || c2 == sl.c);
+    if (act2) {
+      const int Cs = U8 ? it.C : 1;
+      const int P0 = sl.e0 / Cs, P1 = P0 + sl.sws / Cs;  // folded columns of the slab
+      const int xs = xg - it.offx;                         // column whose tap index is 0 for x = xg
+      const int lo = max(P0, xs), hi = min(P1, xs + 8 * steps2);
+      const float2* vrow = sm.VV + p2 * kVVPitch + kVVPad + (U8 ? c2 : 0);
+      if (lo < hi) {
+        const int la = lo - ((lo - xs) & 7);
+        float2 w2[8];
+        #pragma unroll
+        for (int u = 1; u < 8; ++u) w2[u] = sm.U[kTapPad + (la - xs) - 8 + u];
+        const float2* up = sm.U + kTapPad + (la - xs);
+        const float2* vp = vrow + (la - P0) * Cs;
+        for (int x0c = la; x0c < hi; x0c += 8) {
+          #pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            w2[u] = up[u];
+            const float2 d = vp[u * Cs];
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) acc2[j] = ffma2(w2[(u - j) & 7], d, acc2[j]);
+          }
+          up += 8;
+          vp += 8 * Cs;
+        }
+      }
+      // Folded edge columns.
+      #pragma unroll
+      for (int f = 0; f < 2; ++f) {
+        const bool on = f == 0 ? it.foldL : it.foldR;
+        const int ex = f == 0 ? 0 : it.EW - 1;
+        if (on && ex >= P0 && ex < P1) {
+          const float2 d = vrow[(ex - P0) * Cs];
+          #pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int x = xg + j;
+            const float cw = f == 0 ? cum_at(sm.CU, it.offx - x, r) : cum_at(sm.CU, 2 * r + 1 - (it.offx + it.EW - x), r);
+            acc2[j] = ffma2(make_float2(cw, cw), d, acc2[j]);
+          }
+        }
+      }
+    }
+  }
+}
+
+// Per-item geometry from the item record (computed by one thread).
+__device__ __forceinline__ void item_geometry(Item& it, const ItemInfo& inf, const FrameDesc& fd, int rb) {
+  const bool u8 = fd.fmt == FOVEA_U8_HWC;
+  it.in = static_cast<const unsigned char*>(fd.in);
+  it.out = static_cast<unsigned char*>(fd.out);
+  it.W = fd.W; it.H = fd.H; it.C = fd.C;
+  it.isu8 = u8;
+  it.r = inf.r;
+  const int r = it.r;
+  const int bx = inf.block % fd.nbx, by = inf.block / fd.nbx;
+  it.x0 = bx * fd.B; it.y0 = by * fd.B;
+  it.bw = min(fd.B, it.W - it.x0); it.bh = min(fd.B, it.H - it.y0);
+  it.gx0 = max(0, it.x0 - r);
+  it.EW = min(it.W - 1, it.x0 + it.bw - 1 + r) - it.gx0 + 1;
+  it.offx = it.gx0 - (it.x0 - r);
+  it.foldL = it.x0 - r < 0; it.foldR = it.x0 + it.bw - 1 + r > it.W - 1;
+  it.gy0 = max(0, it.y0 - r);
+  it.EH = min(it.H - 1, it.y0 + it.bh - 1 + r) - it.gy0 + 1;
+  it.offy = it.gy0 - (it.y0 - r);
+  it.foldT = it.y0 - r < 0; it.foldB = it.y0 + it.bh - 1 + r > it.H - 1;
+  it.ph = it.offy & (kN1 - 1);
+  it.vrows = (it.EH + it.ph + kN1 - 1) & ~(kN1 - 1);
+  it.pitch = u8 ? (size_t)it.W * it.C : (size_t)it.W * 4;
+  it.fast = (((size_t)it.in & 15) == 0) && ((it.pitch & 15) == 0);
+  const int E = u8 ? it.EW * it.C : it.EW;
+  const int cap = u8 ? (kSlabMax / it.C) * it.C : kSlabMax;
+  const int nsl = (E + cap - 1) / cap;
+  int sw = (E + nsl - 1) / nsl;
+  if (u8) sw = ((sw + it.C - 1) / it.C) * it.C;
+  it.nsl = nsl;
+  it.sw = sw;
+  it.nchunks = (it.vrows + rb - 1) / rb;
+}
+
+// MODE 0: uint8 frames only; 1: float32 frames only; 2: both (batches).
+template <int RB, int MODE>
 __global__ void __launch_bounds__(kThreads, 2)
 forward_kernel(FrameSource src, Workspace ws, int rmax, int row_bytes) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemLayout L = smem_layout(RB, row_bytes, rmax);
-  unsigned char* ring = smem + L.ring;
-  float2* VV = reinterpret_cast<float2*>(smem + L.vv);
+  Smem sm;
+  sm.ring = smem + L.ring;
+  sm.VV = reinterpret_cast<float2*>(smem + L.vv);
   float2* U = reinterpret_cast<float2*>(smem + L.taps);
   float* CU = reinterpret_cast<float*>(smem + L.cum);
+  sm.U = U;
+  sm.CU = CU;
   float* red = reinterpret_cast<float*>(smem + L.red);
-  __shared__ int s_ticket;
+  __shared__ int s_state;  // 0 run, 1 skip item, 2 stop
+  __shared__ Item s_it;
+  __shared__ float s_c;
 
   const int tid = threadIdx.x;
   const int n_items = (int)ws.counters[CNT_NITEMS];
-  const size_t stage_bytes = (size_t)RB * row_bytes;
-  // pass-1 identity: ring word/quad w1i, row group G1 of 8 output rows
-  const int w1i = tid & 63, G1 = tid >> 6;
-  // pass-2 identity: row pair p2, channel c2, group g2 of 8 output columns
   const int g2 = tid >> 6, c2 = (tid >> 4) & 3, p2 = tid & 15;
+  // The VV pads must read as zeros: clear the whole buffer once.
+  for (int i = tid; i < 16 * kVVPitch; i += kThreads) sm.VV[i] = make_float2(0.f, 0.f);
 
   for (;;) {
-    if (tid == 0) s_ticket = (int)atomicAdd(&ws.counters[CNT_TICKET], 1u);
+    __syncthreads();  // the previous item is finished by every thread
+    if (tid == 0) {
+      const int t = (int)atomicAdd(&ws.counters[CNT_TICKET], 1u);
+      int state = 0;
+      if (t >= n_items) {
+        state = 2;
+      } else {
+        const int item = ws.order[t];
+        if ((unsigned)item >= (unsigned)n_items) {  // work list out of step: skip, flag
+          atomicOr(&ws.counters[CNT_ERROR], 16u);
+          state = 1;
+        } else {
+          const ItemInfo inf = ws.items[item];
+          const FrameDesc fd = load_frame(src, inf.frame);
+          const bool u8f = fd.fmt == FOVEA_U8_HWC;
+          const bool fmt_ok = MODE == 2 ? (u8f || row_bytes >= kRowBytesF32) : (MODE == 0 ? u8f : !u8f);
+          if (inf.r > rmax || !fmt_ok) {
+            atomicOr(&ws.counters[CNT_ERROR], 2u);
+            state = 1;
+          } else {
+            item_geometry(s_it, inf, fd, RB);
+            s_c = inf.neg_half_inv_s2;
+          }
+        }
+      }
+      s_state = state;
+    }
     __syncthreads();
-    const int t = s_ticket;
-    __syncthreads();  // s_ticket may be rewritten once every thread has read it
-    if (t >= n_items) break;
-    const int item = ws.order[t];
-    if ((unsigned)item >= (unsigned)n_items) {  // work list out of step: skip, flag
-      if (tid == 0) atomicOr(&ws.counters[CNT_ERROR], 16u);
-      continue;
-    }
-    const ItemInfo inf = ws.items[item];
-    const FrameDesc fd = load_frame(src, inf.frame);
-    if (inf.r > rmax || (fd.fmt != FOVEA_U8_HWC && row_bytes < kRowBytesF32)) {
-      if (tid == 0) atomicOr(&ws.counters[CNT_ERROR], 2u);
-      continue;
-    }
-    Item it;
-    it.in = static_cast<const unsigned char*>(fd.in);
-    it.out = static_cast<unsigned char*>(fd.out);
-    it.W = fd.W; it.H = fd.H; it.C = fd.C;
-    it.u8 = fd.fmt == FOVEA_U8_HWC;
-    it.r = inf.r;
+    if (s_state == 2) break;
+    if (s_state == 1) continue;
+    const Item& it = s_it;
+    const bool u8 = MODE == 0 ? true : (MODE == 1 ? false : it.isu8);
     const int r = it.r;
-    {
-      const int bx = inf.block % fd.nbx, by = inf.block / fd.nbx;
-      it.x0 = bx * fd.B; it.y0 = by * fd.B;
-      it.bw = min(fd.B, it.W - it.x0); it.bh = min(fd.B, it.H - it.y0);
-    }
-    it.gx0 = max(0, it.x0 - r);
-    it.EW = min(it.W - 1, it.x0 + it.bw - 1 + r) - it.gx0 + 1;
-    it.offx = it.gx0 - (it.x0 - r);
-    it.foldL = it.x0 - r < 0; it.foldR = it.x0 + it.bw - 1 + r > it.W - 1;
-    it.gy0 = max(0, it.y0 - r);
-    it.EH = min(it.H - 1, it.y0 + it.bh - 1 + r) - it.gy0 + 1;
-    it.offy = it.gy0 - (it.y0 - r);
-    it.foldT = it.y0 - r < 0; it.foldB = it.y0 + it.bh - 1 + r > it.H - 1;
-    it.ph = it.offy & 7;
-    it.vrows = (it.EH + it.ph + 7) & ~7;
-    it.steps = 1 + ((2 * r + 7) >> 3);
-    it.pitch = it.u8 ? (size_t)it.W * it.C : (size_t)it.W * 4;
-    it.fast = (((size_t)it.in & 15) == 0) && ((it.pitch & 15) == 0);
-    {
-      const int E = it.u8 ? it.EW * it.C : it.EW;
-      const int cap = it.u8 ? (kSlabMax / it.C) * it.C : kSlabMax;
-      const int nsl = (E + cap - 1) / cap;
-      int sw = (E + nsl - 1) / nsl;
-      if (it.u8) sw = ((sw + it.C - 1) / it.C) * it.C;
-      it.nsl = nsl;
-      it.sw = sw;
-    }
-    it.nchunks = (it.vrows + RB - 1) / RB;
-    const int nslabs = it.u8 ? it.nsl : it.nsl * it.C;
-    const int Q = nslabs * it.nchunks;
-    const size_t frame_bytes = (size_t)it.H * it.pitch * (it.u8 ? 1 : it.C);
 
     // Start staging before the taps are ready: the copies do not need them.
-    #pragma unroll
-    for (int q = 0; q < kStages - 1; ++q) {
-      if (q < Q) stage_rows<RB>(it, slab_of(it, q / it.nchunks), q % it.nchunks, ring + (size_t)q * stage_bytes,
-                                row_bytes, frame_bytes);
-      cp_async_commit();
+    {
+      constexpr int rbu = kRowBytesU8, rbf = kRowBytesF32;
+      #pragma unroll
+      for (int q = 0; q < kStages - 1; ++q) {
+        const int Q = (u8 ? it.nsl : it.nsl * it.C) * it.nchunks;
+        if (q < Q) {
+          if (MODE != 1 && u8) stage_rows<true, RB>(it, slab_of<true>(it, q / it.nchunks), q % it.nchunks,
+                                                    sm.ring + (size_t)q * RB * rbu, (size_t)it.H * it.pitch);
+          if (MODE != 0 && !u8) stage_rows<false, RB>(it, slab_of<false>(it, q / it.nchunks), q % it.nchunks,
+                                                      sm.ring + (size_t)q * RB * rbf, (size_t)it.H * it.pitch * it.C);
+        }
+        cp_async_commit();
+      }
     }
-    make_taps(U, tap_len(r), r, inf.neg_half_inv_s2, red);
+    make_taps(U, tap_len(r), r, s_c, red);
     make_cumulative(U, CU, r);
     __syncthreads();
 
-    const int groups1 = (it.bh + 7) >> 3, groups2 = (it.bw + 7) >> 3;
-    // pass-1 row range of this thread's group in virtual rows (8-aligned)
-    const int vs1 = 8 * G1 - it.offy + it.ph;
-    const int v1lo = max(0, vs1), v1hi = min(it.vrows, vs1 + 8 * it.steps);
-    const bool grp1 = G1 < groups1;
-    const int xg = 8 * g2;
-    const bool act2base = g2 < groups2 && c2 < it.C && 2 * p2 < it.bh;
     float2 acc2[8];
     #pragma unroll
     for (int j = 0; j < 8; ++j) acc2[j] = make_float2(0.f, 0.f);
-    float2 a1[8][2];
-    float2 wv[8];
-    #pragma unroll
-    for (int j = 0; j < 8; ++j) wv[j] = make_float2(0.f, 0.f);
+    if (MODE != 1 && u8) process_item<true, RB>(it, sm, acc2);
+    if (MODE != 0 && !u8) process_item<false, RB>(it, sm, acc2);
 
-    for (int q = 0; q < Q; ++q) {
-      cp_async_wait<kStages - 2>();
-      __syncthreads();  // chunk q landed for every thread; chunk q-1 fully consumed
-      {
-        const int qn = q + kStages - 1;
-        if (qn < Q) stage_rows<RB>(it, slab_of(it, qn / it.nchunks), qn % it.nchunks,
-                                   ring + (size_t)(qn % kStages) * stage_bytes, row_bytes, frame_bytes);
-        cp_async_commit();
-      }
-      const int s = q / it.nchunks, k = q - s * it.nchunks;
-      const Slab sl = slab_of(it, s);
-      const unsigned char* st = ring + (size_t)(q % kStages) * stage_bytes;
-      // ring word/quad w1i holds slab elements 4*w1i - ph .. +3
-      const int e_first = 4 * w1i - sl.ph;
-      const bool act1 = grp1 && e_first + 3 >= 0 && e_first < sl.sws;
-      if (k == 0) {
-        #pragma unroll
-        for (int j = 0; j < 8; ++j) a1[j][0] = a1[j][1] = make_float2(0.f, 0.f);
-      }
-      if (act1) {
-        const int R0 = k * RB;
-        const int lo = max(R0, v1lo), hi = min(R0 + RB, v1hi);
-        if (lo < hi && lo == v1lo) {  // first row of the group: preload the tap window
-          #pragma unroll
-          for (int u = 1; u < 8; ++u) wv[u] = U[kTapPad + (lo - vs1) - 8 + u];
-        }
-        for (int v0 = lo; v0 < hi; v0 += 8) {
-          #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int v = v0 + u;
-            wv[u] = U[kTapPad + v - vs1];
-            float2 dlo, dhi;
-            if (it.u8) {
-              const unsigned int wd = *reinterpret_cast<const unsigned int*>(st + (size_t)(v - R0) * row_bytes + 4 * w1i);
-              u8x4_to_f32(wd, dlo, dhi);
-            } else {
-              const float4 d = *reinterpret_cast<const float4*>(st + (size_t)(v - R0) * row_bytes + 16 * w1i);
-              dlo = make_float2(d.x, d.y);
-              dhi = make_float2(d.z, d.w);
-            }
-            #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              a1[j][0] = ffma2(wv[(u - j) & 7], dlo, a1[j][0]);
-              a1[j][1] = ffma2(wv[(u - j) & 7], dhi, a1[j][1]);
-            }
-          }
-        }
-        // Folded edge rows: the taps clamped onto the first / last frame row.
-        #pragma unroll
-        for (int f = 0; f < 2; ++f) {
-          const bool on = f == 0 ? it.foldT : it.foldB;
-          const int v = f == 0 ? it.ph : it.ph + it.EH - 1;
-          if (on && v >= R0 && v < R0 + RB) {
-            float2 dlo, dhi;
-            if (it.u8) {
-              const unsigned int wd = *reinterpret_cast<const unsigned int*>(st + (size_t)(v - R0) * row_bytes + 4 * w1i);
-              u8x4_to_f32(wd, dlo, dhi);
-            } else {
-              const float4 d = *reinterpret_cast<const float4*>(st + (size_t)(v - R0) * row_bytes + 16 * w1i);
-              dlo = make_float2(d.x, d.y);
-              dhi = make_float2(d.z, d.w);
-            }
-            #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const int yo = 8 * G1 + j;
-              const float cw = f == 0 ? cum_at(CU, it.offy - yo, r) : cum_at(CU, 2 * r + 1 - (it.offy + it.EH - yo), r);
-              const float2 w2 = make_float2(cw, cw);
-              a1[j][0] = ffma2(w2, dlo, a1[j][0]);
-              a1[j][1] = ffma2(w2, dhi, a1[j][1]);
-            }
-          }
-        }
-      }
-      if (k != it.nchunks - 1) continue;
-
-      // ---- slab complete: V rows -> row-pair buffer, then pass 2 over the slab
-      if (act1) {
-        #pragma unroll
-        for (int pp = 0; pp < 4; ++pp) {
-          float2* dst = VV + (4 * G1 + pp) * kVVPitch;
-          const float v0[4] = {a1[2 * pp][0].x, a1[2 * pp][0].y, a1[2 * pp][1].x, a1[2 * pp][1].y};
-          const float v1[4] = {a1[2 * pp + 1][0].x, a1[2 * pp + 1][0].y, a1[2 * pp + 1][1].x, a1[2 * pp + 1][1].y};
-          #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int e = e_first + u;
-            if (e >= 0 && e < sl.sws) dst[e] = make_float2(v0[u], v1[u]);
-          }
-        }
-      }
-      __syncthreads();
-      const bool act2 = act2base && (it.u8 || c2 == sl.c);
-      if (act2) {
-        const int Cs = it.u8 ? it.C : 1;
-        const int P0 = sl.e0 / Cs, P1 = P0 + sl.sws / Cs;  // folded columns of the slab
-        const int xs = xg - it.offx;                         // column whose tap index is 0 for x = xg
-        const int lo = max(P0, xs), hi = min(P1, xs + 8 * it.steps);
-        const float2* vrow = VV + p2 * kVVPitch + (it.u8 ? c2 : 0);
-        if (lo < hi) {
-          const int la = lo - ((lo - xs) & 7);
-          float2 w2[8];
-          #pragma unroll
-          for (int u = 1; u < 8; ++u) w2[u] = U[kTapPad + (la - xs) - 8 + u];
-          for (int x0c = la; x0c < hi; x0c += 8) {
-            #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int ex = x0c + u;
-              w2[u] = U[kTapPad + ex - xs];
-              float2 d = make_float2(0.f, 0.f);
-              if (ex >= lo && ex < hi) d = vrow[(ex - P0) * Cs];
-              #pragma unroll
-              for (int j = 0; j < 8; ++j) acc2[j] = ffma2(w2[(u - j) & 7], d, acc2[j]);
-            }
-          }
-        }
-        // Folded edge columns.
-        #pragma unroll
-        for (int f = 0; f < 2; ++f) {
-          const bool on = f == 0 ? it.foldL : it.foldR;
-          const int ex = f == 0 ? 0 : it.EW - 1;
-          if (on && ex >= P0 && ex < P1) {
-            const float2 d = vrow[(ex - P0) * Cs];
-            #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const int x = xg + j;
-              const float cw = f == 0 ? cum_at(CU, it.offx - x, r) : cum_at(CU, 2 * r + 1 - (it.offx + it.EW - x), r);
-              acc2[j] = ffma2(make_float2(cw, cw), d, acc2[j]);
-            }
-          }
-        }
-      }
-    }
     cp_async_wait<0>();
     __syncthreads();  // ring no longer read; it becomes the output stage
 
-    if (!it.u8) {
+    const int groups2 = (it.bw + 7) >> 3, xg = 8 * g2;
+    const bool act2base = g2 < groups2 && c2 < it.C && 2 * p2 < it.bh;
+    if (!u8) {
       if (act2base) {
         float* out = reinterpret_cast<float*>(it.out) + (size_t)c2 * it.W * it.H +
                      (size_t)(it.y0 + 2 * p2) * it.W + it.x0;
@@ -395,7 +452,7 @@ forward_kernel(FrameSource src, Workspace ws, int rmax, int row_bytes) {
         }
       }
     } else {
-      unsigned char* ost = ring;
+      unsigned char* ost = sm.ring;
       const int opitch = 32 * it.C;
       if (act2base) {
         #pragma unroll
@@ -417,26 +474,33 @@ forward_kernel(FrameSource src, Workspace ws, int rmax, int row_bytes) {
   cp_async_wait<0>();
 }
 
-template <int RB>
-void* kernel_ptr() { return reinterpret_cast<void*>(&forward_kernel<RB>); }
+template <int RB, int MODE>
+void* kernel_ptr() { return reinterpret_cast<void*>(&forward_kernel<RB, MODE>); }
 
-void* pick_kernel(int rb) {
+template <int MODE>
+void* pick_rb(int rb) {
   switch (rb) {
-    case 16: return kernel_ptr<16>();
-    case 64: return kernel_ptr<64>();
-    default: return kernel_ptr<32>();
+    case 16: return kernel_ptr<16, MODE>();
+    case 64: return kernel_ptr<64, MODE>();
+    default: return kernel_ptr<32, MODE>();
   }
 }
 
-}  // namespace
-
-size_t forward_smem_bytes(const FwdConfig& cfg, int rmax, bool any_f32) {
-  return smem_layout(cfg.rows_per_chunk, any_f32 ? kRowBytesF32 : kRowBytesU8, rmax).total;
+void* pick_kernel(int rb, int mode) {
+  return mode == 0 ? pick_rb<0>(rb) : (mode == 1 ? pick_rb<1>(rb) : pick_rb<2>(rb));
 }
 
-int forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, bool any_f32) {
-  const size_t smem = forward_smem_bytes(cfg, rmax, any_f32);
-  void* k = pick_kernel(cfg.rows_per_chunk);
+int mode_of(int fmt_mask) { return fmt_mask == 1 ? 0 : (fmt_mask == 2 ? 1 : 2); }
+
+}  // namespace
+
+size_t forward_smem_bytes(const FwdConfig& cfg, int rmax, int fmt_mask) {
+  return smem_layout(cfg.rows_per_chunk, (fmt_mask & 2) ? kRowBytesF32 : kRowBytesU8, rmax).total;
+}
+
+int forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int fmt_mask) {
+  const size_t smem = forward_smem_bytes(cfg, rmax, fmt_mask);
+  void* k = pick_kernel(cfg.rows_per_chunk, mode_of(fmt_mask));
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -450,10 +514,10 @@ int forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, bool any_f32) {
 }
 
 cudaError_t launch_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg,
-                           int rmax, bool any_f32, int grid, cudaStream_t s) {
-  const size_t smem = forward_smem_bytes(cfg, rmax, any_f32);
-  int row_bytes = any_f32 ? kRowBytesF32 : kRowBytesU8;
-  void* k = pick_kernel(cfg.rows_per_chunk);
+                           int rmax, int fmt_mask, int grid, cudaStream_t s) {
+  const size_t smem = forward_smem_bytes(cfg, rmax, fmt_mask);
+  int row_bytes = (fmt_mask & 2) ? kRowBytesF32 : kRowBytesU8;
+  void* k = pick_kernel(cfg.rows_per_chunk, mode_of(fmt_mask));
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   void* args[] = {const_cast<FrameSource*>(&src), const_cast<Workspace*>(&ws), &rmax, &row_bytes};

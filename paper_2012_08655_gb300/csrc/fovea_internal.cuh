@@ -18,7 +18,7 @@ namespace fovea {
 constexpr int kMaxBlock = FOVEA_MAX_BLOCK;   // block side B <= 32
 constexpr int kMaxRadius = FOVEA_MAX_RADIUS; // r <= 1023
 constexpr int kBuckets = 1024;               // radius buckets of the work-list sort
-constexpr int kTapPad = 8;                   // zero taps stored before offset 0
+constexpr int kTapPad = 16;                  // zero taps stored before offset 0
 
 // One frame as the kernels see it (host fills it in; 80 bytes).
 struct FrameDesc {
@@ -162,7 +162,7 @@ __device__ __forceinline__ void make_taps(float2* U, int len, int r, float c, fl
 }
 
 // Number of tap entries a launch needs for radius bound rmax.
-__host__ __device__ __forceinline__ int tap_len(int rmax) { return kTapPad + 2 * rmax + 24; }
+__host__ __device__ __forceinline__ int tap_len(int rmax) { return kTapPad + 2 * rmax + 40; }
 // Entries of the cumulative-tap table for radius bound rmax.
 __host__ __device__ __forceinline__ int cum_len(int rmax) { return 2 * rmax + 4; }
 
@@ -215,6 +215,13 @@ __device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
 #endif
 }
 
+// Two packed bytes (low half of w) -> one float pair, exactly.
+__device__ __forceinline__ float2 u8x2_to_f32(unsigned int w) {
+  const unsigned int k = 0x4B000000u;
+  return fadd2(make_float2(__uint_as_float(__byte_perm(w, k, 0x7650)), __uint_as_float(__byte_perm(w, k, 0x7651))),
+               make_float2(-8388608.0f, -8388608.0f));
+}
+
 // Four packed bytes -> two float pairs, exactly (2^23 + b - 2^23).
 __device__ __forceinline__ void u8x4_to_f32(unsigned int w, float2& lo, float2& hi) {
   const float2 bias = make_float2(-8388608.0f, -8388608.0f);
@@ -244,10 +251,11 @@ struct FwdConfig {
 
 cudaError_t launch_sigma_order(const FrameSource& src, const Workspace& ws, int grid_ctas,
                                float* sigma_out, int* radius_out, cudaStream_t s);
-size_t forward_smem_bytes(const FwdConfig& cfg, int rmax, bool any_f32);
+// fmt_mask: bit 0 = some frame is uint8 HWC, bit 1 = some frame is float32 CHW.
+size_t forward_smem_bytes(const FwdConfig& cfg, int rmax, int fmt_mask);
 cudaError_t launch_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg,
-                           int rmax, bool any_f32, int grid, cudaStream_t s);
-int forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, bool any_f32);
+                           int rmax, int fmt_mask, int grid, cudaStream_t s);
+int forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int fmt_mask);
 size_t adjoint_smem_bytes(int rmax);
 cudaError_t launch_adjoint(const FrameSource& src, const Workspace& ws, int rmax, int grid,
                            cudaStream_t s);
