@@ -69,6 +69,9 @@ struct fovea_ctx {
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
   // optional events bracketing the persistent blur kernel (measurement)
   cudaEvent_t kev_start = nullptr, kev_stop = nullptr;
+  // per-radius item lists of the single-frame path
+  int* blist = nullptr;
+  size_t blist_cap = 0;  // ints
   // device staging for fovea_render_host
   void* host_in_dev = nullptr;
   void* host_out_dev = nullptr;
@@ -379,13 +382,35 @@ int fovea_render(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x,
   src.one = make_desc(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, in_dev, out_dev, fix_x, fix_y, ctx->sigma0, ctx->k, 0);
   src.one_total = (long long)src.one.nbx * src.one.nby;
   const int rmax = radius_bound(ctx->W, ctx->H, ctx->B, fix_x, fix_y, ctx->sigma0, ctx->k);
-  cudaError_t e = launch_sigma_order(src, ctx->ws, sigma_grid(src.one_total, ctx->num_sms), nullptr, nullptr, s);
-  if (e != cudaSuccess) return cuda_fail(e);
   const int fmt_mask = ctx->fmt == FOVEA_F32_CHW ? 2 : 1;
   const int grid = forward_grid(ctx, rmax, fmt_mask);
   if (grid <= 0) return FOVEA_EUNSUPPORTED;
+  // Single frame: the sigma kernel also files every block under its radius
+  // and the blur kernel orders its own work (largest radius first) from the
+  // histogram, so no ordering kernel runs in between.
+  const size_t need = (size_t)(rmax + 1) * (size_t)src.one_total;
+  BucketList bl{nullptr, 0, 0};
+  if (need <= ((size_t)64 << 20)) {
+    if (ctx->blist_cap < need) {
+      if (ctx->blist) {
+        FOVEA_CUDA(cudaDeviceSynchronize());
+        cudaFree(ctx->blist);
+        ctx->blist = nullptr;
+        ctx->blist_cap = 0;
+      }
+      FOVEA_CUDA(cudaMalloc(&ctx->blist, need * sizeof(int)));
+      ctx->blist_cap = need;
+    }
+    bl = BucketList{ctx->blist, (int)src.one_total, rmax + 1};
+  }
+  const int sg = (int)std::min<long long>((src.one_total + sigma_threads() - 1) / sigma_threads(), 8ll * ctx->num_sms);
+  cudaError_t e = bl.list ? launch_sigma_buckets(src, ctx->ws, std::max(sg, 1), bl, s)
+                          : launch_sigma_order(src, ctx->ws, sigma_grid(src.one_total, ctx->num_sms), nullptr, nullptr, s);
+  if (e != cudaSuccess) return cuda_fail(e);
   if (ctx->kev_start) FOVEA_CUDA(cudaEventRecord(ctx->kev_start, s));
-  e = launch_forward(src, ctx->ws, ctx->cfg, rmax, fmt_mask, grid, s);
+  // Programmatic dependent launch lets the blur kernel's prologue overlap the
+  // sigma kernel (not when its launch is bracketed by timing events).
+  e = launch_forward(src, ctx->ws, ctx->cfg, rmax, fmt_mask, grid, s, bl, bl.list && !ctx->kev_start);
   if (e != cudaSuccess) return cuda_fail(e);
   if (ctx->kev_stop) FOVEA_CUDA(cudaEventRecord(ctx->kev_stop, s));
   return FOVEA_OK;
@@ -512,6 +537,7 @@ void fovea_destroy(fovea_ctx* ctx) {
   }
   cudaFree(ctx->host_in_dev);
   cudaFree(ctx->host_out_dev);
+  cudaFree(ctx->blist);
   delete ctx;
 }
 

@@ -349,9 +349,40 @@ __device__ __forceinline__ void item_geometry(Item& it, const ItemInfo& inf, con
 }
 
 // MODE 0: uint8 frames only; 1: float32 frames only; 2: both (batches).
+// Descending exclusive prefix of the radius histogram: start[b] is the first
+// ticket of radius b when tickets are handed out largest radius first.
+__device__ __forceinline__ void bucket_starts(const unsigned int* hist, int nb, int* start, int* wsum) {
+  constexpr int per = kBuckets / kThreads;  // 4 positions per thread
+  unsigned int v[per], run = 0;
+  #pragma unroll
+  for (int j = 0; j < per; ++j) {
+    const int pos = threadIdx.x * per + j, b = nb - 1 - pos;
+    v[j] = b >= 0 ? hist[b] : 0u;
+    run += v[j];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned int incl = run;
+  #pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int n = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += n;
+  }
+  if (lane == 31) wsum[warp] = (int)incl;
+  __syncthreads();
+  unsigned int acc = incl - run;
+  for (int w = 0; w < warp; ++w) acc += (unsigned int)wsum[w];
+  #pragma unroll
+  for (int j = 0; j < per; ++j) {
+    const int pos = threadIdx.x * per + j, b = nb - 1 - pos;
+    if (b >= 0) start[b] = (int)acc;
+    acc += v[j];
+  }
+  __syncthreads();
+}
+
 template <int RB, int MODE>
 __global__ void __launch_bounds__(kThreads, 2)
-forward_kernel(FrameSource src, Workspace ws, int rmax, int row_bytes) {
+forward_kernel(FrameSource src, Workspace ws, int rmax, int row_bytes, BucketList bl) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemLayout L = smem_layout(RB, row_bytes, rmax);
   Smem sm;
@@ -365,12 +396,19 @@ forward_kernel(FrameSource src, Workspace ws, int rmax, int row_bytes) {
   __shared__ int s_state;  // 0 run, 1 skip item, 2 stop
   __shared__ Item s_it;
   __shared__ float s_c;
+  __shared__ int s_start[kBuckets];
+  __shared__ int s_wsum[kThreads / 32];
 
   const int tid = threadIdx.x;
-  const int n_items = (int)ws.counters[CNT_NITEMS];
   const int g2 = tid >> 6, c2 = (tid >> 4) & 3, p2 = tid & 15;
   // The VV pads must read as zeros: clear the whole buffer once.
   for (int i = tid; i < 16 * kVVPitch; i += kThreads) sm.VV[i] = make_float2(0.f, 0.f);
+  // Launched as a programmatic dependent of the sigma kernel: wait for its
+  // results (no-op otherwise).
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const bool own_order = bl.list != nullptr;
+  const int n_items = own_order ? (int)src.one_total : (int)ws.counters[CNT_NITEMS];
+  if (own_order) bucket_starts(ws.counters + CNT_HIST, bl.nb, s_start, s_wsum);
 
   for (;;) {
     __syncthreads();  // the previous item is finished by every thread
@@ -380,7 +418,17 @@ forward_kernel(FrameSource src, Workspace ws, int rmax, int row_bytes) {
       if (t >= n_items) {
         state = 2;
       } else {
-        const int item = ws.order[t];
+        int item;
+        if (own_order) {  // smallest radius bucket whose first ticket is <= t
+          int lo = 0, hi = bl.nb - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_start[mid] <= t) hi = mid; else lo = mid + 1;
+          }
+          item = bl.list[(size_t)lo * bl.cap + (t - s_start[lo])];
+        } else {
+          item = ws.order[t];
+        }
         if ((unsigned)item >= (unsigned)n_items) {  // work list out of step: skip, flag
           atomicOr(&ws.counters[CNT_ERROR], 16u);
           state = 1;
@@ -472,6 +520,21 @@ forward_kernel(FrameSource src, Workspace ws, int rmax, int row_bytes) {
     }
   }
   cp_async_wait<0>();
+  if (own_order) {
+    // The last CTA out clears the histogram and re-arms the ticket counter
+    // for the next launch (every CTA read the histogram before it got here).
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_state = atomicAdd(&ws.counters[CNT_DONE_SIGMA], 1u) == gridDim.x - 1 ? 3 : 0;
+    __syncthreads();
+    if (s_state == 3) {
+      for (int j = tid; j < kBuckets; j += kThreads) ws.counters[CNT_HIST + j] = 0u;
+      if (tid == 0) {
+        ws.counters[CNT_TICKET] = 0u;
+        ws.counters[CNT_DONE_SIGMA] = 0u;
+      }
+    }
+  }
 }
 
 template <int RB, int MODE>
@@ -514,14 +577,25 @@ int forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int fmt_mask) {
 }
 
 cudaError_t launch_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg,
-                           int rmax, int fmt_mask, int grid, cudaStream_t s) {
+                           int rmax, int fmt_mask, int grid, cudaStream_t s, const BucketList& bl, bool pdl) {
   const size_t smem = forward_smem_bytes(cfg, rmax, fmt_mask);
   int row_bytes = (fmt_mask & 2) ? kRowBytesF32 : kRowBytesU8;
   void* k = pick_kernel(cfg.rows_per_chunk, mode_of(fmt_mask));
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  void* args[] = {const_cast<FrameSource*>(&src), const_cast<Workspace*>(&ws), &rmax, &row_bytes};
-  return cudaLaunchKernel(k, dim3(grid), dim3(kThreads), args, smem, s);
+  BucketList b = bl;
+  void* args[] = {const_cast<FrameSource*>(&src), const_cast<Workspace*>(&ws), &rmax, &row_bytes, &b};
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(grid);
+  lc.blockDim = dim3(kThreads);
+  lc.dynamicSmemBytes = smem;
+  lc.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = attr;
+  lc.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelExC(&lc, k, args);
 }
 
 }  // namespace fovea

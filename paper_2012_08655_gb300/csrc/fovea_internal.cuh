@@ -66,6 +66,14 @@ struct Workspace {
   long long capacity;
 };
 
+// Per-radius item lists of a single-frame launch: list[r * cap + k] is the
+// k-th item with radius r (k below the histogram count of r).
+struct BucketList {
+  int* list;
+  int cap;  // items per bucket row (the frame's item count)
+  int nb;   // buckets (radius bound + 1)
+};
+
 // Where the kernels read frame descriptors from: a device-resident batch
 // (hdr != nullptr) or a single frame passed by value in the launch.
 struct FrameSource {
@@ -251,10 +259,18 @@ struct FwdConfig {
 
 cudaError_t launch_sigma_order(const FrameSource& src, const Workspace& ws, int grid_ctas,
                                float* sigma_out, int* radius_out, cudaStream_t s);
+// Sigma kernel only, filling per-radius item lists (single-frame blur path).
+cudaError_t launch_sigma_buckets(const FrameSource& src, const Workspace& ws, int grid_ctas,
+                                 const BucketList& bl, cudaStream_t s);
+int sigma_threads();
 // fmt_mask: bit 0 = some frame is uint8 HWC, bit 1 = some frame is float32 CHW.
 size_t forward_smem_bytes(const FwdConfig& cfg, int rmax, int fmt_mask);
+// With bl.list set, the kernel orders its own work from the radius histogram
+// and bucket lists (single frame), and it may be launched as a programmatic
+// dependent of the sigma kernel (pdl).
 cudaError_t launch_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg,
-                           int rmax, int fmt_mask, int grid, cudaStream_t s);
+                           int rmax, int fmt_mask, int grid, cudaStream_t s,
+                           const BucketList& bl = BucketList{nullptr, 0, 0}, bool pdl = false);
 int forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int fmt_mask);
 size_t adjoint_smem_bytes(int rmax);
 cudaError_t launch_adjoint(const FrameSource& src, const Workspace& ws, int rmax, int grid,

@@ -13,7 +13,7 @@ namespace fovea {
 
 namespace {
 
-constexpr int kSigmaThreads = 256;
+constexpr int kSigmaThreads = 128;
 constexpr int kOrderThreads = 256;
 
 __device__ __forceinline__ int frame_of_item(const FrameSource& src, long long i) {
@@ -27,7 +27,7 @@ __device__ __forceinline__ int frame_of_item(const FrameSource& src, long long i
 }
 
 __global__ void __launch_bounds__(kSigmaThreads) sigma_kernel(FrameSource src, Workspace ws,
-                                                              float* sigma_out, int* radius_out) {
+                                                              float* sigma_out, int* radius_out, BucketList bl) {
   const long long total = source_total(src);
   unsigned int* hist = ws.counters + CNT_HIST;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -52,10 +52,18 @@ __global__ void __launch_bounds__(kSigmaThreads) sigma_kernel(FrameSource src, W
     inf.pad = 0;
     ws.items[i] = inf;
     const int bucket = r < kBuckets ? r : kBuckets - 1;
-    ws.rank[i] = (int)atomicAdd(&hist[bucket], 1u);
+    const int rank = (int)atomicAdd(&hist[bucket], 1u);
+    ws.rank[i] = rank;
+    if (bl.list) {  // per-radius item lists for the single-frame blur kernel
+      if (bucket < bl.nb && rank < bl.cap) bl.list[(size_t)bucket * bl.cap + rank] = (int)i;
+      else atomicOr(&ws.counters[CNT_ERROR], 32u);
+    }
     if (sigma_out) sigma_out[i] = (float)sigma;
     if (radius_out) radius_out[i] = r;
   }
+  // Let a dependent launch (the blur kernel) start its prologue; it waits for
+  // this grid's results with griddepcontrol.wait before reading them.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // Every CTA rebuilds the bucket start offsets (radius descending) from the
@@ -120,11 +128,20 @@ __global__ void __launch_bounds__(kOrderThreads) order_kernel(FrameSource src, W
 
 cudaError_t launch_sigma_order(const FrameSource& src, const Workspace& ws, int grid_ctas,
                                float* sigma_out, int* radius_out, cudaStream_t s) {
-  sigma_kernel<<<grid_ctas, kSigmaThreads, 0, s>>>(src, ws, sigma_out, radius_out);
+  BucketList none{nullptr, 0, 0};
+  sigma_kernel<<<grid_ctas, kSigmaThreads, 0, s>>>(src, ws, sigma_out, radius_out, none);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   order_kernel<<<grid_ctas, kOrderThreads, 0, s>>>(src, ws);
   return cudaGetLastError();
 }
+
+cudaError_t launch_sigma_buckets(const FrameSource& src, const Workspace& ws, int grid_ctas,
+                                 const BucketList& bl, cudaStream_t s) {
+  sigma_kernel<<<grid_ctas, kSigmaThreads, 0, s>>>(src, ws, nullptr, nullptr, bl);
+  return cudaGetLastError();
+}
+
+int sigma_threads() { return kSigmaThreads; }
 
 }  // namespace fovea
