@@ -149,9 +149,11 @@ int fovea_sigma_table(fovea_ctx* ctx, float fix_x, float fix_y, float* sigma_dev
 /* Kernel configuration of the forward path. Chosen by the built-in
  * autotuner (fovea_autotune) or set explicitly (fovea_set_config). */
 typedef struct {
-  int threads;        /* threads per CTA of the forward kernel: 128 or 256 */
+  int threads;        /* threads per CTA of the forward kernel: 256 */
   int ctas_per_sm;    /* persistent CTAs per SM (0 = as many as fit) */
   int rows_per_chunk; /* tile rows staged per chunk: 16, 32 or 64 */
+  int tensor_cores;   /* 1: uint8 frames on the tensor-core kernel (fp16 hi/lo split
+                         operands, fp32 accumulation); 0: fp32 FMA kernel */
 } fovea_config;
 
 int fovea_get_config(const fovea_ctx* ctx, fovea_config* cfg);

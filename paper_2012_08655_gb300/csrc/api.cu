@@ -54,7 +54,7 @@ struct fovea_ctx {
   double sigma0 = 0.0, k = 0.0;
   bool batch_only = false;
   int device = 0, num_sms = 0;
-  FwdConfig cfg{256, 0, 32};
+  FwdConfig cfg{256, 0, 32, 1};
   bool cfg_tuned = false;
   Workspace ws{};
   cudaStream_t capture_stream = nullptr;
@@ -179,8 +179,11 @@ int sigma_grid(long long items, int num_sms) {
   return (int)std::max<long long>(1, std::min<long long>(g, 4ll * num_sms));
 }
 
+bool use_tc(const fovea_ctx* ctx, int fmt_mask) { return ctx->cfg.tc && fmt_mask == 1; }
+
 int forward_grid(fovea_ctx* ctx, int rmax, int fmt_mask) {
-  int per = forward_max_ctas_per_sm(ctx->cfg, rmax, fmt_mask);
+  int per = use_tc(ctx, fmt_mask) ? tc_forward_max_ctas_per_sm(ctx->cfg, rmax)
+                                  : forward_max_ctas_per_sm(ctx->cfg, rmax, fmt_mask);
   if (per <= 0) return 0;
   if (ctx->cfg.ctas_per_sm > 0) per = std::min(per, ctx->cfg.ctas_per_sm);
   return per * ctx->num_sms;
@@ -292,7 +295,8 @@ int enqueue_batch_kernels(fovea_ctx* ctx, bool adjoint, int rbound, int fmt_mask
   } else {
     int grid = forward_grid(ctx, rbound, fmt_mask);
     if (grid <= 0) return FOVEA_EUNSUPPORTED;
-    e = launch_forward(src, ctx->ws, ctx->cfg, rbound, fmt_mask, grid, s);
+    e = use_tc(ctx, fmt_mask) ? launch_tc_forward(src, ctx->ws, ctx->cfg, rbound, grid, s, BucketList{nullptr, 0, 0}, false)
+                              : launch_forward(src, ctx->ws, ctx->cfg, rbound, fmt_mask, grid, s);
   }
   if (e != cudaSuccess) return cuda_fail(e);
   return FOVEA_OK;
@@ -410,7 +414,9 @@ int fovea_render(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x,
   if (ctx->kev_start) FOVEA_CUDA(cudaEventRecord(ctx->kev_start, s));
   // Programmatic dependent launch lets the blur kernel's prologue overlap the
   // sigma kernel (not when its launch is bracketed by timing events).
-  e = launch_forward(src, ctx->ws, ctx->cfg, rmax, fmt_mask, grid, s, bl, bl.list && !ctx->kev_start);
+  const bool pdl = bl.list && !ctx->kev_start;
+  e = use_tc(ctx, fmt_mask) ? launch_tc_forward(src, ctx->ws, ctx->cfg, rmax, grid, s, bl, pdl)
+                            : launch_forward(src, ctx->ws, ctx->cfg, rmax, fmt_mask, grid, s, bl, pdl);
   if (e != cudaSuccess) return cuda_fail(e);
   if (ctx->kev_stop) FOVEA_CUDA(cudaEventRecord(ctx->kev_stop, s));
   return FOVEA_OK;
@@ -497,6 +503,7 @@ int fovea_get_config(const fovea_ctx* ctx, fovea_config* cfg) {
   cfg->threads = ctx->cfg.threads;
   cfg->ctas_per_sm = ctx->cfg.ctas_per_sm;
   cfg->rows_per_chunk = ctx->cfg.rows_per_chunk;
+  cfg->tensor_cores = ctx->cfg.tc;
   return FOVEA_OK;
 }
 
@@ -505,8 +512,9 @@ int fovea_set_config(fovea_ctx* ctx, const fovea_config* cfg) {
   if (cfg->threads != 256) return FOVEA_EUNSUPPORTED;
   if (cfg->rows_per_chunk != 16 && cfg->rows_per_chunk != 32 && cfg->rows_per_chunk != 64) return FOVEA_EUNSUPPORTED;
   if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 8) return FOVEA_EINVAL;
-  FwdConfig c{cfg->threads, cfg->ctas_per_sm, cfg->rows_per_chunk};
-  if (ctx->cfg.rows_per_chunk != c.rows_per_chunk || ctx->cfg.ctas_per_sm != c.ctas_per_sm) {
+  if (cfg->tensor_cores != 0 && cfg->tensor_cores != 1) return FOVEA_EINVAL;
+  FwdConfig c{cfg->threads, cfg->ctas_per_sm, cfg->rows_per_chunk, cfg->tensor_cores};
+  if (ctx->cfg.rows_per_chunk != c.rows_per_chunk || ctx->cfg.ctas_per_sm != c.ctas_per_sm || ctx->cfg.tc != c.tc) {
     for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
     ctx->graphs.clear();
   }

@@ -254,7 +254,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 struct FwdConfig {
   int threads;        // 256
   int ctas_per_sm;
-  int rows_per_chunk; // RB, multiple of 8
+  int rows_per_chunk; // RB, multiple of 16
+  int tc;             // uint8 frames on the tensor-core kernel
 };
 
 cudaError_t launch_sigma_order(const FrameSource& src, const Workspace& ws, int grid_ctas,
@@ -272,6 +273,11 @@ cudaError_t launch_forward(const FrameSource& src, const Workspace& ws, const Fw
                            int rmax, int fmt_mask, int grid, cudaStream_t s,
                            const BucketList& bl = BucketList{nullptr, 0, 0}, bool pdl = false);
 int forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int fmt_mask);
+// Tensor-core variant (uint8 HWC frames only).
+size_t tc_forward_smem_bytes(const FwdConfig& cfg, int rmax);
+int tc_forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax);
+cudaError_t launch_tc_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg, int rmax,
+                              int grid, cudaStream_t s, const BucketList& bl, bool pdl);
 size_t adjoint_smem_bytes(int rmax);
 cudaError_t launch_adjoint(const FrameSource& src, const Workspace& ws, int rmax, int grid,
                            cudaStream_t s);

@@ -25,6 +25,7 @@ namespace {
 struct Choice {
   int rows_per_chunk;
   int ctas_per_sm;
+  int tc;
   double ms;
 };
 
@@ -50,14 +51,14 @@ void load_file(const char* path) {
   std::ifstream f(path);
   std::string line;
   while (std::getline(f, line)) {
-    // "key": {"rows_per_chunk": R, "ctas_per_sm": N, "ms": T},
+    // "key": {"rows_per_chunk": R, "ctas_per_sm": N, "tensor_cores": T, "ms": M},
     size_t a = line.find('"');
     size_t b = a == std::string::npos ? a : line.find('"', a + 1);
     if (b == std::string::npos) continue;
     std::string key = line.substr(a + 1, b - a - 1);
-    Choice c{0, 0, 0.0};
-    if (std::sscanf(line.c_str() + b + 1, ": {\"rows_per_chunk\": %d, \"ctas_per_sm\": %d, \"ms\": %lf",
-                    &c.rows_per_chunk, &c.ctas_per_sm, &c.ms) == 3)
+    Choice c{0, 0, 0, 0.0};
+    if (std::sscanf(line.c_str() + b + 1, ": {\"rows_per_chunk\": %d, \"ctas_per_sm\": %d, \"tensor_cores\": %d, \"ms\": %lf",
+                    &c.rows_per_chunk, &c.ctas_per_sm, &c.tc, &c.ms) == 4)
       g_cache[key] = c;
   }
 }
@@ -68,7 +69,8 @@ void save_file(const char* path) {
   size_t i = 0;
   for (const auto& kv : g_cache) {
     f << "  \"" << kv.first << "\": {\"rows_per_chunk\": " << kv.second.rows_per_chunk
-      << ", \"ctas_per_sm\": " << kv.second.ctas_per_sm << ", \"ms\": " << kv.second.ms << "}"
+      << ", \"ctas_per_sm\": " << kv.second.ctas_per_sm << ", \"tensor_cores\": " << kv.second.tc
+      << ", \"ms\": " << kv.second.ms << "}"
       << (++i < g_cache.size() ? ",\n" : "\n");
   }
   f << "}\n";
@@ -82,7 +84,7 @@ void fovea_apply_cached_config(fovea_ctx* ctx) {
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_cache.find(make_key(ctx));
   if (it == g_cache.end()) return;
-  fovea_config cfg{256, it->second.ctas_per_sm, it->second.rows_per_chunk};
+  fovea_config cfg{256, it->second.ctas_per_sm, it->second.rows_per_chunk, it->second.tc};
   fovea_set_config(ctx, &cfg);
 }
 
@@ -96,7 +98,7 @@ extern "C" int fovea_autotune(fovea_ctx* ctx, int iters, const char* cache_path)
     if (cache_path) load_file(cache_path);
     auto it = g_cache.find(key);
     if (it != g_cache.end()) {
-      fovea_config cfg{256, it->second.ctas_per_sm, it->second.rows_per_chunk};
+      fovea_config cfg{256, it->second.ctas_per_sm, it->second.rows_per_chunk, it->second.tc};
       return fovea_set_config(ctx, &cfg);
     }
   }
@@ -106,7 +108,7 @@ extern "C" int fovea_autotune(fovea_ctx* ctx, int iters, const char* cache_path)
   cudaStream_t s = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int status = FOVEA_OK;
-  Choice best{0, 0, 1e30};
+  Choice best{0, 0, 0, 1e30};
   fovea_config saved;
   fovea_get_config(ctx, &saved);
   if (cudaMalloc(&in, nb) != cudaSuccess || cudaMalloc(&out, nb) != cudaSuccess ||
@@ -118,9 +120,11 @@ extern "C" int fovea_autotune(fovea_ctx* ctx, int iters, const char* cache_path)
   const float fx = 0.5f * (float)W, fy = 0.5f * (float)H;
   const int rbs[3] = {16, 32, 64};
   const int ctas[3] = {1, 2, 0};
+  const int ntc = fmt == FOVEA_U8_HWC ? 2 : 1;
+  for (int tcv = 0; tcv < ntc && status == FOVEA_OK; ++tcv)
   for (int a = 0; a < 3 && status == FOVEA_OK; ++a) {
     for (int b = 0; b < 3 && status == FOVEA_OK; ++b) {
-      fovea_config cfg{256, ctas[b], rbs[a]};
+      fovea_config cfg{256, ctas[b], rbs[a], tcv};
       if (fovea_set_config(ctx, &cfg) != FOVEA_OK) continue;
       int st = FOVEA_OK;
       for (int w = 0; w < 2 && st == FOVEA_OK; ++w) st = fovea_render(ctx, in, out, fx, fy, s);
@@ -133,7 +137,7 @@ extern "C" int fovea_autotune(fovea_ctx* ctx, int iters, const char* cache_path)
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
       const double per = (double)ms / iters;
-      if (per < best.ms) best = Choice{rbs[a], ctas[b], per};
+      if (per < best.ms) best = Choice{rbs[a], ctas[b], tcv, per};
     }
   }
   if (e0) cudaEventDestroy(e0);
@@ -145,7 +149,7 @@ extern "C" int fovea_autotune(fovea_ctx* ctx, int iters, const char* cache_path)
     fovea_set_config(ctx, &saved);
     return status != FOVEA_OK ? status : FOVEA_EUNSUPPORTED;
   }
-  fovea_config cfg{256, best.ctas_per_sm, best.rows_per_chunk};
+  fovea_config cfg{256, best.ctas_per_sm, best.rows_per_chunk, best.tc};
   fovea_set_config(ctx, &cfg);
   std::lock_guard<std::mutex> lk(g_mu);
   g_cache[key] = best;

@@ -47,7 +47,8 @@ class Frame(ctypes.Structure):
 
 
 class Config(ctypes.Structure):
-    _fields_ = [("threads", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("rows_per_chunk", ctypes.c_int)]
+    _fields_ = [("threads", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("rows_per_chunk", ctypes.c_int),
+                ("tensor_cores", ctypes.c_int)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -220,10 +221,11 @@ class Context:
     def get_config(self) -> dict:
         c = Config()
         _check(_lib.fovea_get_config(self._h, ctypes.byref(c)), "fovea_get_config")
-        return {"threads": c.threads, "ctas_per_sm": c.ctas_per_sm, "rows_per_chunk": c.rows_per_chunk}
+        return {"threads": c.threads, "ctas_per_sm": c.ctas_per_sm, "rows_per_chunk": c.rows_per_chunk,
+                "tensor_cores": c.tensor_cores}
 
-    def set_config(self, threads=256, ctas_per_sm=0, rows_per_chunk=32):
-        c = Config(int(threads), int(ctas_per_sm), int(rows_per_chunk))
+    def set_config(self, threads=256, ctas_per_sm=0, rows_per_chunk=32, tensor_cores=1):
+        c = Config(int(threads), int(ctas_per_sm), int(rows_per_chunk), int(tensor_cores))
         _check(_lib.fovea_set_config(self._h, ctypes.byref(c)), "fovea_set_config")
 
     def autotune(self, iters: int = 20, cache_path: Optional[str] = None) -> dict:

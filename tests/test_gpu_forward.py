@@ -181,3 +181,28 @@ def test_argument_errors(fv):
     with pytest.raises(fv.FoveaError) as e:
         big.render(x, torch.empty_like(x), 0.0, 0.0)
     assert e.value.status == fv.EUNSUPPORTED
+
+
+# ---------------------------------------------------------------- tensor-core kernel vs fp32 kernel
+
+@pytest.mark.parametrize("W,H,C,B,fx,fy,k", [
+    (1920, 1080, 3, 32, 960.0, 540.0, 0.02),
+    (333, 221, 1, 32, 10.0, 200.0, 0.1),
+    (640, 480, 4, 16, 600.0, 30.0, 0.3),
+    (129, 77, 2, 8, 64.0, 38.0, 0.05),
+])
+def test_tensor_core_kernel_matches_fp32_kernel(fv, W, H, C, B, fx, fy, k):
+    img = wl.grating_frame(H, W, C, seed=W + C)
+    x = to_dev(img)
+    ctx = fv.Context(W, H, C, B, 0.5, k, fv.U8_HWC)
+    ctx.set_config(256, 0, 32, tensor_cores=0)
+    y32 = torch.empty_like(x)
+    ctx.render(x, y32, fx, fy)
+    ctx.set_config(256, 0, 32, tensor_cores=1)
+    ytc = torch.empty_like(x)
+    ctx.render(x, ytc, fx, fy)
+    torch.cuda.synchronize()
+    assert_u8_close(ytc.cpu().numpy(), y32.cpu().numpy(), min_equal=0.995)
+    blocks = sample_blocks(W, H, B, fx, fy, n_random=16, seed=3)
+    ref = oracle.forward_u8(img, B, fx, fy, 0.5, k, "hwc", blocks=blocks)
+    assert_u8_close(ytc.cpu().numpy(), ref, mask=block_mask(W, H, B, blocks, "hwc", C), min_equal=0.995)
