@@ -174,6 +174,34 @@ int fovea_set_kernel_events(fovea_ctx* ctx, void* ev_start, void* ev_stop);
 
 void fovea_destroy(fovea_ctx* ctx);
 
+/* Most blocks a frame may have for fovea_render_noalloc (e.g. 3840x2160 at
+ * B = 32 is 8160 blocks). */
+#define FOVEA_NOALLOC_MAX_BLOCKS 16384
+
+/* Foveate one device-resident frame without allocating any memory. The paper
+ * has no counterpart; this entry point exists for callers that cannot call
+ * cudaMalloc -- code whose device memory is owned by a host framework or a
+ * server that has reserved it up front, or that must not allocate while it
+ * drives the GPU -- and for whom fovea_create's workspace is not an option.
+ * Arguments are those of fovea_create and fovea_render combined; the caller
+ * still owns and passes the input and output buffers. All working memory
+ * (per-block sigma/radius records, the radius-ordered work list, counters;
+ * about 0.5 MB) is one fixed-size array inside the library image, held by
+ * every GPU that loads the library until the process exits. No cudaMalloc,
+ * cudaFree or allocating library routine is called.
+ *   - Frames with more than FOVEA_NOALLOC_MAX_BLOCKS blocks are refused with
+ *     FOVEA_EUNSUPPORTED before any work is enqueued.
+ *   - The first call on a device looks up the array's device address (a
+ *     one-time set-up per device, with that device current); make that first
+ *     call before any stream capture.
+ *   - Every call uses the same array, which keeps the last call's contents;
+ *     each call clears the counters that must start at zero on its stream.
+ *     Calls whose GPU work overlaps (other streams, other host threads) race
+ *     and must be serialised by the caller. */
+int fovea_render_noalloc(const void* in_dev, void* out_dev, int width, int height, int channels,
+                         int format, int block, double sigma0, double k, float fix_x, float fix_y,
+                         void* stream);
+
 const char* fovea_strerror(int status);
 
 /* The cudaError_t of the last failed CUDA call in this thread (0 if none). */

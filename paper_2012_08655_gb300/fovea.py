@@ -76,6 +76,7 @@ _sig = {
     "fovea_autotune": (_i, [_vp, _i, ctypes.c_char_p]),
     "fovea_set_kernel_events": (_i, [_vp, _vp, _vp]),
     "fovea_destroy": (None, [_vp]),
+    "fovea_render_noalloc": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _d, _d, _f, _f, _vp]),
     "fovea_strerror": (ctypes.c_char_p, [_i]),
     "fovea_last_cuda_error": (_i, []),
     "fovea_server_create": (_i, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)]),
@@ -288,6 +289,21 @@ def foveate(x: torch.Tensor, fix_x: float, fix_y: float, sigma0: float = 0.5, k:
     if out is None:
         out = torch.empty_like(x)
     return ctx.render(x, out, fix_x, fix_y)
+
+
+def render_noalloc(x: torch.Tensor, out: torch.Tensor, fix_x: float, fix_y: float, sigma0: float = 0.5,
+                   k: float = 0.02, block: int = 32, stream=None) -> torch.Tensor:
+    """Foveate one device frame through ``fovea_render_noalloc``: same kernels
+    as :func:`foveate`, no memory allocated by the library (its scratch is a
+    fixed array inside the library; calls that overlap on the GPU race)."""
+    _require_device_frame(x, "input")
+    _require_device_frame(out, "output")
+    fmt = _fmt_of(x)
+    w, h, c = _shape_of(x, fmt)
+    _check(_lib.fovea_render_noalloc(x.data_ptr(), out.data_ptr(), w, h, c, fmt, int(block), float(sigma0),
+                                     float(k), float(fix_x), float(fix_y), _stream_handle(stream)),
+           "fovea_render_noalloc")
+    return out
 
 
 def sigma_table(width: int, height: int, fix_x: float, fix_y: float, sigma0: float = 0.5, k: float = 0.02,
