@@ -65,7 +65,7 @@ struct fovea_ctx {
   cudaEvent_t batch_ev[kBatchSlots] = {};
   size_t batch_host_cap = 0;
   int batch_slot = 0;
-  // CUDA graphs of the batch launch sequence, keyed by (kind + 2*format mask, radius bound)
+  // CUDA graphs of the batch launch sequence, keyed by (kind + 2*format mask + 8*tc channels, radius bound)
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
   // optional events bracketing the persistent blur kernel (measurement)
   cudaEvent_t kev_start = nullptr, kev_stop = nullptr;
@@ -179,11 +179,13 @@ int sigma_grid(long long items, int num_sms) {
   return (int)std::max<long long>(1, std::min<long long>(g, 4ll * num_sms));
 }
 
-bool use_tc(const fovea_ctx* ctx, int fmt_mask) { return ctx->cfg.tc && fmt_mask == 1; }
+// The tensor-core kernel serves launches whose frames are all uint8 with one
+// channel count (tc_c = that count, 0 otherwise).
+bool use_tc(const fovea_ctx* ctx, int fmt_mask, int tc_c) { return ctx->cfg.tc && fmt_mask == 1 && tc_c > 0; }
 
-int forward_grid(fovea_ctx* ctx, int rmax, int fmt_mask) {
-  int per = use_tc(ctx, fmt_mask) ? tc_forward_max_ctas_per_sm(ctx->cfg, rmax)
-                                  : forward_max_ctas_per_sm(ctx->cfg, rmax, fmt_mask);
+int forward_grid(fovea_ctx* ctx, int rmax, int fmt_mask, int tc_c) {
+  int per = use_tc(ctx, fmt_mask, tc_c) ? tc_forward_max_ctas_per_sm(ctx->cfg, rmax, tc_c)
+                                        : forward_max_ctas_per_sm(ctx->cfg, rmax, fmt_mask);
   if (per <= 0) return 0;
   if (ctx->cfg.ctas_per_sm > 0) per = std::min(per, ctx->cfg.ctas_per_sm);
   return per * ctx->num_sms;
@@ -198,12 +200,12 @@ int adjoint_grid(fovea_ctx* ctx, int rmax) {
 // Stage n frame descriptors into the pinned slot ring and copy them to the
 // device-resident batch buffer on `s`. Returns total items in *total.
 int upload_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint, cudaStream_t s,
-                 long long* total, int* rmax, int* fmt_mask) {
+                 long long* total, int* rmax, int* fmt_mask, int* tc_c) {
   if (n <= 0 || !frames) return FOVEA_EINVAL;
   std::vector<FrameDesc> descs((size_t)n);
   long long item0 = 0;
   int rm = 0;
-  int mask = 0;
+  int mask = 0, cc = -1;
   for (int i = 0; i < n; ++i) {
     const fovea_frame& f = frames[i];
     int st = check_frame(f.width, f.height, f.channels, f.format, ctx->B, f.sigma0, f.k, f.fix_x, f.fix_y);
@@ -217,6 +219,7 @@ int upload_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint,
     item0 += (long long)descs[(size_t)i].nbx * descs[(size_t)i].nby;
     rm = std::max(rm, radius_bound(f.width, f.height, ctx->B, f.fix_x, f.fix_y, f.sigma0, f.k));
     mask |= f.format == FOVEA_F32_CHW ? 2 : 1;
+    cc = cc == -1 ? f.channels : (cc == f.channels ? cc : 0);
   }
   if (item0 > (1ll << 31) - 1) return FOVEA_EUNSUPPORTED;
   int st = ensure_workspace(ctx, item0);
@@ -262,6 +265,7 @@ int upload_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint,
   *total = item0;
   *rmax = rm;
   *fmt_mask = mask;
+  *tc_c = cc > 0 ? cc : 0;
   return FOVEA_OK;
 }
 
@@ -274,7 +278,7 @@ FrameSource batch_source(fovea_ctx* ctx) {
 }
 
 // Enqueue (or capture) the batch launch sequence for the current batch buffer.
-int enqueue_batch_kernels(fovea_ctx* ctx, bool adjoint, int rbound, int fmt_mask, cudaStream_t s) {
+int enqueue_batch_kernels(fovea_ctx* ctx, bool adjoint, int rbound, int fmt_mask, int tc_c, cudaStream_t s) {
   const FrameSource src = batch_source(ctx);
   const int sg = 4 * ctx->num_sms;
   if (adjoint) {
@@ -293,10 +297,11 @@ int enqueue_batch_kernels(fovea_ctx* ctx, bool adjoint, int rbound, int fmt_mask
     if (grid <= 0) return FOVEA_EUNSUPPORTED;
     e = launch_adjoint(src, ctx->ws, rbound, grid, s);
   } else {
-    int grid = forward_grid(ctx, rbound, fmt_mask);
+    int grid = forward_grid(ctx, rbound, fmt_mask, tc_c);
     if (grid <= 0) return FOVEA_EUNSUPPORTED;
-    e = use_tc(ctx, fmt_mask) ? launch_tc_forward(src, ctx->ws, ctx->cfg, rbound, grid, s, BucketList{nullptr, 0, 0}, false)
-                              : launch_forward(src, ctx->ws, ctx->cfg, rbound, fmt_mask, grid, s);
+    e = use_tc(ctx, fmt_mask, tc_c)
+            ? launch_tc_forward(src, ctx->ws, ctx->cfg, rbound, tc_c, grid, s, BucketList{nullptr, 0, 0}, false)
+            : launch_forward(src, ctx->ws, ctx->cfg, rbound, fmt_mask, grid, s);
   }
   if (e != cudaSuccess) return cuda_fail(e);
   return FOVEA_OK;
@@ -305,19 +310,19 @@ int enqueue_batch_kernels(fovea_ctx* ctx, bool adjoint, int rbound, int fmt_mask
 int run_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint, cudaStream_t s) {
   long long total = 0;
   int rmax = 0;
-  int fmt_mask = 0;
-  int st = upload_batch(ctx, frames, n, adjoint, s, &total, &rmax, &fmt_mask);
+  int fmt_mask = 0, tc_c = 0;
+  int st = upload_batch(ctx, frames, n, adjoint, s, &total, &rmax, &fmt_mask, &tc_c);
   if (st != FOVEA_OK) return st;
   // Radius bound of the graph: next multiple of 64 (shared-memory size of
   // the persistent kernel depends on it).
   const int rbound = std::min(kMaxRadius, ((rmax + 63) / 64) * 64);
-  const auto key = std::make_pair((adjoint ? 1 : 0) + 2 * fmt_mask, rbound);
+  const auto key = std::make_pair((adjoint ? 1 : 0) + 2 * fmt_mask + 8 * tc_c, rbound);
   auto it = ctx->graphs.find(key);
   if (it == ctx->graphs.end()) {
     if (!ctx->capture_stream) FOVEA_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
     FOVEA_CUDA(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-    st = enqueue_batch_kernels(ctx, adjoint, rbound, fmt_mask, ctx->capture_stream);
+    st = enqueue_batch_kernels(ctx, adjoint, rbound, fmt_mask, tc_c, ctx->capture_stream);
     cudaError_t ee = cudaStreamEndCapture(ctx->capture_stream, &g);
     if (st != FOVEA_OK) {
       if (g) cudaGraphDestroy(g);
@@ -387,7 +392,8 @@ int fovea_render(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x,
   src.one_total = (long long)src.one.nbx * src.one.nby;
   const int rmax = radius_bound(ctx->W, ctx->H, ctx->B, fix_x, fix_y, ctx->sigma0, ctx->k);
   const int fmt_mask = ctx->fmt == FOVEA_F32_CHW ? 2 : 1;
-  const int grid = forward_grid(ctx, rmax, fmt_mask);
+  const int tc_c = ctx->C;
+  const int grid = forward_grid(ctx, rmax, fmt_mask, tc_c);
   if (grid <= 0) return FOVEA_EUNSUPPORTED;
   // Single frame: the sigma kernel also files every block under its radius
   // and the blur kernel orders its own work (largest radius first) from the
@@ -415,8 +421,8 @@ int fovea_render(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x,
   // Programmatic dependent launch lets the blur kernel's prologue overlap the
   // sigma kernel (not when its launch is bracketed by timing events).
   const bool pdl = bl.list && !ctx->kev_start;
-  e = use_tc(ctx, fmt_mask) ? launch_tc_forward(src, ctx->ws, ctx->cfg, rmax, grid, s, bl, pdl)
-                            : launch_forward(src, ctx->ws, ctx->cfg, rmax, fmt_mask, grid, s, bl, pdl);
+  e = use_tc(ctx, fmt_mask, tc_c) ? launch_tc_forward(src, ctx->ws, ctx->cfg, rmax, tc_c, grid, s, bl, pdl)
+                                  : launch_forward(src, ctx->ws, ctx->cfg, rmax, fmt_mask, grid, s, bl, pdl);
   if (e != cudaSuccess) return cuda_fail(e);
   if (ctx->kev_stop) FOVEA_CUDA(cudaEventRecord(ctx->kev_stop, s));
   return FOVEA_OK;

@@ -273,10 +273,10 @@ cudaError_t launch_forward(const FrameSource& src, const Workspace& ws, const Fw
                            int rmax, int fmt_mask, int grid, cudaStream_t s,
                            const BucketList& bl = BucketList{nullptr, 0, 0}, bool pdl = false);
 int forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int fmt_mask);
-// Tensor-core variant (uint8 HWC frames only).
+// Tensor-core variant (uint8 HWC frames, all with C channels).
 size_t tc_forward_smem_bytes(const FwdConfig& cfg, int rmax);
-int tc_forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax);
-cudaError_t launch_tc_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg, int rmax,
+int tc_forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int C);
+cudaError_t launch_tc_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg, int rmax, int C,
                               int grid, cudaStream_t s, const BucketList& bl, bool pdl);
 size_t adjoint_smem_bytes(int rmax);
 cudaError_t launch_adjoint(const FrameSource& src, const Workspace& ws, int rmax, int grid,

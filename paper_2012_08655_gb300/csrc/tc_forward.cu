@@ -30,7 +30,7 @@ constexpr float kWScale = 4096.0f;
 constexpr float kWInv = 1.0f / 4096.0f;
 constexpr int kThPitch = 264;          // halves per staged fp16 row: 528 B (odd multiple of 16 B)
 constexpr int kPairPad = 32;           // tap index -kPairPad is pair entry 0
-constexpr int kVHalves = 128 * 72;     // halves of one V array (max over C of 32C rows x pitch)
+constexpr int kVHalves = 128 * 72;     // halves of one V array (max over C of 32C rows x VP)
 
 __host__ __device__ inline int npair(int rmax) { return rmax + 56; }
 
@@ -56,14 +56,63 @@ __device__ __forceinline__ unsigned int pack_half2(__half a, __half b) {
   return (unsigned int)__half_as_ushort(a) | ((unsigned int)__half_as_ushort(b) << 16);
 }
 
-// 4 uint8 -> 4 fp16, exactly: 0x64XX is 1024 + XX.
-__device__ __forceinline__ uint2 u8x4_to_h4(unsigned int w) {
+// Two bytes (low half of x) -> two fp16, exactly: 0x64XX is 1024 + XX.
+__device__ __forceinline__ unsigned int u8x2_to_h2(unsigned int x) {
+  const unsigned int b = __byte_perm(x, 0x64646464u, 0x5140);
   const __half2 bias = __halves2half2(__ushort_as_half(0x6400), __ushort_as_half(0x6400));
-  const unsigned int lo = __byte_perm(w, 0x64646464u, 0x5140);
-  const unsigned int hi = __byte_perm(w, 0x64646464u, 0x7362);
-  __half2 a = __hsub2(*reinterpret_cast<const __half2*>(&lo), bias);
-  __half2 b = __hsub2(*reinterpret_cast<const __half2*>(&hi), bias);
-  return make_uint2(*reinterpret_cast<unsigned int*>(&a), *reinterpret_cast<unsigned int*>(&b));
+  __half2 h = __hsub2(*reinterpret_cast<const __half2*>(&b), bias);
+  return *reinterpret_cast<unsigned int*>(&h);
+}
+
+__device__ __forceinline__ void stsm_x4(void* p, unsigned int r0, unsigned int r1, unsigned int r2, unsigned int r3) {
+  const unsigned int s = (unsigned int)__cvta_generic_to_shared(p);
+  asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1,%2,%3,%4};\n" ::"r"(s), "r"(r0), "r"(r1), "r"(r2),
+               "r"(r3) : "memory");
+}
+
+__device__ __forceinline__ unsigned int pack_f2h2(float a, float b) {
+  __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<unsigned int*>(&h);
+}
+
+// Per channel count: fp16 columns reserved per channel in a staged row, and
+// the pitch (halves) of the pass-2 operand rows (odd multiple of 16 bytes).
+template <int C> struct TcGeo;
+template <> struct TcGeo<1> { static constexpr int PXP = 256, VP = 264; };
+template <> struct TcGeo<2> { static constexpr int PXP = 128, VP = 136; };
+template <> struct TcGeo<3> { static constexpr int PXP = 80, VP = 88; };
+template <> struct TcGeo<4> { static constexpr int PXP = 64, VP = 72; };
+
+// One staged uint8 row -> fp16, de-interleaving the channels: pixels 8q..8q+7
+// of every channel c go to Th[c*PXP + 8q ...]; pixels >= npx become 0.
+// PH3 is the slab's byte phase modulo 4 (ring byte of pixel p, channel c is
+// ph + C*p + c), so every byte position below is a compile-time constant.
+template <int C, int PH3>
+__device__ __forceinline__ void convert_group(const unsigned char* rowp, int ph, int q, int npx, __half* throw_) {
+  constexpr int NW = 2 * C + 1;
+  const int w0 = (ph + 8 * C * q) >> 2;
+  const unsigned int* wp = reinterpret_cast<const unsigned int*>(rowp);
+  unsigned int wd[NW];
+  #pragma unroll
+  for (int k = 0; k < NW; ++k) wd[k] = (w0 + k < kRowBytesU8 / 4) ? wp[w0 + k] : 0u;
+  #pragma unroll
+  for (int c = 0; c < C; ++c) {
+    unsigned int h[4];
+    #pragma unroll
+    for (int i2 = 0; i2 < 4; ++i2) {
+      const int b0 = PH3 + C * (2 * i2) + c, b1 = b0 + C;
+      const unsigned int x = __byte_perm(wd[b0 >> 2], wd[b1 >> 2], (b0 & 3) | (((b1 & 3) + 4) << 4));
+      h[i2] = u8x2_to_h2(x);
+    }
+    if (8 * q + 8 > npx) {
+      #pragma unroll
+      for (int i2 = 0; i2 < 4; ++i2) {
+        if (8 * q + 2 * i2 >= npx) h[i2] = 0u;
+        else if (8 * q + 2 * i2 + 1 >= npx) h[i2] &= 0xFFFFu;
+      }
+    }
+    *reinterpret_cast<uint4*>(throw_ + c * TcGeo<C>::PXP + 8 * q) = make_uint4(h[0], h[1], h[2], h[3]);
+  }
 }
 
 __device__ __forceinline__ void mma16816(float (&d)[4], const unsigned int (&a)[4], unsigned int b0, unsigned int b1) {
@@ -109,7 +158,274 @@ __device__ __forceinline__ void make_pairs(const float2* U, unsigned int* P, int
   }
 }
 
-template <int RB>
+
+// Everything the tensor-core kernel does for one item with C channels.
+template <int RB, int C>
+__device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned char* ring, __half* Th, __half* Vh,
+                                        __half* Vl, float2* U, float* CU, unsigned int* P, float* red, int np) {
+  constexpr int PXP = TcGeo<C>::PXP, VP = TcGeo<C>::VP;
+  constexpr size_t stage_bytes = (size_t)RB * kRowBytesU8;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int r = it.r;
+  const int Q = it.nsl * it.nchunks;
+  const size_t frame_bytes = (size_t)it.H * it.pitch;
+
+  #pragma unroll
+  for (int q = 0; q < kStages - 1; ++q) {
+    if (q < Q) stage_rows<true, RB>(it, slab_of<true>(it, q / it.nchunks), q % it.nchunks,
+                                    ring + (size_t)q * stage_bytes, frame_bytes);
+    cp_async_commit();
+  }
+  make_taps(U, tap_len(r), r, c_tap, red);
+  make_cumulative(U, CU, r);
+  make_pairs(U, P, r, np);
+  __syncthreads();
+
+  // Pass 1: each lane reads the tap-pair table of its parity (the tap index
+  // of every A register of this lane has the parity of g, D0 being even).
+  const unsigned int* Ph = P + ((g & 1) ? np : 0);
+  const unsigned int* Pl = P + 2 * np + ((g & 1) ? np : 0);
+  const int D0 = it.offy - it.ph;  // tap(v, yo) = v + D0 - yo
+
+  float acc1[2][4][4];
+  float acc2[C][4];
+  #pragma unroll
+  for (int i = 0; i < C; ++i)
+    #pragma unroll
+    for (int k = 0; k < 4; ++k) acc2[i][k] = 0.f;
+
+  for (int q = 0; q < Q; ++q) {
+    cp_async_wait<kStages - 2>();
+    __syncthreads();  // chunk q landed; the previous chunk's fragments are consumed
+    {
+      const int qn = q + kStages - 1;
+      if (qn < Q) stage_rows<true, RB>(it, slab_of<true>(it, qn / it.nchunks), qn % it.nchunks,
+                                       ring + (size_t)(qn % kStages) * stage_bytes, frame_bytes);
+      cp_async_commit();
+    }
+    const int s = q / it.nchunks, k = q - s * it.nchunks;
+    const Slab sl = slab_of<true>(it, s);
+    const int R0 = k * RB;
+    const int npx = sl.sws / C;                 // pixels of the slab
+    const int npx16 = (npx + 15) & ~15;
+    const int ngrp = npx16 >> 3;                // 8-pixel groups per channel
+    // ---- uint8 rows of the chunk -> channel-planar fp16 rows
+    {
+      const unsigned char* st = ring + (size_t)(q % kStages) * stage_bytes;
+      const int ph3 = sl.ph & 3;
+      for (int idx = tid; idx < RB * ngrp; idx += kThreads) {
+        const int row = idx / ngrp, gq = idx - row * ngrp;
+        const unsigned char* rowp = st + (size_t)row * kRowBytesU8;
+        __half* throw_ = Th + (size_t)row * kThPitch;
+        switch (ph3) {
+          case 0: convert_group<C, 0>(rowp, sl.ph, gq, npx, throw_); break;
+          case 1: convert_group<C, 1>(rowp, sl.ph, gq, npx, throw_); break;
+          case 2: convert_group<C, 2>(rowp, sl.ph, gq, npx, throw_); break;
+          default: convert_group<C, 3>(rowp, sl.ph, gq, npx, throw_); break;
+        }
+      }
+    }
+    __syncthreads();
+    // This warp's 32 columns: channel c0 = 32w / PXP, pixel offset inside it.
+    const int colw = 32 * warp;
+    if (k == 0) {
+      #pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+        #pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+          #pragma unroll
+          for (int i = 0; i < 4; ++i) acc1[mt][nt][i] = 0.f;
+      if (it.foldT && colw < C * PXP) {  // folded top row first: fixed summation order
+        const __half* row = Th + (size_t)it.ph * kThPitch;
+        #pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          const float2 df = __half22float2(*reinterpret_cast<const __half2*>(row + colw + 8 * nt + 2 * t));
+          #pragma unroll
+          for (int mt = 0; mt < 2; ++mt) {
+            const float c0 = cum_at(CU, it.offy - (16 * mt + g), r) * kWScale;
+            const float c1 = cum_at(CU, it.offy - (16 * mt + g + 8), r) * kWScale;
+            acc1[mt][nt][0] = fmaf(c0, df.x, acc1[mt][nt][0]);
+            acc1[mt][nt][1] = fmaf(c0, df.y, acc1[mt][nt][1]);
+            acc1[mt][nt][2] = fmaf(c1, df.x, acc1[mt][nt][2]);
+            acc1[mt][nt][3] = fmaf(c1, df.y, acc1[mt][nt][3]);
+          }
+        }
+      }
+    }
+    // n-tile pairs of this warp that hold slab pixels
+    bool pon[2];
+    #pragma unroll
+    for (int np2 = 0; np2 < 2; ++np2) {
+      const int j0 = colw + 16 * np2;
+      pon[np2] = j0 < C * PXP && (j0 % PXP) < npx16;
+    }
+    // ---- pass 1 on the chunk: 16 virtual rows per k-step
+    if (pon[0] || pon[1]) {
+      for (int ks = 0; ks < RB / 16; ++ks) {
+        const int k0 = R0 + 16 * ks;
+        if (k0 >= it.vrows) break;
+        const bool on0 = k0 + 15 >= -D0 && k0 <= 15 - D0 + 2 * r;
+        const bool on1 = k0 + 15 >= 16 - D0 && k0 <= 31 - D0 + 2 * r;
+        if (!on0 && !on1) continue;
+        const int j0 = (k0 + D0 + 2 * t - g + kPairPad) >> 1;
+        unsigned int ah[2][4], al[2][4];
+        {
+          const unsigned int h_m12 = Ph[j0 - 12], h_m8 = Ph[j0 - 8], h_m4 = Ph[j0 - 4], h_0 = Ph[j0], h_p4 = Ph[j0 + 4];
+          const unsigned int l_m12 = Pl[j0 - 12], l_m8 = Pl[j0 - 8], l_m4 = Pl[j0 - 4], l_0 = Pl[j0], l_p4 = Pl[j0 + 4];
+          ah[0][0] = h_0; ah[0][1] = h_m4; ah[0][2] = h_p4; ah[0][3] = h_0;
+          ah[1][0] = h_m8; ah[1][1] = h_m12; ah[1][2] = h_m4; ah[1][3] = h_m8;
+          al[0][0] = l_0; al[0][1] = l_m4; al[0][2] = l_p4; al[0][3] = l_0;
+          al[1][0] = l_m8; al[1][1] = l_m12; al[1][2] = l_m4; al[1][3] = l_m8;
+        }
+        const __half* tb = Th + (size_t)(k0 - R0) * kThPitch + colw;
+        #pragma unroll
+        for (int np2 = 0; np2 < 2; ++np2) {
+          if (!pon[np2]) continue;
+          unsigned int b[4];
+          const int rrow = (lane & 7) + ((lane >> 3) & 1) * 8;
+          const int rcol = 16 * np2 + ((lane >> 4) & 1) * 8;
+          ldsm_x4_t(b, tb + (size_t)rrow * kThPitch + rcol);
+          #pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int nt = 2 * np2 + h;
+            const unsigned int b0 = b[2 * h], b1 = b[2 * h + 1];
+            if (on0) {
+              mma16816(acc1[0][nt], ah[0], b0, b1);
+              mma16816(acc1[0][nt], al[0], b0, b1);
+            }
+            if (on1) {
+              mma16816(acc1[1][nt], ah[1], b0, b1);
+              mma16816(acc1[1][nt], al[1], b0, b1);
+            }
+          }
+        }
+      }
+    }
+    if (k != it.nchunks - 1) continue;
+
+    // ---- slab complete: folded bottom row, then V -> hi/lo fp16 for pass 2
+    {
+      const int vb = it.ph + it.EH - 1;
+      if (it.foldB && vb >= R0 && vb < R0 + RB && colw < C * PXP) {
+        const __half* row = Th + (size_t)(vb - R0) * kThPitch;
+        #pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          const float2 df = __half22float2(*reinterpret_cast<const __half2*>(row + colw + 8 * nt + 2 * t));
+          #pragma unroll
+          for (int mt = 0; mt < 2; ++mt) {
+            const float c0 = cum_at(CU, 2 * r + 1 - (it.offy + it.EH - (16 * mt + g)), r) * kWScale;
+            const float c1 = cum_at(CU, 2 * r + 1 - (it.offy + it.EH - (16 * mt + g + 8)), r) * kWScale;
+            acc1[mt][nt][0] = fmaf(c0, df.x, acc1[mt][nt][0]);
+            acc1[mt][nt][1] = fmaf(c0, df.y, acc1[mt][nt][1]);
+            acc1[mt][nt][2] = fmaf(c1, df.x, acc1[mt][nt][2]);
+            acc1[mt][nt][3] = fmaf(c1, df.y, acc1[mt][nt][3]);
+          }
+        }
+      }
+      // V[(c, yo)][px] = acc / 2^12 as hi + lo fp16, written with stmatrix:
+      // the accumulator fragment layout is the 8x8-tile register layout.
+      #pragma unroll
+      for (int np2 = 0; np2 < 2; ++np2) {
+        if (!pon[np2]) continue;
+        const int j0 = colw + 16 * np2;
+        const int c = j0 / PXP, px0 = j0 - c * PXP;
+        #pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          unsigned int hr[4], lr[4];
+          #pragma unroll
+          for (int q4 = 0; q4 < 4; ++q4) {
+            const int nt = 2 * np2 + (q4 >> 1), ii = (q4 & 1) * 2;
+            const float v0 = acc1[mt][nt][ii] * kWInv, v1 = acc1[mt][nt][ii + 1] * kWInv;
+            hr[q4] = pack_f2h2(v0, v1);
+            const float2 hf = __half22float2(*reinterpret_cast<const __half2*>(&hr[q4]));
+            lr[q4] = pack_f2h2(v0 - hf.x, v1 - hf.y);
+          }
+          const int vrow = c * 32 + 16 * mt + (lane & 7) + ((lane >> 3) & 1) * 8;
+          const int vcol = px0 + ((lane >> 4) & 1) * 8;
+          stsm_x4(Vh + (size_t)vrow * VP + vcol, hr[0], hr[1], hr[2], hr[3]);
+          stsm_x4(Vl + (size_t)vrow * VP + vcol, lr[0], lr[1], lr[2], lr[3]);
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- pass 2 over the slab's pixels: units (row tile, column tile)
+    const int P0 = sl.e0 / C;  // first folded pixel of the slab
+    // tap index of this lane's B registers has the parity of offx + P0 - g
+    const int par2 = (it.offx + P0 + g) & 1;
+    const unsigned int* Qh = P + (par2 ? np : 0);
+    const unsigned int* Ql = P + 2 * np + (par2 ? np : 0);
+    #pragma unroll
+    for (int i = 0; i < C; ++i) {
+      const int u = warp + 8 * i;
+      const int mt2 = u >> 2, nt2 = u & 3;
+      if (it.foldL && P0 == 0) {  // folded left column first: fixed summation order
+        #pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int row = 16 * mt2 + g + 8 * h;
+          const float v = __half2float(Vh[(size_t)row * VP]) + __half2float(Vl[(size_t)row * VP]);
+          #pragma unroll
+          for (int cc = 0; cc < 2; ++cc) {
+            const int x = 8 * nt2 + 2 * t + cc;
+            acc2[i][2 * h + cc] = fmaf(cum_at(CU, it.offx - x, r) * kWScale, v, acc2[i][2 * h + cc]);
+          }
+        }
+      }
+      for (int kk = 0; kk < npx16; kk += 16) {
+        unsigned int a_h[4], a_l[4];
+        const int arow = 16 * mt2 + (lane & 7) + ((lane >> 3) & 1) * 8;
+        const int acol = kk + ((lane >> 4) & 1) * 8;
+        ldsm_x4(a_h, Vh + (size_t)arow * VP + acol);
+        ldsm_x4(a_l, Vl + (size_t)arow * VP + acol);
+        const int jb = (it.offx + P0 + kk + 2 * t - 8 * nt2 - g + kPairPad) >> 1;
+        const unsigned int bh0 = Qh[jb], bh1 = Qh[jb + 4], bl0 = Ql[jb], bl1 = Ql[jb + 4];
+        mma16816(acc2[i], a_h, bh0, bh1);
+        mma16816(acc2[i], a_h, bl0, bl1);
+        mma16816(acc2[i], a_l, bh0, bh1);
+      }
+      const int pr = it.EW - 1 - P0;  // folded right column after the last slab's products
+      if (it.foldR && pr >= 0 && pr < npx) {
+        #pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int row = 16 * mt2 + g + 8 * h;
+          const float v = __half2float(Vh[(size_t)row * VP + pr]) + __half2float(Vl[(size_t)row * VP + pr]);
+          #pragma unroll
+          for (int cc = 0; cc < 2; ++cc) {
+            const int x = 8 * nt2 + 2 * t + cc;
+            acc2[i][2 * h + cc] = fmaf(cum_at(CU, 2 * r + 1 - (it.offx + it.EW - x), r) * kWScale, v, acc2[i][2 * h + cc]);
+          }
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();  // ring and Th no longer read; Th becomes the output stage
+
+  unsigned char* ost = reinterpret_cast<unsigned char*>(Th);
+  constexpr int opitch = 32 * C;
+  #pragma unroll
+  for (int i = 0; i < C; ++i) {
+    const int u = warp + 8 * i;
+    const int mt2 = u >> 2, nt2 = u & 3;
+    #pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int row = 16 * mt2 + g + ((e >> 1) << 3);
+      const int c = row >> 5, yo = row & 31;
+      const int x = 8 * nt2 + 2 * t + (e & 1);
+      ost[yo * opitch + x * C + c] = quant_u8(acc2[i][e] * kWInv);
+    }
+  }
+  __syncthreads();
+  const int rowBytes = it.bw * C;
+  unsigned char* out = it.out + (size_t)it.y0 * it.pitch + (size_t)it.x0 * C;
+  for (int idx = tid; idx < it.bh * rowBytes; idx += kThreads) {
+    const int yo = idx / rowBytes, rem = idx - yo * rowBytes;
+    out[(size_t)yo * it.pitch + rem] = ost[yo * opitch + rem];
+  }
+}
+
+template <int RB, int C>
 __global__ void __launch_bounds__(kThreads, 2)
 tc_forward_kernel(FrameSource src, Workspace ws, int rmax, BucketList bl) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -128,10 +444,8 @@ tc_forward_kernel(FrameSource src, Workspace ws, int rmax, BucketList bl) {
   __shared__ int s_start[kBuckets];
   __shared__ int s_wsum[kThreads / 32];
 
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int g = lane >> 2, t = lane & 3;
+  const int tid = threadIdx.x;
   const int np = npair(rmax);
-  constexpr size_t stage_bytes = (size_t)RB * kRowBytesU8;
 
   asm volatile("griddepcontrol.wait;" ::: "memory");
   const bool own_order = bl.list != nullptr;
@@ -163,7 +477,7 @@ tc_forward_kernel(FrameSource src, Workspace ws, int rmax, BucketList bl) {
         } else {
           const ItemInfo inf = ws.items[item];
           const FrameDesc fd = load_frame(src, inf.frame);
-          if (inf.r > rmax || fd.fmt != FOVEA_U8_HWC) {
+          if (inf.r > rmax || fd.fmt != FOVEA_U8_HWC || fd.C != C) {
             atomicOr(&ws.counters[CNT_ERROR], 2u);
             state = 1;
           } else {
@@ -177,258 +491,7 @@ tc_forward_kernel(FrameSource src, Workspace ws, int rmax, BucketList bl) {
     __syncthreads();
     if (s_state == 2) break;
     if (s_state == 1) continue;
-    const Item& it = s_it;
-    const int r = it.r;
-    const int C = it.C;
-    const int Q = it.nsl * it.nchunks;
-    const size_t frame_bytes = (size_t)it.H * it.pitch;
-
-    #pragma unroll
-    for (int q = 0; q < kStages - 1; ++q) {
-      if (q < Q) stage_rows<true, RB>(it, slab_of<true>(it, q / it.nchunks), q % it.nchunks,
-                                      ring + (size_t)q * stage_bytes, frame_bytes);
-      cp_async_commit();
-    }
-    make_taps(U, tap_len(r), r, s_c, red);
-    make_cumulative(U, CU, r);
-    make_pairs(U, P, r, np);
-    __syncthreads();
-
-    // Pass 1: each lane reads the tap-pair table of its parity (the tap index
-    // of every A register of this lane has the parity of g, D0 being even).
-    const unsigned int* Ph = P + ((g & 1) ? np : 0);
-    const unsigned int* Pl = P + 2 * np + ((g & 1) ? np : 0);
-    const int D0 = it.offy - it.ph;  // tap(v, yo) = v + D0 - yo
-    const int vpitch = (C == 1) ? 264 : (C == 2 ? 136 : (C == 3 ? 88 : 72));
-
-    float acc1[2][4][4];
-    float acc2[4][4];
-    #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      #pragma unroll
-      for (int k = 0; k < 4; ++k) acc2[i][k] = 0.f;
-    }
-
-    for (int q = 0; q < Q; ++q) {
-      cp_async_wait<kStages - 2>();
-      __syncthreads();  // chunk q landed; the previous chunk's fragments are consumed
-      {
-        const int qn = q + kStages - 1;
-        if (qn < Q) stage_rows<true, RB>(it, slab_of<true>(it, qn / it.nchunks), qn % it.nchunks,
-                                         ring + (size_t)(qn % kStages) * stage_bytes, frame_bytes);
-        cp_async_commit();
-      }
-      const int s = q / it.nchunks, k = q - s * it.nchunks;
-      const Slab sl = slab_of<true>(it, s);
-      const int R0 = k * RB;
-      const int ncol = sl.ph + sl.sws;               // staged ring columns holding the slab
-      const int nwords = ((ncol + 7) >> 3) * 2;      // whole 8-column groups
-      // ---- uint8 rows of the chunk -> fp16 rows
-      {
-        const unsigned char* st = ring + (size_t)(q % kStages) * stage_bytes;
-        for (int idx = tid; idx < RB * nwords; idx += kThreads) {
-          const int row = idx / nwords, w = idx - row * nwords;
-          const unsigned int wd = *reinterpret_cast<const unsigned int*>(st + (size_t)row * kRowBytesU8 + 4 * w);
-          *reinterpret_cast<uint2*>(Th + (size_t)row * kThPitch + 4 * w) = u8x4_to_h4(wd);
-        }
-      }
-      __syncthreads();
-      const bool wact = 32 * warp < ncol;  // this warp's four 8-column tiles hold slab data
-      if (k == 0) {
-        #pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-          #pragma unroll
-          for (int nt = 0; nt < 4; ++nt)
-            #pragma unroll
-            for (int i = 0; i < 4; ++i) acc1[mt][nt][i] = 0.f;
-        if (wact && it.foldT) {  // folded top row first: fixed summation order
-          const __half* row = Th + (size_t)it.ph * kThPitch;
-          #pragma unroll
-          for (int nt = 0; nt < 4; ++nt) {
-            const __half2 d = *reinterpret_cast<const __half2*>(row + 32 * warp + 8 * nt + 2 * t);
-            const float2 df = __half22float2(d);
-            #pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-              const float c0 = cum_at(CU, it.offy - (16 * mt + g), r) * kWScale;
-              const float c1 = cum_at(CU, it.offy - (16 * mt + g + 8), r) * kWScale;
-              acc1[mt][nt][0] = fmaf(c0, df.x, acc1[mt][nt][0]);
-              acc1[mt][nt][1] = fmaf(c0, df.y, acc1[mt][nt][1]);
-              acc1[mt][nt][2] = fmaf(c1, df.x, acc1[mt][nt][2]);
-              acc1[mt][nt][3] = fmaf(c1, df.y, acc1[mt][nt][3]);
-            }
-          }
-        }
-      }
-      // ---- pass 1 on the chunk: 16 virtual rows per k-step
-      if (wact) {
-        for (int ks = 0; ks < RB / 16; ++ks) {
-          const int k0 = R0 + 16 * ks;
-          if (k0 >= it.vrows) break;
-          // m-tile mt sees nonzero taps only for v in [16mt - D0, 16mt + 15 - D0 + 2r]
-          const bool on0 = k0 + 15 >= -D0 && k0 <= 15 - D0 + 2 * r;
-          const bool on1 = k0 + 15 >= 16 - D0 && k0 <= 31 - D0 + 2 * r;
-          if (!on0 && !on1) continue;
-          const int j0 = (k0 + D0 + 2 * t - g + kPairPad) >> 1;
-          unsigned int ah[2][4], al[2][4];
-          {
-            const unsigned int h_m12 = Ph[j0 - 12], h_m8 = Ph[j0 - 8], h_m4 = Ph[j0 - 4], h_0 = Ph[j0], h_p4 = Ph[j0 + 4];
-            const unsigned int l_m12 = Pl[j0 - 12], l_m8 = Pl[j0 - 8], l_m4 = Pl[j0 - 4], l_0 = Pl[j0], l_p4 = Pl[j0 + 4];
-            ah[0][0] = h_0; ah[0][1] = h_m4; ah[0][2] = h_p4; ah[0][3] = h_0;
-            ah[1][0] = h_m8; ah[1][1] = h_m12; ah[1][2] = h_m4; ah[1][3] = h_m8;
-            al[0][0] = l_0; al[0][1] = l_m4; al[0][2] = l_p4; al[0][3] = l_0;
-            al[1][0] = l_m8; al[1][1] = l_m12; al[1][2] = l_m4; al[1][3] = l_m8;
-          }
-          const __half* tb = Th + (size_t)(k0 - R0) * kThPitch + 32 * warp;
-          #pragma unroll
-          for (int np2 = 0; np2 < 2; ++np2) {
-            if (32 * warp + 16 * np2 >= ncol) break;
-            unsigned int b[4];
-            // rows k0..k0+15, columns 16*np2 .. +15 of this warp's 32
-            const int rrow = (lane & 7) + ((lane >> 3) & 1) * 8;
-            const int rcol = 16 * np2 + ((lane >> 4) & 1) * 8;
-            ldsm_x4_t(b, tb + (size_t)rrow * kThPitch + rcol);
-            #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int nt = 2 * np2 + h;
-              const unsigned int b0 = b[2 * h], b1 = b[2 * h + 1];
-              if (on0) {
-                mma16816(acc1[0][nt], ah[0], b0, b1);
-                mma16816(acc1[0][nt], al[0], b0, b1);
-              }
-              if (on1) {
-                mma16816(acc1[1][nt], ah[1], b0, b1);
-                mma16816(acc1[1][nt], al[1], b0, b1);
-              }
-            }
-          }
-        }
-      }
-      if (k != it.nchunks - 1) continue;
-
-      // ---- slab complete: folded bottom row, then V -> hi/lo fp16 for pass 2
-      if (wact) {
-        const int vb = it.ph + it.EH - 1;
-        if (it.foldB && vb >= R0 && vb < R0 + RB) {
-          const __half* row = Th + (size_t)(vb - R0) * kThPitch;
-          #pragma unroll
-          for (int nt = 0; nt < 4; ++nt) {
-            const float2 df = __half22float2(*reinterpret_cast<const __half2*>(row + 32 * warp + 8 * nt + 2 * t));
-            #pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-              const float c0 = cum_at(CU, 2 * r + 1 - (it.offy + it.EH - (16 * mt + g)), r) * kWScale;
-              const float c1 = cum_at(CU, 2 * r + 1 - (it.offy + it.EH - (16 * mt + g + 8)), r) * kWScale;
-              acc1[mt][nt][0] = fmaf(c0, df.x, acc1[mt][nt][0]);
-              acc1[mt][nt][1] = fmaf(c0, df.y, acc1[mt][nt][1]);
-              acc1[mt][nt][2] = fmaf(c1, df.x, acc1[mt][nt][2]);
-              acc1[mt][nt][3] = fmaf(c1, df.y, acc1[mt][nt][3]);
-            }
-          }
-        }
-        #pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-          #pragma unroll
-          for (int nt = 0; nt < 4; ++nt)
-            #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const int yo = 16 * mt + g + ((i >> 1) << 3);
-              const int e = 32 * warp + 8 * nt + 2 * t + (i & 1) - sl.ph;
-              if (e >= 0 && e < sl.sws) {
-                const int px = e / C, c = e - px * C;
-                const float v = acc1[mt][nt][i] * kWInv;
-                const __half vh = __float2half_rn(v);
-                const __half vl = __float2half_rn(v - __half2float(vh));
-                const size_t o = (size_t)(c * 32 + yo) * vpitch + px;
-                Vh[o] = vh;
-                Vl[o] = vl;
-              }
-            }
-      }
-      const int npx = sl.sws / C;
-      const int npx16 = (npx + 15) & ~15;
-      for (int idx = tid; idx < 32 * C * (npx16 - npx); idx += kThreads) {  // K padding of pass 2
-        const int row = idx / (npx16 - npx), col = npx + idx % (npx16 - npx);
-        Vh[(size_t)row * vpitch + col] = __float2half_rn(0.f);
-        Vl[(size_t)row * vpitch + col] = __float2half_rn(0.f);
-      }
-      __syncthreads();
-
-      // ---- pass 2 over the slab's pixels: units (row tile, column tile)
-      const int P0 = sl.e0 / C;  // first folded pixel of the slab
-      // tap index of this lane's B registers has the parity of offx + P0 - g
-      const int par2 = (it.offx + P0 + g) & 1;
-      const unsigned int* Qh = P + (par2 ? np : 0);
-      const unsigned int* Ql = P + 2 * np + (par2 ? np : 0);
-      #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (i >= C) break;
-        const int u = warp + 8 * i;
-        const int mt2 = u >> 2, nt2 = u & 3;
-        // folded left column (pixel 0) first: fixed summation order
-        if (it.foldL && P0 == 0) {
-          #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int row = 16 * mt2 + g + 8 * h;
-            const float v = __half2float(Vh[(size_t)row * vpitch]) + __half2float(Vl[(size_t)row * vpitch]);
-            #pragma unroll
-            for (int cc = 0; cc < 2; ++cc) {
-              const int x = 8 * nt2 + 2 * t + cc;
-              acc2[i][2 * h + cc] = fmaf(cum_at(CU, it.offx - x, r) * kWScale, v, acc2[i][2 * h + cc]);
-            }
-          }
-        }
-        for (int kk = 0; kk < npx16; kk += 16) {
-          unsigned int a_h[4], a_l[4];
-          const int arow = 16 * mt2 + (lane & 7) + ((lane >> 3) & 1) * 8;
-          const int acol = kk + ((lane >> 4) & 1) * 8;
-          ldsm_x4(a_h, Vh + (size_t)arow * vpitch + acol);
-          ldsm_x4(a_l, Vl + (size_t)arow * vpitch + acol);
-          const int jb = (it.offx + P0 + kk + 2 * t - 8 * nt2 - g + kPairPad) >> 1;
-          const unsigned int bh0 = Qh[jb], bh1 = Qh[jb + 4], bl0 = Ql[jb], bl1 = Ql[jb + 4];
-          mma16816(acc2[i], a_h, bh0, bh1);
-          mma16816(acc2[i], a_h, bl0, bl1);
-          mma16816(acc2[i], a_l, bh0, bh1);
-        }
-        // folded right column (last pixel) after the last slab's products
-        const int pr = it.EW - 1 - P0;
-        if (it.foldR && pr >= 0 && pr < npx) {
-          #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int row = 16 * mt2 + g + 8 * h;
-            const float v = __half2float(Vh[(size_t)row * vpitch + pr]) + __half2float(Vl[(size_t)row * vpitch + pr]);
-            #pragma unroll
-            for (int cc = 0; cc < 2; ++cc) {
-              const int x = 8 * nt2 + 2 * t + cc;
-              acc2[i][2 * h + cc] = fmaf(cum_at(CU, 2 * r + 1 - (it.offx + it.EW - x), r) * kWScale, v, acc2[i][2 * h + cc]);
-            }
-          }
-        }
-      }
-    }
-    cp_async_wait<0>();
-    __syncthreads();  // ring and Th no longer read; Th becomes the output stage
-
-    unsigned char* ost = reinterpret_cast<unsigned char*>(Th);
-    const int opitch = 32 * C;
-    #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      if (i >= C) break;
-      const int u = warp + 8 * i;
-      const int mt2 = u >> 2, nt2 = u & 3;
-      #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int row = 16 * mt2 + g + ((e >> 1) << 3);
-        const int c = row >> 5, yo = row & 31;
-        const int x = 8 * nt2 + 2 * t + (e & 1);
-        ost[yo * opitch + x * C + c] = quant_u8(acc2[i][e] * kWInv);
-      }
-    }
-    __syncthreads();
-    const int rowBytes = it.bw * C;
-    unsigned char* out = it.out + (size_t)it.y0 * it.pitch + (size_t)it.x0 * C;
-    for (int idx = tid; idx < it.bh * rowBytes; idx += kThreads) {
-      const int yo = idx / rowBytes, rem = idx - yo * rowBytes;
-      out[(size_t)yo * it.pitch + rem] = ost[yo * opitch + rem];
-    }
+    tc_item<RB, C>(s_it, s_c, ring, Th, Vh, Vl, U, CU, P, red, np);
   }
   cp_async_wait<0>();
   if (own_order) {
@@ -446,14 +509,24 @@ tc_forward_kernel(FrameSource src, Workspace ws, int rmax, BucketList bl) {
   }
 }
 
-template <int RB>
-void* tc_kernel_ptr() { return reinterpret_cast<void*>(&tc_forward_kernel<RB>); }
+template <int RB, int C>
+void* tc_kernel_ptr() { return reinterpret_cast<void*>(&tc_forward_kernel<RB, C>); }
 
-void* pick_tc(int rb) {
+template <int C>
+void* pick_tc_rb(int rb) {
   switch (rb) {
-    case 16: return tc_kernel_ptr<16>();
-    case 64: return tc_kernel_ptr<64>();
-    default: return tc_kernel_ptr<32>();
+    case 16: return tc_kernel_ptr<16, C>();
+    case 64: return tc_kernel_ptr<64, C>();
+    default: return tc_kernel_ptr<32, C>();
+  }
+}
+
+void* pick_tc(int rb, int C) {
+  switch (C) {
+    case 1: return pick_tc_rb<1>(rb);
+    case 2: return pick_tc_rb<2>(rb);
+    case 3: return pick_tc_rb<3>(rb);
+    default: return pick_tc_rb<4>(rb);
   }
 }
 
@@ -461,9 +534,9 @@ void* pick_tc(int rb) {
 
 size_t tc_forward_smem_bytes(const FwdConfig& cfg, int rmax) { return tc_layout(cfg.rows_per_chunk, rmax).total; }
 
-int tc_forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax) {
+int tc_forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int C) {
   const size_t smem = tc_forward_smem_bytes(cfg, rmax);
-  void* k = pick_tc(cfg.rows_per_chunk);
+  void* k = pick_tc(cfg.rows_per_chunk, C);
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -476,10 +549,10 @@ int tc_forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax) {
   return n;
 }
 
-cudaError_t launch_tc_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg, int rmax,
+cudaError_t launch_tc_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg, int rmax, int C,
                               int grid, cudaStream_t s, const BucketList& bl, bool pdl) {
   const size_t smem = tc_forward_smem_bytes(cfg, rmax);
-  void* k = pick_tc(cfg.rows_per_chunk);
+  void* k = pick_tc(cfg.rows_per_chunk, C);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   BucketList b = bl;
