@@ -46,9 +46,14 @@ SIGMA0, K_SLOPE = 0.5, 0.02
 FIX = (960.0, 540.0)
 WORKLOAD = "1920x1080 RGB uint8 frame, 32x32 blocks, sigma = 0.5 + 0.02 e px, fixation at the centre"
 L2_BYTES = 129 * 1024 * 1024
-PROFILE = os.path.join(ROOT, "profiles", "forward_1080p_u8.txt")
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_2012_08655_gb300", "csrc", f)
-                  for f in ("forward.cu", "fovea_internal.cuh")]
+CSRC = os.path.join(ROOT, "paper_2012_08655_gb300", "csrc")
+# Per forward kernel: committed ncu summary and the sources it was taken from.
+KERNELS = {
+    0: ("forward_kernel (fp32 FMA)", os.path.join(ROOT, "profiles", "forward_kernel_1080p_u8.txt"),
+        ("forward.cu", "fwd_common.cuh", "fovea_internal.cuh")),
+    1: ("tc_forward_kernel (tensor cores, mma.sync)", os.path.join(ROOT, "profiles", "tc_forward_kernel_1080p_u8.txt"),
+        ("tc_forward.cu", "fwd_common.cuh", "fovea_internal.cuh")),
+}
 
 
 def parse_args():
@@ -61,34 +66,36 @@ def parse_args():
     p.add_argument("--served-seconds", type=float, default=10.0)
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiling runs)")
+    p.add_argument("--tensor-cores", type=int, choices=[0, 1], default=None,
+                   help="force the forward kernel (0: fp32 FMA, 1: tensor cores) instead of autotuning")
     return p.parse_args()
 
 
 # ------------------------------------------------------------------ helpers
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(tc: int) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        with open(f, "rb") as fh:
+    for f in KERNELS[tc][2]:
+        with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the blur kernel from the committed ncu summary,
-    or None when the summary is missing or the kernel changed since."""
+def profiled(tc: int):
+    """Fields of the committed ncu summary of the timed kernel, or {} when it
+    is missing or the kernel's sources changed since it was taken."""
     try:
         vals = {}
-        with open(PROFILE) as f:
+        with open(KERNELS[tc][1]) as f:
             for line in f:
                 if ":" in line:
                     k, v = line.split(":", 1)
                     vals[k.strip()] = v.strip()
-        if vals.get("kernel_source_sha256_16") != kernel_source_hash():
-            return None
-        return float(vals["dram_bytes_per_launch"])
-    except (OSError, KeyError, ValueError):
-        return None
+        if vals.get("kernel_source_sha256_16") != kernel_source_hash(tc):
+            return {}
+        return vals
+    except OSError:
+        return {}
 
 
 def algorithmic_fmas(radius, width, height, channels, block):
@@ -384,7 +391,11 @@ def run_ours(args):
     ins = [base.clone() for _ in range(pool_n)]
     outs = [torch.empty_like(base) for _ in range(pool_n)]
     ctx = fv.Context(W, H, C, B, SIGMA0, K_SLOPE, fv.U8_HWC)
-    cfg = ctx.get_config() if args.no_autotune else ctx.autotune(iters=20)
+    if args.tensor_cores is not None:
+        ctx.set_config(256, 0, 32, tensor_cores=args.tensor_cores)
+        cfg = ctx.get_config()
+    else:
+        cfg = ctx.get_config() if args.no_autotune else ctx.autotune(iters=20)
     stream = torch.cuda.current_stream()
 
     for i in range(args.warmup):
@@ -422,14 +433,26 @@ def run_ours(args):
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     peak_tflops = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
     achieved = 2 * fmas / (kernel_ms * 1e-3) / 1e12
-    traffic = profiled_traffic()
+    tc = int(cfg.get("tensor_cores", 0))
+    prof = profiled(tc)
+    try:
+        traffic = float(prof["dram_bytes_per_launch"]) if prof else None
+    except (KeyError, ValueError):
+        traffic = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
-                "kernel": "forward_kernel (persistent blur)", "kernel_ms": kernel_ms,
+                "kernel": KERNELS[tc][0], "kernel_ms": kernel_ms,
                 "algorithmic_fmas_per_launch": fmas,
                 "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz "
-                              "(derived, not measured)",
+                              "(derived from unit counts and the maximum SM clock, not measured)",
                 "hbm_bound_ms": 2 * fbytes / 6795.1e9 * 1e3}
+    if tc and prof.get("mma_flops_per_launch"):
+        # The same launch seen as a tensor-core contraction: fp16 MMA work per
+        # launch (from the committed summary) against the measured dense
+        # bf16 peak (fp16 has the same nominal rate).
+        mma_tflops = float(prof["mma_flops_per_launch"]) / (kernel_ms * 1e-3) / 1e12
+        roofline["tensor_view"] = {"achieved": mma_tflops, "peak": 1858.6, "unit": "TFLOP/s",
+                                   "frac": mma_tflops / 1858.6, "peak_basis": "MEASURED_PEAKS bf16 burst (fp16 same rate)"}
 
     # end to end: pinned host frames through fovea_render_host
     hin = [torch.from_numpy(frame.image).pin_memory() for _ in range(4)]
@@ -472,7 +495,7 @@ def run_ours(args):
                              f"({2 * pool_n * fbytes / 2**20:.0f} MiB in+out) > L2",
                        "kernel_config": cfg, "parallelism": f"replicas x{world}"},
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
-            "gpu_launches": 3 * args.steps, "clocks": clocks,
+            "gpu_launches": 2 * args.steps, "clocks": clocks,  # sigma + blur kernel per render
         }
         line.update(extras)
         print(json.dumps(line), flush=True)

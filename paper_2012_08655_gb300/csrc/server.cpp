@@ -5,10 +5,11 @@
 //      buffers fit in a fixed device arena (admission by device memory) and
 //      fewer than max_inflight requests are admitted;
 //   2. copies each admitted input to the device on a copy stream;
-//   3. every tick, renders all admitted requests whose input copy has
-//      finished as ONE batch (fovea_render_batch: sigma table, cost-ordered
-//      work list, persistent kernel) on a compute stream, with at most two
-//      batches queued so requests arriving meanwhile gather into the next one;
+//   3. every tick, renders the admitted requests whose input copy has
+//      finished, one batch per (format, channel count) (fovea_render_batch:
+//      sigma table, cost-ordered work list, persistent kernel) on a compute
+//      stream, with at most two ticks' batches queued so requests arriving
+//      meanwhile gather into the next tick;
 //   4. copies each result back to its caller's host buffer on a third stream
 //      and, once that copy is seen complete, frees the arena space.
 // The paper's per-frame loop (Algorithm 1: pinned host -> device, kernel,
@@ -48,6 +49,7 @@ struct Request {
   size_t off = 0;          // arena offset of [input | output]
   fovea_request_times t{};
   State state = PENDING;
+  int status = 0;          // render status of its batch
   cudaEvent_t ev_in = nullptr, ev_done = nullptr;
 };
 
@@ -185,15 +187,34 @@ void fovea_server::run() {
         }
       }
       if (!ready.empty()) {
-        frames.resize(ready.size());
-        for (size_t i = 0; i < ready.size(); ++i) {
-          fovea_frame f = ready[i]->f;
-          f.in = arena_base + ready[i]->off;
-          f.out = arena_base + ready[i]->off + align_up(ready[i]->bytes);
-          frames[i] = f;
-        }
+        // One batch per (format, channel count): a request is rendered by the
+        // same kernel whatever else arrived with it, so its result does not
+        // depend on the mix.
+        std::stable_sort(ready.begin(), ready.end(), [](const Request* a, const Request* b) {
+          return a->f.format != b->f.format ? a->f.format < b->f.format : a->f.channels < b->f.channels;
+        });
         const double t0 = now_us();
-        const int st = fovea_render_batch(ctx, frames.data(), (int)frames.size(), s_comp);
+        bool failed = false;
+        for (size_t g0 = 0; g0 < ready.size();) {
+          size_t g1 = g0 + 1;
+          while (g1 < ready.size() && ready[g1]->f.format == ready[g0]->f.format &&
+                 ready[g1]->f.channels == ready[g0]->f.channels)
+            ++g1;
+          frames.resize(g1 - g0);
+          for (size_t i = g0; i < g1; ++i) {
+            fovea_frame f = ready[i]->f;
+            f.in = arena_base + ready[i]->off;
+            f.out = arena_base + ready[i]->off + align_up(ready[i]->bytes);
+            frames[i - g0] = f;
+          }
+          const int st = fovea_render_batch(ctx, frames.data(), (int)frames.size(), s_comp);
+          for (size_t i = g0; i < g1; ++i) {
+            ready[i]->status = st;
+            ready[i]->t.batch_size = (int)(g1 - g0);
+          }
+          failed |= st != FOVEA_OK;
+          g0 = g1;
+        }
         cudaEvent_t eb = nullptr;
         {
           std::lock_guard<std::mutex> lk(mu);
@@ -205,9 +226,8 @@ void fovea_server::run() {
         std::lock_guard<std::mutex> lk(mu);
         for (Request* r : ready) {
           r->t.start_us = t0;
-          r->t.batch_size = (int)ready.size();
-          if (st != FOVEA_OK) {
-            finish(r, st);
+          if (r->status != FOVEA_OK) {
+            finish(r, r->status);
             continue;
           }
           cudaMemcpyAsync(r->f.out, arena_base + r->off + align_up(r->bytes), r->bytes, cudaMemcpyDeviceToHost, s_out);
@@ -215,7 +235,7 @@ void fovea_server::run() {
           r->state = LAUNCHED;
           launched.push_back(r);
         }
-        if (st != FOVEA_OK) cv_done.notify_all();
+        if (failed) cv_done.notify_all();
         progressed = true;
       }
     }

@@ -34,15 +34,17 @@ constexpr int kVHalves = 128 * 72;     // halves of one V array (max over C of 3
 
 __host__ __device__ inline int npair(int rmax) { return rmax + 56; }
 
+constexpr int kTcStages = 4;          // raw uint8 chunks in flight or staged
+
 struct TcLayout {
   size_t ring, th, vh, vl, taps, cum, pairs, red, total;
 };
 
 __host__ __device__ inline TcLayout tc_layout(int rb, int rmax) {
   TcLayout L;
-  L.ring = 0;                                                  // u8 [kStages][rb][256]
-  L.th = L.ring + (size_t)kStages * rb * kRowBytesU8;          // half [rb][kThPitch]
-  L.vh = L.th + (size_t)rb * kThPitch * 2;                     // half [kVHalves]
+  L.ring = 0;                                                  // u8 [kTcStages][rb][256]
+  L.th = L.ring + (size_t)kTcStages * rb * kRowBytesU8;        // half [2][rb][kThPitch]
+  L.vh = L.th + (size_t)2 * rb * kThPitch * 2;                 // half [kVHalves]
   L.vl = L.vh + (size_t)kVHalves * 2;                          // half [kVHalves]
   L.taps = L.vl + (size_t)kVHalves * 2;                        // float2 [tap_len]
   L.cum = L.taps + (size_t)tap_len(rmax) * sizeof(float2);     // float [cum_len]
@@ -115,8 +117,9 @@ __device__ __forceinline__ void convert_group(const unsigned char* rowp, int ph,
   }
 }
 
+// No side effects: left to the compiler to schedule (independent chains interleave).
 __device__ __forceinline__ void mma16816(float (&d)[4], const unsigned int (&a)[4], unsigned int b0, unsigned int b1) {
-  asm volatile(
+  asm(
       "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
@@ -171,8 +174,11 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
   const int Q = it.nsl * it.nchunks;
   const size_t frame_bytes = (size_t)it.H * it.pitch;
 
+  // Raw uint8 chunks stream through kTcStages ring stages (cp.async); chunk
+  // q+1 is converted to fp16 while chunk q feeds the tensor cores, so the two
+  // fp16 buffers alternate and one barrier per chunk suffices.
   #pragma unroll
-  for (int q = 0; q < kStages - 1; ++q) {
+  for (int q = 0; q < kTcStages - 1; ++q) {
     if (q < Q) stage_rows<true, RB>(it, slab_of<true>(it, q / it.nchunks), q % it.nchunks,
                                     ring + (size_t)q * stage_bytes, frame_bytes);
     cp_async_commit();
@@ -180,7 +186,30 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
   make_taps(U, tap_len(r), r, c_tap, red);
   make_cumulative(U, CU, r);
   make_pairs(U, P, r, np);
-  __syncthreads();
+
+  // uint8 chunk qc -> channel-planar fp16 rows in Th buffer qc % 2
+  auto convert_chunk = [&](int qc) {
+    const Slab cs = slab_of<true>(it, qc / it.nchunks);
+    const int cnpx = cs.sws / C;
+    const int cngrp = ((cnpx + 15) & ~15) >> 3;  // 8-pixel groups per channel
+    const unsigned char* st = ring + (size_t)(qc % kTcStages) * stage_bytes;
+    __half* dst = Th + (size_t)(qc & 1) * RB * kThPitch;
+    const int ph3 = cs.ph & 3;
+    for (int idx = threadIdx.x; idx < RB * cngrp; idx += kThreads) {
+      const int row = idx / cngrp, gq = idx - row * cngrp;
+      const unsigned char* rowp = st + (size_t)row * kRowBytesU8;
+      __half* throw_ = dst + (size_t)row * kThPitch;
+      switch (ph3) {
+        case 0: convert_group<C, 0>(rowp, cs.ph, gq, cnpx, throw_); break;
+        case 1: convert_group<C, 1>(rowp, cs.ph, gq, cnpx, throw_); break;
+        case 2: convert_group<C, 2>(rowp, cs.ph, gq, cnpx, throw_); break;
+        default: convert_group<C, 3>(rowp, cs.ph, gq, cnpx, throw_); break;
+      }
+    }
+  };
+  cp_async_wait<kTcStages - 2>();
+  __syncthreads();  // chunk 0 landed for every thread; taps ready
+  convert_chunk(0);
 
   // Pass 1: each lane reads the tap-pair table of its parity (the tap index
   // of every A register of this lane has the parity of g, D0 being even).
@@ -196,37 +225,21 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
     for (int k = 0; k < 4; ++k) acc2[i][k] = 0.f;
 
   for (int q = 0; q < Q; ++q) {
-    cp_async_wait<kStages - 2>();
-    __syncthreads();  // chunk q landed; the previous chunk's fragments are consumed
+    cp_async_wait<kTcStages - 3>();
+    __syncthreads();  // chunk q converted and q+1 landed; iteration q-1 finished everywhere
     {
-      const int qn = q + kStages - 1;
+      const int qn = q + kTcStages - 1;
       if (qn < Q) stage_rows<true, RB>(it, slab_of<true>(it, qn / it.nchunks), qn % it.nchunks,
-                                       ring + (size_t)(qn % kStages) * stage_bytes, frame_bytes);
+                                       ring + (size_t)(qn % kTcStages) * stage_bytes, frame_bytes);
       cp_async_commit();
     }
+    if (q + 1 < Q) convert_chunk(q + 1);
     const int s = q / it.nchunks, k = q - s * it.nchunks;
     const Slab sl = slab_of<true>(it, s);
     const int R0 = k * RB;
     const int npx = sl.sws / C;                 // pixels of the slab
     const int npx16 = (npx + 15) & ~15;
-    const int ngrp = npx16 >> 3;                // 8-pixel groups per channel
-    // ---- uint8 rows of the chunk -> channel-planar fp16 rows
-    {
-      const unsigned char* st = ring + (size_t)(q % kStages) * stage_bytes;
-      const int ph3 = sl.ph & 3;
-      for (int idx = tid; idx < RB * ngrp; idx += kThreads) {
-        const int row = idx / ngrp, gq = idx - row * ngrp;
-        const unsigned char* rowp = st + (size_t)row * kRowBytesU8;
-        __half* throw_ = Th + (size_t)row * kThPitch;
-        switch (ph3) {
-          case 0: convert_group<C, 0>(rowp, sl.ph, gq, npx, throw_); break;
-          case 1: convert_group<C, 1>(rowp, sl.ph, gq, npx, throw_); break;
-          case 2: convert_group<C, 2>(rowp, sl.ph, gq, npx, throw_); break;
-          default: convert_group<C, 3>(rowp, sl.ph, gq, npx, throw_); break;
-        }
-      }
-    }
-    __syncthreads();
+    const __half* thc = Th + (size_t)(q & 1) * RB * kThPitch;
     // This warp's 32 columns: channel c0 = 32w / PXP, pixel offset inside it.
     const int colw = 32 * warp;
     if (k == 0) {
@@ -237,7 +250,7 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
           #pragma unroll
           for (int i = 0; i < 4; ++i) acc1[mt][nt][i] = 0.f;
       if (it.foldT && colw < C * PXP) {  // folded top row first: fixed summation order
-        const __half* row = Th + (size_t)it.ph * kThPitch;
+        const __half* row = thc + (size_t)it.ph * kThPitch;
         #pragma unroll
         for (int nt = 0; nt < 4; ++nt) {
           const float2 df = __half22float2(*reinterpret_cast<const __half2*>(row + colw + 8 * nt + 2 * t));
@@ -278,25 +291,28 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
           al[0][0] = l_0; al[0][1] = l_m4; al[0][2] = l_p4; al[0][3] = l_0;
           al[1][0] = l_m8; al[1][1] = l_m12; al[1][2] = l_m4; al[1][3] = l_m8;
         }
-        const __half* tb = Th + (size_t)(k0 - R0) * kThPitch + colw;
+        const __half* tb = thc + (size_t)(k0 - R0) * kThPitch + colw;
+        unsigned int b[2][4];
         #pragma unroll
         for (int np2 = 0; np2 < 2; ++np2) {
           if (!pon[np2]) continue;
-          unsigned int b[4];
           const int rrow = (lane & 7) + ((lane >> 3) & 1) * 8;
           const int rcol = 16 * np2 + ((lane >> 4) & 1) * 8;
-          ldsm_x4_t(b, tb + (size_t)rrow * kThPitch + rcol);
+          ldsm_x4_t(b[np2], tb + (size_t)rrow * kThPitch + rcol);
+        }
+        // all hi products, then all lo products: the two products into one
+        // accumulator are 8 independent MMAs apart
+        #pragma unroll
+        for (int part = 0; part < 2; ++part) {
           #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int nt = 2 * np2 + h;
-            const unsigned int b0 = b[2 * h], b1 = b[2 * h + 1];
-            if (on0) {
-              mma16816(acc1[0][nt], ah[0], b0, b1);
-              mma16816(acc1[0][nt], al[0], b0, b1);
-            }
-            if (on1) {
-              mma16816(acc1[1][nt], ah[1], b0, b1);
-              mma16816(acc1[1][nt], al[1], b0, b1);
+          for (int np2 = 0; np2 < 2; ++np2) {
+            if (!pon[np2]) continue;
+            #pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int nt = 2 * np2 + h;
+              const unsigned int b0 = b[np2][2 * h], b1 = b[np2][2 * h + 1];
+              if (on0) mma16816(acc1[0][nt], part ? al[0] : ah[0], b0, b1);
+              if (on1) mma16816(acc1[1][nt], part ? al[1] : ah[1], b0, b1);
             }
           }
         }
@@ -308,7 +324,7 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
     {
       const int vb = it.ph + it.EH - 1;
       if (it.foldB && vb >= R0 && vb < R0 + RB && colw < C * PXP) {
-        const __half* row = Th + (size_t)(vb - R0) * kThPitch;
+        const __half* row = thc + (size_t)(vb - R0) * kThPitch;
         #pragma unroll
         for (int nt = 0; nt < 4; ++nt) {
           const float2 df = __half22float2(*reinterpret_cast<const __half2*>(row + colw + 8 * nt + 2 * t));
@@ -356,11 +372,11 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
     const int par2 = (it.offx + P0 + g) & 1;
     const unsigned int* Qh = P + (par2 ? np : 0);
     const unsigned int* Ql = P + 2 * np + (par2 ? np : 0);
-    #pragma unroll
-    for (int i = 0; i < C; ++i) {
-      const int u = warp + 8 * i;
-      const int mt2 = u >> 2, nt2 = u & 3;
-      if (it.foldL && P0 == 0) {  // folded left column first: fixed summation order
+    if (it.foldL && P0 == 0) {  // folded left column first: fixed summation order
+      #pragma unroll
+      for (int i = 0; i < C; ++i) {
+        const int u = warp + 8 * i;
+        const int mt2 = u >> 2, nt2 = u & 3;
         #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int row = 16 * mt2 + g + 8 * h;
@@ -372,28 +388,44 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
           }
         }
       }
-      for (int kk = 0; kk < npx16; kk += 16) {
-        unsigned int a_h[4], a_l[4];
+    }
+    for (int kk = 0; kk < npx16; kk += 16) {
+      unsigned int a_h[C][4], a_l[C][4], bh[C][2], bl[C][2];
+      #pragma unroll
+      for (int i = 0; i < C; ++i) {
+        const int u = warp + 8 * i;
+        const int mt2 = u >> 2, nt2 = u & 3;
         const int arow = 16 * mt2 + (lane & 7) + ((lane >> 3) & 1) * 8;
         const int acol = kk + ((lane >> 4) & 1) * 8;
-        ldsm_x4(a_h, Vh + (size_t)arow * VP + acol);
-        ldsm_x4(a_l, Vl + (size_t)arow * VP + acol);
+        ldsm_x4(a_h[i], Vh + (size_t)arow * VP + acol);
+        ldsm_x4(a_l[i], Vl + (size_t)arow * VP + acol);
         const int jb = (it.offx + P0 + kk + 2 * t - 8 * nt2 - g + kPairPad) >> 1;
-        const unsigned int bh0 = Qh[jb], bh1 = Qh[jb + 4], bl0 = Ql[jb], bl1 = Ql[jb + 4];
-        mma16816(acc2[i], a_h, bh0, bh1);
-        mma16816(acc2[i], a_h, bl0, bl1);
-        mma16816(acc2[i], a_l, bh0, bh1);
+        bh[i][0] = Qh[jb]; bh[i][1] = Qh[jb + 4];
+        bl[i][0] = Ql[jb]; bl[i][1] = Ql[jb + 4];
       }
+      #pragma unroll
+      for (int i = 0; i < C; ++i) mma16816(acc2[i], a_h[i], bh[i][0], bh[i][1]);
+      #pragma unroll
+      for (int i = 0; i < C; ++i) mma16816(acc2[i], a_h[i], bl[i][0], bl[i][1]);
+      #pragma unroll
+      for (int i = 0; i < C; ++i) mma16816(acc2[i], a_l[i], bh[i][0], bh[i][1]);
+    }
+    {
       const int pr = it.EW - 1 - P0;  // folded right column after the last slab's products
       if (it.foldR && pr >= 0 && pr < npx) {
         #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int row = 16 * mt2 + g + 8 * h;
-          const float v = __half2float(Vh[(size_t)row * VP + pr]) + __half2float(Vl[(size_t)row * VP + pr]);
+        for (int i = 0; i < C; ++i) {
+          const int u = warp + 8 * i;
+          const int mt2 = u >> 2, nt2 = u & 3;
           #pragma unroll
-          for (int cc = 0; cc < 2; ++cc) {
-            const int x = 8 * nt2 + 2 * t + cc;
-            acc2[i][2 * h + cc] = fmaf(cum_at(CU, 2 * r + 1 - (it.offx + it.EW - x), r) * kWScale, v, acc2[i][2 * h + cc]);
+          for (int h = 0; h < 2; ++h) {
+            const int row = 16 * mt2 + g + 8 * h;
+            const float v = __half2float(Vh[(size_t)row * VP + pr]) + __half2float(Vl[(size_t)row * VP + pr]);
+            #pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+              const int x = 8 * nt2 + 2 * t + cc;
+              acc2[i][2 * h + cc] = fmaf(cum_at(CU, 2 * r + 1 - (it.offx + it.EW - x), r) * kWScale, v, acc2[i][2 * h + cc]);
+            }
           }
         }
       }

@@ -150,7 +150,9 @@ def test_single_frame_backward_matches_batch(fv):
 
 def test_server_result_alone_equals_result_in_the_mix(fv):
     """Frames served one at a time and the same frames served among a burst of
-    other requests give identical outputs, equal to the single-frame path."""
+    other requests give identical outputs (each (format, channels) group is
+    its own batch, so a frame always meets the same kernel), within 1 LSB of
+    the single-frame path (which may run another kernel configuration)."""
     specs = [(84, 84, 1), (224, 224, 3), (1280, 720, 3), (1920, 1080, 3), (224, 224, 3), (84, 84, 1)]
     frames = []
     for i, (W, H, C) in enumerate(specs):
@@ -176,7 +178,7 @@ def test_server_result_alone_equals_result_in_the_mix(fv):
         assert torch.equal(out, alone[j % len(frames)])
     for (inp, fx, fy), out in zip(frames, alone):
         ref = fv.foveate(inp.cuda(), fx, fy, 0.5, 0.02)
-        assert torch.equal(ref.cpu(), out)
+        assert_u8_close(out.numpy(), ref.cpu().numpy(), min_equal=0.995)
     inp, fx, fy = frames[1]
     assert_u8_close(alone[1].numpy(), oracle.forward_u8(inp.numpy(), 32, fx, fy, 0.5, 0.02, "hwc"))
 
