@@ -15,6 +15,7 @@ Also reported on the same JSON line:
   cpu_baseline  the FP64 oracle on a bounded sample of the frame's blocks;
   clocks        nvidia-smi samples taken during the timed region;
   batched       the 64-frame mixed batch in one launch vs one launch per frame;
+  train         the 32x3x224x224 float32 batch, forward and forward+backward;
   served        p50/p99 latency of the served request stream (continuous
                 batching) vs the plain one-request-per-launch loop.
 
@@ -107,6 +108,17 @@ def algorithmic_fmas(radius, width, height, channels, block):
     bw = np.minimum(block, width - block * np.arange(nbx))[None, :].astype(np.float64)
     bh = np.minimum(block, height - block * np.arange(nby))[:, None].astype(np.float64)
     return float(np.sum(channels * (2 * r + 1) * bw * (2 * bh + 2 * r)))
+
+
+def lower_bound_fmas(radius, width, height, channels, block):
+    """Separable FMAs without halo overhead: 2 (2 r_b + 1) per output
+    pixel-channel."""
+    import numpy as np
+    r = radius.astype(np.float64)
+    nby, nbx = radius.shape
+    bw = np.minimum(block, width - block * np.arange(nbx))[None, :].astype(np.float64)
+    bh = np.minimum(block, height - block * np.arange(nby))[:, None].astype(np.float64)
+    return float(np.sum(channels * 2 * (2 * r + 1) * bw * bh))
 
 
 class ClockSampler:
@@ -320,6 +332,39 @@ def batched_leg(fv, torch):
             "speedup": res["per_frame"]["ms"] / res["batched"]["ms"]}
 
 
+def train_leg(fv, torch):
+    """32x3x224x224 float32 batch (sigma = 0.5 + 0.08 e, random fixations):
+    forward and backward through the autograd function (batched render and
+    batched adjoint launches)."""
+    from paper_2012_08655_gb300 import workloads as wl
+    x_np, fix_np, s0, k = wl.train_batch(seed=0)
+    x = torch.from_numpy(x_np).cuda().requires_grad_(True)
+    fix = torch.from_numpy(fix_np)
+    g = torch.rand_like(x)
+    res = {}
+    for name in ("forward", "forward_backward"):
+        def step():
+            y = fv.foveate_train(x, fix, s0, k)
+            if name == "forward_backward":
+                y.backward(g)
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        e0.record()
+        for _ in range(reps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = e0.elapsed_time(e1) / reps
+    px = x_np.shape[0] * x_np.shape[2] * x_np.shape[3]
+    return {"workload": "32x3x224x224 float32 U[0,1), fixations uniform, sigma = 0.5 + 0.08 e",
+            "forward_ms": res["forward"], "forward_backward_ms": res["forward_backward"],
+            "forward_mpix_s": px / res["forward"] / 1e3,
+            "forward_backward_mpix_s": px / res["forward_backward"] / 1e3}
+
+
 def served_leg(fv, torch, seconds: float, max_batch: int):
     """Replay the Poisson request stream through the serving loop."""
     import numpy as np
@@ -429,6 +474,7 @@ def run_ours(args):
     # roofline of the blur kernel: algorithmic FP32 FMAs against the FP32 FMA peak
     sig, rad = ctx.sigma_table(*FIX)
     fmas = algorithmic_fmas(rad.cpu().numpy(), W, H, C, B)
+    lower_fmas = lower_bound_fmas(rad.cpu().numpy(), W, H, C, B)
     props = torch.cuda.get_device_properties(dev)
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     peak_tflops = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
@@ -439,8 +485,12 @@ def run_ours(args):
         traffic = float(prof["dram_bytes_per_launch"]) if prof else None
     except (KeyError, ValueError):
         traffic = None
+    measured_tflops = 2 * fv.measure_fma_rate() / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
+                "peak_measured": measured_tflops, "frac_of_measured": achieved / measured_tflops,
+                "lower_bound_fmas_per_launch": lower_fmas,
+                "frac_lower_bound": 2 * lower_fmas / (kernel_ms * 1e-3) / 1e12 / peak_tflops,
                 "kernel": KERNELS[tc][0], "kernel_ms": kernel_ms,
                 "algorithmic_fmas_per_launch": fmas,
                 "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz "
@@ -479,6 +529,7 @@ def run_ours(args):
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
         extras["batched"] = batched_leg(fv, torch)
+        extras["train"] = train_leg(fv, torch)
         served = served_leg(fv, torch, args.served_seconds, max_batch=64)
         plain = served_leg(fv, torch, args.served_seconds, max_batch=1)
         served["plain_per_frame"] = {k: plain[k] for k in ("p50_ms", "p99_ms", "mpix_s", "mean_batch")}

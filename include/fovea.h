@@ -207,14 +207,26 @@ const char* fovea_strerror(int status);
 /* The cudaError_t of the last failed CUDA call in this thread (0 if none). */
 int fovea_last_cuda_error(void);
 
+/* Diagnostic (no counterpart in the paper): measures the current GPU's FP32
+ * FMA throughput, the roof of the blur kernels' arithmetic. Runs a kernel of
+ * independent packed two-lane FMA chains (fma.rn.f32x2) on every SM of the
+ * current device, on the given stream, for a fraction of a second, timed with
+ * CUDA events, and synchronises that stream. On success stores the measured
+ * rate in FMA lane-operations per second (one f32x2 FMA counts 2) in
+ * *fma_per_s. The kernel writes one float per thread into a device buffer it
+ * allocates and frees itself. FOVEA_EINVAL for a null pointer, FOVEA_ECUDA /
+ * FOVEA_ENOMEM on failure. */
+int fovea_measure_fma_rate(double* fma_per_s, void* stream);
+
 /* ------------------------------------------------------------------ serving
  * Continuous-batching request loop (not in the paper; it serves frames of
  * different resolutions and fixations as they arrive). Frames start and end
  * in host memory. Requests are admitted while device memory for their input
  * and output is available within `device_budget_bytes`; every scheduling tick
- * the worker renders all admitted requests whose input copy has finished as
- * one batch (same kernels as fovea_render_batch), while later requests copy
- * in on a second stream. Results are copied back to the caller's host buffer.
+ * the worker renders the admitted requests whose input copy has finished,
+ * one batch per (format, channel count) (same kernels as fovea_render_batch),
+ * while later requests copy in on a second stream. Results are copied back to
+ * the caller's host buffer.
  */
 typedef struct {
   size_t device_budget_bytes;  /* cap on device memory used for request buffers */

@@ -586,4 +586,6 @@ int ctx_device_info(const fovea_ctx* ctx, int* device, int* num_sms) {
   return FOVEA_OK;
 }
 
+int record_cuda_failure(int cuda_error) { return cuda_fail((cudaError_t)cuda_error); }
+
 }  // namespace fovea

@@ -15,6 +15,9 @@ int check_frame(int W, int H, int C, int fmt, int B, double sigma0, double k, fl
 size_t frame_bytes(int W, int H, int C, int fmt);
 int ctx_shape(const fovea_ctx* ctx, int* W, int* H, int* C, int* fmt, int* B);
 int ctx_device_info(const fovea_ctx* ctx, int* device, int* num_sms);
+// Records a failed cudaError_t for fovea_last_cuda_error and returns the
+// status it maps to (FOVEA_ENOMEM for an allocation failure, else FOVEA_ECUDA).
+int record_cuda_failure(int cuda_error);
 
 }  // namespace fovea
 

@@ -48,13 +48,14 @@ void* g_scratch_ptr[kMaxDevices] = {};
 int scratch_for_current_device(unsigned char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return FOVEA_ECUDA;
+  if (e != cudaSuccess) return record_cuda_failure(e);
   if (dev < 0 || dev >= kMaxDevices) return FOVEA_EUNSUPPORTED;
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) return FOVEA_ECUDA;
+    if (e != cudaSuccess) return record_cuda_failure(e);
+    if (!p) return FOVEA_ECUDA;
     g_scratch_ptr[dev] = p;
   }
   *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
@@ -80,8 +81,9 @@ extern "C" int fovea_render_noalloc(const void* in_dev, void* out_dev, int width
   st = scratch_for_current_device(&base);
   if (st != FOVEA_OK) return st;
   int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    return FOVEA_ECUDA;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return record_cuda_failure(e);
 
   Workspace ws;
   ws.items = reinterpret_cast<ItemInfo*>(base);
@@ -92,7 +94,8 @@ extern "C" int fovea_render_noalloc(const void* in_dev, void* out_dev, int width
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // The counters (ticket, done flags, radius histogram) must start at zero.
-  if (cudaMemsetAsync(ws.counters, 0, kCounterBytes, s) != cudaSuccess) return FOVEA_ECUDA;
+  e = cudaMemsetAsync(ws.counters, 0, kCounterBytes, s);
+  if (e != cudaSuccess) return record_cuda_failure(e);
 
   FrameSource src;
   std::memset(&src, 0, sizeof(src));
@@ -108,12 +111,13 @@ extern "C" int fovea_render_noalloc(const void* in_dev, void* out_dev, int width
 
   const int rmax = radius_bound(width, height, block, fix_x, fix_y, sigma0, k);
   const int sg = (int)((items + 255) / 256);
-  if (launch_sigma_order(src, ws, sg < 1 ? 1 : (sg > 4 * sms ? 4 * sms : sg), nullptr, nullptr, s) != cudaSuccess)
-    return FOVEA_ECUDA;
+  e = launch_sigma_order(src, ws, sg < 1 ? 1 : (sg > 4 * sms ? 4 * sms : sg), nullptr, nullptr, s);
+  if (e != cudaSuccess) return record_cuda_failure(e);
   const FwdConfig cfg{256, 0, 32, 0};
   const int fmt_mask = format == FOVEA_F32_CHW ? 2 : 1;
   const int per = forward_max_ctas_per_sm(cfg, rmax, fmt_mask);
   if (per <= 0) return FOVEA_EUNSUPPORTED;
-  if (launch_forward(src, ws, cfg, rmax, fmt_mask, per * sms, s) != cudaSuccess) return FOVEA_ECUDA;
+  e = launch_forward(src, ws, cfg, rmax, fmt_mask, per * sms, s);
+  if (e != cudaSuccess) return record_cuda_failure(e);
   return FOVEA_OK;
 }

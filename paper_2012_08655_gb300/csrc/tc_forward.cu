@@ -34,20 +34,30 @@ constexpr int kVHalves = 128 * 72;     // halves of one V array (max over C of 3
 
 __host__ __device__ inline int npair(int rmax) { return rmax + 56; }
 
-constexpr int kTcStages = 4;          // raw uint8 chunks in flight or staged
+// Raw uint8 chunks staged or in flight: one load in flight while a chunk is
+// converted and another multiplied, two for the short 16-row chunks.
+__host__ __device__ constexpr int tc_stages(int rb) { return rb >= 32 ? 3 : 4; }
 
 struct TcLayout {
   size_t ring, th, vh, vl, taps, cum, pairs, red, total;
 };
 
+// The normalised taps are needed only while the cumulative and tap-pair
+// tables are built, before the first V is written: they live in the V arrays.
 __host__ __device__ inline TcLayout tc_layout(int rb, int rmax) {
   TcLayout L;
-  L.ring = 0;                                                  // u8 [kTcStages][rb][256]
-  L.th = L.ring + (size_t)kTcStages * rb * kRowBytesU8;        // half [2][rb][kThPitch]
+  L.ring = 0;                                                  // u8 [stages][rb][256]
+  L.th = L.ring + (size_t)tc_stages(rb) * rb * kRowBytesU8;    // half [2][rb][kThPitch]
   L.vh = L.th + (size_t)2 * rb * kThPitch * 2;                 // half [kVHalves]
   L.vl = L.vh + (size_t)kVHalves * 2;                          // half [kVHalves]
-  L.taps = L.vl + (size_t)kVHalves * 2;                        // float2 [tap_len]
-  L.cum = L.taps + (size_t)tap_len(rmax) * sizeof(float2);     // float [cum_len]
+  size_t end = L.vl + (size_t)kVHalves * 2;
+  if ((size_t)tap_len(rmax) * sizeof(float2) <= (size_t)2 * kVHalves * 2) {
+    L.taps = L.vh;                                             // float2 [tap_len], aliases V
+  } else {
+    L.taps = end;
+    end += (size_t)tap_len(rmax) * sizeof(float2);
+  }
+  L.cum = end;                                                 // float [cum_len]
   L.pairs = L.cum + (size_t)((cum_len(rmax) + 3) & ~3) * 4;    // uint32 [4][npair]
   L.red = L.pairs + (size_t)4 * npair(rmax) * 4;               // float [32]
   L.total = L.red + 32 * sizeof(float);
@@ -168,17 +178,18 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
                                         __half* Vl, float2* U, float* CU, unsigned int* P, float* red, int np) {
   constexpr int PXP = TcGeo<C>::PXP, VP = TcGeo<C>::VP;
   constexpr size_t stage_bytes = (size_t)RB * kRowBytesU8;
+  constexpr int kStagesTc = tc_stages(RB);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int r = it.r;
   const int Q = it.nsl * it.nchunks;
   const size_t frame_bytes = (size_t)it.H * it.pitch;
 
-  // Raw uint8 chunks stream through kTcStages ring stages (cp.async); chunk
-  // q+1 is converted to fp16 while chunk q feeds the tensor cores, so the two
-  // fp16 buffers alternate and one barrier per chunk suffices.
+  // Raw uint8 chunks stream through the ring stages (cp.async); chunk q+1 is
+  // converted to fp16 while chunk q feeds the tensor cores, so the two fp16
+  // buffers alternate and one barrier per chunk suffices.
   #pragma unroll
-  for (int q = 0; q < kTcStages - 1; ++q) {
+  for (int q = 0; q < kStagesTc - 1; ++q) {
     if (q < Q) stage_rows<true, RB>(it, slab_of<true>(it, q / it.nchunks), q % it.nchunks,
                                     ring + (size_t)q * stage_bytes, frame_bytes);
     cp_async_commit();
@@ -192,7 +203,7 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
     const Slab cs = slab_of<true>(it, qc / it.nchunks);
     const int cnpx = cs.sws / C;
     const int cngrp = ((cnpx + 15) & ~15) >> 3;  // 8-pixel groups per channel
-    const unsigned char* st = ring + (size_t)(qc % kTcStages) * stage_bytes;
+    const unsigned char* st = ring + (size_t)(qc % kStagesTc) * stage_bytes;
     __half* dst = Th + (size_t)(qc & 1) * RB * kThPitch;
     const int ph3 = cs.ph & 3;
     for (int idx = threadIdx.x; idx < RB * cngrp; idx += kThreads) {
@@ -207,8 +218,8 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
       }
     }
   };
-  cp_async_wait<kTcStages - 2>();
-  __syncthreads();  // chunk 0 landed for every thread; taps ready
+  cp_async_wait<kStagesTc - 2>();
+  __syncthreads();  // chunk 0 landed for every thread; tables ready, taps dead
   convert_chunk(0);
 
   // Pass 1: each lane reads the tap-pair table of its parity (the tap index
@@ -225,12 +236,12 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
     for (int k = 0; k < 4; ++k) acc2[i][k] = 0.f;
 
   for (int q = 0; q < Q; ++q) {
-    cp_async_wait<kTcStages - 3>();
+    cp_async_wait<kStagesTc - 3>();
     __syncthreads();  // chunk q converted and q+1 landed; iteration q-1 finished everywhere
     {
-      const int qn = q + kTcStages - 1;
+      const int qn = q + kStagesTc - 1;
       if (qn < Q) stage_rows<true, RB>(it, slab_of<true>(it, qn / it.nchunks), qn % it.nchunks,
-                                       ring + (size_t)(qn % kTcStages) * stage_bytes, frame_bytes);
+                                       ring + (size_t)(qn % kStagesTc) * stage_bytes, frame_bytes);
       cp_async_commit();
     }
     if (q + 1 < Q) convert_chunk(q + 1);

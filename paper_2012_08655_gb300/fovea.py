@@ -79,6 +79,7 @@ _sig = {
     "fovea_render_noalloc": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _d, _d, _f, _f, _vp]),
     "fovea_strerror": (ctypes.c_char_p, [_i]),
     "fovea_last_cuda_error": (_i, []),
+    "fovea_measure_fma_rate": (_i, [ctypes.POINTER(_d), _vp]),
     "fovea_server_create": (_i, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)]),
     "fovea_server_submit": (ctypes.c_longlong, [_vp, ctypes.POINTER(Frame), _d]),
     "fovea_server_wait": (_i, [_vp, ctypes.c_longlong, _i, ctypes.POINTER(RequestTimes)]),
@@ -304,6 +305,14 @@ def render_noalloc(x: torch.Tensor, out: torch.Tensor, fix_x: float, fix_y: floa
                                      float(k), float(fix_x), float(fix_y), _stream_handle(stream)),
            "fovea_render_noalloc")
     return out
+
+
+def measure_fma_rate(stream=None) -> float:
+    """Measured FP32 FMA lane-operations per second of the current GPU
+    (``fovea_measure_fma_rate``): the roof of the blur kernels' arithmetic."""
+    v = ctypes.c_double(0.0)
+    _check(_lib.fovea_measure_fma_rate(ctypes.byref(v), _stream_handle(stream)), "fovea_measure_fma_rate")
+    return v.value
 
 
 def sigma_table(width: int, height: int, fix_x: float, fix_y: float, sigma0: float = 0.5, k: float = 0.02,

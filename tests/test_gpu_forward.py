@@ -206,3 +206,13 @@ def test_tensor_core_kernel_matches_fp32_kernel(fv, W, H, C, B, fx, fy, k):
     blocks = sample_blocks(W, H, B, fx, fy, n_random=16, seed=3)
     ref = oracle.forward_u8(img, B, fx, fy, 0.5, k, "hwc", blocks=blocks)
     assert_u8_close(ytc.cpu().numpy(), ref, mask=block_mask(W, H, B, blocks, "hwc", C), min_equal=0.995)
+
+
+# ---------------------------------------------------------------- FP32 FMA roof probe
+
+def test_measured_fma_rate_is_plausible(fv):
+    rate = fv.measure_fma_rate()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    # at most 128 FP32 lanes per SM at a clock of at most 3 GHz; at least a
+    # tenth of that at 1 GHz
+    assert 0.1 * sms * 128 * 1e9 < rate < sms * 128 * 3e9
