@@ -69,6 +69,8 @@ def parse_args():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiling runs)")
     p.add_argument("--tensor-cores", type=int, choices=[0, 1], default=None,
                    help="force the forward kernel (0: fp32 FMA, 1: tensor cores) instead of autotuning")
+    p.add_argument("--rows-per-chunk", type=int, choices=[16, 32, 64], default=32,
+                   help="row chunk of the forced kernel (with --tensor-cores)")
     return p.parse_args()
 
 
@@ -82,9 +84,10 @@ def kernel_source_hash(tc: int) -> str:
     return h.hexdigest()[:16]
 
 
-def profiled(tc: int):
+def profiled(tc: int, rows_per_chunk: int):
     """Fields of the committed ncu summary of the timed kernel, or {} when it
-    is missing or the kernel's sources changed since it was taken."""
+    is missing, was taken with another row chunk, or the kernel's sources
+    changed since it was taken."""
     try:
         vals = {}
         with open(KERNELS[tc][1]) as f:
@@ -93,6 +96,8 @@ def profiled(tc: int):
                     k, v = line.split(":", 1)
                     vals[k.strip()] = v.strip()
         if vals.get("kernel_source_sha256_16") != kernel_source_hash(tc):
+            return {}
+        if vals.get("rows_per_chunk") != str(rows_per_chunk):
             return {}
         return vals
     except OSError:
@@ -437,7 +442,7 @@ def run_ours(args):
     outs = [torch.empty_like(base) for _ in range(pool_n)]
     ctx = fv.Context(W, H, C, B, SIGMA0, K_SLOPE, fv.U8_HWC)
     if args.tensor_cores is not None:
-        ctx.set_config(256, 0, 32, tensor_cores=args.tensor_cores)
+        ctx.set_config(256, 0, args.rows_per_chunk, tensor_cores=args.tensor_cores)
         cfg = ctx.get_config()
     else:
         cfg = ctx.get_config() if args.no_autotune else ctx.autotune(iters=20)
@@ -480,7 +485,7 @@ def run_ours(args):
     peak_tflops = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
     achieved = 2 * fmas / (kernel_ms * 1e-3) / 1e12
     tc = int(cfg.get("tensor_cores", 0))
-    prof = profiled(tc)
+    prof = profiled(tc, int(cfg.get("rows_per_chunk", 32)))
     try:
         traffic = float(prof["dram_bytes_per_launch"]) if prof else None
     except (KeyError, ValueError):

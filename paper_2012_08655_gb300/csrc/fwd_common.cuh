@@ -64,12 +64,13 @@ __device__ __forceinline__ Slab slab_of(const Item& it, int s) {
   return sl;
 }
 
-// Stage rows [k*RB, (k+1)*RB) (virtual) of slab `sl` into one ring stage.
-template <bool U8, int RB>
+// Stage rows [k*RB, (k+1)*RB) (virtual) of slab `sl` into one ring stage
+// whose rows are ROWB bytes apart.
+template <bool U8, int RB, int ROWB = (U8 ? kRowBytesU8 : kRowBytesF32)>
 __device__ __forceinline__ void stage_rows(const Item& it, const Slab& sl, int k, unsigned char* ring,
                                            size_t frame_bytes) {
   constexpr int esz = U8 ? 1 : 4;
-  constexpr int row_bytes = U8 ? kRowBytesU8 : kRowBytesF32;
+  constexpr int row_bytes = ROWB;
   if (it.fast) {
     const int nch = (sl.ph * esz + sl.sws * esz + 15) >> 4;  // 16-byte copies per row
     for (int idx = threadIdx.x; idx < RB * nch; idx += kThreads) {

@@ -6,16 +6,20 @@
 //   pass 1 (vertical):   V[yo][e] = sum_v Wv[yo][v] T[v][e],  Wv[yo][v] = u(v - yo + D0)
 //   pass 2 (horizontal): O[(c,yo)][x] = sum_p V[(c,yo)][p] Wh[p][x],  Wh[p][x] = u(offx + p - x)
 // and run on the tensor cores with mma.sync.m16n8k16 (fp16 operands, fp32
-// accumulation). uint8 values are exact in fp16. To keep fp32-level accuracy
-// the taps (scaled by 2^12, clear of fp16 subnormals) are split into
-// hi + lo fp16 parts, and so is the intermediate V:
+// accumulation). To keep fp32-level accuracy the taps (scaled by 2^12, clear
+// of fp16 subnormals) are split into hi + lo fp16 parts, and so is the
+// intermediate V:
 //   pass 1: Whi T + Wlo T;   pass 2: Vhi Whi + Vhi Wlo + Vlo Whi.
 // Toeplitz structure means an operand fragment of Wv or Wh is a pair of
 // consecutive taps per register: the fragments come straight from 1D
-// tap-pair tables, no 2D weight matrix is built. The taps of the folded edge
+// tap-pair tables, no 2D weight matrix is built. Pass 1 reads its data
+// operand straight from the staged uint8 rows: a byte b placed in the low
+// bits of an fp16 is the subnormal b * 2^-24, exactly, so two byte permutes
+// turn two staged rows into the fragment registers of four n-tiles and no
+// converted copy of the tile is ever written. The taps of the folded edge
 // rows / columns (clamp-to-edge, see forward.cu) are added as fp32 rank-one
-// corrections. Tile staging, slabs and the work list are shared with the
-// fp32 kernel (fwd_common.cuh).
+// corrections. Slabs, row staging and the work list are shared with the fp32
+// kernel (fwd_common.cuh).
 #include <cuda_fp16.h>
 
 #include "fwd_common.cuh"
@@ -26,10 +30,12 @@ namespace {
 
 using namespace fwd;
 
-constexpr float kWScale = 4096.0f;
+constexpr float kWScale = 4096.0f;          // taps scaled by 2^12
 constexpr float kWInv = 1.0f / 4096.0f;
-constexpr int kThPitch = 264;          // halves per staged fp16 row: 528 B (odd multiple of 16 B)
-constexpr int kPairPad = 32;           // tap index -kPairPad is pair entry 0
+constexpr float kDScale = 1.0f / 16777216.0f;  // a staged byte b enters pass 1 as b * 2^-24
+constexpr float kVScale = 4096.0f;          // V = pass-1 accumulator * 2^12 (= 2^24 / 2^12)
+constexpr int kRingPitch = 272;             // bytes per staged row: 68 words, rows 2 apart 8 banks apart
+constexpr int kPairPad = 32;                // tap index -kPairPad is pair entry 0
 constexpr int kVHalves = 128 * 72;     // halves of one V array (max over C of 32C rows x VP)
 
 __host__ __device__ inline int npair(int rmax) { return rmax + 56; }
@@ -39,16 +45,15 @@ __host__ __device__ inline int npair(int rmax) { return rmax + 56; }
 __host__ __device__ constexpr int tc_stages(int rb) { return rb >= 32 ? 3 : 4; }
 
 struct TcLayout {
-  size_t ring, th, vh, vl, taps, cum, pairs, red, total;
+  size_t ring, vh, vl, taps, cum, pairs, red, total;
 };
 
 // The normalised taps are needed only while the cumulative and tap-pair
 // tables are built, before the first V is written: they live in the V arrays.
 __host__ __device__ inline TcLayout tc_layout(int rb, int rmax) {
   TcLayout L;
-  L.ring = 0;                                                  // u8 [stages][rb][256]
-  L.th = L.ring + (size_t)tc_stages(rb) * rb * kRowBytesU8;    // half [2][rb][kThPitch]
-  L.vh = L.th + (size_t)2 * rb * kThPitch * 2;                 // half [kVHalves]
+  L.ring = 0;                                                  // u8 [stages][rb][kRingPitch]
+  L.vh = L.ring + (size_t)tc_stages(rb) * rb * kRingPitch;     // half [kVHalves]
   L.vl = L.vh + (size_t)kVHalves * 2;                          // half [kVHalves]
   size_t end = L.vl + (size_t)kVHalves * 2;
   if ((size_t)tap_len(rmax) * sizeof(float2) <= (size_t)2 * kVHalves * 2) {
@@ -68,64 +73,13 @@ __device__ __forceinline__ unsigned int pack_half2(__half a, __half b) {
   return (unsigned int)__half_as_ushort(a) | ((unsigned int)__half_as_ushort(b) << 16);
 }
 
-// Two bytes (low half of x) -> two fp16, exactly: 0x64XX is 1024 + XX.
-__device__ __forceinline__ unsigned int u8x2_to_h2(unsigned int x) {
-  const unsigned int b = __byte_perm(x, 0x64646464u, 0x5140);
-  const __half2 bias = __halves2half2(__ushort_as_half(0x6400), __ushort_as_half(0x6400));
-  __half2 h = __hsub2(*reinterpret_cast<const __half2*>(&b), bias);
-  return *reinterpret_cast<unsigned int*>(&h);
-}
-
-__device__ __forceinline__ void stsm_x4(void* p, unsigned int r0, unsigned int r1, unsigned int r2, unsigned int r3) {
-  const unsigned int s = (unsigned int)__cvta_generic_to_shared(p);
-  asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1,%2,%3,%4};\n" ::"r"(s), "r"(r0), "r"(r1), "r"(r2),
-               "r"(r3) : "memory");
-}
-
-__device__ __forceinline__ unsigned int pack_f2h2(float a, float b) {
-  __half2 h = __floats2half2_rn(a, b);
-  return *reinterpret_cast<unsigned int*>(&h);
-}
-
-// Per channel count: fp16 columns reserved per channel in a staged row, and
-// the pitch (halves) of the pass-2 operand rows (odd multiple of 16 bytes).
+// Per channel count: pitch (halves) of the pass-2 operand rows V[(c, yo)][p]
+// (an odd multiple of 16 bytes, at least the slab's pixels rounded up to 16).
 template <int C> struct TcGeo;
-template <> struct TcGeo<1> { static constexpr int PXP = 256, VP = 264; };
-template <> struct TcGeo<2> { static constexpr int PXP = 128, VP = 136; };
-template <> struct TcGeo<3> { static constexpr int PXP = 80, VP = 88; };
-template <> struct TcGeo<4> { static constexpr int PXP = 64, VP = 72; };
-
-// One staged uint8 row -> fp16, de-interleaving the channels: pixels 8q..8q+7
-// of every channel c go to Th[c*PXP + 8q ...]; pixels >= npx become 0.
-// PH3 is the slab's byte phase modulo 4 (ring byte of pixel p, channel c is
-// ph + C*p + c), so every byte position below is a compile-time constant.
-template <int C, int PH3>
-__device__ __forceinline__ void convert_group(const unsigned char* rowp, int ph, int q, int npx, __half* throw_) {
-  constexpr int NW = 2 * C + 1;
-  const int w0 = (ph + 8 * C * q) >> 2;
-  const unsigned int* wp = reinterpret_cast<const unsigned int*>(rowp);
-  unsigned int wd[NW];
-  #pragma unroll
-  for (int k = 0; k < NW; ++k) wd[k] = (w0 + k < kRowBytesU8 / 4) ? wp[w0 + k] : 0u;
-  #pragma unroll
-  for (int c = 0; c < C; ++c) {
-    unsigned int h[4];
-    #pragma unroll
-    for (int i2 = 0; i2 < 4; ++i2) {
-      const int b0 = PH3 + C * (2 * i2) + c, b1 = b0 + C;
-      const unsigned int x = __byte_perm(wd[b0 >> 2], wd[b1 >> 2], (b0 & 3) | (((b1 & 3) + 4) << 4));
-      h[i2] = u8x2_to_h2(x);
-    }
-    if (8 * q + 8 > npx) {
-      #pragma unroll
-      for (int i2 = 0; i2 < 4; ++i2) {
-        if (8 * q + 2 * i2 >= npx) h[i2] = 0u;
-        else if (8 * q + 2 * i2 + 1 >= npx) h[i2] &= 0xFFFFu;
-      }
-    }
-    *reinterpret_cast<uint4*>(throw_ + c * TcGeo<C>::PXP + 8 * q) = make_uint4(h[0], h[1], h[2], h[3]);
-  }
-}
+template <> struct TcGeo<1> { static constexpr int VP = 264; };
+template <> struct TcGeo<2> { static constexpr int VP = 136; };
+template <> struct TcGeo<3> { static constexpr int VP = 88; };
+template <> struct TcGeo<4> { static constexpr int VP = 72; };
 
 // No side effects: left to the compiler to schedule (independent chains interleave).
 __device__ __forceinline__ void mma16816(float (&d)[4], const unsigned int (&a)[4], unsigned int b0, unsigned int b1) {
@@ -138,12 +92,6 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const unsigned int (&a)[
 __device__ __forceinline__ void ldsm_x4(unsigned int (&r)[4], const void* p) {
   const unsigned int s = (unsigned int)__cvta_generic_to_shared(p);
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(s));
-}
-
-__device__ __forceinline__ void ldsm_x4_t(unsigned int (&r)[4], const void* p) {
-  const unsigned int s = (unsigned int)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(s));
 }
 
@@ -174,10 +122,10 @@ __device__ __forceinline__ void make_pairs(const float2* U, unsigned int* P, int
 
 // Everything the tensor-core kernel does for one item with C channels.
 template <int RB, int C>
-__device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned char* ring, __half* Th, __half* Vh,
-                                        __half* Vl, float2* U, float* CU, unsigned int* P, float* red, int np) {
-  constexpr int PXP = TcGeo<C>::PXP, VP = TcGeo<C>::VP;
-  constexpr size_t stage_bytes = (size_t)RB * kRowBytesU8;
+__device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned char* ring, __half* Vh, __half* Vl,
+                                        float2* U, float* CU, unsigned int* P, float* red, int np) {
+  constexpr int VP = TcGeo<C>::VP;
+  constexpr size_t stage_bytes = (size_t)RB * kRingPitch;
   constexpr int kStagesTc = tc_stages(RB);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
@@ -185,48 +133,27 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
   const int Q = it.nsl * it.nchunks;
   const size_t frame_bytes = (size_t)it.H * it.pitch;
 
-  // Raw uint8 chunks stream through the ring stages (cp.async); chunk q+1 is
-  // converted to fp16 while chunk q feeds the tensor cores, so the two fp16
-  // buffers alternate and one barrier per chunk suffices.
+  // Raw uint8 chunks (slab s, rows k*RB ..) stream through the ring stages.
   #pragma unroll
   for (int q = 0; q < kStagesTc - 1; ++q) {
-    if (q < Q) stage_rows<true, RB>(it, slab_of<true>(it, q / it.nchunks), q % it.nchunks,
-                                    ring + (size_t)q * stage_bytes, frame_bytes);
+    if (q < Q) stage_rows<true, RB, kRingPitch>(it, slab_of<true>(it, q / it.nchunks), q % it.nchunks,
+                                                ring + (size_t)q * stage_bytes, frame_bytes);
     cp_async_commit();
   }
   make_taps(U, tap_len(r), r, c_tap, red);
   make_cumulative(U, CU, r);
   make_pairs(U, P, r, np);
 
-  // uint8 chunk qc -> channel-planar fp16 rows in Th buffer qc % 2
-  auto convert_chunk = [&](int qc) {
-    const Slab cs = slab_of<true>(it, qc / it.nchunks);
-    const int cnpx = cs.sws / C;
-    const int cngrp = ((cnpx + 15) & ~15) >> 3;  // 8-pixel groups per channel
-    const unsigned char* st = ring + (size_t)(qc % kStagesTc) * stage_bytes;
-    __half* dst = Th + (size_t)(qc & 1) * RB * kThPitch;
-    const int ph3 = cs.ph & 3;
-    for (int idx = threadIdx.x; idx < RB * cngrp; idx += kThreads) {
-      const int row = idx / cngrp, gq = idx - row * cngrp;
-      const unsigned char* rowp = st + (size_t)row * kRowBytesU8;
-      __half* throw_ = dst + (size_t)row * kThPitch;
-      switch (ph3) {
-        case 0: convert_group<C, 0>(rowp, cs.ph, gq, cnpx, throw_); break;
-        case 1: convert_group<C, 1>(rowp, cs.ph, gq, cnpx, throw_); break;
-        case 2: convert_group<C, 2>(rowp, cs.ph, gq, cnpx, throw_); break;
-        default: convert_group<C, 3>(rowp, cs.ph, gq, cnpx, throw_); break;
-      }
-    }
-  };
-  cp_async_wait<kStagesTc - 2>();
-  __syncthreads();  // chunk 0 landed for every thread; tables ready, taps dead
-  convert_chunk(0);
-
   // Pass 1: each lane reads the tap-pair table of its parity (the tap index
   // of every A register of this lane has the parity of g, D0 being even).
   const unsigned int* Ph = P + ((g & 1) ? np : 0);
   const unsigned int* Pl = P + 2 * np + ((g & 1) ? np : 0);
   const int D0 = it.offy - it.ph;  // tap(v, yo) = v + D0 - yo
+  // This warp's pass-1 columns are ring bytes 32w .. 32w+31. Lane (g, t)
+  // feeds bytes 32w + 4g + j to n-tile j (column g) and accumulates, for
+  // n-tile j, the ring bytes 32w + 8t + j (column 2t) and 32w + 8t + 4 + j
+  // (column 2t + 1).
+  const int colw = 32 * warp;
 
   float acc1[2][4][4];
   float acc2[C][4];
@@ -236,23 +163,19 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
     for (int k = 0; k < 4; ++k) acc2[i][k] = 0.f;
 
   for (int q = 0; q < Q; ++q) {
-    cp_async_wait<kStagesTc - 3>();
-    __syncthreads();  // chunk q converted and q+1 landed; iteration q-1 finished everywhere
+    cp_async_wait<kStagesTc - 2>();
+    __syncthreads();  // chunk q landed for every thread; iteration q-1 finished everywhere
     {
       const int qn = q + kStagesTc - 1;
-      if (qn < Q) stage_rows<true, RB>(it, slab_of<true>(it, qn / it.nchunks), qn % it.nchunks,
-                                       ring + (size_t)(qn % kStagesTc) * stage_bytes, frame_bytes);
+      if (qn < Q) stage_rows<true, RB, kRingPitch>(it, slab_of<true>(it, qn / it.nchunks), qn % it.nchunks,
+                                                   ring + (size_t)(qn % kStagesTc) * stage_bytes, frame_bytes);
       cp_async_commit();
     }
-    if (q + 1 < Q) convert_chunk(q + 1);
     const int s = q / it.nchunks, k = q - s * it.nchunks;
     const Slab sl = slab_of<true>(it, s);
     const int R0 = k * RB;
-    const int npx = sl.sws / C;                 // pixels of the slab
-    const int npx16 = (npx + 15) & ~15;
-    const __half* thc = Th + (size_t)(q & 1) * RB * kThPitch;
-    // This warp's 32 columns: channel c0 = 32w / PXP, pixel offset inside it.
-    const int colw = 32 * warp;
+    const unsigned char* st = ring + (size_t)(q % kStagesTc) * stage_bytes;
+    const bool wact = colw < sl.ph + sl.sws && colw + 32 > sl.ph;  // warp holds slab bytes
     if (k == 0) {
       #pragma unroll
       for (int mt = 0; mt < 2; ++mt)
@@ -260,32 +183,25 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
         for (int nt = 0; nt < 4; ++nt)
           #pragma unroll
           for (int i = 0; i < 4; ++i) acc1[mt][nt][i] = 0.f;
-      if (it.foldT && colw < C * PXP) {  // folded top row first: fixed summation order
-        const __half* row = thc + (size_t)it.ph * kThPitch;
+      if (it.foldT && wact) {  // folded top row first: fixed summation order
+        const uint2 wd = *reinterpret_cast<const uint2*>(st + (size_t)it.ph * kRingPitch + colw + 8 * t);
         #pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-          const float2 df = __half22float2(*reinterpret_cast<const __half2*>(row + colw + 8 * nt + 2 * t));
+        for (int mt = 0; mt < 2; ++mt) {
+          const float c0 = cum_at(CU, it.offy - (16 * mt + g), r) * (kWScale * kDScale);
+          const float c1 = cum_at(CU, it.offy - (16 * mt + g + 8), r) * (kWScale * kDScale);
           #pragma unroll
-          for (int mt = 0; mt < 2; ++mt) {
-            const float c0 = cum_at(CU, it.offy - (16 * mt + g), r) * kWScale;
-            const float c1 = cum_at(CU, it.offy - (16 * mt + g + 8), r) * kWScale;
-            acc1[mt][nt][0] = fmaf(c0, df.x, acc1[mt][nt][0]);
-            acc1[mt][nt][1] = fmaf(c0, df.y, acc1[mt][nt][1]);
-            acc1[mt][nt][2] = fmaf(c1, df.x, acc1[mt][nt][2]);
-            acc1[mt][nt][3] = fmaf(c1, df.y, acc1[mt][nt][3]);
+          for (int j = 0; j < 4; ++j) {
+            const float d0 = (float)((wd.x >> (8 * j)) & 0xFFu), d1 = (float)((wd.y >> (8 * j)) & 0xFFu);
+            acc1[mt][j][0] = fmaf(c0, d0, acc1[mt][j][0]);
+            acc1[mt][j][1] = fmaf(c0, d1, acc1[mt][j][1]);
+            acc1[mt][j][2] = fmaf(c1, d0, acc1[mt][j][2]);
+            acc1[mt][j][3] = fmaf(c1, d1, acc1[mt][j][3]);
           }
         }
       }
     }
-    // n-tile pairs of this warp that hold slab pixels
-    bool pon[2];
-    #pragma unroll
-    for (int np2 = 0; np2 < 2; ++np2) {
-      const int j0 = colw + 16 * np2;
-      pon[np2] = j0 < C * PXP && (j0 % PXP) < npx16;
-    }
     // ---- pass 1 on the chunk: 16 virtual rows per k-step
-    if (pon[0] || pon[1]) {
+    if (wact) {
       for (int ks = 0; ks < RB / 16; ++ks) {
         const int k0 = R0 + 16 * ks;
         if (k0 >= it.vrows) break;
@@ -302,29 +218,30 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
           al[0][0] = l_0; al[0][1] = l_m4; al[0][2] = l_p4; al[0][3] = l_0;
           al[1][0] = l_m8; al[1][1] = l_m12; al[1][2] = l_m4; al[1][3] = l_m8;
         }
-        const __half* tb = thc + (size_t)(k0 - R0) * kThPitch + colw;
-        unsigned int b[2][4];
-        #pragma unroll
-        for (int np2 = 0; np2 < 2; ++np2) {
-          if (!pon[np2]) continue;
-          const int rrow = (lane & 7) + ((lane >> 3) & 1) * 8;
-          const int rcol = 16 * np2 + ((lane >> 4) & 1) * 8;
-          ldsm_x4_t(b[np2], tb + (size_t)rrow * kThPitch + rcol);
+        // B fragments of the four n-tiles from rows 2t, 2t+1, 2t+8, 2t+9:
+        // (byte of row v, byte of row v+1) -> two fp16 subnormals.
+        unsigned int b[4][2];
+        {
+          const unsigned char* sb = st + (size_t)(k0 - R0 + 2 * t) * kRingPitch + colw + 4 * g;
+          const unsigned int w0 = *reinterpret_cast<const unsigned int*>(sb);
+          const unsigned int w1 = *reinterpret_cast<const unsigned int*>(sb + kRingPitch);
+          const unsigned int w8 = *reinterpret_cast<const unsigned int*>(sb + 8 * kRingPitch);
+          const unsigned int w9 = *reinterpret_cast<const unsigned int*>(sb + 9 * kRingPitch);
+          const unsigned int lo01 = __byte_perm(w0, w1, 0x5140), lo23 = __byte_perm(w0, w1, 0x7362);
+          const unsigned int hi01 = __byte_perm(w8, w9, 0x5140), hi23 = __byte_perm(w8, w9, 0x7362);
+          b[0][0] = __byte_perm(lo01, 0u, 0x4140); b[1][0] = __byte_perm(lo01, 0u, 0x4342);
+          b[2][0] = __byte_perm(lo23, 0u, 0x4140); b[3][0] = __byte_perm(lo23, 0u, 0x4342);
+          b[0][1] = __byte_perm(hi01, 0u, 0x4140); b[1][1] = __byte_perm(hi01, 0u, 0x4342);
+          b[2][1] = __byte_perm(hi23, 0u, 0x4140); b[3][1] = __byte_perm(hi23, 0u, 0x4342);
         }
         // all hi products, then all lo products: the two products into one
         // accumulator are 8 independent MMAs apart
         #pragma unroll
         for (int part = 0; part < 2; ++part) {
           #pragma unroll
-          for (int np2 = 0; np2 < 2; ++np2) {
-            if (!pon[np2]) continue;
-            #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int nt = 2 * np2 + h;
-              const unsigned int b0 = b[np2][2 * h], b1 = b[np2][2 * h + 1];
-              if (on0) mma16816(acc1[0][nt], part ? al[0] : ah[0], b0, b1);
-              if (on1) mma16816(acc1[1][nt], part ? al[1] : ah[1], b0, b1);
-            }
+          for (int j = 0; j < 4; ++j) {
+            if (on0) mma16816(acc1[0][j], part ? al[0] : ah[0], b[j][0], b[j][1]);
+            if (on1) mma16816(acc1[1][j], part ? al[1] : ah[1], b[j][0], b[j][1]);
           }
         }
       }
@@ -332,47 +249,54 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
     if (k != it.nchunks - 1) continue;
 
     // ---- slab complete: folded bottom row, then V -> hi/lo fp16 for pass 2
+    const int npx = sl.sws / C;                 // pixels of the slab
+    const int npx16 = (npx + 15) & ~15;
     {
       const int vb = it.ph + it.EH - 1;
-      if (it.foldB && vb >= R0 && vb < R0 + RB && colw < C * PXP) {
-        const __half* row = thc + (size_t)(vb - R0) * kThPitch;
+      if (it.foldB && vb >= R0 && vb < R0 + RB && wact) {
+        const uint2 wd = *reinterpret_cast<const uint2*>(st + (size_t)(vb - R0) * kRingPitch + colw + 8 * t);
         #pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-          const float2 df = __half22float2(*reinterpret_cast<const __half2*>(row + colw + 8 * nt + 2 * t));
+        for (int mt = 0; mt < 2; ++mt) {
+          const float c0 = cum_at(CU, 2 * r + 1 - (it.offy + it.EH - (16 * mt + g)), r) * (kWScale * kDScale);
+          const float c1 = cum_at(CU, 2 * r + 1 - (it.offy + it.EH - (16 * mt + g + 8)), r) * (kWScale * kDScale);
           #pragma unroll
-          for (int mt = 0; mt < 2; ++mt) {
-            const float c0 = cum_at(CU, 2 * r + 1 - (it.offy + it.EH - (16 * mt + g)), r) * kWScale;
-            const float c1 = cum_at(CU, 2 * r + 1 - (it.offy + it.EH - (16 * mt + g + 8)), r) * kWScale;
-            acc1[mt][nt][0] = fmaf(c0, df.x, acc1[mt][nt][0]);
-            acc1[mt][nt][1] = fmaf(c0, df.y, acc1[mt][nt][1]);
-            acc1[mt][nt][2] = fmaf(c1, df.x, acc1[mt][nt][2]);
-            acc1[mt][nt][3] = fmaf(c1, df.y, acc1[mt][nt][3]);
+          for (int j = 0; j < 4; ++j) {
+            const float d0 = (float)((wd.x >> (8 * j)) & 0xFFu), d1 = (float)((wd.y >> (8 * j)) & 0xFFu);
+            acc1[mt][j][0] = fmaf(c0, d0, acc1[mt][j][0]);
+            acc1[mt][j][1] = fmaf(c0, d1, acc1[mt][j][1]);
+            acc1[mt][j][2] = fmaf(c1, d0, acc1[mt][j][2]);
+            acc1[mt][j][3] = fmaf(c1, d1, acc1[mt][j][3]);
           }
         }
       }
-      // V[(c, yo)][px] = acc / 2^12 as hi + lo fp16, written with stmatrix:
-      // the accumulator fragment layout is the 8x8-tile register layout.
-      #pragma unroll
-      for (int np2 = 0; np2 < 2; ++np2) {
-        if (!pon[np2]) continue;
-        const int j0 = colw + 16 * np2;
-        const int c = j0 / PXP, px0 = j0 - c * PXP;
+      // V[(c, yo)][px] = acc * 2^12 as hi + lo fp16, de-interleaving the
+      // channels: ring byte 32w + 8t + e8 is slab element e = byte - ph.
+      if (wact) {
         #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-          unsigned int hr[4], lr[4];
+        for (int e8 = 0; e8 < 8; ++e8) {
+          const int e = colw + 8 * t + e8 - sl.ph;
+          if (e < 0 || e >= sl.sws) continue;
+          const int px = e / C, c = e - px * C;
           #pragma unroll
-          for (int q4 = 0; q4 < 4; ++q4) {
-            const int nt = 2 * np2 + (q4 >> 1), ii = (q4 & 1) * 2;
-            const float v0 = acc1[mt][nt][ii] * kWInv, v1 = acc1[mt][nt][ii + 1] * kWInv;
-            hr[q4] = pack_f2h2(v0, v1);
-            const float2 hf = __half22float2(*reinterpret_cast<const __half2*>(&hr[q4]));
-            lr[q4] = pack_f2h2(v0 - hf.x, v1 - hf.y);
+          for (int mt = 0; mt < 2; ++mt) {
+            #pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+              const float v = acc1[mt][e8 & 3][2 * hh + (e8 >> 2)] * kVScale;
+              const __half h = __float2half_rn(v);
+              const __half l = __float2half_rn(v - __half2float(h));
+              const size_t o = (size_t)(c * 32 + 16 * mt + g + 8 * hh) * VP + px;
+              Vh[o] = h;
+              Vl[o] = l;
+            }
           }
-          const int vrow = c * 32 + 16 * mt + (lane & 7) + ((lane >> 3) & 1) * 8;
-          const int vcol = px0 + ((lane >> 4) & 1) * 8;
-          stsm_x4(Vh + (size_t)vrow * VP + vcol, hr[0], hr[1], hr[2], hr[3]);
-          stsm_x4(Vl + (size_t)vrow * VP + vcol, lr[0], lr[1], lr[2], lr[3]);
         }
+      }
+      // zero the columns px in [npx, npx16) that pass 2 reads
+      const int zc = npx16 - npx;
+      for (int idx = tid; idx < C * 32 * zc; idx += kThreads) {
+        const int row = idx / zc, px = npx + (idx - row * zc);
+        Vh[(size_t)row * VP + px] = __ushort_as_half(0);
+        Vl[(size_t)row * VP + px] = __ushort_as_half(0);
       }
     }
     __syncthreads();
@@ -443,9 +367,9 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
     }
   }
   cp_async_wait<0>();
-  __syncthreads();  // ring and Th no longer read; Th becomes the output stage
+  __syncthreads();  // the ring is no longer read: it becomes the output stage
 
-  unsigned char* ost = reinterpret_cast<unsigned char*>(Th);
+  unsigned char* ost = ring;
   constexpr int opitch = 32 * C;
   #pragma unroll
   for (int i = 0; i < C; ++i) {
@@ -462,9 +386,18 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
   __syncthreads();
   const int rowBytes = it.bw * C;
   unsigned char* out = it.out + (size_t)it.y0 * it.pitch + (size_t)it.x0 * C;
-  for (int idx = tid; idx < it.bh * rowBytes; idx += kThreads) {
-    const int yo = idx / rowBytes, rem = idx - yo * rowBytes;
-    out[(size_t)yo * it.pitch + rem] = ost[yo * opitch + rem];
+  if (((((size_t)out) | it.pitch | (size_t)rowBytes) & 15) == 0) {
+    const int nv = rowBytes >> 4;  // 16-byte pieces per row
+    for (int idx = tid; idx < it.bh * nv; idx += kThreads) {
+      const int yo = idx / nv, v = idx - yo * nv;
+      *reinterpret_cast<uint4*>(out + (size_t)yo * it.pitch + 16 * v) =
+          *reinterpret_cast<const uint4*>(ost + yo * opitch + 16 * v);
+    }
+  } else {
+    for (int idx = tid; idx < it.bh * rowBytes; idx += kThreads) {
+      const int yo = idx / rowBytes, rem = idx - yo * rowBytes;
+      out[(size_t)yo * it.pitch + rem] = ost[yo * opitch + rem];
+    }
   }
 }
 
@@ -474,7 +407,6 @@ tc_forward_kernel(FrameSource src, Workspace ws, int rmax, BucketList bl) {
   extern __shared__ __align__(16) unsigned char smem[];
   const TcLayout L = tc_layout(RB, rmax);
   unsigned char* ring = smem + L.ring;
-  __half* Th = reinterpret_cast<__half*>(smem + L.th);
   __half* Vh = reinterpret_cast<__half*>(smem + L.vh);
   __half* Vl = reinterpret_cast<__half*>(smem + L.vl);
   float2* U = reinterpret_cast<float2*>(smem + L.taps);
@@ -495,10 +427,15 @@ tc_forward_kernel(FrameSource src, Workspace ws, int rmax, BucketList bl) {
   const int n_items = own_order ? (int)src.one_total : (int)ws.counters[CNT_NITEMS];
   if (own_order) bucket_starts(ws.counters + CNT_HIST, bl.nb, s_start, s_wsum);
 
+  // Thread 0 holds the ticket of the item after the current one, so the
+  // ticket counter's round trip overlaps the current item.
+  int next_tk = 0;
+  if (tid == 0) next_tk = (int)atomicAdd(&ws.counters[CNT_TICKET], 1u);
   for (;;) {
     __syncthreads();  // the previous item is finished by every thread
     if (tid == 0) {
-      const int tk = (int)atomicAdd(&ws.counters[CNT_TICKET], 1u);
+      const int tk = next_tk;
+      if (tk < n_items) next_tk = (int)atomicAdd(&ws.counters[CNT_TICKET], 1u);
       int state = 0;
       if (tk >= n_items) {
         state = 2;
@@ -534,7 +471,7 @@ tc_forward_kernel(FrameSource src, Workspace ws, int rmax, BucketList bl) {
     __syncthreads();
     if (s_state == 2) break;
     if (s_state == 1) continue;
-    tc_item<RB, C>(s_it, s_c, ring, Th, Vh, Vl, U, CU, P, red, np);
+    tc_item<RB, C>(s_it, s_c, ring, Vh, Vl, U, CU, P, red, np);
   }
   cp_async_wait<0>();
   if (own_order) {
