@@ -1,4 +1,6 @@
 // C ABI of libfovea: contexts, argument checks, workspace, launches, graphs.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -224,7 +226,11 @@ int upload_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint,
   if (item0 > (1ll << 31) - 1) return FOVEA_EUNSUPPORTED;
   int st = ensure_workspace(ctx, item0);
   if (st != FOVEA_OK) return st;
-  const size_t bytes = sizeof(BatchHeader) + (size_t)n * sizeof(FrameDesc);
+  // tensor maps of the uint8 frames for the tensor-core kernel's row loads
+  const size_t maps_off = (sizeof(BatchHeader) + (size_t)n * sizeof(FrameDesc) + kTensorMapAlign - 1) &
+                          ~(kTensorMapAlign - 1);
+  const size_t bytes = maps_off + (size_t)n * kTensorMapBytes;
+  if (maps_off > (size_t)0x7fffffff) return FOVEA_EUNSUPPORTED;
   if (bytes > ctx->batch_dev_cap) {
     if (ctx->batch_dev) {
       FOVEA_CUDA(cudaDeviceSynchronize());
@@ -255,9 +261,16 @@ int upload_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint,
   FOVEA_CUDA(cudaEventSynchronize(ctx->batch_ev[slot]));  // copy from this slot finished
   BatchHeader hdr;
   hdr.nframes = n;
-  hdr.pad = 0;
+  hdr.maps_offset = (int)maps_off;
   hdr.total_items = item0;
   char* hbuf = static_cast<char*>(ctx->batch_host[slot]);
+  for (int i = 0; i < n; ++i) {
+    FrameDesc& d = descs[(size_t)i];
+    void* map = hbuf + maps_off + (size_t)i * kTensorMapBytes;
+    d.tma = (!adjoint && d.fmt == FOVEA_U8_HWC &&
+             make_u8_tensor_map(map, d.in, d.W, d.H, d.C, ctx->cfg.rows_per_chunk)) ? 1 : 0;
+    if (!d.tma) std::memset(map, 0, kTensorMapBytes);
+  }
   std::memcpy(hbuf, &hdr, sizeof(hdr));
   std::memcpy(hbuf + sizeof(hdr), descs.data(), (size_t)n * sizeof(FrameDesc));
   FOVEA_CUDA(cudaMemcpyAsync(ctx->batch_dev, hbuf, bytes, cudaMemcpyHostToDevice, s));
@@ -300,7 +313,7 @@ int enqueue_batch_kernels(fovea_ctx* ctx, bool adjoint, int rbound, int fmt_mask
     int grid = forward_grid(ctx, rbound, fmt_mask, tc_c);
     if (grid <= 0) return FOVEA_EUNSUPPORTED;
     e = use_tc(ctx, fmt_mask, tc_c)
-            ? launch_tc_forward(src, ctx->ws, ctx->cfg, rbound, tc_c, grid, s, BucketList{nullptr, 0, 0}, false)
+            ? launch_tc_forward(src, ctx->ws, ctx->cfg, rbound, tc_c, grid, s, BucketList{nullptr, 0, 0}, false, nullptr)
             : launch_forward(src, ctx->ws, ctx->cfg, rbound, fmt_mask, grid, s);
   }
   if (e != cudaSuccess) return cuda_fail(e);
@@ -421,8 +434,13 @@ int fovea_render(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x,
   // Programmatic dependent launch lets the blur kernel's prologue overlap the
   // sigma kernel (not when its launch is bracketed by timing events).
   const bool pdl = bl.list && !ctx->kev_start;
-  e = use_tc(ctx, fmt_mask, tc_c) ? launch_tc_forward(src, ctx->ws, ctx->cfg, rmax, tc_c, grid, s, bl, pdl)
-                                  : launch_forward(src, ctx->ws, ctx->cfg, rmax, fmt_mask, grid, s, bl, pdl);
+  if (use_tc(ctx, fmt_mask, tc_c)) {
+    alignas(64) unsigned char map[kTensorMapBytes];
+    src.one.tma = make_u8_tensor_map(map, src.one.in, src.one.W, src.one.H, src.one.C, ctx->cfg.rows_per_chunk) ? 1 : 0;
+    e = launch_tc_forward(src, ctx->ws, ctx->cfg, rmax, tc_c, grid, s, bl, pdl, map);
+  } else {
+    e = launch_forward(src, ctx->ws, ctx->cfg, rmax, fmt_mask, grid, s, bl, pdl);
+  }
   if (e != cudaSuccess) return cuda_fail(e);
   if (ctx->kev_stop) FOVEA_CUDA(cudaEventRecord(ctx->kev_stop, s));
   return FOVEA_OK;
@@ -587,5 +605,34 @@ int ctx_device_info(const fovea_ctx* ctx, int* device, int* num_sms) {
 }
 
 int record_cuda_failure(int cuda_error) { return cuda_fail((cudaError_t)cuda_error); }
+
+bool make_u8_tensor_map(void* map, const void* base, int W, int H, int C, int rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static std::once_flag once;
+  std::memset(map, 0, kTensorMapBytes);
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    cudaGetLastError();
+  });
+  const unsigned long long pitch = (unsigned long long)W * (unsigned long long)C;
+  if (!encode || !base || ((uintptr_t)base & 15) || (pitch & 15) || W <= 0 || H <= 0 || rows <= 0 || rows > 256)
+    return false;
+  const cuuint64_t dims[2] = {pitch, (cuuint64_t)H};
+  const cuuint64_t strides[1] = {pitch};
+  const cuuint32_t box[2] = {128, (cuuint32_t)rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(static_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base),
+                            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    std::memset(map, 0, kTensorMapBytes);
+    return false;
+  }
+  return true;
+}
 
 }  // namespace fovea

@@ -15,6 +15,15 @@ int check_frame(int W, int H, int C, int fmt, int B, double sigma0, double k, fl
 size_t frame_bytes(int W, int H, int C, int fmt);
 int ctx_shape(const fovea_ctx* ctx, int* W, int* H, int* C, int* fmt, int* B);
 int ctx_device_info(const fovea_ctx* ctx, int* device, int* num_sms);
+// Bytes of one tensor map (CUtensorMap) and the alignment it needs.
+constexpr size_t kTensorMapBytes = 128;
+constexpr size_t kTensorMapAlign = 64;
+// Encodes the tensor map the tensor-core kernel loads a uint8 HWC frame's
+// rows with (2D: W*C bytes x H rows, boxes of 128 bytes x `rows`, 128-byte
+// swizzle, zero fill outside the frame) into map (kTensorMapBytes, aligned to
+// kTensorMapAlign). Returns false, leaving map zeroed, when the frame's base
+// address or row pitch is not a multiple of 16 bytes or the driver refuses.
+bool make_u8_tensor_map(void* map, const void* base, int W, int H, int C, int rows);
 // Records a failed cudaError_t for fovea_last_cuda_error and returns the
 // status it maps to (FOVEA_ENOMEM for an allocation failure, else FOVEA_ECUDA).
 int record_cuda_failure(int cuda_error);

@@ -25,16 +25,18 @@ struct FrameDesc {
   const void* in;
   void* out;
   int W, H, C, fmt;        // fmt: FOVEA_U8_HWC or FOVEA_F32_CHW
-  int nbx, nby, B, pad0;   // block grid and block side
+  int nbx, nby, B, tma;    // block grid and block side; tma: a tensor map is provided (uint8 HWC)
   float fx, fy;            // fixation (pixels)
   double sigma0, k;        // sigma law
   long long item0;         // index of the frame's first item in a batch
 };
 
-// Device-resident batch: header followed by the frame descriptors.
+// Device-resident batch: header followed by the frame descriptors, then
+// (at maps_offset bytes from the header, 64-byte aligned) one 128-byte
+// tensor map per frame, valid for the frames whose tma flag is set.
 struct BatchHeader {
   int nframes;
-  int pad;
+  int maps_offset;
   long long total_items;
 };
 
@@ -276,8 +278,11 @@ int forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int fmt_mask);
 // Tensor-core variant (uint8 HWC frames, all with C channels).
 size_t tc_forward_smem_bytes(const FwdConfig& cfg, int rmax);
 int tc_forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int C);
+// tmap_one: tensor map (128-byte CUtensorMap) of a single frame, read when
+// src.one.tma is set; a batch's maps sit in its device buffer (see
+// BatchHeader::maps_offset).
 cudaError_t launch_tc_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg, int rmax, int C,
-                              int grid, cudaStream_t s, const BucketList& bl, bool pdl);
+                              int grid, cudaStream_t s, const BucketList& bl, bool pdl, const void* tmap_one);
 size_t adjoint_smem_bytes(int rmax);
 cudaError_t launch_adjoint(const FrameSource& src, const Workspace& ws, int rmax, int grid,
                            cudaStream_t s);

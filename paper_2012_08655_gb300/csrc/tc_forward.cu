@@ -18,9 +18,15 @@
 // turn two staged rows into the fragment registers of four n-tiles and no
 // converted copy of the tile is ever written. The taps of the folded edge
 // rows / columns (clamp-to-edge, see forward.cu) are added as fp32 rank-one
-// corrections. Slabs, row staging and the work list are shared with the fp32
+// corrections. The staged rows arrive by TMA: one thread issues, per row
+// chunk, two 128-byte-wide tensor-map boxes (128-byte swizzle, so the
+// fragment loads are free of bank conflicts) that complete on the stage's
+// mbarrier. Slabs, item geometry and the work list are shared with the fp32
 // kernel (fwd_common.cuh).
+#include <cuda.h>
 #include <cuda_fp16.h>
+
+#include <cstring>
 
 #include "fwd_common.cuh"
 
@@ -34,39 +40,90 @@ constexpr float kWScale = 4096.0f;          // taps scaled by 2^12
 constexpr float kWInv = 1.0f / 4096.0f;
 constexpr float kDScale = 1.0f / 16777216.0f;  // a staged byte b enters pass 1 as b * 2^-24
 constexpr float kVScale = 4096.0f;          // V = pass-1 accumulator * 2^12 (= 2^24 / 2^12)
-constexpr int kRingPitch = 272;             // bytes per staged row: 68 words, rows 2 apart 8 banks apart
+constexpr int kRingRow = 256;               // bytes per staged row: two 128-byte swizzled boxes
 constexpr int kPairPad = 32;                // tap index -kPairPad is pair entry 0
 constexpr int kVHalves = 128 * 72;     // halves of one V array (max over C of 32C rows x VP)
 
 __host__ __device__ inline int npair(int rmax) { return rmax + 56; }
 
-// Raw uint8 chunks staged or in flight: one load in flight while a chunk is
-// converted and another multiplied, two for the short 16-row chunks.
-__host__ __device__ constexpr int tc_stages(int rb) { return rb >= 32 ? 3 : 4; }
+// Raw uint8 row chunks staged or in flight: about 160 rows (at least three
+// chunks), so that a chunk's load has several chunks' worth of work to hide
+// behind.
+__host__ __device__ constexpr int tc_stages(int rb) { return 160 / rb > 3 ? 160 / rb : 3; }
+constexpr int kMaxTcStages = 10;
 
 struct TcLayout {
-  size_t ring, vh, vl, taps, cum, pairs, red, total;
+  size_t ring, vh, vl, cum, pairs, total;
 };
 
-// The normalised taps are needed only while the cumulative and tap-pair
-// tables are built, before the first V is written: they live in the V arrays.
+// Offsets from the 1024-byte aligned start of the dynamic shared memory (the
+// 128-byte swizzle pattern repeats every 1024 bytes).
 __host__ __device__ inline TcLayout tc_layout(int rb, int rmax) {
   TcLayout L;
-  L.ring = 0;                                                  // u8 [stages][rb][kRingPitch]
-  L.vh = L.ring + (size_t)tc_stages(rb) * rb * kRingPitch;     // half [kVHalves]
+  L.ring = 0;                                                  // u8 [stages][2][rb][128] (swizzled)
+  L.vh = L.ring + (size_t)tc_stages(rb) * rb * kRingRow;       // half [kVHalves]
   L.vl = L.vh + (size_t)kVHalves * 2;                          // half [kVHalves]
-  size_t end = L.vl + (size_t)kVHalves * 2;
-  if ((size_t)tap_len(rmax) * sizeof(float2) <= (size_t)2 * kVHalves * 2) {
-    L.taps = L.vh;                                             // float2 [tap_len], aliases V
-  } else {
-    L.taps = end;
-    end += (size_t)tap_len(rmax) * sizeof(float2);
-  }
-  L.cum = end;                                                 // float [cum_len]
+  L.cum = L.vl + (size_t)kVHalves * 2;                         // float [cum_len]
   L.pairs = L.cum + (size_t)((cum_len(rmax) + 3) & ~3) * 4;    // uint32 [4][npair]
-  L.red = L.pairs + (size_t)4 * npair(rmax) * 4;               // float [32]
-  L.total = L.red + 32 * sizeof(float);
+  L.total = L.pairs + (size_t)4 * npair(rmax) * 4 + 1024;      // + alignment slack
   return L;
+}
+
+// Byte b (0..255) of staged row rho of a ring stage: box b / 128, 128-byte
+// rows, 16-byte chunk index XOR (rho mod 8).
+template <int RB>
+__device__ __forceinline__ int ring_off(int rho, int b) {
+  return (((b >> 7) * RB + rho) << 7) + ((((b >> 4) & 7) ^ (rho & 7)) << 4) + (b & 15);
+}
+
+__device__ __forceinline__ unsigned int smem_u32(const void* p) {
+  return (unsigned int)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned int bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned int parity) {
+  unsigned int ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for the given phase parity of an mbarrier, at most kWaitLimit polls
+// (each poll may suspend for a short, hardware-chosen time). False: gave up.
+constexpr int kWaitLimit = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int parity) {
+  for (int i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// One 2D tensor-map box into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int x, int y, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+      ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// A tensor map in global memory is rewritten (by a host copy) between
+// launches: order those generic writes before its use by the tensor-map
+// proxy, which may otherwise hold the previous contents.
+__device__ __forceinline__ void fence_tensormap_acquire(const void* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(map) : "memory");
 }
 
 __device__ __forceinline__ unsigned int pack_half2(__half a, __half b) {
@@ -95,10 +152,31 @@ __device__ __forceinline__ void ldsm_x4(unsigned int (&r)[4], const void* p) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(s));
 }
 
+// Unnormalised tap of offset d: exp(c d^2) (c = -1 / (2 sigma^2)), 1 at d = 0.
+__device__ __forceinline__ float tap_w(int d, float c) { return d == 0 ? 1.0f : expf(c * (float)(d * d)); }
+
+// Sum S of the unnormalised taps over |d| <= r, computed by every warp on
+// its own in one fixed order (lane-strided partial sums, then a butterfly,
+// which leaves the same value in every lane), so every warp holds the same S
+// without a block-wide barrier.
+__device__ __forceinline__ float warp_tap_sum(int r, float c) {
+  const int lane = threadIdx.x & 31;
+  float s = 0.0f;
+  for (int d = -r + lane; d <= r; d += 32) s += tap_w(d, c);
+  #pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// Normalised tap of index m (offset m - r), zero outside [0, 2r].
+__device__ __forceinline__ float tap_u(int m, int r, float c, float S) {
+  return (m >= 0 && m <= 2 * r) ? tap_w(m - r, c) / S : 0.0f;
+}
+
 // Tap-pair tables: entry j of the even table holds (w(m), w(m+1)) with
 // m = 2j - kPairPad, the odd table the pair starting one tap later; hi and lo
-// parts of the scaled taps. w is zero outside [0, 2r].
-__device__ __forceinline__ void make_pairs(const float2* U, unsigned int* P, int r, int np) {
+// parts of the scaled taps w = u * 2^12.
+__device__ __forceinline__ void make_pairs(unsigned int* P, int r, float c, float S, int np) {
   unsigned int* PEh = P;
   unsigned int* POh = P + np;
   unsigned int* PEl = P + 2 * np;
@@ -107,8 +185,7 @@ __device__ __forceinline__ void make_pairs(const float2* U, unsigned int* P, int
     __half h[3], l[3];
     #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      const int m = 2 * j - kPairPad + q;
-      const float w = (m >= 0 && m <= 2 * r) ? U[kTapPad + m].x * kWScale : 0.0f;
+      const float w = tap_u(2 * j - kPairPad + q, r, c, S) * kWScale;
       h[q] = __float2half_rn(w);
       l[q] = __float2half_rn(w - __half2float(h[q]));
     }
@@ -119,30 +196,91 @@ __device__ __forceinline__ void make_pairs(const float2* U, unsigned int* P, int
   }
 }
 
+// Exclusive prefix sums of the normalised taps, CU[m] = sum_{m' < m} u(m')
+// for m in [0, 2r+1] (used to fold clamped taps onto edge rows/columns, as
+// in the fp32 kernel). One warp: contiguous lane segments, then a scan.
+__device__ __forceinline__ void make_cumulative_tc(float* CU, int r, float c, float S) {
+  const int lane = threadIdx.x & 31;
+  const int n = 2 * r + 1;
+  const int seg = (n + 31) >> 5;
+  const int b = lane * seg, e = min(n, b + seg);
+  float sum = 0.0f;
+  for (int m = b; m < e; ++m) sum += tap_u(m, r, c, S);
+  float incl = sum;
+  #pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  float run = incl - sum;
+  for (int m = b; m < e; ++m) {
+    CU[m] = run;
+    run += tap_u(m, r, c, S);
+  }
+  if (lane == 31) CU[n] = incl;
+}
 
 // Everything the tensor-core kernel does for one item with C channels.
-template <int RB, int C>
-__device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned char* ring, __half* Vh, __half* Vl,
-                                        float2* U, float* CU, unsigned int* P, float* red, int np) {
+// Returns false if a staged chunk never arrived (the item is abandoned and
+// an error flag set; the caller stops). lookahead(step) is called by thread
+// 0 at two points of the item (step 0 once the tables are built, step 1 once
+// the first chunk has arrived) to fetch the next item's record in the
+// background.
+template <int RB, int C, typename LookAhead>
+__device__ __forceinline__ bool tc_item(const Item& it, float c_tap, unsigned char* ring, __half* Vh, __half* Vl,
+                                        float* CU, unsigned int* P, int np,
+                                        unsigned long long* bars, const void* map, bool map_in_global,
+                                        int& gq0, unsigned int* err, LookAhead&& lookahead) {
   constexpr int VP = TcGeo<C>::VP;
-  constexpr size_t stage_bytes = (size_t)RB * kRingPitch;
+  constexpr size_t stage_bytes = (size_t)RB * kRingRow;
   constexpr int kStagesTc = tc_stages(RB);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int r = it.r;
   const int Q = it.nsl * it.nchunks;
-  const size_t frame_bytes = (size_t)it.H * it.pitch;
 
-  // Raw uint8 chunks (slab s, rows k*RB ..) stream through the ring stages.
-  #pragma unroll
-  for (int q = 0; q < kStagesTc - 1; ++q) {
-    if (q < Q) stage_rows<true, RB, kRingPitch>(it, slab_of<true>(it, q / it.nchunks), q % it.nchunks,
-                                                ring + (size_t)q * stage_bytes, frame_bytes);
-    cp_async_commit();
+  // Raw uint8 chunks (slab s, rows k*RB ..) stream through the ring stages:
+  // global chunk number gq0 + q uses stage (gq0 + q) % stages, and its
+  // mbarrier completes for the ((gq0 + q) / stages)-th time.
+  auto issue = [&](int qq) {  // one thread: the chunk's two TMA boxes
+    const Slab cs = slab_of<true>(it, qq / it.nchunks);
+    const int gq = gq0 + qq, stg = gq % kStagesTc;
+    unsigned char* dst = ring + (size_t)stg * stage_bytes;
+    const int x = (int)cs.src - cs.ph;  // 16-byte aligned byte column
+    const int y = it.gy0 - it.ph + (qq % it.nchunks) * RB;
+    mbar_expect_tx(bars + stg, 2u * 128u * RB);
+    tma_load_2d(dst, map, x, y, bars + stg);
+    tma_load_2d(dst + 128 * RB, map, x + 128, y, bars + stg);
+  };
+  auto load_plain = [&](int qq) {  // all threads: rows that TMA cannot load
+    const Slab cs = slab_of<true>(it, qq / it.nchunks);
+    unsigned char* dst = ring + (size_t)((gq0 + qq) % kStagesTc) * stage_bytes;
+    const long long x0 = (long long)cs.src - cs.ph;
+    const int nb = min(256, (cs.ph + cs.sws + 31) & ~31);
+    const int y0 = it.gy0 - it.ph + (qq % it.nchunks) * RB;
+    for (int idx = threadIdx.x; idx < RB * nb; idx += kThreads) {
+      const int rho = idx / nb, b = idx - rho * nb;
+      const int y = y0 + rho;
+      const long long xb = x0 + b;
+      unsigned char v = 0;
+      if (y >= 0 && y < it.H && xb < (long long)it.pitch) v = it.in[(size_t)y * it.pitch + (size_t)xb];
+      dst[ring_off<RB>(rho, b)] = v;
+    }
+  };
+  if (map && tid == 0) {
+    if (map_in_global) fence_tensormap_acquire(map);
+    fence_proxy_async();
+    for (int q = 0; q < kStagesTc - 1 && q < Q; ++q) issue(q);
   }
-  make_taps(U, tap_len(r), r, c_tap, red);
-  make_cumulative(U, CU, r);
-  make_pairs(U, P, r, np);
+  // Tables of the item (no block barrier: the first chunk's barrier below
+  // publishes them).
+  {
+    const float S = warp_tap_sum(r, c_tap);
+    make_pairs(P, r, c_tap, S, np);
+    if ((it.foldT || it.foldB || it.foldL || it.foldR) && warp == kThreads / 32 - 1)
+      make_cumulative_tc(CU, r, c_tap, S);
+  }
+  if (tid == 0) lookahead(0);
 
   // Pass 1: each lane reads the tap-pair table of its parity (the tap index
   // of every A register of this lane has the parity of g, D0 being even).
@@ -162,19 +300,36 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
     #pragma unroll
     for (int k = 0; k < 4; ++k) acc2[i][k] = 0.f;
 
-  for (int q = 0; q < Q; ++q) {
-    cp_async_wait<kStagesTc - 2>();
-    __syncthreads();  // chunk q landed for every thread; iteration q-1 finished everywhere
-    {
-      const int qn = q + kStagesTc - 1;
-      if (qn < Q) stage_rows<true, RB, kRingPitch>(it, slab_of<true>(it, qn / it.nchunks), qn % it.nchunks,
-                                                   ring + (size_t)(qn % kStagesTc) * stage_bytes, frame_bytes);
-      cp_async_commit();
+  // this lane's pass-1 data word: byte colw + 4g of rows 2t, 2t+1 (+8) of a
+  // k-step (row mod 8 is 2t or 2t+1, so the swizzled column is fixed)
+  const int bcol = colw + 4 * g;
+  const int dbox = (bcol >> 7) * RB;
+  const int doffA = ((((bcol >> 4) & 7) ^ (2 * t)) << 4) + (bcol & 15);
+  const int doffB = ((((bcol >> 4) & 7) ^ (2 * t + 1)) << 4) + (bcol & 15);
+
+  int q = 0;
+  bool ok = true;
+  for (; q < Q; ++q) {
+    if (map) {
+      const int gq = gq0 + q;
+      bool got = mbar_wait(bars + gq % kStagesTc, (unsigned int)(gq / kStagesTc) & 1u);
+      // chunk q visible to every thread; iteration q-1 finished everywhere
+      got = __syncthreads_and(got) != 0;
+      if (!got) {
+        ok = false;
+        break;
+      }
+      if (tid == 0 && q + kStagesTc - 1 < Q) issue(q + kStagesTc - 1);
+    } else {
+      __syncthreads();  // iteration q-1 finished everywhere
+      load_plain(q);
+      __syncthreads();
     }
+    if (q == 0 && tid == 0) lookahead(1);
     const int s = q / it.nchunks, k = q - s * it.nchunks;
     const Slab sl = slab_of<true>(it, s);
     const int R0 = k * RB;
-    const unsigned char* st = ring + (size_t)(q % kStagesTc) * stage_bytes;
+    const unsigned char* st = ring + (size_t)((gq0 + q) % kStagesTc) * stage_bytes;
     const bool wact = colw < sl.ph + sl.sws && colw + 32 > sl.ph;  // warp holds slab bytes
     if (k == 0) {
       #pragma unroll
@@ -184,7 +339,7 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
           #pragma unroll
           for (int i = 0; i < 4; ++i) acc1[mt][nt][i] = 0.f;
       if (it.foldT && wact) {  // folded top row first: fixed summation order
-        const uint2 wd = *reinterpret_cast<const uint2*>(st + (size_t)it.ph * kRingPitch + colw + 8 * t);
+        const uint2 wd = *reinterpret_cast<const uint2*>(st + ring_off<RB>(it.ph, colw + 8 * t));
         #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
           const float c0 = cum_at(CU, it.offy - (16 * mt + g), r) * (kWScale * kDScale);
@@ -222,11 +377,11 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
         // (byte of row v, byte of row v+1) -> two fp16 subnormals.
         unsigned int b[4][2];
         {
-          const unsigned char* sb = st + (size_t)(k0 - R0 + 2 * t) * kRingPitch + colw + 4 * g;
-          const unsigned int w0 = *reinterpret_cast<const unsigned int*>(sb);
-          const unsigned int w1 = *reinterpret_cast<const unsigned int*>(sb + kRingPitch);
-          const unsigned int w8 = *reinterpret_cast<const unsigned int*>(sb + 8 * kRingPitch);
-          const unsigned int w9 = *reinterpret_cast<const unsigned int*>(sb + 9 * kRingPitch);
+          const unsigned char* sb = st + ((dbox + k0 - R0 + 2 * t) << 7);
+          const unsigned int w0 = *reinterpret_cast<const unsigned int*>(sb + doffA);
+          const unsigned int w1 = *reinterpret_cast<const unsigned int*>(sb + 128 + doffB);
+          const unsigned int w8 = *reinterpret_cast<const unsigned int*>(sb + 8 * 128 + doffA);
+          const unsigned int w9 = *reinterpret_cast<const unsigned int*>(sb + 9 * 128 + doffB);
           const unsigned int lo01 = __byte_perm(w0, w1, 0x5140), lo23 = __byte_perm(w0, w1, 0x7362);
           const unsigned int hi01 = __byte_perm(w8, w9, 0x5140), hi23 = __byte_perm(w8, w9, 0x7362);
           b[0][0] = __byte_perm(lo01, 0u, 0x4140); b[1][0] = __byte_perm(lo01, 0u, 0x4342);
@@ -254,7 +409,7 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
     {
       const int vb = it.ph + it.EH - 1;
       if (it.foldB && vb >= R0 && vb < R0 + RB && wact) {
-        const uint2 wd = *reinterpret_cast<const uint2*>(st + (size_t)(vb - R0) * kRingPitch + colw + 8 * t);
+        const uint2 wd = *reinterpret_cast<const uint2*>(st + ring_off<RB>(vb - R0, colw + 8 * t));
         #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
           const float c0 = cum_at(CU, 2 * r + 1 - (it.offy + it.EH - (16 * mt + g)), r) * (kWScale * kDScale);
@@ -366,7 +521,20 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
       }
     }
   }
-  cp_async_wait<0>();
+  if (!ok) {
+    // a chunk never arrived: flag it, let the chunks still in flight land
+    // (bounded) and give up on the item
+    if (tid == 0) {
+      atomicOr(err, 64u);
+      for (int qq = q; qq < Q && qq < q + kStagesTc - 1; ++qq) {
+        const int gq = gq0 + qq;
+        mbar_wait(bars + gq % kStagesTc, (unsigned int)(gq / kStagesTc) & 1u);
+      }
+    }
+    __syncthreads();
+    return false;
+  }
+  gq0 += Q;
   __syncthreads();  // the ring is no longer read: it becomes the output stage
 
   unsigned char* ost = ring;
@@ -399,63 +567,89 @@ __device__ __forceinline__ void tc_item(const Item& it, float c_tap, unsigned ch
       out[(size_t)yo * it.pitch + rem] = ost[yo * opitch + rem];
     }
   }
+  fence_proxy_async();  // the next item's TMA boxes overwrite the output stage
+  return true;
 }
 
 template <int RB, int C>
 __global__ void __launch_bounds__(kThreads, 2)
-tc_forward_kernel(FrameSource src, Workspace ws, int rmax, BucketList bl) {
-  extern __shared__ __align__(16) unsigned char smem[];
+tc_forward_kernel(const __grid_constant__ FrameSource src, Workspace ws, int rmax, BucketList bl,
+                  const __grid_constant__ CUtensorMap tmap1) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const TcLayout L = tc_layout(RB, rmax);
   unsigned char* ring = smem + L.ring;
   __half* Vh = reinterpret_cast<__half*>(smem + L.vh);
   __half* Vl = reinterpret_cast<__half*>(smem + L.vl);
-  float2* U = reinterpret_cast<float2*>(smem + L.taps);
   float* CU = reinterpret_cast<float*>(smem + L.cum);
   unsigned int* P = reinterpret_cast<unsigned int*>(smem + L.pairs);
-  float* red = reinterpret_cast<float*>(smem + L.red);
+  __shared__ __align__(8) unsigned long long s_bar[kMaxTcStages];
   __shared__ int s_state;
   __shared__ Item s_it;
   __shared__ float s_c;
+  __shared__ const void* s_map;
   __shared__ int s_start[kBuckets];
   __shared__ int s_wsum[kThreads / 32];
 
   const int tid = threadIdx.x;
   const int np = npair(rmax);
+  if (tid == 0) {
+    for (int i = 0; i < kMaxTcStages; ++i) mbar_init(&s_bar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    fence_proxy_async();
+  }
+  int gq0 = 0;  // chunks staged by this CTA so far (identical in every thread)
 
   asm volatile("griddepcontrol.wait;" ::: "memory");
   const bool own_order = bl.list != nullptr;
   const int n_items = own_order ? (int)src.one_total : (int)ws.counters[CNT_NITEMS];
   if (own_order) bucket_starts(ws.counters + CNT_HIST, bl.nb, s_start, s_wsum);
+  const CUtensorMap* batch_maps =
+      src.hdr ? reinterpret_cast<const CUtensorMap*>(reinterpret_cast<const char*>(src.hdr) + src.hdr->maps_offset)
+              : nullptr;
 
-  // Thread 0 holds the ticket of the item after the current one, so the
-  // ticket counter's round trip overlaps the current item.
+  // Thread 0 looks one item ahead: it holds the next item's ticket, and
+  // during the current item it loads the next item's index and record, so
+  // the work list's dependent loads overlap the current item.
   int next_tk = 0;
+  int nx_item = -1;        // next item's index (lookahead step 0)
+  ItemInfo nx_inf;         // next item's record (lookahead step 1)
+  bool nx_have = false;
+  auto lookup = [&](int tk) -> int {
+    if (!own_order) return ws.order[tk];
+    int lo = 0, hi = bl.nb - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (s_start[mid] <= tk) hi = mid; else lo = mid + 1;
+    }
+    return bl.list[(size_t)lo * bl.cap + (tk - s_start[lo])];
+  };
+  auto lookahead = [&](int step) {
+    if (step == 0) {
+      nx_have = false;
+      nx_item = next_tk < n_items ? lookup(next_tk) : -1;
+    } else if ((unsigned)nx_item < (unsigned)n_items) {
+      nx_inf = ws.items[nx_item];
+      nx_have = true;
+    }
+  };
   if (tid == 0) next_tk = (int)atomicAdd(&ws.counters[CNT_TICKET], 1u);
   for (;;) {
     __syncthreads();  // the previous item is finished by every thread
     if (tid == 0) {
       const int tk = next_tk;
-      if (tk < n_items) next_tk = (int)atomicAdd(&ws.counters[CNT_TICKET], 1u);
       int state = 0;
       if (tk >= n_items) {
         state = 2;
       } else {
-        int item;
-        if (own_order) {
-          int lo = 0, hi = bl.nb - 1;
-          while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (s_start[mid] <= tk) hi = mid; else lo = mid + 1;
-          }
-          item = bl.list[(size_t)lo * bl.cap + (tk - s_start[lo])];
-        } else {
-          item = ws.order[tk];
-        }
+        next_tk = (int)atomicAdd(&ws.counters[CNT_TICKET], 1u);
+        const int item = nx_have ? nx_item : lookup(tk);
         if ((unsigned)item >= (unsigned)n_items) {
           atomicOr(&ws.counters[CNT_ERROR], 16u);
           state = 1;
         } else {
-          const ItemInfo inf = ws.items[item];
+          const ItemInfo inf = nx_have ? nx_inf : ws.items[item];
           const FrameDesc fd = load_frame(src, inf.frame);
           if (inf.r > rmax || fd.fmt != FOVEA_U8_HWC || fd.C != C) {
             atomicOr(&ws.counters[CNT_ERROR], 2u);
@@ -463,17 +657,21 @@ tc_forward_kernel(FrameSource src, Workspace ws, int rmax, BucketList bl) {
           } else {
             item_geometry(s_it, inf, fd, RB);
             s_c = inf.neg_half_inv_s2;
+            s_map = !fd.tma ? nullptr : (batch_maps ? static_cast<const void*>(batch_maps + inf.frame)
+                                                    : static_cast<const void*>(&tmap1));
           }
         }
       }
+      nx_have = false;
       s_state = state;
     }
     __syncthreads();
     if (s_state == 2) break;
     if (s_state == 1) continue;
-    tc_item<RB, C>(s_it, s_c, ring, Vh, Vl, U, CU, P, red, np);
+    if (!tc_item<RB, C>(s_it, s_c, ring, Vh, Vl, CU, P, np, s_bar, s_map, batch_maps != nullptr, gq0,
+                        ws.counters + CNT_ERROR, lookahead))
+      break;  // staging failed (flag set): stop taking items
   }
-  cp_async_wait<0>();
   if (own_order) {
     __threadfence();
     __syncthreads();
@@ -530,13 +728,16 @@ int tc_forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int C) {
 }
 
 cudaError_t launch_tc_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg, int rmax, int C,
-                              int grid, cudaStream_t s, const BucketList& bl, bool pdl) {
+                              int grid, cudaStream_t s, const BucketList& bl, bool pdl, const void* tmap_one) {
   const size_t smem = tc_forward_smem_bytes(cfg, rmax);
   void* k = pick_tc(cfg.rows_per_chunk, C);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   BucketList b = bl;
-  void* args[] = {const_cast<FrameSource*>(&src), const_cast<Workspace*>(&ws), &rmax, &b};
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  if (tmap_one) std::memcpy(&map, tmap_one, sizeof(map));
+  void* args[] = {const_cast<FrameSource*>(&src), const_cast<Workspace*>(&ws), &rmax, &b, &map};
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(grid);
   lc.blockDim = dim3(kThreads);

@@ -70,6 +70,25 @@ def test_batch_of_mixed_formats_and_channels(fv):
             assert_f32_close(bf.out.cpu().numpy(), oracle.forward(img, 32, fx, fy, s0, k, "chw"))
 
 
+def test_consecutive_batches_with_new_buffers(fv):
+    """Back-to-back batches of the same shape through one batch context, each
+    on freshly allocated frames (the per-frame descriptors, tensor maps
+    included, are rewritten in place between launches): every frame equals
+    its single-frame render."""
+    shapes = [(224, 224), (640, 480), (1280, 720), (224, 224), (1920, 1080)]
+    for rnd in range(4):
+        ins = [torch.from_numpy(wl.grating_frame(h, w, 3, seed=100 * rnd + i)).cuda()
+               for i, (w, h) in enumerate(shapes)]
+        outs = [torch.empty_like(x) for x in ins]
+        fix = [(0.25 * w + 17.0 * rnd, 0.6 * h) for (w, h) in shapes]
+        fv.foveate_batch([fv.BatchFrame(ins[i], outs[i], fix[i][0], fix[i][1], 0.5, 0.03) for i in range(len(ins))])
+        torch.cuda.synchronize()
+        for i in range(len(ins)):
+            single = fv.foveate(ins[i], fix[i][0], fix[i][1], 0.5, 0.03)
+            torch.cuda.synchronize()
+            assert torch.equal(single, outs[i]), f"round {rnd} frame {i}: batch differs from single-frame render"
+
+
 # ---------------------------------------------------------------- differentiable form
 
 def test_train_batch_forward_backward_vs_oracle(fv):
