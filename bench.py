@@ -53,7 +53,10 @@ KERNELS = {
     0: ("forward_kernel (fp32 FMA)", os.path.join(ROOT, "profiles", "forward_kernel_1080p_u8.txt"),
         ("forward.cu", "fwd_common.cuh", "fovea_internal.cuh")),
     1: ("tc_forward_kernel (tensor cores, mma.sync)", os.path.join(ROOT, "profiles", "tc_forward_kernel_1080p_u8.txt"),
-        ("tc_forward.cu", "fwd_common.cuh", "fovea_internal.cuh")),
+        ("tc_forward.cu", "tc_common.cuh", "fwd_common.cuh", "fovea_internal.cuh")),
+    2: ("umma_forward_kernel (vertical pass tcgen05 + TMEM, horizontal pass mma.sync)",
+        os.path.join(ROOT, "profiles", "umma_forward_kernel_1080p_u8.txt"),
+        ("umma_forward.cu", "tc_common.cuh", "fwd_common.cuh", "fovea_internal.cuh")),
 }
 
 
@@ -67,8 +70,9 @@ def parse_args():
     p.add_argument("--served-seconds", type=float, default=10.0)
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiling runs)")
-    p.add_argument("--tensor-cores", type=int, choices=[0, 1], default=None,
-                   help="force the forward kernel (0: fp32 FMA, 1: tensor cores) instead of autotuning")
+    p.add_argument("--tensor-cores", type=int, choices=[0, 1, 2], default=None,
+                   help="force the forward kernel (0: fp32 FMA, 1: mma.sync, 2: tcgen05 vertical pass) "
+                        "instead of autotuning")
     p.add_argument("--rows-per-chunk", type=int, choices=[16, 32, 64], default=32,
                    help="row chunk of the forced kernel (with --tensor-cores)")
     return p.parse_args()

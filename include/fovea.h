@@ -152,8 +152,11 @@ typedef struct {
   int threads;        /* threads per CTA of the forward kernel: 256 */
   int ctas_per_sm;    /* persistent CTAs per SM (0 = as many as fit) */
   int rows_per_chunk; /* tile rows staged per chunk: 16, 32 or 64 */
-  int tensor_cores;   /* 1: uint8 frames on the tensor-core kernel (fp16 hi/lo split
-                         operands, fp32 accumulation); 0: fp32 FMA kernel */
+  int tensor_cores;   /* uint8 frames on the tensor cores (fp16 hi/lo split operands,
+                         fp32 accumulation): 1 both passes on mma.sync; 2 the
+                         vertical pass on tcgen05 with its accumulator in tensor
+                         memory (radius bound <= 255 and 16 or 32 rows per chunk,
+                         else as 1); 0: fp32 FMA kernel */
 } fovea_config;
 
 int fovea_get_config(const fovea_ctx* ctx, fovea_config* cfg);

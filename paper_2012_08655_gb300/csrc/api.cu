@@ -181,13 +181,22 @@ int sigma_grid(long long items, int num_sms) {
   return (int)std::max<long long>(1, std::min<long long>(g, 4ll * num_sms));
 }
 
-// The tensor-core kernel serves launches whose frames are all uint8 with one
-// channel count (tc_c = that count, 0 otherwise).
-bool use_tc(const fovea_ctx* ctx, int fmt_mask, int tc_c) { return ctx->cfg.tc && fmt_mask == 1 && tc_c > 0; }
+// The tensor-core kernels serve launches whose frames are all uint8 with one
+// channel count (tc_c = that count, 0 otherwise). Returns the kernel a
+// launch runs on: 0 the fp32 FMA kernel, 1 the mma.sync kernel, 2 the
+// kernel with pass 1 on tcgen05 (radius bound and row chunk permitting,
+// else the mma.sync kernel).
+int tc_kind(const fovea_ctx* ctx, int fmt_mask, int tc_c, int rmax) {
+  if (!ctx->cfg.tc || fmt_mask != 1 || tc_c <= 0) return 0;
+  if (ctx->cfg.tc == 2 && rmax <= kUmmaMaxRadius && ctx->cfg.rows_per_chunk <= 32) return 2;
+  return 1;
+}
 
 int forward_grid(fovea_ctx* ctx, int rmax, int fmt_mask, int tc_c) {
-  int per = use_tc(ctx, fmt_mask, tc_c) ? tc_forward_max_ctas_per_sm(ctx->cfg, rmax, tc_c)
-                                        : forward_max_ctas_per_sm(ctx->cfg, rmax, fmt_mask);
+  const int kind = tc_kind(ctx, fmt_mask, tc_c, rmax);
+  int per = kind == 2   ? umma_forward_max_ctas_per_sm(ctx->cfg, rmax, tc_c)
+            : kind == 1 ? tc_forward_max_ctas_per_sm(ctx->cfg, rmax, tc_c)
+                        : forward_max_ctas_per_sm(ctx->cfg, rmax, fmt_mask);
   if (per <= 0) return 0;
   if (ctx->cfg.ctas_per_sm > 0) per = std::min(per, ctx->cfg.ctas_per_sm);
   return per * ctx->num_sms;
@@ -312,9 +321,18 @@ int enqueue_batch_kernels(fovea_ctx* ctx, bool adjoint, int rbound, int fmt_mask
   } else {
     int grid = forward_grid(ctx, rbound, fmt_mask, tc_c);
     if (grid <= 0) return FOVEA_EUNSUPPORTED;
-    e = use_tc(ctx, fmt_mask, tc_c)
-            ? launch_tc_forward(src, ctx->ws, ctx->cfg, rbound, tc_c, grid, s, BucketList{nullptr, 0, 0}, false, nullptr)
-            : launch_forward(src, ctx->ws, ctx->cfg, rbound, fmt_mask, grid, s);
+    switch (tc_kind(ctx, fmt_mask, tc_c, rbound)) {
+      case 2:
+        e = launch_umma_forward(src, ctx->ws, ctx->cfg, rbound, tc_c, grid, s, BucketList{nullptr, 0, 0}, false,
+                                nullptr);
+        break;
+      case 1:
+        e = launch_tc_forward(src, ctx->ws, ctx->cfg, rbound, tc_c, grid, s, BucketList{nullptr, 0, 0}, false,
+                              nullptr);
+        break;
+      default:
+        e = launch_forward(src, ctx->ws, ctx->cfg, rbound, fmt_mask, grid, s);
+    }
   }
   if (e != cudaSuccess) return cuda_fail(e);
   return FOVEA_OK;
@@ -434,10 +452,12 @@ int fovea_render(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x,
   // Programmatic dependent launch lets the blur kernel's prologue overlap the
   // sigma kernel (not when its launch is bracketed by timing events).
   const bool pdl = bl.list && !ctx->kev_start;
-  if (use_tc(ctx, fmt_mask, tc_c)) {
+  const int kind = tc_kind(ctx, fmt_mask, tc_c, rmax);
+  if (kind) {
     alignas(64) unsigned char map[kTensorMapBytes];
     src.one.tma = make_u8_tensor_map(map, src.one.in, src.one.W, src.one.H, src.one.C, ctx->cfg.rows_per_chunk) ? 1 : 0;
-    e = launch_tc_forward(src, ctx->ws, ctx->cfg, rmax, tc_c, grid, s, bl, pdl, map);
+    e = kind == 2 ? launch_umma_forward(src, ctx->ws, ctx->cfg, rmax, tc_c, grid, s, bl, pdl, map)
+                  : launch_tc_forward(src, ctx->ws, ctx->cfg, rmax, tc_c, grid, s, bl, pdl, map);
   } else {
     e = launch_forward(src, ctx->ws, ctx->cfg, rmax, fmt_mask, grid, s, bl, pdl);
   }
@@ -536,7 +556,7 @@ int fovea_set_config(fovea_ctx* ctx, const fovea_config* cfg) {
   if (cfg->threads != 256) return FOVEA_EUNSUPPORTED;
   if (cfg->rows_per_chunk != 16 && cfg->rows_per_chunk != 32 && cfg->rows_per_chunk != 64) return FOVEA_EUNSUPPORTED;
   if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 8) return FOVEA_EINVAL;
-  if (cfg->tensor_cores != 0 && cfg->tensor_cores != 1) return FOVEA_EINVAL;
+  if (cfg->tensor_cores < 0 || cfg->tensor_cores > 2) return FOVEA_EINVAL;
   FwdConfig c{cfg->threads, cfg->ctas_per_sm, cfg->rows_per_chunk, cfg->tensor_cores};
   if (ctx->cfg.rows_per_chunk != c.rows_per_chunk || ctx->cfg.ctas_per_sm != c.ctas_per_sm || ctx->cfg.tc != c.tc) {
     for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);

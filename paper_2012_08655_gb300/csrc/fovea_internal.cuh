@@ -283,6 +283,13 @@ int tc_forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int C);
 // BatchHeader::maps_offset).
 cudaError_t launch_tc_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg, int rmax, int C,
                               int grid, cudaStream_t s, const BucketList& bl, bool pdl, const void* tmap_one);
+// Pass 1 on tcgen05 (umma_forward.cu): radius bound up to kUmmaMaxRadius
+// (its tap strips grow with r), row chunks of 16 or 32 rows.
+constexpr int kUmmaMaxRadius = 255;
+size_t umma_forward_smem_bytes(const FwdConfig& cfg, int rmax, int C);
+int umma_forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int C);
+cudaError_t launch_umma_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg, int rmax, int C,
+                                int grid, cudaStream_t s, const BucketList& bl, bool pdl, const void* tmap_one);
 size_t adjoint_smem_bytes(int rmax);
 cudaError_t launch_adjoint(const FrameSource& src, const Workspace& ws, int rmax, int grid,
                            cudaStream_t s);

@@ -1,0 +1,410 @@
+// Pieces shared by the tensor-core forward kernels (tc_forward.cu: both
+// passes on mma.sync; umma_forward.cu: pass 1 on tcgen05 with its
+// accumulator in tensor memory): scaling constants of the fp16 hi/lo split,
+// the TMA row ring (tensor-map boxes, 128-byte swizzle, mbarriers with
+// bounded waits), the per-item tap tables, the mma.sync helpers, and the
+// persistent item loop with its one-item lookahead.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include "fwd_common.cuh"
+
+namespace fovea {
+namespace tcc {
+
+using namespace fwd;
+
+constexpr float kWScale = 4096.0f;          // taps scaled by 2^12
+constexpr float kWInv = 1.0f / 4096.0f;
+constexpr float kDScale = 1.0f / 16777216.0f;  // a staged byte b enters pass 1 as b * 2^-24
+constexpr float kVScale = 4096.0f;          // V = pass-1 accumulator * 2^12 (= 2^24 / 2^12)
+constexpr int kRingRow = 256;               // bytes per staged row: two 128-byte swizzled boxes
+constexpr int kPairPad = 32;                // tap index -kPairPad is pair entry 0
+constexpr int kVHalves = 128 * 72;     // halves of one V array (max over C of 32C rows x VP)
+
+__host__ __device__ inline int npair(int rmax) { return rmax + 56; }
+
+// Raw uint8 row chunks staged or in flight: about 160 rows (at least three
+// chunks), so that a chunk's load has several chunks' worth of work to hide
+// behind.
+__host__ __device__ constexpr int tc_stages(int rb) { return 160 / rb > 3 ? 160 / rb : 3; }
+constexpr int kMaxTcStages = 10;
+
+// Byte b (0..255) of staged row rho of a ring stage: box b / 128, 128-byte
+// rows, 16-byte chunk index XOR (rho mod 8).
+template <int RB>
+__device__ __forceinline__ int ring_off(int rho, int b) {
+  return (((b >> 7) * RB + rho) << 7) + ((((b >> 4) & 7) ^ (rho & 7)) << 4) + (b & 15);
+}
+
+__device__ __forceinline__ unsigned int smem_u32(const void* p) {
+  return (unsigned int)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned int bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned int parity) {
+  unsigned int ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for the given phase parity of an mbarrier, at most kWaitLimit polls
+// (each poll may suspend for a short, hardware-chosen time). False: gave up.
+constexpr int kWaitLimit = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int parity) {
+  for (int i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// One 2D tensor-map box into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int x, int y, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+      ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// A tensor map in global memory is rewritten (by a host copy) between
+// launches: order those generic writes before its use by the tensor-map
+// proxy, which may otherwise hold the previous contents.
+__device__ __forceinline__ void fence_tensormap_acquire(const void* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(map) : "memory");
+}
+
+__device__ __forceinline__ unsigned int pack_half2(__half a, __half b) {
+  return (unsigned int)__half_as_ushort(a) | ((unsigned int)__half_as_ushort(b) << 16);
+}
+
+// Per channel count: pitch (halves) of the pass-2 operand rows V[(c, yo)][p]
+// (an odd multiple of 16 bytes, at least the slab's pixels rounded up to 16).
+template <int C> struct TcGeo;
+template <> struct TcGeo<1> { static constexpr int VP = 264; };
+template <> struct TcGeo<2> { static constexpr int VP = 136; };
+template <> struct TcGeo<3> { static constexpr int VP = 88; };
+template <> struct TcGeo<4> { static constexpr int VP = 72; };
+
+// No side effects: left to the compiler to schedule (independent chains interleave).
+__device__ __forceinline__ void mma16816(float (&d)[4], const unsigned int (&a)[4], unsigned int b0, unsigned int b1) {
+  asm(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned int (&r)[4], const void* p) {
+  const unsigned int s = (unsigned int)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(s));
+}
+
+// Unnormalised tap of offset d: exp(c d^2) (c = -1 / (2 sigma^2)), 1 at d = 0.
+__device__ __forceinline__ float tap_w(int d, float c) { return d == 0 ? 1.0f : expf(c * (float)(d * d)); }
+
+// Sum S of the unnormalised taps over |d| <= r, computed by every warp on
+// its own in one fixed order (lane-strided partial sums, then a butterfly,
+// which leaves the same value in every lane), so every warp holds the same S
+// without a block-wide barrier.
+__device__ __forceinline__ float warp_tap_sum(int r, float c) {
+  const int lane = threadIdx.x & 31;
+  float s = 0.0f;
+  for (int d = -r + lane; d <= r; d += 32) s += tap_w(d, c);
+  #pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// Normalised tap of index m (offset m - r), zero outside [0, 2r].
+__device__ __forceinline__ float tap_u(int m, int r, float c, float S) {
+  return (m >= 0 && m <= 2 * r) ? tap_w(m - r, c) / S : 0.0f;
+}
+
+// Tap-pair tables: entry j of the even table holds (w(m), w(m+1)) with
+// m = 2j - kPairPad, the odd table the pair starting one tap later; hi and lo
+// parts of the scaled taps w = u * 2^12.
+__device__ __forceinline__ void make_pairs(unsigned int* P, int r, float c, float S, int np) {
+  unsigned int* PEh = P;
+  unsigned int* POh = P + np;
+  unsigned int* PEl = P + 2 * np;
+  unsigned int* POl = P + 3 * np;
+  for (int j = threadIdx.x; j < np; j += kThreads) {
+    __half h[3], l[3];
+    #pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float w = tap_u(2 * j - kPairPad + q, r, c, S) * kWScale;
+      h[q] = __float2half_rn(w);
+      l[q] = __float2half_rn(w - __half2float(h[q]));
+    }
+    PEh[j] = pack_half2(h[0], h[1]);
+    POh[j] = pack_half2(h[1], h[2]);
+    PEl[j] = pack_half2(l[0], l[1]);
+    POl[j] = pack_half2(l[1], l[2]);
+  }
+}
+
+// Exclusive prefix sums of the normalised taps, CU[m] = sum_{m' < m} u(m')
+// for m in [0, 2r+1] (used to fold clamped taps onto edge rows/columns, as
+// in the fp32 kernel). One warp: contiguous lane segments, then a scan.
+__device__ __forceinline__ void make_cumulative_tc(float* CU, int r, float c, float S) {
+  const int lane = threadIdx.x & 31;
+  const int n = 2 * r + 1;
+  const int seg = (n + 31) >> 5;
+  const int b = lane * seg, e = min(n, b + seg);
+  float sum = 0.0f;
+  for (int m = b; m < e; ++m) sum += tap_u(m, r, c, S);
+  float incl = sum;
+  #pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  float run = incl - sum;
+  for (int m = b; m < e; ++m) {
+    CU[m] = run;
+    run += tap_u(m, r, c, S);
+  }
+  if (lane == 31) CU[n] = incl;
+}
+
+// Everything the tensor-core kernel does for one item with C channels.
+// Pass 2 of one slab on mma.sync: O[(c,yo)][x] += sum_p V[(c,yo)][p] Wh[p][x]
+// over the slab's pixels, V as hi/lo fp16 rows of pitch TcGeo<C>::VP
+// (Vhi Whi + Vhi Wlo + Vlo Whi), the tap pairs from the tables P; the folded
+// left column (first slab) is added before and the folded right column after
+// the products. Warp w owns units u = w + 8i (row tile u / 4, column tile
+// u % 4) and accumulates them in acc2[i] across slabs.
+template <int C>
+__device__ __forceinline__ void tc_pass2_slab(const Item& it, const Slab& sl, const __half* Vh, const __half* Vl,
+                                              const float* CU, const unsigned int* P, int np, float (&acc2)[C][4]) {
+  constexpr int VP = TcGeo<C>::VP;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int r = it.r;
+  const int npx = sl.sws / C;
+  const int npx16 = (npx + 15) & ~15;
+  const int P0 = sl.e0 / C;  // first folded pixel of the slab
+  // tap index of this lane's B registers has the parity of offx + P0 - g
+  const int par2 = (it.offx + P0 + g) & 1;
+  const unsigned int* Qh = P + (par2 ? np : 0);
+  const unsigned int* Ql = P + 2 * np + (par2 ? np : 0);
+  if (it.foldL && P0 == 0) {  // folded left column first: fixed summation order
+    #pragma unroll
+    for (int i = 0; i < C; ++i) {
+      const int u = warp + 8 * i;
+      const int mt2 = u >> 2, nt2 = u & 3;
+      #pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int row = 16 * mt2 + g + 8 * h;
+        const float v = __half2float(Vh[(size_t)row * VP]) + __half2float(Vl[(size_t)row * VP]);
+        #pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          const int x = 8 * nt2 + 2 * t + cc;
+          acc2[i][2 * h + cc] = fmaf(cum_at(CU, it.offx - x, r) * kWScale, v, acc2[i][2 * h + cc]);
+        }
+      }
+    }
+  }
+  for (int kk = 0; kk < npx16; kk += 16) {
+    unsigned int a_h[C][4], a_l[C][4], bh[C][2], bl[C][2];
+    #pragma unroll
+    for (int i = 0; i < C; ++i) {
+      const int u = warp + 8 * i;
+      const int mt2 = u >> 2, nt2 = u & 3;
+      const int arow = 16 * mt2 + (lane & 7) + ((lane >> 3) & 1) * 8;
+      const int acol = kk + ((lane >> 4) & 1) * 8;
+      ldsm_x4(a_h[i], Vh + (size_t)arow * VP + acol);
+      ldsm_x4(a_l[i], Vl + (size_t)arow * VP + acol);
+      const int jb = (it.offx + P0 + kk + 2 * t - 8 * nt2 - g + kPairPad) >> 1;
+      bh[i][0] = Qh[jb]; bh[i][1] = Qh[jb + 4];
+      bl[i][0] = Ql[jb]; bl[i][1] = Ql[jb + 4];
+    }
+    #pragma unroll
+    for (int i = 0; i < C; ++i) mma16816(acc2[i], a_h[i], bh[i][0], bh[i][1]);
+    #pragma unroll
+    for (int i = 0; i < C; ++i) mma16816(acc2[i], a_h[i], bl[i][0], bl[i][1]);
+    #pragma unroll
+    for (int i = 0; i < C; ++i) mma16816(acc2[i], a_l[i], bh[i][0], bh[i][1]);
+  }
+  {
+    const int pr = it.EW - 1 - P0;  // folded right column after the last slab's products
+    if (it.foldR && pr >= 0 && pr < npx) {
+      #pragma unroll
+      for (int i = 0; i < C; ++i) {
+        const int u = warp + 8 * i;
+        const int mt2 = u >> 2, nt2 = u & 3;
+        #pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int row = 16 * mt2 + g + 8 * h;
+          const float v = __half2float(Vh[(size_t)row * VP + pr]) + __half2float(Vl[(size_t)row * VP + pr]);
+          #pragma unroll
+          for (int cc = 0; cc < 2; ++cc) {
+            const int x = 8 * nt2 + 2 * t + cc;
+            acc2[i][2 * h + cc] = fmaf(cum_at(CU, 2 * r + 1 - (it.offx + it.EW - x), r) * kWScale, v, acc2[i][2 * h + cc]);
+          }
+        }
+      }
+    }
+  }
+}
+
+// Rounds the item's outputs (acc2, scaled by 2^12) to uint8, stages them in
+// ost (32 rows of 32 C bytes) and writes the block's rows with 16-byte
+// stores where the frame's alignment allows.
+template <int C>
+__device__ __forceinline__ void tc_write_output(const Item& it, unsigned char* ost, const float (&acc2)[C][4]) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  constexpr int opitch = 32 * C;
+  #pragma unroll
+  for (int i = 0; i < C; ++i) {
+    const int u = warp + 8 * i;
+    const int mt2 = u >> 2, nt2 = u & 3;
+    #pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int row = 16 * mt2 + g + ((e >> 1) << 3);
+      const int c = row >> 5, yo = row & 31;
+      const int x = 8 * nt2 + 2 * t + (e & 1);
+      ost[yo * opitch + x * C + c] = quant_u8(acc2[i][e] * kWInv);
+    }
+  }
+  __syncthreads();
+  const int rowBytes = it.bw * C;
+  unsigned char* out = it.out + (size_t)it.y0 * it.pitch + (size_t)it.x0 * C;
+  if (((((size_t)out) | it.pitch | (size_t)rowBytes) & 15) == 0) {
+    const int nv = rowBytes >> 4;  // 16-byte pieces per row
+    for (int idx = tid; idx < it.bh * nv; idx += kThreads) {
+      const int yo = idx / nv, v = idx - yo * nv;
+      *reinterpret_cast<uint4*>(out + (size_t)yo * it.pitch + 16 * v) =
+          *reinterpret_cast<const uint4*>(ost + yo * opitch + 16 * v);
+    }
+  } else {
+    for (int idx = tid; idx < it.bh * rowBytes; idx += kThreads) {
+      const int yo = idx / rowBytes, rem = idx - yo * rowBytes;
+      out[(size_t)yo * it.pitch + rem] = ost[yo * opitch + rem];
+    }
+  }
+}
+
+// Persistent item loop of the tensor-core kernels. Thread 0 takes tickets
+// (largest radius first: the frame's own bucket order, or the batch work
+// list), checks the item and derives its geometry; item_fn(it, c, map,
+// map_in_global, lookahead) then processes it with the whole CTA and
+// returns false to stop (staging failure, flag already set). Thread 0 looks
+// one item ahead: it holds the next item's ticket, and lookahead(0) /
+// lookahead(1), called by item_fn at two points of the current item, load
+// the next item's index and record, so the work list's dependent loads
+// overlap the current item. Ends with the single-frame counter reset.
+template <int RB, int C, typename ItemFn>
+__device__ __forceinline__ void tc_item_loop(const FrameSource& src, const CUtensorMap& tmap1, const Workspace& ws,
+                                             int rmax, const BucketList& bl, ItemFn&& item_fn) {
+  __shared__ int s_state;
+  __shared__ Item s_it;
+  __shared__ float s_c;
+  __shared__ const void* s_map;
+  __shared__ int s_start[kBuckets];
+  __shared__ int s_wsum[kThreads / 32];
+  const int tid = threadIdx.x;
+
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const bool own_order = bl.list != nullptr;
+  const int n_items = own_order ? (int)src.one_total : (int)ws.counters[CNT_NITEMS];
+  if (own_order) bucket_starts(ws.counters + CNT_HIST, bl.nb, s_start, s_wsum);
+  const CUtensorMap* batch_maps =
+      src.hdr ? reinterpret_cast<const CUtensorMap*>(reinterpret_cast<const char*>(src.hdr) + src.hdr->maps_offset)
+              : nullptr;
+
+  // Thread 0 looks one item ahead: it holds the next item's ticket, and
+  // during the current item it loads the next item's index and record, so
+  // the work list's dependent loads overlap the current item.
+  int next_tk = 0;
+  int nx_item = -1;        // next item's index (lookahead step 0)
+  ItemInfo nx_inf;         // next item's record (lookahead step 1)
+  bool nx_have = false;
+  auto lookup = [&](int tk) -> int {
+    if (!own_order) return ws.order[tk];
+    int lo = 0, hi = bl.nb - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (s_start[mid] <= tk) hi = mid; else lo = mid + 1;
+    }
+    return bl.list[(size_t)lo * bl.cap + (tk - s_start[lo])];
+  };
+  auto lookahead = [&](int step) {
+    if (step == 0) {
+      nx_have = false;
+      nx_item = next_tk < n_items ? lookup(next_tk) : -1;
+    } else if ((unsigned)nx_item < (unsigned)n_items) {
+      nx_inf = ws.items[nx_item];
+      nx_have = true;
+    }
+  };
+  if (tid == 0) next_tk = (int)atomicAdd(&ws.counters[CNT_TICKET], 1u);
+  for (;;) {
+    __syncthreads();  // the previous item is finished by every thread
+    if (tid == 0) {
+      const int tk = next_tk;
+      int state = 0;
+      if (tk >= n_items) {
+        state = 2;
+      } else {
+        next_tk = (int)atomicAdd(&ws.counters[CNT_TICKET], 1u);
+        const int item = nx_have ? nx_item : lookup(tk);
+        if ((unsigned)item >= (unsigned)n_items) {
+          atomicOr(&ws.counters[CNT_ERROR], 16u);
+          state = 1;
+        } else {
+          const ItemInfo inf = nx_have ? nx_inf : ws.items[item];
+          const FrameDesc fd = load_frame(src, inf.frame);
+          if (inf.r > rmax || fd.fmt != FOVEA_U8_HWC || fd.C != C) {
+            atomicOr(&ws.counters[CNT_ERROR], 2u);
+            state = 1;
+          } else {
+            item_geometry(s_it, inf, fd, RB);
+            s_c = inf.neg_half_inv_s2;
+            s_map = !fd.tma ? nullptr : (batch_maps ? static_cast<const void*>(batch_maps + inf.frame)
+                                                    : static_cast<const void*>(&tmap1));
+          }
+        }
+      }
+      nx_have = false;
+      s_state = state;
+    }
+    __syncthreads();
+    if (s_state == 2) break;
+    if (s_state == 1) continue;
+    if (!item_fn(s_it, s_c, s_map, batch_maps != nullptr, lookahead)) break;
+  }
+  if (own_order) {
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_state = atomicAdd(&ws.counters[CNT_DONE_SIGMA], 1u) == gridDim.x - 1 ? 3 : 0;
+    __syncthreads();
+    if (s_state == 3) {
+      for (int j = tid; j < kBuckets; j += kThreads) ws.counters[CNT_HIST + j] = 0u;
+      if (tid == 0) {
+        ws.counters[CNT_TICKET] = 0u;
+        ws.counters[CNT_DONE_SIGMA] = 0u;
+      }
+    }
+  }
+}
+
+}  // namespace tcc
+}  // namespace fovea

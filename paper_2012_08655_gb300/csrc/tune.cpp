@@ -120,10 +120,11 @@ extern "C" int fovea_autotune(fovea_ctx* ctx, int iters, const char* cache_path)
   const float fx = 0.5f * (float)W, fy = 0.5f * (float)H;
   const int rbs[3] = {16, 32, 64};
   const int ctas[3] = {1, 2, 0};
-  const int ntc = fmt == FOVEA_U8_HWC ? 2 : 1;
+  const int ntc = fmt == FOVEA_U8_HWC ? 3 : 1;
   for (int tcv = 0; tcv < ntc && status == FOVEA_OK; ++tcv)
   for (int a = 0; a < 3 && status == FOVEA_OK; ++a) {
     for (int b = 0; b < 3 && status == FOVEA_OK; ++b) {
+      if (tcv == 2 && rbs[a] > 32) continue;  // the tcgen05 kernel stages 16 or 32 rows
       fovea_config cfg{256, ctas[b], rbs[a], tcv};
       if (fovea_set_config(ctx, &cfg) != FOVEA_OK) continue;
       int st = FOVEA_OK;

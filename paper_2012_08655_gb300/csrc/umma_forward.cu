@@ -1,0 +1,496 @@
+// Tensor-core forward kernel for uint8 HWC frames with pass 1 on the
+// 5th-generation tensor cores (tcgen05): the same block-wise separable blur
+// (paper Section 2, Algorithm 1; taps of Eq. 1 truncated at r = ceil(3 sigma))
+// and the same two banded Toeplitz contractions as tc_forward.cu, but the
+// vertical pass, the larger of the two, is issued by one thread as
+// asynchronous tcgen05.mma instructions with its accumulator in tensor memory:
+//
+//   D1[e][n] = sum_v T[v][e] * u(v + n - 31 + D0),    n = 31 - yo,
+//
+// M = 128 staged byte columns e (two M tiles cover a 256-byte slab row),
+// N = 32 output rows (reversed), K = 16 staged rows per instruction, fp16
+// operands, fp32 accumulation. A (the tile, M x K) is converted from the TMA
+// row ring into fp16 K-major core matrices (a byte b becomes the exact fp16
+// subnormal b * 2^-24). B (the taps) is a Hankel matrix once its N index is
+// reversed: element (n, k) depends on n + k only, so the 8 x 8 core matrix of
+// N group a and K group b is entry a + b of one strip of 128-byte core
+// matrices, and a matrix descriptor with both strides 128 bytes reads it
+// directly; the strip holds the taps scaled by 2^12 split into fp16 hi and
+// lo parts, one instruction each. The accumulator is read back with
+// tcgen05.ld, the clamp-to-edge folds of the top and bottom rows are added,
+// and V = D1 * 2^12 goes to shared memory as fp16 hi/lo rows for pass 2,
+// which runs on mma.sync exactly as in tc_forward.cu (tc_common.cuh).
+#include <cstring>
+
+#include "tc_common.cuh"
+
+namespace fovea {
+
+namespace {
+
+using namespace fwd;
+using namespace tcc;
+
+constexpr int kTmemCols = 64;      // D1: two M tiles x 32 fp32 columns
+constexpr int kXOff = 8;           // strip entry j holds Hankel index X = j - kXOff
+constexpr unsigned int kIdescM128N32 =
+    (1u << 4)                      // D format: f32
+    | (0u << 7) | (0u << 10)       // A, B format: f16
+    | (0u << 15) | (0u << 16)      // A, B K-major
+    | ((32u >> 3) << 17)           // N = 32
+    | ((128u >> 4) << 24);         // M = 128
+
+__host__ __device__ constexpr int um_stages(int rb) { return 96 / rb; }   // 96 staged rows
+constexpr int kMaxUmStages = 6;
+// A1 (pass-1 A operand), one M tile: 16 groups of 8 columns x RB/8 groups of
+// 8 rows; K-adjacent core matrices 128 bytes apart, M-adjacent ones
+// 16 RB + 16 bytes apart (the 16-byte skew keeps the conversion's 8-byte
+// stores free of bank conflicts).
+__host__ __device__ constexpr int a1_sbo(int rb) { return 16 * rb + 16; }
+__host__ __device__ constexpr int a1_tile_bytes(int rb) { return 16 * a1_sbo(rb); }
+__host__ __device__ inline int strip_entries(int rmax) { return rmax / 4 + 16; }
+
+struct UmLayout {
+  size_t ring, a1, vh, vl, strip, cum, pairs, edge, total;
+};
+
+// Offsets from the 1024-byte aligned start of the dynamic shared memory.
+__host__ __device__ inline UmLayout um_layout(int rb, int rmax, int C) {
+  UmLayout L;
+  const int vp = C == 1 ? TcGeo<1>::VP : C == 2 ? TcGeo<2>::VP : C == 3 ? TcGeo<3>::VP : TcGeo<4>::VP;
+  const size_t vbytes = (size_t)32 * C * vp * 2;
+  L.ring = 0;                                                        // u8 [stages][2][rb][128] (swizzled)
+  L.a1 = L.ring + (size_t)um_stages(rb) * rb * kRingRow;             // half: [2 buffers][2 tiles] A1
+  L.vh = L.a1 + (size_t)4 * a1_tile_bytes(rb);                       // half [32 C][VP]
+  L.vl = L.vh + ((vbytes + 127) & ~(size_t)127);
+  L.strip = L.vl + ((vbytes + 127) & ~(size_t)127);                  // half [2][entries][8][8]
+  L.cum = L.strip + (size_t)2 * strip_entries(rmax) * 128;           // float [cum_len]
+  L.pairs = L.cum + (size_t)((cum_len(rmax) + 3) & ~3) * 4;          // uint32 [4][npair]
+  L.edge = L.pairs + (size_t)4 * npair(rmax) * 4;                    // float [2][256]
+  L.total = L.edge + (size_t)2 * 256 * 4 + 1024;                     // + alignment slack
+  return L;
+}
+
+// ---------------------------------------------------------------- tcgen05
+
+// Shared-memory matrix descriptor: no swizzle, K-major core matrices of 8
+// rows x 16 bytes; lbo / sbo = byte distance between core matrices adjacent
+// in K / in M (or N). Bits 46-48 hold the descriptor version 1.
+__device__ __forceinline__ unsigned long long umma_desc(const void* p, unsigned int lbo, unsigned int sbo) {
+  const unsigned int a = smem_u32(p);
+  return (unsigned long long)((a & 0x3FFFFu) >> 4) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void umma_f16(unsigned int d_tmem, unsigned long long a, unsigned long long b,
+                                         unsigned int idesc, unsigned int accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrives on `bar` once every tcgen05.mma issued so far by this thread is done.
+__device__ __forceinline__ void umma_commit(unsigned long long* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc05_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc05_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// 32 consecutive fp32 columns of this thread's tensor-memory lane.
+__device__ __forceinline__ void tmem_ld32(unsigned int taddr, float (&d)[32]) {
+  unsigned int u[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+        "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]),
+        "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]),
+        "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+  #pragma unroll
+  for (int i = 0; i < 32; ++i) d[i] = __uint_as_float(u[i]);
+}
+
+// Hankel strips of one item for pass 1: entry j, row rho, column i holds
+// the scaled tap u(8 (j - kXOff) + rho + i + delta) * 2^12, hi and lo fp16.
+__device__ __forceinline__ void make_strips(__half* Sh, __half* Sl, int nent, int r, float c, float S, int delta) {
+  for (int idx = threadIdx.x; idx < nent * 32; idx += kThreads) {
+    const int j = idx >> 5, rho = (idx >> 2) & 7, i0 = (idx & 3) * 2;
+    const int m0 = 8 * (j - kXOff) + rho + i0 + delta;
+    const float w0 = tap_u(m0, r, c, S) * kWScale, w1 = tap_u(m0 + 1, r, c, S) * kWScale;
+    const __half h0 = __float2half_rn(w0), h1 = __float2half_rn(w1);
+    const __half l0 = __float2half_rn(w0 - __half2float(h0)), l1 = __float2half_rn(w1 - __half2float(h1));
+    const int o = j * 64 + rho * 8 + i0;
+    *reinterpret_cast<unsigned int*>(Sh + o) = pack_half2(h0, h1);
+    *reinterpret_cast<unsigned int*>(Sl + o) = pack_half2(l0, l1);
+  }
+}
+
+// One item. bars: TMA ring stages; mbar_mma[2]: MMA completion per A1
+// buffer. gq0: chunks this CTA has staged so far (identical in all threads).
+template <int RB, int C, typename LookAhead>
+__device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned char* ring, __half* A1, __half* Vh,
+                                        __half* Vl, __half* Sh, __half* Sl, float* CU, unsigned int* P,
+                                        float* edge, int np, int nent, unsigned int tmem, int* s_tile_has,
+                                        unsigned long long* bars, unsigned long long* mbar_mma, const void* map,
+                                        bool map_in_global, int& gq0, unsigned int* err, LookAhead&& lookahead) {
+  constexpr int VP = TcGeo<C>::VP;
+  constexpr size_t stage_bytes = (size_t)RB * kRingRow;
+  constexpr int kStages = um_stages(RB);
+  constexpr int kTileBytes = a1_tile_bytes(RB);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int r = it.r;
+  const int Q = it.nsl * it.nchunks;
+  const int D0 = it.offy - it.ph;      // tap(v, yo) = v + D0 - yo
+  const int delta1 = (D0 + 1) & 7;      // (D0 - 31) mod 8
+
+  auto issue = [&](int qq) {  // one thread: the chunk's two TMA boxes
+    const Slab cs = slab_of<true>(it, qq / it.nchunks);
+    const int gq = gq0 + qq, stg = gq % kStages;
+    unsigned char* dst = ring + (size_t)stg * stage_bytes;
+    const int x = (int)cs.src - cs.ph;
+    const int y = it.gy0 - it.ph + (qq % it.nchunks) * RB;
+    mbar_expect_tx(bars + stg, 2u * 128u * RB);
+    tma_load_2d(dst, map, x, y, bars + stg);
+    tma_load_2d(dst + 128 * RB, map, x + 128, y, bars + stg);
+  };
+  auto load_plain = [&](int qq) {  // all threads: rows that TMA cannot load
+    const Slab cs = slab_of<true>(it, qq / it.nchunks);
+    unsigned char* dst = ring + (size_t)((gq0 + qq) % kStages) * stage_bytes;
+    const long long x0 = (long long)cs.src - cs.ph;
+    const int nb = min(256, (cs.ph + cs.sws + 31) & ~31);
+    const int y0 = it.gy0 - it.ph + (qq % it.nchunks) * RB;
+    for (int idx = threadIdx.x; idx < RB * nb; idx += kThreads) {
+      const int rho = idx / nb, b = idx - rho * nb;
+      const int y = y0 + rho;
+      const long long xb = x0 + b;
+      unsigned char v = 0;
+      if (y >= 0 && y < it.H && xb < (long long)it.pitch) v = it.in[(size_t)y * it.pitch + (size_t)xb];
+      dst[ring_off<RB>(rho, b)] = v;
+    }
+  };
+  if (map && tid == 0) {
+    if (map_in_global) fence_tensormap_acquire(map);
+    fence_proxy_async();
+    for (int q = 0; q < kStages - 1 && q < Q; ++q) issue(q);
+  }
+  {
+    const float S = warp_tap_sum(r, c_tap);
+    make_pairs(P, r, c_tap, S, np);
+    make_strips(Sh, Sl, nent, r, c_tap, S, delta1);
+    if ((it.foldT || it.foldB || it.foldL || it.foldR) && warp == kThreads / 32 - 1)
+      make_cumulative_tc(CU, r, c_tap, S);
+  }
+  if (tid == 0) lookahead(0);
+
+  float acc2[C][4];
+  #pragma unroll
+  for (int i = 0; i < C; ++i)
+    #pragma unroll
+    for (int k = 0; k < 4; ++k) acc2[i][k] = 0.f;
+
+  int q = 0;
+  bool ok = true;
+  int started[2] = {0, 0};  // thread 0: the slab's accumulation into M tile h has begun
+  int last_commit = -1;     // thread 0: global chunk of the latest MMA commit
+  for (; q < Q; ++q) {
+    const int gq = gq0 + q;
+    const int s = q / it.nchunks, k = q - s * it.nchunks;
+    const Slab sl = slab_of<true>(it, s);
+    const int R0 = k * RB;
+    bool got = true;
+    if (map) {
+      got = mbar_wait(bars + gq % kStages, (unsigned int)(gq / kStages) & 1u);
+    } else {
+      __syncthreads();  // iteration q-1 finished everywhere
+      load_plain(q);
+      __syncthreads();
+    }
+    // the MMAs of chunk gq - 2 read the A1 buffer this chunk is converted into
+    if (gq >= 2) got = mbar_wait(&mbar_mma[gq & 1], (unsigned int)((gq - 2) >> 1) & 1u) && got;
+    const unsigned char* st = ring + (size_t)(gq % kStages) * stage_bytes;
+    __half* a1b = A1 + (size_t)(gq & 1) * kTileBytes;  // buffer gq % 2: two tiles of kTileBytes bytes
+    // ---- convert the chunk: 8 columns x 4 rows per work unit, transposed
+    // into K-major core matrices; stash the folded edge rows as floats
+    const int vb = it.ph + it.EH - 1;
+    for (int idx = tid; idx < 8 * RB; idx += kThreads) {
+      const int mi = (idx & 7) + ((idx >> 4) & 1) * 8;  // column group 0..15
+      const int half = (idx >> 3) & 1;                    // rows 0-3 or 4-7 of a core matrix
+      const int rest = idx >> 5;
+      const int ki = rest % (RB / 8), h = rest / (RB / 8);
+      const int b = 128 * h + 8 * mi;                     // first ring byte
+      if (b >= sl.ph + sl.sws || b + 8 <= sl.ph) continue;  // no slab byte here
+      const int v0 = 8 * ki + 4 * half;
+      uint2 w[4];
+      #pragma unroll
+      for (int j = 0; j < 4; ++j) w[j] = *reinterpret_cast<const uint2*>(st + ring_off<RB>(v0 + j, b));
+      #pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int vv = R0 + v0 + j;
+        if ((k == 0 && vv == it.ph) || vv == vb) {
+          float* ed = edge + (vv == vb ? 256 : 0) + b;
+          #pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            ed[i] = (float)((w[j].x >> (8 * i)) & 0xFFu);
+            ed[4 + i] = (float)((w[j].y >> (8 * i)) & 0xFFu);
+          }
+        }
+      }
+      // rows (v0, v0+1) and (v0+2, v0+3) of column i -> two fp16 subnormal pairs
+      unsigned int o[8][2];
+      {
+        const unsigned int p01 = __byte_perm(w[0].x, w[1].x, 0x5140), p23 = __byte_perm(w[0].x, w[1].x, 0x7362);
+        const unsigned int q01 = __byte_perm(w[2].x, w[3].x, 0x5140), q23 = __byte_perm(w[2].x, w[3].x, 0x7362);
+        const unsigned int p45 = __byte_perm(w[0].y, w[1].y, 0x5140), p67 = __byte_perm(w[0].y, w[1].y, 0x7362);
+        const unsigned int q45 = __byte_perm(w[2].y, w[3].y, 0x5140), q67 = __byte_perm(w[2].y, w[3].y, 0x7362);
+        o[0][0] = __byte_perm(p01, 0u, 0x4140); o[0][1] = __byte_perm(q01, 0u, 0x4140);
+        o[1][0] = __byte_perm(p01, 0u, 0x4342); o[1][1] = __byte_perm(q01, 0u, 0x4342);
+        o[2][0] = __byte_perm(p23, 0u, 0x4140); o[2][1] = __byte_perm(q23, 0u, 0x4140);
+        o[3][0] = __byte_perm(p23, 0u, 0x4342); o[3][1] = __byte_perm(q23, 0u, 0x4342);
+        o[4][0] = __byte_perm(p45, 0u, 0x4140); o[4][1] = __byte_perm(q45, 0u, 0x4140);
+        o[5][0] = __byte_perm(p45, 0u, 0x4342); o[5][1] = __byte_perm(q45, 0u, 0x4342);
+        o[6][0] = __byte_perm(p67, 0u, 0x4140); o[6][1] = __byte_perm(q67, 0u, 0x4140);
+        o[7][0] = __byte_perm(p67, 0u, 0x4342); o[7][1] = __byte_perm(q67, 0u, 0x4342);
+      }
+      unsigned char* dst = reinterpret_cast<unsigned char*>(a1b) + (size_t)h * kTileBytes + mi * a1_sbo(RB) +
+                           ki * 128 + half * 8;
+      #pragma unroll
+      for (int i = 0; i < 8; ++i) *reinterpret_cast<uint2*>(dst + i * 16) = make_uint2(o[i][0], o[i][1]);
+    }
+    fence_proxy_async();  // the converted chunk is read by the tensor cores
+    tc05_fence_before();
+    got = __syncthreads_and(got) != 0;  // chunk converted everywhere; iteration q-1 finished
+    if (!got) {
+      ok = false;
+      break;
+    }
+    if (tid == 0) {
+      tc05_fence_after();
+      if (map && q + kStages - 1 < Q) issue(q + kStages - 1);
+      if (k == 0) started[0] = started[1] = 0;
+      // ---- pass 1 on the chunk: 16 staged rows per instruction, both M tiles
+      for (int ks = 0; ks < RB / 16; ++ks) {
+        const int k0 = R0 + 16 * ks;
+        if (k0 >= it.vrows) break;
+        if (k0 + 15 < -D0 || k0 > 31 - D0 + 2 * r) continue;  // no tap of the 32 rows here
+        const int j0 = (k0 + D0 - 31 - delta1) / 8 + kXOff;
+        const unsigned long long bhi = umma_desc(Sh + (size_t)j0 * 64, 128, 128);
+        const unsigned long long blo = umma_desc(Sl + (size_t)j0 * 64, 128, 128);
+        #pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (128 * h >= sl.ph + sl.sws || 128 * h + 128 <= sl.ph) continue;
+          const unsigned long long ad = umma_desc(reinterpret_cast<unsigned char*>(a1b) + (size_t)h * kTileBytes +
+                                                      ks * 256, 128, a1_sbo(RB));
+          umma_f16(tmem + 32 * h, ad, bhi, kIdescM128N32, started[h]);
+          umma_f16(tmem + 32 * h, ad, blo, kIdescM128N32, 1u);
+          started[h] = 1;
+        }
+      }
+      umma_commit(&mbar_mma[gq & 1]);
+      last_commit = gq;
+      if (k == it.nchunks - 1) {
+        s_tile_has[0] = started[0];
+        s_tile_has[1] = started[1];
+      }
+    }
+    if (q == 0 && tid == 0) lookahead(1);
+    if (k != it.nchunks - 1) continue;
+
+    // ---- slab complete: read D1 back, add the folded rows, V -> hi/lo fp16
+    const bool done = __all_sync(0xffffffffu, mbar_wait(&mbar_mma[gq & 1], (unsigned int)(gq >> 1) & 1u));
+    __syncthreads();  // s_tile_has visible
+    tc05_fence_after();
+    const int npx = sl.sws / C;
+    const int npx16 = (npx + 15) & ~15;
+    {
+      const int h = warp >> 2;                 // M tile of this warp
+      const int e = 32 * (warp & 3) + lane;    // its tensor-memory lane
+      const int b = 128 * h + e;               // ring byte = slab element + ph
+      const int ee = b - sl.ph;
+      const bool tile_on = done && s_tile_has[h] != 0;
+      float d[32];
+      if (tile_on) {
+        tmem_ld32(tmem + ((unsigned int)(32 * (warp & 3)) << 16) + 32 * h, d);
+      }
+      if (tile_on && ee >= 0 && ee < sl.sws) {
+        const float et = it.foldT ? edge[b] : 0.0f, eb = it.foldB ? edge[256 + b] : 0.0f;
+        const int px = ee / C, c = ee - px * C;
+        __half* vh = Vh + (size_t)(c * 32) * VP + px;
+        __half* vl = Vl + (size_t)(c * 32) * VP + px;
+        #pragma unroll
+        for (int yo = 0; yo < 32; ++yo) {
+          float a = d[31 - yo];
+          if (it.foldT) a = fmaf(cum_at(CU, it.offy - yo, r) * (kWScale * kDScale), et, a);
+          if (it.foldB) a = fmaf(cum_at(CU, 2 * r + 1 - (it.offy + it.EH - yo), r) * (kWScale * kDScale), eb, a);
+          const float v = a * kVScale;
+          const __half hv = __float2half_rn(v);
+          vh[(size_t)yo * VP] = hv;
+          vl[(size_t)yo * VP] = __float2half_rn(v - __half2float(hv));
+        }
+      }
+      // zero the columns px in [npx, npx16) that pass 2 reads
+      const int zc = npx16 - npx;
+      for (int idx = tid; idx < C * 32 * zc; idx += kThreads) {
+        const int row = idx / zc, px = npx + (idx - row * zc);
+        Vh[(size_t)row * VP + px] = __ushort_as_half(0);
+        Vl[(size_t)row * VP + px] = __ushort_as_half(0);
+      }
+    }
+    tc05_fence_before();
+    if (__syncthreads_and(done ? 1 : 0) == 0) {  // also: D1 read everywhere before the next slab's MMAs
+      ok = false;
+      break;
+    }
+    tc_pass2_slab<C>(it, sl, Vh, Vl, CU, P, np, acc2);
+  }
+  if (!ok) {
+    // a chunk never arrived or an MMA never finished: flag it, let what is
+    // still in flight land (bounded) and give up on the item
+    if (tid == 0) {
+      atomicOr(err, 64u);
+      for (int qq = q; qq < Q && qq < q + kStages - 1; ++qq) {
+        const int g2 = gq0 + qq;
+        if (map) mbar_wait(bars + g2 % kStages, (unsigned int)(g2 / kStages) & 1u);
+      }
+      if (last_commit >= 0) mbar_wait(&mbar_mma[last_commit & 1], (unsigned int)(last_commit >> 1) & 1u);
+    }
+    __syncthreads();
+    return false;
+  }
+  gq0 += Q;
+  __syncthreads();  // the ring is no longer read: it becomes the output stage
+  tc_write_output<C>(it, ring, acc2);
+  fence_proxy_async();  // the next item's TMA boxes overwrite the output stage
+  return true;
+}
+
+template <int RB, int C>
+__global__ void __launch_bounds__(kThreads, 2)
+umma_forward_kernel(const __grid_constant__ FrameSource src, Workspace ws, int rmax, BucketList bl,
+                    const __grid_constant__ CUtensorMap tmap1) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const UmLayout L = um_layout(RB, rmax, C);
+  unsigned char* ring = smem + L.ring;
+  __half* A1 = reinterpret_cast<__half*>(smem + L.a1);
+  __half* Vh = reinterpret_cast<__half*>(smem + L.vh);
+  __half* Vl = reinterpret_cast<__half*>(smem + L.vl);
+  const int nent = strip_entries(rmax);
+  __half* Sh = reinterpret_cast<__half*>(smem + L.strip);
+  __half* Sl = Sh + (size_t)nent * 64;
+  float* CU = reinterpret_cast<float*>(smem + L.cum);
+  unsigned int* P = reinterpret_cast<unsigned int*>(smem + L.pairs);
+  float* edge = reinterpret_cast<float*>(smem + L.edge);
+  __shared__ __align__(8) unsigned long long s_bar[kMaxUmStages];
+  __shared__ __align__(8) unsigned long long s_mma[2];
+  __shared__ unsigned int s_tmem;
+  __shared__ int s_tile_has[2];
+  const int np = npair(rmax);
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kMaxUmStages; ++i) mbar_init(&s_bar[i], 1);
+    mbar_init(&s_mma[0], 1);
+    mbar_init(&s_mma[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    fence_proxy_async();
+  }
+  if (warp == 0) {  // tensor memory for D1 (two CTAs per SM take 128 of 512 columns)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
+                 "r"((unsigned int)kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  tc05_fence_before();
+  __syncthreads();
+  tc05_fence_after();
+  const unsigned int tmem = s_tmem;
+  int gq0 = 0;
+  tc_item_loop<RB, C>(src, tmap1, ws, rmax, bl,
+                      [&](const Item& it, float c, const void* map, bool map_global, auto& lookahead) {
+                        return um_item<RB, C>(it, c, ring, A1, Vh, Vl, Sh, Sl, CU, P, edge, np, nent, tmem,
+                                              s_tile_has, s_bar, s_mma, map, map_global, gq0,
+                                              ws.counters + CNT_ERROR, lookahead);
+                      });
+  tc05_fence_before();
+  __syncthreads();  // every MMA was waited for before its accumulator was read
+  if (warp == 0) {
+    tc05_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((unsigned int)kTmemCols)
+                 : "memory");
+  }
+}
+
+template <int RB, int C>
+void* um_kernel_ptr() { return reinterpret_cast<void*>(&umma_forward_kernel<RB, C>); }
+
+template <int C>
+void* pick_um_rb(int rb) {
+  return rb == 16 ? um_kernel_ptr<16, C>() : um_kernel_ptr<32, C>();
+}
+
+void* pick_um(int rb, int C) {
+  switch (C) {
+    case 1: return pick_um_rb<1>(rb);
+    case 2: return pick_um_rb<2>(rb);
+    case 3: return pick_um_rb<3>(rb);
+    default: return pick_um_rb<4>(rb);
+  }
+}
+
+int um_rb(const FwdConfig& cfg) { return cfg.rows_per_chunk == 16 ? 16 : 32; }
+
+}  // namespace
+
+size_t umma_forward_smem_bytes(const FwdConfig& cfg, int rmax, int C) {
+  return um_layout(um_rb(cfg), rmax, C).total;
+}
+
+int umma_forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int C) {
+  if (rmax > kUmmaMaxRadius) return 0;
+  const size_t smem = umma_forward_smem_bytes(cfg, rmax, C);
+  void* k = pick_um(um_rb(cfg), C);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kThreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+cudaError_t launch_umma_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg, int rmax, int C,
+                                int grid, cudaStream_t s, const BucketList& bl, bool pdl, const void* tmap_one) {
+  const size_t smem = umma_forward_smem_bytes(cfg, rmax, C);
+  void* k = pick_um(um_rb(cfg), C);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  BucketList b = bl;
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  if (tmap_one) std::memcpy(&map, tmap_one, sizeof(map));
+  void* args[] = {const_cast<FrameSource*>(&src), const_cast<Workspace*>(&ws), &rmax, &b, &map};
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(grid);
+  lc.blockDim = dim3(kThreads);
+  lc.dynamicSmemBytes = smem;
+  lc.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = attr;
+  lc.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelExC(&lc, k, args);
+}
+
+}  // namespace fovea

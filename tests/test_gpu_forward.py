@@ -148,14 +148,16 @@ def test_render_host_and_batch_match_render(fv):
 
 # ---------------------------------------------------------------- configurations
 
-def test_every_config_gives_identical_output(fv):
+@pytest.mark.parametrize("tc", [0, 1, 2])
+def test_every_config_gives_identical_output(fv, tc):
+    """Within one kernel, the row chunk and the CTA count change nothing."""
     s = wl.frame_1080p(seed=9)
     x = to_dev(s.image)
     ctx = fv.Context(1920, 1080, 3, 32, s.sigma0, s.k, fv.U8_HWC)
     outs = []
-    for rb in (16, 32, 64):
+    for rb in ((16, 32) if tc == 2 else (16, 32, 64)):
         for ctas in (1, 2, 0):
-            ctx.set_config(256, ctas, rb)
+            ctx.set_config(256, ctas, rb, tensor_cores=tc)
             y = torch.empty_like(x)
             ctx.render(x, y, s.fix_x, s.fix_y)
             outs.append(y)
@@ -185,20 +187,25 @@ def test_argument_errors(fv):
 
 # ---------------------------------------------------------------- tensor-core kernel vs fp32 kernel
 
+@pytest.mark.parametrize("tc", [1, 2])
 @pytest.mark.parametrize("W,H,C,B,fx,fy,k", [
     (1920, 1080, 3, 32, 960.0, 540.0, 0.02),
     (333, 221, 1, 32, 10.0, 200.0, 0.1),
     (640, 480, 4, 16, 600.0, 30.0, 0.3),
     (129, 77, 2, 8, 64.0, 38.0, 0.05),
+    (256, 200, 3, 32, 250.0, 10.0, 0.7),
 ])
-def test_tensor_core_kernel_matches_fp32_kernel(fv, W, H, C, B, fx, fy, k):
+def test_tensor_core_kernel_matches_fp32_kernel(fv, W, H, C, B, fx, fy, k, tc):
+    """Both tensor-core kernels (1: mma.sync; 2: vertical pass on tcgen05)
+    against the fp32 FMA kernel and the oracle; the last case has radii
+    above the tcgen05 kernel's bound, which falls back to mma.sync."""
     img = wl.grating_frame(H, W, C, seed=W + C)
     x = to_dev(img)
     ctx = fv.Context(W, H, C, B, 0.5, k, fv.U8_HWC)
     ctx.set_config(256, 0, 32, tensor_cores=0)
     y32 = torch.empty_like(x)
     ctx.render(x, y32, fx, fy)
-    ctx.set_config(256, 0, 32, tensor_cores=1)
+    ctx.set_config(256, 0, 32, tensor_cores=tc)
     ytc = torch.empty_like(x)
     ctx.render(x, ytc, fx, fy)
     torch.cuda.synchronize()
