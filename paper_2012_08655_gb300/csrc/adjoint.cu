@@ -227,7 +227,7 @@ size_t adjoint_smem_bytes(int rmax) { return smem_layout(rmax).total; }
 
 int adjoint_max_ctas_per_sm(int rmax) {
   const size_t smem = adjoint_smem_bytes(rmax);
-  if (cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  if (set_smem_attrs(reinterpret_cast<const void*>(adjoint_kernel), smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -242,7 +242,7 @@ int adjoint_max_ctas_per_sm(int rmax) {
 cudaError_t launch_adjoint(const FrameSource& src, const Workspace& ws, int rmax, int grid,
                            cudaStream_t s) {
   const size_t smem = adjoint_smem_bytes(rmax);
-  cudaError_t e = cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem_attrs(reinterpret_cast<const void*>(adjoint_kernel), smem);
   if (e != cudaSuccess) return e;
   adjoint_kernel<<<grid, kThreads, smem, s>>>(src, ws, rmax);
   return cudaGetLastError();

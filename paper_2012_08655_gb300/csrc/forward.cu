@@ -398,7 +398,7 @@ size_t forward_smem_bytes(const FwdConfig& cfg, int rmax, int fmt_mask) {
 int forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int fmt_mask) {
   const size_t smem = forward_smem_bytes(cfg, rmax, fmt_mask);
   void* k = pick_kernel(cfg.rows_per_chunk, mode_of(fmt_mask));
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  if (set_smem_attrs(reinterpret_cast<const void*>(k), smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -415,7 +415,7 @@ cudaError_t launch_forward(const FrameSource& src, const Workspace& ws, const Fw
   const size_t smem = forward_smem_bytes(cfg, rmax, fmt_mask);
   int row_bytes = (fmt_mask & 2) ? kRowBytesF32 : kRowBytesU8;
   void* k = pick_kernel(cfg.rows_per_chunk, mode_of(fmt_mask));
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem_attrs(reinterpret_cast<const void*>(k), smem);
   if (e != cudaSuccess) return e;
   BucketList b = bl;
   void* args[] = {const_cast<FrameSource*>(&src), const_cast<Workspace*>(&ws), &rmax, &row_bytes, &b};

@@ -250,6 +250,16 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// Lets kernel k use `smem` bytes of dynamic shared memory and asks for the
+// largest shared-memory carveout, so that as many CTAs fit per SM as the
+// shared memory allows (the occupancy calculator and the launch both follow
+// the carveout preference).
+inline cudaError_t set_smem_attrs(const void* k, size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+}
+
 // ------------------------------------------------------------------ launchers
 // (defined in sigma.cu, forward.cu, adjoint.cu)
 

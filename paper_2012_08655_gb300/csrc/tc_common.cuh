@@ -185,12 +185,28 @@ __device__ __forceinline__ void make_cumulative_tc(float* CU, int r, float c, fl
 
 // Everything the tensor-core kernel does for one item with C channels.
 // Pass 2 of one slab on mma.sync: O[(c,yo)][x] += sum_p V[(c,yo)][p] Wh[p][x]
-// over the slab's pixels, V as hi/lo fp16 rows of pitch TcGeo<C>::VP
-// (Vhi Whi + Vhi Wlo + Vlo Whi), the tap pairs from the tables P; the folded
+// over the slab's pixels, V as hi/lo fp16 (Vhi Whi + Vhi Wlo + Vlo Whi), the tap pairs from the tables P; the folded
 // left column (first slab) is added before and the folded right column after
 // the products. Warp w owns units u = w + 8i (row tile u / 4, column tile
 // u % 4) and accumulates them in acc2[i] across slabs.
-template <int C>
+//
+// Two layouts of V: VT = false, row (c, yo) = 32 c + yo of pitch VP, pixels
+// contiguous; VT = true, row (px, c) = C px + c of kVtPitch halves, the 32
+// output rows contiguous (fragments then come from ldmatrix.trans).
+constexpr int kVtPitch = 40;  // 32 rows + 8: row starts 20 words apart, conflict-free for odd C
+
+__device__ __forceinline__ void ldsm_x4_t(unsigned int (&r)[4], const void* p) {
+  const unsigned int s = (unsigned int)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(s));
+}
+
+template <int C, bool VT>
+__device__ __forceinline__ size_t v_index(int c, int yo, int px) {
+  return VT ? (size_t)(px * C + c) * kVtPitch + yo : (size_t)(c * 32 + yo) * TcGeo<C>::VP + px;
+}
+
+template <int C, bool VT = false>
 __device__ __forceinline__ void tc_pass2_slab(const Item& it, const Slab& sl, const __half* Vh, const __half* Vl,
                                               const float* CU, const unsigned int* P, int np, float (&acc2)[C][4]) {
   constexpr int VP = TcGeo<C>::VP;
@@ -212,7 +228,8 @@ __device__ __forceinline__ void tc_pass2_slab(const Item& it, const Slab& sl, co
       #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int row = 16 * mt2 + g + 8 * h;
-        const float v = __half2float(Vh[(size_t)row * VP]) + __half2float(Vl[(size_t)row * VP]);
+        const size_t o = v_index<C, VT>(row >> 5, row & 31, 0);
+        const float v = __half2float(Vh[o]) + __half2float(Vl[o]);
         #pragma unroll
         for (int cc = 0; cc < 2; ++cc) {
           const int x = 8 * nt2 + 2 * t + cc;
@@ -227,10 +244,18 @@ __device__ __forceinline__ void tc_pass2_slab(const Item& it, const Slab& sl, co
     for (int i = 0; i < C; ++i) {
       const int u = warp + 8 * i;
       const int mt2 = u >> 2, nt2 = u & 3;
-      const int arow = 16 * mt2 + (lane & 7) + ((lane >> 3) & 1) * 8;
-      const int acol = kk + ((lane >> 4) & 1) * 8;
-      ldsm_x4(a_h[i], Vh + (size_t)arow * VP + acol);
-      ldsm_x4(a_l[i], Vl + (size_t)arow * VP + acol);
+      if (VT) {  // stored rows are pixels: transpose on load
+        const int m0 = 16 * mt2 + ((lane >> 3) & 1) * 8;
+        const int krow = kk + (lane & 7) + ((lane >> 4) & 1) * 8;
+        const size_t o = v_index<C, true>(m0 >> 5, m0 & 31, krow);
+        ldsm_x4_t(a_h[i], Vh + o);
+        ldsm_x4_t(a_l[i], Vl + o);
+      } else {
+        const int arow = 16 * mt2 + (lane & 7) + ((lane >> 3) & 1) * 8;
+        const int acol = kk + ((lane >> 4) & 1) * 8;
+        ldsm_x4(a_h[i], Vh + (size_t)arow * VP + acol);
+        ldsm_x4(a_l[i], Vl + (size_t)arow * VP + acol);
+      }
       const int jb = (it.offx + P0 + kk + 2 * t - 8 * nt2 - g + kPairPad) >> 1;
       bh[i][0] = Qh[jb]; bh[i][1] = Qh[jb + 4];
       bl[i][0] = Ql[jb]; bl[i][1] = Ql[jb + 4];
@@ -252,7 +277,8 @@ __device__ __forceinline__ void tc_pass2_slab(const Item& it, const Slab& sl, co
         #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int row = 16 * mt2 + g + 8 * h;
-          const float v = __half2float(Vh[(size_t)row * VP + pr]) + __half2float(Vl[(size_t)row * VP + pr]);
+          const size_t o = v_index<C, VT>(row >> 5, row & 31, pr);
+          const float v = __half2float(Vh[o]) + __half2float(Vl[o]);
           #pragma unroll
           for (int cc = 0; cc < 2; ++cc) {
             const int x = 8 * nt2 + 2 * t + cc;
@@ -311,14 +337,14 @@ __device__ __forceinline__ void tc_write_output(const Item& it, unsigned char* o
 // lookahead(1), called by item_fn at two points of the current item, load
 // the next item's index and record, so the work list's dependent loads
 // overlap the current item. Ends with the single-frame counter reset.
+// s_start: shared memory for rmax + 1 bucket starts (single frames).
 template <int RB, int C, typename ItemFn>
 __device__ __forceinline__ void tc_item_loop(const FrameSource& src, const CUtensorMap& tmap1, const Workspace& ws,
-                                             int rmax, const BucketList& bl, ItemFn&& item_fn) {
+                                             int rmax, const BucketList& bl, int* s_start, ItemFn&& item_fn) {
   __shared__ int s_state;
   __shared__ Item s_it;
   __shared__ float s_c;
   __shared__ const void* s_map;
-  __shared__ int s_start[kBuckets];
   __shared__ int s_wsum[kThreads / 32];
   const int tid = threadIdx.x;
 

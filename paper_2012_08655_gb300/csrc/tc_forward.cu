@@ -35,7 +35,7 @@ using namespace fwd;
 using namespace tcc;
 
 struct TcLayout {
-  size_t ring, vh, vl, cum, pairs, total;
+  size_t ring, vh, vl, cum, pairs, starts, total;
 };
 
 // Offsets from the 1024-byte aligned start of the dynamic shared memory (the
@@ -47,7 +47,8 @@ __host__ __device__ inline TcLayout tc_layout(int rb, int rmax) {
   L.vl = L.vh + (size_t)kVHalves * 2;                          // half [kVHalves]
   L.cum = L.vl + (size_t)kVHalves * 2;                         // float [cum_len]
   L.pairs = L.cum + (size_t)((cum_len(rmax) + 3) & ~3) * 4;    // uint32 [4][npair]
-  L.total = L.pairs + (size_t)4 * npair(rmax) * 4 + 1024;      // + alignment slack
+  L.starts = L.pairs + (size_t)4 * npair(rmax) * 4;           // int [rmax + 1] bucket starts
+  L.total = L.starts + (size_t)(rmax + 1) * 4 + 1024;          // + alignment slack
   return L;
 }
 
@@ -330,7 +331,7 @@ tc_forward_kernel(const __grid_constant__ FrameSource src, Workspace ws, int rma
     fence_proxy_async();
   }
   int gq0 = 0;  // chunks staged by this CTA so far (identical in every thread)
-  tc_item_loop<RB, C>(src, tmap1, ws, rmax, bl,
+  tc_item_loop<RB, C>(src, tmap1, ws, rmax, bl, reinterpret_cast<int*>(smem + L.starts),
                       [&](const Item& it, float c, const void* map, bool map_global, auto& lookahead) {
                         return tc_item<RB, C>(it, c, ring, Vh, Vl, CU, P, np, s_bar, map, map_global, gq0,
                                               ws.counters + CNT_ERROR, lookahead);
@@ -365,7 +366,7 @@ size_t tc_forward_smem_bytes(const FwdConfig& cfg, int rmax) { return tc_layout(
 int tc_forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int C) {
   const size_t smem = tc_forward_smem_bytes(cfg, rmax);
   void* k = pick_tc(cfg.rows_per_chunk, C);
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  if (set_smem_attrs(reinterpret_cast<const void*>(k), smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -381,7 +382,7 @@ cudaError_t launch_tc_forward(const FrameSource& src, const Workspace& ws, const
                               int grid, cudaStream_t s, const BucketList& bl, bool pdl, const void* tmap_one) {
   const size_t smem = tc_forward_smem_bytes(cfg, rmax);
   void* k = pick_tc(cfg.rows_per_chunk, C);
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem_attrs(reinterpret_cast<const void*>(k), smem);
   if (e != cudaSuccess) return e;
   BucketList b = bl;
   CUtensorMap map;

@@ -51,23 +51,28 @@ __host__ __device__ constexpr int a1_tile_bytes(int rb) { return 16 * a1_sbo(rb)
 __host__ __device__ inline int strip_entries(int rmax) { return rmax / 4 + 16; }
 
 struct UmLayout {
-  size_t ring, a1, vh, vl, strip, cum, pairs, edge, total;
+  size_t ring, a1, vh, vl, strip, cum, pairs, edge, foldw, starts, total;
 };
+
+// Rows (pixel, channel) of the transposed V arrays: the slab's pixels
+// rounded up to 16, times C.
+__host__ __device__ constexpr int vt_rows(int C) { return C == 1 ? 240 : C == 2 ? 256 : C == 3 ? 240 : 256; }
 
 // Offsets from the 1024-byte aligned start of the dynamic shared memory.
 __host__ __device__ inline UmLayout um_layout(int rb, int rmax, int C) {
   UmLayout L;
-  const int vp = C == 1 ? TcGeo<1>::VP : C == 2 ? TcGeo<2>::VP : C == 3 ? TcGeo<3>::VP : TcGeo<4>::VP;
-  const size_t vbytes = (size_t)32 * C * vp * 2;
+  const size_t vbytes = (size_t)vt_rows(C) * kVtPitch * 2;
   L.ring = 0;                                                        // u8 [stages][2][rb][128] (swizzled)
   L.a1 = L.ring + (size_t)um_stages(rb) * rb * kRingRow;             // half: [2 buffers][2 tiles] A1
-  L.vh = L.a1 + (size_t)4 * a1_tile_bytes(rb);                       // half [32 C][VP]
-  L.vl = L.vh + ((vbytes + 127) & ~(size_t)127);
-  L.strip = L.vl + ((vbytes + 127) & ~(size_t)127);                  // half [2][entries][8][8]
+  L.vh = L.a1 + (size_t)4 * a1_tile_bytes(rb);                       // half [C px + c][kVtPitch]
+  L.vl = L.vh + vbytes;
+  L.strip = L.vl + vbytes;                                           // half [2][entries][8][8]
   L.cum = L.strip + (size_t)2 * strip_entries(rmax) * 128;           // float [cum_len]
   L.pairs = L.cum + (size_t)((cum_len(rmax) + 3) & ~3) * 4;          // uint32 [4][npair]
   L.edge = L.pairs + (size_t)4 * npair(rmax) * 4;                    // float [2][256]
-  L.total = L.edge + (size_t)2 * 256 * 4 + 1024;                     // + alignment slack
+  L.foldw = L.edge + (size_t)2 * 256 * 4;                            // float [2][32]
+  L.starts = L.foldw + (size_t)2 * 32 * 4;                           // int [rmax + 1]
+  L.total = L.starts + (size_t)(rmax + 1) * 4 + 1024;                // + alignment slack
   return L;
 }
 
@@ -138,10 +143,10 @@ __device__ __forceinline__ void make_strips(__half* Sh, __half* Sl, int nent, in
 template <int RB, int C, typename LookAhead>
 __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned char* ring, __half* A1, __half* Vh,
                                         __half* Vl, __half* Sh, __half* Sl, float* CU, unsigned int* P,
-                                        float* edge, int np, int nent, unsigned int tmem, int* s_tile_has,
+                                        float* edge, float* foldw, int np, int nent, unsigned int tmem,
+                                        int* s_tile_has,
                                         unsigned long long* bars, unsigned long long* mbar_mma, const void* map,
                                         bool map_in_global, int& gq0, unsigned int* err, LookAhead&& lookahead) {
-  constexpr int VP = TcGeo<C>::VP;
   constexpr size_t stage_bytes = (size_t)RB * kRingRow;
   constexpr int kStages = um_stages(RB);
   constexpr int kTileBytes = a1_tile_bytes(RB);
@@ -185,8 +190,13 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
     const float S = warp_tap_sum(r, c_tap);
     make_pairs(P, r, c_tap, S, np);
     make_strips(Sh, Sl, nent, r, c_tap, S, delta1);
-    if ((it.foldT || it.foldB || it.foldL || it.foldR) && warp == kThreads / 32 - 1)
+    if ((it.foldT || it.foldB || it.foldL || it.foldR) && warp == kThreads / 32 - 1) {
       make_cumulative_tc(CU, r, c_tap, S);
+      __syncwarp();
+      // weights of the folded top / bottom rows for output row yo = lane
+      foldw[lane] = cum_at(CU, it.offy - lane, r) * (kWScale * kDScale);
+      foldw[32 + lane] = cum_at(CU, 2 * r + 1 - (it.offy + it.EH - lane), r) * (kWScale * kDScale);
+    }
   }
   if (tid == 0) lookahead(0);
 
@@ -320,27 +330,43 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
         tmem_ld32(tmem + ((unsigned int)(32 * (warp & 3)) << 16) + 32 * h, d);
       }
       if (tile_on && ee >= 0 && ee < sl.sws) {
+        // V row (px, c), the 32 output rows contiguous: 4 x 16 bytes of hi
+        // and of lo fp16 parts
         const float et = it.foldT ? edge[b] : 0.0f, eb = it.foldB ? edge[256 + b] : 0.0f;
         const int px = ee / C, c = ee - px * C;
-        __half* vh = Vh + (size_t)(c * 32) * VP + px;
-        __half* vl = Vl + (size_t)(c * 32) * VP + px;
+        uint4* vh = reinterpret_cast<uint4*>(Vh + v_index<C, true>(c, 0, px));
+        uint4* vl = reinterpret_cast<uint4*>(Vl + v_index<C, true>(c, 0, px));
         #pragma unroll
-        for (int yo = 0; yo < 32; ++yo) {
-          float a = d[31 - yo];
-          if (it.foldT) a = fmaf(cum_at(CU, it.offy - yo, r) * (kWScale * kDScale), et, a);
-          if (it.foldB) a = fmaf(cum_at(CU, 2 * r + 1 - (it.offy + it.EH - yo), r) * (kWScale * kDScale), eb, a);
-          const float v = a * kVScale;
-          const __half hv = __float2half_rn(v);
-          vh[(size_t)yo * VP] = hv;
-          vl[(size_t)yo * VP] = __float2half_rn(v - __half2float(hv));
+        for (int q8 = 0; q8 < 4; ++q8) {
+          unsigned int hw[4], lw[4];
+          #pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int yo = 8 * q8 + 2 * j;
+            float a0v = d[31 - yo], a1v = d[30 - yo];
+            if (it.foldT) {
+              a0v = fmaf(foldw[yo], et, a0v);
+              a1v = fmaf(foldw[yo + 1], et, a1v);
+            }
+            if (it.foldB) {
+              a0v = fmaf(foldw[32 + yo], eb, a0v);
+              a1v = fmaf(foldw[33 + yo], eb, a1v);
+            }
+            const float v0 = a0v * kVScale, v1 = a1v * kVScale;
+            const __half2 h2 = __floats2half2_rn(v0, v1);
+            const float2 f2 = __half22float2(h2);
+            const __half2 l2 = __floats2half2_rn(v0 - f2.x, v1 - f2.y);
+            hw[j] = *reinterpret_cast<const unsigned int*>(&h2);
+            lw[j] = *reinterpret_cast<const unsigned int*>(&l2);
+          }
+          vh[q8] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          vl[q8] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
       }
-      // zero the columns px in [npx, npx16) that pass 2 reads
-      const int zc = npx16 - npx;
-      for (int idx = tid; idx < C * 32 * zc; idx += kThreads) {
-        const int row = idx / zc, px = npx + (idx - row * zc);
-        Vh[(size_t)row * VP + px] = __ushort_as_half(0);
-        Vl[(size_t)row * VP + px] = __ushort_as_half(0);
+      // zero the pixels px in [npx, npx16) that pass 2 reads
+      for (int idx = tid; idx < (npx16 - npx) * C * 4; idx += kThreads) {
+        const int row = npx * C + (idx >> 2), q8 = idx & 3;
+        reinterpret_cast<uint4*>(Vh + (size_t)row * kVtPitch)[q8] = make_uint4(0u, 0u, 0u, 0u);
+        reinterpret_cast<uint4*>(Vl + (size_t)row * kVtPitch)[q8] = make_uint4(0u, 0u, 0u, 0u);
       }
     }
     tc05_fence_before();
@@ -348,7 +374,7 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
       ok = false;
       break;
     }
-    tc_pass2_slab<C>(it, sl, Vh, Vl, CU, P, np, acc2);
+    tc_pass2_slab<C, true>(it, sl, Vh, Vl, CU, P, np, acc2);
   }
   if (!ok) {
     // a chunk never arrived or an MMA never finished: flag it, let what is
@@ -389,6 +415,7 @@ umma_forward_kernel(const __grid_constant__ FrameSource src, Workspace ws, int r
   float* CU = reinterpret_cast<float*>(smem + L.cum);
   unsigned int* P = reinterpret_cast<unsigned int*>(smem + L.pairs);
   float* edge = reinterpret_cast<float*>(smem + L.edge);
+  float* foldw = reinterpret_cast<float*>(smem + L.foldw);
   __shared__ __align__(8) unsigned long long s_bar[kMaxUmStages];
   __shared__ __align__(8) unsigned long long s_mma[2];
   __shared__ unsigned int s_tmem;
@@ -413,9 +440,9 @@ umma_forward_kernel(const __grid_constant__ FrameSource src, Workspace ws, int r
   tc05_fence_after();
   const unsigned int tmem = s_tmem;
   int gq0 = 0;
-  tc_item_loop<RB, C>(src, tmap1, ws, rmax, bl,
+  tc_item_loop<RB, C>(src, tmap1, ws, rmax, bl, reinterpret_cast<int*>(smem + L.starts),
                       [&](const Item& it, float c, const void* map, bool map_global, auto& lookahead) {
-                        return um_item<RB, C>(it, c, ring, A1, Vh, Vl, Sh, Sl, CU, P, edge, np, nent, tmem,
+                        return um_item<RB, C>(it, c, ring, A1, Vh, Vl, Sh, Sl, CU, P, edge, foldw, np, nent, tmem,
                                               s_tile_has, s_bar, s_mma, map, map_global, gq0,
                                               ws.counters + CNT_ERROR, lookahead);
                       });
@@ -457,7 +484,7 @@ int umma_forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int C) {
   if (rmax > kUmmaMaxRadius) return 0;
   const size_t smem = umma_forward_smem_bytes(cfg, rmax, C);
   void* k = pick_um(um_rb(cfg), C);
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  if (set_smem_attrs(reinterpret_cast<const void*>(k), smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -473,7 +500,7 @@ cudaError_t launch_umma_forward(const FrameSource& src, const Workspace& ws, con
                                 int grid, cudaStream_t s, const BucketList& bl, bool pdl, const void* tmap_one) {
   const size_t smem = umma_forward_smem_bytes(cfg, rmax, C);
   void* k = pick_um(um_rb(cfg), C);
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem_attrs(reinterpret_cast<const void*>(k), smem);
   if (e != cudaSuccess) return e;
   BucketList b = bl;
   CUtensorMap map;
