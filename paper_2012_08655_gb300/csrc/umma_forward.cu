@@ -20,6 +20,7 @@
 // tcgen05.ld, the clamp-to-edge folds of the top and bottom rows are added,
 // and V = D1 * 2^12 goes to shared memory as fp16 hi/lo rows for pass 2,
 // which runs on mma.sync exactly as in tc_forward.cu (tc_common.cuh).
+#include <algorithm>
 #include <cstring>
 
 #include "tc_common.cuh"
@@ -488,12 +489,24 @@ int umma_forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int C) {
     cudaGetLastError();
     return 0;
   }
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kThreads, smem) != cudaSuccess) {
+  // CTAs per SM from shared memory and registers. (The occupancy calculator
+  // answers 1 for a kernel that allocates tensor memory; each CTA here takes
+  // kTmemCols of the SM's 512 columns, so tensor memory is not the limit.)
+  int dev = 0, smem_sm = 0, reserved = 0;
+  cudaFuncAttributes fa;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, k) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
-  return n;
+  const size_t per_cta = smem + fa.sharedSizeBytes + (size_t)reserved;
+  const int by_smem = (int)((size_t)smem_sm / per_cta);
+  const int regs = ((fa.numRegs + 7) & ~7) * kThreads;
+  const int by_regs = regs > 0 ? 65536 / regs : 0;
+  const int by_tmem = 512 / kTmemCols;
+  return std::min(std::min(by_smem, by_regs), std::min(by_tmem, 2));
 }
 
 cudaError_t launch_umma_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg, int rmax, int C,
