@@ -63,6 +63,10 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
   return ok != 0;
 }
 
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Waits for the given phase parity of an mbarrier, at most kWaitLimit polls
 // (each poll may suspend for a short, hardware-chosen time). False: gave up.
 constexpr int kWaitLimit = 1 << 22;

@@ -145,8 +145,9 @@ template <int RB, int C, typename LookAhead>
 __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned char* ring, __half* A1, __half* Vh,
                                         __half* Vl, __half* Sh, __half* Sl, float* CU, unsigned int* P,
                                         float* edge, float* foldw, int np, int nent, unsigned int tmem,
-                                        int* s_tile_has,
-                                        unsigned long long* bars, unsigned long long* mbar_mma, const void* map,
+                                        int* s_tile_has, volatile int* s_abort,
+                                        unsigned long long* bars, unsigned long long* mbar_mma,
+                                        unsigned long long* conv_full, const void* map,
                                         bool map_in_global, int& gq0, unsigned int* err, LookAhead&& lookahead) {
   constexpr size_t stage_bytes = (size_t)RB * kRingRow;
   constexpr int kStages = um_stages(RB);
@@ -167,13 +168,13 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
     tma_load_2d(dst, map, x, y, bars + stg);
     tma_load_2d(dst + 128 * RB, map, x + 128, y, bars + stg);
   };
-  auto load_plain = [&](int qq) {  // all threads: rows that TMA cannot load
+  auto load_plain_conv = [&](int qq, int ct) {  // converter threads: rows that TMA cannot load
     const Slab cs = slab_of<true>(it, qq / it.nchunks);
     unsigned char* dst = ring + (size_t)((gq0 + qq) % kStages) * stage_bytes;
     const long long x0 = (long long)cs.src - cs.ph;
     const int nb = min(256, (cs.ph + cs.sws + 31) & ~31);
     const int y0 = it.gy0 - it.ph + (qq % it.nchunks) * RB;
-    for (int idx = threadIdx.x; idx < RB * nb; idx += kThreads) {
+    for (int idx = ct; idx < RB * nb; idx += kThreads - 32) {
       const int rho = idx / nb, b = idx - rho * nb;
       const int y = y0 + rho;
       const long long xb = x0 + b;
@@ -182,10 +183,11 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
       dst[ring_off<RB>(rho, b)] = v;
     }
   };
+  int issued = 0;  // thread 0: chunks of this item whose rows were requested
   if (map && tid == 0) {
     if (map_in_global) fence_tensormap_acquire(map);
     fence_proxy_async();
-    for (int q = 0; q < kStages - 1 && q < Q; ++q) issue(q);
+    for (; issued < kStages && issued < Q; ++issued) issue(issued);
   }
   {
     const float S = warp_tap_sum(r, c_tap);
@@ -207,117 +209,134 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
     #pragma unroll
     for (int k = 0; k < 4; ++k) acc2[i][k] = 0.f;
 
-  int q = 0;
+  // Within a slab the warps split roles: warps 1..7 convert chunks (wait for
+  // the chunk's rows, wait until the MMAs of two chunks back have released
+  // the A1 buffer, convert, arrive on conv_full), lane 0 of warp 0 issues
+  // (wait conv_full, refill the chunk's ring stage, issue its MMAs, commit to
+  // mma_done). Nobody waits for the slowest warp at every chunk; the CTA
+  // meets once per slab to read the accumulator back. Every wait is bounded;
+  // a timeout sets s_abort and the protocol continues (arrivals, commits) so
+  // that no one waits forever, and the item is abandoned at the slab's end.
+  const int vb = it.ph + it.EH - 1;
   bool ok = true;
-  int started[2] = {0, 0};  // thread 0: the slab's accumulation into M tile h has begun
-  int last_commit = -1;     // thread 0: global chunk of the latest MMA commit
-  for (; q < Q; ++q) {
-    const int gq = gq0 + q;
-    const int s = q / it.nchunks, k = q - s * it.nchunks;
+  int q = 0;
+  for (int s = 0; s < it.nsl && ok; ++s) {
     const Slab sl = slab_of<true>(it, s);
-    const int R0 = k * RB;
-    bool got = true;
-    if (map) {
-      got = mbar_wait(bars + gq % kStages, (unsigned int)(gq / kStages) & 1u);
-    } else {
-      __syncthreads();  // iteration q-1 finished everywhere
-      load_plain(q);
-      __syncthreads();
-    }
-    // the MMAs of chunk gq - 2 read the A1 buffer this chunk is converted into
-    if (gq >= 2) got = mbar_wait(&mbar_mma[gq & 1], (unsigned int)((gq - 2) >> 1) & 1u) && got;
-    const unsigned char* st = ring + (size_t)(gq % kStages) * stage_bytes;
-    __half* a1b = A1 + (size_t)(gq & 1) * kTileBytes;  // buffer gq % 2: two tiles of kTileBytes bytes
-    // ---- convert the chunk: 8 columns x 4 rows per work unit, transposed
-    // into K-major core matrices; stash the folded edge rows as floats
-    const int vb = it.ph + it.EH - 1;
-    for (int idx = tid; idx < 8 * RB; idx += kThreads) {
-      const int mi = (idx & 7) + ((idx >> 4) & 1) * 8;  // column group 0..15
-      const int half = (idx >> 3) & 1;                    // rows 0-3 or 4-7 of a core matrix
-      const int rest = idx >> 5;
-      const int ki = rest % (RB / 8), h = rest / (RB / 8);
-      const int b = 128 * h + 8 * mi;                     // first ring byte
-      if (b >= sl.ph + sl.sws || b + 8 <= sl.ph) continue;  // no slab byte here
-      const int v0 = 8 * ki + 4 * half;
-      uint2 w[4];
-      #pragma unroll
-      for (int j = 0; j < 4; ++j) w[j] = *reinterpret_cast<const uint2*>(st + ring_off<RB>(v0 + j, b));
-      #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int vv = R0 + v0 + j;
-        if ((k == 0 && vv == it.ph) || vv == vb) {
-          float* ed = edge + (vv == vb ? 256 : 0) + b;
-          #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            ed[i] = (float)((w[j].x >> (8 * i)) & 0xFFu);
-            ed[4 + i] = (float)((w[j].y >> (8 * i)) & 0xFFu);
+    const int qs = s * it.nchunks;  // first chunk of the slab
+    if (warp == 0) {
+      if (lane == 0) {
+        int started[2] = {0, 0};
+        for (int k = 0; k < it.nchunks; ++k) {
+          const int qq = qs + k, gq = gq0 + qq;
+          if (!mbar_wait(&conv_full[gq & 1], (unsigned int)(gq >> 1) & 1u)) *s_abort = 1;
+          tc05_fence_after();
+          if (map && qq + kStages < Q) {  // this chunk's stage is converted: refill it
+            issue(qq + kStages);
+            issued = qq + kStages + 1;
           }
+          const int R0 = k * RB;
+          __half* a1b = A1 + (size_t)(gq & 1) * kTileBytes;
+          for (int ks = 0; ks < RB / 16 && !*s_abort; ++ks) {
+            const int k0 = R0 + 16 * ks;
+            if (k0 >= it.vrows) break;
+            if (k0 + 15 < -D0 || k0 > 31 - D0 + 2 * r) continue;  // no tap of the 32 rows here
+            const int j0 = (k0 + D0 - 31 - delta1) / 8 + kXOff;
+            const unsigned long long bhi = umma_desc(Sh + (size_t)j0 * 64, 128, 128);
+            const unsigned long long blo = umma_desc(Sl + (size_t)j0 * 64, 128, 128);
+            #pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              if (128 * h >= sl.ph + sl.sws || 128 * h + 128 <= sl.ph) continue;
+              const unsigned long long ad = umma_desc(reinterpret_cast<unsigned char*>(a1b) +
+                                                          (size_t)h * kTileBytes + ks * 256, 128, a1_sbo(RB));
+              umma_f16(tmem + 32 * h, ad, bhi, kIdescM128N32, started[h]);
+              umma_f16(tmem + 32 * h, ad, blo, kIdescM128N32, 1u);
+              started[h] = 1;
+            }
+          }
+          umma_commit(&mbar_mma[gq & 1]);
         }
+        s_tile_has[0] = started[0];
+        s_tile_has[1] = started[1];
+        if (s == 0) lookahead(1);  // idle until the slab's MMAs finish anyway
       }
-      // rows (v0, v0+1) and (v0+2, v0+3) of column i -> two fp16 subnormal pairs
-      unsigned int o[8][2];
-      {
-        const unsigned int p01 = __byte_perm(w[0].x, w[1].x, 0x5140), p23 = __byte_perm(w[0].x, w[1].x, 0x7362);
-        const unsigned int q01 = __byte_perm(w[2].x, w[3].x, 0x5140), q23 = __byte_perm(w[2].x, w[3].x, 0x7362);
-        const unsigned int p45 = __byte_perm(w[0].y, w[1].y, 0x5140), p67 = __byte_perm(w[0].y, w[1].y, 0x7362);
-        const unsigned int q45 = __byte_perm(w[2].y, w[3].y, 0x5140), q67 = __byte_perm(w[2].y, w[3].y, 0x7362);
-        o[0][0] = __byte_perm(p01, 0u, 0x4140); o[0][1] = __byte_perm(q01, 0u, 0x4140);
-        o[1][0] = __byte_perm(p01, 0u, 0x4342); o[1][1] = __byte_perm(q01, 0u, 0x4342);
-        o[2][0] = __byte_perm(p23, 0u, 0x4140); o[2][1] = __byte_perm(q23, 0u, 0x4140);
-        o[3][0] = __byte_perm(p23, 0u, 0x4342); o[3][1] = __byte_perm(q23, 0u, 0x4342);
-        o[4][0] = __byte_perm(p45, 0u, 0x4140); o[4][1] = __byte_perm(q45, 0u, 0x4140);
-        o[5][0] = __byte_perm(p45, 0u, 0x4342); o[5][1] = __byte_perm(q45, 0u, 0x4342);
-        o[6][0] = __byte_perm(p67, 0u, 0x4140); o[6][1] = __byte_perm(q67, 0u, 0x4140);
-        o[7][0] = __byte_perm(p67, 0u, 0x4342); o[7][1] = __byte_perm(q67, 0u, 0x4342);
+      __syncwarp();
+    } else {
+      const int ct = tid - 32;  // converter thread 0..223
+      for (int k = 0; k < it.nchunks; ++k) {
+        const int qq = qs + k, gq = gq0 + qq;
+        const int R0 = k * RB;
+        if (map) {
+          if (!mbar_wait(bars + gq % kStages, (unsigned int)(gq / kStages) & 1u)) *s_abort = 1;
+        } else {
+          asm volatile("bar.sync 1, 224;" ::: "memory");  // converters done with this stage's old rows
+          load_plain_conv(qq, ct);
+          asm volatile("bar.sync 1, 224;" ::: "memory");
+        }
+        // the MMAs of chunk gq - 2 read the A1 buffer this chunk is converted into
+        if (gq >= 2 && !mbar_wait(&mbar_mma[gq & 1], (unsigned int)((gq - 2) >> 1) & 1u)) *s_abort = 1;
+        const unsigned char* st = ring + (size_t)(gq % kStages) * stage_bytes;
+        __half* a1b = A1 + (size_t)(gq & 1) * kTileBytes;
+        // ---- convert: 8 columns x 4 rows per work unit, transposed into
+        // K-major core matrices; stash the folded edge rows as floats
+        for (int idx = ct; idx < 8 * RB; idx += kThreads - 32) {
+          const int mi = (idx & 7) + ((idx >> 4) & 1) * 8;  // column group 0..15
+          const int half = (idx >> 3) & 1;                    // rows 0-3 or 4-7 of a core matrix
+          const int rest = idx >> 5;
+          const int ki = rest % (RB / 8), h = rest / (RB / 8);
+          const int b = 128 * h + 8 * mi;                     // first ring byte
+          if (b >= sl.ph + sl.sws || b + 8 <= sl.ph) continue;  // no slab byte here
+          const int v0 = 8 * ki + 4 * half;
+          uint2 w[4];
+          #pragma unroll
+          for (int j = 0; j < 4; ++j) w[j] = *reinterpret_cast<const uint2*>(st + ring_off<RB>(v0 + j, b));
+          #pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int vv = R0 + v0 + j;
+            if ((k == 0 && vv == it.ph) || vv == vb) {
+              float* ed = edge + (vv == vb ? 256 : 0) + b;
+              #pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                ed[i] = (float)((w[j].x >> (8 * i)) & 0xFFu);
+                ed[4 + i] = (float)((w[j].y >> (8 * i)) & 0xFFu);
+              }
+            }
+          }
+          // rows (v0, v0+1) and (v0+2, v0+3) of column i -> two fp16 subnormal pairs
+          unsigned int o[8][2];
+          {
+            const unsigned int p01 = __byte_perm(w[0].x, w[1].x, 0x5140), p23 = __byte_perm(w[0].x, w[1].x, 0x7362);
+            const unsigned int q01 = __byte_perm(w[2].x, w[3].x, 0x5140), q23 = __byte_perm(w[2].x, w[3].x, 0x7362);
+            const unsigned int p45 = __byte_perm(w[0].y, w[1].y, 0x5140), p67 = __byte_perm(w[0].y, w[1].y, 0x7362);
+            const unsigned int q45 = __byte_perm(w[2].y, w[3].y, 0x5140), q67 = __byte_perm(w[2].y, w[3].y, 0x7362);
+            o[0][0] = __byte_perm(p01, 0u, 0x4140); o[0][1] = __byte_perm(q01, 0u, 0x4140);
+            o[1][0] = __byte_perm(p01, 0u, 0x4342); o[1][1] = __byte_perm(q01, 0u, 0x4342);
+            o[2][0] = __byte_perm(p23, 0u, 0x4140); o[2][1] = __byte_perm(q23, 0u, 0x4140);
+            o[3][0] = __byte_perm(p23, 0u, 0x4342); o[3][1] = __byte_perm(q23, 0u, 0x4342);
+            o[4][0] = __byte_perm(p45, 0u, 0x4140); o[4][1] = __byte_perm(q45, 0u, 0x4140);
+            o[5][0] = __byte_perm(p45, 0u, 0x4342); o[5][1] = __byte_perm(q45, 0u, 0x4342);
+            o[6][0] = __byte_perm(p67, 0u, 0x4140); o[6][1] = __byte_perm(q67, 0u, 0x4140);
+            o[7][0] = __byte_perm(p67, 0u, 0x4342); o[7][1] = __byte_perm(q67, 0u, 0x4342);
+          }
+          unsigned char* dst = reinterpret_cast<unsigned char*>(a1b) + (size_t)h * kTileBytes + mi * a1_sbo(RB) +
+                               ki * 128 + half * 8;
+          #pragma unroll
+          for (int i = 0; i < 8; ++i) *reinterpret_cast<uint2*>(dst + i * 16) = make_uint2(o[i][0], o[i][1]);
+        }
+        fence_proxy_async();  // the converted chunk is read by the tensor cores
+        mbar_arrive(&conv_full[gq & 1]);
       }
-      unsigned char* dst = reinterpret_cast<unsigned char*>(a1b) + (size_t)h * kTileBytes + mi * a1_sbo(RB) +
-                           ki * 128 + half * 8;
-      #pragma unroll
-      for (int i = 0; i < 8; ++i) *reinterpret_cast<uint2*>(dst + i * 16) = make_uint2(o[i][0], o[i][1]);
     }
-    fence_proxy_async();  // the converted chunk is read by the tensor cores
-    tc05_fence_before();
-    got = __syncthreads_and(got) != 0;  // chunk converted everywhere; iteration q-1 finished
-    if (!got) {
+    q = qs + it.nchunks - 1;
+    // ---- slab complete: read D1 back, add the folded rows, V -> hi/lo fp16
+    const int gl = gq0 + q;  // the slab's last chunk
+    const bool done = __all_sync(0xffffffffu, mbar_wait(&mbar_mma[gl & 1], (unsigned int)(gl >> 1) & 1u));
+    if (!done) *s_abort = 1;
+    __syncthreads();  // s_tile_has, edge rows, abort flag visible
+    tc05_fence_after();
+    if (*s_abort) {
       ok = false;
       break;
     }
-    if (tid == 0) {
-      tc05_fence_after();
-      if (map && q + kStages - 1 < Q) issue(q + kStages - 1);
-      if (k == 0) started[0] = started[1] = 0;
-      // ---- pass 1 on the chunk: 16 staged rows per instruction, both M tiles
-      for (int ks = 0; ks < RB / 16; ++ks) {
-        const int k0 = R0 + 16 * ks;
-        if (k0 >= it.vrows) break;
-        if (k0 + 15 < -D0 || k0 > 31 - D0 + 2 * r) continue;  // no tap of the 32 rows here
-        const int j0 = (k0 + D0 - 31 - delta1) / 8 + kXOff;
-        const unsigned long long bhi = umma_desc(Sh + (size_t)j0 * 64, 128, 128);
-        const unsigned long long blo = umma_desc(Sl + (size_t)j0 * 64, 128, 128);
-        #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (128 * h >= sl.ph + sl.sws || 128 * h + 128 <= sl.ph) continue;
-          const unsigned long long ad = umma_desc(reinterpret_cast<unsigned char*>(a1b) + (size_t)h * kTileBytes +
-                                                      ks * 256, 128, a1_sbo(RB));
-          umma_f16(tmem + 32 * h, ad, bhi, kIdescM128N32, started[h]);
-          umma_f16(tmem + 32 * h, ad, blo, kIdescM128N32, 1u);
-          started[h] = 1;
-        }
-      }
-      umma_commit(&mbar_mma[gq & 1]);
-      last_commit = gq;
-      if (k == it.nchunks - 1) {
-        s_tile_has[0] = started[0];
-        s_tile_has[1] = started[1];
-      }
-    }
-    if (q == 0 && tid == 0) lookahead(1);
-    if (k != it.nchunks - 1) continue;
-
-    // ---- slab complete: read D1 back, add the folded rows, V -> hi/lo fp16
-    const bool done = __all_sync(0xffffffffu, mbar_wait(&mbar_mma[gq & 1], (unsigned int)(gq >> 1) & 1u));
-    __syncthreads();  // s_tile_has visible
-    tc05_fence_after();
     const int npx = sl.sws / C;
     const int npx16 = (npx + 15) & ~15;
     {
@@ -325,7 +344,7 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
       const int e = 32 * (warp & 3) + lane;    // its tensor-memory lane
       const int b = 128 * h + e;               // ring byte = slab element + ph
       const int ee = b - sl.ph;
-      const bool tile_on = done && s_tile_has[h] != 0;
+      const bool tile_on = s_tile_has[h] != 0;
       float d[32];
       if (tile_on) {
         tmem_ld32(tmem + ((unsigned int)(32 * (warp & 3)) << 16) + 32 * h, d);
@@ -371,22 +390,19 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
       }
     }
     tc05_fence_before();
-    if (__syncthreads_and(done ? 1 : 0) == 0) {  // also: D1 read everywhere before the next slab's MMAs
-      ok = false;
-      break;
-    }
+    __syncthreads();  // V complete; D1 read everywhere before the next slab's MMAs
     tc_pass2_slab<C, true>(it, sl, Vh, Vl, CU, P, np, acc2);
   }
   if (!ok) {
-    // a chunk never arrived or an MMA never finished: flag it, let what is
-    // still in flight land (bounded) and give up on the item
+    // a chunk never arrived or an MMA never finished: flag it, let the row
+    // loads still in flight land (bounded) and give up on the item; every
+    // arrival and commit was still made, so nobody else is left waiting
     if (tid == 0) {
       atomicOr(err, 64u);
-      for (int qq = q; qq < Q && qq < q + kStages - 1; ++qq) {
+      for (int qq = q + 1; qq < issued; ++qq) {
         const int g2 = gq0 + qq;
-        if (map) mbar_wait(bars + g2 % kStages, (unsigned int)(g2 / kStages) & 1u);
+        mbar_wait(bars + g2 % kStages, (unsigned int)(g2 / kStages) & 1u);
       }
-      if (last_commit >= 0) mbar_wait(&mbar_mma[last_commit & 1], (unsigned int)(last_commit >> 1) & 1u);
     }
     __syncthreads();
     return false;
@@ -419,6 +435,8 @@ umma_forward_kernel(const __grid_constant__ FrameSource src, Workspace ws, int r
   float* foldw = reinterpret_cast<float*>(smem + L.foldw);
   __shared__ __align__(8) unsigned long long s_bar[kMaxUmStages];
   __shared__ __align__(8) unsigned long long s_mma[2];
+  __shared__ __align__(8) unsigned long long s_conv[2];
+  __shared__ int s_abort;
   __shared__ unsigned int s_tmem;
   __shared__ int s_tile_has[2];
   const int np = npair(rmax);
@@ -427,6 +445,9 @@ umma_forward_kernel(const __grid_constant__ FrameSource src, Workspace ws, int r
     for (int i = 0; i < kMaxUmStages; ++i) mbar_init(&s_bar[i], 1);
     mbar_init(&s_mma[0], 1);
     mbar_init(&s_mma[1], 1);
+    mbar_init(&s_conv[0], kThreads - 32);  // every converter thread arrives once per chunk
+    mbar_init(&s_conv[1], kThreads - 32);
+    s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     fence_proxy_async();
   }
@@ -444,7 +465,7 @@ umma_forward_kernel(const __grid_constant__ FrameSource src, Workspace ws, int r
   tc_item_loop<RB, C>(src, tmap1, ws, rmax, bl, reinterpret_cast<int*>(smem + L.starts),
                       [&](const Item& it, float c, const void* map, bool map_global, auto& lookahead) {
                         return um_item<RB, C>(it, c, ring, A1, Vh, Vl, Sh, Sl, CU, P, edge, foldw, np, nent, tmem,
-                                              s_tile_has, s_bar, s_mma, map, map_global, gq0,
+                                              s_tile_has, &s_abort, s_bar, s_mma, s_conv, map, map_global, gq0,
                                               ws.counters + CNT_ERROR, lookahead);
                       });
   tc05_fence_before();
