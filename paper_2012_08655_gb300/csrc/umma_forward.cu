@@ -32,17 +32,17 @@ namespace {
 using namespace fwd;
 using namespace tcc;
 
-constexpr int kTmemCols = 64;      // D1: two M tiles x 32 fp32 columns
+constexpr int kTmemCols = 128;     // D1: two M tiles x 64 fp32 columns (hi and lo parts)
 constexpr int kXOff = 8;           // strip entry j holds Hankel index X = j - kXOff
-constexpr unsigned int kIdescM128N32 =
+constexpr unsigned int kIdescM128N64 =
     (1u << 4)                      // D format: f32
     | (0u << 7) | (0u << 10)       // A, B format: f16
     | (0u << 15) | (0u << 16)      // A, B K-major
-    | ((32u >> 3) << 17)           // N = 32
+    | ((64u >> 3) << 17)           // N = 64
     | ((128u >> 4) << 24);         // M = 128
 
-__host__ __device__ constexpr int um_stages(int rb) { return 96 / rb; }   // 96 staged rows
-constexpr int kMaxUmStages = 6;
+__host__ __device__ constexpr int um_stages(int rb) { return 192 / rb; }   // 192 staged rows
+constexpr int kMaxUmStages = 12;
 // A1 (pass-1 A operand), one M tile: 16 groups of 8 columns x RB/8 groups of
 // 8 rows; K-adjacent core matrices 128 bytes apart, M-adjacent ones
 // 16 RB + 16 bytes apart (the 16-byte skew keeps the conversion's 8-byte
@@ -65,9 +65,14 @@ __host__ __device__ inline UmLayout um_layout(int rb, int rmax, int C) {
   const size_t vbytes = (size_t)vt_rows(C) * kVtPitch * 2;
   L.ring = 0;                                                        // u8 [stages][2][rb][128] (swizzled)
   L.a1 = L.ring + (size_t)um_stages(rb) * rb * kRingRow;             // half: [2 buffers][2 tiles] A1
-  L.vh = L.a1 + (size_t)4 * a1_tile_bytes(rb);                       // half [C px + c][kVtPitch]
+  // V is written after a slab's last MMA has finished and read until the
+  // slab's end, when no chunk of the next slab has been converted yet: it
+  // shares its space with A1
+  L.vh = L.a1;                                                       // half [C px + c][kVtPitch]
   L.vl = L.vh + vbytes;
-  L.strip = L.vl + vbytes;                                           // half [2][entries][8][8]
+  const size_t a1b = (size_t)4 * a1_tile_bytes(rb);
+  const size_t a1v = a1b > 2 * vbytes ? a1b : 2 * vbytes;
+  L.strip = L.a1 + a1v;                                              // half [2][entries][8][8]
   L.cum = L.strip + (size_t)2 * strip_entries(rmax) * 128;           // float [cum_len]
   L.pairs = L.cum + (size_t)((cum_len(rmax) + 3) & ~3) * 4;          // uint32 [4][npair]
   L.edge = L.pairs + (size_t)4 * npair(rmax) * 4;                    // float [2][256]
@@ -124,18 +129,22 @@ __device__ __forceinline__ void tmem_ld32(unsigned int taddr, float (&d)[32]) {
   for (int i = 0; i < 32; ++i) d[i] = __uint_as_float(u[i]);
 }
 
-// Hankel strips of one item for pass 1: entry j, row rho, column i holds
-// the scaled tap u(8 (j - kXOff) + rho + i + delta) * 2^12, hi and lo fp16.
-__device__ __forceinline__ void make_strips(__half* Sh, __half* Sl, int nent, int r, float c, float S, int delta) {
+// Hankel strip of one item for pass 1: entry j is two 128-byte core
+// matrices, hi then lo, whose row rho, column i holds the hi / lo fp16 part
+// of the scaled tap u(8 (j - kXOff) + rho + i + delta) * 2^12. Read with N
+// groups 128 bytes apart and K groups 256 bytes apart, N group 2a' + p of
+// the MMA's B is part p (hi, lo) of the Hankel core matrix a' + b: one
+// N = 64 instruction computes both products.
+__device__ __forceinline__ void make_strips(__half* S2, int nent, int r, float c, float S, int delta) {
   for (int idx = threadIdx.x; idx < nent * 32; idx += kThreads) {
     const int j = idx >> 5, rho = (idx >> 2) & 7, i0 = (idx & 3) * 2;
     const int m0 = 8 * (j - kXOff) + rho + i0 + delta;
     const float w0 = tap_u(m0, r, c, S) * kWScale, w1 = tap_u(m0 + 1, r, c, S) * kWScale;
     const __half h0 = __float2half_rn(w0), h1 = __float2half_rn(w1);
     const __half l0 = __float2half_rn(w0 - __half2float(h0)), l1 = __float2half_rn(w1 - __half2float(h1));
-    const int o = j * 64 + rho * 8 + i0;
-    *reinterpret_cast<unsigned int*>(Sh + o) = pack_half2(h0, h1);
-    *reinterpret_cast<unsigned int*>(Sl + o) = pack_half2(l0, l1);
+    const int o = j * 128 + rho * 8 + i0;
+    *reinterpret_cast<unsigned int*>(S2 + o) = pack_half2(h0, h1);
+    *reinterpret_cast<unsigned int*>(S2 + o + 64) = pack_half2(l0, l1);
   }
 }
 
@@ -143,7 +152,7 @@ __device__ __forceinline__ void make_strips(__half* Sh, __half* Sl, int nent, in
 // buffer. gq0: chunks this CTA has staged so far (identical in all threads).
 template <int RB, int C, typename LookAhead>
 __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned char* ring, __half* A1, __half* Vh,
-                                        __half* Vl, __half* Sh, __half* Sl, float* CU, unsigned int* P,
+                                        __half* Vl, __half* Sh, float* CU, unsigned int* P,
                                         float* edge, float* foldw, int np, int nent, unsigned int tmem,
                                         int* s_tile_has, volatile int* s_abort,
                                         unsigned long long* bars, unsigned long long* mbar_mma,
@@ -192,7 +201,7 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
   {
     const float S = warp_tap_sum(r, c_tap);
     make_pairs(P, r, c_tap, S, np);
-    make_strips(Sh, Sl, nent, r, c_tap, S, delta1);
+    make_strips(Sh, nent, r, c_tap, S, delta1);
     if ((it.foldT || it.foldB || it.foldL || it.foldR) && warp == kThreads / 32 - 1) {
       make_cumulative_tc(CU, r, c_tap, S);
       __syncwarp();
@@ -241,15 +250,13 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
             if (k0 >= it.vrows) break;
             if (k0 + 15 < -D0 || k0 > 31 - D0 + 2 * r) continue;  // no tap of the 32 rows here
             const int j0 = (k0 + D0 - 31 - delta1) / 8 + kXOff;
-            const unsigned long long bhi = umma_desc(Sh + (size_t)j0 * 64, 128, 128);
-            const unsigned long long blo = umma_desc(Sl + (size_t)j0 * 64, 128, 128);
+            const unsigned long long bd = umma_desc(Sh + (size_t)j0 * 128, 256, 128);
             #pragma unroll
             for (int h = 0; h < 2; ++h) {
               if (128 * h >= sl.ph + sl.sws || 128 * h + 128 <= sl.ph) continue;
               const unsigned long long ad = umma_desc(reinterpret_cast<unsigned char*>(a1b) +
                                                           (size_t)h * kTileBytes + ks * 256, 128, a1_sbo(RB));
-              umma_f16(tmem + 32 * h, ad, bhi, kIdescM128N32, started[h]);
-              umma_f16(tmem + 32 * h, ad, blo, kIdescM128N32, 1u);
+              umma_f16(tmem + 64 * h, ad, bd, kIdescM128N64, started[h]);
               started[h] = 1;
             }
           }
@@ -346,8 +353,20 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
       const int ee = b - sl.ph;
       const bool tile_on = s_tile_has[h] != 0;
       float d[32];
-      if (tile_on) {
-        tmem_ld32(tmem + ((unsigned int)(32 * (warp & 3)) << 16) + 32 * h, d);
+      if (tile_on) {  // column 16 a' + 8 p + rho: part p of output row 31 - (8 a' + rho)
+        float dd[32];
+        tmem_ld32(tmem + ((unsigned int)(32 * (warp & 3)) << 16) + 64 * h, d);
+        tmem_ld32(tmem + ((unsigned int)(32 * (warp & 3)) << 16) + 64 * h + 32, dd);
+        float t[32];
+        #pragma unroll
+        for (int a = 0; a < 2; ++a)
+          #pragma unroll
+          for (int rho = 0; rho < 8; ++rho) {
+            t[8 * a + rho] = d[16 * a + rho] + d[16 * a + 8 + rho];
+            t[16 + 8 * a + rho] = dd[16 * a + rho] + dd[16 * a + 8 + rho];
+          }
+        #pragma unroll
+        for (int n = 0; n < 32; ++n) d[n] = t[n];
       }
       if (tile_on && ee >= 0 && ee < sl.sws) {
         // V row (px, c), the 32 output rows contiguous: 4 x 16 bytes of hi
@@ -392,6 +411,7 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
     tc05_fence_before();
     __syncthreads();  // V complete; D1 read everywhere before the next slab's MMAs
     tc_pass2_slab<C, true>(it, sl, Vh, Vl, CU, P, np, acc2);
+    __syncthreads();  // V (the A1 space) read everywhere before the next slab's chunks are converted
   }
   if (!ok) {
     // a chunk never arrived or an MMA never finished: flag it, let the row
@@ -427,8 +447,7 @@ umma_forward_kernel(const __grid_constant__ FrameSource src, Workspace ws, int r
   __half* Vh = reinterpret_cast<__half*>(smem + L.vh);
   __half* Vl = reinterpret_cast<__half*>(smem + L.vl);
   const int nent = strip_entries(rmax);
-  __half* Sh = reinterpret_cast<__half*>(smem + L.strip);
-  __half* Sl = Sh + (size_t)nent * 64;
+  __half* Sh = reinterpret_cast<__half*>(smem + L.strip);  // interleaved hi / lo strip
   float* CU = reinterpret_cast<float*>(smem + L.cum);
   unsigned int* P = reinterpret_cast<unsigned int*>(smem + L.pairs);
   float* edge = reinterpret_cast<float*>(smem + L.edge);
@@ -464,7 +483,7 @@ umma_forward_kernel(const __grid_constant__ FrameSource src, Workspace ws, int r
   int gq0 = 0;
   tc_item_loop<RB, C>(src, tmap1, ws, rmax, bl, reinterpret_cast<int*>(smem + L.starts),
                       [&](const Item& it, float c, const void* map, bool map_global, auto& lookahead) {
-                        return um_item<RB, C>(it, c, ring, A1, Vh, Vl, Sh, Sl, CU, P, edge, foldw, np, nent, tmem,
+                        return um_item<RB, C>(it, c, ring, A1, Vh, Vl, Sh, CU, P, edge, foldw, np, nent, tmem,
                                               s_tile_has, &s_abort, s_bar, s_mma, s_conv, map, map_global, gq0,
                                               ws.counters + CNT_ERROR, lookahead);
                       });
