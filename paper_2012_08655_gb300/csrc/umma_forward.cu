@@ -41,8 +41,11 @@ constexpr unsigned int kIdescM128N64 =
     | ((64u >> 3) << 17)           // N = 64
     | ((128u >> 4) << 24);         // M = 128
 
-__host__ __device__ constexpr int um_stages(int rb) { return 192 / rb; }   // 192 staged rows
-constexpr int kMaxUmStages = 12;
+__host__ __device__ constexpr int um_stages(int rb) { return 96 / rb; }   // 96 staged rows
+constexpr int kMaxUmStages = 6;
+// A1 buffers: converted chunks waiting for (or read by) their MMAs; the
+// converting warps may run this many chunks ahead of the tensor core.
+constexpr int kA1Bufs = 4;
 // A1 (pass-1 A operand), one M tile: 16 groups of 8 columns x RB/8 groups of
 // 8 rows; K-adjacent core matrices 128 bytes apart, M-adjacent ones
 // 16 RB + 16 bytes apart (the 16-byte skew keeps the conversion's 8-byte
@@ -70,7 +73,7 @@ __host__ __device__ inline UmLayout um_layout(int rb, int rmax, int C) {
   // shares its space with A1
   L.vh = L.a1;                                                       // half [C px + c][kVtPitch]
   L.vl = L.vh + vbytes;
-  const size_t a1b = (size_t)4 * a1_tile_bytes(rb);
+  const size_t a1b = (size_t)2 * kA1Bufs * a1_tile_bytes(rb);
   const size_t a1v = a1b > 2 * vbytes ? a1b : 2 * vbytes;
   L.strip = L.a1 + a1v;                                              // half [2][entries][8][8]
   L.cum = L.strip + (size_t)2 * strip_entries(rmax) * 128;           // float [cum_len]
@@ -148,8 +151,8 @@ __device__ __forceinline__ void make_strips(__half* S2, int nent, int r, float c
   }
 }
 
-// One item. bars: TMA ring stages; mbar_mma[2]: MMA completion per A1
-// buffer. gq0: chunks this CTA has staged so far (identical in all threads).
+// One item. bars: TMA ring stages; mbar_mma / conv_full[kA1Bufs]: MMA
+// completion and conversion completion per A1 buffer. gq0: chunks this CTA has staged so far (identical in all threads).
 template <int RB, int C, typename LookAhead>
 __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned char* ring, __half* A1, __half* Vh,
                                         __half* Vl, __half* Sh, float* CU, unsigned int* P,
@@ -237,14 +240,14 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
         int started[2] = {0, 0};
         for (int k = 0; k < it.nchunks; ++k) {
           const int qq = qs + k, gq = gq0 + qq;
-          if (!mbar_wait(&conv_full[gq & 1], (unsigned int)(gq >> 1) & 1u)) *s_abort = 1;
+          if (!mbar_wait(&conv_full[gq % kA1Bufs], (unsigned int)(gq / kA1Bufs) & 1u)) *s_abort = 1;
           tc05_fence_after();
           if (map && qq + kStages < Q) {  // this chunk's stage is converted: refill it
             issue(qq + kStages);
             issued = qq + kStages + 1;
           }
           const int R0 = k * RB;
-          __half* a1b = A1 + (size_t)(gq & 1) * kTileBytes;
+          __half* a1b = A1 + (size_t)(gq % kA1Bufs) * kTileBytes;
           for (int ks = 0; ks < RB / 16 && !*s_abort; ++ks) {
             const int k0 = R0 + 16 * ks;
             if (k0 >= it.vrows) break;
@@ -260,7 +263,7 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
               started[h] = 1;
             }
           }
-          umma_commit(&mbar_mma[gq & 1]);
+          umma_commit(&mbar_mma[gq % kA1Bufs]);
         }
         s_tile_has[0] = started[0];
         s_tile_has[1] = started[1];
@@ -279,10 +282,11 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
           load_plain_conv(qq, ct);
           asm volatile("bar.sync 1, 224;" ::: "memory");
         }
-        // the MMAs of chunk gq - 2 read the A1 buffer this chunk is converted into
-        if (gq >= 2 && !mbar_wait(&mbar_mma[gq & 1], (unsigned int)((gq - 2) >> 1) & 1u)) *s_abort = 1;
+        // the MMAs of chunk gq - kA1Bufs read the A1 buffer this chunk is converted into
+        if (gq >= kA1Bufs && !mbar_wait(&mbar_mma[gq % kA1Bufs], (unsigned int)((gq - kA1Bufs) / kA1Bufs) & 1u))
+          *s_abort = 1;
         const unsigned char* st = ring + (size_t)(gq % kStages) * stage_bytes;
-        __half* a1b = A1 + (size_t)(gq & 1) * kTileBytes;
+        __half* a1b = A1 + (size_t)(gq % kA1Bufs) * kTileBytes;
         // ---- convert: 8 columns x 4 rows per work unit, transposed into
         // K-major core matrices; stash the folded edge rows as floats
         for (int idx = ct; idx < 8 * RB; idx += kThreads - 32) {
@@ -330,13 +334,14 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
           for (int i = 0; i < 8; ++i) *reinterpret_cast<uint2*>(dst + i * 16) = make_uint2(o[i][0], o[i][1]);
         }
         fence_proxy_async();  // the converted chunk is read by the tensor cores
-        mbar_arrive(&conv_full[gq & 1]);
+        mbar_arrive(&conv_full[gq % kA1Bufs]);
       }
     }
     q = qs + it.nchunks - 1;
     // ---- slab complete: read D1 back, add the folded rows, V -> hi/lo fp16
     const int gl = gq0 + q;  // the slab's last chunk
-    const bool done = __all_sync(0xffffffffu, mbar_wait(&mbar_mma[gl & 1], (unsigned int)(gl >> 1) & 1u));
+    const bool done =
+        __all_sync(0xffffffffu, mbar_wait(&mbar_mma[gl % kA1Bufs], (unsigned int)(gl / kA1Bufs) & 1u));
     if (!done) *s_abort = 1;
     __syncthreads();  // s_tile_has, edge rows, abort flag visible
     tc05_fence_after();
@@ -453,8 +458,8 @@ umma_forward_kernel(const __grid_constant__ FrameSource src, Workspace ws, int r
   float* edge = reinterpret_cast<float*>(smem + L.edge);
   float* foldw = reinterpret_cast<float*>(smem + L.foldw);
   __shared__ __align__(8) unsigned long long s_bar[kMaxUmStages];
-  __shared__ __align__(8) unsigned long long s_mma[2];
-  __shared__ __align__(8) unsigned long long s_conv[2];
+  __shared__ __align__(8) unsigned long long s_mma[kA1Bufs];
+  __shared__ __align__(8) unsigned long long s_conv[kA1Bufs];
   __shared__ int s_abort;
   __shared__ unsigned int s_tmem;
   __shared__ int s_tile_has[2];
@@ -462,10 +467,10 @@ umma_forward_kernel(const __grid_constant__ FrameSource src, Workspace ws, int r
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     for (int i = 0; i < kMaxUmStages; ++i) mbar_init(&s_bar[i], 1);
-    mbar_init(&s_mma[0], 1);
-    mbar_init(&s_mma[1], 1);
-    mbar_init(&s_conv[0], kThreads - 32);  // every converter thread arrives once per chunk
-    mbar_init(&s_conv[1], kThreads - 32);
+    for (int i = 0; i < kA1Bufs; ++i) {
+      mbar_init(&s_mma[i], 1);
+      mbar_init(&s_conv[i], kThreads - 32);  // every converter thread arrives once per chunk
+    }
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     fence_proxy_async();
