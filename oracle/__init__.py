@@ -65,6 +65,18 @@ def _load():
             lib.oracle_quantize_u8.restype = None
             lib.oracle_max_threads.argtypes = []
             lib.oracle_max_threads.restype = i
+            lib.oracle_sigma_table_ex.argtypes = [i, i, i, i, i, d, d, d, d, p, p, p]
+            lib.oracle_sigma_table_ex.restype = None
+            lib.oracle_forward_ex.argtypes = [p, p, i, i, i, l, l, l, i, i, i, d, d, d, d, p, p, i, i]
+            lib.oracle_forward_ex.restype = None
+            lib.oracle_adjoint_ex.argtypes = [p, p, i, i, i, l, l, l, i, i, i, d, d, d, d, p, i]
+            lib.oracle_adjoint_ex.restype = None
+            lib.oracle_gp_sigma.argtypes = [d, i, i, d]
+            lib.oracle_gp_sigma.restype = d
+            lib.oracle_gp_linear.argtypes = [i, i, d, ctypes.POINTER(d), ctypes.POINTER(d)]
+            lib.oracle_gp_linear.restype = None
+            lib.oracle_centred_origin.argtypes = [d, i]
+            lib.oracle_centred_origin.restype = i
             _lib = lib
     return _lib
 
@@ -74,19 +86,50 @@ def max_threads() -> int:
     return int(_load().oracle_max_threads())
 
 
-def grid_shape(width: int, height: int, block: int) -> tuple[int, int]:
-    """(blocks along y, blocks along x)."""
-    return (height + block - 1) // block, (width + block - 1) // block
+def grid_shape(width: int, height: int, block: int, origin=(0, 0)) -> tuple[int, int]:
+    """(blocks along y, blocks along x) for grid origin offsets (ox, oy)."""
+    ox, oy = origin
+    return (height + oy + block - 1) // block, (width + ox + block - 1) // block
 
 
-def sigma_table(width, height, block, fix_x, fix_y, sigma0, k):
-    """Per-block sigma (float64) and radius (int32), shape (nby, nbx)."""
-    nby, nbx = grid_shape(width, height, block)
+def _map_arg(sigma_map, shape):
+    if sigma_map is None:
+        return None, None
+    m = np.ascontiguousarray(np.asarray(sigma_map, dtype=np.float64))
+    if m.shape != shape:
+        raise ValueError(f"sigma map of shape {m.shape}, expected {shape}")
+    return m, m.ctypes.data
+
+
+def sigma_table(width, height, block, fix_x, fix_y, sigma0, k, origin=(0, 0), sigma_map=None):
+    """Per-block sigma (float64) and radius (int32), shape (nby, nbx).
+
+    ``origin`` = (ox, oy): grid origin offsets; ``sigma_map``: per-block
+    sigma replacing the law."""
+    nby, nbx = grid_shape(width, height, block, origin)
     sig = np.zeros((nby, nbx), np.float64)
     rad = np.zeros((nby, nbx), np.int32)
-    _load().oracle_sigma_table(width, height, block, float(fix_x), float(fix_y), float(sigma0),
-                               float(k), sig.ctypes.data, rad.ctypes.data)
+    keep, mp = _map_arg(sigma_map, (nby, nbx))
+    _load().oracle_sigma_table_ex(width, height, block, int(origin[0]), int(origin[1]), float(fix_x), float(fix_y),
+                                  float(sigma0), float(k), mp, sig.ctypes.data, rad.ctypes.data)
     return sig, rad
+
+
+def gp_sigma(d, width, height, e_corner):
+    """Geisler-Perry sigma at pixel distance d, by the literal chain of Eqs. 2-6."""
+    return float(_load().oracle_gp_sigma(float(d), int(width), int(height), float(e_corner)))
+
+
+def gp_linear(width, height, e_corner):
+    """(sigma0, k) of the Geisler-Perry law written as sigma = sigma0 + k d."""
+    s0, k = ctypes.c_double(), ctypes.c_double()
+    _load().oracle_gp_linear(int(width), int(height), float(e_corner), ctypes.byref(s0), ctypes.byref(k))
+    return s0.value, k.value
+
+
+def centred_origin(fix, block):
+    """Grid origin offset that centres a fragment on fixation coordinate ``fix``."""
+    return int(_load().oracle_centred_origin(float(fix), int(block)))
 
 
 def taps(sigma: float, r: int) -> np.ndarray:
@@ -110,12 +153,14 @@ def _geometry(img: np.ndarray, layout: str):
     raise ValueError(f"unknown layout {layout!r}")
 
 
-def forward(img, block, fix_x, fix_y, sigma0, k, layout="hwc", blocks=None, nthreads=0):
+def forward(img, block, fix_x, fix_y, sigma0, k, layout="hwc", blocks=None, nthreads=0, origin=(0, 0),
+            sigma_map=None):
     """Foveated blur of one image in binary64.
 
     ``img`` is (H, W), (H, W, C) for layout 'hwc' or (C, H, W) for 'chw'; any
     real dtype (converted exactly to float64). ``blocks`` optionally lists
     row-major block indices to compute; other pixels of the result are NaN.
+    ``origin`` / ``sigma_map`` as in :func:`sigma_table`.
     """
     x = np.ascontiguousarray(img, dtype=np.float64)
     H, W, C, sy, sx, sc = _geometry(x, layout)
@@ -125,18 +170,21 @@ def forward(img, block, fix_x, fix_y, sigma0, k, layout="hwc", blocks=None, nthr
     else:
         barr = np.ascontiguousarray(np.asarray(blocks, dtype=np.int32))
         bl, nl = barr.ctypes.data, int(barr.size)
-    _load().oracle_forward(x.ctypes.data, out.ctypes.data, W, H, C, sy, sx, sc, int(block),
-                           float(fix_x), float(fix_y), float(sigma0), float(k), bl, nl, int(nthreads))
+    keep, mp = _map_arg(sigma_map, grid_shape(W, H, block, origin))
+    _load().oracle_forward_ex(x.ctypes.data, out.ctypes.data, W, H, C, sy, sx, sc, int(block), int(origin[0]),
+                              int(origin[1]), float(fix_x), float(fix_y), float(sigma0), float(k), mp, bl, nl,
+                              int(nthreads))
     return out
 
 
-def adjoint(g_out, block, fix_x, fix_y, sigma0, k, layout="chw", nthreads=0):
+def adjoint(g_out, block, fix_x, fix_y, sigma0, k, layout="chw", nthreads=0, origin=(0, 0), sigma_map=None):
     """Transpose of :func:`forward` applied to ``g_out`` (binary64)."""
     g = np.ascontiguousarray(g_out, dtype=np.float64)
     H, W, C, sy, sx, sc = _geometry(g, layout)
     out = np.zeros_like(g)
-    _load().oracle_adjoint(g.ctypes.data, out.ctypes.data, W, H, C, sy, sx, sc, int(block),
-                           float(fix_x), float(fix_y), float(sigma0), float(k), int(nthreads))
+    keep, mp = _map_arg(sigma_map, grid_shape(W, H, block, origin))
+    _load().oracle_adjoint_ex(g.ctypes.data, out.ctypes.data, W, H, C, sy, sx, sc, int(block), int(origin[0]),
+                              int(origin[1]), float(fix_x), float(fix_y), float(sigma0), float(k), mp, int(nthreads))
     return out
 
 
@@ -148,10 +196,11 @@ def quantize_u8(v) -> np.ndarray:
     return q
 
 
-def forward_u8(img_u8, block, fix_x, fix_y, sigma0, k, layout="hwc", blocks=None, nthreads=0):
+def forward_u8(img_u8, block, fix_x, fix_y, sigma0, k, layout="hwc", blocks=None, nthreads=0, origin=(0, 0),
+               sigma_map=None):
     """Foveated blur of a uint8 image, coded back to uint8.
 
     With ``blocks`` given, pixels outside the listed blocks come back as 0.
     """
-    v = forward(img_u8, block, fix_x, fix_y, sigma0, k, layout, blocks, nthreads)
+    v = forward(img_u8, block, fix_x, fix_y, sigma0, k, layout, blocks, nthreads, origin, sigma_map)
     return quantize_u8(np.nan_to_num(v, nan=0.0))

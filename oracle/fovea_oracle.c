@@ -22,7 +22,13 @@
  *  - Sigma law: sigma_b = sigma0 + k * e_b, e_b the Euclidean distance in
  *    pixels from the block centre to the fixation. (The Geisler-Perry law of
  *    Appendix "Choosing the Standard Deviation", Eqs. 2-6, is linear in the
- *    pixel distance, so it is an instance of this form.)
+ *    pixel distance, so it is an instance of this form; oracle_gp_sigma
+ *    evaluates its chain of equations literally and oracle_gp_linear gives
+ *    the two coefficients.) Alternatively a per-block sigma map.
+ *  - Block grid: block (bx, by) covers pixels x in [B bx - ox, B bx - ox + B)
+ *    clipped to the frame (likewise in y), with an origin offset 0 <= ox < B
+ *    (0: the grid starts at the frame corner; Algorithm 1 shifts it so that
+ *    a fragment is centred on the fixation, see oracle_centred_origin).
  *
  * The forward map is written as the DIRECT 2D double sum over the
  * (2r+1) x (2r+1) normalised 2D kernel for every output pixel -- no
@@ -51,17 +57,22 @@
 #include <omp.h>
 #endif
 
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
 /* Centre of block index b along one axis: B*b + B/2 in continuous pixel
  * coordinates (pixel x covers [x, x+1)); nominal even for a partial edge
  * block (Section 2: "distance from its midpoint to the point of fixation"). */
 static double block_centre(int b, int B) { return (double)B * (double)b + 0.5 * (double)B; }
 
 /* Sigma and radius of one block (Section 2; Eq. 5 makes eccentricity linear in
- * pixel distance, and the linear law sigma = sigma0 + k*e follows). */
-static void block_sigma(int bx, int by, int B, double fx, double fy, double sigma0, double k,
-                        double* sigma, int* radius) {
-  double dx = block_centre(bx, B) - fx;
-  double dy = block_centre(by, B) - fy;
+ * pixel distance, and the linear law sigma = sigma0 + k*e follows). The
+ * block centre is B*b + B/2 - o along each axis for grid origin offset o. */
+static void block_sigma_o(int bx, int by, int B, int ox, int oy, double fx, double fy, double sigma0, double k,
+                          double* sigma, int* radius) {
+  double dx = (block_centre(bx, B) - (double)ox) - fx;
+  double dy = (block_centre(by, B) - (double)oy) - fy;
   double dx2 = dx * dx;
   double dy2 = dy * dy;
   double e = sqrt(dx2 + dy2);
@@ -72,18 +83,93 @@ static void block_sigma(int bx, int by, int B, double fx, double fy, double sigm
   *radius = (int)ceil(three_s);
 }
 
+static void block_sigma(int bx, int by, int B, double fx, double fy, double sigma0, double k,
+                        double* sigma, int* radius) {
+  block_sigma_o(bx, by, B, 0, 0, fx, fy, sigma0, k, sigma, radius);
+}
+
+/* Blocks along an axis of n pixels with origin offset o: ceil((n + o) / B). */
+static int grid_count(int n, int B, int o) { return (n + o + B - 1) / B; }
+
+/* Pixel range [*a0, *a1) of block index b along an axis of n pixels. */
+static void block_span(int b, int B, int o, int n, int* a0, int* a1) {
+  int s = B * b - o;
+  *a0 = s < 0 ? 0 : s;
+  *a1 = s + B < n ? s + B : n;
+}
+
+/* Sigma of one block: from the law, or map[by * nbx + bx] when map != NULL
+ * (r = ceil(3 sigma) either way). */
+static void block_sigma_any(int bx, int by, int nbx, int B, int ox, int oy, double fx, double fy,
+                            double sigma0, double k, const double* map, double* sigma, int* radius) {
+  if (map) {
+    double s = map[by * nbx + bx];
+    double three_s = 3.0 * s;
+    *sigma = s;
+    *radius = (int)ceil(three_s);
+  } else {
+    block_sigma_o(bx, by, B, ox, oy, fx, fy, sigma0, k, sigma, radius);
+  }
+}
+
+/* Geisler-Perry chain (Appendix "Choosing the Standard Deviation"), taken
+ * step by step for a pixel at distance d from the fixation in a W x H frame
+ * whose corner is at eccentricity e_corner degrees:
+ *   Eq. 5  e = d / d_corner * e_corner,  d_corner = half the frame diagonal
+ *   Eq. 3  f_c_deg = e2 / (alpha (e + e2)) ln(1 / CT0)   (Eq. 2 set to 1)
+ *          f_max = f_c_deg at e = 0 (highest acuity, at the fovea)
+ *   Eq. 4  f_c_pix = 0.5 f_c_deg / f_max
+ *   Eq. 6  sigma = 1 / (2 pi f_c_pix)
+ * with alpha = 0.106, e2 = 2.3, CT0 = 1/64. */
+double oracle_gp_sigma(double d, int W, int H, double e_corner) {
+  const double alpha = 0.106, e2 = 2.3, ct0 = 1.0 / 64.0;
+  double d_corner = 0.5 * sqrt((double)W * (double)W + (double)H * (double)H);
+  double e = d / d_corner * e_corner;
+  double f_c_deg = e2 / (alpha * (e + e2)) * log(1.0 / ct0);
+  double f_max = e2 / (alpha * (0.0 + e2)) * log(1.0 / ct0);
+  double f_c_pix = 0.5 * f_c_deg / f_max;
+  return 1.0 / (2.0 * M_PI * f_c_pix);
+}
+
+/* The same law as sigma = sigma0 + k d: the chain above reduces to
+ * sigma = (1 + e / e2) / pi, so sigma0 = 1 / pi and
+ * k = e_corner / ((pi e2) d_corner). */
+void oracle_gp_linear(int W, int H, double e_corner, double* sigma0, double* k) {
+  const double e2 = 2.3;
+  double d_corner = 0.5 * sqrt((double)W * (double)W + (double)H * (double)H);
+  *sigma0 = 1.0 / M_PI;
+  *k = e_corner / ((M_PI * e2) * d_corner);
+}
+
+/* Grid origin offset that centres a fragment on the fixation (Algorithm 1,
+ * Section 3.1), to the nearest pixel: the fragment starting at
+ * floor(f + 1/2) - floor(B/2) is a whole block, so
+ * o = (floor(B/2) - floor(f + 1/2)) mod B. */
+int oracle_centred_origin(double f, int B) {
+  long c = (long)floor(f + 0.5);
+  long o = ((long)(B / 2) - c) % B;
+  if (o < 0) o += B;
+  return (int)o;
+}
+
 int oracle_num_blocks(int W, int H, int B) {
   if (W <= 0 || H <= 0 || B <= 0) return 0;
   return ((W + B - 1) / B) * ((H + B - 1) / B);
 }
 
 /* Per-block sigma and radius, row-major over the block grid. */
-void oracle_sigma_table(int W, int H, int B, double fx, double fy, double sigma0, double k,
-                        double* sigma_out, int* radius_out) {
-  int nbx = (W + B - 1) / B, nby = (H + B - 1) / B;
+void oracle_sigma_table_ex(int W, int H, int B, int ox, int oy, double fx, double fy, double sigma0, double k,
+                           const double* map, double* sigma_out, int* radius_out) {
+  int nbx = grid_count(W, B, ox), nby = grid_count(H, B, oy);
   for (int by = 0; by < nby; ++by)
     for (int bx = 0; bx < nbx; ++bx)
-      block_sigma(bx, by, B, fx, fy, sigma0, k, &sigma_out[by * nbx + bx], &radius_out[by * nbx + bx]);
+      block_sigma_any(bx, by, nbx, B, ox, oy, fx, fy, sigma0, k, map, &sigma_out[by * nbx + bx],
+                      &radius_out[by * nbx + bx]);
+}
+
+void oracle_sigma_table(int W, int H, int B, double fx, double fy, double sigma0, double k,
+                        double* sigma_out, int* radius_out) {
+  oracle_sigma_table_ex(W, H, B, 0, 0, fx, fy, sigma0, k, NULL, sigma_out, radius_out);
 }
 
 /* Normalised 1D taps w[0..2r] for offsets -r..r (Eq. 1 sampled at integer
@@ -105,10 +191,10 @@ static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v
 /* Forward map over a list of blocks (all blocks when block_list is NULL).
  * Element (x, y, c) lives at base[y*sy + x*sx + c*sc] for both in and out.
  * Only the pixels of the listed blocks are written. */
-void oracle_forward(const double* in, double* out, int W, int H, int C, long sy, long sx, long sc,
-                    int B, double fx, double fy, double sigma0, double k,
-                    const int* block_list, int nlist, int nthreads) {
-  int nbx = (W + B - 1) / B, nby = (H + B - 1) / B;
+void oracle_forward_ex(const double* in, double* out, int W, int H, int C, long sy, long sx, long sc,
+                       int B, int ox, int oy, double fx, double fy, double sigma0, double k, const double* map,
+                       const int* block_list, int nlist, int nthreads) {
+  int nbx = grid_count(W, B, ox), nby = grid_count(H, B, oy);
   int nb = block_list ? nlist : nbx * nby;
   int nt = 1;
 #ifdef _OPENMP
@@ -122,15 +208,16 @@ void oracle_forward(const double* in, double* out, int W, int H, int C, long sy,
       int bx = b % nbx, by = b / nbx;
       double sigma;
       int r;
-      block_sigma(bx, by, B, fx, fy, sigma0, k, &sigma, &r);
+      block_sigma_any(bx, by, nbx, B, ox, oy, fx, fy, sigma0, k, map, &sigma, &r);
       size_t n = (size_t)(2 * r + 1);
       double* w = (double*)malloc(n * sizeof(double));
       double* K = (double*)malloc(n * n * sizeof(double));
       oracle_taps(sigma, r, w);
       for (size_t j = 0; j < n; ++j)
         for (size_t i = 0; i < n; ++i) K[j * n + i] = w[i] * w[j];
-      int x0 = bx * B, y0 = by * B;
-      int x1 = x0 + B < W ? x0 + B : W, y1 = y0 + B < H ? y0 + B : H;
+      int x0, x1, y0, y1;
+      block_span(bx, B, ox, W, &x0, &x1);
+      block_span(by, B, oy, H, &y0, &y1);
       for (int c = 0; c < C; ++c)
         for (int y = y0; y < y1; ++y)
           for (int x = x0; x < x1; ++x) {
@@ -149,12 +236,19 @@ void oracle_forward(const double* in, double* out, int W, int H, int C, long sy,
     }
 }
 
+void oracle_forward(const double* in, double* out, int W, int H, int C, long sy, long sx, long sc,
+                    int B, double fx, double fy, double sigma0, double k,
+                    const int* block_list, int nlist, int nthreads) {
+  oracle_forward_ex(in, out, W, H, C, sy, sx, sc, B, 0, 0, fx, fy, sigma0, k, NULL, block_list, nlist, nthreads);
+}
+
 /* Adjoint (transpose) of the forward map: g_in = A^T g_out, written as the
  * scatter of every output pixel's weighted value to the clamped input
  * positions it was computed from. g_in is overwritten. */
-void oracle_adjoint(const double* g_out, double* g_in, int W, int H, int C, long sy, long sx, long sc,
-                    int B, double fx, double fy, double sigma0, double k, int nthreads) {
-  int nbx = (W + B - 1) / B, nby = (H + B - 1) / B;
+void oracle_adjoint_ex(const double* g_out, double* g_in, int W, int H, int C, long sy, long sx, long sc,
+                       int B, int ox, int oy, double fx, double fy, double sigma0, double k, const double* map,
+                       int nthreads) {
+  int nbx = grid_count(W, B, ox), nby = grid_count(H, B, oy);
   size_t total = (size_t)W * H * C;
   int nt = 1;
 #ifdef _OPENMP
@@ -177,12 +271,13 @@ void oracle_adjoint(const double* g_out, double* g_in, int W, int H, int C, long
       int bx = b % nbx, by = b / nbx;
       double sigma;
       int r;
-      block_sigma(bx, by, B, fx, fy, sigma0, k, &sigma, &r);
+      block_sigma_any(bx, by, nbx, B, ox, oy, fx, fy, sigma0, k, map, &sigma, &r);
       int n = 2 * r + 1;
       double* w = (double*)malloc((size_t)n * sizeof(double));
       oracle_taps(sigma, r, w);
-      int x0 = bx * B, y0 = by * B;
-      int x1 = x0 + B < W ? x0 + B : W, y1 = y0 + B < H ? y0 + B : H;
+      int x0, x1, y0, y1;
+      block_span(bx, B, ox, W, &x0, &x1);
+      block_span(by, B, oy, H, &y0, &y1);
       for (int c = 0; c < C; ++c)
         for (int y = y0; y < y1; ++y)
           for (int x = x0; x < x1; ++x) {
@@ -206,6 +301,11 @@ void oracle_adjoint(const double* g_out, double* g_in, int W, int H, int C, long
         g_in[y * sy + x * sx + c * sc] = s;
       }
   free(priv);
+}
+
+void oracle_adjoint(const double* g_out, double* g_in, int W, int H, int C, long sy, long sx, long sc,
+                    int B, double fx, double fy, double sigma0, double k, int nthreads) {
+  oracle_adjoint_ex(g_out, g_in, W, H, C, sy, sx, sc, B, 0, 0, fx, fy, sigma0, k, NULL, nthreads);
 }
 
 /* uint8 output coding: nearest integer with halves rounded up, clamped to

@@ -269,3 +269,95 @@ def test_eq7_max_filter_sizes_pin_tile_geometry():
         frag, nmax = case["fragment"], case["max_filter"]
         assert usage(frag, nmax) <= limit < usage(frag, nmax + 1)
         assert usage(frag, nmax) == case["bytes_at_max"]
+
+
+# ---------------------------------------------------------------- other sigma laws, shifted grid
+
+def test_geisler_perry_chain_reduces_to_the_linear_law():
+    """Eqs. 2-6 taken step by step give sigma = (1 + e/e2) / pi, i.e. the
+    linear law with sigma0 = 1/pi and k = e_corner / (pi e2 d_corner)."""
+    g = wl.rng(5)
+    for _ in range(50):
+        W, H = int(g.integers(16, 4000)), int(g.integers(16, 3000))
+        ec = float(g.uniform(1.0, 60.0))
+        s0, k = oracle.gp_linear(W, H, ec)
+        assert s0 == 1.0 / np.pi
+        for d in g.uniform(0.0, 3000.0, size=8):
+            np.testing.assert_allclose(oracle.gp_sigma(d, W, H, ec), s0 + k * d, rtol=1e-13)
+    # at the frame corner the eccentricity is e_corner: sigma = (1 + e_corner / 2.3) / pi
+    W, H, ec = 1920, 1080, 20.0
+    dc = 0.5 * np.hypot(W, H)
+    np.testing.assert_allclose(oracle.gp_sigma(dc, W, H, ec), (1.0 + ec / 2.3) / np.pi, rtol=1e-14)
+    # the fovea keeps the finest filter: the cut-off frequency is the
+    # highest there, half a cycle per pixel, so sigma = 1 / pi
+    assert oracle.gp_sigma(0.0, W, H, ec) == pytest.approx(1.0 / np.pi, rel=1e-15)
+
+
+@pytest.mark.parametrize("B", [8, 16, 32])
+def test_centred_origin_puts_a_block_centre_on_the_fixation(B):
+    g = wl.rng(6)
+    for _ in range(200):
+        f = float(g.uniform(-100.0, 2000.0))
+        o = oracle.centred_origin(f, B)
+        assert 0 <= o < B
+        # the block starting at floor(f + 1/2) - floor(B/2) is on the grid
+        start = int(np.floor(f + 0.5)) - B // 2
+        assert (start + o) % B == 0
+        if B % 2 == 0:  # its nominal centre is the nearest pixel corner to f
+            assert start + B / 2 == np.floor(f + 0.5)
+
+
+def test_shifted_grid_blockwise_equals_per_block_uniform_blur():
+    """With a shifted grid every (clipped) block is still the uniform blur
+    at its own sigma, and sigma follows the shifted block centres."""
+    W, H, C, B = 90, 70, 2, 16
+    img = wl.uniform_f32((H, W, C), seed=12).astype(np.float64)
+    fx, fy = 41.3, 27.8
+    ox, oy = oracle.centred_origin(fx, B), oracle.centred_origin(fy, B)
+    assert (ox, oy) != (0, 0)
+    out = oracle.forward(img, B, fx, fy, 0.4, 0.06, "hwc", origin=(ox, oy))
+    sig, rad = oracle.sigma_table(W, H, B, fx, fy, 0.4, 0.06, origin=(ox, oy))
+    assert sig.shape == ((H + oy + B - 1) // B, (W + ox + B - 1) // B)
+    # the block holding the fixation has the smallest sigma, at most 1/sqrt(2) px off-centre
+    iy, ix = np.unravel_index(np.argmin(sig), sig.shape)
+    assert B * ix - ox <= fx < B * ix - ox + B and B * iy - oy <= fy < B * iy - oy + B
+    assert sig[iy, ix] <= 0.4 + 0.06 * np.sqrt(0.5) + 1e-12
+    for by in range(sig.shape[0]):
+        for bx in range(sig.shape[1]):
+            cx, cy = B * bx + B / 2 - ox, B * by + B / 2 - oy
+            assert sig[by, bx] == 0.4 + 0.06 * np.sqrt((cx - fx) ** 2 + (cy - fy) ** 2)
+            ref = _scipy_uniform(img, sig[by, bx], int(rad[by, bx]), "hwc")
+            ys = slice(max(0, B * by - oy), min(H, B * by - oy + B))
+            xs = slice(max(0, B * bx - ox), min(W, B * bx - ox + B))
+            np.testing.assert_allclose(out[ys, xs], ref[ys, xs], rtol=0, atol=1e-13)
+
+
+def test_mirror_commutes_with_centred_grid():
+    W, H, B = 224, 160, 32
+    img = wl.uniform_f32((H, W, 3), seed=13).astype(np.float64)
+    fx, fy = 100.0, 37.0
+    org = (oracle.centred_origin(fx, B), oracle.centred_origin(fy, B))
+    out = oracle.forward(img, B, fx, fy, 0.5, 0.05, "hwc", origin=org)
+    mx = W - fx
+    orgx = (oracle.centred_origin(mx, B), org[1])
+    flip = oracle.forward(img[:, ::-1], B, mx, fy, 0.5, 0.05, "hwc", origin=orgx)
+    np.testing.assert_allclose(flip, out[:, ::-1], rtol=0, atol=1e-13)
+
+
+def test_sigma_map_equal_to_the_law_reproduces_it_and_a_constant_map_is_uniform():
+    W, H, B = 75, 50, 16
+    img = wl.uniform_f32((2, H, W), seed=14).astype(np.float64)
+    sig, rad = oracle.sigma_table(W, H, B, 30.0, 20.0, 0.5, 0.07)
+    a = oracle.forward(img, B, 30.0, 20.0, 0.5, 0.07, "chw")
+    b = oracle.forward(img, B, 0.0, 0.0, 0.0, 0.0, "chw", sigma_map=sig)
+    assert np.array_equal(a, b)
+    const = np.full(sig.shape, 1.7)
+    c = oracle.forward(img, B, 0.0, 0.0, 0.0, 0.0, "chw", sigma_map=const)
+    np.testing.assert_allclose(c, _scipy_uniform(img, 1.7, 6, "chw"), rtol=0, atol=1e-13)
+    s2, r2 = oracle.sigma_table(W, H, B, 0.0, 0.0, 0.0, 0.0, sigma_map=const)
+    assert np.all(s2 == 1.7) and np.all(r2 == 6)
+    # the adjoint follows the map too
+    g = wl.uniform_f32((2, H, W), seed=15).astype(np.float64)
+    lhs = np.vdot(c, g)
+    rhs = np.vdot(img, oracle.adjoint(g, B, 0.0, 0.0, 0.0, 0.0, "chw", sigma_map=const))
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-12)
