@@ -66,17 +66,47 @@ typedef enum {
 
 typedef enum { FOVEA_U8_HWC = 0, FOVEA_F32_CHW = 1 } fovea_format;
 
-typedef enum { FOVEA_LAW_LINEAR = 0 } fovea_law_kind;
+typedef enum {
+  FOVEA_LAW_LINEAR = 0,         /* sigma_b = sigma0 + k * e_b (pixels) */
+  FOVEA_LAW_GEISLER_PERRY = 1,  /* Eqs. 2-6 with the frame corner at e_corner_deg */
+  FOVEA_LAW_MAP = 2             /* caller-supplied sigma per block */
+} fovea_law_kind;
 
-/* Sigma law sigma_b = sigma0 + k * e_b (pixels). Both must be finite and >= 0.
- * (Appendix "Choosing the Standard Deviation", Eqs. 2-6: the Geisler-Perry
- * cut-off law with eccentricity proportional to pixel distance, Eq. 5, is
- * linear in e_b and is expressed through these two numbers.) */
+typedef enum {
+  FOVEA_GRID_ANCHORED = 0,  /* block (bx, by) starts at pixel (B bx, B by) */
+  FOVEA_GRID_CENTRED = 1    /* the grid is shifted so that a block is centred on the
+                               fixation (Algorithm 1), to the nearest pixel */
+} fovea_grid_mode;
+
+/* Sigma law of a context (Section 2; Appendix "Choosing the Standard
+ * Deviation", Eqs. 2-6). e_b is the distance in pixels from block b's
+ * nominal centre to the fixation.
+ *  - LINEAR: sigma0 and k finite and >= 0.
+ *  - GEISLER_PERRY: the cut-off law with alpha = 0.106, e2 = 2.3, CT0 = 1/64
+ *    and eccentricity proportional to pixel distance (Eq. 5), the frame
+ *    corner at e_corner_deg degrees (finite, >= 0). It is linear in e_b,
+ *    sigma = 1/pi + e_corner / (pi e2 d_corner) e_b (see fovea_gp_law).
+ *  - MAP: sigma_map is a device array of nby x nbx floats (row-major, the
+ *    grid in force for the frame: see fovea_grid) owned by the caller and
+ *    read by every render; sigma_map_max is an upper bound of its values
+ *    (it sizes the kernels; larger values are clamped and flagged, and the
+ *    call then fails with FOVEA_ECUDA). The fixation only places the grid.
+ * grid: a fovea_grid_mode. */
 typedef struct {
-  int kind;       /* FOVEA_LAW_LINEAR */
-  double sigma0;
-  double k;
+  int kind;                /* fovea_law_kind */
+  double sigma0;           /* LINEAR */
+  double k;                /* LINEAR */
+  double e_corner_deg;     /* GEISLER_PERRY */
+  const float* sigma_map;  /* MAP: device pointer */
+  double sigma_map_max;    /* MAP */
+  int grid;                /* fovea_grid_mode */
 } fovea_sigma_law;
+
+/* The Geisler-Perry law of a width x height frame whose corner lies at
+ * e_corner_deg degrees, as the linear law's coefficients: *sigma0 = 1/pi,
+ * *k = e_corner_deg / ((pi * 2.3) * d_corner), d_corner = half the frame
+ * diagonal (binary64, in that order). FOVEA_EINVAL for a bad argument. */
+int fovea_gp_law(int width, int height, double e_corner_deg, double* sigma0, double* k);
 
 /* Largest radius r = ceil(3 sigma) a block may reach; larger requests are
  * refused with FOVEA_EUNSUPPORTED before any work is enqueued. */
@@ -102,14 +132,26 @@ int fovea_render(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x,
                  void* stream);
 
 /* One frame of a batch. Frames of one batch may differ in size, channels,
- * format, fixation and sigma law; the block side is the context's. */
+ * format, fixation, sigma law and grid mode; the block side is the
+ * context's. The law is linear (sigma0, k; fovea_gp_law converts the
+ * Geisler-Perry law) unless sigma_map is set (a device array of per-block
+ * sigma for this frame's grid, bounded by sigma_map_max, as in
+ * fovea_sigma_law). */
 typedef struct {
   int width, height, channels, format;
   const void* in;     /* device pointer */
   void* out;          /* device pointer */
   float fix_x, fix_y;
   double sigma0, k;
+  int grid;                /* fovea_grid_mode */
+  const float* sigma_map;  /* or NULL */
+  double sigma_map_max;
 } fovea_frame;
+
+/* Block grid of a frame of the context's shape for a fixation: *nbx x *nby
+ * blocks, block (bx, by) starting at pixel (B bx - *ox, B by - *oy) (clipped
+ * to the frame); sigma tables and sigma maps are laid out on this grid. */
+int fovea_grid(const fovea_ctx* ctx, float fix_x, float fix_y, int* nbx, int* nby, int* ox, int* oy);
 
 /* Foveate n frames in one launch sequence: a sigma-table kernel over every
  * (frame, block), a cost-ordered work list, and one persistent kernel that
@@ -140,7 +182,7 @@ int fovea_backward_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, void*
 
 /* Per-block sigma (float32, rounded from the binary64 value) and radius for
  * the context's frame at the given fixation, row-major over the block grid
- * (ceil(H/B) x ceil(W/B)), written to device arrays. This is the table the
+ * (nby x nbx of fovea_grid), written to device arrays. This is the table the
  * render path computes internally (Algorithm 1, "blur grid" with its per-frame
  * offset to the fixation). */
 int fovea_sigma_table(fovea_ctx* ctx, float fix_x, float fix_y, float* sigma_dev, int* radius_dev,

@@ -36,6 +36,7 @@ int cuda_fail(cudaError_t e) {
 bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
 
 constexpr int kBatchSlots = 4;
+constexpr double kPi = 3.14159265358979323846;
 
 // Zero the output planes of every frame of a device-resident batch (the
 // adjoint accumulates into them).
@@ -53,7 +54,7 @@ __global__ void zero_outputs_kernel(const BatchHeader* hdr, const FrameDesc* fra
 
 struct fovea_ctx {
   int W = 0, H = 0, C = 0, B = 32, fmt = 0;
-  double sigma0 = 0.0, k = 0.0;
+  fovea::FrameLaw law;
   bool batch_only = false;
   int device = 0, num_sms = 0;
   FwdConfig cfg{256, 0, 32, 1};
@@ -84,18 +85,40 @@ namespace fovea {
 
 double block_centre_host(int b, int B) { return (double)B * (double)b + 0.5 * (double)B; }
 
-int radius_bound(int W, int H, int B, double fx, double fy, double sigma0, double k) {
+int grid_origin(float f, int B, int grid) {
+  if (grid != FOVEA_GRID_CENTRED) return 0;
+  const long long c = (long long)std::floor((double)f + 0.5);
+  long long o = ((long long)(B / 2) - c) % B;
+  if (o < 0) o += B;
+  return (int)o;
+}
+
+void grid_dims(int W, int H, int B, int ox, int oy, int* nbx, int* nby) {
+  *nbx = (W + ox + B - 1) / B;
+  *nby = (H + oy + B - 1) / B;
+}
+
+int radius_bound(int W, int H, int B, float fxf, float fyf, const FrameLaw& law) {
+  if (law.smap) {
+    const double s3 = 3.0 * law.smap_max;
+    return s3 > 1e9 ? 1000000000 : (int)std::ceil(s3);
+  }
   // The largest eccentricity over the block grid is reached at one of its
   // four corner blocks; every step is rounded on its own (this file is
   // compiled without floating-point contraction), so the result equals the
   // device's radius of that block.
-  const int nbx = (W + B - 1) / B, nby = (H + B - 1) / B;
+  const double fx = fxf, fy = fyf, sigma0 = law.sigma0, k = law.k;
+  const int ox = grid_origin(fxf, B, law.grid), oy = grid_origin(fyf, B, law.grid);
+  int nbx, nby;
+  grid_dims(W, H, B, ox, oy, &nbx, &nby);
   const int bxs[2] = {0, nbx - 1}, bys[2] = {0, nby - 1};
   int rmax = 0;
   for (int bx : bxs)
     for (int by : bys) {
-      volatile double dx = block_centre_host(bx, B) - fx;
-      volatile double dy = block_centre_host(by, B) - fy;
+      volatile double cx = block_centre_host(bx, B) - (double)ox;
+      volatile double cy = block_centre_host(by, B) - (double)oy;
+      volatile double dx = cx - fx;
+      volatile double dy = cy - fy;
       volatile double dx2 = dx * dx;
       volatile double dy2 = dy * dy;
       volatile double e = std::sqrt(dx2 + dy2);
@@ -109,15 +132,20 @@ int radius_bound(int W, int H, int B, double fx, double fy, double sigma0, doubl
   return rmax;
 }
 
-int check_frame(int W, int H, int C, int fmt, int B, double sigma0, double k, float fx, float fy) {
+int check_frame(int W, int H, int C, int fmt, int B, const FrameLaw& law, float fx, float fy) {
   if (W <= 0 || H <= 0 || B <= 0) return FOVEA_EINVAL;
   if (B > kMaxBlock) return FOVEA_EUNSUPPORTED;
   if (C < 1 || C > 4) return FOVEA_EINVAL;
   if (fmt != FOVEA_U8_HWC && fmt != FOVEA_F32_CHW) return FOVEA_EINVAL;
-  if (!finite_nonneg(sigma0) || !finite_nonneg(k)) return FOVEA_EINVAL;
+  if (law.grid != FOVEA_GRID_ANCHORED && law.grid != FOVEA_GRID_CENTRED) return FOVEA_EINVAL;
+  if (law.smap) {
+    if (!finite_nonneg(law.smap_max)) return FOVEA_EINVAL;
+  } else if (!finite_nonneg(law.sigma0) || !finite_nonneg(law.k)) {
+    return FOVEA_EINVAL;
+  }
   if (!std::isfinite(fx) || !std::isfinite(fy)) return FOVEA_EINVAL;
   if ((long long)W * H * C > (1ll << 31) - 1) return FOVEA_EUNSUPPORTED;
-  if (radius_bound(W, H, B, fx, fy, sigma0, k) > kMaxRadius) return FOVEA_EUNSUPPORTED;
+  if (radius_bound(W, H, B, fx, fy, law) > kMaxRadius) return FOVEA_EUNSUPPORTED;
   return FOVEA_OK;
 }
 
@@ -131,18 +159,20 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   return pa < pb + nb && pb < pa + na;
 }
 
-FrameDesc make_desc(int W, int H, int C, int fmt, int B, const void* in, void* out, float fx,
-                    float fy, double sigma0, double k, long long item0) {
+FrameDesc make_desc(int W, int H, int C, int fmt, int B, const void* in, void* out, float fx, float fy,
+                    const FrameLaw& law, long long item0) {
   FrameDesc d;
   std::memset(&d, 0, sizeof(d));
   d.in = in;
   d.out = out;
   d.W = W; d.H = H; d.C = C; d.fmt = fmt;
   d.B = B;
-  d.nbx = (W + B - 1) / B;
-  d.nby = (H + B - 1) / B;
+  d.ox = grid_origin(fx, B, law.grid);
+  d.oy = grid_origin(fy, B, law.grid);
+  grid_dims(W, H, B, d.ox, d.oy, &d.nbx, &d.nby);
   d.fx = fx; d.fy = fy;
-  d.sigma0 = sigma0; d.k = k;
+  d.sigma0 = law.sigma0; d.k = law.k;
+  d.smap = law.smap;
   d.item0 = item0;
   return d;
 }
@@ -219,16 +249,18 @@ int upload_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint,
   int mask = 0, cc = -1;
   for (int i = 0; i < n; ++i) {
     const fovea_frame& f = frames[i];
-    int st = check_frame(f.width, f.height, f.channels, f.format, ctx->B, f.sigma0, f.k, f.fix_x, f.fix_y);
+    FrameLaw fl;
+    fl.sigma0 = f.sigma0; fl.k = f.k; fl.smap = f.sigma_map; fl.smap_max = f.sigma_map_max; fl.grid = f.grid;
+    int st = check_frame(f.width, f.height, f.channels, f.format, ctx->B, fl, f.fix_x, f.fix_y);
     if (st != FOVEA_OK) return st;
     if (adjoint && f.format != FOVEA_F32_CHW) return FOVEA_EINVAL;
     if (!f.in || !f.out) return FOVEA_EINVAL;
     const size_t nb = frame_bytes(f.width, f.height, f.channels, f.format);
     if (overlaps(f.in, nb, f.out, nb)) return FOVEA_EINVAL;
     descs[(size_t)i] = make_desc(f.width, f.height, f.channels, f.format, ctx->B, f.in, f.out, f.fix_x,
-                                 f.fix_y, f.sigma0, f.k, item0);
+                                 f.fix_y, fl, item0);
     item0 += (long long)descs[(size_t)i].nbx * descs[(size_t)i].nby;
-    rm = std::max(rm, radius_bound(f.width, f.height, ctx->B, f.fix_x, f.fix_y, f.sigma0, f.k));
+    rm = std::max(rm, radius_bound(f.width, f.height, ctx->B, f.fix_x, f.fix_y, fl));
     mask |= f.format == FOVEA_F32_CHW ? 2 : 1;
     cc = cc == -1 ? f.channels : (cc == f.channels ? cc : 0);
   }
@@ -378,8 +410,29 @@ int fovea_create(int width, int height, int channels, int block, const fovea_sig
                  fovea_ctx** out) {
   if (!out || !law) return FOVEA_EINVAL;
   *out = nullptr;
-  if (law->kind != FOVEA_LAW_LINEAR) return FOVEA_EUNSUPPORTED;
-  if (!finite_nonneg(law->sigma0) || !finite_nonneg(law->k)) return FOVEA_EINVAL;
+  FrameLaw fl;
+  fl.grid = law->grid;
+  if (fl.grid != FOVEA_GRID_ANCHORED && fl.grid != FOVEA_GRID_CENTRED) return FOVEA_EINVAL;
+  switch (law->kind) {
+    case FOVEA_LAW_LINEAR:
+      if (!finite_nonneg(law->sigma0) || !finite_nonneg(law->k)) return FOVEA_EINVAL;
+      fl.sigma0 = law->sigma0;
+      fl.k = law->k;
+      break;
+    case FOVEA_LAW_GEISLER_PERRY: {
+      if (width <= 0 || height <= 0) return FOVEA_EINVAL;  // the law depends on the frame diagonal
+      const int st = fovea_gp_law(width, height, law->e_corner_deg, &fl.sigma0, &fl.k);
+      if (st != FOVEA_OK) return st;
+      break;
+    }
+    case FOVEA_LAW_MAP:
+      if (!law->sigma_map || !finite_nonneg(law->sigma_map_max)) return FOVEA_EINVAL;
+      fl.smap = law->sigma_map;
+      fl.smap_max = law->sigma_map_max;
+      break;
+    default:
+      return FOVEA_EINVAL;
+  }
   if (block <= 0) return FOVEA_EINVAL;
   if (block > kMaxBlock) return FOVEA_EUNSUPPORTED;
   if (format != FOVEA_U8_HWC && format != FOVEA_F32_CHW) return FOVEA_EINVAL;
@@ -391,7 +444,7 @@ int fovea_create(int width, int height, int channels, int block, const fovea_sig
   fovea_ctx* ctx = new (std::nothrow) fovea_ctx();
   if (!ctx) return FOVEA_ENOMEM;
   ctx->W = width; ctx->H = height; ctx->C = channels; ctx->B = block; ctx->fmt = format;
-  ctx->sigma0 = law->sigma0; ctx->k = law->k;
+  ctx->law = fl;
   ctx->batch_only = batch_only;
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -399,7 +452,10 @@ int fovea_create(int width, int height, int channels, int block, const fovea_sig
     delete ctx;
     return cuda_fail(e);
   }
-  long long items = batch_only ? 1024 : (long long)((width + block - 1) / block) * ((height + block - 1) / block);
+  // a shifted grid has at most one more block along each axis
+  const int extra = fl.grid == FOVEA_GRID_CENTRED ? 1 : 0;
+  long long items = batch_only ? 1024
+                               : (long long)((width + block - 1) / block + extra) * ((height + block - 1) / block + extra);
   int st = ensure_workspace(ctx, items);
   if (st != FOVEA_OK) {
     fovea_destroy(ctx);
@@ -412,16 +468,16 @@ int fovea_create(int width, int height, int channels, int block, const fovea_sig
 
 int fovea_render(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x, float fix_y, void* stream) {
   if (!ctx || !in_dev || !out_dev || ctx->batch_only) return FOVEA_EINVAL;
-  int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->sigma0, ctx->k, fix_x, fix_y);
+  int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->law, fix_x, fix_y);
   if (st != FOVEA_OK) return st;
   const size_t nb = frame_bytes(ctx->W, ctx->H, ctx->C, ctx->fmt);
   if (overlaps(in_dev, nb, out_dev, nb)) return FOVEA_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   FrameSource src;
   std::memset(&src, 0, sizeof(src));
-  src.one = make_desc(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, in_dev, out_dev, fix_x, fix_y, ctx->sigma0, ctx->k, 0);
+  src.one = make_desc(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, in_dev, out_dev, fix_x, fix_y, ctx->law, 0);
   src.one_total = (long long)src.one.nbx * src.one.nby;
-  const int rmax = radius_bound(ctx->W, ctx->H, ctx->B, fix_x, fix_y, ctx->sigma0, ctx->k);
+  const int rmax = radius_bound(ctx->W, ctx->H, ctx->B, fix_x, fix_y, ctx->law);
   const int fmt_mask = ctx->fmt == FOVEA_F32_CHW ? 2 : 1;
   const int tc_c = ctx->C;
   const int grid = forward_grid(ctx, rmax, fmt_mask, tc_c);
@@ -479,7 +535,7 @@ int fovea_backward_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, void*
 int fovea_render_host(fovea_ctx* ctx, const void* in_host, void* out_host, float fix_x, float fix_y,
                       void* stream) {
   if (!ctx || !in_host || !out_host || ctx->batch_only) return FOVEA_EINVAL;
-  int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->sigma0, ctx->k, fix_x, fix_y);
+  int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->law, fix_x, fix_y);
   if (st != FOVEA_OK) return st;
   const size_t nb = frame_bytes(ctx->W, ctx->H, ctx->C, ctx->fmt);
   if (overlaps(in_host, nb, out_host, nb)) return FOVEA_EINVAL;
@@ -506,7 +562,7 @@ int fovea_backward(fovea_ctx* ctx, const float* grad_out_dev, float* grad_in_dev
                    void* stream) {
   if (!ctx || !grad_out_dev || !grad_in_dev || ctx->batch_only) return FOVEA_EINVAL;
   if (ctx->fmt != FOVEA_F32_CHW) return FOVEA_EINVAL;
-  int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->sigma0, ctx->k, fix_x, fix_y);
+  int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->law, fix_x, fix_y);
   if (st != FOVEA_OK) return st;
   const size_t nb = frame_bytes(ctx->W, ctx->H, ctx->C, ctx->fmt);
   if (overlaps(grad_out_dev, nb, grad_in_dev, nb)) return FOVEA_EINVAL;
@@ -514,9 +570,9 @@ int fovea_backward(fovea_ctx* ctx, const float* grad_out_dev, float* grad_in_dev
   FrameSource src;
   std::memset(&src, 0, sizeof(src));
   src.one = make_desc(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, grad_out_dev, grad_in_dev, fix_x, fix_y,
-                      ctx->sigma0, ctx->k, 0);
+                      ctx->law, 0);
   src.one_total = (long long)src.one.nbx * src.one.nby;
-  const int rmax = radius_bound(ctx->W, ctx->H, ctx->B, fix_x, fix_y, ctx->sigma0, ctx->k);
+  const int rmax = radius_bound(ctx->W, ctx->H, ctx->B, fix_x, fix_y, ctx->law);
   FOVEA_CUDA(cudaMemsetAsync(grad_in_dev, 0, nb, s));
   cudaError_t e = launch_sigma_order(src, ctx->ws, sigma_grid(src.one_total, ctx->num_sms), nullptr, nullptr, s);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -529,16 +585,36 @@ int fovea_backward(fovea_ctx* ctx, const float* grad_out_dev, float* grad_in_dev
 
 int fovea_sigma_table(fovea_ctx* ctx, float fix_x, float fix_y, float* sigma_dev, int* radius_dev, void* stream) {
   if (!ctx || !sigma_dev || !radius_dev || ctx->batch_only) return FOVEA_EINVAL;
-  int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->sigma0, ctx->k, fix_x, fix_y);
+  int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->law, fix_x, fix_y);
   if (st != FOVEA_OK) return st;
   FrameSource src;
   std::memset(&src, 0, sizeof(src));
-  src.one = make_desc(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, nullptr, nullptr, fix_x, fix_y, ctx->sigma0,
-                      ctx->k, 0);
+  src.one = make_desc(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, nullptr, nullptr, fix_x, fix_y, ctx->law, 0);
   src.one_total = (long long)src.one.nbx * src.one.nby;
   cudaError_t e = launch_sigma_order(src, ctx->ws, sigma_grid(src.one_total, ctx->num_sms), sigma_dev, radius_dev,
                                      static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e);
+  return FOVEA_OK;
+}
+
+int fovea_gp_law(int width, int height, double e_corner_deg, double* sigma0, double* k) {
+  if (width <= 0 || height <= 0 || !sigma0 || !k || !finite_nonneg(e_corner_deg)) return FOVEA_EINVAL;
+  const double e2 = 2.3;
+  volatile double w2 = (double)width * (double)width;
+  volatile double h2 = (double)height * (double)height;
+  volatile double d_corner = 0.5 * std::sqrt(w2 + h2);
+  volatile double pe2 = kPi * e2;
+  *sigma0 = 1.0 / kPi;
+  *k = e_corner_deg / (pe2 * d_corner);
+  return FOVEA_OK;
+}
+
+int fovea_grid(const fovea_ctx* ctx, float fix_x, float fix_y, int* nbx, int* nby, int* ox, int* oy) {
+  if (!ctx || !nbx || !nby || !ox || !oy || ctx->batch_only) return FOVEA_EINVAL;
+  if (!std::isfinite(fix_x) || !std::isfinite(fix_y)) return FOVEA_EINVAL;
+  *ox = grid_origin(fix_x, ctx->B, ctx->law.grid);
+  *oy = grid_origin(fix_y, ctx->B, ctx->law.grid);
+  grid_dims(ctx->W, ctx->H, ctx->B, *ox, *oy, nbx, nby);
   return FOVEA_OK;
 }
 

@@ -7,11 +7,26 @@
 
 namespace fovea {
 
+// Sigma law and block grid of one frame as the host sees it: the linear law
+// (sigma0, k), or a per-block device map with an upper bound of its values;
+// and a fovea_grid_mode.
+struct FrameLaw {
+  double sigma0 = 0.0, k = 0.0;
+  const float* smap = nullptr;
+  double smap_max = 0.0;
+  int grid = FOVEA_GRID_ANCHORED;
+};
+// Grid origin offset along one axis (0, or the offset that centres a block
+// on fixation coordinate f: (floor(B/2) - floor(f + 1/2)) mod B).
+int grid_origin(float f, int B, int grid);
+// Blocks along each axis for origin offsets (ox, oy).
+void grid_dims(int W, int H, int B, int ox, int oy, int* nbx, int* nby);
 // Largest radius ceil(3 sigma) over the block grid of a W x H frame
-// (computed exactly as the device does for the farthest block).
-int radius_bound(int W, int H, int B, double fx, double fy, double sigma0, double k);
+// (computed exactly as the device does for the farthest block; for a map,
+// ceil(3 smap_max)).
+int radius_bound(int W, int H, int B, float fx, float fy, const FrameLaw& law);
 // FOVEA_OK or the status a frame with these parameters is refused with.
-int check_frame(int W, int H, int C, int fmt, int B, double sigma0, double k, float fx, float fy);
+int check_frame(int W, int H, int C, int fmt, int B, const FrameLaw& law, float fx, float fy);
 size_t frame_bytes(int W, int H, int C, int fmt);
 int ctx_shape(const fovea_ctx* ctx, int* W, int* H, int* C, int* fmt, int* B);
 int ctx_device_info(const fovea_ctx* ctx, int* device, int* num_sms);

@@ -20,7 +20,7 @@ constexpr int kMaxRadius = FOVEA_MAX_RADIUS; // r <= 1023
 constexpr int kBuckets = 1024;               // radius buckets of the work-list sort
 constexpr int kTapPad = 16;                  // zero taps stored before offset 0
 
-// One frame as the kernels see it (host fills it in; 80 bytes).
+// One frame as the kernels see it (host fills it in; 96 bytes).
 struct FrameDesc {
   const void* in;
   void* out;
@@ -29,6 +29,8 @@ struct FrameDesc {
   float fx, fy;            // fixation (pixels)
   double sigma0, k;        // sigma law
   long long item0;         // index of the frame's first item in a batch
+  int ox, oy;              // grid origin: block (bx, by) starts at (B bx - ox, B by - oy)
+  const float* smap;       // per-block sigma [nby][nbx] replacing the law, or null
 };
 
 // Device-resident batch: header followed by the frame descriptors, then
@@ -97,16 +99,29 @@ __device__ __forceinline__ long long source_total(const FrameSource& s) {
 // its own (no fused multiply-add), so the radius ceil(3 sigma) is reproduced
 // bit for bit by any implementation that follows the same order:
 //   centre = B*b + B/2;  e = sqrt(dx*dx + dy*dy);  sigma = sigma0 + k*e.
-__device__ __forceinline__ void block_sigma(int bx, int by, int B, double fx, double fy,
+__device__ __forceinline__ void block_sigma(int bx, int by, int B, int ox, int oy, double fx, double fy,
                                             double sigma0, double k, double& sigma, int& r) {
   double half = __dmul_rn(0.5, (double)B);
-  double cx = __dadd_rn(__dmul_rn((double)B, (double)bx), half);
-  double cy = __dadd_rn(__dmul_rn((double)B, (double)by), half);
+  double cx = __dsub_rn(__dadd_rn(__dmul_rn((double)B, (double)bx), half), (double)ox);
+  double cy = __dsub_rn(__dadd_rn(__dmul_rn((double)B, (double)by), half), (double)oy);
   double dx = __dsub_rn(cx, fx);
   double dy = __dsub_rn(cy, fy);
   double e = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
   sigma = __dadd_rn(sigma0, __dmul_rn(k, e));
   r = (int)ceil(__dmul_rn(3.0, sigma));
+}
+
+// Sigma and radius of block (bx, by) of a frame: the sigma law at the
+// block's nominal centre, or the frame's per-block map (r = ceil(3 sigma) of
+// the map value in binary64). A map value that is negative or not finite
+// gives r = -1, which the caller flags.
+__device__ __forceinline__ void item_sigma(const FrameDesc& fd, int bx, int by, double& sigma, int& r) {
+  if (fd.smap) {
+    sigma = (double)fd.smap[(size_t)by * fd.nbx + bx];
+    r = (sigma >= 0.0 && sigma <= 1e6) ? (int)ceil(__dmul_rn(3.0, sigma)) : -1;
+  } else {
+    block_sigma(bx, by, fd.B, fd.ox, fd.oy, (double)fd.fx, (double)fd.fy, fd.sigma0, fd.k, sigma, r);
+  }
 }
 
 // Packed two-lane FMA: d = a * b + c on both float lanes (one f32x2

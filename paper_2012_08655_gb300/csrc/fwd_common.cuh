@@ -122,8 +122,9 @@ __device__ __forceinline__ void item_geometry(Item& it, const ItemInfo& inf, con
   it.r = inf.r;
   const int r = it.r;
   const int bx = inf.block % fd.nbx, by = inf.block / fd.nbx;
-  it.x0 = bx * fd.B; it.y0 = by * fd.B;
-  it.bw = min(fd.B, it.W - it.x0); it.bh = min(fd.B, it.H - it.y0);
+  const int xs = bx * fd.B - fd.ox, ys = by * fd.B - fd.oy;  // unclipped block start
+  it.x0 = max(0, xs); it.y0 = max(0, ys);
+  it.bw = min(xs + fd.B, it.W) - it.x0; it.bh = min(ys + fd.B, it.H) - it.y0;
   it.gx0 = max(0, it.x0 - r);
   it.EW = min(it.W - 1, it.x0 + it.bw - 1 + r) - it.gx0 + 1;
   it.offx = it.gx0 - (it.x0 - r);

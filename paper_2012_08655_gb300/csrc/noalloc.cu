@@ -68,7 +68,10 @@ extern "C" int fovea_render_noalloc(const void* in_dev, void* out_dev, int width
                                     int format, int block, double sigma0, double k, float fix_x, float fix_y,
                                     void* stream) {
   if (!in_dev || !out_dev) return FOVEA_EINVAL;
-  int st = check_frame(width, height, channels, format, block, sigma0, k, fix_x, fix_y);
+  FrameLaw law;
+  law.sigma0 = sigma0;
+  law.k = k;
+  int st = check_frame(width, height, channels, format, block, law, fix_x, fix_y);
   if (st != FOVEA_OK) return st;
   const size_t nb = frame_bytes(width, height, channels, format);
   const char* a = static_cast<const char*>(in_dev);
@@ -109,7 +112,7 @@ extern "C" int fovea_render_noalloc(const void* in_dev, void* out_dev, int width
   src.one.sigma0 = sigma0; src.one.k = k;
   src.one_total = items;
 
-  const int rmax = radius_bound(width, height, block, fix_x, fix_y, sigma0, k);
+  const int rmax = radius_bound(width, height, block, fix_x, fix_y, law);
   const int sg = (int)((items + 255) / 256);
   e = launch_sigma_order(src, ws, sg < 1 ? 1 : (sg > 4 * sms ? 4 * sms : sg), nullptr, nullptr, s);
   if (e != cudaSuccess) return record_cuda_failure(e);

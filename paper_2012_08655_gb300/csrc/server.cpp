@@ -304,8 +304,11 @@ int fovea_server_create(const fovea_server_config* cfg, fovea_server** out) {
 
 long long fovea_server_submit(fovea_server* s, const fovea_frame* f, double arrival_us) {
   if (!s || !f || !f->in || !f->out) return FOVEA_EINVAL;
-  const int st = fovea::check_frame(f->width, f->height, f->channels, f->format, s->cfg.block, f->sigma0, f->k,
-                                    f->fix_x, f->fix_y);
+  fovea::FrameLaw law;
+  law.sigma0 = f->sigma0; law.k = f->k; law.smap = f->sigma_map; law.smap_max = f->sigma_map_max;
+  law.grid = f->grid;
+  const int st = fovea::check_frame(f->width, f->height, f->channels, f->format, s->cfg.block, law, f->fix_x,
+                                    f->fix_y);
   if (st != FOVEA_OK) return st;
   const size_t bytes = fovea::frame_bytes(f->width, f->height, f->channels, f->format);
   if (2 * align_up(bytes) > s->cfg.device_budget_bytes) return FOVEA_EBUSY;

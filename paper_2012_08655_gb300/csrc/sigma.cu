@@ -38,9 +38,10 @@ __global__ void __launch_bounds__(kSigmaThreads) sigma_kernel(FrameSource src, W
     const int bx = b % fd.nbx, by = b / fd.nbx;
     double sigma;
     int r;
-    block_sigma(bx, by, fd.B, (double)fd.fx, (double)fd.fy, fd.sigma0, fd.k, sigma, r);
-    if (r > kMaxRadius || r < 0) {  // the host refuses such launches; never reached
+    item_sigma(fd, bx, by, sigma, r);
+    if (r > kMaxRadius || r < 0) {  // the host refuses such laws; a sigma map may still hold such values
       r = r < 0 ? 0 : kMaxRadius;
+      if (!(sigma >= 0.0)) sigma = 0.0;
       atomicOr(&ws.counters[CNT_ERROR], 1u);
     }
     ItemInfo inf;

@@ -35,15 +35,22 @@ MAX_RADIUS = 1023
 MAX_BLOCK = 32
 
 
+LAW_LINEAR, LAW_GEISLER_PERRY, LAW_MAP = 0, 1, 2
+GRID_ANCHORED, GRID_CENTRED = 0, 1
+
+
 class SigmaLaw(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int), ("sigma0", ctypes.c_double), ("k", ctypes.c_double)]
+    _fields_ = [("kind", ctypes.c_int), ("sigma0", ctypes.c_double), ("k", ctypes.c_double),
+                ("e_corner_deg", ctypes.c_double), ("sigma_map", ctypes.c_void_p),
+                ("sigma_map_max", ctypes.c_double), ("grid", ctypes.c_int)]
 
 
 class Frame(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("channels", ctypes.c_int),
                 ("format", ctypes.c_int), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p),
                 ("fix_x", ctypes.c_float), ("fix_y", ctypes.c_float),
-                ("sigma0", ctypes.c_double), ("k", ctypes.c_double)]
+                ("sigma0", ctypes.c_double), ("k", ctypes.c_double),
+                ("grid", ctypes.c_int), ("sigma_map", ctypes.c_void_p), ("sigma_map_max", ctypes.c_double)]
 
 
 class Config(ctypes.Structure):
@@ -80,6 +87,9 @@ _sig = {
     "fovea_strerror": (ctypes.c_char_p, [_i]),
     "fovea_last_cuda_error": (_i, []),
     "fovea_measure_fma_rate": (_i, [ctypes.POINTER(_d), _vp]),
+    "fovea_gp_law": (_i, [_i, _i, _d, ctypes.POINTER(_d), ctypes.POINTER(_d)]),
+    "fovea_grid": (_i, [_vp, _f, _f, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                        ctypes.POINTER(_i)]),
     "fovea_server_create": (_i, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)]),
     "fovea_server_submit": (ctypes.c_longlong, [_vp, ctypes.POINTER(Frame), _d]),
     "fovea_server_wait": (_i, [_vp, ctypes.c_longlong, _i, ctypes.POINTER(RequestTimes)]),
@@ -142,17 +152,34 @@ def _require_device_frame(t: torch.Tensor, name: str):
 
 
 class Context:
-    """One fovea context (``fovea_create``): frame shape, format, block side, sigma law."""
+    """One fovea context (``fovea_create``): frame shape, format, block side,
+    sigma law and grid mode.
+
+    ``law``: LAW_LINEAR (sigma0 + k e), LAW_GEISLER_PERRY (``e_corner`` degrees
+    at the frame corner) or LAW_MAP (``sigma_map``: a float32 CUDA tensor of
+    per-block sigma on this context's grid, kept alive by the caller;
+    ``sigma_map_max`` bounds its values). ``grid``: GRID_ANCHORED or
+    GRID_CENTRED (a block centred on the fixation)."""
 
     def __init__(self, width: int, height: int, channels: int, block: int = 32,
-                 sigma0: float = 0.5, k: float = 0.02, fmt: int = U8_HWC):
-        law = SigmaLaw(0, float(sigma0), float(k))
+                 sigma0: float = 0.5, k: float = 0.02, fmt: int = U8_HWC, *, law: int = LAW_LINEAR,
+                 e_corner: float = 0.0, sigma_map: Optional[torch.Tensor] = None,
+                 sigma_map_max: Optional[float] = None, grid: int = GRID_ANCHORED):
+        mp, mmax = 0, 0.0
+        if law == LAW_MAP:
+            if sigma_map is None or not sigma_map.is_cuda or sigma_map.dtype != torch.float32:
+                raise ValueError("LAW_MAP needs a float32 CUDA sigma_map")
+            mp = sigma_map.data_ptr()
+            mmax = float(sigma_map.max().item()) if sigma_map_max is None else float(sigma_map_max)
+        sl = SigmaLaw(int(law), float(sigma0), float(k), float(e_corner), mp, mmax, int(grid))
         h = _vp()
-        _check(_lib.fovea_create(int(width), int(height), int(channels), int(block), ctypes.byref(law),
+        _check(_lib.fovea_create(int(width), int(height), int(channels), int(block), ctypes.byref(sl),
                                  int(fmt), ctypes.byref(h)), "fovea_create")
         self._h = h
+        self._map = sigma_map
         self.width, self.height, self.channels, self.block = int(width), int(height), int(channels), int(block)
         self.sigma0, self.k, self.fmt = float(sigma0), float(k), int(fmt)
+        self.law, self.grid = int(law), int(grid)
 
     @property
     def handle(self) -> int:
@@ -197,9 +224,15 @@ class Context:
                                    _stream_handle(stream)), "fovea_backward")
         return grad_in
 
+    def grid_shape(self, fix_x: float, fix_y: float):
+        """(nby, nbx, oy, ox): block grid for this fixation (``fovea_grid``)."""
+        nbx, nby, ox, oy = _i(), _i(), _i(), _i()
+        _check(_lib.fovea_grid(self._h, float(fix_x), float(fix_y), ctypes.byref(nbx), ctypes.byref(nby),
+                               ctypes.byref(ox), ctypes.byref(oy)), "fovea_grid")
+        return nby.value, nbx.value, oy.value, ox.value
+
     def sigma_table(self, fix_x: float, fix_y: float, stream=None):
-        nby = (self.height + self.block - 1) // self.block
-        nbx = (self.width + self.block - 1) // self.block
+        nby, nbx, _, _ = self.grid_shape(fix_x, fix_y)
         sig = torch.empty((nby, nbx), dtype=torch.float32, device="cuda")
         rad = torch.empty((nby, nbx), dtype=torch.int32, device="cuda")
         _check(_lib.fovea_sigma_table(self._h, float(fix_x), float(fix_y), sig.data_ptr(), rad.data_ptr(),
@@ -249,6 +282,9 @@ class BatchFrame:
     fix_y: float
     sigma0: float
     k: float
+    grid: int = GRID_ANCHORED
+    sigma_map: Optional[torch.Tensor] = None
+    sigma_map_max: float = 0.0
 
 
 def _frames_array(frames: Sequence[BatchFrame]):
@@ -261,8 +297,9 @@ def _frames_array(frames: Sequence[BatchFrame]):
         _require_device_frame(fr.out, f"frame {i} output")
         fmt = _fmt_of(fr.inp)
         w, h, c = _shape_of(fr.inp, fmt)
+        mp = fr.sigma_map.data_ptr() if fr.sigma_map is not None else None
         arr[i] = Frame(w, h, c, fmt, fr.inp.data_ptr(), fr.out.data_ptr(), float(fr.fix_x), float(fr.fix_y),
-                       float(fr.sigma0), float(fr.k))
+                       float(fr.sigma0), float(fr.k), int(fr.grid), mp, float(fr.sigma_map_max))
         keep.append(fr)
     return arr
 
@@ -271,22 +308,38 @@ def _frames_array(frames: Sequence[BatchFrame]):
 _ctx_cache: dict = {}
 
 
-def _ctx_for(w, h, c, block, sigma0, k, fmt) -> Context:
-    key = (torch.cuda.current_device(), w, h, c, block, float(sigma0), float(k), fmt)
+def _ctx_for(w, h, c, block, sigma0, k, fmt, grid=GRID_ANCHORED, e_corner=None) -> Context:
+    key = (torch.cuda.current_device(), w, h, c, block, float(sigma0), float(k), fmt, int(grid), e_corner)
     ctx = _ctx_cache.get(key)
     if ctx is None:
-        ctx = Context(w, h, c, block, sigma0, k, fmt)
+        if e_corner is None:
+            ctx = Context(w, h, c, block, sigma0, k, fmt, grid=grid)
+        else:
+            ctx = Context(w, h, c, block, 0.0, 0.0, fmt, law=LAW_GEISLER_PERRY, e_corner=e_corner, grid=grid)
         _ctx_cache[key] = ctx
     return ctx
 
 
+def gp_law(width: int, height: int, e_corner: float):
+    """(sigma0, k) of the Geisler-Perry law for this frame size (``fovea_gp_law``)."""
+    s0, k = _d(), _d()
+    _check(_lib.fovea_gp_law(int(width), int(height), float(e_corner), ctypes.byref(s0), ctypes.byref(k)),
+           "fovea_gp_law")
+    return s0.value, k.value
+
+
 def foveate(x: torch.Tensor, fix_x: float, fix_y: float, sigma0: float = 0.5, k: float = 0.02,
-            block: int = 32, out: Optional[torch.Tensor] = None) -> torch.Tensor:
-    """Foveate one frame: uint8 (H, W[, C]) or float32 ([C,] H, W), on the GPU."""
+            block: int = 32, out: Optional[torch.Tensor] = None, *, grid: int = GRID_ANCHORED,
+            e_corner: Optional[float] = None) -> torch.Tensor:
+    """Foveate one frame: uint8 (H, W[, C]) or float32 ([C,] H, W), on the GPU.
+
+    ``e_corner`` (degrees at the frame corner) selects the Geisler-Perry law
+    instead of (sigma0, k); ``grid`` = GRID_CENTRED centres a block on the
+    fixation."""
     _require_device_frame(x, "input")
     fmt = _fmt_of(x)
     w, h, c = _shape_of(x, fmt)
-    ctx = _ctx_for(w, h, c, block, sigma0, k, fmt)
+    ctx = _ctx_for(w, h, c, block, sigma0, k, fmt, grid, e_corner)
     if out is None:
         out = torch.empty_like(x)
     return ctx.render(x, out, fix_x, fix_y)
@@ -316,9 +369,9 @@ def measure_fma_rate(stream=None) -> float:
 
 
 def sigma_table(width: int, height: int, fix_x: float, fix_y: float, sigma0: float = 0.5, k: float = 0.02,
-                block: int = 32):
+                block: int = 32, *, grid: int = GRID_ANCHORED, e_corner: Optional[float] = None):
     """Per-block (sigma float32, radius int32) computed by the sigma-table kernel."""
-    return _ctx_for(width, height, 1, block, sigma0, k, F32_CHW).sigma_table(fix_x, fix_y)
+    return _ctx_for(width, height, 1, block, sigma0, k, F32_CHW, grid, e_corner).sigma_table(fix_x, fix_y)
 
 
 def _batch_ctx(block: int) -> Context:
@@ -386,12 +439,13 @@ class Server:
         return float(_lib.fovea_server_now_us())
 
     def submit(self, inp: torch.Tensor, out: torch.Tensor, fix_x: float, fix_y: float, sigma0: float,
-               k: float, arrival_us: Optional[float] = None) -> int:
+               k: float, arrival_us: Optional[float] = None, grid: int = GRID_ANCHORED) -> int:
         if inp.is_cuda or out.is_cuda:
             raise ValueError("the server takes host (preferably pinned) frames")
         fmt = _fmt_of(inp)
         w, h, c = _shape_of(inp, fmt)
-        fr = Frame(w, h, c, fmt, inp.data_ptr(), out.data_ptr(), float(fix_x), float(fix_y), float(sigma0), float(k))
+        fr = Frame(w, h, c, fmt, inp.data_ptr(), out.data_ptr(), float(fix_x), float(fix_y), float(sigma0), float(k),
+                   int(grid), None, 0.0)
         t = self.now_us() if arrival_us is None else float(arrival_us)
         return _check(int(_lib.fovea_server_submit(self._h, ctypes.byref(fr), t)), "fovea_server_submit")
 

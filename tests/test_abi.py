@@ -44,7 +44,9 @@ def test_strerror_and_invalid_arguments(lib):
     assert lib.fovea_strerror(-6) == b"unsupported"
 
     class Law(ctypes.Structure):
-        _fields_ = [("kind", ctypes.c_int), ("sigma0", ctypes.c_double), ("k", ctypes.c_double)]
+        _fields_ = [("kind", ctypes.c_int), ("sigma0", ctypes.c_double), ("k", ctypes.c_double),
+                    ("e_corner_deg", ctypes.c_double), ("sigma_map", ctypes.c_void_p),
+                    ("sigma_map_max", ctypes.c_double), ("grid", ctypes.c_int)]
 
     h = ctypes.c_void_p()
     create = lib.fovea_create
@@ -57,7 +59,18 @@ def test_strerror_and_invalid_arguments(lib):
     assert create(64, 64, 3, 32, ctypes.byref(good), 7, ctypes.byref(h)) == -1  # format
     assert create(64, 64, 3, 32, ctypes.byref(Law(0, -1.0, 0.02)), 0, ctypes.byref(h)) == -1
     assert create(64, 64, 3, 32, ctypes.byref(Law(0, 0.5, float("nan"))), 0, ctypes.byref(h)) == -1
-    assert create(64, 64, 3, 32, ctypes.byref(Law(3, 0.5, 0.02)), 0, ctypes.byref(h)) == -6
+    assert create(64, 64, 3, 32, ctypes.byref(Law(3, 0.5, 0.02)), 0, ctypes.byref(h)) == -1   # unknown law
+    assert create(64, 64, 3, 32, ctypes.byref(Law(0, 0.5, 0.02, 0.0, None, 0.0, 5)), 0, ctypes.byref(h)) == -1
+    assert create(0, 0, 3, 32, ctypes.byref(Law(1, 0.0, 0.0, 20.0)), 0, ctypes.byref(h)) == -1  # GP needs a size
+    assert create(64, 64, 3, 32, ctypes.byref(Law(1, 0.0, 0.0, -2.0)), 0, ctypes.byref(h)) == -1
+    assert create(64, 64, 3, 32, ctypes.byref(Law(2, 0.0, 0.0, 0.0, None, 3.0)), 0, ctypes.byref(h)) == -1
+    s0, k = ctypes.c_double(), ctypes.c_double()
+    lib.fovea_gp_law.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double)]
+    assert lib.fovea_gp_law(1920, 1080, 20.0, ctypes.byref(s0), ctypes.byref(k)) == 0
+    import oracle
+    assert (s0.value, k.value) == oracle.gp_linear(1920, 1080, 20.0)  # bit for bit
+    assert lib.fovea_gp_law(0, 1080, 20.0, ctypes.byref(s0), ctypes.byref(k)) == -1
     assert create(-4, 64, 3, 32, ctypes.byref(good), 0, ctypes.byref(h)) == -1
     assert h.value is None
     lib.fovea_render.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_float] * 2 + [ctypes.c_void_p]
