@@ -16,6 +16,7 @@ Also reported on the same JSON line:
   clocks        nvidia-smi samples taken during the timed region;
   batched       the 64-frame mixed batch in one launch vs one launch per frame;
   train         the 32x3x224x224 float32 batch, forward and forward+backward;
+  block_sweep   render time and halo overhead for block sides 8, 16, 32, 64;
   served        p50/p99 latency of the served request stream (continuous
                 batching) vs the plain one-request-per-launch loop.
 
@@ -374,6 +375,36 @@ def train_leg(fv, torch):
             "forward_backward_mpix_s": px / res["forward_backward"] / 1e3}
 
 
+def block_sweep_leg(fv, torch):
+    """Fragment-size sweep at 1080p RGB: render time and the algorithmic work
+    (halo overhead) for B in {8, 16, 32, 64}."""
+    import numpy as np
+    from paper_2012_08655_gb300 import workloads as wl
+    frame = wl.frame_1080p(seed=0)
+    x = torch.from_numpy(frame.image).cuda()
+    y = torch.empty_like(x)
+    res = {}
+    for B in (8, 16, 32, 64):
+        ctx = fv.Context(W, H, C, B, SIGMA0, K_SLOPE, fv.U8_HWC)
+        cfg = ctx.autotune(iters=5)
+        for _ in range(5):
+            ctx.render(x, y, *FIX)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 50
+        e0.record()
+        for _ in range(reps):
+            ctx.render(x, y, *FIX)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        _, rad = ctx.sigma_table(*FIX)
+        fmas = algorithmic_fmas(rad.cpu().numpy(), W, H, C, B)
+        res[str(B)] = {"ms": ms, "mpix_s": W * H / ms / 1e3, "algorithmic_fmas": fmas,
+                       "fmas_per_pixel_channel": fmas / (W * H * C), "kernel_config": cfg}
+    return {"workload": WORKLOAD.replace("32x32 blocks", "B x B blocks"), "by_block": res}
+
+
 def served_leg(fv, torch, seconds: float, max_batch: int):
     """Replay the Poisson request stream through the serving loop."""
     import numpy as np
@@ -539,6 +570,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_extras:
         extras["batched"] = batched_leg(fv, torch)
         extras["train"] = train_leg(fv, torch)
+        extras["block_sweep"] = block_sweep_leg(fv, torch)
         served = served_leg(fv, torch, args.served_seconds, max_batch=64)
         plain = served_leg(fv, torch, args.served_seconds, max_batch=1)
         served["plain_per_frame"] = {k: plain[k] for k in ("p50_ms", "p99_ms", "mpix_s", "mean_batch")}

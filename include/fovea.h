@@ -111,8 +111,9 @@ int fovea_gp_law(int width, int height, double e_corner_deg, double* sigma0, dou
 /* Largest radius r = ceil(3 sigma) a block may reach; larger requests are
  * refused with FOVEA_EUNSUPPORTED before any work is enqueued. */
 #define FOVEA_MAX_RADIUS 1023
-/* Block side B must satisfy 1 <= B <= FOVEA_MAX_BLOCK. */
-#define FOVEA_MAX_BLOCK 32
+/* Block side B: 1 <= B <= 32, or a multiple of 32 up to FOVEA_MAX_BLOCK (a
+ * block larger than 32 is processed as 32 x 32 tiles sharing its sigma). */
+#define FOVEA_MAX_BLOCK 256
 
 /* Create a context for frames of width x height x channels (channels in
  * {1, 2, 3, 4}) in `format`, split into block x block blocks, with sigma law
@@ -228,8 +229,9 @@ void fovea_destroy(fovea_ctx* ctx);
  * cudaMalloc -- code whose device memory is owned by a host framework or a
  * server that has reserved it up front, or that must not allocate while it
  * drives the GPU -- and for whom fovea_create's workspace is not an option.
- * Arguments are those of fovea_create and fovea_render combined; the caller
- * still owns and passes the input and output buffers. All working memory
+ * Arguments are those of fovea_create and fovea_render combined (the linear
+ * sigma law on the anchored grid); the caller still owns and passes the input
+ * and output buffers. All working memory
  * (per-block sigma/radius records, the radius-ordered work list, counters;
  * about 0.5 MB) is one fixed-size array inside the library image, held by
  * every GPU that loads the library until the process exits. No cudaMalloc,

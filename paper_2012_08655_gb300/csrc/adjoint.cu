@@ -73,11 +73,11 @@ adjoint_kernel(FrameSource src, Workspace ws, int rmax) {
       if (tid == 0) atomicOr(&ws.counters[CNT_ERROR], 4u);
       continue;
     }
-    const int W = fd.W, H = fd.H, C = fd.C, B = fd.B;
-    const int bx = inf.block % fd.nbx, by = inf.block / fd.nbx;
-    const int xs = bx * B - fd.ox, ys = by * B - fd.oy;  // unclipped block start
+    const int W = fd.W, H = fd.H, C = fd.C, T = fd.T;
+    const int tx = inf.block % fd.nbx, ty = inf.block / fd.nbx;  // tile
+    const int xs = tx * T - fd.ox, ys = ty * T - fd.oy;          // unclipped tile start
     const int x0 = max(0, xs), y0 = max(0, ys);
-    const int bw = min(xs + B, W) - x0, bh = min(ys + B, H) - y0;
+    const int bw = min(xs + T, W) - x0, bh = min(ys + T, H) - y0;
     // Folded tile: frame columns gx0 .. gx0+EW-1 and rows gy0 .. gy0+EH-1; the
     // tap index of (tile column ex, block column xo) is offx + ex - xo.
     const int gx0 = max(0, x0 - r), EW = min(W - 1, x0 + bw - 1 + r) - gx0 + 1, offx = gx0 - (x0 - r);

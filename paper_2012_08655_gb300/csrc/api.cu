@@ -134,7 +134,7 @@ int radius_bound(int W, int H, int B, float fxf, float fyf, const FrameLaw& law)
 
 int check_frame(int W, int H, int C, int fmt, int B, const FrameLaw& law, float fx, float fy) {
   if (W <= 0 || H <= 0 || B <= 0) return FOVEA_EINVAL;
-  if (B > kMaxBlock) return FOVEA_EUNSUPPORTED;
+  if (B > kMaxBlock || (B > 32 && B % 32 != 0)) return FOVEA_EUNSUPPORTED;
   if (C < 1 || C > 4) return FOVEA_EINVAL;
   if (fmt != FOVEA_U8_HWC && fmt != FOVEA_F32_CHW) return FOVEA_EINVAL;
   if (law.grid != FOVEA_GRID_ANCHORED && law.grid != FOVEA_GRID_CENTRED) return FOVEA_EINVAL;
@@ -159,8 +159,10 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   return pa < pb + nb && pb < pa + na;
 }
 
+// Items are tiles of side min(B, 32) (per_block: one item per block, for
+// sigma tables only).
 FrameDesc make_desc(int W, int H, int C, int fmt, int B, const void* in, void* out, float fx, float fy,
-                    const FrameLaw& law, long long item0) {
+                    const FrameLaw& law, long long item0, bool per_block = false) {
   FrameDesc d;
   std::memset(&d, 0, sizeof(d));
   d.in = in;
@@ -169,7 +171,10 @@ FrameDesc make_desc(int W, int H, int C, int fmt, int B, const void* in, void* o
   d.B = B;
   d.ox = grid_origin(fx, B, law.grid);
   d.oy = grid_origin(fy, B, law.grid);
-  grid_dims(W, H, B, d.ox, d.oy, &d.nbx, &d.nby);
+  d.T = (per_block || B <= 32) ? B : 32;
+  grid_dims(W, H, d.T, d.ox, d.oy, &d.nbx, &d.nby);
+  int nbyb = 0;
+  grid_dims(W, H, B, d.ox, d.oy, &d.nbxb, &nbyb);
   d.fx = fx; d.fy = fy;
   d.sigma0 = law.sigma0; d.k = law.k;
   d.smap = law.smap;
@@ -434,7 +439,7 @@ int fovea_create(int width, int height, int channels, int block, const fovea_sig
       return FOVEA_EINVAL;
   }
   if (block <= 0) return FOVEA_EINVAL;
-  if (block > kMaxBlock) return FOVEA_EUNSUPPORTED;
+  if (block > kMaxBlock || (block > 32 && block % 32 != 0)) return FOVEA_EUNSUPPORTED;
   if (format != FOVEA_U8_HWC && format != FOVEA_F32_CHW) return FOVEA_EINVAL;
   const bool batch_only = width == 0 && height == 0;
   if (!batch_only) {
@@ -452,10 +457,11 @@ int fovea_create(int width, int height, int channels, int block, const fovea_sig
     delete ctx;
     return cuda_fail(e);
   }
-  // a shifted grid has at most one more block along each axis
-  const int extra = fl.grid == FOVEA_GRID_CENTRED ? 1 : 0;
+  // work items are tiles of side min(B, 32); a shifted grid may start up to
+  // B - 1 pixels before the frame
+  const int tile = block <= 32 ? block : 32, shift = fl.grid == FOVEA_GRID_CENTRED ? block - 1 : 0;
   long long items = batch_only ? 1024
-                               : (long long)((width + block - 1) / block + extra) * ((height + block - 1) / block + extra);
+                               : (long long)((width + shift + tile - 1) / tile) * ((height + shift + tile - 1) / tile);
   int st = ensure_workspace(ctx, items);
   if (st != FOVEA_OK) {
     fovea_destroy(ctx);
@@ -589,7 +595,7 @@ int fovea_sigma_table(fovea_ctx* ctx, float fix_x, float fix_y, float* sigma_dev
   if (st != FOVEA_OK) return st;
   FrameSource src;
   std::memset(&src, 0, sizeof(src));
-  src.one = make_desc(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, nullptr, nullptr, fix_x, fix_y, ctx->law, 0);
+  src.one = make_desc(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, nullptr, nullptr, fix_x, fix_y, ctx->law, 0, true);
   src.one_total = (long long)src.one.nbx * src.one.nby;
   cudaError_t e = launch_sigma_order(src, ctx->ws, sigma_grid(src.one_total, ctx->num_sms), sigma_dev, radius_dev,
                                      static_cast<cudaStream_t>(stream));

@@ -15,12 +15,14 @@
 
 namespace fovea {
 
-constexpr int kMaxBlock = FOVEA_MAX_BLOCK;   // block side B <= 32
+constexpr int kMaxBlock = FOVEA_MAX_BLOCK;   // block side: <= 32, or a multiple of 32 up to this
 constexpr int kMaxRadius = FOVEA_MAX_RADIUS; // r <= 1023
 constexpr int kBuckets = 1024;               // radius buckets of the work-list sort
 constexpr int kTapPad = 16;                  // zero taps stored before offset 0
 
-// One frame as the kernels see it (host fills it in; 96 bytes).
+// One frame as the kernels see it (host fills it in; 104 bytes). Work items
+// are tiles of side T = min(B, 32); a block of side B > 32 (a multiple of 32)
+// is (B / T)^2 tiles that share its sigma.
 struct FrameDesc {
   const void* in;
   void* out;
@@ -30,7 +32,8 @@ struct FrameDesc {
   double sigma0, k;        // sigma law
   long long item0;         // index of the frame's first item in a batch
   int ox, oy;              // grid origin: block (bx, by) starts at (B bx - ox, B by - oy)
-  const float* smap;       // per-block sigma [nby][nbx] replacing the law, or null
+  const float* smap;       // per-block sigma [blocks along y][nbxb] replacing the law, or null
+  int T, nbxb;             // tile side; blocks along x (nbx, nby count tiles)
 };
 
 // Device-resident batch: header followed by the frame descriptors, then
@@ -117,7 +120,7 @@ __device__ __forceinline__ void block_sigma(int bx, int by, int B, int ox, int o
 // gives r = -1, which the caller flags.
 __device__ __forceinline__ void item_sigma(const FrameDesc& fd, int bx, int by, double& sigma, int& r) {
   if (fd.smap) {
-    sigma = (double)fd.smap[(size_t)by * fd.nbx + bx];
+    sigma = (double)fd.smap[(size_t)by * fd.nbxb + bx];
     r = (sigma >= 0.0 && sigma <= 1e6) ? (int)ceil(__dmul_rn(3.0, sigma)) : -1;
   } else {
     block_sigma(bx, by, fd.B, fd.ox, fd.oy, (double)fd.fx, (double)fd.fy, fd.sigma0, fd.k, sigma, r);

@@ -121,10 +121,10 @@ __device__ __forceinline__ void item_geometry(Item& it, const ItemInfo& inf, con
   it.isu8 = u8;
   it.r = inf.r;
   const int r = it.r;
-  const int bx = inf.block % fd.nbx, by = inf.block / fd.nbx;
-  const int xs = bx * fd.B - fd.ox, ys = by * fd.B - fd.oy;  // unclipped block start
+  const int tx = inf.block % fd.nbx, ty = inf.block / fd.nbx;  // tile
+  const int xs = tx * fd.T - fd.ox, ys = ty * fd.T - fd.oy;    // unclipped tile start
   it.x0 = max(0, xs); it.y0 = max(0, ys);
-  it.bw = min(xs + fd.B, it.W) - it.x0; it.bh = min(ys + fd.B, it.H) - it.y0;
+  it.bw = min(xs + fd.T, it.W) - it.x0; it.bh = min(ys + fd.T, it.H) - it.y0;
   it.gx0 = max(0, it.x0 - r);
   it.EW = min(it.W - 1, it.x0 + it.bw - 1 + r) - it.gx0 + 1;
   it.offx = it.gx0 - (it.x0 - r);

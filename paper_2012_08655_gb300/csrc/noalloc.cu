@@ -73,6 +73,7 @@ extern "C" int fovea_render_noalloc(const void* in_dev, void* out_dev, int width
   law.k = k;
   int st = check_frame(width, height, channels, format, block, law, fix_x, fix_y);
   if (st != FOVEA_OK) return st;
+  if (block > 32) return FOVEA_EUNSUPPORTED;  // one work item per block here
   const size_t nb = frame_bytes(width, height, channels, format);
   const char* a = static_cast<const char*>(in_dev);
   const char* b = static_cast<const char*>(out_dev);
@@ -106,7 +107,9 @@ extern "C" int fovea_render_noalloc(const void* in_dev, void* out_dev, int width
   src.one.out = out_dev;
   src.one.W = width; src.one.H = height; src.one.C = channels; src.one.fmt = format;
   src.one.B = block;
+  src.one.T = block;
   src.one.nbx = (width + block - 1) / block;
+  src.one.nbxb = src.one.nbx;
   src.one.nby = (height + block - 1) / block;
   src.one.fx = fix_x; src.one.fy = fix_y;
   src.one.sigma0 = sigma0; src.one.k = k;

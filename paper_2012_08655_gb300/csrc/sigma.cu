@@ -34,8 +34,9 @@ __global__ void __launch_bounds__(kSigmaThreads) sigma_kernel(FrameSource src, W
        i += (long long)gridDim.x * blockDim.x) {
     const int f = frame_of_item(src, i);
     const FrameDesc fd = load_frame(src, f);
-    const int b = (int)(i - fd.item0);
-    const int bx = b % fd.nbx, by = b / fd.nbx;
+    const int b = (int)(i - fd.item0);        // tile index
+    const int tpb = fd.B / fd.T;              // tiles per block side
+    const int bx = (b % fd.nbx) / tpb, by = (b / fd.nbx) / tpb;
     double sigma;
     int r;
     item_sigma(fd, bx, by, sigma, r);

@@ -32,7 +32,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 U8_HWC, F32_CHW = 0, 1
 MAX_RADIUS = 1023
-MAX_BLOCK = 32
+MAX_BLOCK = 256
 
 
 LAW_LINEAR, LAW_GEISLER_PERRY, LAW_MAP = 0, 1, 2

@@ -54,7 +54,8 @@ def test_strerror_and_invalid_arguments(lib):
     good = Law(0, 0.5, 0.02)
     assert create(64, 64, 3, 32, None, 0, ctypes.byref(h)) == -1           # null law
     assert create(64, 64, 3, 0, ctypes.byref(good), 0, ctypes.byref(h)) == -1   # block <= 0
-    assert create(64, 64, 3, 64, ctypes.byref(good), 0, ctypes.byref(h)) == -6  # block > 32
+    assert create(64, 64, 3, 48, ctypes.byref(good), 0, ctypes.byref(h)) == -6  # block > 32, not a multiple of 32
+    assert create(64, 64, 3, 288, ctypes.byref(good), 0, ctypes.byref(h)) == -6  # block > 256
     assert create(64, 64, 5, 32, ctypes.byref(good), 0, ctypes.byref(h)) == -1  # channels
     assert create(64, 64, 3, 32, ctypes.byref(good), 7, ctypes.byref(h)) == -1  # format
     assert create(64, 64, 3, 32, ctypes.byref(Law(0, -1.0, 0.02)), 0, ctypes.byref(h)) == -1

@@ -150,3 +150,40 @@ def test_batch_mixes_grids_laws_and_maps(fv):
     torch.cuda.synchronize()
     for fr, ref in zip(frames, refs):
         assert_u8_close(fr.out.cpu().numpy(), ref, min_equal=0.99)
+
+
+# ---------------------------------------------------------------- blocks larger than 32 (32 x 32 tiles sharing sigma)
+
+@pytest.mark.parametrize("tc", [0, 1, 2])
+@pytest.mark.parametrize("grid", [0, 1])
+def test_block_64_u8_matches_oracle(fv, tc, grid):
+    W, H, C, B = 500, 300, 3, 64
+    img = wl.grating_frame(H, W, C, seed=81)
+    fx, fy = 210.7, 140.2
+    ctx = fv.Context(W, H, C, B, 0.5, 0.02, fv.U8_HWC, grid=grid)
+    ctx.set_config(256, 0, 32, tensor_cores=tc)
+    x = to_dev(img)
+    y = torch.empty_like(x)
+    ctx.render(x, y, fx, fy)
+    sig, rad = ctx.sigma_table(fx, fy)
+    torch.cuda.synchronize()
+    org = (oracle.centred_origin(np.float32(fx), B), oracle.centred_origin(np.float32(fy), B)) if grid else (0, 0)
+    osig, orad = oracle.sigma_table(W, H, B, np.float32(fx), np.float32(fy), 0.5, 0.02, origin=org)
+    assert np.array_equal(rad.cpu().numpy(), orad)
+    ref = oracle.forward_u8(img, B, fx, fy, 0.5, 0.02, "hwc", origin=org)
+    assert_u8_close(y.cpu().numpy(), ref, min_equal=0.99)
+
+
+def test_block_64_f32_forward_and_backward(fv):
+    W, H, C, B = 150, 100, 2, 64
+    img = wl.uniform_f32((C, H, W), seed=82)
+    gout = wl.uniform_f32((C, H, W), seed=83)
+    ctx = fv.Context(W, H, C, B, 0.4, 0.05, fv.F32_CHW)
+    y = torch.empty(C, H, W, device="cuda")
+    gin = torch.empty(C, H, W, device="cuda")
+    ctx.render(to_dev(img), y, 60.0, 20.0)
+    ctx.backward(to_dev(gout), gin, 60.0, 20.0)
+    torch.cuda.synchronize()
+    assert_f32_close(y.cpu().numpy(), oracle.forward(img, B, 60.0, 20.0, 0.4, 0.05, "chw"))
+    np.testing.assert_allclose(gin.cpu().numpy(), oracle.adjoint(gout, B, 60.0, 20.0, 0.4, 0.05, "chw"),
+                               rtol=1e-5, atol=1e-5)
