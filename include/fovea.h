@@ -160,13 +160,19 @@ int fovea_grid(const fovea_ctx* ctx, float fix_x, float fix_y, int* nbx, int* nb
  * `frames` array is read before the call returns. */
 int fovea_render_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, void* stream);
 
-/* Foveate one frame held in HOST memory: copies the input to device staging
- * buffers the context owns, renders, and copies the result back into
- * `out_host`, all on `stream` (Algorithm 1 steps "transfer input image from
- * CPU pinned memory" and "transfer output image to CPU pinned memory"). Host
- * buffers should be pinned (cudaHostAlloc) for the copies to be asynchronous.
- * The call returns once the work is enqueued; out_host is valid after the
- * stream is synchronised. */
+/* Foveate one frame held in HOST memory (Algorithm 1's transfers of the
+ * input from and the output to pinned host memory around the render). The
+ * context owns two device staging slots and three internal streams (copy in,
+ * kernels, copy out); consecutive calls alternate slots, so the input copy of
+ * call i+1 and the output copy of call i-1 overlap the kernels of call i.
+ * Ordering: the kernels run after this context's earlier calls on `stream`;
+ * `stream` is made to wait for this call's output copy, so synchronising it
+ * (or any later work on it) sees out_host complete. The input copy starts as
+ * soon as the call is made: in_host must already hold the frame (it is not
+ * ordered after other work on `stream`) and must stay unchanged, like
+ * out_host, until `stream` is synchronised. Host buffers should be pinned
+ * (cudaHostAlloc) for the copies to be asynchronous. Not capturable into a
+ * CUDA graph (the internal streams are not part of the capture). */
 int fovea_render_host(fovea_ctx* ctx, const void* in_host, void* out_host, float fix_x,
                       float fix_y, void* stream);
 

@@ -75,10 +75,21 @@ struct fovea_ctx {
   // per-radius item lists of the single-frame path
   int* blist = nullptr;
   size_t blist_cap = 0;  // ints
-  // device staging for fovea_render_host
-  void* host_in_dev = nullptr;
-  void* host_out_dev = nullptr;
+  // fovea_render_host: two staging slots and three internal streams, so that
+  // the copies of one call overlap the kernels of the next
+  struct HostSlot {
+    void* in_dev = nullptr;
+    void* out_dev = nullptr;
+    cudaEvent_t ev_h2d = nullptr, ev_comp = nullptr, ev_d2h = nullptr;
+    bool used = false;
+  } hslot[2];
+  int hslot_next = 0;
+  cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
+  cudaEvent_t ev_entry = nullptr;
   size_t host_io_bytes = 0;
+  // set by every call that enqueues workspace use on the caller's stream;
+  // the next fovea_render_host orders its kernels after that work
+  bool caller_stream_used = false;
 };
 
 namespace fovea {
@@ -472,13 +483,12 @@ int fovea_create(int width, int height, int channels, int block, const fovea_sig
   return FOVEA_OK;
 }
 
-int fovea_render(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x, float fix_y, void* stream) {
-  if (!ctx || !in_dev || !out_dev || ctx->batch_only) return FOVEA_EINVAL;
+static int render_one(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x, float fix_y,
+                      cudaStream_t s) {
   int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->law, fix_x, fix_y);
   if (st != FOVEA_OK) return st;
   const size_t nb = frame_bytes(ctx->W, ctx->H, ctx->C, ctx->fmt);
   if (overlaps(in_dev, nb, out_dev, nb)) return FOVEA_EINVAL;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   FrameSource src;
   std::memset(&src, 0, sizeof(src));
   src.one = make_desc(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, in_dev, out_dev, fix_x, fix_y, ctx->law, 0);
@@ -528,13 +538,21 @@ int fovea_render(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x,
   return FOVEA_OK;
 }
 
+int fovea_render(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x, float fix_y, void* stream) {
+  if (!ctx || !in_dev || !out_dev || ctx->batch_only) return FOVEA_EINVAL;
+  ctx->caller_stream_used = true;
+  return render_one(ctx, in_dev, out_dev, fix_x, fix_y, static_cast<cudaStream_t>(stream));
+}
+
 int fovea_render_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, void* stream) {
   if (!ctx) return FOVEA_EINVAL;
+  ctx->caller_stream_used = true;
   return run_batch(ctx, frames, n, false, static_cast<cudaStream_t>(stream));
 }
 
 int fovea_backward_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, void* stream) {
   if (!ctx) return FOVEA_EINVAL;
+  ctx->caller_stream_used = true;
   return run_batch(ctx, frames, n, true, static_cast<cudaStream_t>(stream));
 }
 
@@ -545,22 +563,58 @@ int fovea_render_host(fovea_ctx* ctx, const void* in_host, void* out_host, float
   if (st != FOVEA_OK) return st;
   const size_t nb = frame_bytes(ctx->W, ctx->H, ctx->C, ctx->fmt);
   if (overlaps(in_host, nb, out_host, nb)) return FOVEA_EINVAL;
-  if (ctx->host_io_bytes < nb) {
-    if (ctx->host_in_dev) {
-      FOVEA_CUDA(cudaDeviceSynchronize());
-      cudaFree(ctx->host_in_dev);
-      cudaFree(ctx->host_out_dev);
-      ctx->host_in_dev = ctx->host_out_dev = nullptr;
+  if (!ctx->s_h2d) {
+    FOVEA_CUDA(cudaStreamCreateWithFlags(&ctx->s_h2d, cudaStreamNonBlocking));
+    FOVEA_CUDA(cudaStreamCreateWithFlags(&ctx->s_comp, cudaStreamNonBlocking));
+    FOVEA_CUDA(cudaStreamCreateWithFlags(&ctx->s_d2h, cudaStreamNonBlocking));
+    FOVEA_CUDA(cudaEventCreateWithFlags(&ctx->ev_entry, cudaEventDisableTiming));
+    for (auto& sl : ctx->hslot) {
+      FOVEA_CUDA(cudaEventCreateWithFlags(&sl.ev_h2d, cudaEventDisableTiming));
+      FOVEA_CUDA(cudaEventCreateWithFlags(&sl.ev_comp, cudaEventDisableTiming));
+      FOVEA_CUDA(cudaEventCreateWithFlags(&sl.ev_d2h, cudaEventDisableTiming));
     }
-    FOVEA_CUDA(cudaMalloc(&ctx->host_in_dev, nb));
-    FOVEA_CUDA(cudaMalloc(&ctx->host_out_dev, nb));
+  }
+  if (ctx->host_io_bytes < nb) {
+    FOVEA_CUDA(cudaDeviceSynchronize());
+    for (auto& sl : ctx->hslot) {
+      if (sl.in_dev) cudaFree(sl.in_dev);
+      if (sl.out_dev) cudaFree(sl.out_dev);
+      sl.in_dev = sl.out_dev = nullptr;
+      sl.used = false;
+    }
+    ctx->host_io_bytes = 0;
+    for (auto& sl : ctx->hslot) {
+      FOVEA_CUDA(cudaMalloc(&sl.in_dev, nb));
+      FOVEA_CUDA(cudaMalloc(&sl.out_dev, nb));
+    }
     ctx->host_io_bytes = nb;
   }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  FOVEA_CUDA(cudaMemcpyAsync(ctx->host_in_dev, in_host, nb, cudaMemcpyHostToDevice, s));
-  st = fovea_render(ctx, ctx->host_in_dev, ctx->host_out_dev, fix_x, fix_y, stream);
+  cudaStream_t caller = static_cast<cudaStream_t>(stream);
+  if (ctx->caller_stream_used) {
+    // earlier calls of this context on the caller's stream use the workspace
+    FOVEA_CUDA(cudaEventRecord(ctx->ev_entry, caller));
+    FOVEA_CUDA(cudaStreamWaitEvent(ctx->s_comp, ctx->ev_entry, 0));
+    ctx->caller_stream_used = false;
+  }
+  auto& sl = ctx->hslot[ctx->hslot_next];
+  ctx->hslot_next ^= 1;
+  // H2D once the slot's previous kernel has read its input
+  if (sl.used) FOVEA_CUDA(cudaStreamWaitEvent(ctx->s_h2d, sl.ev_comp, 0));
+  FOVEA_CUDA(cudaMemcpyAsync(sl.in_dev, in_host, nb, cudaMemcpyHostToDevice, ctx->s_h2d));
+  FOVEA_CUDA(cudaEventRecord(sl.ev_h2d, ctx->s_h2d));
+  // kernels once the input is there and the slot's previous result is copied out
+  FOVEA_CUDA(cudaStreamWaitEvent(ctx->s_comp, sl.ev_h2d, 0));
+  if (sl.used) FOVEA_CUDA(cudaStreamWaitEvent(ctx->s_comp, sl.ev_d2h, 0));
+  st = render_one(ctx, sl.in_dev, sl.out_dev, fix_x, fix_y, ctx->s_comp);
   if (st != FOVEA_OK) return st;
-  FOVEA_CUDA(cudaMemcpyAsync(out_host, ctx->host_out_dev, nb, cudaMemcpyDeviceToHost, s));
+  FOVEA_CUDA(cudaEventRecord(sl.ev_comp, ctx->s_comp));
+  FOVEA_CUDA(cudaStreamWaitEvent(ctx->s_d2h, sl.ev_comp, 0));
+  FOVEA_CUDA(cudaMemcpyAsync(out_host, sl.out_dev, nb, cudaMemcpyDeviceToHost, ctx->s_d2h));
+  FOVEA_CUDA(cudaEventRecord(sl.ev_d2h, ctx->s_d2h));
+  sl.used = true;
+  // the caller's stream completes this call's work (so later calls on it are
+  // ordered after these kernels, and synchronising it means out_host is ready)
+  FOVEA_CUDA(cudaStreamWaitEvent(caller, sl.ev_d2h, 0));
   return FOVEA_OK;
 }
 
@@ -572,6 +626,7 @@ int fovea_backward(fovea_ctx* ctx, const float* grad_out_dev, float* grad_in_dev
   if (st != FOVEA_OK) return st;
   const size_t nb = frame_bytes(ctx->W, ctx->H, ctx->C, ctx->fmt);
   if (overlaps(grad_out_dev, nb, grad_in_dev, nb)) return FOVEA_EINVAL;
+  ctx->caller_stream_used = true;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   FrameSource src;
   std::memset(&src, 0, sizeof(src));
@@ -597,6 +652,7 @@ int fovea_sigma_table(fovea_ctx* ctx, float fix_x, float fix_y, float* sigma_dev
   std::memset(&src, 0, sizeof(src));
   src.one = make_desc(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, nullptr, nullptr, fix_x, fix_y, ctx->law, 0, true);
   src.one_total = (long long)src.one.nbx * src.one.nby;
+  ctx->caller_stream_used = true;
   cudaError_t e = launch_sigma_order(src, ctx->ws, sigma_grid(src.one_total, ctx->num_sms), sigma_dev, radius_dev,
                                      static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e);
@@ -669,8 +725,17 @@ void fovea_destroy(fovea_ctx* ctx) {
     if (ctx->batch_host[i]) cudaFreeHost(ctx->batch_host[i]);
     if (ctx->batch_ev[i]) cudaEventDestroy(ctx->batch_ev[i]);
   }
-  cudaFree(ctx->host_in_dev);
-  cudaFree(ctx->host_out_dev);
+  for (auto& sl : ctx->hslot) {
+    if (sl.in_dev) cudaFree(sl.in_dev);
+    if (sl.out_dev) cudaFree(sl.out_dev);
+    if (sl.ev_h2d) cudaEventDestroy(sl.ev_h2d);
+    if (sl.ev_comp) cudaEventDestroy(sl.ev_comp);
+    if (sl.ev_d2h) cudaEventDestroy(sl.ev_d2h);
+  }
+  if (ctx->ev_entry) cudaEventDestroy(ctx->ev_entry);
+  if (ctx->s_h2d) cudaStreamDestroy(ctx->s_h2d);
+  if (ctx->s_comp) cudaStreamDestroy(ctx->s_comp);
+  if (ctx->s_d2h) cudaStreamDestroy(ctx->s_d2h);
   cudaFree(ctx->blist);
   delete ctx;
 }

@@ -146,6 +146,36 @@ def test_render_host_and_batch_match_render(fv):
     assert torch.equal(y1, y3)
 
 
+def test_render_host_pipelined_calls(fv):
+    """Consecutive host calls alternate staging slots and overlap one another's
+    copies and kernels; interleaved device-path calls on the same stream stay
+    ordered with them. Every result equals the device path's."""
+    frames = [wl.frame_1080p(seed=20 + i) for i in range(5)]
+    fix = [(960.0, 540.0), (100.5, 1000.25), (1800.0, 30.0), (500.0, 500.0), (1919.0, 0.0)]
+    s0 = frames[0]
+    ctx = fv.Context(1920, 1080, 3, 32, s0.sigma0, s0.k, fv.U8_HWC)
+    hin = [torch.from_numpy(f.image).pin_memory() for f in frames]
+    hout = [torch.empty_like(h).pin_memory() for h in hin]
+    dev_in = to_dev(frames[2].image)
+    dev_out = torch.empty_like(dev_in)
+    for i in range(5):
+        ctx.render_host(hin[i], hout[i], *fix[i])
+        if i == 2:
+            ctx.render(dev_in, dev_out, 7.0, 9.0)
+    torch.cuda.current_stream().synchronize()
+    ref_ctx = fv.Context(1920, 1080, 3, 32, s0.sigma0, s0.k, fv.U8_HWC)
+    for i in range(5):
+        x = to_dev(frames[i].image)
+        y = torch.empty_like(x)
+        ref_ctx.render(x, y, *fix[i])
+        torch.cuda.synchronize()
+        assert torch.equal(y.cpu(), hout[i]), i
+    y = torch.empty_like(dev_in)
+    ref_ctx.render(dev_in, y, 7.0, 9.0)
+    torch.cuda.synchronize()
+    assert torch.equal(y, dev_out)
+
+
 # ---------------------------------------------------------------- configurations
 
 @pytest.mark.parametrize("tc", [0, 1, 2])
