@@ -14,10 +14,14 @@ the sigma law of Appendix "Choosing the Standard Deviation"). In short:
     out(p)  = sum_{|i|,|j| <= r_b} w_i w_j / S^2 * in(clamp(p + (i, j)))
 
 written as a direct 2D sum per output pixel, and its adjoint as a scatter.
+Per-pixel foveation (Section 3.1's quality reference) is the same sum with
+sigma taken at every pixel's own centre; ``ssim_map`` is the SSIM of Wang et
+al. (2004) with its standard 11x11, sigma 1.5 Gaussian window.
 
 Parity status: every function here is pinned by tests under ``tests/``
 (scipy's uniform Gaussian filter, brute-force unit-vector matrices, closed
-forms and invariants); none is "parity unpinned".
+forms and invariants; for SSIM, closed forms of constant and affine pairs
+with local moments from scipy); none is "parity unpinned".
 """
 from __future__ import annotations
 
@@ -77,6 +81,12 @@ def _load():
             lib.oracle_gp_linear.restype = None
             lib.oracle_centred_origin.argtypes = [d, i]
             lib.oracle_centred_origin.restype = i
+            lib.oracle_pixel_sigma.argtypes = [i, i, d, d, d, d, ctypes.POINTER(d), ctypes.POINTER(i)]
+            lib.oracle_pixel_sigma.restype = None
+            lib.oracle_forward_pixel.argtypes = [p, p, i, i, i, l, l, l, d, d, d, d, p, l, i]
+            lib.oracle_forward_pixel.restype = None
+            lib.oracle_ssim_map.argtypes = [p, p, i, i, i, l, l, l, d, p, i]
+            lib.oracle_ssim_map.restype = None
             _lib = lib
     return _lib
 
@@ -204,3 +214,50 @@ def forward_u8(img_u8, block, fix_x, fix_y, sigma0, k, layout="hwc", blocks=None
     """
     v = forward(img_u8, block, fix_x, fix_y, sigma0, k, layout, blocks, nthreads, origin, sigma_map)
     return quantize_u8(np.nan_to_num(v, nan=0.0))
+
+
+def pixel_sigma(x, y, fix_x, fix_y, sigma0, k):
+    """(sigma, radius) of pixel (x, y) under per-pixel foveation."""
+    sg, r = ctypes.c_double(), ctypes.c_int()
+    _load().oracle_pixel_sigma(int(x), int(y), float(fix_x), float(fix_y), float(sigma0), float(k),
+                               ctypes.byref(sg), ctypes.byref(r))
+    return sg.value, r.value
+
+
+def forward_pixel(img, fix_x, fix_y, sigma0, k, layout="hwc", pixels=None, nthreads=0):
+    """Per-pixel ("perfect") foveation in binary64: every pixel blurred with
+    the sigma of its own centre. ``pixels`` optionally lists row-major pixel
+    indices y * W + x to compute; other pixels of the result are NaN."""
+    x = np.ascontiguousarray(img, dtype=np.float64)
+    H, W, C, sy, sx, sc = _geometry(x, layout)
+    out = np.full_like(x, np.nan)
+    if pixels is None:
+        pl, nl = None, 0
+    else:
+        parr = np.ascontiguousarray(np.asarray(pixels, dtype=np.int64))
+        pl, nl = parr.ctypes.data, int(parr.size)
+    _load().oracle_forward_pixel(x.ctypes.data, out.ctypes.data, W, H, C, sy, sx, sc, float(fix_x), float(fix_y),
+                                 float(sigma0), float(k), pl, nl, int(nthreads))
+    return out
+
+
+def forward_pixel_u8(img_u8, fix_x, fix_y, sigma0, k, layout="hwc", pixels=None, nthreads=0):
+    """Per-pixel foveation of a uint8 image, coded back to uint8 (unlisted
+    pixels come back as 0)."""
+    v = forward_pixel(img_u8, fix_x, fix_y, sigma0, k, layout, pixels, nthreads)
+    return quantize_u8(np.nan_to_num(v, nan=0.0))
+
+
+def ssim_map(a, b, data_range, layout="hwc", nthreads=0):
+    """SSIM map (H, W) of two images of equal shape, binary64: 11x11 Gaussian
+    window (sigma 1.5), C1 = (0.01 L)^2, C2 = (0.03 L)^2, clamp-to-edge
+    border, mean over channels."""
+    x = np.ascontiguousarray(a, dtype=np.float64)
+    y = np.ascontiguousarray(b, dtype=np.float64)
+    if x.shape != y.shape:
+        raise ValueError("images differ in shape")
+    H, W, C, sy, sx, sc = _geometry(x, layout)
+    m = np.zeros((H, W), np.float64)
+    _load().oracle_ssim_map(x.ctypes.data, y.ctypes.data, W, H, C, sy, sx, sc, float(data_range), m.ctypes.data,
+                            int(nthreads))
+    return m

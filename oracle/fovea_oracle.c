@@ -43,6 +43,11 @@
  *   g_in(q,c) += K[j][i] * g_out(p,c)  for every output p and tap (i,j)
  *                                      with clamp(p + (i,j)) = q.
  *
+ * Two further functions serve the per-pixel workload of Section 3.1: the
+ * per-pixel ("perfect") foveation the paper uses as its quality reference
+ * (every pixel blurred with the sigma of its own centre), and the SSIM map
+ * (Wang et al. 2004, standard window and constants) it is scored with.
+ *
  * Floating-point rules shared with any implementation that wants bit-exact
  * radii: the sigma law is evaluated in IEEE binary64 with no fused
  * multiply-add (this file must be compiled with -ffp-contract=off), sqrt is
@@ -325,4 +330,128 @@ int oracle_max_threads(void) {
 #else
   return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------
+ * Per-pixel ("perfect") foveation: the reference the paper scores its
+ * block-wise output against (Section 3.1, Fig. 3). Every pixel gets its own
+ * sigma from the distance between ITS centre (x + 1/2, y + 1/2) and the
+ * fixation, with the same law, the same truncated, normalised taps and the
+ * same clamp-to-edge border as the block-wise map:
+ *
+ *   sigma_p = sigma0 + k * |(x + 1/2, y + 1/2) - f|,  r_p = ceil(3 sigma_p)
+ *   out(x,y,c) = sum_{|i|,|j| <= r_p} w_i w_j / S^2 * in(clamp(x+i), clamp(y+j), c)
+ *
+ * (binary64, no FMA, as for the block sigma). Written as the direct 2D sum.
+ * ------------------------------------------------------------------------ */
+
+/* Sigma and radius of pixel (x, y). */
+void oracle_pixel_sigma(int x, int y, double fx, double fy, double sigma0, double k, double* sigma, int* radius) {
+  double dx = ((double)x + 0.5) - fx;
+  double dy = ((double)y + 0.5) - fy;
+  double dx2 = dx * dx;
+  double dy2 = dy * dy;
+  double e = sqrt(dx2 + dy2);
+  double ke = k * e;
+  double s = sigma0 + ke;
+  double three_s = 3.0 * s;
+  *sigma = s;
+  *radius = (int)ceil(three_s);
+}
+
+/* Per-pixel foveation of the listed pixels (row-major indices y * W + x; all
+ * pixels when pixel_list is NULL), every channel. Layout as oracle_forward_ex.
+ * Pixels not listed are left untouched. */
+void oracle_forward_pixel(const double* in, double* out, int W, int H, int C, long sy, long sx, long sc,
+                          double fx, double fy, double sigma0, double k, const long* pixel_list, long nlist,
+                          int nthreads) {
+  long np = pixel_list ? nlist : (long)W * (long)H;
+  int nt = 1;
+#ifdef _OPENMP
+  nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#else
+  (void)nthreads;
+#endif
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 64)
+  for (long t = 0; t < np; ++t) {
+    long p = pixel_list ? pixel_list[t] : t;
+    int x = (int)(p % W), y = (int)(p / W);
+    double sigma;
+    int r;
+    oracle_pixel_sigma(x, y, fx, fy, sigma0, k, &sigma, &r);
+    double* w = (double*)malloc((size_t)(2 * r + 1) * sizeof(double));
+    oracle_taps(sigma, r, w);
+    for (int c = 0; c < C; ++c) {
+      double acc = 0.0;
+      for (int j = -r; j <= r; ++j) {
+        int yy = clampi(y + j, 0, H - 1);
+        for (int i = -r; i <= r; ++i) {
+          int xx = clampi(x + i, 0, W - 1);
+          acc += (w[i + r] * w[j + r]) * in[yy * sy + xx * sx + c * sc];
+        }
+      }
+      out[y * sy + x * sx + c * sc] = acc;
+    }
+    free(w);
+  }
+}
+
+/* ------------------------------------------------------------------------
+ * SSIM map (the image-quality measure of Section 3.1; Wang, Bovik, Sheikh and
+ * Simoncelli 2004, with their standard settings): for every pixel and
+ * channel, local statistics under an 11 x 11 Gaussian window of standard
+ * deviation 1.5 normalised to unit sum (clamp-to-edge at the border),
+ *
+ *   mu_a = sum w a,  var_a = sum w (a - mu_a)^2,  cov = sum w (a - mu_a)(b - mu_b)
+ *   SSIM = (2 mu_a mu_b + C1)(2 cov + C2) / ((mu_a^2 + mu_b^2 + C1)(var_a + var_b + C2))
+ *
+ * with C1 = (0.01 L)^2, C2 = (0.03 L)^2 for dynamic range L. The map value of
+ * a pixel is the mean over its channels. Written out pixel by pixel in
+ * binary64, two passes over the window (means first, then the centred
+ * moments).
+ * ------------------------------------------------------------------------ */
+void oracle_ssim_map(const double* a, const double* b, int W, int H, int C, long sy, long sx, long sc,
+                     double L, double* map, int nthreads) {
+  const int R = 5;
+  double g[11], gs = 0.0;
+  for (int i = -R; i <= R; ++i) {
+    g[i + R] = exp(-((double)i * (double)i) / (2.0 * 1.5 * 1.5));
+    gs += g[i + R];
+  }
+  for (int i = 0; i <= 2 * R; ++i) g[i] /= gs;
+  const double C1 = (0.01 * L) * (0.01 * L);
+  const double C2 = (0.03 * L) * (0.03 * L);
+  int nt = 1;
+#ifdef _OPENMP
+  nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#else
+  (void)nthreads;
+#endif
+#pragma omp parallel for num_threads(nt) schedule(static)
+  for (int y = 0; y < H; ++y)
+    for (int x = 0; x < W; ++x) {
+      double total = 0.0;
+      for (int c = 0; c < C; ++c) {
+        double ma = 0.0, mb = 0.0;
+        for (int j = -R; j <= R; ++j)
+          for (int i = -R; i <= R; ++i) {
+            long q = clampi(y + j, 0, H - 1) * sy + clampi(x + i, 0, W - 1) * sx + c * sc;
+            double wij = g[i + R] * g[j + R];
+            ma += wij * a[q];
+            mb += wij * b[q];
+          }
+        double va = 0.0, vb = 0.0, cv = 0.0;
+        for (int j = -R; j <= R; ++j)
+          for (int i = -R; i <= R; ++i) {
+            long q = clampi(y + j, 0, H - 1) * sy + clampi(x + i, 0, W - 1) * sx + c * sc;
+            double wij = g[i + R] * g[j + R];
+            double da = a[q] - ma, db = b[q] - mb;
+            va += wij * da * da;
+            vb += wij * db * db;
+            cv += wij * da * db;
+          }
+        total += ((2.0 * ma * mb + C1) * (2.0 * cv + C2)) / ((ma * ma + mb * mb + C1) * (va + vb + C2));
+      }
+      map[(long)y * W + x] = total / (double)C;
+    }
 }

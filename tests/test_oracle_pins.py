@@ -361,3 +361,118 @@ def test_sigma_map_equal_to_the_law_reproduces_it_and_a_constant_map_is_uniform(
     lhs = np.vdot(c, g)
     rhs = np.vdot(img, oracle.adjoint(g, B, 0.0, 0.0, 0.0, 0.0, "chw", sigma_map=const))
     np.testing.assert_allclose(lhs, rhs, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- per-pixel foveation
+
+def _pixel_sigma_def(x, y, fx, fy, s0, k):
+    return s0 + k * np.hypot(x + 0.5 - fx, y + 0.5 - fy)
+
+
+def test_pixel_sigma_closed_form():
+    # Pixel (3, 4) has centre (3.5, 4.5); from fixation (0.5, 0.5) that is a 3-4-5 triangle.
+    assert oracle.pixel_sigma(3, 4, 0.5, 0.5, 0.25, 0.5) == (2.75, 9)
+    # A fixation on a pixel centre gives that pixel sigma0.
+    assert oracle.pixel_sigma(7, 2, 7.5, 2.5, 1.1, 3.0) == (1.1, 4)
+    # Mirror pixel about the fixation has the same sigma.
+    assert oracle.pixel_sigma(10, 3, 6.0, 6.0, 0.5, 0.1) == oracle.pixel_sigma(1, 8, 6.0, 6.0, 0.5, 0.1)
+
+
+@pytest.mark.parametrize("W,H,C,layout,fx,fy,s0,k", [
+    (24, 18, 1, "hwc", 7.3, 11.9, 0.4, 0.21),
+    (19, 15, 3, "hwc", -3.0, 4.0, 0.0, 0.3),     # fixation outside the frame, sigma0 = 0
+    (16, 21, 2, "chw", 8.0, 10.5, 0.7, 0.12),
+])
+def test_perpixel_equals_uniform_blur_at_each_pixels_sigma(W, H, C, layout, fx, fy, s0, k):
+    """Every output pixel equals scipy's uniform Gaussian blur at that pixel's
+    own sigma (pixel-centre distance), read at that pixel."""
+    shape = (C, H, W) if layout == "chw" else (H, W, C)
+    img = wl.uniform_f32(shape, seed=5).astype(np.float64)
+    out = oracle.forward_pixel(img, fx, fy, s0, k, layout)
+    for y in range(H):
+        for x in range(W):
+            sg = _pixel_sigma_def(x, y, fx, fy, s0, k)
+            d = abs(3 * sg - round(3 * sg))
+            assert d == 0 or d > 1e-9  # an exact integer 3 sigma is unambiguous
+            r = int(np.ceil(3 * sg))
+            if r == 0:
+                ref = img
+            else:
+                ref = _scipy_uniform(img, sg, r, layout)
+            if layout == "chw":
+                np.testing.assert_allclose(out[:, y, x], ref[:, y, x], rtol=0, atol=1e-13)
+            else:
+                np.testing.assert_allclose(out[y, x], ref[y, x], rtol=0, atol=1e-13)
+
+
+def test_perpixel_is_blockwise_with_one_pixel_blocks():
+    """A 1x1 block's centre is its pixel's centre: per-pixel foveation is the
+    block-wise map at B = 1 (a different code path of the oracle, pinned to
+    scipy block by block)."""
+    img = wl.uniform_f32((23, 31, 3), seed=8).astype(np.float64)
+    a = oracle.forward_pixel(img, 12.25, 5.5, 0.3, 0.15, "hwc")
+    b = oracle.forward(img, 1, 12.25, 5.5, 0.3, 0.15, "hwc")
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-14)
+
+
+def test_perpixel_mirror_constant_and_sampling():
+    W, H = 26, 20
+    img = wl.uniform_f32((H, W), seed=9).astype(np.float64)
+    fx, fy = 9.75, 6.5
+    a = oracle.forward_pixel(img, fx, fy, 0.5, 0.2)
+    m = oracle.forward_pixel(img[:, ::-1], W - fx, fy, 0.5, 0.2)
+    np.testing.assert_allclose(a, m[:, ::-1], rtol=0, atol=1e-13)
+    m = oracle.forward_pixel(img[::-1, :], fx, H - fy, 0.5, 0.2)
+    np.testing.assert_allclose(a, m[::-1, :], rtol=0, atol=1e-13)
+    c = oracle.forward_pixel(np.full((H, W), 0.375), fx, fy, 0.5, 0.2)
+    np.testing.assert_allclose(c, 0.375, rtol=0, atol=1e-14)
+    pix = [0, W - 1, 7 * W + 3, H * W - 1]
+    s = oracle.forward_pixel(img, fx, fy, 0.5, 0.2, pixels=pix)
+    flat_a, flat_s = a.reshape(-1), s.reshape(-1)
+    assert np.array_equal(flat_s[pix], flat_a[pix])
+    assert np.isnan(np.delete(flat_s, pix)).all()
+
+
+# ---------------------------------------------------------------- SSIM
+
+def _gauss_stats(img):
+    f = lambda v: ndimage.gaussian_filter(v, 1.5, mode="nearest", radius=5)
+    mu = f(img)
+    return mu, f(img * img) - mu * mu
+
+
+def test_ssim_identical_images_and_constants():
+    a = wl.uniform_f32((17, 23), seed=1).astype(np.float64)
+    np.testing.assert_allclose(oracle.ssim_map(a, a, 1.0), 1.0, rtol=0, atol=1e-14)
+    al, be, L = 40.0, 200.0, 255.0
+    C1 = (0.01 * L) ** 2
+    m = oracle.ssim_map(np.full((9, 12), al), np.full((9, 12), be), L)
+    np.testing.assert_allclose(m, (2 * al * be + C1) / (al * al + be * be + C1), rtol=1e-14)
+
+
+@pytest.mark.parametrize("s,t", [(0.6, 0.2), (-0.7, 0.9), (1.0, 0.05)])
+def test_ssim_of_an_affine_copy_matches_library_moments(s, t):
+    """b = s a + t: cov = s var_a, var_b = s^2 var_a, mu_b = s mu_a + t, so
+    SSIM = l * (2 s var + C2) / ((1 + s^2) var + C2) with the local moments
+    taken from scipy's Gaussian filter (sigma 1.5, radius 5, nearest)."""
+    a = wl.uniform_f32((21, 26), seed=4).astype(np.float64)
+    b = s * a + t
+    mu, var = _gauss_stats(a)
+    mub = s * mu + t
+    C1, C2 = 0.01 ** 2, 0.03 ** 2
+    ref = (2 * mu * mub + C1) / (mu * mu + mub * mub + C1) * (2 * s * var + C2) / ((1 + s * s) * var + C2)
+    np.testing.assert_allclose(oracle.ssim_map(a, b, 1.0), ref, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(oracle.ssim_map(b, a, 1.0), ref, rtol=0, atol=1e-12)
+
+
+def test_ssim_range_scaling_and_channel_mean():
+    rng = np.random.default_rng(2)
+    a = rng.random((14, 19, 3))
+    b = np.clip(a + 0.1 * rng.standard_normal(a.shape), 0, 1)
+    m1 = oracle.ssim_map(a, b, 1.0, "hwc")
+    np.testing.assert_allclose(oracle.ssim_map(255 * a, 255 * b, 255.0, "hwc"), m1, rtol=0, atol=1e-12)
+    per = [oracle.ssim_map(a[:, :, c], b[:, :, c], 1.0) for c in range(3)]
+    np.testing.assert_allclose(m1, np.mean(per, axis=0), rtol=0, atol=1e-14)
+    chw = oracle.ssim_map(np.moveaxis(a, 2, 0).copy(), np.moveaxis(b, 2, 0).copy(), 1.0, "chw")
+    np.testing.assert_allclose(chw, m1, rtol=0, atol=1e-14)
+    assert (m1 < 1).all() and (m1 > -1).all()
