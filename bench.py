@@ -72,6 +72,8 @@ def parse_args():
     p.add_argument("--no-extras", action="store_true", help="skip the batched and served legs")
     p.add_argument("--served-seconds", type=float, default=10.0)
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--pixelwise-only", action="store_true",
+                   help="run only the per-pixel foveation leg (--steps launches per kernel) and print it")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiling runs)")
     p.add_argument("--tensor-cores", type=int, choices=[0, 1, 2], default=None,
                    help="force the forward kernel (0: fp32 FMA, 1: mma.sync, 2: tcgen05 vertical pass) "
@@ -407,6 +409,86 @@ def block_sweep_leg(fv, torch):
     return {"workload": WORKLOAD.replace("32x32 blocks", "B x B blocks"), "by_block": res}
 
 
+def pixel_radii(width, height, fix_x, fix_y, sigma0, k):
+    """Per-pixel radius ceil(3 sigma) at pixel centres (the workload's size)."""
+    import numpy as np
+    x = np.arange(width) + 0.5
+    y = np.arange(height) + 0.5
+    e = np.sqrt((x[None, :] - fix_x) ** 2 + (y[:, None] - fix_y) ** 2)
+    return np.ceil(3 * (sigma0 + k * e))
+
+
+def pixelwise_mma_macs(width, height, channels, fix_x, fix_y, sigma0, k):
+    """fp16 MMA multiply-adds one launch of the tensor-core per-pixel kernel
+    issues: per 16 x 16 tile of radius R, per output column lx and channel
+    plane, hi and lo products over ceil((16 + 2R) / 16) k-steps and the
+    ceil((lx + 2R + 1) / 32) groups of 32 pixels (4 n-tiles) that hold the
+    column's window."""
+    import numpy as np
+    r = pixel_radii(width, height, fix_x, fix_y, sigma0, k)
+    macs = 0
+    for y0 in range(0, height, 16):
+        for x0 in range(0, width, 16):
+            R = int(r[y0:y0 + 16, x0:x0 + 16].max())
+            ks = (16 + 2 * R + 15) // 16
+            lx = np.arange(min(16, width - x0))
+            groups = int(((lx + 2 * R + 1 + 31) // 32).sum())
+            macs += 2 * ks * 4 * groups * channels * 16 * 8 * 16
+    return float(macs)
+
+
+def pixelwise_leg(fv, torch, reps: int = 20):
+    """Per-pixel ("perfect") foveation of the 1080p frame (Section 3.1's
+    quality reference) on both kernels, and the SSIM of the block-wise output
+    (anchored and fixation-centred grid) against it."""
+    import numpy as np
+    from paper_2012_08655_gb300 import workloads as wl
+    frame = wl.frame_1080p(seed=0)
+    x = torch.from_numpy(frame.image).cuda()
+    y = torch.empty_like(x)
+    r = pixel_radii(W, H, *FIX, SIGMA0, K_SLOPE)
+    direct = float(C * ((2 * r + 1) ** 2).sum())
+    res = {"workload": "1920x1080 RGB uint8 frame, every pixel its own sigma = 0.5 + 0.02 e px, "
+                       "fixation at the centre",
+           "direct_fmas_per_launch": direct, "max_radius": int(r.max())}
+    for tc, n in ((1, reps), (0, max(2, reps // 8))):
+        ctx = fv.Context(W, H, C, B, SIGMA0, K_SLOPE, fv.U8_HWC)
+        ctx.set_config(256, 0, 32, tensor_cores=tc)
+        for _ in range(3):
+            ctx.render_pixelwise(x, y, *FIX)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n):
+            ctx.render_pixelwise(x, y, *FIX)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        leg = {"ms": ms, "mpix_s": W * H / ms / 1e3,
+               "direct_tflops": 2 * direct / (ms * 1e-3) / 1e12}
+        if tc:
+            macs = pixelwise_mma_macs(W, H, C, *FIX, SIGMA0, K_SLOPE)
+            leg["mma_flops_per_launch"] = 2 * macs
+            leg["mma_tflops"] = 2 * macs / (ms * 1e-3) / 1e12
+        res["tensor_core_kernel" if tc else "fp32_kernel"] = leg
+    ref = fv.foveate_pixelwise(x, *FIX, SIGMA0, K_SLOPE)
+    for name, grid in (("anchored_grid", fv.GRID_ANCHORED), ("centred_grid", fv.GRID_CENTRED)):
+        blk = fv.foveate(x, *FIX, SIGMA0, K_SLOPE, grid=grid)
+        m, mean = fv.ssim(blk, ref)
+        mh = m.cpu().numpy()
+        reg = mh[:H // 32 * 32, :W // 32 * 32].reshape(H // 32, 32, W // 32, 32).mean(axis=(1, 3))
+        res["ssim_" + name] = {"mean": mean, "min": float(mh.min()), "worst_32px_region": float(reg.min())}
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fv.ssim(ref, ref, want_map=False)
+    e1.record()
+    torch.cuda.synchronize()
+    res["ssim_ms"] = e0.elapsed_time(e1) / reps
+    return res
+
+
 def served_leg(fv, torch, seconds: float, max_batch: int):
     """Replay the Poisson request stream through the serving loop."""
     import numpy as np
@@ -468,6 +550,10 @@ def run_ours(args):
 
     world, rank, local = dist_setup(args)
     from paper_2012_08655_gb300 import fovea as fv
+    if args.pixelwise_only:
+        if rank == 0:
+            print(json.dumps({"pixelwise": pixelwise_leg(fv, torch, reps=args.steps)}), flush=True)
+        return 0
     from paper_2012_08655_gb300 import workloads as wl
 
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -583,6 +669,7 @@ def run_ours(args):
         extras["batched"] = batched_leg(fv, torch)
         extras["train"] = train_leg(fv, torch)
         extras["block_sweep"] = block_sweep_leg(fv, torch)
+        extras["pixelwise"] = pixelwise_leg(fv, torch)
         served = served_leg(fv, torch, args.served_seconds, max_batch=64)
         plain = served_leg(fv, torch, args.served_seconds, max_batch=1)
         served["plain_per_frame"] = {k: plain[k] for k in ("p50_ms", "p99_ms", "mpix_s", "mean_batch")}

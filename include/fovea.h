@@ -187,6 +187,34 @@ int fovea_backward(fovea_ctx* ctx, const float* grad_out_dev, float* grad_in_dev
  * `in` is grad_out and `out` (overwritten) is grad_in. */
 int fovea_backward_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, void* stream);
 
+/* Per-pixel ("perfect") foveation: the reference the paper scores its
+ * block-wise output against (Section 3.1, Fig. 3). Every pixel is blurred
+ * with the Gaussian of its own eccentricity: sigma_p = sigma0 + k * |c_p - f|
+ * for the pixel centre c_p = (x + 1/2, y + 1/2) (binary64, the block law's
+ * operations in the same order), r_p = ceil(3 sigma_p), taps of Eq. 1
+ * truncated at r_p and normalised, clamp-to-edge border; this equals the
+ * block-wise map with 1 x 1 blocks. Uses the context's frame shape, format
+ * and law (linear or Geisler-Perry; a context with a per-block sigma map is
+ * refused with FOVEA_EINVAL); its block size and grid mode play no part.
+ * uint8 frames run on the tensor cores (unless the context's configuration
+ * has tensor_cores = 0) while the shared memory they need fits, else, like
+ * float32 frames, on the fp32 kernel. Radii above 255 anywhere in the frame
+ * are refused with FOVEA_EUNSUPPORTED. in_dev and out_dev must not overlap. */
+int fovea_render_pixelwise(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x, float fix_y,
+                           void* stream);
+
+/* SSIM map of two device images of the same shape and format (the quality
+ * measure of Section 3.1; Wang, Bovik, Sheikh and Simoncelli 2004): 11 x 11
+ * Gaussian window of standard deviation 1.5 normalised to unit sum,
+ * clamp-to-edge border, C1 = (0.01 L)^2, C2 = (0.03 L)^2 with L = data_range
+ * (<= 0 selects 255 for uint8 and 1 for float32); the value of a pixel is the
+ * mean over its channels. Writes the height x width float map to map_dev
+ * and/or the sum of the map (one double, zeroed by the call) to sum_dev;
+ * either may be NULL, not both. Computed in fp32 (values taken relative to
+ * L/2), within about 1e-4 of the binary64 definition. */
+int fovea_ssim(int width, int height, int channels, int format, const void* a_dev, const void* b_dev,
+               double data_range, float* map_dev, double* sum_dev, void* stream);
+
 /* Per-block sigma (float32, rounded from the binary64 value) and radius for
  * the context's frame at the given fixation, row-major over the block grid
  * (nby x nbx of fovea_grid), written to device arrays. This is the table the

@@ -659,6 +659,78 @@ int fovea_sigma_table(fovea_ctx* ctx, float fix_x, float fix_y, float* sigma_dev
   return FOVEA_OK;
 }
 
+namespace {
+
+// Largest per-pixel radius of a W x H frame: the farthest pixel centre from
+// the fixation is a corner pixel's; every step rounded on its own, as the
+// device computes it.
+int pixel_radius_bound(int W, int H, double fx, double fy, double sigma0, double k) {
+  const int xs[2] = {0, W - 1}, ys[2] = {0, H - 1};
+  int rmax = 0;
+  for (int x : xs)
+    for (int y : ys) {
+      volatile double cx = (double)x + 0.5;
+      volatile double cy = (double)y + 0.5;
+      volatile double dx = cx - fx;
+      volatile double dy = cy - fy;
+      volatile double dx2 = dx * dx;
+      volatile double dy2 = dy * dy;
+      volatile double e = std::sqrt(dx2 + dy2);
+      volatile double ke = k * e;
+      volatile double sg = sigma0 + ke;
+      volatile double s3 = 3.0 * sg;
+      const double rc = std::ceil(s3);
+      rmax = std::max(rmax, rc > 1e9 ? 1000000000 : (int)rc);
+    }
+  return rmax;
+}
+
+}  // namespace
+
+int fovea_render_pixelwise(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x, float fix_y,
+                           void* stream) {
+  if (!ctx || !in_dev || !out_dev || ctx->batch_only) return FOVEA_EINVAL;
+  if (ctx->law.smap) return FOVEA_EINVAL;  // a per-block map gives no per-pixel law
+  int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->law, fix_x, fix_y);
+  if (st != FOVEA_OK) return st;
+  const size_t nb = frame_bytes(ctx->W, ctx->H, ctx->C, ctx->fmt);
+  if (overlaps(in_dev, nb, out_dev, nb)) return FOVEA_EINVAL;
+  const int rmax = pixel_radius_bound(ctx->W, ctx->H, fix_x, fix_y, ctx->law.sigma0, ctx->law.k);
+  if (rmax > kPixelMaxRadius) return FOVEA_EUNSUPPORTED;
+  const bool isu8 = ctx->fmt == FOVEA_U8_HWC;
+  const bool tc = isu8 && ctx->cfg.tc != 0 && pixel_tc_fits(rmax, ctx->C);
+  if (!tc && pixel_fp32_rows(rmax, ctx->C) <= 0) return FOVEA_EUNSUPPORTED;
+  ctx->caller_stream_used = true;
+  PixelParams pp;
+  pp.in = in_dev;
+  pp.out = out_dev;
+  pp.W = ctx->W; pp.H = ctx->H; pp.C = ctx->C; pp.isu8 = isu8 ? 1 : 0;
+  pp.fx = fix_x; pp.fy = fix_y; pp.sigma0 = ctx->law.sigma0; pp.k = ctx->law.k;
+  pp.rmax = rmax;
+  pp.words = ((size_t)ctx->W * ctx->C) % 4 == 0 && reinterpret_cast<uintptr_t>(in_dev) % 4 == 0;
+  pp.err = ctx->ws.counters ? ctx->ws.counters + CNT_ERROR : nullptr;
+  if (!pp.err) return FOVEA_EINVAL;
+  cudaError_t e = launch_pixel_forward(pp, tc, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e);
+  return FOVEA_OK;
+}
+
+int fovea_ssim(int width, int height, int channels, int format, const void* a_dev, const void* b_dev,
+               double data_range, float* map_dev, double* sum_dev, void* stream) {
+  if (!a_dev || !b_dev || width <= 0 || height <= 0) return FOVEA_EINVAL;
+  if (channels < 1 || channels > 4) return FOVEA_EINVAL;
+  if (format != FOVEA_U8_HWC && format != FOVEA_F32_CHW) return FOVEA_EINVAL;
+  if (!map_dev && !sum_dev) return FOVEA_EINVAL;
+  if ((long long)width * height * channels > (1ll << 31) - 1) return FOVEA_EUNSUPPORTED;
+  double L = data_range;
+  if (L <= 0.0) L = format == FOVEA_U8_HWC ? 255.0 : 1.0;
+  if (!std::isfinite(L)) return FOVEA_EINVAL;
+  cudaError_t e = launch_ssim(a_dev, b_dev, width, height, channels, format == FOVEA_U8_HWC ? 1 : 0, (float)L,
+                              map_dev, sum_dev, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e);
+  return FOVEA_OK;
+}
+
 int fovea_gp_law(int width, int height, double e_corner_deg, double* sigma0, double* k) {
   if (width <= 0 || height <= 0 || !sigma0 || !k || !finite_nonneg(e_corner_deg)) return FOVEA_EINVAL;
   const double e2 = 2.3;

@@ -323,4 +323,58 @@ cudaError_t launch_adjoint(const FrameSource& src, const Workspace& ws, int rmax
                            cudaStream_t s);
 int adjoint_max_ctas_per_sm(int rmax);
 
+// ------------------------------------------------------------------ per-pixel foveation
+// (pixel_forward.cu): every pixel blurred with the sigma of its own centre.
+
+struct PixelParams {
+  const void* in;
+  void* out;
+  int W, H, C, isu8;       // uint8 HWC or float32 CHW
+  double fx, fy, sigma0, k;
+  int rmax;                // bound on every pixel's radius (the frame's corner pixels)
+  int words;               // uint8 rows may be read as aligned 32-bit words
+  unsigned int* err;       // bit 0: a pixel's radius exceeded rmax (never expected)
+};
+
+constexpr size_t kPixelSmemBudget = 220 * 1024;
+constexpr int kPixelMaxRadius = 255;
+
+// Shared memory of the tensor-core per-pixel kernel (uint8 HWC, 16 x 16
+// output tiles): per channel a plane of `pr` pair rows of `pp` bytes, where a
+// pair row interleaves two staged rows byte by byte in 8-byte words of 4
+// pixels (pp = 32 or 96 mod 128: conflict-free 8-byte fragment loads); then
+// the per-pixel tap tables (tp 4-byte entries for each of the 256 pixels)
+// and small per-pixel arrays.
+struct PixelTcLayout {
+  int tp, pp, pr, sw;
+  size_t plane_bytes, tile_bytes, tap_bytes, total;
+};
+__host__ __device__ inline PixelTcLayout pixel_tc_layout(int rmax, int C) {
+  PixelTcLayout L;
+  // Table of a pixel: offsets 0 .. rmax, then zero entries; the stride is
+  // 9 or 23 mod 32 words, which spreads the fragment gathers over the banks.
+  L.tp = rmax + 2;
+  while (L.tp % 32 != 9 && L.tp % 32 != 23) ++L.tp;
+  L.sw = (16 + 2 * rmax + 31) / 32 * 32;           // staged pixels per row (whole 32-pixel groups)
+  int pp = 2 * L.sw;
+  while (pp % 128 != 32 && pp % 128 != 96) pp += 32;
+  L.pp = pp;
+  L.pr = (16 + 2 * rmax + 15) / 16 * 8;            // pair rows: whole 16-row k-steps
+  L.plane_bytes = (size_t)L.pr * L.pp;
+  L.tile_bytes = L.plane_bytes * C;
+  L.tap_bytes = (size_t)256 * L.tp * 4;
+  L.total = L.tile_bytes + L.tap_bytes + 2 * 256 * 4 + 16;
+  return L;
+}
+bool pixel_tc_fits(int rmax, int C);
+// Rows of input the fp32 per-pixel kernel stages at a time (0: rmax too
+// large), and its shared memory for that chunk.
+int pixel_fp32_rows(int rmax, int C);
+size_t pixel_fp32_smem(int rmax, int C, int rb);
+cudaError_t launch_pixel_forward(const PixelParams& pp, bool tensor_cores, cudaStream_t s);
+
+// ------------------------------------------------------------------ SSIM (ssim.cu)
+cudaError_t launch_ssim(const void* a, const void* b, int W, int H, int C, int isu8, float data_range,
+                        float* map, double* sum, cudaStream_t s);
+
 }  // namespace fovea

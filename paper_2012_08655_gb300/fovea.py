@@ -75,6 +75,8 @@ _sig = {
     "fovea_render": (_i, [_vp, _vp, _vp, _f, _f, _vp]),
     "fovea_render_batch": (_i, [_vp, ctypes.POINTER(Frame), _i, _vp]),
     "fovea_render_host": (_i, [_vp, _vp, _vp, _f, _f, _vp]),
+    "fovea_render_pixelwise": (_i, [_vp, _vp, _vp, _f, _f, _vp]),
+    "fovea_ssim": (_i, [_i, _i, _i, _i, _vp, _vp, _d, _vp, _vp, _vp]),
     "fovea_backward": (_i, [_vp, _vp, _vp, _f, _f, _vp]),
     "fovea_backward_batch": (_i, [_vp, ctypes.POINTER(Frame), _i, _vp]),
     "fovea_sigma_table": (_i, [_vp, _f, _f, _vp, _vp, _vp]),
@@ -210,6 +212,15 @@ class Context:
                                  _stream_handle(stream)), "fovea_render")
         return out
 
+    def render_pixelwise(self, inp: torch.Tensor, out: torch.Tensor, fix_x: float, fix_y: float, stream=None):
+        """Per-pixel ("perfect") foveation of one device frame with this
+        context's shape, format and law (``fovea_render_pixelwise``)."""
+        _require_device_frame(inp, "input")
+        _require_device_frame(out, "output")
+        _check(_lib.fovea_render_pixelwise(self._h, inp.data_ptr(), out.data_ptr(), float(fix_x), float(fix_y),
+                                           _stream_handle(stream)), "fovea_render_pixelwise")
+        return out
+
     def render_host(self, inp: torch.Tensor, out: torch.Tensor, fix_x: float, fix_y: float, stream=None):
         if inp.is_cuda or out.is_cuda:
             raise ValueError("render_host takes host (preferably pinned) tensors")
@@ -343,6 +354,38 @@ def foveate(x: torch.Tensor, fix_x: float, fix_y: float, sigma0: float = 0.5, k:
     if out is None:
         out = torch.empty_like(x)
     return ctx.render(x, out, fix_x, fix_y)
+
+
+def foveate_pixelwise(x: torch.Tensor, fix_x: float, fix_y: float, sigma0: float = 0.5, k: float = 0.02,
+                      out: Optional[torch.Tensor] = None, *, e_corner: Optional[float] = None) -> torch.Tensor:
+    """Per-pixel ("perfect") foveation of one frame on the GPU: every pixel
+    blurred with the sigma of its own centre (the block-wise map's quality
+    reference)."""
+    _require_device_frame(x, "input")
+    fmt = _fmt_of(x)
+    w, h, c = _shape_of(x, fmt)
+    ctx = _ctx_for(w, h, c, 32, sigma0, k, fmt, GRID_ANCHORED, e_corner)
+    if out is None:
+        out = torch.empty_like(x)
+    return ctx.render_pixelwise(x, out, fix_x, fix_y)
+
+
+def ssim(a: torch.Tensor, b: torch.Tensor, data_range: float = 0.0, want_map: bool = True, stream=None):
+    """SSIM of two device frames of one shape and format (``fovea_ssim``):
+    returns (map, mean) with the (H, W) float32 map (None unless
+    ``want_map``) and the mean over the map as a Python float."""
+    _require_device_frame(a, "a")
+    _require_device_frame(b, "b")
+    if a.shape != b.shape or a.dtype != b.dtype:
+        raise ValueError("SSIM needs two frames of one shape and dtype")
+    fmt = _fmt_of(a)
+    w, h, c = _shape_of(a, fmt)
+    m = torch.empty((h, w), dtype=torch.float32, device=a.device) if want_map else None
+    total = torch.empty(1, dtype=torch.float64, device=a.device)
+    _check(_lib.fovea_ssim(w, h, c, fmt, a.data_ptr(), b.data_ptr(), float(data_range),
+                           m.data_ptr() if m is not None else None, total.data_ptr(), _stream_handle(stream)),
+           "fovea_ssim")
+    return m, float(total.item()) / (w * h)
 
 
 def render_noalloc(x: torch.Tensor, out: torch.Tensor, fix_x: float, fix_y: float, sigma0: float = 0.5,

@@ -28,7 +28,8 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ["fovea_create", "fovea_render", "fovea_render_batch", "fovea_backward",
-                     "fovea_destroy", "fovea_strerror", "fovea_sigma_table", "fovea_render_host"]:
+                     "fovea_destroy", "fovea_strerror", "fovea_sigma_table", "fovea_render_host",
+                     "fovea_render_pixelwise", "fovea_ssim"]:
         assert required in names
 
 
@@ -76,6 +77,15 @@ def test_strerror_and_invalid_arguments(lib):
     assert h.value is None
     lib.fovea_render.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_float] * 2 + [ctypes.c_void_p]
     assert lib.fovea_render(None, None, None, 1.0, 1.0, None) == -1
+    lib.fovea_render_pixelwise.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_float] * 2 + [ctypes.c_void_p]
+    assert lib.fovea_render_pixelwise(None, None, None, 1.0, 1.0, None) == -1
+    lib.fovea_ssim.argtypes = [ctypes.c_int] * 4 + [ctypes.c_void_p] * 2 + [ctypes.c_double] + [ctypes.c_void_p] * 3
+    fake = ctypes.c_void_p(16)  # never dereferenced: every call below is refused on the host
+    assert lib.fovea_ssim(8, 8, 3, 0, None, fake, 0.0, fake, None, None) == -1      # null image
+    assert lib.fovea_ssim(8, 8, 5, 0, fake, fake, 0.0, fake, None, None) == -1      # channels
+    assert lib.fovea_ssim(8, 8, 3, 9, fake, fake, 0.0, fake, None, None) == -1      # format
+    assert lib.fovea_ssim(8, 8, 3, 0, fake, fake, 0.0, None, None, None) == -1      # no output
+    assert lib.fovea_ssim(0, 8, 3, 0, fake, fake, 0.0, fake, None, None) == -1      # empty
 
 
 def test_python_binding_imports_without_gpu():
