@@ -16,12 +16,16 @@ the sigma law of Appendix "Choosing the Standard Deviation"). In short:
 written as a direct 2D sum per output pixel, and its adjoint as a scatter.
 Per-pixel foveation (Section 3.1's quality reference) is the same sum with
 sigma taken at every pixel's own centre; ``ssim_map`` is the SSIM of Wang et
-al. (2004) with its standard 11x11, sigma 1.5 Gaussian window.
+al. (2004) with its standard 11x11, sigma 1.5 Gaussian window;
+``forward_pyramid`` is the Gaussian-pyramid (mipmap) foveation the paper
+compares against: a Burt-Adelson pyramid sampled at level log4(3 sigma^2 + 1).
 
 Parity status: every function here is pinned by tests under ``tests/``
 (scipy's uniform Gaussian filter, brute-force unit-vector matrices, closed
 forms and invariants; for SSIM, closed forms of constant and affine pairs
-with local moments from scipy); none is "parity unpinned".
+with local moments from scipy; for the pyramid, scipy's filter-and-subsample
+and order-1 interpolation and the closed-form level variance); none is
+"parity unpinned".
 """
 from __future__ import annotations
 
@@ -87,6 +91,12 @@ def _load():
             lib.oracle_forward_pixel.restype = None
             lib.oracle_ssim_map.argtypes = [p, p, i, i, i, l, l, l, d, p, i]
             lib.oracle_ssim_map.restype = None
+            lib.oracle_pyramid_levels.argtypes = [i, i]
+            lib.oracle_pyramid_levels.restype = i
+            lib.oracle_pyramid_reduce.argtypes = [p, i, i, p]
+            lib.oracle_pyramid_reduce.restype = None
+            lib.oracle_forward_pyramid.argtypes = [p, p, i, i, i, l, l, l, d, d, d, d, p, l]
+            lib.oracle_forward_pyramid.restype = None
             _lib = lib
     return _lib
 
@@ -261,3 +271,40 @@ def ssim_map(a, b, data_range, layout="hwc", nthreads=0):
     _load().oracle_ssim_map(x.ctypes.data, y.ctypes.data, W, H, C, sy, sx, sc, float(data_range), m.ctypes.data,
                             int(nthreads))
     return m
+
+
+def pyramid_levels(width, height):
+    """Levels of a width x height Gaussian pyramid down to 1 x 1 (level 0 included)."""
+    return int(_load().oracle_pyramid_levels(int(width), int(height)))
+
+
+def pyramid_reduce(plane):
+    """One REDUCE (5-tap (1,4,6,4,1)/16 kernel, clamp, subsample by two) of a 2-D plane."""
+    x = np.ascontiguousarray(plane, dtype=np.float64)
+    H, W = x.shape
+    out = np.zeros(((H + 1) // 2, (W + 1) // 2), np.float64)
+    _load().oracle_pyramid_reduce(x.ctypes.data, W, H, out.ctypes.data)
+    return out
+
+
+def forward_pyramid(img, fix_x, fix_y, sigma0, k, layout="hwc", pixels=None):
+    """Gaussian-pyramid (mipmap) foveation in binary64: each pixel
+    interpolated from the pyramid at level log4(3 sigma_p^2 + 1). ``pixels``
+    optionally lists row-major pixel indices; others come back NaN."""
+    x = np.ascontiguousarray(img, dtype=np.float64)
+    H, W, C, sy, sx, sc = _geometry(x, layout)
+    out = np.full_like(x, np.nan)
+    if pixels is None:
+        pl, nl = None, 0
+    else:
+        parr = np.ascontiguousarray(np.asarray(pixels, dtype=np.int64))
+        pl, nl = parr.ctypes.data, int(parr.size)
+    _load().oracle_forward_pyramid(x.ctypes.data, out.ctypes.data, W, H, C, sy, sx, sc, float(fix_x), float(fix_y),
+                                   float(sigma0), float(k), pl, nl)
+    return out
+
+
+def forward_pyramid_u8(img_u8, fix_x, fix_y, sigma0, k, layout="hwc", pixels=None):
+    """Pyramid foveation of a uint8 image, coded back to uint8 (unlisted pixels 0)."""
+    v = forward_pyramid(img_u8, fix_x, fix_y, sigma0, k, layout, pixels)
+    return quantize_u8(np.nan_to_num(v, nan=0.0))

@@ -47,6 +47,8 @@
  * per-pixel ("perfect") foveation the paper uses as its quality reference
  * (every pixel blurred with the sigma of its own centre), and the SSIM map
  * (Wang et al. 2004, standard window and constants) it is scored with.
+ * And the Gaussian-pyramid (mipmap) foveation the paper compares its speed
+ * and smoothness against (Section 3.2 and its appendix on previous work).
  *
  * Floating-point rules shared with any implementation that wants bit-exact
  * radii: the sigma law is evaluated in IEEE binary64 with no fused
@@ -454,4 +456,108 @@ void oracle_ssim_map(const double* a, const double* b, int W, int H, int C, long
       }
       map[(long)y * W + x] = total / (double)C;
     }
+}
+
+/* ------------------------------------------------------------------------
+ * Gaussian-pyramid (mipmap) foveation: the earlier approach the paper
+ * compares against (Section 3.2, Fig. 4, and its appendix on previous
+ * foveated rendering): a Burt-Adelson pyramid (each level the previous one
+ * convolved with a small Gaussian and subsampled by two in each axis), and
+ * every output pixel interpolated from the pyramid at a fractional level.
+ *
+ *  - REDUCE with the 5-tap generating kernel w = (1, 4, 6, 4, 1) / 16,
+ *    clamp-to-edge:  g_{l+1}(i, j) = sum_{m,n} w(m) w(n) g_l(2i + m, 2j + n),
+ *    level sizes W_{l+1} = (W_l + 1) / 2 (samples at the even indices).
+ *  - Sample i of level l sits on original pixel 2^l i. w has unit variance,
+ *    so level l is the original blurred with variance (4^l - 1) / 3 (in
+ *    original pixels, per axis); the level whose blur matches a pixel's
+ *    sigma_p is L = log4(3 sigma_p^2 + 1), clamped to [0, top level].
+ *  - out = (1 - f) S_{l0} + f S_{l0+1}, l0 = floor(L), f = L - l0, where S_l
+ *    is the bilinear interpolation of level l at u = x / 2^l, v = y / 2^l
+ *    (neighbour indices clamped to the level).
+ * sigma_p is the per-pixel law at the pixel centre (oracle_pixel_sigma).
+ * ------------------------------------------------------------------------ */
+
+/* Number of levels of a W x H pyramid down to 1 x 1 (level 0 included). */
+int oracle_pyramid_levels(int W, int H) {
+  int n = 1;
+  while (W > 1 || H > 1) {
+    W = (W + 1) / 2;
+    H = (H + 1) / 2;
+    ++n;
+  }
+  return n;
+}
+
+/* One REDUCE of a plane (W x H, row-major) into (W+1)/2 x (H+1)/2. */
+void oracle_pyramid_reduce(const double* in, int W, int H, double* out) {
+  static const double w[5] = {1.0 / 16.0, 4.0 / 16.0, 6.0 / 16.0, 4.0 / 16.0, 1.0 / 16.0};
+  int W2 = (W + 1) / 2, H2 = (H + 1) / 2;
+  for (int j = 0; j < H2; ++j)
+    for (int i = 0; i < W2; ++i) {
+      double acc = 0.0;
+      for (int n = -2; n <= 2; ++n)
+        for (int m = -2; m <= 2; ++m)
+          acc += w[n + 2] * w[m + 2] * in[(long)clampi(2 * j + n, 0, H - 1) * W + clampi(2 * i + m, 0, W - 1)];
+      out[(long)j * W2 + i] = acc;
+    }
+}
+
+/* Bilinear sample of a level plane (Wl x Hl) at level coordinates (u, v). */
+static double bilinear(const double* g, int Wl, int Hl, double u, double v) {
+  int i0 = (int)floor(u), j0 = (int)floor(v);
+  double fu = u - (double)i0, fv = v - (double)j0;
+  int i1 = clampi(i0 + 1, 0, Wl - 1), j1 = clampi(j0 + 1, 0, Hl - 1);
+  i0 = clampi(i0, 0, Wl - 1);
+  j0 = clampi(j0, 0, Hl - 1);
+  return (1.0 - fu) * (1.0 - fv) * g[(long)j0 * Wl + i0] + fu * (1.0 - fv) * g[(long)j0 * Wl + i1] +
+         (1.0 - fu) * fv * g[(long)j1 * Wl + i0] + fu * fv * g[(long)j1 * Wl + i1];
+}
+
+/* Pyramid foveation of the listed pixels (all when pixel_list is NULL);
+ * layout as oracle_forward_ex. */
+void oracle_forward_pyramid(const double* in, double* out, int W, int H, int C, long sy, long sx, long sc,
+                            double fx, double fy, double sigma0, double k, const long* pixel_list, long nlist) {
+  int NL = oracle_pyramid_levels(W, H);
+  double** lev = (double**)malloc((size_t)NL * sizeof(double*));
+  int* lw = (int*)malloc((size_t)NL * sizeof(int));
+  int* lh = (int*)malloc((size_t)NL * sizeof(int));
+  long np = pixel_list ? nlist : (long)W * (long)H;
+  for (int c = 0; c < C; ++c) {
+    lw[0] = W;
+    lh[0] = H;
+    lev[0] = (double*)malloc((size_t)W * H * sizeof(double));
+    for (int y = 0; y < H; ++y)
+      for (int x = 0; x < W; ++x) lev[0][(long)y * W + x] = in[y * sy + x * sx + c * sc];
+    for (int l = 1; l < NL; ++l) {
+      lw[l] = (lw[l - 1] + 1) / 2;
+      lh[l] = (lh[l - 1] + 1) / 2;
+      lev[l] = (double*)malloc((size_t)lw[l] * lh[l] * sizeof(double));
+      oracle_pyramid_reduce(lev[l - 1], lw[l - 1], lh[l - 1], lev[l]);
+    }
+    for (long t = 0; t < np; ++t) {
+      long p = pixel_list ? pixel_list[t] : t;
+      int x = (int)(p % W), y = (int)(p / W);
+      double sigma;
+      int r;
+      oracle_pixel_sigma(x, y, fx, fy, sigma0, k, &sigma, &r);
+      double L = log(3.0 * sigma * sigma + 1.0) / log(4.0);
+      if (L < 0.0) L = 0.0;
+      if (L > (double)(NL - 1)) L = (double)(NL - 1);
+      int l0 = (int)floor(L);
+      double f = L - (double)l0;
+      double s0 = bilinear(lev[l0], lw[l0], lh[l0], (double)x / ldexp(1.0, l0), (double)y / ldexp(1.0, l0));
+      double v = s0;
+      if (l0 + 1 < NL && f > 0.0) {
+        double s1 = bilinear(lev[l0 + 1], lw[l0 + 1], lh[l0 + 1], (double)x / ldexp(1.0, l0 + 1),
+                             (double)y / ldexp(1.0, l0 + 1));
+        v = (1.0 - f) * s0 + f * s1;
+      }
+      out[y * sy + x * sx + c * sc] = v;
+    }
+    for (int l = 0; l < NL; ++l) free(lev[l]);
+  }
+  free(lh);
+  free(lw);
+  free(lev);
 }

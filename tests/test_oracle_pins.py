@@ -476,3 +476,79 @@ def test_ssim_range_scaling_and_channel_mean():
     chw = oracle.ssim_map(np.moveaxis(a, 2, 0).copy(), np.moveaxis(b, 2, 0).copy(), 1.0, "chw")
     np.testing.assert_allclose(chw, m1, rtol=0, atol=1e-14)
     assert (m1 < 1).all() and (m1 > -1).all()
+
+
+# ---------------------------------------------------------------- Gaussian pyramid (mipmap) foveation
+
+_W5 = np.array([1, 4, 6, 4, 1], np.float64) / 16.0
+
+
+def _scipy_reduce(plane):
+    blurred = ndimage.convolve1d(ndimage.convolve1d(plane, _W5, axis=0, mode="nearest"), _W5, axis=1, mode="nearest")
+    return blurred[::2, ::2]
+
+
+def test_pyramid_reduce_equals_library_filter_and_subsample():
+    for shape in [(17, 23), (16, 16), (5, 2), (1, 7)]:
+        img = wl.uniform_f32(shape, seed=sum(shape)).astype(np.float64)
+        np.testing.assert_allclose(oracle.pyramid_reduce(img), _scipy_reduce(img), rtol=0, atol=1e-14)
+    assert oracle.pyramid_levels(1920, 1080) == 12 and oracle.pyramid_levels(1, 1) == 1
+    assert oracle.pyramid_levels(5, 3) == 4  # 5x3 -> 3x2 -> 2x1 -> 1x1
+
+
+def test_pyramid_levels_have_variance_4l_minus_1_over_3():
+    """The equivalent kernel of level l (response of the sample on the
+    origin to an impulse at x, far from the border) sums to 1 and has
+    variance (4^l - 1) / 3 per axis: the kernel has unit variance and every
+    level doubles the sample spacing."""
+    n = 129
+    for level in (1, 2, 3):
+        h = np.zeros(n)
+        for x in range(n):
+            img = np.zeros((1, n))
+            img[0, x] = 1.0
+            g = img
+            for _ in range(level):
+                g = oracle.pyramid_reduce(g)
+            h[x] = g[0, 64 >> level]
+        pos = np.arange(n) - 64
+        assert abs(h.sum() - 1.0) < 1e-12
+        assert abs((h * pos).sum()) < 1e-12
+        assert abs((h * pos * pos).sum() - (4 ** level - 1) / 3) < 1e-10
+
+
+@pytest.mark.parametrize("level_target", [1.0, 2.0, 1.5])
+def test_pyramid_output_is_bilinear_interpolation_between_levels(level_target):
+    """Uniform sigma with 3 sigma^2 + 1 = 4^L: the output is scipy's order-1
+    interpolation of the library-reduced levels, blended by the fraction."""
+    H, W = 21, 34
+    img = wl.uniform_f32((H, W), seed=12).astype(np.float64)
+    sigma = np.sqrt((4.0 ** level_target - 1.0) / 3.0)
+    out = oracle.forward_pyramid(img, 3.0, 4.0, sigma, 0.0)
+    levels = [img]
+    for _ in range(3):
+        levels.append(_scipy_reduce(levels[-1]))
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+
+    def up(l):
+        return ndimage.map_coordinates(levels[l], [yy / 2 ** l, xx / 2 ** l], order=1, mode="nearest")
+
+    l0 = int(np.floor(level_target + 1e-12))
+    f = level_target - l0
+    ref = up(l0) if f == 0 else (1 - f) * up(l0) + f * up(l0 + 1)
+    np.testing.assert_allclose(out, ref, rtol=0, atol=1e-9)
+
+
+def test_pyramid_identity_constants_linearity_and_sampling():
+    img = wl.uniform_f32((18, 27, 3), seed=13).astype(np.float64)
+    np.testing.assert_allclose(oracle.forward_pyramid(img, 9.0, 9.0, 0.0, 0.0), img, rtol=0, atol=0)
+    c = oracle.forward_pyramid(np.full((18, 27, 3), 0.625), 9.0, 9.0, 0.5, 0.3)
+    np.testing.assert_allclose(c, 0.625, rtol=0, atol=1e-14)
+    b = wl.uniform_f32((18, 27, 3), seed=14).astype(np.float64)
+    lhs = oracle.forward_pyramid(2.0 * img - 0.5 * b, 4.5, 11.0, 0.5, 0.3)
+    rhs = 2.0 * oracle.forward_pyramid(img, 4.5, 11.0, 0.5, 0.3) - 0.5 * oracle.forward_pyramid(b, 4.5, 11.0, 0.5, 0.3)
+    np.testing.assert_allclose(lhs, rhs, rtol=0, atol=1e-13)
+    full = oracle.forward_pyramid(img, 4.5, 11.0, 0.5, 0.3)
+    pix = [0, 26, 5 * 27 + 7, 18 * 27 - 1]
+    s = oracle.forward_pyramid(img, 4.5, 11.0, 0.5, 0.3, pixels=pix)
+    assert np.array_equal(s.reshape(-1, 3)[pix], full.reshape(-1, 3)[pix])
