@@ -471,9 +471,25 @@ def pixelwise_leg(fv, torch, reps: int = 20):
             leg["mma_flops_per_launch"] = 2 * macs
             leg["mma_tflops"] = 2 * macs / (ms * 1e-3) / 1e12
         res["tensor_core_kernel" if tc else "fp32_kernel"] = leg
+    # Gaussian-pyramid (mipmap) foveation of the same frame: the comparison
+    # approach of Section 3.2 (pyramid build + sampling, all launches)
+    ctx = fv.Context(W, H, C, B, SIGMA0, K_SLOPE, fv.U8_HWC)
+    for _ in range(3):
+        ctx.render_pyramid(x, y, *FIX)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        ctx.render_pyramid(x, y, *FIX)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    res["pyramid"] = {"ms": ms, "mpix_s": W * H / ms / 1e3}
     ref = fv.foveate_pixelwise(x, *FIX, SIGMA0, K_SLOPE)
-    for name, grid in (("anchored_grid", fv.GRID_ANCHORED), ("centred_grid", fv.GRID_CENTRED)):
-        blk = fv.foveate(x, *FIX, SIGMA0, K_SLOPE, grid=grid)
+    pyr = fv.foveate_pyramid(x, *FIX, SIGMA0, K_SLOPE)
+    outs = [("anchored_grid", fv.foveate(x, *FIX, SIGMA0, K_SLOPE, grid=fv.GRID_ANCHORED)),
+            ("centred_grid", fv.foveate(x, *FIX, SIGMA0, K_SLOPE, grid=fv.GRID_CENTRED)), ("pyramid", pyr)]
+    for name, blk in outs:
         m, mean = fv.ssim(blk, ref)
         mh = m.cpu().numpy()
         reg = mh[:H // 32 * 32, :W // 32 * 32].reshape(H // 32, 32, W // 32, 32).mean(axis=(1, 3))

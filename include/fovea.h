@@ -203,6 +203,20 @@ int fovea_backward_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, void*
 int fovea_render_pixelwise(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x, float fix_y,
                            void* stream);
 
+/* Gaussian-pyramid (mipmap) foveation, the earlier approach the paper
+ * compares its block-wise blur against (Section 3.2, Fig. 4; appendix on
+ * previous foveated rendering), in CUDA: a Burt-Adelson pyramid (5-tap
+ * (1,4,6,4,1)/16 kernel, clamp-to-edge, subsampling at the even indices) is
+ * built on the device, and every pixel is read at the fractional level
+ * L = log4(3 sigma_p^2 + 1) (level l carries a blur of variance
+ * (4^l - 1)/3) by bilinear interpolation in levels floor(L) and floor(L)+1,
+ * blended by the fraction; sigma_p is the per-pixel law at the pixel centre
+ * (computed in fp32 here: L is continuous in sigma). Levels are built up to
+ * the largest L the frame needs, in a device workspace the context owns.
+ * Same context rules as fovea_render_pixelwise (a per-block map is refused). */
+int fovea_render_pyramid(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x, float fix_y,
+                         void* stream);
+
 /* SSIM map of two device images of the same shape and format (the quality
  * measure of Section 3.1; Wang, Bovik, Sheikh and Simoncelli 2004): 11 x 11
  * Gaussian window of standard deviation 1.5 normalised to unit sum,

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfovea.so")
 
-SOURCES = ["sigma.cu", "forward.cu", "tc_forward.cu", "umma_forward.cu", "pixel_forward.cu", "ssim.cu", "adjoint.cu", "noalloc.cu", "peak.cu",
+SOURCES = ["sigma.cu", "forward.cu", "tc_forward.cu", "umma_forward.cu", "pixel_forward.cu", "pyramid.cu", "ssim.cu", "adjoint.cu", "noalloc.cu", "peak.cu",
            "api.cu", "tune.cpp", "server.cpp"]
 HEADERS = ["fovea_internal.cuh", "fovea_host.h", "fwd_common.cuh", "tc_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -87,6 +87,9 @@ struct fovea_ctx {
   cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
   cudaEvent_t ev_entry = nullptr;
   size_t host_io_bytes = 0;
+  // Gaussian-pyramid levels (fovea_render_pyramid)
+  float* pyr = nullptr;
+  size_t pyr_bytes = 0;
   // set by every call that enqueues workspace use on the caller's stream;
   // the next fovea_render_host orders its kernels after that work
   bool caller_stream_used = false;
@@ -715,6 +718,59 @@ int fovea_render_pixelwise(fovea_ctx* ctx, const void* in_dev, void* out_dev, fl
   return FOVEA_OK;
 }
 
+int fovea_render_pyramid(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x, float fix_y,
+                         void* stream) {
+  if (!ctx || !in_dev || !out_dev || ctx->batch_only) return FOVEA_EINVAL;
+  if (ctx->law.smap) return FOVEA_EINVAL;
+  int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->law, fix_x, fix_y);
+  if (st != FOVEA_OK) return st;
+  const size_t nb = frame_bytes(ctx->W, ctx->H, ctx->C, ctx->fmt);
+  if (overlaps(in_dev, nb, out_dev, nb)) return FOVEA_EINVAL;
+  // levels down to 1 x 1, of which those up to the largest fractional level
+  // any pixel reads (the farthest corner pixel's sigma) are built
+  PyramidLevels lv;
+  std::memset(&lv, 0, sizeof(lv));
+  lv.w[0] = ctx->W;
+  lv.h[0] = ctx->H;
+  int nl = 1;
+  while ((lv.w[nl - 1] > 1 || lv.h[nl - 1] > 1) && nl < kMaxPyramidLevels) {
+    lv.w[nl] = (lv.w[nl - 1] + 1) / 2;
+    lv.h[nl] = (lv.h[nl - 1] + 1) / 2;
+    ++nl;
+  }
+  double smax = 0.0;
+  for (int x : {0, ctx->W - 1})
+    for (int y : {0, ctx->H - 1}) {
+      const double dx = (double)x + 0.5 - fix_x, dy = (double)y + 0.5 - fix_y;
+      smax = std::max(smax, ctx->law.sigma0 + ctx->law.k * std::sqrt(dx * dx + dy * dy));
+    }
+  const double lmax = std::log(3.0 * smax * smax + 1.0) / std::log(4.0);
+  lv.top = std::min(nl - 1, (int)std::ceil(lmax));
+  size_t need = 0;
+  for (int l = 1; l <= lv.top; ++l) need += (size_t)lv.w[l] * lv.h[l] * ctx->C * sizeof(float);
+  if (need > ctx->pyr_bytes) {
+    if (ctx->pyr) {
+      FOVEA_CUDA(cudaDeviceSynchronize());
+      cudaFree(ctx->pyr);
+      ctx->pyr = nullptr;
+      ctx->pyr_bytes = 0;
+    }
+    FOVEA_CUDA(cudaMalloc(&ctx->pyr, need));
+    ctx->pyr_bytes = need;
+  }
+  size_t off = 0;
+  for (int l = 1; l <= lv.top; ++l) {
+    lv.ptr[l] = ctx->pyr + off / sizeof(float);
+    off += (size_t)lv.w[l] * lv.h[l] * ctx->C * sizeof(float);
+  }
+  ctx->caller_stream_used = true;
+  cudaError_t e = launch_pyramid(in_dev, out_dev, ctx->W, ctx->H, ctx->C, ctx->fmt == FOVEA_U8_HWC ? 1 : 0, fix_x,
+                                 fix_y, (float)ctx->law.sigma0, (float)ctx->law.k, lv,
+                                 static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e);
+  return FOVEA_OK;
+}
+
 int fovea_ssim(int width, int height, int channels, int format, const void* a_dev, const void* b_dev,
                double data_range, float* map_dev, double* sum_dev, void* stream) {
   if (!a_dev || !b_dev || width <= 0 || height <= 0) return FOVEA_EINVAL;
@@ -804,6 +860,7 @@ void fovea_destroy(fovea_ctx* ctx) {
     if (sl.ev_comp) cudaEventDestroy(sl.ev_comp);
     if (sl.ev_d2h) cudaEventDestroy(sl.ev_d2h);
   }
+  if (ctx->pyr) cudaFree(ctx->pyr);
   if (ctx->ev_entry) cudaEventDestroy(ctx->ev_entry);
   if (ctx->s_h2d) cudaStreamDestroy(ctx->s_h2d);
   if (ctx->s_comp) cudaStreamDestroy(ctx->s_comp);

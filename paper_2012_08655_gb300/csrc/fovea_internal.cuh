@@ -373,6 +373,18 @@ int pixel_fp32_rows(int rmax, int C);
 size_t pixel_fp32_smem(int rmax, int C, int rb);
 cudaError_t launch_pixel_forward(const PixelParams& pp, bool tensor_cores, cudaStream_t s);
 
+// ------------------------------------------------------------------ pyramid (pyramid.cu)
+// Levels 1 .. top of a Gaussian pyramid (float32 planes, channel-major);
+// level 0 is the frame.
+constexpr int kMaxPyramidLevels = 32;
+struct PyramidLevels {
+  float* ptr[kMaxPyramidLevels];
+  int w[kMaxPyramidLevels], h[kMaxPyramidLevels];
+  int top;
+};
+cudaError_t launch_pyramid(const void* in, void* out, int W, int H, int C, int isu8, float fx, float fy,
+                           float sigma0, float k, const PyramidLevels& lv, cudaStream_t s);
+
 // ------------------------------------------------------------------ SSIM (ssim.cu)
 cudaError_t launch_ssim(const void* a, const void* b, int W, int H, int C, int isu8, float data_range,
                         float* map, double* sum, cudaStream_t s);

@@ -76,6 +76,7 @@ _sig = {
     "fovea_render_batch": (_i, [_vp, ctypes.POINTER(Frame), _i, _vp]),
     "fovea_render_host": (_i, [_vp, _vp, _vp, _f, _f, _vp]),
     "fovea_render_pixelwise": (_i, [_vp, _vp, _vp, _f, _f, _vp]),
+    "fovea_render_pyramid": (_i, [_vp, _vp, _vp, _f, _f, _vp]),
     "fovea_ssim": (_i, [_i, _i, _i, _i, _vp, _vp, _d, _vp, _vp, _vp]),
     "fovea_backward": (_i, [_vp, _vp, _vp, _f, _f, _vp]),
     "fovea_backward_batch": (_i, [_vp, ctypes.POINTER(Frame), _i, _vp]),
@@ -219,6 +220,15 @@ class Context:
         _require_device_frame(out, "output")
         _check(_lib.fovea_render_pixelwise(self._h, inp.data_ptr(), out.data_ptr(), float(fix_x), float(fix_y),
                                            _stream_handle(stream)), "fovea_render_pixelwise")
+        return out
+
+    def render_pyramid(self, inp: torch.Tensor, out: torch.Tensor, fix_x: float, fix_y: float, stream=None):
+        """Gaussian-pyramid (mipmap) foveation of one device frame with this
+        context's shape, format and law (``fovea_render_pyramid``)."""
+        _require_device_frame(inp, "input")
+        _require_device_frame(out, "output")
+        _check(_lib.fovea_render_pyramid(self._h, inp.data_ptr(), out.data_ptr(), float(fix_x), float(fix_y),
+                                         _stream_handle(stream)), "fovea_render_pyramid")
         return out
 
     def render_host(self, inp: torch.Tensor, out: torch.Tensor, fix_x: float, fix_y: float, stream=None):
@@ -368,6 +378,18 @@ def foveate_pixelwise(x: torch.Tensor, fix_x: float, fix_y: float, sigma0: float
     if out is None:
         out = torch.empty_like(x)
     return ctx.render_pixelwise(x, out, fix_x, fix_y)
+
+
+def foveate_pyramid(x: torch.Tensor, fix_x: float, fix_y: float, sigma0: float = 0.5, k: float = 0.02,
+                    out: Optional[torch.Tensor] = None, *, e_corner: Optional[float] = None) -> torch.Tensor:
+    """Gaussian-pyramid (mipmap) foveation of one frame on the GPU."""
+    _require_device_frame(x, "input")
+    fmt = _fmt_of(x)
+    w, h, c = _shape_of(x, fmt)
+    ctx = _ctx_for(w, h, c, 32, sigma0, k, fmt, GRID_ANCHORED, e_corner)
+    if out is None:
+        out = torch.empty_like(x)
+    return ctx.render_pyramid(x, out, fix_x, fix_y)
 
 
 def ssim(a: torch.Tensor, b: torch.Tensor, data_range: float = 0.0, want_map: bool = True, stream=None):
