@@ -113,7 +113,10 @@ __device__ __forceinline__ void stage_rows(const Item& it, const Slab& sl, int k
 }
 
 // Per-item geometry from the item record (computed by one thread).
-__device__ __forceinline__ void item_geometry(Item& it, const ItemInfo& inf, const FrameDesc& fd, int rb) {
+// full_slabs: every slab but the last is as wide as allowed (otherwise the
+// slabs share the width evenly).
+__device__ __forceinline__ void item_geometry(Item& it, const ItemInfo& inf, const FrameDesc& fd, int rb,
+                                              bool full_slabs = false) {
   const bool u8 = fd.fmt == FOVEA_U8_HWC;
   it.in = static_cast<const unsigned char*>(fd.in);
   it.out = static_cast<unsigned char*>(fd.out);
@@ -140,7 +143,7 @@ __device__ __forceinline__ void item_geometry(Item& it, const ItemInfo& inf, con
   const int E = u8 ? it.EW * it.C : it.EW;
   const int cap = u8 ? (kSlabMax / it.C) * it.C : kSlabMax;
   const int nsl = (E + cap - 1) / cap;
-  int sw = (E + nsl - 1) / nsl;
+  int sw = full_slabs && nsl > 1 ? cap : (E + nsl - 1) / nsl;
   if (u8) sw = ((sw + it.C - 1) / it.C) * it.C;
   it.nsl = nsl;
   it.sw = sw;

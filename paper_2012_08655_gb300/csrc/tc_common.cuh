@@ -242,12 +242,20 @@ __device__ __forceinline__ void tc_pass2_slab(const Item& it, const Slab& sl, co
       }
     }
   }
+  // this warp's n-tile: u = warp + 8 i has u & 3 = warp & 3 for every i, so
+  // the tap fragments of a k-step are shared by the warp's C m-tiles
+  const int nt2w = warp & 3;
   for (int kk = 0; kk < npx16; kk += 16) {
-    unsigned int a_h[C][4], a_l[C][4], bh[C][2], bl[C][2];
+    unsigned int a_h[C][4], a_l[C][4], bh[2], bl[2];
+    {
+      const int jb = (it.offx + P0 + kk + 2 * t - 8 * nt2w - g + kPairPad) >> 1;
+      bh[0] = Qh[jb]; bh[1] = Qh[jb + 4];
+      bl[0] = Ql[jb]; bl[1] = Ql[jb + 4];
+    }
     #pragma unroll
     for (int i = 0; i < C; ++i) {
       const int u = warp + 8 * i;
-      const int mt2 = u >> 2, nt2 = u & 3;
+      const int mt2 = u >> 2;
       if (VT) {  // stored rows are pixels: transpose on load
         const int m0 = 16 * mt2 + ((lane >> 3) & 1) * 8;
         const int krow = kk + (lane & 7) + ((lane >> 4) & 1) * 8;
@@ -260,16 +268,13 @@ __device__ __forceinline__ void tc_pass2_slab(const Item& it, const Slab& sl, co
         ldsm_x4(a_h[i], Vh + (size_t)arow * VP + acol);
         ldsm_x4(a_l[i], Vl + (size_t)arow * VP + acol);
       }
-      const int jb = (it.offx + P0 + kk + 2 * t - 8 * nt2 - g + kPairPad) >> 1;
-      bh[i][0] = Qh[jb]; bh[i][1] = Qh[jb + 4];
-      bl[i][0] = Ql[jb]; bl[i][1] = Ql[jb + 4];
     }
     #pragma unroll
-    for (int i = 0; i < C; ++i) mma16816(acc2[i], a_h[i], bh[i][0], bh[i][1]);
+    for (int i = 0; i < C; ++i) mma16816(acc2[i], a_h[i], bh[0], bh[1]);
     #pragma unroll
-    for (int i = 0; i < C; ++i) mma16816(acc2[i], a_h[i], bl[i][0], bl[i][1]);
+    for (int i = 0; i < C; ++i) mma16816(acc2[i], a_h[i], bl[0], bl[1]);
     #pragma unroll
-    for (int i = 0; i < C; ++i) mma16816(acc2[i], a_l[i], bh[i][0], bh[i][1]);
+    for (int i = 0; i < C; ++i) mma16816(acc2[i], a_l[i], bh[0], bh[1]);
   }
   {
     const int pr = it.EW - 1 - P0;  // folded right column after the last slab's products
@@ -342,7 +347,7 @@ __device__ __forceinline__ void tc_write_output(const Item& it, unsigned char* o
 // the next item's index and record, so the work list's dependent loads
 // overlap the current item. Ends with the single-frame counter reset.
 // s_start: shared memory for rmax + 1 bucket starts (single frames).
-template <int RB, int C, typename ItemFn>
+template <int RB, int C, bool FULL_SLABS = false, typename ItemFn>
 __device__ __forceinline__ void tc_item_loop(const FrameSource& src, const CUtensorMap& tmap1, const Workspace& ws,
                                              int rmax, const BucketList& bl, int* s_start, ItemFn&& item_fn) {
   __shared__ int s_state;
@@ -406,7 +411,7 @@ __device__ __forceinline__ void tc_item_loop(const FrameSource& src, const CUten
             atomicOr(&ws.counters[CNT_ERROR], 2u);
             state = 1;
           } else {
-            item_geometry(s_it, inf, fd, RB);
+            item_geometry(s_it, inf, fd, RB, FULL_SLABS);
             s_c = inf.neg_half_inv_s2;
             s_map = !fd.tma ? nullptr : (batch_maps ? static_cast<const void*>(batch_maps + inf.frame)
                                                     : static_cast<const void*>(&tmap1));

@@ -121,7 +121,9 @@ __device__ __forceinline__ bool tc_item(const Item& it, float c_tap, unsigned ch
   // This warp's pass-1 columns are ring bytes 32w .. 32w+31. Lane (g, t)
   // feeds bytes 32w + 4g + j to n-tile j (column g) and accumulates, for
   // n-tile j, the ring bytes 32w + 8t + j (column 2t) and 32w + 8t + 4 + j
-  // (column 2t + 1).
+  // (column 2t + 1). (Giving two warps one 32-byte unit, one m-tile each,
+  // when a slab has at most four units measured slower: the warps' loads and
+  // fragment work do not shrink with their MMAs.)
   const int colw = 32 * warp;
 
   float acc1[2][4][4];
@@ -331,7 +333,7 @@ tc_forward_kernel(const __grid_constant__ FrameSource src, Workspace ws, int rma
     fence_proxy_async();
   }
   int gq0 = 0;  // chunks staged by this CTA so far (identical in every thread)
-  tc_item_loop<RB, C>(src, tmap1, ws, rmax, bl, reinterpret_cast<int*>(smem + L.starts),
+  tc_item_loop<RB, C, true>(src, tmap1, ws, rmax, bl, reinterpret_cast<int*>(smem + L.starts),
                       [&](const Item& it, float c, const void* map, bool map_global, auto& lookahead) {
                         return tc_item<RB, C>(it, c, ring, Vh, Vl, CU, P, np, s_bar, map, map_global, gq0,
                                               ws.counters + CNT_ERROR, lookahead);
