@@ -391,13 +391,30 @@ int mode_of(int fmt_mask) { return fmt_mask == 1 ? 0 : (fmt_mask == 2 ? 1 : 2); 
 
 }  // namespace
 
+namespace {
+
+// Row chunk the launch uses: the configured one, halved (down to 16 rows)
+// while a float32 launch's ring of 1024-byte rows would leave room for only
+// one CTA per SM (measured: 16-row chunks with two CTAs per SM beat 32-row
+// chunks with one on 224 x 224 float32 batches).
+int effective_rb(const FwdConfig& cfg, int rmax, int fmt_mask) {
+  int rb = cfg.rows_per_chunk;
+  if (fmt_mask & 2) {
+    constexpr size_t kTwoPerSm = 110 * 1024;
+    while (rb > 16 && smem_layout(rb, kRowBytesF32, rmax).total > kTwoPerSm) rb /= 2;
+  }
+  return rb;
+}
+
+}  // namespace
+
 size_t forward_smem_bytes(const FwdConfig& cfg, int rmax, int fmt_mask) {
-  return smem_layout(cfg.rows_per_chunk, (fmt_mask & 2) ? kRowBytesF32 : kRowBytesU8, rmax).total;
+  return smem_layout(effective_rb(cfg, rmax, fmt_mask), (fmt_mask & 2) ? kRowBytesF32 : kRowBytesU8, rmax).total;
 }
 
 int forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int fmt_mask) {
   const size_t smem = forward_smem_bytes(cfg, rmax, fmt_mask);
-  void* k = pick_kernel(cfg.rows_per_chunk, mode_of(fmt_mask));
+  void* k = pick_kernel(effective_rb(cfg, rmax, fmt_mask), mode_of(fmt_mask));
   if (set_smem_attrs(reinterpret_cast<const void*>(k), smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -414,7 +431,7 @@ cudaError_t launch_forward(const FrameSource& src, const Workspace& ws, const Fw
                            int rmax, int fmt_mask, int grid, cudaStream_t s, const BucketList& bl, bool pdl) {
   const size_t smem = forward_smem_bytes(cfg, rmax, fmt_mask);
   int row_bytes = (fmt_mask & 2) ? kRowBytesF32 : kRowBytesU8;
-  void* k = pick_kernel(cfg.rows_per_chunk, mode_of(fmt_mask));
+  void* k = pick_kernel(effective_rb(cfg, rmax, fmt_mask), mode_of(fmt_mask));
   cudaError_t e = set_smem_attrs(reinterpret_cast<const void*>(k), smem);
   if (e != cudaSuccess) return e;
   BucketList b = bl;
