@@ -40,14 +40,27 @@ constexpr double kPi = 3.14159265358979323846;
 
 // Zero the output planes of every frame of a device-resident batch (the
 // adjoint accumulates into them).
+// Zeroes every frame's float32 output (the adjoint scatter-adds into it).
+// The launch is captured once for any batch size, so the grid is fixed: CTA
+// row y takes frames y, y + gridDim.y, ...; the CTAs of a row split a frame
+// with 16-byte stores where its alignment allows.
 __global__ void zero_outputs_kernel(const BatchHeader* hdr, const FrameDesc* frames) {
-  const int f = blockIdx.y;
-  if (f >= hdr->nframes) return;
-  const FrameDesc fd = frames[f];
-  const size_t n = (size_t)fd.W * fd.H * fd.C;
-  float* out = static_cast<float*>(fd.out);
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = 0.0f;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nf = hdr->nframes;
+  for (int f = blockIdx.y; f < nf; f += gridDim.y) {
+    const FrameDesc fd = frames[f];
+    const size_t n = (size_t)fd.W * fd.H * fd.C;
+    float* out = static_cast<float*>(fd.out);
+    size_t head = 0;
+    if ((reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+      const size_t n4 = n / 4;
+      float4* o4 = reinterpret_cast<float4*>(out);
+      for (size_t i = t0; i < n4; i += stride) o4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      head = 4 * n4;
+    }
+    for (size_t i = head + t0; i < n; i += stride) out[i] = 0.0f;
+  }
 }
 
 }  // namespace
@@ -355,12 +368,8 @@ int enqueue_batch_kernels(fovea_ctx* ctx, bool adjoint, int rbound, int fmt_mask
   const FrameSource src = batch_source(ctx);
   const int sg = 4 * ctx->num_sms;
   if (adjoint) {
-    dim3 zg(64, 1);
-    // frames of a batch are at most 65535 (grid y)
     cudaError_t e;
-    int nmax = (int)((ctx->batch_dev_cap - sizeof(BatchHeader)) / sizeof(FrameDesc));
-    zg.y = (unsigned)std::min(nmax, 65535);
-    zero_outputs_kernel<<<zg, 256, 0, s>>>(src.hdr, src.frames);
+    zero_outputs_kernel<<<dim3(16, 64), 256, 0, s>>>(src.hdr, src.frames);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
   }
   cudaError_t e = launch_sigma_order(src, ctx->ws, sg, nullptr, nullptr, s);
