@@ -59,10 +59,10 @@ __device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b :
 
 constexpr int kTcM = 16;            // output rows per tile (the MMA's M)
 constexpr int kTcN = 16;            // output columns per tile
-constexpr int kTcWarps = 8;         // each warp takes columns w and w + 8
+constexpr int kTcWarps = 16;        // warp w takes output columns w, w + kTcWarps, ...
 constexpr int kTcThreads = 32 * kTcWarps;
 constexpr int kTcPix = kTcM * kTcN;
-constexpr int kTcGroups = 6;        // 32-pixel groups (4 n-tiles each) accumulated at a time
+constexpr int kTcGroups = 3;        // 32-pixel groups (4 n-tiles each) accumulated at a time
 
 template <int C>
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -84,7 +84,7 @@ pixel_tc_kernel(PixelParams pp) {
   // ---- per-pixel sigma, radius, tap exponent (pixel p = row * 16 + column); tile radius
   if (tid == 0) *s_R = 0;
   __syncthreads();
-  {
+  if (tid < kTcPix) {
     const int lx = tid & (kTcN - 1), ly = tid / kTcN;
     const int x = x0 + lx, y = y0 + ly;
     int r = 0;
@@ -132,19 +132,23 @@ pixel_tc_kernel(PixelParams pp) {
   // fp16, zero for d > r_p (the last entry is always zero); tables in
   // column-major pixel order (column * 16 + row)
   {
-    const int pr = (tid & (kTcM - 1)) * kTcN + tid / kTcM;  // thread tid builds table tid
+    // threads 2b and 2b+1 build table b (even and odd offsets)
+    static_assert(kTcThreads == 2 * kTcPix, "two threads per tap table");
+    const int tb = tid >> 1, h = tid & 1;
+    const int pr = (tb & (kTcM - 1)) * kTcN + tb / kTcM;
     const int r = tc_r[pr];
     const float c = tc_c[pr];
-    unsigned int* tw = taps + tid * TP;
+    unsigned int* tw = taps + tb * TP;
     float* twf = reinterpret_cast<float*>(tw);
     float s = 0.0f;
-    for (int d = 0; d < TP; ++d) {
+    for (int d = h; d < TP; d += 2) {
       const float w = d <= r ? tap_w(d, c) : 0.0f;
       twf[d] = w;
       if (d >= 1) s += w;
     }
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
     const float inv = kWScale / (1.0f + 2.0f * s);
-    for (int d = 0; d < TP; ++d) {
+    for (int d = h; d < TP; d += 2) {
       const float w = twf[d] * inv;
       const __half hh = __float2half_rn(w);
       const __half ll = __float2half_rn(w - __half2float(hh));
@@ -153,14 +157,14 @@ pixel_tc_kernel(PixelParams pp) {
   }
   __syncthreads();
 
-  // ---- per warp, output columns warp and warp + 8: for each channel plane,
+  // ---- per warp, output columns warp, warp + kTcWarps, ...: for each channel plane,
   // G[m][n] = sum_k A_x[m][k] B[k][n] over the column's window (32-pixel
   // groups from pixel 0), then out[m][c] = sum_n u_m(n - x - R) G[m][n]
   const int g = lane >> 2, t = lane & 3;
   const int KS = (16 + 2 * R + 15) >> 4;
   #pragma unroll 1
-  for (int half = 0; half < 2; ++half) {
-    const int lx = warp + 8 * half, x = x0 + lx;
+  for (int half = 0; half < kTcN / kTcWarps; ++half) {
+    const int lx = warp + kTcWarps * half, x = x0 + lx;
     if (x >= W) break;  // warp-uniform; no barrier follows
     const unsigned int* TA = taps + (lx * kTcM + g) * TP;          // pixel (x, y0 + g)
     const unsigned int* TB = taps + (lx * kTcM + g + 8) * TP;      // pixel (x, y0 + g + 8)
