@@ -250,9 +250,33 @@ def cpu_oracle_sample(target_s: float = 8.0, seed: int = 0):
     oracle.forward(frame.image, B, FIX[0], FIX[1], SIGMA0, K_SLOPE, "hwc", blocks=blocks)
     dt = time.perf_counter() - t0
     px = n * B * B
+    # the same oracle on one core, on a smaller sample (about a quarter of the time)
+    n1 = max(1, int(n / threads / 4))
+    t1 = time.perf_counter()
+    oracle.forward(frame.image, B, FIX[0], FIX[1], SIGMA0, K_SLOPE, "hwc", blocks=order[:n1].tolist(), nthreads=1)
+    dt1 = time.perf_counter() - t1
     return {"value": px / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{n} of {nb} blocks of the 1080p frame (seeded random), FP64 direct 2D sum, "
-                      f"{threads} OpenMP threads, {dt:.2f} s"}
+                      f"{threads} OpenMP threads, {dt:.2f} s",
+            "one_core": {"value": n1 * B * B / dt1 / 1e6, "unit": UNIT,
+                         "sample": f"first {n1} blocks of the same sample, 1 thread, {dt1:.2f} s"},
+            "host": cpu_model()}
+
+
+def cpu_model() -> str:
+    """The host CPU as the OS reports it (model name, or Arm implementer/part)."""
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    name = fields.get("model name") or " ".join(
+        f"{k} {fields[k]}" for k in ("CPU implementer", "CPU part") if k in fields)
+    return f"{name or 'unknown'}, {os.cpu_count()} logical CPUs"
 
 
 def run_reference(args):
@@ -407,6 +431,30 @@ def block_sweep_leg(fv, torch):
         res[str(B)] = {"ms": ms, "mpix_s": W * H / ms / 1e3, "algorithmic_fmas": fmas,
                        "fmas_per_pixel_channel": fmas / (W * H * C), "kernel_config": cfg}
     return {"workload": WORKLOAD.replace("32x32 blocks", "B x B blocks"), "by_block": res}
+
+
+def plain_leg(fv, torch, reps: int = 2000):
+    """The 256 x 256 single-channel float32 frame (sigma = 0.5 + 0.02 e,
+    fixation at the centre): too small to fill the GPU, so it is reported as
+    microseconds per render (launch latency), not against a roofline."""
+    from paper_2012_08655_gb300 import workloads as wl
+    spec = wl.plain_f32()
+    x = torch.from_numpy(spec.image).cuda()
+    y = torch.empty_like(x)
+    h, w = spec.image.shape[-2:]
+    ctx = fv.Context(w, h, 1, B, spec.sigma0, spec.k, fv.F32_CHW)
+    for _ in range(20):
+        ctx.render(x, y, spec.fix_x, spec.fix_y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        ctx.render(x, y, spec.fix_x, spec.fix_y)
+    e1.record()
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) / reps * 1e3
+    return {"workload": f"{w}x{h}x1 float32 U[0,1), sigma = {spec.sigma0} + {spec.k} e, fixation ({spec.fix_x}, "
+                        f"{spec.fix_y})", "us_per_render": us, "renders": reps}
 
 
 def pixel_radii(width, height, fix_x, fix_y, sigma0, k):
@@ -686,6 +734,7 @@ def run_ours(args):
         extras["train"] = train_leg(fv, torch)
         extras["block_sweep"] = block_sweep_leg(fv, torch)
         extras["pixelwise"] = pixelwise_leg(fv, torch)
+        extras["plain_256"] = plain_leg(fv, torch)
         served = served_leg(fv, torch, args.served_seconds, max_batch=64)
         plain = served_leg(fv, torch, args.served_seconds, max_batch=1)
         served["plain_per_frame"] = {k: plain[k] for k in ("p50_ms", "p99_ms", "mpix_s", "mean_batch")}
