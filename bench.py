@@ -397,10 +397,23 @@ def train_leg(fv, torch):
         torch.cuda.synchronize()
         res[name] = e0.elapsed_time(e1) / reps
     px = x_np.shape[0] * x_np.shape[2] * x_np.shape[3]
+    # algorithmic work of the forward (the method's separable FMAs, halo
+    # rows included, clamping not folded) from each image's radius table
+    n, c, hh, ww = x_np.shape
+    ctx = fv.Context(ww, hh, c, 32, s0, k, fv.F32_CHW)
+    fmas = 0.0
+    for i in range(n):
+        _, rad = ctx.sigma_table(float(fix_np[i, 0]), float(fix_np[i, 1]))
+        fmas += algorithmic_fmas(rad.cpu().numpy(), ww, hh, c, 32)
+    tflops = 2 * fmas / (res["forward"] * 1e-3) / 1e12
     return {"workload": "32x3x224x224 float32 U[0,1), fixations uniform, sigma = 0.5 + 0.08 e",
             "forward_ms": res["forward"], "forward_backward_ms": res["forward_backward"],
             "forward_mpix_s": px / res["forward"] / 1e3,
-            "forward_backward_mpix_s": px / res["forward_backward"] / 1e3}
+            "forward_backward_mpix_s": px / res["forward_backward"] / 1e3,
+            "forward_algorithmic_fmas": fmas,
+            "forward_tflops": tflops,
+            "forward_note": "whole forward call (sigma, order and blur kernels, Python autograd overhead) "
+                            "against the algorithmic FMAs; fp32 CUDA-core kernel (float32 frames)"}
 
 
 def block_sweep_leg(fv, torch):
