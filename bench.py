@@ -50,7 +50,7 @@ WORKLOAD = "1920x1080 RGB uint8 frame, 32x32 blocks, sigma = 0.5 + 0.02 e px, fi
 L2_BYTES = 129 * 1024 * 1024
 CSRC = os.path.join(ROOT, "paper_2012_08655_gb300", "csrc")
 # Per forward kernel: committed ncu summary and the sources it was taken from.
-KEV_EVERY = 4  # blur-kernel events on one step in KEV_EVERY of the timed region
+KEV_EVERY = 16  # blur-kernel events on one step in KEV_EVERY of the timed region
 
 KERNELS = {
     0: ("forward_kernel (fp32 FMA)", os.path.join(ROOT, "profiles", "forward_kernel_1080p_u8.txt"),
