@@ -74,6 +74,8 @@ def parse_args():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--pixelwise-only", action="store_true",
                    help="run only the per-pixel foveation leg (--steps launches per kernel) and print it")
+    p.add_argument("--train-only", action="store_true",
+                   help="run only the float32 training leg (forward and backward) and print it")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiling runs)")
     p.add_argument("--tensor-cores", type=int, choices=[0, 1, 2], default=None,
                    help="force the forward kernel (0: fp32 FMA, 1: mma.sync, 2: tcgen05 vertical pass) "
@@ -370,7 +372,7 @@ def batched_leg(fv, torch):
             "speedup": res["per_frame"]["ms"] / res["batched"]["ms"]}
 
 
-def train_leg(fv, torch):
+def train_leg(fv, torch, reps: int = 20):
     """32x3x224x224 float32 batch (sigma = 0.5 + 0.08 e, random fixations):
     forward and backward through the autograd function (batched render and
     batched adjoint launches)."""
@@ -389,7 +391,6 @@ def train_leg(fv, torch):
             step()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 20
         e0.record()
         for _ in range(reps):
             step()
@@ -684,6 +685,10 @@ def run_ours(args):
     if args.pixelwise_only:
         if rank == 0:
             print(json.dumps({"pixelwise": pixelwise_leg(fv, torch, reps=args.steps)}), flush=True)
+        return 0
+    if args.train_only:
+        if rank == 0:
+            print(json.dumps({"train": train_leg(fv, torch, reps=args.steps)}), flush=True)
         return 0
     from paper_2012_08655_gb300 import workloads as wl
 
