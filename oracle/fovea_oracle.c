@@ -90,11 +90,6 @@ static void block_sigma_o(int bx, int by, int B, int ox, int oy, double fx, doub
   *radius = (int)ceil(three_s);
 }
 
-static void block_sigma(int bx, int by, int B, double fx, double fy, double sigma0, double k,
-                        double* sigma, int* radius) {
-  block_sigma_o(bx, by, B, 0, 0, fx, fy, sigma0, k, sigma, radius);
-}
-
 /* Blocks along an axis of n pixels with origin offset o: ceil((n + o) / B). */
 static int grid_count(int n, int B, int o) { return (n + o + B - 1) / B; }
 

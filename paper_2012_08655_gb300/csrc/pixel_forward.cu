@@ -52,9 +52,6 @@ __device__ __forceinline__ float neg_half_inv_s2(double sigma) {
 
 __device__ __forceinline__ float tap_w(int d, float c) { return d == 0 ? 1.0f : expf(c * (float)(d * d)); }
 
-// Floor division by a positive divisor, for negative numerators too.
-__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
-
 // ---------------------------------------------------------------- tensor-core kernel
 
 constexpr int kTcM = 16;            // output rows per tile (the MMA's M)

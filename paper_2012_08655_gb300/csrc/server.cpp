@@ -291,7 +291,7 @@ int fovea_server_create(const fovea_server_config* cfg, fovea_server** out) {
     return FOVEA_ENOMEM;
   }
   s->arena.reset(cfg->device_budget_bytes);
-  fovea_sigma_law law{FOVEA_LAW_LINEAR, 0.5, 0.02};
+  fovea_sigma_law law{FOVEA_LAW_LINEAR, 0.5, 0.02, 0.0, nullptr, 0.0, FOVEA_GRID_ANCHORED};
   int st = fovea_create(0, 0, 3, cfg->block, &law, FOVEA_U8_HWC, &s->ctx);
   if (st != FOVEA_OK) {
     fovea_server_destroy(s);
