@@ -243,8 +243,9 @@ typedef struct {
   int threads;        /* threads per CTA of the forward kernel: 256 */
   int ctas_per_sm;    /* persistent CTAs per SM (0 = as many as fit) */
   int rows_per_chunk; /* tile rows staged per chunk: 16, 32 or 64 (float32
-                         launches of the fp32 kernel halve it, down to 16,
-                         while its staging ring would fit only one CTA per SM) */
+                         launches of the fp32 kernel keep a two-stage ring and
+                         halve it, down to 16, while the ring would fit only
+                         one CTA per SM) */
   int tensor_cores;   /* uint8 frames on the tensor cores (fp16 hi/lo split operands,
                          fp32 accumulation): 1 both passes on mma.sync; 2 the
                          vertical pass on tcgen05 with its accumulator in tensor

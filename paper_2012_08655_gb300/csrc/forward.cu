@@ -37,10 +37,14 @@ struct SmemLayout {
   size_t ring, vv, taps, cum, red, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int rb, int row_bytes, int rmax) {
+// Ring stages of a kernel mode: float32-only launches (1024-byte rows) keep
+// two stages, so that 32-row chunks still leave room for two CTAs per SM.
+__host__ __device__ constexpr int mode_stages(int mode) { return mode == 1 ? 2 : kStages; }
+
+__host__ __device__ inline SmemLayout smem_layout(int rb, int row_bytes, int rmax, int stages) {
   SmemLayout L;
   L.ring = 0;
-  L.vv = L.ring + (size_t)kStages * rb * row_bytes;
+  L.vv = L.ring + (size_t)stages * rb * row_bytes;
   L.taps = L.vv + (size_t)16 * kVVPitch * sizeof(float2);
   L.cum = L.taps + (size_t)tap_len(rmax) * sizeof(float2);
   L.red = L.cum + (size_t)cum_len(rmax) * sizeof(float);
@@ -66,7 +70,7 @@ struct Smem {
 };
 
 // All slabs of one item; returns with acc2 holding the block's outputs.
-template <bool U8, int RB>
+template <bool U8, int RB, int ST>
 __device__ __forceinline__ void process_item(const Item& it, const Smem& sm, float2 (&acc2)[8]) {
   constexpr int row_bytes = U8 ? kRowBytesU8 : kRowBytesF32;
   constexpr size_t stage_bytes = (size_t)RB * row_bytes;
@@ -92,17 +96,17 @@ __device__ __forceinline__ void process_item(const Item& it, const Smem& sm, flo
   float2 wv[kN1];
 
   for (int q = 0; q < Q; ++q) {
-    cp_async_wait<kStages - 2>();
+    cp_async_wait<ST - 2>();
     __syncthreads();  // chunk q landed for every thread; chunk q-1 fully consumed
     {
-      const int qn = q + kStages - 1;
+      const int qn = q + ST - 1;
       if (qn < Q) stage_rows<U8, RB>(it, slab_of<U8>(it, qn / it.nchunks), qn % it.nchunks,
-                                     sm.ring + (size_t)(qn % kStages) * stage_bytes, frame_bytes);
+                                     sm.ring + (size_t)(qn % ST) * stage_bytes, frame_bytes);
       cp_async_commit();
     }
     const int s = q / it.nchunks, k = q - s * it.nchunks;
     const Slab sl = slab_of<U8>(it, s);
-    const unsigned char* st = sm.ring + (size_t)(q % kStages) * stage_bytes;
+    const unsigned char* st = sm.ring + (size_t)(q % ST) * stage_bytes;
     const int R0 = k * RB;
     // ring pair pi holds slab elements 2*pi - ph and 2*pi - ph + 1
     const int e_first = 2 * pi - sl.ph;
@@ -218,7 +222,7 @@ template <int RB, int MODE>
 __global__ void __launch_bounds__(kThreads, 2)
 forward_kernel(FrameSource src, Workspace ws, int rmax, int row_bytes, BucketList bl) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const SmemLayout L = smem_layout(RB, row_bytes, rmax);
+  const SmemLayout L = smem_layout(RB, row_bytes, rmax, mode_stages(MODE));
   Smem sm;
   sm.ring = smem + L.ring;
   sm.VV = reinterpret_cast<float2*>(smem + L.vv);
@@ -293,7 +297,7 @@ forward_kernel(FrameSource src, Workspace ws, int rmax, int row_bytes, BucketLis
     {
       constexpr int rbu = kRowBytesU8, rbf = kRowBytesF32;
       #pragma unroll
-      for (int q = 0; q < kStages - 1; ++q) {
+      for (int q = 0; q < mode_stages(MODE) - 1; ++q) {
         const int Q = (u8 ? it.nsl : it.nsl * it.C) * it.nchunks;
         if (q < Q) {
           if (MODE != 1 && u8) stage_rows<true, RB>(it, slab_of<true>(it, q / it.nchunks), q % it.nchunks,
@@ -311,8 +315,8 @@ forward_kernel(FrameSource src, Workspace ws, int rmax, int row_bytes, BucketLis
     float2 acc2[8];
     #pragma unroll
     for (int j = 0; j < 8; ++j) acc2[j] = make_float2(0.f, 0.f);
-    if (MODE != 1 && u8) process_item<true, RB>(it, sm, acc2);
-    if (MODE != 0 && !u8) process_item<false, RB>(it, sm, acc2);
+    if (MODE != 1 && u8) process_item<true, RB, mode_stages(MODE)>(it, sm, acc2);
+    if (MODE != 0 && !u8) process_item<false, RB, mode_stages(MODE)>(it, sm, acc2);
 
     cp_async_wait<0>();
     __syncthreads();  // ring no longer read; it becomes the output stage
@@ -395,13 +399,14 @@ namespace {
 
 // Row chunk the launch uses: the configured one, halved (down to 16 rows)
 // while a float32 launch's ring of 1024-byte rows would leave room for only
-// one CTA per SM (measured: 16-row chunks with two CTAs per SM beat 32-row
-// chunks with one on 224 x 224 float32 batches).
+// one CTA per SM (measured on 224 x 224 float32 batches: two CTAs per SM beat
+// one with longer chunks).
 int effective_rb(const FwdConfig& cfg, int rmax, int fmt_mask) {
   int rb = cfg.rows_per_chunk;
   if (fmt_mask & 2) {
     constexpr size_t kTwoPerSm = 110 * 1024;
-    while (rb > 16 && smem_layout(rb, kRowBytesF32, rmax).total > kTwoPerSm) rb /= 2;
+    const int st = mode_stages(mode_of(fmt_mask));
+    while (rb > 16 && smem_layout(rb, kRowBytesF32, rmax, st).total > kTwoPerSm) rb /= 2;
   }
   return rb;
 }
@@ -409,7 +414,8 @@ int effective_rb(const FwdConfig& cfg, int rmax, int fmt_mask) {
 }  // namespace
 
 size_t forward_smem_bytes(const FwdConfig& cfg, int rmax, int fmt_mask) {
-  return smem_layout(effective_rb(cfg, rmax, fmt_mask), (fmt_mask & 2) ? kRowBytesF32 : kRowBytesU8, rmax).total;
+  return smem_layout(effective_rb(cfg, rmax, fmt_mask), (fmt_mask & 2) ? kRowBytesF32 : kRowBytesU8, rmax,
+                     mode_stages(mode_of(fmt_mask))).total;
 }
 
 int forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int fmt_mask) {
