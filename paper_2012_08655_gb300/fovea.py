@@ -325,6 +325,18 @@ def _frames_array(frames: Sequence[BatchFrame]):
     return arr
 
 
+def _frames_of_nchw(x: torch.Tensor, y: torch.Tensor, fixes, sigma0: float, k: float):
+    """Frame array of a contiguous float32 [N, C, H, W] batch (input x,
+    output y) from the base pointers, without a tensor view per image."""
+    n, c, h, w = x.shape
+    step = c * h * w * 4
+    xi, yo = x.data_ptr(), y.data_ptr()
+    arr = (Frame * n)()
+    for i, (fx, fy) in enumerate(fixes):
+        arr[i] = Frame(w, h, c, F32_CHW, xi + i * step, yo + i * step, fx, fy, sigma0, k, GRID_ANCHORED, None, 0.0)
+    return arr
+
+
 # ------------------------------------------------------------------ functional API
 _ctx_cache: dict = {}
 
@@ -466,10 +478,13 @@ class FoveaFunction(torch.autograd.Function):
         if x.dtype != torch.float32 or x.dim() != 4:
             raise ValueError("FoveaFunction takes float32 [N, C, H, W]")
         x = x.contiguous()
+        if not x.is_cuda:
+            raise ValueError("FoveaFunction takes a CUDA tensor")
         fixes = [(float(a), float(b)) for a, b in fix.detach().cpu().tolist()]
         y = torch.empty_like(x)
-        frames = [BatchFrame(x[i], y[i], fx, fy, sigma0, k) for i, (fx, fy) in enumerate(fixes)]
-        _batch_ctx(block).render_batch(frames)
+        bctx = _batch_ctx(block)
+        arr = _frames_of_nchw(x, y, fixes, float(sigma0), float(k))
+        _check(_lib.fovea_render_batch(bctx._h, arr, len(fixes), _stream_handle(None)), "fovea_render_batch")
         ctx.fixes, ctx.sigma0, ctx.k, ctx.block = fixes, sigma0, k, block
         return y
 
@@ -477,8 +492,9 @@ class FoveaFunction(torch.autograd.Function):
     def backward(ctx, gy: torch.Tensor):
         gy = gy.contiguous()
         gx = torch.empty_like(gy)
-        frames = [BatchFrame(gy[i], gx[i], fx, fy, ctx.sigma0, ctx.k) for i, (fx, fy) in enumerate(ctx.fixes)]
-        _batch_ctx(ctx.block).backward_batch(frames)
+        bctx = _batch_ctx(ctx.block)
+        arr = _frames_of_nchw(gy, gx, ctx.fixes, float(ctx.sigma0), float(ctx.k))
+        _check(_lib.fovea_backward_batch(bctx._h, arr, len(ctx.fixes), _stream_handle(None)), "fovea_backward_batch")
         return gx, None, None, None, None
 
 
