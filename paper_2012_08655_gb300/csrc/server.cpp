@@ -14,6 +14,9 @@
 //      and, once that copy is seen complete, frees the arena space.
 // The paper's per-frame loop (Algorithm 1: pinned host -> device, kernel,
 // device -> pinned host) is the special case max_batch = 1.
+#if defined(__linux__)
+#include <sys/prctl.h>
+#endif
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -112,6 +115,8 @@ struct fovea_server {
   long long next_id = 0;
   bool stop = false;
   std::thread worker;
+  double hold_since_us = -1.0;  // a partial batch waits for inputs still copying in since then
+  static constexpr double kBatchWindowUs = 30.0;
 
   cudaEvent_t get_event() {
     if (!event_pool.empty()) {
@@ -139,6 +144,9 @@ struct fovea_server {
 
 void fovea_server::run() {
   cudaSetDevice(device);
+#if defined(__linux__)
+  prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);  // 1 us: short polling sleeps stay short
+#endif
   std::vector<Request*> fresh, ready;
   std::vector<fovea_frame> frames;
   for (;;) {
@@ -166,25 +174,41 @@ void fovea_server::run() {
       cudaEventRecord(r->ev_in, s_in);
       progressed = true;
     }
-    // retire finished renders so at most two batches queue on the compute stream
+    // Retire finished renders. One batch at a time on the compute stream:
+    // requests that become ready while it runs form the next batch (an idle
+    // GPU takes a request at once, a busy one collects them).
     while (!batch_events.empty() && cudaEventQuery(batch_events.front()) == cudaSuccess) {
       std::lock_guard<std::mutex> lk(mu);
       event_pool.push_back(batch_events.front());
       batch_events.pop_front();
     }
-    if (batch_events.size() < 2) {
+    if (batch_events.empty()) {
       ready.clear();
       {
         std::lock_guard<std::mutex> lk(mu);
+        int copying = 0;
         for (size_t i = 0; i < admitted.size() && (int)ready.size() < cfg.max_batch;) {
           Request* r = admitted[i];
           if (cudaEventQuery(r->ev_in) == cudaSuccess) {
             ready.push_back(r);
             admitted.erase(admitted.begin() + (long)i);
           } else {
+            ++copying;
             ++i;
           }
         }
+        // While more inputs are still copying in, hold a partial batch for up
+        // to kBatchWindowUs so that they join it (a stream of frames arriving
+        // together runs as one batch); a lone request goes at once.
+        if (!ready.empty() && copying > 0 && (int)ready.size() < cfg.max_batch) {
+          const double now = now_us();
+          if (hold_since_us < 0.0) hold_since_us = now;
+          if (now - hold_since_us < kBatchWindowUs) {
+            admitted.insert(admitted.begin(), ready.begin(), ready.end());
+            ready.clear();
+          }
+        }
+        if (!ready.empty()) hold_since_us = -1.0;
       }
       if (!ready.empty()) {
         // One batch per (format, channel count): a request is rendered by the
@@ -259,11 +283,14 @@ void fovea_server::run() {
     }
     if (!progressed) {
       std::unique_lock<std::mutex> lk(mu);
-      if (pending.empty() && admitted.empty() && launched.empty() && !stop)
+      if (pending.empty() && admitted.empty() && launched.empty() && !stop) {
         cv_work.wait_for(lk, std::chrono::milliseconds(5));
-      else {
+      } else {
+        // Work is in flight: poll again after 10 us (the worker runs with a
+        // 1 us timer slack, so the sleep stays short, yet the submitting
+        // threads still get the lock between polls).
         lk.unlock();
-        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        std::this_thread::sleep_for(std::chrono::microseconds(10));
       }
     }
   }

@@ -185,13 +185,17 @@ def test_server_result_alone_equals_result_in_the_mix(fv):
             t = srv.wait(rid)
             assert t["status"] == 0 and t["batch_size"] == 1
             alone.append(out)
-        outs, rids = [], []
-        for rep in range(3):
-            for inp, fx, fy in frames:
-                out = torch.empty_like(inp).pin_memory()
-                rids.append(srv.submit(inp, out, fx, fy, 0.5, 0.02))
-                outs.append(out)
-        sizes = [srv.wait(r)["batch_size"] for r in rids]
+        # The burst: outputs allocated first so that the submissions follow one
+        # another closely, and a 4K frame in front keeps the GPU busy while
+        # the rest arrive (the loop launches a request as soon as it can).
+        big = torch.from_numpy(wl.grating_frame(2160, 3840, 3, seed=29)).pin_memory()
+        big_out = torch.empty_like(big).pin_memory()
+        outs = [torch.empty_like(inp).pin_memory() for rep in range(3) for inp, _, _ in frames]
+        rids = [srv.submit(big, big_out, 1000.0, 500.0, 0.5, 0.02)]
+        for j, out in enumerate(outs):
+            inp, fx, fy = frames[j % len(frames)]
+            rids.append(srv.submit(inp, out, fx, fy, 0.5, 0.02))
+        sizes = [srv.wait(r)["batch_size"] for r in rids][1:]
     assert max(sizes) > 1, "the burst was never batched"
     for j, out in enumerate(outs):
         assert torch.equal(out, alone[j % len(frames)])
