@@ -508,8 +508,10 @@ static int render_one(fovea_ctx* ctx, const void* in_dev, void* out_dev, float f
   const int rmax = radius_bound(ctx->W, ctx->H, ctx->B, fix_x, fix_y, ctx->law);
   const int fmt_mask = ctx->fmt == FOVEA_F32_CHW ? 2 : 1;
   const int tc_c = ctx->C;
-  const int grid = forward_grid(ctx, rmax, fmt_mask, tc_c);
+  int grid = forward_grid(ctx, rmax, fmt_mask, tc_c);
   if (grid <= 0) return FOVEA_EUNSUPPORTED;
+  // no more persistent CTAs than items (small frames start fewer CTAs)
+  grid = (int)std::min<long long>(grid, src.one_total);
   // Single frame: the sigma kernel also files every block under its radius
   // and the blur kernel orders its own work (largest radius first) from the
   // histogram, so no ordering kernel runs in between.
