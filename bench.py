@@ -638,12 +638,23 @@ def served_leg(fv, torch, seconds: float, max_batch: int):
     bs = np.array([t["batch_size"] for _, t in done])
     span = (max(t["done_us"] for _, t in done) - t0) * 1e-6
     px = sum(r.width * r.height for r in reqs)
+    # Where the slowest 1 % of requests spend their time: waiting for
+    # admission, waiting for their input copy and batch launch, and from the
+    # batch launch until the worker saw their output copy finish.
+    tail = lat >= np.percentile(lat, 99)
+    ph = np.array([[t["admit_us"] - t["arrival_us"], t["start_us"] - t["admit_us"], t["done_us"] - t["start_us"]]
+                   for _, t in done]) * 1e-3
+    rpx = np.array([reqs[i].width * reqs[i].height for i, _ in done])
+    tail_info = {"requests": int(tail.sum()), "mean_ms": float(lat[tail].mean()),
+                 "admit_ms": float(ph[tail, 0].mean()), "copy_and_launch_ms": float(ph[tail, 1].mean()),
+                 "render_and_d2h_ms": float(ph[tail, 2].mean()), "mean_mpix": float(rpx[tail].mean() / 1e6),
+                 "mean_batch": float(bs[tail].mean())}
     return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "mpix_s": px / span / 1e6, "requests": len(reqs),
             "mean_batch": float(bs.mean()), "errors": int(sum(1 for _, t in done if t["status"] != 0)),
             "from_submit_p50_ms": float(np.percentile(srv_lat, 50)),
             "from_submit_p99_ms": float(np.percentile(srv_lat, 99)),
-            "generator_late_p99_ms": float(np.percentile(late, 99)),
+            "generator_late_p99_ms": float(np.percentile(late, 99)), "slowest_1pct": tail_info,
             "latency_note": "p50/p99 from the scheduled (Poisson) arrival; from_submit_* from the moment the "
                             "Python generator handed the request over (its lateness is generator_late_*)"}
 

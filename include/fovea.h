@@ -160,6 +160,20 @@ int fovea_grid(const fovea_ctx* ctx, float fix_x, float fix_y, int* nbx, int* nb
  * `frames` array is read before the call returns. */
 int fovea_render_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, void* stream);
 
+/* Pre-size the context's batch buffers for batches of up to `max_frames`
+ * frames holding up to `max_items` (frame, block) items in all (an item is
+ * one block of one frame; a W x H frame has about ceil(W/B) * ceil(H/B)).
+ * Without it the buffers grow on demand, at least twofold each time, and a
+ * growth recaptures the batch graphs on the calling thread (hundreds of
+ * microseconds), which a latency-bound caller such as a serving loop wants to
+ * pay up front. Zero leaves that part as it is. Memory: 32 device bytes per
+ * item, and per frame 232 bytes of device table plus as much in each of four
+ * pinned host staging slots; replaced buffers stay allocated until
+ * fovea_destroy. Returns FOVEA_EINVAL for a null context, negative sizes,
+ * max_frames above 2^24 or max_items above 2^31 - 1, FOVEA_ECUDA when an
+ * allocation fails. Not in the paper: buffer management of the batch path. */
+int fovea_reserve(fovea_ctx* ctx, int max_frames, long long max_items);
+
 /* Foveate one frame held in HOST memory (Algorithm 1's transfers of the
  * input from and the output to pinned host memory around the render). The
  * context owns two device staging slots and three internal streams (copy in,

@@ -83,6 +83,9 @@ struct fovea_ctx {
   int batch_slot = 0;
   // CUDA graphs of the batch launch sequence, keyed by (kind + 2*format mask + 8*tc channels, radius bound)
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+  // Batch buffers replaced by larger ones while queued work may still read
+  // them: freed by fovea_destroy, so growing never waits for the device.
+  std::vector<void*> retired_dev, retired_host;
   // optional events bracketing the persistent blur kernel (measurement)
   cudaEvent_t kev_start = nullptr, kev_stop = nullptr;
   // per-radius item lists of the single-frame path
@@ -213,18 +216,28 @@ FrameDesc make_desc(int W, int H, int C, int fmt, int B, const void* in, void* o
 
 namespace {
 
+void drop_graphs(fovea_ctx* ctx) {
+  // An executable graph destroyed while a launch of it is in flight is
+  // released when that launch completes.
+  for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  ctx->graphs.clear();
+}
+
+// Item workspace for `items` items. Grows at least twofold, so a stream of
+// ever larger batches reallocates (and recaptures its graphs) a logarithmic
+// number of times; the old buffers may still be read by queued work and are
+// retired rather than freed, so growing does not wait for the device.
 int ensure_workspace(fovea_ctx* ctx, long long items) {
   if (ctx->ws.capacity >= items && ctx->ws.counters) return FOVEA_OK;
-  long long cap = std::max<long long>(items, 1024);
+  long long cap = std::max<long long>({items, 2 * ctx->ws.capacity, 1024});
   if (ctx->ws.items) {
-    // Growing: the old buffers may still be in use by queued work.
-    FOVEA_CUDA(cudaDeviceSynchronize());
-    cudaFree(ctx->ws.items);
-    cudaFree(ctx->ws.rank);
-    cudaFree(ctx->ws.order);
+    ctx->retired_dev.push_back(ctx->ws.items);
+    ctx->retired_dev.push_back(ctx->ws.rank);
+    ctx->retired_dev.push_back(ctx->ws.order);
     ctx->ws.items = nullptr;
-    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-    ctx->graphs.clear();
+    ctx->ws.rank = ctx->ws.order = nullptr;
+    ctx->ws.capacity = 0;
+    drop_graphs(ctx);
   }
   FOVEA_CUDA(cudaMalloc(&ctx->ws.items, cap * sizeof(ItemInfo)));
   FOVEA_CUDA(cudaMalloc(&ctx->ws.rank, cap * sizeof(int)));
@@ -272,6 +285,44 @@ int adjoint_grid(fovea_ctx* ctx, int rmax) {
 
 // Stage n frame descriptors into the pinned slot ring and copy them to the
 // device-resident batch buffer on `s`. Returns total items in *total.
+// Bytes of the batch table for n frames: header, descriptors, then one
+// tensor map per frame on its alignment.
+size_t batch_table_maps_offset(int n) {
+  return (sizeof(BatchHeader) + (size_t)n * sizeof(FrameDesc) + kTensorMapAlign - 1) & ~(kTensorMapAlign - 1);
+}
+size_t batch_table_bytes(int n) { return batch_table_maps_offset(n) + (size_t)n * kTensorMapBytes; }
+
+// Device batch table and its pinned host staging slots for `bytes` bytes.
+// Replaced buffers are retired (queued copies and kernels may still use
+// them), so growing waits for nothing.
+int ensure_batch_tables(fovea_ctx* ctx, size_t bytes) {
+  if (bytes > ctx->batch_dev_cap) {
+    if (ctx->batch_dev) {
+      ctx->retired_dev.push_back(ctx->batch_dev);
+      ctx->batch_dev = nullptr;
+      ctx->batch_dev_cap = 0;
+      drop_graphs(ctx);
+    }
+    size_t cap = std::max<size_t>(bytes * 2, 64 * 1024);
+    FOVEA_CUDA(cudaMalloc(&ctx->batch_dev, cap));
+    ctx->batch_dev_cap = cap;
+  }
+  if (bytes > ctx->batch_host_cap) {
+    for (int i = 0; i < kBatchSlots; ++i) {
+      if (ctx->batch_host[i]) ctx->retired_host.push_back(ctx->batch_host[i]);
+      ctx->batch_host[i] = nullptr;
+    }
+    ctx->batch_host_cap = 0;
+    size_t cap = std::max<size_t>(bytes * 2, 64 * 1024);
+    for (int i = 0; i < kBatchSlots; ++i) {
+      FOVEA_CUDA(cudaHostAlloc(&ctx->batch_host[i], cap, cudaHostAllocDefault));
+      if (!ctx->batch_ev[i]) FOVEA_CUDA(cudaEventCreateWithFlags(&ctx->batch_ev[i], cudaEventDisableTiming));
+    }
+    ctx->batch_host_cap = cap;
+  }
+  return FOVEA_OK;
+}
+
 int upload_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint, cudaStream_t s,
                  long long* total, int* rmax, int* fmt_mask, int* tc_c) {
   if (n <= 0 || !frames) return FOVEA_EINVAL;
@@ -300,35 +351,11 @@ int upload_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint,
   int st = ensure_workspace(ctx, item0);
   if (st != FOVEA_OK) return st;
   // tensor maps of the uint8 frames for the tensor-core kernel's row loads
-  const size_t maps_off = (sizeof(BatchHeader) + (size_t)n * sizeof(FrameDesc) + kTensorMapAlign - 1) &
-                          ~(kTensorMapAlign - 1);
-  const size_t bytes = maps_off + (size_t)n * kTensorMapBytes;
+  const size_t maps_off = batch_table_maps_offset(n);
+  const size_t bytes = batch_table_bytes(n);
   if (maps_off > (size_t)0x7fffffff) return FOVEA_EUNSUPPORTED;
-  if (bytes > ctx->batch_dev_cap) {
-    if (ctx->batch_dev) {
-      FOVEA_CUDA(cudaDeviceSynchronize());
-      cudaFree(ctx->batch_dev);
-      ctx->batch_dev = nullptr;
-      for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-      ctx->graphs.clear();
-    }
-    size_t cap = std::max<size_t>(bytes * 2, 64 * 1024);
-    FOVEA_CUDA(cudaMalloc(&ctx->batch_dev, cap));
-    ctx->batch_dev_cap = cap;
-  }
-  if (bytes > ctx->batch_host_cap) {
-    for (int i = 0; i < kBatchSlots; ++i) {
-      if (ctx->batch_ev[i]) cudaEventSynchronize(ctx->batch_ev[i]);
-      if (ctx->batch_host[i]) cudaFreeHost(ctx->batch_host[i]);
-      ctx->batch_host[i] = nullptr;
-    }
-    size_t cap = std::max<size_t>(bytes * 2, 64 * 1024);
-    for (int i = 0; i < kBatchSlots; ++i) {
-      FOVEA_CUDA(cudaHostAlloc(&ctx->batch_host[i], cap, cudaHostAllocDefault));
-      if (!ctx->batch_ev[i]) FOVEA_CUDA(cudaEventCreateWithFlags(&ctx->batch_ev[i], cudaEventDisableTiming));
-    }
-    ctx->batch_host_cap = cap;
-  }
+  st = ensure_batch_tables(ctx, bytes);
+  if (st != FOVEA_OK) return st;
   const int slot = ctx->batch_slot;
   ctx->batch_slot = (slot + 1) % kBatchSlots;
   FOVEA_CUDA(cudaEventSynchronize(ctx->batch_ev[slot]));  // copy from this slot finished
@@ -843,6 +870,20 @@ int fovea_set_config(fovea_ctx* ctx, const fovea_config* cfg) {
   return FOVEA_OK;
 }
 
+int fovea_reserve(fovea_ctx* ctx, int max_frames, long long max_items) {
+  if (!ctx || max_frames < 0 || max_items < 0 || max_frames > (1 << 24) || max_items > (1ll << 31) - 1)
+    return FOVEA_EINVAL;
+  if (max_items > 0) {
+    int st = ensure_workspace(ctx, max_items);
+    if (st != FOVEA_OK) return st;
+  }
+  if (max_frames > 0) {
+    int st = ensure_batch_tables(ctx, batch_table_bytes(max_frames));
+    if (st != FOVEA_OK) return st;
+  }
+  return FOVEA_OK;
+}
+
 int fovea_set_kernel_events(fovea_ctx* ctx, void* ev_start, void* ev_stop) {
   if (!ctx || (ev_start == nullptr) != (ev_stop == nullptr)) return FOVEA_EINVAL;
   ctx->kev_start = static_cast<cudaEvent_t>(ev_start);
@@ -872,6 +913,8 @@ void fovea_destroy(fovea_ctx* ctx) {
     if (sl.ev_d2h) cudaEventDestroy(sl.ev_d2h);
   }
   if (ctx->pyr) cudaFree(ctx->pyr);
+  for (void* p : ctx->retired_dev) cudaFree(p);
+  for (void* p : ctx->retired_host) cudaFreeHost(p);
   if (ctx->ev_entry) cudaEventDestroy(ctx->ev_entry);
   if (ctx->s_h2d) cudaStreamDestroy(ctx->s_h2d);
   if (ctx->s_comp) cudaStreamDestroy(ctx->s_comp);

@@ -320,6 +320,20 @@ int fovea_server_create(const fovea_server_config* cfg, fovea_server** out) {
   s->arena.reset(cfg->device_budget_bytes);
   fovea_sigma_law law{FOVEA_LAW_LINEAR, 0.5, 0.02, 0.0, nullptr, 0.0, FOVEA_GRID_ANCHORED};
   int st = fovea_create(0, 0, 3, cfg->block, &law, FOVEA_U8_HWC, &s->ctx);
+  // Size the batch buffers for the largest batch the arena can hold, so that
+  // no batch grows them (a growth recaptures the batch graphs on this
+  // thread, and the backlog that makes a batch large is when that hurts
+  // most). A batch's frames are all resident in the arena, input and output,
+  // so they hold at most budget / 2 pixels; a frame of W x H pixels has at
+  // most (W / B + 1) (H / B + 1) items, at most 4 W H / B^2 when both sides
+  // are at least B. Smaller frames are covered by 16 items a frame; beyond
+  // the cap the buffers still grow on demand.
+  if (st == FOVEA_OK) {
+    const long long bb = (long long)cfg->block * cfg->block;
+    const long long items = std::min<long long>(
+        2 * (long long)(cfg->device_budget_bytes / (size_t)bb) + 16ll * cfg->max_batch, 1ll << 22);
+    st = fovea_reserve(s->ctx, std::min(cfg->max_batch, 1 << 24), items);
+  }
   if (st != FOVEA_OK) {
     fovea_server_destroy(s);
     return st;

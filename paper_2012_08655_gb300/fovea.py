@@ -74,6 +74,7 @@ _sig = {
     "fovea_create": (_i, [_i, _i, _i, _i, ctypes.POINTER(SigmaLaw), _i, ctypes.POINTER(_vp)]),
     "fovea_render": (_i, [_vp, _vp, _vp, _f, _f, _vp]),
     "fovea_render_batch": (_i, [_vp, ctypes.POINTER(Frame), _i, _vp]),
+    "fovea_reserve": (_i, [_vp, _i, ctypes.c_longlong]),
     "fovea_render_host": (_i, [_vp, _vp, _vp, _f, _f, _vp]),
     "fovea_render_pixelwise": (_i, [_vp, _vp, _vp, _f, _f, _vp]),
     "fovea_render_pyramid": (_i, [_vp, _vp, _vp, _f, _f, _vp]),
@@ -263,6 +264,10 @@ class Context:
     def render_batch(self, frames: Sequence["BatchFrame"], stream=None):
         arr = _frames_array(frames)
         _check(_lib.fovea_render_batch(self._h, arr, len(frames), _stream_handle(stream)), "fovea_render_batch")
+
+    def reserve(self, max_frames: int, max_items: int):
+        """Pre-size the batch buffers (frames per batch, (frame, block) items in all)."""
+        _check(_lib.fovea_reserve(self._h, int(max_frames), int(max_items)), "fovea_reserve")
 
     def backward_batch(self, frames: Sequence["BatchFrame"], stream=None):
         arr = _frames_array(frames)

@@ -81,6 +81,8 @@ def test_strerror_and_invalid_arguments(lib):
     assert lib.fovea_render_pixelwise(None, None, None, 1.0, 1.0, None) == -1
     lib.fovea_render_pyramid.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_float] * 2 + [ctypes.c_void_p]
     assert lib.fovea_render_pyramid(None, None, None, 1.0, 1.0, None) == -1
+    lib.fovea_reserve.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong]
+    assert lib.fovea_reserve(None, 4, 1024) == -1
     lib.fovea_ssim.argtypes = [ctypes.c_int] * 4 + [ctypes.c_void_p] * 2 + [ctypes.c_double] + [ctypes.c_void_p] * 3
     fake = ctypes.c_void_p(16)  # never dereferenced: every call below is refused on the host
     assert lib.fovea_ssim(8, 8, 3, 0, None, fake, 0.0, fake, None, None) == -1      # null image

@@ -89,6 +89,45 @@ def test_consecutive_batches_with_new_buffers(fv):
             assert torch.equal(single, outs[i]), f"round {rnd} frame {i}: batch differs from single-frame render"
 
 
+def test_batch_buffers_grow_while_earlier_batches_are_queued(fv):
+    """A fresh batch context given ever larger batches back to back on one
+    stream, with no synchronisation between them: each launch outgrows the
+    item workspace or the batch table, so the buffers the queued launches
+    read are replaced (and kept) while those launches are still pending.
+    Every frame equals its single-frame render; a context whose buffers were
+    reserved up front renders the same bytes."""
+    shapes = [(84, 84), (224, 224), (640, 480), (1280, 720), (1920, 1080), (3840, 2160)]
+    jobs = []
+    for n in (1, 3, 9, 24):
+        ins = [torch.from_numpy(wl.grating_frame(shapes[i % 6][1], shapes[i % 6][0], 3, seed=7 * n + i)).cuda()
+               for i in range(n)]
+        fix = [(0.3 * x.shape[1] + n, 0.55 * x.shape[0]) for x in ins]
+        jobs.append((ins, fix))
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    grown, reserved = fv.batch_context(32), fv.batch_context(32)
+    reserved.reserve(64, 1 << 20)
+    results = []
+    with torch.cuda.stream(stream):
+        for ins, fix in jobs:
+            outs = [torch.empty_like(x) for x in ins]
+            grown.render_batch([fv.BatchFrame(x, o, f[0], f[1], 0.5, 0.02) for x, o, f in zip(ins, outs, fix)],
+                               stream)
+            outs_r = [torch.empty_like(x) for x in ins]
+            reserved.render_batch([fv.BatchFrame(x, o, f[0], f[1], 0.5, 0.02) for x, o, f in zip(ins, outs_r, fix)],
+                                  stream)
+            results.append((outs, outs_r))
+    stream.synchronize()
+    for (ins, fix), (outs, outs_r) in zip(jobs, results):
+        for i, x in enumerate(ins):
+            single = fv.foveate(x, fix[i][0], fix[i][1], 0.5, 0.02)
+            torch.cuda.synchronize()
+            assert torch.equal(single, outs[i]), f"batch of {len(ins)}, frame {i}: differs after growth"
+            assert torch.equal(single, outs_r[i]), f"batch of {len(ins)}, frame {i}: differs with reserved buffers"
+    grown.close()
+    reserved.close()
+
+
 # ---------------------------------------------------------------- differentiable form
 
 def test_train_batch_forward_backward_vs_oracle(fv):
