@@ -659,6 +659,41 @@ def served_leg(fv, torch, seconds: float, max_batch: int):
                             "Python generator handed the request over (its lateness is generator_late_*)"}
 
 
+def served_device_only(fv, torch, reps: int = 200):
+    """Device-only time of the served stream's requests: per request class,
+    one frame per batch launch from device-resident buffers (no copies),
+    CUDA events around `reps` back-to-back launches with the stream's own
+    fixations; the mean over the class mix weights each class by its share."""
+    from paper_2012_08655_gb300 import workloads as wl
+    stream = wl.served_stream(seed=0, duration_s=10.0)
+    ctx = fv.batch_context(32)
+    cur = torch.cuda.current_stream()
+    by, wsum, tsum, psum = {}, 0.0, 0.0, 0.0
+    for ci, (w, h, c, wt, _) in enumerate(wl.STREAM_CLASSES):
+        x = torch.from_numpy(wl.grating_frame(h, w, c, seed=100 + ci)).cuda()
+        o = torch.empty_like(x)
+        fixes = [(r.fix_x, r.fix_y) for r in stream.requests if (r.width, r.height) == (w, h)][:reps]
+        frames = [[fv.BatchFrame(x, o, fx, fy, stream.sigma0, stream.k)] for fx, fy in fixes]
+        for f in frames[:20]:
+            ctx.render_batch(f, cur)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(cur)
+        for f in frames:
+            ctx.render_batch(f, cur)
+        e1.record(cur)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / len(frames)
+        by[f"{w}x{h}x{c}"] = ms
+        wsum += wt
+        tsum += wt * ms
+        psum += wt * w * h
+    ctx.close()
+    return {"per_request_ms": by, "mix_mean_ms": tsum / wsum, "mix_capacity_mpix_s": psum / (tsum * 1e-3) / 1e6,
+            "note": "one frame per batch launch (sigma, order and blur kernels), device-resident buffers, "
+                    f"CUDA events over {reps} back-to-back launches per class"}
+
+
 def saturated_leg(fv, torch, seconds: float):
     """The served stream's requests all at once (no pacing): the serving loop
     (continuous batching) against the plain path, one fovea_render_host call
@@ -847,6 +882,7 @@ def run_ours(args):
         served = served_leg(fv, torch, args.served_seconds, max_batch=64)
         plain = served_leg(fv, torch, args.served_seconds, max_batch=1)
         served["plain_per_frame"] = {k: plain[k] for k in ("p50_ms", "p99_ms", "mpix_s", "mean_batch")}
+        served["device_only"] = served_device_only(fv, torch)
         extras["served"] = served
         extras["saturated"] = saturated_leg(fv, torch, args.served_seconds)
 
