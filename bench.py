@@ -479,8 +479,39 @@ def plain_leg(fv, torch, reps: int = 2000):
     e1.record()
     torch.cuda.synchronize()
     us = e0.elapsed_time(e1) / reps * 1e3
+    # The same renders captured into a CUDA graph (100 per graph) and
+    # replayed: the device time per render without host launch overhead,
+    # the median over replays.
+    graph = None
+    try:
+        import numpy as np
+        cs = torch.cuda.Stream()
+        cs.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(cs):
+            for _ in range(3):
+                ctx.render(x, y, spec.fix_x, spec.fix_y)
+        cs.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cs):
+            for _ in range(100):
+                ctx.render(x, y, spec.fix_x, spec.fix_y)
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        per = []
+        cur = torch.cuda.current_stream()
+        for _ in range(50):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(cur)
+            g.replay()
+            b.record(cur)
+            b.synchronize()
+            per.append(a.elapsed_time(b) * 10.0)  # ms per 100 renders -> us per render
+        graph = {"us_per_render_median": float(np.median(per)), "replays": len(per), "renders_per_graph": 100}
+    except Exception as ex:  # reported, not fatal: the eager figure stands
+        graph = {"error": str(ex)[:200]}
     return {"workload": f"{w}x{h}x1 float32 U[0,1), sigma = {spec.sigma0} + {spec.k} e, fixation ({spec.fix_x}, "
-                        f"{spec.fix_y})", "us_per_render": us, "renders": reps}
+                        f"{spec.fix_y})", "us_per_render": us, "renders": reps, "graph_replay": graph}
 
 
 def pixel_radii(width, height, fix_x, fix_y, sigma0, k):

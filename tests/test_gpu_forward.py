@@ -146,6 +146,44 @@ def test_render_host_and_batch_match_render(fv):
     assert torch.equal(y1, y3)
 
 
+@pytest.mark.parametrize("kind", ["f32_256", "u8_1080p"])
+def test_render_captured_in_a_cuda_graph(fv, kind):
+    """fovea_render captured into a CUDA graph (after one eager call at the
+    same size and fixation, which sizes the context) and replayed: every
+    replay writes the eager output bit for bit, with the input changed in
+    place between replays."""
+    if kind == "f32_256":
+        spec = wl.plain_f32()
+        x = to_dev(spec.image)
+        ctx = fv.Context(256, 256, 1, 32, spec.sigma0, spec.k, fv.F32_CHW)
+        fx, fy = spec.fix_x, spec.fix_y
+        other = to_dev(wl.uniform_f32(spec.image.shape, seed=3))
+    else:
+        s = wl.frame_1080p(seed=6)
+        x = to_dev(s.image)
+        ctx = fv.Context(1920, 1080, 3, 32, s.sigma0, s.k, fv.U8_HWC)
+        fx, fy = s.fix_x, s.fix_y
+        other = to_dev(wl.uniform_u8(s.image.shape, seed=3))
+    y = torch.empty_like(x)
+    cs = torch.cuda.Stream()
+    cs.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(cs):
+        ctx.render(x, y, fx, fy)
+    cs.synchronize()
+    src = x.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=cs):
+        ctx.render(src, y, fx, fy)
+    for inp in (x, other, x):
+        src.copy_(inp)
+        y.zero_()
+        g.replay()
+        ref = torch.empty_like(inp)
+        ctx.render(inp, ref, fx, fy)
+        torch.cuda.synchronize()
+        assert torch.equal(y, ref)
+
+
 def test_render_host_pipelined_calls(fv):
     """Consecutive host calls alternate staging slots and overlap one another's
     copies and kernels; interleaved device-path calls on the same stream stay
