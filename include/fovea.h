@@ -128,7 +128,11 @@ int fovea_create(int width, int height, int channels, int block, const fovea_sig
  * per-frame GPU steps: padded tile, horizontal and vertical convolution,
  * write-out). `in_dev` and `out_dev` hold one frame in the context's format
  * and shape; the fixation (fix_x, fix_y) is in pixel coordinates and may lie
- * anywhere, inside or outside the frame (Section 2). */
+ * anywhere, inside or outside the frame (Section 2). The call may be
+ * captured into a CUDA graph once an earlier call on this context had a
+ * radius bound at least as large (the same fixation, for instance): a call
+ * whose bound exceeds every earlier one grows a work-list buffer, which
+ * synchronises the device and would end the capture with an error. */
 int fovea_render(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x, float fix_y,
                  void* stream);
 
