@@ -338,11 +338,13 @@ int fovea_measure_fma_rate(double* fma_per_s, void* stream);
  * Continuous-batching request loop (not in the paper; it serves frames of
  * different resolutions and fixations as they arrive). Frames start and end
  * in host memory. Requests are admitted while device memory for their input
- * and output is available within `device_budget_bytes`; every scheduling tick
- * the worker renders the admitted requests whose input copy has finished,
- * one batch per (format, channel count) (same kernels as fovea_render_batch),
- * while later requests copy in on a second stream. Results are copied back to
- * the caller's host buffer.
+ * and output is available within `device_budget_bytes`, and their inputs
+ * copy in on a copy stream at once. Whenever no batch is rendering, the
+ * worker renders up to max_batch admitted requests, one batch per (format,
+ * channel count) (same kernels as fovea_render_batch), on a compute stream
+ * that waits on the device for their input copies; requests admitted while a
+ * batch renders gather into the next one. Results are copied back to the
+ * caller's host buffer.
  */
 typedef struct {
   size_t device_budget_bytes;  /* cap on device memory used for request buffers */

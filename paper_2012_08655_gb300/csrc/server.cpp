@@ -5,11 +5,11 @@
 //      buffers fit in a fixed device arena (admission by device memory) and
 //      fewer than max_inflight requests are admitted;
 //   2. copies each admitted input to the device on a copy stream;
-//   3. every tick, renders the admitted requests whose input copy has
-//      finished, one batch per (format, channel count) (fovea_render_batch:
+//   3. whenever no batch is rendering, renders up to max_batch admitted
+//      requests, one batch per (format, channel count) (fovea_render_batch:
 //      sigma table, cost-ordered work list, persistent kernel) on a compute
-//      stream, with at most two ticks' batches queued so requests arriving
-//      meanwhile gather into the next tick;
+//      stream that waits on the device for their input copies; requests
+//      admitted while a batch renders gather into the next one;
 //   4. copies each result back to its caller's host buffer on a third stream
 //      and, once that copy is seen complete, frees the arena space.
 // The paper's per-frame loop (Algorithm 1: pinned host -> device, kernel,
@@ -115,8 +115,6 @@ struct fovea_server {
   long long next_id = 0;
   bool stop = false;
   std::thread worker;
-  double hold_since_us = -1.0;  // a partial batch waits for inputs still copying in since then
-  static constexpr double kBatchWindowUs = 30.0;
 
   cudaEvent_t get_event() {
     if (!event_pool.empty()) {
@@ -185,30 +183,17 @@ void fovea_server::run() {
     if (batch_events.empty()) {
       ready.clear();
       {
+        // Every admitted request joins the batch, whether or not its input
+        // copy has landed: the compute stream waits for the copies on the
+        // device, so the launch overlaps them and no host poll sits between
+        // a copy finishing and its render starting.
         std::lock_guard<std::mutex> lk(mu);
-        int copying = 0;
-        for (size_t i = 0; i < admitted.size() && (int)ready.size() < cfg.max_batch;) {
-          Request* r = admitted[i];
-          if (cudaEventQuery(r->ev_in) == cudaSuccess) {
-            ready.push_back(r);
-            admitted.erase(admitted.begin() + (long)i);
-          } else {
-            ++copying;
-            ++i;
-          }
-        }
-        // While more inputs are still copying in, hold a partial batch for up
-        // to kBatchWindowUs so that they join it (a stream of frames arriving
-        // together runs as one batch); a lone request goes at once.
-        if (!ready.empty() && copying > 0 && (int)ready.size() < cfg.max_batch) {
-          const double now = now_us();
-          if (hold_since_us < 0.0) hold_since_us = now;
-          if (now - hold_since_us < kBatchWindowUs) {
-            admitted.insert(admitted.begin(), ready.begin(), ready.end());
-            ready.clear();
-          }
-        }
-        if (!ready.empty()) hold_since_us = -1.0;
+        const size_t take = std::min(admitted.size(), (size_t)cfg.max_batch);
+        ready.assign(admitted.begin(), admitted.begin() + (long)take);
+        admitted.erase(admitted.begin(), admitted.begin() + (long)take);
+      }
+      for (Request* r : ready) {
+        if (cudaEventQuery(r->ev_in) != cudaSuccess) cudaStreamWaitEvent(s_comp, r->ev_in, 0);
       }
       if (!ready.empty()) {
         // One batch per (format, channel count): a request is rendered by the
