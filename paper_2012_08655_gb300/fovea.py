@@ -511,10 +511,15 @@ def foveate_train(x: torch.Tensor, fix: torch.Tensor, sigma0: float = 0.5, k: fl
 
 # ------------------------------------------------------------------ serving
 class Server:
-    """Continuous-batching request loop (``fovea_server_*``)."""
+    """Continuous-batching request loop (``fovea_server_*``).
+
+    The host tensors of a request are held by this object from ``submit``
+    until ``wait`` reports the request done (or until ``close``), so the
+    library's copies never outlive them."""
 
     def __init__(self, device_budget_bytes: int = 1 << 30, max_batch: int = 64, block: int = 32,
                  max_inflight: int = 256):
+        self._held = {}
         cfg = ServerConfig(int(device_budget_bytes), int(max_batch), int(block), int(max_inflight))
         h = _vp()
         _check(_lib.fovea_server_create(ctypes.byref(cfg), ctypes.byref(h)), "fovea_server_create")
@@ -533,18 +538,23 @@ class Server:
         fr = Frame(w, h, c, fmt, inp.data_ptr(), out.data_ptr(), float(fix_x), float(fix_y), float(sigma0), float(k),
                    int(grid), None, 0.0)
         t = self.now_us() if arrival_us is None else float(arrival_us)
-        return _check(int(_lib.fovea_server_submit(self._h, ctypes.byref(fr), t)), "fovea_server_submit")
+        rid = _check(int(_lib.fovea_server_submit(self._h, ctypes.byref(fr), t)), "fovea_server_submit")
+        self._held[rid] = (inp, out)
+        return rid
 
     def wait(self, rid: int, timeout_ms: int = 10000) -> dict:
         t = RequestTimes()
         _check(_lib.fovea_server_wait(self._h, int(rid), int(timeout_ms), ctypes.byref(t)), "fovea_server_wait")
+        self._held.pop(int(rid), None)
         return {"arrival_us": t.arrival_us, "admit_us": t.admit_us, "start_us": t.start_us,
                 "done_us": t.done_us, "batch_size": t.batch_size, "status": t.status}
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
-            _lib.fovea_server_destroy(self._h)
+            _lib.fovea_server_destroy(self._h)  # finishes every admitted request first
             self._h = _vp()
+        if hasattr(self, "_held"):
+            self._held.clear()
 
     def __del__(self):
         try:

@@ -260,3 +260,26 @@ def test_server_admission_limits(fv):
             assert srv.wait(r, timeout_ms=20000)["status"] == 0
     ref = fv.foveate(small[3].cuda(), 100.0, 100.0, 0.5, 0.02).cpu()
     assert torch.equal(ref, outs[3])
+
+
+def test_server_holds_request_tensors_until_waited(fv):
+    """The binding keeps a request's host tensors alive from submit until wait
+    reports it done: a caller that drops its own references right after
+    submitting still gets the right result back through the held output."""
+    import gc
+    img = wl.grating_frame(720, 1280, 3, seed=41)
+    ref = fv.foveate(torch.from_numpy(img).cuda(), 400.0, 300.0, 0.5, 0.02).cpu()
+    with fv.Server(device_budget_bytes=64 << 20, max_batch=8) as srv:
+        rids = []
+        for _ in range(4):
+            inp = torch.from_numpy(img.copy()).pin_memory()
+            out = torch.empty_like(inp).pin_memory()
+            rids.append(srv.submit(inp, out, 400.0, 300.0, 0.5, 0.02))
+            del inp, out
+        gc.collect()
+        held = [srv._held[r][1] for r in rids]
+        for r in rids:
+            assert srv.wait(r, timeout_ms=20000)["status"] == 0
+        assert not srv._held
+    for out in held:
+        assert torch.equal(out, ref)
