@@ -30,6 +30,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "arena.h"
 #include "fovea.h"
 #include "fovea_host.h"
 
@@ -56,52 +57,13 @@ struct Request {
   cudaEvent_t ev_in = nullptr, ev_done = nullptr;
 };
 
-// First-fit allocator over a fixed device arena (offsets only).
-class Arena {
- public:
-  void reset(size_t size) {
-    free_.clear();
-    if (size) free_[0] = size;
-  }
-  bool alloc(size_t n, size_t* off) {
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second >= n) {
-        *off = it->first;
-        const size_t rest = it->second - n, start = it->first + n;
-        free_.erase(it);
-        if (rest) free_[start] = rest;
-        return true;
-      }
-    }
-    return false;
-  }
-  void release(size_t off, size_t n) {
-    auto it = free_.emplace(off, n).first;
-    auto nx = std::next(it);
-    if (nx != free_.end() && it->first + it->second == nx->first) {
-      it->second += nx->second;
-      free_.erase(nx);
-    }
-    if (it != free_.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second == it->first) {
-        pv->second += it->second;
-        free_.erase(it);
-      }
-    }
-  }
-
- private:
-  std::map<size_t, size_t> free_;
-};
-
 }  // namespace
 
 struct fovea_server {
   fovea_server_config cfg{};
   int device = 0;
   char* arena_base = nullptr;
-  Arena arena;
+  fovea::Arena arena;
   fovea_ctx* ctx = nullptr;
   cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
   std::vector<cudaEvent_t> event_pool;
