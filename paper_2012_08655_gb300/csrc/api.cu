@@ -948,6 +948,11 @@ int ctx_shape(const fovea_ctx* ctx, int* W, int* H, int* C, int* fmt, int* B) {
   return ctx->batch_only ? FOVEA_EINVAL : FOVEA_OK;
 }
 
+int ctx_centre_radius_bound(const fovea_ctx* ctx) {
+  if (ctx->batch_only || ctx->W <= 0 || ctx->H <= 0) return 0;
+  return radius_bound(ctx->W, ctx->H, ctx->B, 0.5f * (float)ctx->W, 0.5f * (float)ctx->H, ctx->law);
+}
+
 int ctx_device_info(const fovea_ctx* ctx, int* device, int* num_sms) {
   *device = ctx->device;
   *num_sms = ctx->num_sms;

@@ -30,6 +30,9 @@ int check_frame(int W, int H, int C, int fmt, int B, const FrameLaw& law, float 
 size_t frame_bytes(int W, int H, int C, int fmt);
 int ctx_shape(const fovea_ctx* ctx, int* W, int* H, int* C, int* fmt, int* B);
 int ctx_device_info(const fovea_ctx* ctx, int* device, int* num_sms);
+// Radius bound of a sized context with the fixation at the frame centre (the
+// autotuner's timing frame); 0 for a batch-only context.
+int ctx_centre_radius_bound(const fovea_ctx* ctx);
 // Bytes of one tensor map (CUtensorMap) and the alignment it needs.
 constexpr size_t kTensorMapBytes = 128;
 constexpr size_t kTensorMapAlign = 64;

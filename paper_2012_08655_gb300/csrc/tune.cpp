@@ -4,8 +4,10 @@
 // (1, 2, as many as fit). Each is timed with CUDA events on a synthetic frame
 // of the context's own shape (fixation at the centre), and the fastest is
 // kept in a process-wide cache keyed by device name, SM count, frame shape,
-// format, block side and radius bucket; the cache can be persisted as a small
-// JSON file (one entry per line).
+// format, block side and radius bucket (the radius bound at that fixation,
+// rounded up to a multiple of 64: contexts of one shape whose sigma laws
+// differ that much get their own choice); the cache can be persisted as a
+// small JSON file (one entry per line).
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -40,10 +42,9 @@ std::string make_key(const fovea_ctx* ctx) {
   std::string name = "unknown";
   if (cudaGetDeviceProperties(&p, dev) == cudaSuccess) name = p.name;
   else cudaGetLastError();
-  fovea_config cfg;
-  (void)cfg;
+  const int rbucket = (fovea::ctx_centre_radius_bound(ctx) + 63) / 64 * 64;
   std::ostringstream os;
-  os << name << "|" << sms << "|" << W << "x" << H << "x" << C << "|f" << fmt << "|b" << B;
+  os << name << "|" << sms << "|" << W << "x" << H << "x" << C << "|f" << fmt << "|b" << B << "|r" << rbucket;
   return os.str();
 }
 
