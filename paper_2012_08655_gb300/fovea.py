@@ -155,6 +155,32 @@ def _require_device_frame(t: torch.Tensor, name: str):
         raise ValueError(f"{name} must be contiguous")
 
 
+def _require_host_frame(t: torch.Tensor, name: str):
+    if t.is_cuda:
+        raise ValueError(f"{name} must be a host (preferably pinned) tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _require_frame_size(t: torch.Tensor, name: str, width: int, height: int, channels: int, fmt: int):
+    """The library reads and writes width x height x channels elements of the
+    format's type through the tensor's pointer: anything smaller would be
+    accessed out of bounds, so the dtype and element count must match."""
+    want = torch.uint8 if fmt == U8_HWC else torch.float32
+    if t.dtype != want:
+        raise TypeError(f"{name} is {t.dtype}, the frame format needs {want}")
+    n = int(width) * int(height) * int(channels)
+    if t.numel() != n:
+        raise ValueError(f"{name} holds {t.numel()} elements; the frame ({width}x{height}x{channels}) has {n}")
+
+
+def _require_like(t: torch.Tensor, ref: torch.Tensor, name: str):
+    """An output (or second operand) that matches the input frame's dtype and size."""
+    if t.dtype != ref.dtype or t.numel() != ref.numel():
+        raise ValueError(f"{name} ({t.dtype}, {t.numel()} elements) does not match the input "
+                         f"({ref.dtype}, {ref.numel()} elements)")
+
+
 class Context:
     """One fovea context (``fovea_create``): frame shape, format, block side,
     sigma law and grid mode.
@@ -207,9 +233,14 @@ class Context:
         self.close()
 
     # ---------------------------------------------------------------- calls
+    def _frames(self, pairs, device: bool = True, fmt: Optional[int] = None):
+        """Check (tensor, name) pairs against this context's frame."""
+        for t, name in pairs:
+            (_require_device_frame if device else _require_host_frame)(t, name)
+            _require_frame_size(t, name, self.width, self.height, self.channels, self.fmt if fmt is None else fmt)
+
     def render(self, inp: torch.Tensor, out: torch.Tensor, fix_x: float, fix_y: float, stream=None):
-        _require_device_frame(inp, "input")
-        _require_device_frame(out, "output")
+        self._frames([(inp, "input"), (out, "output")])
         _check(_lib.fovea_render(self._h, inp.data_ptr(), out.data_ptr(), float(fix_x), float(fix_y),
                                  _stream_handle(stream)), "fovea_render")
         return out
@@ -217,8 +248,7 @@ class Context:
     def render_pixelwise(self, inp: torch.Tensor, out: torch.Tensor, fix_x: float, fix_y: float, stream=None):
         """Per-pixel ("perfect") foveation of one device frame with this
         context's shape, format and law (``fovea_render_pixelwise``)."""
-        _require_device_frame(inp, "input")
-        _require_device_frame(out, "output")
+        self._frames([(inp, "input"), (out, "output")])
         _check(_lib.fovea_render_pixelwise(self._h, inp.data_ptr(), out.data_ptr(), float(fix_x), float(fix_y),
                                            _stream_handle(stream)), "fovea_render_pixelwise")
         return out
@@ -226,22 +256,19 @@ class Context:
     def render_pyramid(self, inp: torch.Tensor, out: torch.Tensor, fix_x: float, fix_y: float, stream=None):
         """Gaussian-pyramid (mipmap) foveation of one device frame with this
         context's shape, format and law (``fovea_render_pyramid``)."""
-        _require_device_frame(inp, "input")
-        _require_device_frame(out, "output")
+        self._frames([(inp, "input"), (out, "output")])
         _check(_lib.fovea_render_pyramid(self._h, inp.data_ptr(), out.data_ptr(), float(fix_x), float(fix_y),
                                          _stream_handle(stream)), "fovea_render_pyramid")
         return out
 
     def render_host(self, inp: torch.Tensor, out: torch.Tensor, fix_x: float, fix_y: float, stream=None):
-        if inp.is_cuda or out.is_cuda:
-            raise ValueError("render_host takes host (preferably pinned) tensors")
+        self._frames([(inp, "input"), (out, "output")], device=False)
         _check(_lib.fovea_render_host(self._h, inp.data_ptr(), out.data_ptr(), float(fix_x), float(fix_y),
                                       _stream_handle(stream)), "fovea_render_host")
         return out
 
     def backward(self, grad_out: torch.Tensor, grad_in: torch.Tensor, fix_x: float, fix_y: float, stream=None):
-        _require_device_frame(grad_out, "grad_out")
-        _require_device_frame(grad_in, "grad_in")
+        self._frames([(grad_out, "grad_out"), (grad_in, "grad_in")], fmt=F32_CHW)
         _check(_lib.fovea_backward(self._h, grad_out.data_ptr(), grad_in.data_ptr(), float(fix_x), float(fix_y),
                                    _stream_handle(stream)), "fovea_backward")
         return grad_in
@@ -321,6 +348,7 @@ def _frames_array(frames: Sequence[BatchFrame]):
     for i, fr in enumerate(frames):
         _require_device_frame(fr.inp, f"frame {i} input")
         _require_device_frame(fr.out, f"frame {i} output")
+        _require_like(fr.out, fr.inp, f"frame {i} output")
         fmt = _fmt_of(fr.inp)
         w, h, c = _shape_of(fr.inp, fmt)
         mp = fr.sigma_map.data_ptr() if fr.sigma_map is not None else None
@@ -415,6 +443,7 @@ def ssim(a: torch.Tensor, b: torch.Tensor, data_range: float = 0.0, want_map: bo
     ``want_map``) and the mean over the map as a Python float."""
     _require_device_frame(a, "a")
     _require_device_frame(b, "b")
+    _require_like(b, a, "b")
     if a.shape != b.shape or a.dtype != b.dtype:
         raise ValueError("SSIM needs two frames of one shape and dtype")
     fmt = _fmt_of(a)
@@ -434,6 +463,7 @@ def render_noalloc(x: torch.Tensor, out: torch.Tensor, fix_x: float, fix_y: floa
     fixed array inside the library; calls that overlap on the GPU race)."""
     _require_device_frame(x, "input")
     _require_device_frame(out, "output")
+    _require_like(out, x, "output")
     fmt = _fmt_of(x)
     w, h, c = _shape_of(x, fmt)
     _check(_lib.fovea_render_noalloc(x.data_ptr(), out.data_ptr(), w, h, c, fmt, int(block), float(sigma0),
@@ -531,8 +561,9 @@ class Server:
 
     def submit(self, inp: torch.Tensor, out: torch.Tensor, fix_x: float, fix_y: float, sigma0: float,
                k: float, arrival_us: Optional[float] = None, grid: int = GRID_ANCHORED) -> int:
-        if inp.is_cuda or out.is_cuda:
-            raise ValueError("the server takes host (preferably pinned) frames")
+        _require_host_frame(inp, "input")
+        _require_host_frame(out, "output")
+        _require_like(out, inp, "output")
         fmt = _fmt_of(inp)
         w, h, c = _shape_of(inp, fmt)
         fr = Frame(w, h, c, fmt, inp.data_ptr(), out.data_ptr(), float(fix_x), float(fix_y), float(sigma0), float(k),

@@ -1,0 +1,67 @@
+"""Argument checks of the Python binding, on the CPU: the library reads and
+writes as many elements as the frame has through the tensors' pointers, so
+the binding refuses tensors of the wrong dtype, size, device or layout before
+any library call."""
+import pytest
+import torch
+
+from paper_2012_08655_gb300 import fovea as fv
+
+
+def test_frame_size_check():
+    fv._require_frame_size(torch.zeros((10, 12, 3), dtype=torch.uint8), "x", 12, 10, 3, fv.U8_HWC)
+    fv._require_frame_size(torch.zeros((10, 12), dtype=torch.uint8), "x", 12, 10, 1, fv.U8_HWC)
+    fv._require_frame_size(torch.zeros((3, 10, 12), dtype=torch.float32), "x", 12, 10, 3, fv.F32_CHW)
+    fv._require_frame_size(torch.zeros((1, 10, 12), dtype=torch.float32), "x", 12, 10, 1, fv.F32_CHW)
+    with pytest.raises(ValueError):
+        fv._require_frame_size(torch.zeros((10, 11, 3), dtype=torch.uint8), "x", 12, 10, 3, fv.U8_HWC)
+    with pytest.raises(TypeError):
+        fv._require_frame_size(torch.zeros((10, 12, 3), dtype=torch.float32), "x", 12, 10, 3, fv.U8_HWC)
+    with pytest.raises(TypeError):
+        fv._require_frame_size(torch.zeros((3, 10, 12), dtype=torch.float64), "x", 12, 10, 3, fv.F32_CHW)
+
+
+def test_host_frame_and_like_checks():
+    a = torch.zeros((8, 6, 3), dtype=torch.uint8)
+    fv._require_host_frame(a, "a")
+    with pytest.raises(ValueError):
+        fv._require_host_frame(a.transpose(0, 1), "a")  # not contiguous
+    fv._require_like(torch.empty_like(a), a, "b")
+    with pytest.raises(ValueError):
+        fv._require_like(torch.zeros((8, 6, 2), dtype=torch.uint8), a, "b")
+    with pytest.raises(ValueError):
+        fv._require_like(torch.zeros((8, 6, 3), dtype=torch.float32), a, "b")
+    with pytest.raises(ValueError):
+        fv._require_device_frame(a, "a")  # a host tensor where a device one is needed
+
+
+def _bare(cls, **attrs):
+    obj = cls.__new__(cls)  # no library handle: every check below must fire first
+    for k, v in attrs.items():
+        setattr(obj, k, v)
+    return obj
+
+
+def test_context_refuses_mismatched_frames_before_the_library():
+    ctx = _bare(fv.Context, width=12, height=10, channels=3, fmt=fv.U8_HWC)
+    good = torch.zeros((10, 12, 3), dtype=torch.uint8)
+    ctx._frames([(good, "input"), (torch.empty_like(good), "output")], device=False)
+    with pytest.raises(ValueError):
+        ctx.render_host(good, torch.zeros((10, 12, 1), dtype=torch.uint8), 1.0, 1.0)
+    with pytest.raises(ValueError):
+        ctx.render_host(torch.zeros((9, 12, 3), dtype=torch.uint8), good, 1.0, 1.0)
+    with pytest.raises(ValueError):
+        ctx.render(good, torch.empty_like(good), 1.0, 1.0)  # host tensors for a device call
+    f32 = _bare(fv.Context, width=12, height=10, channels=3, fmt=fv.F32_CHW)
+    with pytest.raises(TypeError):
+        f32._frames([(good, "grad_out")], device=False, fmt=fv.F32_CHW)
+
+
+def test_server_refuses_mismatched_output_before_the_library():
+    srv = _bare(fv.Server, _held={})
+    inp = torch.zeros((10, 12, 3), dtype=torch.uint8)
+    with pytest.raises(ValueError):
+        srv.submit(inp, torch.zeros((10, 12), dtype=torch.uint8), 1.0, 1.0, 0.5, 0.02)
+    with pytest.raises(ValueError):
+        srv.submit(inp.transpose(0, 1), torch.empty_like(inp), 1.0, 1.0, 0.5, 0.02)
+    assert srv._held == {}
