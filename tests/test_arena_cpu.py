@@ -42,16 +42,18 @@ int main() {
 
 
 @pytest.fixture(scope="module")
-def driver(tmp_path_factory):
+def driver():
     gxx = shutil.which("g++")
     if gxx is None:
         pytest.skip("no C++ compiler")
-    d = tmp_path_factory.mktemp("arena")
-    src = d / "driver.cpp"
-    src.write_text(DRIVER)
-    exe = d / "driver"
-    subprocess.run([gxx, "-std=c++17", "-O1", "-I", CSRC, str(src), "-o", str(exe)], check=True)
-    return str(exe)
+    d = os.path.join(HERE, "_build", "arena")  # git-ignored build folder inside the tree
+    os.makedirs(d, exist_ok=True)
+    src = os.path.join(d, "driver.cpp")
+    with open(src, "w") as f:
+        f.write(DRIVER)
+    exe = os.path.join(d, "driver")
+    subprocess.run([gxx, "-std=c++17", "-O1", "-I", CSRC, src, "-o", exe], check=True)
+    return exe
 
 
 class FirstFit:
