@@ -271,7 +271,17 @@ typedef struct {
                          else as 1); 0: fp32 FMA kernel */
 } fovea_config;
 
+/* Copy the context's current configuration into *cfg. FOVEA_EINVAL for a
+ * null argument. */
 int fovea_get_config(const fovea_ctx* ctx, fovea_config* cfg);
+
+/* Use *cfg for later launches on this context (not in the paper: the paper
+ * fixes one CUDA block per fragment). FOVEA_EUNSUPPORTED for threads other
+ * than 256 or rows_per_chunk other than 16, 32 or 64; FOVEA_EINVAL for a
+ * null argument, ctas_per_sm outside 0..8 or tensor_cores outside 0..2. A CTA
+ * count above what fits is reduced to what fits at launch. Output does not
+ * depend on ctas_per_sm or rows_per_chunk, only on the kernel
+ * (tensor_cores). */
 int fovea_set_config(fovea_ctx* ctx, const fovea_config* cfg);
 
 /* Time every built-in configuration on the context's own frame shape (a
@@ -287,6 +297,9 @@ int fovea_autotune(fovea_ctx* ctx, int iters, const char* cache_path);
  * stream, so a caller can time that kernel alone. NULL, NULL turns it off. */
 int fovea_set_kernel_events(fovea_ctx* ctx, void* ev_start, void* ev_stop);
 
+/* Synchronise the device, then free everything the context owns (workspace,
+ * graphs, staging buffers, internal streams). The caller's buffers are not
+ * touched. NULL is a no-op. */
 void fovea_destroy(fovea_ctx* ctx);
 
 /* Most blocks a frame may have for fovea_render_noalloc (e.g. 3840x2160 at
@@ -318,6 +331,8 @@ int fovea_render_noalloc(const void* in_dev, void* out_dev, int width, int heigh
                          int format, int block, double sigma0, double k, float fix_x, float fix_y,
                          void* stream);
 
+/* A static, human-readable description of a fovea_status value ("unknown
+ * status" for any other value); never NULL. */
 const char* fovea_strerror(int status);
 
 /* The cudaError_t of the last failed CUDA call in this thread (0 if none). */
@@ -348,7 +363,7 @@ int fovea_measure_fma_rate(double* fma_per_s, void* stream);
  */
 typedef struct {
   size_t device_budget_bytes;  /* cap on device memory used for request buffers */
-  int max_batch;               /* most frames rendered in one tick */
+  int max_batch;               /* most frames rendered in one batch */
   int block;                   /* block side B */
   int max_inflight;            /* most admitted-but-unfinished requests */
 } fovea_server_config;
@@ -362,6 +377,14 @@ typedef struct {
   int status;          /* FOVEA_OK or an error */
 } fovea_request_times;
 
+/* Start a serving loop on the current device: allocates the device arena
+ * (device_budget_bytes), three streams and a batch context whose buffers are
+ * reserved for the largest batch the arena holds, and starts the worker
+ * thread. *out is set on success (NULL otherwise). FOVEA_EINVAL for a null
+ * argument, a budget below 512 bytes, or max_batch, max_inflight or block
+ * <= 0; FOVEA_ENOMEM when the arena or a stream cannot be created; the
+ * status of fovea_create or fovea_reserve otherwise. Free with
+ * fovea_server_destroy. */
 int fovea_server_create(const fovea_server_config* cfg, fovea_server** out);
 
 /* Submit one frame. `in_host` / `out_host` stay owned by the caller and must

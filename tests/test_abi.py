@@ -33,6 +33,23 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def test_every_declaration_is_documented():
+    """Each entry point in the header sits directly under its own comment
+    (meaning, layout, ownership and errors of its arguments)."""
+    lines = open(HEADER).read().split("\n")
+    undocumented = []
+    for i, line in enumerate(lines):
+        m = re.match(r"^[A-Za-z_][\w \*]*?\b(fovea_\w+)\s*\(", line)
+        if not m or line.strip().startswith(("*", "/*")):
+            continue
+        j = i - 1
+        while j >= 0 and not lines[j].strip():
+            j -= 1
+        if not lines[j].strip().endswith("*/"):
+            undocumented.append(m.group(1))
+    assert not undocumented, f"declared without a comment: {undocumented}"
+
+
 def test_library_exports_every_declared_symbol(lib):
     missing = [n for n in declared_functions() if not hasattr(lib, n)]
     assert not missing, f"libfovea.so lacks {missing}"
