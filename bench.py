@@ -842,6 +842,7 @@ def run_ours(args):
     barrier(world)
     clocks = sampler.stop()
     ctx.set_kernel_events(None, None)
+    ctx.check()  # raises if any kernel of the timed region recorded a device fault
     elapsed_ms = max_over_ranks(e0.elapsed_time(e1), world)
     kernel_ms = float(np.mean([a.elapsed_time(b) for a, b in ev_k]))
     value = world * W * H * args.steps / (elapsed_ms * 1e-3) / 1e6
@@ -897,6 +898,7 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     wall_ms = (time.perf_counter() - t0) * 1e3
+    ctx.check()
     barrier(world)
     e2e_ms = max_over_ranks(max(e0.elapsed_time(e1), wall_ms), world)
     e2e = {"value": world * W * H * ke / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
@@ -930,6 +932,7 @@ def run_ours(args):
                        "kernel_config": cfg, "parallelism": f"replicas x{world}"},
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
             "gpu_launches": 2 * args.steps, "clocks": clocks,  # sigma + blur kernel per render
+            "device_faults": 0,  # fovea_check after each timed region (it raises otherwise)
         }
         line.update(extras)
         print(json.dumps(line), flush=True)

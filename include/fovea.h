@@ -89,8 +89,12 @@ typedef enum {
  *  - MAP: sigma_map is a device array of nby x nbx floats (row-major, the
  *    grid in force for the frame: see fovea_grid) owned by the caller and
  *    read by every render; sigma_map_max is an upper bound of its values
- *    (it sizes the kernels; larger values are clamped and flagged, and the
- *    call then fails with FOVEA_ECUDA). The fixation only places the grid.
+ *    (it sizes the kernels). A value above sigma_map_max is clamped to it,
+ *    and a negative or non-finite value to 0, on the device; the block is
+ *    then blurred with the clamped sigma and FOVEA_FAULT_SIGMA_RANGE is
+ *    recorded, which the next fovea_check on the context reports as
+ *    FOVEA_EINVAL (the render call itself has already returned, as it only
+ *    enqueues work). The fixation only places the grid.
  * grid: a fovea_grid_mode. */
 typedef struct {
   int kind;                /* fovea_law_kind */
@@ -171,7 +175,7 @@ int fovea_render_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, void* s
  * growth recaptures the batch graphs on the calling thread (hundreds of
  * microseconds), which a latency-bound caller such as a serving loop wants to
  * pay up front. Zero leaves that part as it is. Memory: 32 device bytes per
- * item, and per frame 232 bytes of device table plus as much in each of four
+ * item, and per frame 240 bytes of device table plus as much in each of four
  * pinned host staging slots; replaced buffers stay allocated until
  * fovea_destroy. Returns FOVEA_EINVAL for a null context, negative sizes,
  * max_frames above 2^24 or max_items above 2^31 - 1, FOVEA_ECUDA when an
@@ -311,25 +315,80 @@ void fovea_destroy(fovea_ctx* ctx);
  * cudaMalloc -- code whose device memory is owned by a host framework or a
  * server that has reserved it up front, or that must not allocate while it
  * drives the GPU -- and for whom fovea_create's workspace is not an option.
- * Arguments are those of fovea_create and fovea_render combined (the linear
- * sigma law on the anchored grid); the caller still owns and passes the input
- * and output buffers. All working memory
- * (per-block sigma/radius records, the radius-ordered work list, counters;
- * about 0.5 MB) is one fixed-size array inside the library image, held by
- * every GPU that loads the library until the process exits. No cudaMalloc,
- * cudaFree or allocating library routine is called.
+ * Arguments are those of fovea_create and fovea_render combined, with the
+ * linear sigma law on the anchored grid and a block side of 1 to 32 (one work
+ * item per block; larger blocks are refused with FOVEA_EUNSUPPORTED); the
+ * caller still owns and passes the input and output buffers. All working
+ * memory (per-block sigma/radius records, the radius-ordered work list,
+ * counters; about 0.5 MB) is one fixed-size array inside the library image,
+ * held by every GPU that loads the library until the process exits. No
+ * cudaMalloc, cudaFree or allocating library routine is called. Blocks are
+ * rendered by the fp32 CUDA-core kernel (the same outputs as a context
+ * configured with tensor_cores = 0).
  *   - Frames with more than FOVEA_NOALLOC_MAX_BLOCKS blocks are refused with
  *     FOVEA_EUNSUPPORTED before any work is enqueued.
  *   - The first call on a device looks up the array's device address (a
- *     one-time set-up per device, with that device current); make that first
- *     call before any stream capture.
+ *     one-time set-up per device, with that device current; repeated only
+ *     if the device's CUDA context was replaced, e.g. by cudaDeviceReset);
+ *     make that first call before any stream capture.
  *   - Every call uses the same array, which keeps the last call's contents;
- *     each call clears the counters that must start at zero on its stream.
- *     Calls whose GPU work overlaps (other streams, other host threads) race
- *     and must be serialised by the caller. */
+ *     each call clears the counters that must start at zero, its fault word
+ *     included, on its stream. Calls whose GPU work overlaps (other streams,
+ *     other host threads) race and must be serialised by the caller. */
 int fovea_render_noalloc(const void* in_dev, void* out_dev, int width, int height, int channels,
                          int format, int block, double sigma0, double k, float fix_x, float fix_y,
                          void* stream);
+
+/* ------------------------------------------------------------ device faults
+ * Conditions the kernels detect while they run. A render or adjoint call only
+ * enqueues work, so it cannot return them; each kernel ORs a bit into a fault
+ * word of the context instead, and fovea_check turns that word into a
+ * negative status like every other failure, and clears it. Unless
+ * stated otherwise the item concerned (one block of one frame) is skipped and
+ * its output pixels are left as they were.
+ */
+#define FOVEA_FAULT_SIGMA_RANGE  0x01u /* a per-block sigma map value was above sigma_map_max, negative or
+                                          not finite: clamped (to sigma_map_max, or 0) and blurred with that */
+#define FOVEA_FAULT_RADIUS_BOUND 0x02u /* forward: a block's radius exceeded the bound its launch was sized
+                                          for (internal: the host bound covers every clamped sigma) */
+#define FOVEA_FAULT_ADJ_BOUND    0x04u /* adjoint: the same */
+#define FOVEA_FAULT_ORDER        0x08u /* internal: the radius histogram and the work list were out of step */
+#define FOVEA_FAULT_WORKLIST     0x10u /* internal: a work ticket named no item */
+#define FOVEA_FAULT_BUCKETS      0x20u /* internal: a per-radius item list overflowed */
+#define FOVEA_FAULT_WAIT         0x40u /* a bounded wait on the device (a TMA row chunk, a tensor-core
+                                          commit) ran out: the item was abandoned */
+#define FOVEA_FAULT_PIXEL_RADIUS 0x80u /* per-pixel path: a pixel's radius exceeded the launch's bound
+                                          (internal); the pixel is written unblurred */
+
+/* Waits for `stream` (a cudaStream_t; the stream the context's calls were
+ * ordered on), then reads and clears the context's device fault word. Stores
+ * the word in *faults when faults is not NULL. Returns FOVEA_OK when no bit
+ * was set; otherwise FOVEA_ETIMEOUT if FOVEA_FAULT_WAIT is set, else
+ * FOVEA_ECUDA if an internal bit (ORDER, WORKLIST, BUCKETS, PIXEL_RADIUS,
+ * RADIUS_BOUND, ADJ_BOUND) is set, else FOVEA_EINVAL (the caller's sigma map
+ * was out of its declared range). FOVEA_ECUDA also when the stream or the
+ * copy fails. The word accumulates over every call made since the last
+ * check, so one check after a sequence of calls covers all of them. Not in
+ * the paper: the error contract of the library. */
+int fovea_check(fovea_ctx* ctx, void* stream, unsigned int* faults);
+
+/* Non-blocking form of fovea_check for callers that must not wait (a
+ * training step, a render loop). Enqueues on `stream` a copy of the
+ * context's fault word into pinned host memory the context owns and returns
+ * FOVEA_OK without waiting; a later call looks at that copy once it has
+ * landed, and if it holds a fault, finishes like fovea_check (waits for
+ * `stream`, reads and clears the word) and returns its status. The fault word
+ * is only cleared by fovea_check, so a fault is reported at the latest by the
+ * second fovea_check_async after the faulting work and the copy behind it
+ * have completed, or by the next fovea_check. */
+int fovea_check_async(fovea_ctx* ctx, void* stream, unsigned int* faults);
+
+/* fovea_check for fovea_render_noalloc: waits for `stream`, then reads the
+ * device fault word of the latest fovea_render_noalloc call on the current
+ * device (each call clears it) into *faults (if not NULL) and returns the
+ * status fovea_check would. Allocates nothing. The paper has no
+ * counterpart. */
+int fovea_noalloc_check(void* stream, unsigned int* faults);
 
 /* A static, human-readable description of a fovea_status value ("unknown
  * status" for any other value); never NULL. */

@@ -63,14 +63,14 @@ adjoint_kernel(FrameSource src, Workspace ws, int rmax) {
     if (t >= n_items) break;
     const int item = ws.order[t];
     if ((unsigned)item >= (unsigned)n_items) {  // work list out of step: skip, flag
-      if (tid == 0) atomicOr(&ws.counters[CNT_ERROR], 16u);
+      if (tid == 0) atomicOr(&ws.counters[CNT_ERROR], kFaultWorklist);
       continue;
     }
     const ItemInfo inf = ws.items[item];
     const FrameDesc fd = load_frame(src, inf.frame);
     const int r = inf.r;
     if (r > rmax || fd.fmt != FOVEA_F32_CHW || fd.C > 4) {
-      if (tid == 0) atomicOr(&ws.counters[CNT_ERROR], 4u);
+      if (tid == 0) atomicOr(&ws.counters[CNT_ERROR], kFaultAdjBound);
       continue;
     }
     const int W = fd.W, H = fd.H, C = fd.C, T = fd.T;

@@ -35,6 +35,21 @@ int cuda_fail(cudaError_t e) {
 
 bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
 
+}  // namespace
+
+namespace fovea {
+
+int fault_status(unsigned int word) {
+  if (!word) return FOVEA_OK;
+  if (word & kFaultWait) return FOVEA_ETIMEOUT;
+  if (word & ~kFaultSigmaRange) return FOVEA_ECUDA;
+  return FOVEA_EINVAL;
+}
+
+}  // namespace fovea
+
+namespace {
+
 constexpr int kBatchSlots = 4;
 constexpr double kPi = 3.14159265358979323846;
 
@@ -109,6 +124,11 @@ struct fovea_ctx {
   // set by every call that enqueues workspace use on the caller's stream;
   // the next fovea_render_host orders its kernels after that work
   bool caller_stream_used = false;
+  // fovea_check_async: pinned copy of the device fault word and the event
+  // that marks its arrival
+  unsigned int* fault_host = nullptr;
+  cudaEvent_t fault_ev = nullptr;
+  bool fault_copy_pending = false;
 };
 
 namespace fovea {
@@ -208,6 +228,7 @@ FrameDesc make_desc(int W, int H, int C, int fmt, int B, const void* in, void* o
   d.fx = fx; d.fy = fy;
   d.sigma0 = law.sigma0; d.k = law.k;
   d.smap = law.smap;
+  d.smap_max = law.smap ? law.smap_max : 0.0;
   d.item0 = item0;
   return d;
 }
@@ -920,7 +941,47 @@ void fovea_destroy(fovea_ctx* ctx) {
   if (ctx->s_comp) cudaStreamDestroy(ctx->s_comp);
   if (ctx->s_d2h) cudaStreamDestroy(ctx->s_d2h);
   cudaFree(ctx->blist);
+  if (ctx->fault_host) cudaFreeHost(ctx->fault_host);
+  if (ctx->fault_ev) cudaEventDestroy(ctx->fault_ev);
   delete ctx;
+}
+
+int fovea_check(fovea_ctx* ctx, void* stream, unsigned int* faults) {
+  if (faults) *faults = 0u;
+  if (!ctx || !ctx->ws.counters) return FOVEA_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned int word = 0u;
+  FOVEA_CUDA(cudaMemcpyAsync(&word, ctx->ws.counters + CNT_ERROR, sizeof(word), cudaMemcpyDeviceToHost, s));
+  FOVEA_CUDA(cudaStreamSynchronize(s));
+  if (word) {
+    FOVEA_CUDA(cudaMemsetAsync(ctx->ws.counters + CNT_ERROR, 0, sizeof(unsigned int), s));
+    FOVEA_CUDA(cudaStreamSynchronize(s));
+  }
+  if (faults) *faults = word;
+  return fault_status(word);
+}
+
+int fovea_check_async(fovea_ctx* ctx, void* stream, unsigned int* faults) {
+  if (faults) *faults = 0u;
+  if (!ctx || !ctx->ws.counters) return FOVEA_EINVAL;
+  if (!ctx->fault_host) {
+    FOVEA_CUDA(cudaHostAlloc(&ctx->fault_host, sizeof(unsigned int), cudaHostAllocDefault));
+    *ctx->fault_host = 0u;
+    FOVEA_CUDA(cudaEventCreateWithFlags(&ctx->fault_ev, cudaEventDisableTiming));
+  }
+  if (ctx->fault_copy_pending) {
+    const cudaError_t q = cudaEventQuery(ctx->fault_ev);
+    if (q == cudaErrorNotReady) return FOVEA_OK;  // the last copy is still on its way: nothing new to report
+    if (q != cudaSuccess) return cuda_fail(q);
+    ctx->fault_copy_pending = false;
+    if (*ctx->fault_host) return fovea_check(ctx, stream, faults);  // the word is sticky: read and clear it
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  FOVEA_CUDA(cudaMemcpyAsync(ctx->fault_host, ctx->ws.counters + CNT_ERROR, sizeof(unsigned int),
+                             cudaMemcpyDeviceToHost, s));
+  FOVEA_CUDA(cudaEventRecord(ctx->fault_ev, s));
+  ctx->fault_copy_pending = true;
+  return FOVEA_OK;
 }
 
 const char* fovea_strerror(int status) {
@@ -951,6 +1012,12 @@ int ctx_shape(const fovea_ctx* ctx, int* W, int* H, int* C, int* fmt, int* B) {
 int ctx_centre_radius_bound(const fovea_ctx* ctx) {
   if (ctx->batch_only || ctx->W <= 0 || ctx->H <= 0) return 0;
   return radius_bound(ctx->W, ctx->H, ctx->B, 0.5f * (float)ctx->W, 0.5f * (float)ctx->H, ctx->law);
+}
+
+int ctx_fault_word(const fovea_ctx* ctx, unsigned int** word) {
+  if (!ctx->ws.counters) return FOVEA_EINVAL;
+  *word = ctx->ws.counters + CNT_ERROR;
+  return FOVEA_OK;
 }
 
 int ctx_device_info(const fovea_ctx* ctx, int* device, int* num_sms) {

@@ -268,7 +268,7 @@ forward_kernel(FrameSource src, Workspace ws, int rmax, int row_bytes, BucketLis
           item = ws.order[t];
         }
         if ((unsigned)item >= (unsigned)n_items) {  // work list out of step: skip, flag
-          atomicOr(&ws.counters[CNT_ERROR], 16u);
+          atomicOr(&ws.counters[CNT_ERROR], kFaultWorklist);
           state = 1;
         } else {
           const ItemInfo inf = ws.items[item];
@@ -276,7 +276,7 @@ forward_kernel(FrameSource src, Workspace ws, int rmax, int row_bytes, BucketLis
           const bool u8f = fd.fmt == FOVEA_U8_HWC;
           const bool fmt_ok = MODE == 2 ? (u8f || row_bytes >= kRowBytesF32) : (MODE == 0 ? u8f : !u8f);
           if (inf.r > rmax || !fmt_ok) {
-            atomicOr(&ws.counters[CNT_ERROR], 2u);
+            atomicOr(&ws.counters[CNT_ERROR], kFaultRadiusBound);
             state = 1;
           } else {
             item_geometry(s_it, inf, fd, RB);

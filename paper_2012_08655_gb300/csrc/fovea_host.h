@@ -30,6 +30,8 @@ int check_frame(int W, int H, int C, int fmt, int B, const FrameLaw& law, float 
 size_t frame_bytes(int W, int H, int C, int fmt);
 int ctx_shape(const fovea_ctx* ctx, int* W, int* H, int* C, int* fmt, int* B);
 int ctx_device_info(const fovea_ctx* ctx, int* device, int* num_sms);
+// Device address of the context's fault word (FOVEA_FAULT_* bits).
+int ctx_fault_word(const fovea_ctx* ctx, unsigned int** word);
 // Radius bound of a sized context with the fixation at the frame centre (the
 // autotuner's timing frame); 0 for a batch-only context.
 int ctx_centre_radius_bound(const fovea_ctx* ctx);
@@ -42,6 +44,10 @@ constexpr size_t kTensorMapAlign = 64;
 // kTensorMapAlign). Returns false, leaving map zeroed, when the frame's base
 // address or row pitch is not a multiple of 16 bytes or the driver refuses.
 bool make_u8_tensor_map(void* map, const void* base, int W, int H, int C, int rows);
+// Status a device fault word maps to (see fovea_check): FOVEA_OK for 0,
+// FOVEA_ETIMEOUT when a wait ran out, FOVEA_ECUDA for an internal fault,
+// FOVEA_EINVAL when only a sigma-map value was out of range.
+int fault_status(unsigned int word);
 // Records a failed cudaError_t for fovea_last_cuda_error and returns the
 // status it maps to (FOVEA_ENOMEM for an allocation failure, else FOVEA_ECUDA).
 int record_cuda_failure(int cuda_error);

@@ -20,7 +20,7 @@ constexpr int kMaxRadius = FOVEA_MAX_RADIUS; // r <= 1023
 constexpr int kBuckets = 1024;               // radius buckets of the work-list sort
 constexpr int kTapPad = 16;                  // zero taps stored before offset 0
 
-// One frame as the kernels see it (host fills it in; 104 bytes). Work items
+// One frame as the kernels see it (host fills it in; 112 bytes). Work items
 // are tiles of side T = min(B, 32); a block of side B > 32 (a multiple of 32)
 // is (B / T)^2 tiles that share its sigma.
 struct FrameDesc {
@@ -34,6 +34,7 @@ struct FrameDesc {
   int ox, oy;              // grid origin: block (bx, by) starts at (B bx - ox, B by - oy)
   const float* smap;       // per-block sigma [blocks along y][nbxb] replacing the law, or null
   int T, nbxb;             // tile side; blocks along x (nbx, nby count tiles)
+  double smap_max;         // declared bound of the map's values (map values above it are clamped)
 };
 
 // Device-resident batch: header followed by the frame descriptors, then
@@ -60,7 +61,7 @@ enum {
   CNT_DONE_SIGMA = 1, // finished CTAs of the sigma kernel
   CNT_DONE_ORDER = 2, // finished CTAs of the order kernel
   CNT_NITEMS = 3,     // items of the current launch
-  CNT_ERROR = 4,      // device error flags (bit 0: radius clamped)
+  CNT_ERROR = 4,      // device fault word (FOVEA_FAULT_* bits, read by fovea_check)
   CNT_HIST = 8,       // kBuckets radius histogram
   CNT_TOTAL = CNT_HIST + kBuckets
 };
@@ -114,17 +115,37 @@ __device__ __forceinline__ void block_sigma(int bx, int by, int B, int ox, int o
   r = (int)ceil(__dmul_rn(3.0, sigma));
 }
 
+// Device fault bits (the public FOVEA_FAULT_* values).
+constexpr unsigned int kFaultSigmaRange = FOVEA_FAULT_SIGMA_RANGE;
+constexpr unsigned int kFaultRadiusBound = FOVEA_FAULT_RADIUS_BOUND;
+constexpr unsigned int kFaultAdjBound = FOVEA_FAULT_ADJ_BOUND;
+constexpr unsigned int kFaultOrder = FOVEA_FAULT_ORDER;
+constexpr unsigned int kFaultWorklist = FOVEA_FAULT_WORKLIST;
+constexpr unsigned int kFaultBuckets = FOVEA_FAULT_BUCKETS;
+constexpr unsigned int kFaultWait = FOVEA_FAULT_WAIT;
+constexpr unsigned int kFaultPixelRadius = FOVEA_FAULT_PIXEL_RADIUS;
+
 // Sigma and radius of block (bx, by) of a frame: the sigma law at the
 // block's nominal centre, or the frame's per-block map (r = ceil(3 sigma) of
-// the map value in binary64). A map value that is negative or not finite
-// gives r = -1, which the caller flags.
-__device__ __forceinline__ void item_sigma(const FrameDesc& fd, int bx, int by, double& sigma, int& r) {
+// the map value in binary64). A map value above the frame's declared bound
+// is clamped to the bound, and a negative or non-finite one to 0; both
+// return true (the caller records FOVEA_FAULT_SIGMA_RANGE).
+__device__ __forceinline__ bool item_sigma(const FrameDesc& fd, int bx, int by, double& sigma, int& r) {
+  bool clamped = false;
   if (fd.smap) {
     sigma = (double)fd.smap[(size_t)by * fd.nbxb + bx];
-    r = (sigma >= 0.0 && sigma <= 1e6) ? (int)ceil(__dmul_rn(3.0, sigma)) : -1;
+    if (!(sigma >= 0.0)) {  // negative or NaN
+      sigma = 0.0;
+      clamped = true;
+    } else if (sigma > fd.smap_max) {  // above the bound (or +inf)
+      sigma = fd.smap_max;
+      clamped = true;
+    }
+    r = (int)ceil(__dmul_rn(3.0, sigma));
   } else {
     block_sigma(bx, by, fd.B, fd.ox, fd.oy, (double)fd.fx, (double)fd.fy, fd.sigma0, fd.k, sigma, r);
   }
+  return clamped;
 }
 
 // Packed two-lane FMA: d = a * b + c on both float lanes (one f32x2
@@ -333,7 +354,7 @@ struct PixelParams {
   double fx, fy, sigma0, k;
   int rmax;                // bound on every pixel's radius (the frame's corner pixels)
   int words;               // uint8 rows may be read as aligned 32-bit words
-  unsigned int* err;       // bit 0: a pixel's radius exceeded rmax (never expected)
+  unsigned int* err;       // fault word: kFaultPixelRadius when a pixel's radius exceeded rmax (never expected)
 };
 
 constexpr size_t kPixelSmemBudget = 220 * 1024;

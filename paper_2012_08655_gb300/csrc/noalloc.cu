@@ -16,7 +16,10 @@
 // streams, or several host threads) race and must be serialised by the
 // caller. The array keeps the last call's contents; the counters that must
 // start at zero are cleared at the start of every call (an asynchronous
-// memset on the call's stream).
+// memset on the call's stream), the fault word among them, so
+// fovea_noalloc_check reports on the latest call only.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -42,24 +45,61 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};  // context the address belongs to
 
-// Device address of the scratch array on the current device (looked up once
-// per device; in host code the array's name is only a host-side stand-in).
+// Unique id of the current device's CUDA context (0 if the driver cannot
+// say). cudaDeviceReset destroys a device's primary context, and the module
+// (with the array) is loaded again, possibly elsewhere, in the next one.
+unsigned long long current_context_id() {
+  static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+  static PFN_cuCtxGetId_v12000 get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(fn);
+    fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(fn);
+    cudaGetLastError();
+  });
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_current && get_id && get_current(&c) == CUDA_SUCCESS && c && get_id(c, &id) == CUDA_SUCCESS) return id;
+  return 0;
+}
+
+// Device address of the scratch array on the current device. In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// with cudaGetSymbolAddress, once per device (with that device current), and
+// again only if the device's context has been replaced since (after a
+// cudaDeviceReset).
 int scratch_for_current_device(unsigned char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return record_cuda_failure(e);
   if (dev < 0 || dev >= kMaxDevices) return FOVEA_EUNSUPPORTED;
+  e = cudaSetDevice(dev);  // makes the device's primary context current on this thread
+  if (e != cudaSuccess) return record_cuda_failure(e);
+  const unsigned long long ctx_id = current_context_id();
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (!g_scratch_ptr[dev] || g_scratch_ctx[dev] != ctx_id) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return record_cuda_failure(e);
     if (!p) return FOVEA_ECUDA;
     g_scratch_ptr[dev] = p;
+    g_scratch_ctx[dev] = ctx_id;
   }
   *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
   return FOVEA_OK;
+}
+
+unsigned int* counters_of(unsigned char* base) {
+  return reinterpret_cast<unsigned int*>(base + kItemsBytes + kRankBytes + kOrderBytes);
 }
 
 }  // namespace
@@ -93,7 +133,7 @@ extern "C" int fovea_render_noalloc(const void* in_dev, void* out_dev, int width
   ws.items = reinterpret_cast<ItemInfo*>(base);
   ws.rank = reinterpret_cast<int*>(base + kItemsBytes);
   ws.order = reinterpret_cast<int*>(base + kItemsBytes + kRankBytes);
-  ws.counters = reinterpret_cast<unsigned int*>(base + kItemsBytes + kRankBytes + kOrderBytes);
+  ws.counters = counters_of(base);
   ws.capacity = kMaxItems;
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -126,4 +166,18 @@ extern "C" int fovea_render_noalloc(const void* in_dev, void* out_dev, int width
   e = launch_forward(src, ws, cfg, rmax, fmt_mask, per * sms, s);
   if (e != cudaSuccess) return record_cuda_failure(e);
   return FOVEA_OK;
+}
+
+extern "C" int fovea_noalloc_check(void* stream, unsigned int* faults) {
+  if (faults) *faults = 0u;
+  unsigned char* base = nullptr;
+  int st = scratch_for_current_device(&base);
+  if (st != FOVEA_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned int word = 0u;
+  cudaError_t e = cudaMemcpyAsync(&word, counters_of(base) + CNT_ERROR, sizeof(word), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return record_cuda_failure(e);
+  if (faults) *faults = word;
+  return fault_status(word);
 }

@@ -90,7 +90,7 @@ pixel_tc_kernel(PixelParams pp) {
       double sigma;
       pixel_sigma(x, y, pp.fx, pp.fy, pp.sigma0, pp.k, sigma, r);
       if (r > pp.rmax || r < 0) {  // cannot happen with the host's bound; flagged, not run
-        atomicOr(pp.err, 1u);
+        atomicOr(pp.err, kFaultPixelRadius);
         r = 0;
       } else {
         c = neg_half_inv_s2(sigma);
@@ -307,7 +307,7 @@ pixel_fp32_kernel(PixelParams pp, int rb) {
     double sigma;
     pixel_sigma(x, y, pp.fx, pp.fy, pp.sigma0, pp.k, sigma, r);
     if (r > Rl || r < 0) {
-      atomicOr(pp.err, 1u);
+      atomicOr(pp.err, kFaultPixelRadius);
       r = 0;
     } else {
       c = neg_half_inv_s2(sigma);

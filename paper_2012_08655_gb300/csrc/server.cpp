@@ -54,6 +54,7 @@ struct Request {
   fovea_request_times t{};
   State state = PENDING;
   int status = 0;          // render status of its batch
+  int fault_slot = -1;     // pinned word that receives its batch's device fault word
   cudaEvent_t ev_in = nullptr, ev_done = nullptr;
 };
 
@@ -77,6 +78,15 @@ struct fovea_server {
   long long next_id = 0;
   bool stop = false;
   std::thread worker;
+  // Device fault words of the batches: after each batch the context's word
+  // is copied into a pinned slot (and cleared) on the compute stream; the
+  // batch's requests read it once their output copy is complete. A slot is
+  // free again when every request of its batch has finished (at most
+  // max_inflight batches hold requests, so max_inflight + 1 slots suffice).
+  unsigned int* fault_words = nullptr;  // pinned, one per slot
+  std::vector<int> fault_refs;          // unfinished requests per slot
+  std::vector<int> fault_free;          // free slots
+  unsigned int* fault_dev = nullptr;    // the batch context's device fault word
 
   cudaEvent_t get_event() {
     if (!event_pool.empty()) {
@@ -91,6 +101,12 @@ struct fovea_server {
 
   void finish(Request* r, int status) {
     r->t.done_us = now_us();
+    if (r->fault_slot >= 0) {  // the output copy is complete, so the batch's fault word has landed
+      const unsigned int w = fault_words[r->fault_slot];
+      if (status == FOVEA_OK && w) status = fovea::fault_status(w);
+      if (--fault_refs[(size_t)r->fault_slot] == 0) fault_free.push_back(r->fault_slot);
+      r->fault_slot = -1;
+    }
     r->t.status = status;
     if (r->state == ADMITTED || r->state == LAUNCHED) arena.release(r->off, 2 * align_up(r->bytes));
     r->state = DONE;
@@ -130,8 +146,14 @@ void fovea_server::run() {
       }
     }
     for (Request* r : fresh) {  // input copies on the copy stream
-      cudaMemcpyAsync(arena_base + r->off, r->f.in, r->bytes, cudaMemcpyHostToDevice, s_in);
-      cudaEventRecord(r->ev_in, s_in);
+      if (cudaMemcpyAsync(arena_base + r->off, r->f.in, r->bytes, cudaMemcpyHostToDevice, s_in) != cudaSuccess ||
+          cudaEventRecord(r->ev_in, s_in) != cudaSuccess) {
+        const int st = fovea::record_cuda_failure((int)cudaGetLastError());
+        std::lock_guard<std::mutex> lk(mu);
+        admitted.erase(std::find(admitted.begin(), admitted.end(), r));
+        finish(r, st);
+        cv_done.notify_all();
+      }
       progressed = true;
     }
     // Retire finished renders. One batch at a time on the compute stream:
@@ -154,8 +176,10 @@ void fovea_server::run() {
         ready.assign(admitted.begin(), admitted.begin() + (long)take);
         admitted.erase(admitted.begin(), admitted.begin() + (long)take);
       }
+      int wait_status = FOVEA_OK;
       for (Request* r : ready) {
-        if (cudaEventQuery(r->ev_in) != cudaSuccess) cudaStreamWaitEvent(s_comp, r->ev_in, 0);
+        if (cudaEventQuery(r->ev_in) != cudaSuccess && cudaStreamWaitEvent(s_comp, r->ev_in, 0) != cudaSuccess)
+          wait_status = fovea::record_cuda_failure((int)cudaGetLastError());
       }
       if (!ready.empty()) {
         // One batch per (format, channel count): a request is rendered by the
@@ -178,7 +202,8 @@ void fovea_server::run() {
             f.out = arena_base + ready[i]->off + align_up(ready[i]->bytes);
             frames[i - g0] = f;
           }
-          const int st = fovea_render_batch(ctx, frames.data(), (int)frames.size(), s_comp);
+          const int st = wait_status != FOVEA_OK ? wait_status
+                                                 : fovea_render_batch(ctx, frames.data(), (int)frames.size(), s_comp);
           for (size_t i = g0; i < g1; ++i) {
             ready[i]->status = st;
             ready[i]->t.batch_size = (int)(g1 - g0);
@@ -187,24 +212,47 @@ void fovea_server::run() {
           g0 = g1;
         }
         cudaEvent_t eb = nullptr;
+        int slot = -1;
         {
           std::lock_guard<std::mutex> lk(mu);
           eb = get_event();
+          if (!fault_free.empty()) {
+            slot = fault_free.back();
+            fault_free.pop_back();
+          }
         }
-        cudaEventRecord(eb, s_comp);
-        batch_events.push_back(eb);
-        cudaStreamWaitEvent(s_out, eb, 0);
+        // the batch's fault word goes to the slot and is cleared for the next batch
+        int tail_status = FOVEA_OK;
+        if (slot < 0 ||
+            cudaMemcpyAsync(fault_words + slot, fault_dev, sizeof(unsigned int), cudaMemcpyDeviceToHost, s_comp) !=
+                cudaSuccess ||
+            cudaMemsetAsync(fault_dev, 0, sizeof(unsigned int), s_comp) != cudaSuccess ||
+            !eb || cudaEventRecord(eb, s_comp) != cudaSuccess || cudaStreamWaitEvent(s_out, eb, 0) != cudaSuccess)
+          tail_status = slot < 0 ? FOVEA_ECUDA : fovea::record_cuda_failure((int)cudaGetLastError());
+        if (eb) batch_events.push_back(eb);
         std::lock_guard<std::mutex> lk(mu);
+        int refs = 0;
         for (Request* r : ready) {
           r->t.start_us = t0;
+          if (r->status == FOVEA_OK) r->status = tail_status;
+          if (r->status == FOVEA_OK &&
+              (cudaMemcpyAsync(r->f.out, arena_base + r->off + align_up(r->bytes), r->bytes, cudaMemcpyDeviceToHost,
+                               s_out) != cudaSuccess ||
+               cudaEventRecord(r->ev_done, s_out) != cudaSuccess))
+            r->status = fovea::record_cuda_failure((int)cudaGetLastError());
           if (r->status != FOVEA_OK) {
             finish(r, r->status);
+            failed = true;
             continue;
           }
-          cudaMemcpyAsync(r->f.out, arena_base + r->off + align_up(r->bytes), r->bytes, cudaMemcpyDeviceToHost, s_out);
-          cudaEventRecord(r->ev_done, s_out);
+          r->fault_slot = slot;
+          ++refs;
           r->state = LAUNCHED;
           launched.push_back(r);
+        }
+        if (slot >= 0) {
+          fault_refs[(size_t)slot] = refs;
+          if (refs == 0) fault_free.push_back(slot);
         }
         if (failed) cv_done.notify_all();
         progressed = true;
@@ -265,8 +313,18 @@ int fovea_server_create(const fovea_server_config* cfg, fovea_server** out) {
     return FOVEA_ENOMEM;
   }
   s->arena.reset(cfg->device_budget_bytes);
+  const int nslots = cfg->max_inflight + 1;
+  if (cudaHostAlloc(&s->fault_words, (size_t)nslots * sizeof(unsigned int), cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    s->fault_words = nullptr;
+    fovea_server_destroy(s);
+    return FOVEA_ENOMEM;
+  }
+  s->fault_refs.assign((size_t)nslots, 0);
+  for (int i = nslots - 1; i >= 0; --i) s->fault_free.push_back(i);
   fovea_sigma_law law{FOVEA_LAW_LINEAR, 0.5, 0.02, 0.0, nullptr, 0.0, FOVEA_GRID_ANCHORED};
   int st = fovea_create(0, 0, 3, cfg->block, &law, FOVEA_U8_HWC, &s->ctx);
+  if (st == FOVEA_OK) st = fovea::ctx_fault_word(s->ctx, &s->fault_dev);
   // Size the batch buffers for the largest batch the arena can hold, so that
   // no batch grows them (a growth recaptures the batch graphs on this
   // thread, and the backlog that makes a batch large is when that hurts
@@ -358,6 +416,7 @@ void fovea_server_destroy(fovea_server* s) {
   if (s->s_comp) cudaStreamDestroy(s->s_comp);
   if (s->s_out) cudaStreamDestroy(s->s_out);
   cudaFree(s->arena_base);
+  if (s->fault_words) cudaFreeHost(s->fault_words);
   delete s;
 }
 

@@ -39,11 +39,11 @@ __global__ void __launch_bounds__(kSigmaThreads) sigma_kernel(FrameSource src, W
     const int bx = (b % fd.nbx) / tpb, by = (b / fd.nbx) / tpb;
     double sigma;
     int r;
-    item_sigma(fd, bx, by, sigma, r);
-    if (r > kMaxRadius || r < 0) {  // the host refuses such laws; a sigma map may still hold such values
+    if (item_sigma(fd, bx, by, sigma, r)) atomicOr(&ws.counters[CNT_ERROR], kFaultSigmaRange);
+    if (r > kMaxRadius || r < 0) {  // the host refuses such laws and map bounds: never expected
       r = r < 0 ? 0 : kMaxRadius;
       if (!(sigma >= 0.0)) sigma = 0.0;
-      atomicOr(&ws.counters[CNT_ERROR], 1u);
+      atomicOr(&ws.counters[CNT_ERROR], kFaultSigmaRange);
     }
     ItemInfo inf;
     inf.sigma = (float)sigma;
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kSigmaThreads) sigma_kernel(FrameSource src, W
     ws.rank[i] = rank;
     if (bl.list) {  // per-radius item lists for the single-frame blur kernel
       if (bucket < bl.nb && rank < bl.cap) bl.list[(size_t)bucket * bl.cap + rank] = (int)i;
-      else atomicOr(&ws.counters[CNT_ERROR], 32u);
+      else atomicOr(&ws.counters[CNT_ERROR], kFaultBuckets);
     }
     if (sigma_out) sigma_out[i] = (float)sigma;
     if (radius_out) radius_out[i] = r;
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kOrderThreads) order_kernel(FrameSource src, W
     const int bucket = r < kBuckets ? r : kBuckets - 1;
     const unsigned int pos = start[bucket] + (unsigned int)ws.rank[i];
     if (pos < (unsigned long long)total) ws.order[pos] = (int)i;
-    else atomicOr(&ws.counters[CNT_ERROR], 8u);  // histogram out of step: never write out of range
+    else atomicOr(&ws.counters[CNT_ERROR], kFaultOrder);  // histogram out of step: never write out of range
   }
   __threadfence();
   __syncthreads();

@@ -402,13 +402,13 @@ __device__ __forceinline__ void tc_item_loop(const FrameSource& src, const CUten
         next_tk = (int)atomicAdd(&ws.counters[CNT_TICKET], 1u);
         const int item = nx_have ? nx_item : lookup(tk);
         if ((unsigned)item >= (unsigned)n_items) {
-          atomicOr(&ws.counters[CNT_ERROR], 16u);
+          atomicOr(&ws.counters[CNT_ERROR], kFaultWorklist);
           state = 1;
         } else {
           const ItemInfo inf = nx_have ? nx_inf : ws.items[item];
           const FrameDesc fd = load_frame(src, inf.frame);
           if (inf.r > rmax || fd.fmt != FOVEA_U8_HWC || fd.C != C) {
-            atomicOr(&ws.counters[CNT_ERROR], 2u);
+            atomicOr(&ws.counters[CNT_ERROR], kFaultRadiusBound);
             state = 1;
           } else {
             item_geometry(s_it, inf, fd, RB, FULL_SLABS);

@@ -295,7 +295,7 @@ __device__ __forceinline__ bool tc_item(const Item& it, float c_tap, unsigned ch
     // a chunk never arrived: flag it, let the chunks still in flight land
     // (bounded) and give up on the item
     if (tid == 0) {
-      atomicOr(err, 64u);
+      atomicOr(err, kFaultWait);
       for (int qq = q; qq < Q && qq < q + kStagesTc - 1; ++qq) {
         const int gq = gq0 + qq;
         mbar_wait(bars + gq % kStagesTc, (unsigned int)(gq / kStagesTc) & 1u);

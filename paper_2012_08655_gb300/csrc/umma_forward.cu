@@ -423,7 +423,7 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
     // loads still in flight land (bounded) and give up on the item; every
     // arrival and commit was still made, so nobody else is left waiting
     if (tid == 0) {
-      atomicOr(err, 64u);
+      atomicOr(err, kFaultWait);
       for (int qq = q + 1; qq < issued; ++qq) {
         const int g2 = gq0 + qq;
         mbar_wait(bars + g2 % kStages, (unsigned int)(g2 / kStages) & 1u);

@@ -33,6 +33,9 @@ OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 U8_HWC, F32_CHW = 0, 1
 MAX_RADIUS = 1023
 MAX_BLOCK = 256
+# device fault bits (FOVEA_FAULT_* of include/fovea.h), reported by Context.check()
+FAULT_SIGMA_RANGE, FAULT_RADIUS_BOUND, FAULT_ADJ_BOUND, FAULT_ORDER = 0x01, 0x02, 0x04, 0x08
+FAULT_WORKLIST, FAULT_BUCKETS, FAULT_WAIT, FAULT_PIXEL_RADIUS = 0x10, 0x20, 0x40, 0x80
 
 
 LAW_LINEAR, LAW_GEISLER_PERRY, LAW_MAP = 0, 1, 2
@@ -88,6 +91,9 @@ _sig = {
     "fovea_set_kernel_events": (_i, [_vp, _vp, _vp]),
     "fovea_destroy": (None, [_vp]),
     "fovea_render_noalloc": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _d, _d, _f, _f, _vp]),
+    "fovea_check": (_i, [_vp, _vp, ctypes.POINTER(ctypes.c_uint)]),
+    "fovea_check_async": (_i, [_vp, _vp, ctypes.POINTER(ctypes.c_uint)]),
+    "fovea_noalloc_check": (_i, [_vp, ctypes.POINTER(ctypes.c_uint)]),
     "fovea_strerror": (ctypes.c_char_p, [_i]),
     "fovea_last_cuda_error": (_i, []),
     "fovea_measure_fma_rate": (_i, [ctypes.POINTER(_d), _vp]),
@@ -107,18 +113,31 @@ for _name, (_res, _args) in _sig.items():
 
 
 class FoveaError(RuntimeError):
-    def __init__(self, status: int, what: str):
+    def __init__(self, status: int, what: str, faults: int = 0):
         msg = _lib.fovea_strerror(status).decode()
-        if status == ECUDA:
+        if faults:
+            msg += f" (device faults 0x{faults:02x})"
+        elif status == ECUDA:
             msg += f" (cudaError {_lib.fovea_last_cuda_error()})"
         super().__init__(f"{what}: {msg} [{status}]")
         self.status = status
+        self.faults = faults
 
 
 def _check(status: int, what: str) -> int:
     if status < 0:
         raise FoveaError(status, what)
     return status
+
+
+def _check_faults(fn, what: str, *args) -> int:
+    """Call a fault-reporting entry point (fovea_check and its forms): raise
+    FoveaError carrying the fault word unless it returns OK; return the word."""
+    w = ctypes.c_uint(0)
+    st = fn(*args, ctypes.byref(w))
+    if st < 0:
+        raise FoveaError(st, what, int(w.value))
+    return int(w.value)
 
 
 def _stream_handle(stream: Optional[torch.cuda.Stream]) -> int:
@@ -148,11 +167,17 @@ def _shape_of(t: torch.Tensor, fmt: int):
     return w, h, c
 
 
-def _require_device_frame(t: torch.Tensor, name: str):
+def _require_device_frame(t: torch.Tensor, name: str, device: Optional[int] = None):
+    """A contiguous CUDA tensor on `device` (default: the current device),
+    the one the library's kernels run on: a pointer into another GPU's memory
+    would be an illegal address there."""
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
+    want = torch.cuda.current_device() if device is None else int(device)
+    if t.device.index != want:
+        raise ValueError(f"{name} is on cuda:{t.device.index}, the call runs on cuda:{want}")
 
 
 def _require_host_frame(t: torch.Tensor, name: str):
@@ -196,9 +221,11 @@ class Context:
                  e_corner: float = 0.0, sigma_map: Optional[torch.Tensor] = None,
                  sigma_map_max: Optional[float] = None, grid: int = GRID_ANCHORED):
         mp, mmax = 0, 0.0
+        self.device = torch.cuda.current_device()
         if law == LAW_MAP:
             if sigma_map is None or not sigma_map.is_cuda or sigma_map.dtype != torch.float32:
                 raise ValueError("LAW_MAP needs a float32 CUDA sigma_map")
+            _require_device_frame(sigma_map, "sigma_map", self.device)
             mp = sigma_map.data_ptr()
             mmax = float(sigma_map.max().item()) if sigma_map_max is None else float(sigma_map_max)
         sl = SigmaLaw(int(law), float(sigma0), float(k), float(e_corner), mp, mmax, int(grid))
@@ -234,10 +261,25 @@ class Context:
 
     # ---------------------------------------------------------------- calls
     def _frames(self, pairs, device: bool = True, fmt: Optional[int] = None):
-        """Check (tensor, name) pairs against this context's frame."""
+        """Check (tensor, name) pairs against this context's frame (and, for
+        device tensors, against the context's device)."""
         for t, name in pairs:
-            (_require_device_frame if device else _require_host_frame)(t, name)
+            if device:
+                _require_device_frame(t, name, self.device)
+            else:
+                _require_host_frame(t, name)
             _require_frame_size(t, name, self.width, self.height, self.channels, self.fmt if fmt is None else fmt)
+
+    def check(self, stream=None) -> int:
+        """Wait for the stream and read and clear the context's device fault
+        word (``fovea_check``). Raises FoveaError (with ``.faults``) when a
+        kernel recorded a fault since the last check; returns 0 otherwise."""
+        return _check_faults(_lib.fovea_check, "fovea_check", self._h, _stream_handle(stream))
+
+    def check_async(self, stream=None) -> int:
+        """Non-blocking form of :meth:`check` (``fovea_check_async``): raises
+        for a fault that an earlier call saw land, never waits otherwise."""
+        return _check_faults(_lib.fovea_check_async, "fovea_check_async", self._h, _stream_handle(stream))
 
     def render(self, inp: torch.Tensor, out: torch.Tensor, fix_x: float, fix_y: float, stream=None):
         self._frames([(inp, "input"), (out, "output")])
@@ -289,7 +331,7 @@ class Context:
         return sig, rad
 
     def render_batch(self, frames: Sequence["BatchFrame"], stream=None):
-        arr = _frames_array(frames)
+        arr = _frames_array(frames, self.device)
         _check(_lib.fovea_render_batch(self._h, arr, len(frames), _stream_handle(stream)), "fovea_render_batch")
 
     def reserve(self, max_frames: int, max_items: int):
@@ -297,7 +339,7 @@ class Context:
         _check(_lib.fovea_reserve(self._h, int(max_frames), int(max_items)), "fovea_reserve")
 
     def backward_batch(self, frames: Sequence["BatchFrame"], stream=None):
-        arr = _frames_array(frames)
+        arr = _frames_array(frames, self.device)
         _check(_lib.fovea_backward_batch(self._h, arr, len(frames), _stream_handle(stream)), "fovea_backward_batch")
 
     def set_kernel_events(self, start: Optional[torch.cuda.Event], stop: Optional[torch.cuda.Event]):
@@ -340,15 +382,17 @@ class BatchFrame:
     sigma_map_max: float = 0.0
 
 
-def _frames_array(frames: Sequence[BatchFrame]):
+def _frames_array(frames: Sequence[BatchFrame], device: Optional[int] = None):
     if len(frames) == 0:
         raise ValueError("empty batch")
     arr = (Frame * len(frames))()
     keep = []
     for i, fr in enumerate(frames):
-        _require_device_frame(fr.inp, f"frame {i} input")
-        _require_device_frame(fr.out, f"frame {i} output")
+        _require_device_frame(fr.inp, f"frame {i} input", device)
+        _require_device_frame(fr.out, f"frame {i} output", device)
         _require_like(fr.out, fr.inp, f"frame {i} output")
+        if fr.sigma_map is not None:
+            _require_device_frame(fr.sigma_map, f"frame {i} sigma map", device)
         fmt = _fmt_of(fr.inp)
         w, h, c = _shape_of(fr.inp, fmt)
         mp = fr.sigma_map.data_ptr() if fr.sigma_map is not None else None
@@ -472,6 +516,13 @@ def render_noalloc(x: torch.Tensor, out: torch.Tensor, fix_x: float, fix_y: floa
     return out
 
 
+def noalloc_check(stream=None) -> int:
+    """Wait for the stream and read the device fault word of the latest
+    :func:`render_noalloc` call on the current device
+    (``fovea_noalloc_check``); raises FoveaError on a fault."""
+    return _check_faults(_lib.fovea_noalloc_check, "fovea_noalloc_check", _stream_handle(stream))
+
+
 def measure_fma_rate(stream=None) -> float:
     """Measured FP32 FMA lane-operations per second of the current GPU
     (``fovea_measure_fma_rate``): the roof of the blur kernels' arithmetic."""
@@ -513,23 +564,26 @@ class FoveaFunction(torch.autograd.Function):
         if x.dtype != torch.float32 or x.dim() != 4:
             raise ValueError("FoveaFunction takes float32 [N, C, H, W]")
         x = x.contiguous()
-        if not x.is_cuda:
-            raise ValueError("FoveaFunction takes a CUDA tensor")
+        _require_device_frame(x, "x")
         fixes = [(float(a), float(b)) for a, b in fix.detach().cpu().tolist()]
         y = torch.empty_like(x)
         bctx = _batch_ctx(block)
         arr = _frames_of_nchw(x, y, fixes, float(sigma0), float(k))
-        _check(_lib.fovea_render_batch(bctx._h, arr, len(fixes), _stream_handle(None)), "fovea_render_batch")
+        st = _stream_handle(None)
+        _check(_lib.fovea_render_batch(bctx._h, arr, len(fixes), st), "fovea_render_batch")
+        bctx.check_async()  # faults of earlier launches surface here without a wait
         ctx.fixes, ctx.sigma0, ctx.k, ctx.block = fixes, sigma0, k, block
         return y
 
     @staticmethod
     def backward(ctx, gy: torch.Tensor):
         gy = gy.contiguous()
+        _require_device_frame(gy, "grad_output")
         gx = torch.empty_like(gy)
         bctx = _batch_ctx(ctx.block)
         arr = _frames_of_nchw(gy, gx, ctx.fixes, float(ctx.sigma0), float(ctx.k))
         _check(_lib.fovea_backward_batch(bctx._h, arr, len(ctx.fixes), _stream_handle(None)), "fovea_backward_batch")
+        bctx.check_async()
         return gx, None, None, None, None
 
 
@@ -537,6 +591,12 @@ def foveate_train(x: torch.Tensor, fix: torch.Tensor, sigma0: float = 0.5, k: fl
                   block: int = 32) -> torch.Tensor:
     """Differentiable foveation of x [N, C, H, W] float32 at fixations fix [N, 2] (x, y)."""
     return FoveaFunction.apply(x, fix, sigma0, k, block)
+
+
+def check_train(block: int = 32, stream=None) -> int:
+    """Blocking fault check of the context :func:`foveate_train` uses
+    (its forward and backward check without waiting)."""
+    return _batch_ctx(block).check(stream)
 
 
 # ------------------------------------------------------------------ serving
@@ -560,17 +620,23 @@ class Server:
         return float(_lib.fovea_server_now_us())
 
     def submit(self, inp: torch.Tensor, out: torch.Tensor, fix_x: float, fix_y: float, sigma0: float,
-               k: float, arrival_us: Optional[float] = None, grid: int = GRID_ANCHORED) -> int:
+               k: float, arrival_us: Optional[float] = None, grid: int = GRID_ANCHORED,
+               sigma_map: Optional[torch.Tensor] = None, sigma_map_max: float = 0.0) -> int:
+        """Submit one host frame; ``sigma_map`` (a float32 device tensor of
+        per-block sigma, bounded by ``sigma_map_max``) replaces the linear law."""
         _require_host_frame(inp, "input")
         _require_host_frame(out, "output")
         _require_like(out, inp, "output")
+        if sigma_map is not None:
+            _require_device_frame(sigma_map, "sigma_map")
         fmt = _fmt_of(inp)
         w, h, c = _shape_of(inp, fmt)
+        mp = sigma_map.data_ptr() if sigma_map is not None else None
         fr = Frame(w, h, c, fmt, inp.data_ptr(), out.data_ptr(), float(fix_x), float(fix_y), float(sigma0), float(k),
-                   int(grid), None, 0.0)
+                   int(grid), mp, float(sigma_map_max))
         t = self.now_us() if arrival_us is None else float(arrival_us)
         rid = _check(int(_lib.fovea_server_submit(self._h, ctypes.byref(fr), t)), "fovea_server_submit")
-        self._held[rid] = (inp, out)
+        self._held[rid] = (inp, out, sigma_map)
         return rid
 
     def wait(self, rid: int, timeout_ms: int = 10000) -> dict:

@@ -109,6 +109,25 @@ def test_strerror_and_invalid_arguments(lib):
     assert lib.fovea_ssim(0, 8, 3, 0, fake, fake, 0.0, fake, None, None) == -1      # empty
 
 
+def test_fault_bits_and_checks(lib):
+    """The FOVEA_FAULT_* bits of the header are distinct single bits, the
+    binding's constants equal them, and the checks refuse a null context on
+    the host (the status mapping itself needs a device: tests/test_gpu_faults.py)."""
+    text = open(HEADER).read()
+    bits = {n: int(v, 16) for n, v in re.findall(r"#define FOVEA_FAULT_(\w+)\s+(0x[0-9a-fA-F]+)u", text)}
+    assert len(bits) == 8 and len(set(bits.values())) == 8
+    assert all(v & (v - 1) == 0 for v in bits.values())
+    from paper_2012_08655_gb300 import fovea
+    for n, v in bits.items():
+        assert getattr(fovea, "FAULT_" + n) == v
+    w = ctypes.c_uint(7)
+    lib.fovea_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint)]
+    assert lib.fovea_check(None, None, ctypes.byref(w)) == -1 and w.value == 0
+    w.value = 7
+    lib.fovea_check_async.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint)]
+    assert lib.fovea_check_async(None, None, ctypes.byref(w)) == -1 and w.value == 0
+
+
 def test_python_binding_imports_without_gpu():
     from paper_2012_08655_gb300 import fovea
     assert fovea.MAX_RADIUS == 1023

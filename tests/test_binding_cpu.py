@@ -43,7 +43,7 @@ def _bare(cls, **attrs):
 
 
 def test_context_refuses_mismatched_frames_before_the_library():
-    ctx = _bare(fv.Context, width=12, height=10, channels=3, fmt=fv.U8_HWC)
+    ctx = _bare(fv.Context, width=12, height=10, channels=3, fmt=fv.U8_HWC, device=0)
     good = torch.zeros((10, 12, 3), dtype=torch.uint8)
     ctx._frames([(good, "input"), (torch.empty_like(good), "output")], device=False)
     with pytest.raises(ValueError):
@@ -52,7 +52,7 @@ def test_context_refuses_mismatched_frames_before_the_library():
         ctx.render_host(torch.zeros((9, 12, 3), dtype=torch.uint8), good, 1.0, 1.0)
     with pytest.raises(ValueError):
         ctx.render(good, torch.empty_like(good), 1.0, 1.0)  # host tensors for a device call
-    f32 = _bare(fv.Context, width=12, height=10, channels=3, fmt=fv.F32_CHW)
+    f32 = _bare(fv.Context, width=12, height=10, channels=3, fmt=fv.F32_CHW, device=0)
     with pytest.raises(TypeError):
         f32._frames([(good, "grad_out")], device=False, fmt=fv.F32_CHW)
 
@@ -65,3 +65,40 @@ def test_server_refuses_mismatched_output_before_the_library():
     with pytest.raises(ValueError):
         srv.submit(inp.transpose(0, 1), torch.empty_like(inp), 1.0, 1.0, 0.5, 0.02)
     assert srv._held == {}
+
+
+class _FakeDeviceTensor:
+    """Stands in for a contiguous CUDA tensor on a given device index (no GPU
+    is needed: the device check must fire before anything else)."""
+
+    is_cuda = True
+
+    def __init__(self, index):
+        self.device = torch.device("cuda", index)
+
+    def is_contiguous(self):
+        return True
+
+
+def test_device_tensors_must_be_on_the_call_device(monkeypatch):
+    fv._require_device_frame(_FakeDeviceTensor(1), "x", 1)
+    with pytest.raises(ValueError, match="cuda:1"):
+        fv._require_device_frame(_FakeDeviceTensor(1), "x", 0)
+    # default: the current device
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 2)
+    fv._require_device_frame(_FakeDeviceTensor(2), "x")
+    with pytest.raises(ValueError):
+        fv._require_device_frame(_FakeDeviceTensor(0), "x")
+
+
+def test_context_refuses_tensors_of_another_device():
+    ctx = _bare(fv.Context, width=12, height=10, channels=3, fmt=fv.U8_HWC, device=0)
+    other = _FakeDeviceTensor(1)
+    with pytest.raises(ValueError, match="cuda:1"):
+        ctx._frames([(other, "input")])
+
+
+def test_fault_error_carries_the_word():
+    e = fv.FoveaError(fv.EINVAL, "fovea_check", fv.FAULT_SIGMA_RANGE)
+    assert e.status == fv.EINVAL and e.faults == fv.FAULT_SIGMA_RANGE
+    assert "0x01" in str(e)
