@@ -262,7 +262,11 @@ int fovea_sigma_table(fovea_ctx* ctx, float fix_x, float fix_y, float* sigma_dev
 /* Kernel configuration of the forward path. Chosen by the built-in
  * autotuner (fovea_autotune) or set explicitly (fovea_set_config). */
 typedef struct {
-  int threads;        /* threads per CTA of the forward kernel: 256 */
+  int threads;        /* threads per CTA of the mma.sync tensor-core kernel: 128,
+                         256 or 512 (4, 8 or 16 warps; a staged row, and so a
+                         column slab of the halo tile, is 32 bytes per warp:
+                         112, 240 or 496 bytes of data). The fp32 and tcgen05
+                         kernels always run 256. */
   int ctas_per_sm;    /* persistent CTAs per SM (0 = as many as fit) */
   int rows_per_chunk; /* tile rows staged per chunk: 16, 32 or 64 (float32
                          launches of the fp32 kernel keep a two-stage ring and
@@ -281,19 +285,42 @@ int fovea_get_config(const fovea_ctx* ctx, fovea_config* cfg);
 
 /* Use *cfg for later launches on this context (not in the paper: the paper
  * fixes one CUDA block per fragment). FOVEA_EUNSUPPORTED for threads other
- * than 256 or rows_per_chunk other than 16, 32 or 64; FOVEA_EINVAL for a
- * null argument, ctas_per_sm outside 0..8 or tensor_cores outside 0..2. A CTA
- * count above what fits is reduced to what fits at launch. Output does not
- * depend on ctas_per_sm or rows_per_chunk, only on the kernel
- * (tensor_cores). */
+ * than 128, 256 or 512 or rows_per_chunk other than 16, 32 or 64;
+ * FOVEA_EINVAL for a null argument, ctas_per_sm outside 0..8 or tensor_cores
+ * outside 0..2. A CTA count above what fits is reduced to what fits at
+ * launch. Output does not depend on ctas_per_sm or rows_per_chunk, only on
+ * the kernel (tensor_cores and, for the mma.sync kernel, threads, which sets
+ * where a wide halo tile is cut into column slabs and so the fp32 summation
+ * order). After this call the context's batches also run *cfg, instead of a
+ * configuration fovea_autotune_batch chose for them. */
 int fovea_set_config(fovea_ctx* ctx, const fovea_config* cfg);
 
 /* Time every built-in configuration on the context's own frame shape (a
- * synthetic frame, fixation at the centre, `iters` timed launches each),
- * keep the fastest, and cache it under the device name, SM count, shape,
- * format and radius bucket. Synchronises the device. If `cache_path` is not
- * NULL the cache is read from and written to that JSON file. */
+ * synthetic frame, fixation at the centre, `iters` timed launches each):
+ * the kernel (fp32; mma.sync tensor cores with 128, 256 or 512 threads per
+ * CTA, i.e. staged tiles of rows_per_chunk rows x 112, 240 or 496 bytes;
+ * tcgen05 vertical pass) and rows per chunk, then CTAs per SM for the
+ * fastest. Keeps the fastest, and caches it under the device
+ * name, SM count, shape, format, block side and radius bucket. Synchronises
+ * the device. If `cache_path` is not NULL the cache is read from and written
+ * to that JSON file. */
 int fovea_autotune(fovea_ctx* ctx, int iters, const char* cache_path);
+
+/* The same search on the caller's own batch: every candidate renders
+ * `frames` (their outputs are overwritten with the usual results) with
+ * `iters` timed launches after one untimed one, and the fastest is cached
+ * under the batch's key: device, SM count, block side, the formats and
+ * channel count of the frames, their largest block radius (rounded up to a
+ * multiple of 64) and the numbers of blocks and frames (rounded down to
+ * powers of two). Later fovea_render_batch calls on any context of the
+ * process run batches with the same key with that configuration, unless
+ * fovea_set_config fixed the context's own. An existing entry for the key is
+ * kept (no timing). Synchronises the device first. *chosen (if not NULL)
+ * receives the configuration. FOVEA_EINVAL for a null or empty batch or
+ * iters <= 0; the statuses of fovea_render_batch for a bad frame. Not in the
+ * paper, which fixes one CUDA block per fragment. */
+int fovea_autotune_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, int iters, const char* cache_path,
+                         fovea_config* chosen);
 
 /* Measurement hook: when both are non-NULL, every later render call on this
  * context records `ev_start` (a cudaEvent_t) immediately before launching its

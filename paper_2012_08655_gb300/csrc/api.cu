@@ -87,6 +87,9 @@ struct fovea_ctx {
   int device = 0, num_sms = 0;
   FwdConfig cfg{256, 0, 32, 1};
   bool cfg_tuned = false;
+  // set by fovea_set_config: batches then run ctx->cfg instead of the
+  // configuration tuned for their kind of batch
+  bool cfg_explicit = false;
   Workspace ws{};
   cudaStream_t capture_stream = nullptr;
   // device-resident batch (header + descriptors)
@@ -96,8 +99,10 @@ struct fovea_ctx {
   cudaEvent_t batch_ev[kBatchSlots] = {};
   size_t batch_host_cap = 0;
   int batch_slot = 0;
-  // CUDA graphs of the batch launch sequence, keyed by (kind + 2*format mask + 8*tc channels, radius bound)
-  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+  // CUDA graphs of the batch launch sequence, keyed by the launch (adjoint,
+  // format mask, tensor-core channel count, radius bound) and the
+  // configuration it was captured with
+  std::map<std::pair<long long, long long>, cudaGraphExec_t> graphs;
   // Batch buffers replaced by larger ones while queued work may still read
   // them: freed by fovea_destroy, so growing never waits for the device.
   std::vector<void*> retired_dev, retired_host;
@@ -282,20 +287,29 @@ int sigma_grid(long long items, int num_sms) {
 // launch runs on: 0 the fp32 FMA kernel, 1 the mma.sync kernel, 2 the
 // kernel with pass 1 on tcgen05 (radius bound and row chunk permitting,
 // else the mma.sync kernel).
-int tc_kind(const fovea_ctx* ctx, int fmt_mask, int tc_c, int rmax) {
-  if (!ctx->cfg.tc || fmt_mask != 1 || tc_c <= 0) return 0;
-  if (ctx->cfg.tc == 2 && rmax <= kUmmaMaxRadius && ctx->cfg.rows_per_chunk <= 32) return 2;
+int tc_kind(const FwdConfig& cfg, int fmt_mask, int tc_c, int rmax) {
+  if (!cfg.tc || fmt_mask != 1 || tc_c <= 0) return 0;
+  if (cfg.tc == 2 && rmax <= kUmmaMaxRadius && cfg.rows_per_chunk <= 32) return 2;
   return 1;
 }
 
-int forward_grid(fovea_ctx* ctx, int rmax, int fmt_mask, int tc_c) {
-  const int kind = tc_kind(ctx, fmt_mask, tc_c, rmax);
-  int per = kind == 2   ? umma_forward_max_ctas_per_sm(ctx->cfg, rmax, tc_c)
-            : kind == 1 ? tc_forward_max_ctas_per_sm(ctx->cfg, rmax, tc_c)
-                        : forward_max_ctas_per_sm(ctx->cfg, rmax, fmt_mask);
+int forward_grid(const fovea_ctx* ctx, const FwdConfig& cfg, int rmax, int fmt_mask, int tc_c) {
+  const int kind = tc_kind(cfg, fmt_mask, tc_c, rmax);
+  int per = kind == 2   ? umma_forward_max_ctas_per_sm(cfg, rmax, tc_c)
+            : kind == 1 ? tc_forward_max_ctas_per_sm(cfg, rmax, tc_c)
+                        : forward_max_ctas_per_sm(cfg, rmax, fmt_mask);
   if (per <= 0) return 0;
-  if (ctx->cfg.ctas_per_sm > 0) per = std::min(per, ctx->cfg.ctas_per_sm);
+  if (cfg.ctas_per_sm > 0) per = std::min(per, cfg.ctas_per_sm);
   return per * ctx->num_sms;
+}
+
+FwdConfig to_fwd(const fovea_config& c) {
+  return FwdConfig{c.threads, c.ctas_per_sm, c.rows_per_chunk, c.tensor_cores};
+}
+
+// A configuration as one number (part of the batch graphs' key).
+long long config_code(const FwdConfig& c) {
+  return (((long long)c.threads * 128 + c.rows_per_chunk) * 4 + c.tc) * 16 + c.ctas_per_sm;
 }
 
 int adjoint_grid(fovea_ctx* ctx, int rmax) {
@@ -344,7 +358,13 @@ int ensure_batch_tables(fovea_ctx* ctx, size_t bytes) {
   return FOVEA_OK;
 }
 
-int upload_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint, cudaStream_t s,
+FrameLaw law_of(const fovea_frame& f) {
+  FrameLaw fl;
+  fl.sigma0 = f.sigma0; fl.k = f.k; fl.smap = f.sigma_map; fl.smap_max = f.sigma_map_max; fl.grid = f.grid;
+  return fl;
+}
+
+int upload_batch(fovea_ctx* ctx, const FwdConfig& cfg, const fovea_frame* frames, int n, bool adjoint, cudaStream_t s,
                  long long* total, int* rmax, int* fmt_mask, int* tc_c) {
   if (n <= 0 || !frames) return FOVEA_EINVAL;
   std::vector<FrameDesc> descs((size_t)n);
@@ -353,8 +373,7 @@ int upload_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint,
   int mask = 0, cc = -1;
   for (int i = 0; i < n; ++i) {
     const fovea_frame& f = frames[i];
-    FrameLaw fl;
-    fl.sigma0 = f.sigma0; fl.k = f.k; fl.smap = f.sigma_map; fl.smap_max = f.sigma_map_max; fl.grid = f.grid;
+    const FrameLaw fl = law_of(f);
     int st = check_frame(f.width, f.height, f.channels, f.format, ctx->B, fl, f.fix_x, f.fix_y);
     if (st != FOVEA_OK) return st;
     if (adjoint && f.format != FOVEA_F32_CHW) return FOVEA_EINVAL;
@@ -389,7 +408,7 @@ int upload_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint,
     FrameDesc& d = descs[(size_t)i];
     void* map = hbuf + maps_off + (size_t)i * kTensorMapBytes;
     d.tma = (!adjoint && d.fmt == FOVEA_U8_HWC &&
-             make_u8_tensor_map(map, d.in, d.W, d.H, d.C, ctx->cfg.rows_per_chunk)) ? 1 : 0;
+             make_u8_tensor_map(map, d.in, d.W, d.H, d.C, cfg.rows_per_chunk)) ? 1 : 0;
     if (!d.tma) std::memset(map, 0, kTensorMapBytes);
   }
   std::memcpy(hbuf, &hdr, sizeof(hdr));
@@ -412,7 +431,8 @@ FrameSource batch_source(fovea_ctx* ctx) {
 }
 
 // Enqueue (or capture) the batch launch sequence for the current batch buffer.
-int enqueue_batch_kernels(fovea_ctx* ctx, bool adjoint, int rbound, int fmt_mask, int tc_c, cudaStream_t s) {
+int enqueue_batch_kernels(fovea_ctx* ctx, const FwdConfig& cfg, bool adjoint, int rbound, int fmt_mask, int tc_c,
+                          cudaStream_t s) {
   const FrameSource src = batch_source(ctx);
   const int sg = 4 * ctx->num_sms;
   if (adjoint) {
@@ -427,41 +447,53 @@ int enqueue_batch_kernels(fovea_ctx* ctx, bool adjoint, int rbound, int fmt_mask
     if (grid <= 0) return FOVEA_EUNSUPPORTED;
     e = launch_adjoint(src, ctx->ws, rbound, grid, s);
   } else {
-    int grid = forward_grid(ctx, rbound, fmt_mask, tc_c);
+    int grid = forward_grid(ctx, cfg, rbound, fmt_mask, tc_c);
     if (grid <= 0) return FOVEA_EUNSUPPORTED;
-    switch (tc_kind(ctx, fmt_mask, tc_c, rbound)) {
+    switch (tc_kind(cfg, fmt_mask, tc_c, rbound)) {
       case 2:
-        e = launch_umma_forward(src, ctx->ws, ctx->cfg, rbound, tc_c, grid, s, BucketList{nullptr, 0, 0}, false,
-                                nullptr);
+        e = launch_umma_forward(src, ctx->ws, cfg, rbound, tc_c, grid, s, BucketList{nullptr, 0, 0}, false, nullptr);
         break;
       case 1:
-        e = launch_tc_forward(src, ctx->ws, ctx->cfg, rbound, tc_c, grid, s, BucketList{nullptr, 0, 0}, false,
-                              nullptr);
+        e = launch_tc_forward(src, ctx->ws, cfg, rbound, tc_c, grid, s, BucketList{nullptr, 0, 0}, false, nullptr);
         break;
       default:
-        e = launch_forward(src, ctx->ws, ctx->cfg, rbound, fmt_mask, grid, s);
+        e = launch_forward(src, ctx->ws, cfg, rbound, fmt_mask, grid, s);
     }
   }
   if (e != cudaSuccess) return cuda_fail(e);
   return FOVEA_OK;
 }
 
-int run_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint, cudaStream_t s) {
+// The configuration a batch runs with: the context's own after
+// fovea_set_config, else the one fovea_autotune_batch chose for batches of
+// this kind (see batch_tune_key), else the context's default.
+FwdConfig batch_config(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint) {
+  if (ctx->cfg_explicit || adjoint || n <= 0 || !frames) return ctx->cfg;
+  BatchSummary bs;
+  if (summarize_batch(ctx, frames, n, &bs) != FOVEA_OK) return ctx->cfg;
+  fovea_config c;
+  return lookup_batch_config(ctx, bs, &c) ? to_fwd(c) : ctx->cfg;
+}
+
+int run_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint, cudaStream_t s,
+              const FwdConfig* forced = nullptr) {
+  const FwdConfig cfg = forced ? *forced : batch_config(ctx, frames, n, adjoint);
   long long total = 0;
   int rmax = 0;
   int fmt_mask = 0, tc_c = 0;
-  int st = upload_batch(ctx, frames, n, adjoint, s, &total, &rmax, &fmt_mask, &tc_c);
+  int st = upload_batch(ctx, cfg, frames, n, adjoint, s, &total, &rmax, &fmt_mask, &tc_c);
   if (st != FOVEA_OK) return st;
   // Radius bound of the graph: next multiple of 64 (shared-memory size of
   // the persistent kernel depends on it).
   const int rbound = std::min(kMaxRadius, ((rmax + 63) / 64) * 64);
-  const auto key = std::make_pair((adjoint ? 1 : 0) + 2 * fmt_mask + 8 * tc_c, rbound);
+  const auto key = std::make_pair((long long)((adjoint ? 1 : 0) + 2 * fmt_mask + 8 * tc_c) * 2048 + rbound,
+                                  config_code(cfg));
   auto it = ctx->graphs.find(key);
   if (it == ctx->graphs.end()) {
     if (!ctx->capture_stream) FOVEA_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
     FOVEA_CUDA(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-    st = enqueue_batch_kernels(ctx, adjoint, rbound, fmt_mask, tc_c, ctx->capture_stream);
+    st = enqueue_batch_kernels(ctx, cfg, adjoint, rbound, fmt_mask, tc_c, ctx->capture_stream);
     cudaError_t ee = cudaStreamEndCapture(ctx->capture_stream, &g);
     if (st != FOVEA_OK) {
       if (g) cudaGraphDestroy(g);
@@ -556,7 +588,7 @@ static int render_one(fovea_ctx* ctx, const void* in_dev, void* out_dev, float f
   const int rmax = radius_bound(ctx->W, ctx->H, ctx->B, fix_x, fix_y, ctx->law);
   const int fmt_mask = ctx->fmt == FOVEA_F32_CHW ? 2 : 1;
   const int tc_c = ctx->C;
-  int grid = forward_grid(ctx, rmax, fmt_mask, tc_c);
+  int grid = forward_grid(ctx, ctx->cfg, rmax, fmt_mask, tc_c);
   if (grid <= 0) return FOVEA_EUNSUPPORTED;
   // no more persistent CTAs than items (small frames start fewer CTAs)
   grid = (int)std::min<long long>(grid, src.one_total);
@@ -586,7 +618,7 @@ static int render_one(fovea_ctx* ctx, const void* in_dev, void* out_dev, float f
   // Programmatic dependent launch lets the blur kernel's prologue overlap the
   // sigma kernel (not when its launch is bracketed by timing events).
   const bool pdl = bl.list && !ctx->kev_start;
-  const int kind = tc_kind(ctx, fmt_mask, tc_c, rmax);
+  const int kind = tc_kind(ctx->cfg, fmt_mask, tc_c, rmax);
   if (kind) {
     alignas(64) unsigned char map[kTensorMapBytes];
     src.one.tma = make_u8_tensor_map(map, src.one.in, src.one.W, src.one.H, src.one.C, ctx->cfg.rows_per_chunk) ? 1 : 0;
@@ -878,17 +910,9 @@ int fovea_get_config(const fovea_ctx* ctx, fovea_config* cfg) {
 
 int fovea_set_config(fovea_ctx* ctx, const fovea_config* cfg) {
   if (!ctx || !cfg) return FOVEA_EINVAL;
-  if (cfg->threads != 256) return FOVEA_EUNSUPPORTED;
-  if (cfg->rows_per_chunk != 16 && cfg->rows_per_chunk != 32 && cfg->rows_per_chunk != 64) return FOVEA_EUNSUPPORTED;
-  if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 8) return FOVEA_EINVAL;
-  if (cfg->tensor_cores < 0 || cfg->tensor_cores > 2) return FOVEA_EINVAL;
-  FwdConfig c{cfg->threads, cfg->ctas_per_sm, cfg->rows_per_chunk, cfg->tensor_cores};
-  if (ctx->cfg.rows_per_chunk != c.rows_per_chunk || ctx->cfg.ctas_per_sm != c.ctas_per_sm || ctx->cfg.tc != c.tc) {
-    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-    ctx->graphs.clear();
-  }
-  ctx->cfg = c;
-  return FOVEA_OK;
+  const int st = fovea::apply_config(ctx, cfg);
+  if (st == FOVEA_OK) ctx->cfg_explicit = true;
+  return st;
 }
 
 int fovea_reserve(fovea_ctx* ctx, int max_frames, long long max_items) {
@@ -1012,6 +1036,46 @@ int ctx_shape(const fovea_ctx* ctx, int* W, int* H, int* C, int* fmt, int* B) {
 int ctx_centre_radius_bound(const fovea_ctx* ctx) {
   if (ctx->batch_only || ctx->W <= 0 || ctx->H <= 0) return 0;
   return radius_bound(ctx->W, ctx->H, ctx->B, 0.5f * (float)ctx->W, 0.5f * (float)ctx->H, ctx->law);
+}
+
+int check_config(const fovea_config* cfg) {
+  if (cfg->threads != 128 && cfg->threads != 256 && cfg->threads != 512) return FOVEA_EUNSUPPORTED;
+  if (cfg->rows_per_chunk != 16 && cfg->rows_per_chunk != 32 && cfg->rows_per_chunk != 64) return FOVEA_EUNSUPPORTED;
+  if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 8) return FOVEA_EINVAL;
+  if (cfg->tensor_cores < 0 || cfg->tensor_cores > 2) return FOVEA_EINVAL;
+  return FOVEA_OK;
+}
+
+int apply_config(fovea_ctx* ctx, const fovea_config* cfg) {
+  const int st = check_config(cfg);
+  if (st != FOVEA_OK) return st;
+  ctx->cfg = to_fwd(*cfg);  // batch graphs are keyed by configuration: nothing to drop
+  return FOVEA_OK;
+}
+
+int summarize_batch(const fovea_ctx* ctx, const fovea_frame* frames, int n, BatchSummary* out) {
+  if (!ctx || !frames || n <= 0 || !out) return FOVEA_EINVAL;
+  BatchSummary bs{0, -1, 0, 0, n};
+  for (int i = 0; i < n; ++i) {
+    const fovea_frame& f = frames[i];
+    if (f.width <= 0 || f.height <= 0 || f.channels < 1 || f.channels > 4) return FOVEA_EINVAL;
+    if (!std::isfinite(f.fix_x) || !std::isfinite(f.fix_y)) return FOVEA_EINVAL;
+    bs.fmt_mask |= f.format == FOVEA_F32_CHW ? 2 : 1;
+    bs.channels = bs.channels == -1 ? f.channels : (bs.channels == f.channels ? bs.channels : 0);
+    bs.rmax = std::max(bs.rmax, radius_bound(f.width, f.height, ctx->B, f.fix_x, f.fix_y, law_of(f)));
+    bs.blocks += (long long)((f.width + ctx->B - 1) / ctx->B) * ((f.height + ctx->B - 1) / ctx->B);
+  }
+  *out = bs;
+  return FOVEA_OK;
+}
+
+int render_batch_with(fovea_ctx* ctx, const fovea_frame* frames, int n, const fovea_config* cfg, void* stream) {
+  if (!ctx || !cfg) return FOVEA_EINVAL;
+  const int st = check_config(cfg);
+  if (st != FOVEA_OK) return st;
+  const FwdConfig c = to_fwd(*cfg);
+  ctx->caller_stream_used = true;
+  return run_batch(ctx, frames, n, false, static_cast<cudaStream_t>(stream), &c);
 }
 
 int ctx_fault_word(const fovea_ctx* ctx, unsigned int** word) {

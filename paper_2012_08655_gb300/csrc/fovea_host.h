@@ -30,6 +30,24 @@ int check_frame(int W, int H, int C, int fmt, int B, const FrameLaw& law, float 
 size_t frame_bytes(int W, int H, int C, int fmt);
 int ctx_shape(const fovea_ctx* ctx, int* W, int* H, int* C, int* fmt, int* B);
 int ctx_device_info(const fovea_ctx* ctx, int* device, int* num_sms);
+// A configuration's validity (the fovea_set_config statuses), and setting it
+// on a context without marking it as the caller's choice (the autotuner).
+int check_config(const fovea_config* cfg);
+int apply_config(fovea_ctx* ctx, const fovea_config* cfg);
+// What the batch autotuner keys its choice on: the formats and channel
+// counts of the frames (fmt_mask bit 0 uint8, bit 1 float32; channels 0 when
+// mixed), the largest block radius, the number of blocks and of frames.
+struct BatchSummary {
+  int fmt_mask, channels, rmax;
+  long long blocks;
+  int frames;
+};
+int summarize_batch(const fovea_ctx* ctx, const fovea_frame* frames, int n, BatchSummary* out);
+// The configuration fovea_autotune_batch chose for batches like bs on this
+// context's device (false if none); defined with the autotuner.
+bool lookup_batch_config(const fovea_ctx* ctx, const BatchSummary& bs, fovea_config* cfg);
+// fovea_render_batch with a given configuration (the autotuner's timing runs).
+int render_batch_with(fovea_ctx* ctx, const fovea_frame* frames, int n, const fovea_config* cfg, void* stream);
 // Device address of the context's fault word (FOVEA_FAULT_* bits).
 int ctx_fault_word(const fovea_ctx* ctx, unsigned int** word);
 // Radius bound of a sized context with the fixation at the frame centre (the

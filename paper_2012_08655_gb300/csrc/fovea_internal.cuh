@@ -303,7 +303,7 @@ inline cudaError_t set_smem_attrs(const void* k, size_t smem) {
 // (defined in sigma.cu, forward.cu, adjoint.cu)
 
 struct FwdConfig {
-  int threads;        // 256
+  int threads;        // threads per CTA of the mma.sync tensor-core kernel: 128, 256 or 512 (others: 256)
   int ctas_per_sm;
   int rows_per_chunk; // RB, multiple of 16
   int tc;             // uint8 frames on the tensor-core kernel

@@ -114,9 +114,9 @@ __device__ __forceinline__ void stage_rows(const Item& it, const Slab& sl, int k
 
 // Per-item geometry from the item record (computed by one thread).
 // full_slabs: every slab but the last is as wide as allowed (otherwise the
-// slabs share the width evenly).
+// slabs share the width evenly); slab_max: elements a slab may hold.
 __device__ __forceinline__ void item_geometry(Item& it, const ItemInfo& inf, const FrameDesc& fd, int rb,
-                                              bool full_slabs = false) {
+                                              bool full_slabs = false, int slab_max = kSlabMax) {
   const bool u8 = fd.fmt == FOVEA_U8_HWC;
   it.in = static_cast<const unsigned char*>(fd.in);
   it.out = static_cast<unsigned char*>(fd.out);
@@ -141,7 +141,7 @@ __device__ __forceinline__ void item_geometry(Item& it, const ItemInfo& inf, con
   it.pitch = u8 ? (size_t)it.W * it.C : (size_t)it.W * 4;
   it.fast = (((size_t)it.in & 15) == 0) && ((it.pitch & 15) == 0);
   const int E = u8 ? it.EW * it.C : it.EW;
-  const int cap = u8 ? (kSlabMax / it.C) * it.C : kSlabMax;
+  const int cap = u8 ? (slab_max / it.C) * it.C : slab_max;
   const int nsl = (E + cap - 1) / cap;
   int sw = full_slabs && nsl > 1 ? cap : (E + nsl - 1) / nsl;
   if (u8) sw = ((sw + it.C - 1) / it.C) * it.C;
@@ -151,9 +151,11 @@ __device__ __forceinline__ void item_geometry(Item& it, const ItemInfo& inf, con
 }
 
 // Descending exclusive prefix of the radius histogram: start[b] is the first
-// ticket of radius b when tickets are handed out largest radius first.
+// ticket of radius b when tickets are handed out largest radius first. NT:
+// threads of the CTA (wsum holds NT / 32 ints).
+template <int NT = kThreads>
 __device__ __forceinline__ void bucket_starts(const unsigned int* hist, int nb, int* start, int* wsum) {
-  constexpr int per = kBuckets / kThreads;  // 4 positions per thread
+  constexpr int per = kBuckets / NT;  // positions per thread
   unsigned int v[per], run = 0;
   #pragma unroll
   for (int j = 0; j < per; ++j) {

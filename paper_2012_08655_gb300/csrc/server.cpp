@@ -325,6 +325,13 @@ int fovea_server_create(const fovea_server_config* cfg, fovea_server** out) {
   fovea_sigma_law law{FOVEA_LAW_LINEAR, 0.5, 0.02, 0.0, nullptr, 0.0, FOVEA_GRID_ANCHORED};
   int st = fovea_create(0, 0, 3, cfg->block, &law, FOVEA_U8_HWC, &s->ctx);
   if (st == FOVEA_OK) st = fovea::ctx_fault_word(s->ctx, &s->fault_dev);
+  // Every batch runs one fixed configuration (not one the batch autotuner
+  // chose for batches of its kind), so a request's result does not depend on
+  // what it is batched with.
+  if (st == FOVEA_OK) {
+    const fovea_config fixed{256, 0, 32, 1};
+    st = fovea_set_config(s->ctx, &fixed);
+  }
   // Size the batch buffers for the largest batch the arena can hold, so that
   // no batch grows them (a growth recaptures the batch graphs on this
   // thread, and the backlog that makes a batch large is when that hurts

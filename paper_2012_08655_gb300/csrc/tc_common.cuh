@@ -20,9 +20,37 @@ constexpr float kWScale = 4096.0f;          // taps scaled by 2^12
 constexpr float kWInv = 1.0f / 4096.0f;
 constexpr float kDScale = 1.0f / 16777216.0f;  // a staged byte b enters pass 1 as b * 2^-24
 constexpr float kVScale = 4096.0f;          // V = pass-1 accumulator * 2^12 (= 2^24 / 2^12)
-constexpr int kRingRow = 256;               // bytes per staged row: two 128-byte swizzled boxes
+constexpr int kRingRow = 256;               // bytes per staged row of the 8-warp kernels: two 128-byte boxes
 constexpr int kPairPad = 32;                // tap index -kPairPad is pair entry 0
-constexpr int kVHalves = 128 * 72;     // halves of one V array (max over C of 32C rows x VP)
+
+// Shapes of the mma.sync kernel with NW warps (NW = 4, 8 or 16): in pass 1
+// warp w owns staged bytes 32w .. 32w+31, so a staged row is 32 NW bytes
+// (NW / 4 tensor-map boxes of 128 bytes) and a slab holds up to 32 NW - 16
+// bytes (the row also holds up to 15 bytes of alignment padding).
+template <int NW>
+struct TcDims {
+  static_assert(NW == 4 || NW == 8 || NW == 16, "4, 8 or 16 warps");
+  static constexpr int NT = 32 * NW;
+  static constexpr int ROW = 32 * NW;
+  static constexpr int BOXES = NW / 4;
+  static constexpr int SLAB = ROW - 16;
+};
+
+// Pitch (halves) of the pass-2 operand rows V[(c, yo)][p] for C channels and
+// NW warps: the slab's pixels rounded up to 16, then to an odd multiple of 8
+// halves (16 bytes), so the 8 rows an ldmatrix reads fall in distinct banks.
+__host__ __device__ constexpr int tc_vp(int C, int NW) {
+  return ((((32 * NW - 16) / C + 15) / 16 * 16) / 8) % 2 ? (((32 * NW - 16) / C + 15) / 16 * 16)
+                                                          : (((32 * NW - 16) / C + 15) / 16 * 16) + 8;
+}
+__host__ __device__ constexpr int tc_vmax(int a, int b) { return a > b ? a : b; }
+// Halves of one V array: the largest 32 C x VP over C = 1 .. 4.
+__host__ __device__ constexpr int tc_vhalves(int NW) {
+  return tc_vmax(tc_vmax(32 * tc_vp(1, NW), 64 * tc_vp(2, NW)), tc_vmax(96 * tc_vp(3, NW), 128 * tc_vp(4, NW)));
+}
+// Pass-2 units (16-row m-tile x 8-column n-tile) per warp: the 2C x 4 units
+// of an item dealt to NW warps, unit u to warp u mod NW.
+__host__ __device__ constexpr int tc_units(int C, int NW) { return (8 * C + NW - 1) / NW; }
 
 __host__ __device__ inline int npair(int rmax) { return rmax + 56; }
 
@@ -97,13 +125,6 @@ __device__ __forceinline__ unsigned int pack_half2(__half a, __half b) {
   return (unsigned int)__half_as_ushort(a) | ((unsigned int)__half_as_ushort(b) << 16);
 }
 
-// Per channel count: pitch (halves) of the pass-2 operand rows V[(c, yo)][p]
-// (an odd multiple of 16 bytes, at least the slab's pixels rounded up to 16).
-template <int C> struct TcGeo;
-template <> struct TcGeo<1> { static constexpr int VP = 264; };
-template <> struct TcGeo<2> { static constexpr int VP = 136; };
-template <> struct TcGeo<3> { static constexpr int VP = 88; };
-template <> struct TcGeo<4> { static constexpr int VP = 72; };
 
 // No side effects: left to the compiler to schedule (independent chains interleave).
 __device__ __forceinline__ void mma16816(float (&d)[4], const unsigned int (&a)[4], unsigned int b0, unsigned int b1) {
@@ -142,13 +163,14 @@ __device__ __forceinline__ float tap_u(int m, int r, float c, float S) {
 
 // Tap-pair tables: entry j of the even table holds (w(m), w(m+1)) with
 // m = 2j - kPairPad, the odd table the pair starting one tap later; hi and lo
-// parts of the scaled taps w = u * 2^12.
+// parts of the scaled taps w = u * 2^12. NT: threads of the CTA.
+template <int NT = kThreads>
 __device__ __forceinline__ void make_pairs(unsigned int* P, int r, float c, float S, int np) {
   unsigned int* PEh = P;
   unsigned int* POh = P + np;
   unsigned int* PEl = P + 2 * np;
   unsigned int* POl = P + 3 * np;
-  for (int j = threadIdx.x; j < np; j += kThreads) {
+  for (int j = threadIdx.x; j < np; j += NT) {
     __half h[3], l[3];
     #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -205,15 +227,23 @@ __device__ __forceinline__ void ldsm_x4_t(unsigned int (&r)[4], const void* p) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(s));
 }
 
-template <int C, bool VT>
+template <int C, bool VT, int NW = 8>
 __device__ __forceinline__ size_t v_index(int c, int yo, int px) {
-  return VT ? (size_t)(px * C + c) * kVtPitch + yo : (size_t)(c * 32 + yo) * TcGeo<C>::VP + px;
+  return VT ? (size_t)(px * C + c) * kVtPitch + yo : (size_t)(c * 32 + yo) * tc_vp(C, NW) + px;
 }
 
-template <int C, bool VT = false>
+// Unit i of a warp (u = warp + NW i) exists: 8 C units are dealt to NW warps.
+template <int C, int NW>
+__device__ __forceinline__ bool tc_unit_exists(int warp, int i) {
+  return (8 * C) % NW == 0 ? true : warp + NW * i < 8 * C;
+}
+
+template <int C, bool VT = false, int NW = 8>
 __device__ __forceinline__ void tc_pass2_slab(const Item& it, const Slab& sl, const __half* Vh, const __half* Vl,
-                                              const float* CU, const unsigned int* P, int np, float (&acc2)[C][4]) {
-  constexpr int VP = TcGeo<C>::VP;
+                                              const float* CU, const unsigned int* P, int np,
+                                              float (&acc2)[tc_units(C, NW)][4]) {
+  constexpr int VP = tc_vp(C, NW);
+  constexpr int U = tc_units(C, NW);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int r = it.r;
@@ -226,13 +256,14 @@ __device__ __forceinline__ void tc_pass2_slab(const Item& it, const Slab& sl, co
   const unsigned int* Ql = P + 2 * np + (par2 ? np : 0);
   if (it.foldL && P0 == 0) {  // folded left column first: fixed summation order
     #pragma unroll
-    for (int i = 0; i < C; ++i) {
-      const int u = warp + 8 * i;
+    for (int i = 0; i < U; ++i) {
+      const int u = warp + NW * i;
+      if (!tc_unit_exists<C, NW>(warp, i)) continue;
       const int mt2 = u >> 2, nt2 = u & 3;
       #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int row = 16 * mt2 + g + 8 * h;
-        const size_t o = v_index<C, VT>(row >> 5, row & 31, 0);
+        const size_t o = v_index<C, VT, NW>(row >> 5, row & 31, 0);
         const float v = __half2float(Vh[o]) + __half2float(Vl[o]);
         #pragma unroll
         for (int cc = 0; cc < 2; ++cc) {
@@ -242,24 +273,26 @@ __device__ __forceinline__ void tc_pass2_slab(const Item& it, const Slab& sl, co
       }
     }
   }
-  // this warp's n-tile: u = warp + 8 i has u & 3 = warp & 3 for every i, so
-  // the tap fragments of a k-step are shared by the warp's C m-tiles
+  // this warp's n-tile: u = warp + NW i has u & 3 = warp & 3 for every i (NW
+  // is a multiple of 4), so the tap fragments of a k-step are shared by the
+  // warp's m-tiles
   const int nt2w = warp & 3;
   for (int kk = 0; kk < npx16; kk += 16) {
-    unsigned int a_h[C][4], a_l[C][4], bh[2], bl[2];
+    unsigned int a_h[U][4], a_l[U][4], bh[2], bl[2];
     {
       const int jb = (it.offx + P0 + kk + 2 * t - 8 * nt2w - g + kPairPad) >> 1;
       bh[0] = Qh[jb]; bh[1] = Qh[jb + 4];
       bl[0] = Ql[jb]; bl[1] = Ql[jb + 4];
     }
     #pragma unroll
-    for (int i = 0; i < C; ++i) {
-      const int u = warp + 8 * i;
+    for (int i = 0; i < U; ++i) {
+      if (!tc_unit_exists<C, NW>(warp, i)) continue;
+      const int u = warp + NW * i;
       const int mt2 = u >> 2;
       if (VT) {  // stored rows are pixels: transpose on load
         const int m0 = 16 * mt2 + ((lane >> 3) & 1) * 8;
         const int krow = kk + (lane & 7) + ((lane >> 4) & 1) * 8;
-        const size_t o = v_index<C, true>(m0 >> 5, m0 & 31, krow);
+        const size_t o = v_index<C, true, NW>(m0 >> 5, m0 & 31, krow);
         ldsm_x4_t(a_h[i], Vh + o);
         ldsm_x4_t(a_l[i], Vl + o);
       } else {
@@ -270,23 +303,27 @@ __device__ __forceinline__ void tc_pass2_slab(const Item& it, const Slab& sl, co
       }
     }
     #pragma unroll
-    for (int i = 0; i < C; ++i) mma16816(acc2[i], a_h[i], bh[0], bh[1]);
+    for (int i = 0; i < U; ++i)
+      if (tc_unit_exists<C, NW>(warp, i)) mma16816(acc2[i], a_h[i], bh[0], bh[1]);
     #pragma unroll
-    for (int i = 0; i < C; ++i) mma16816(acc2[i], a_h[i], bl[0], bl[1]);
+    for (int i = 0; i < U; ++i)
+      if (tc_unit_exists<C, NW>(warp, i)) mma16816(acc2[i], a_h[i], bl[0], bl[1]);
     #pragma unroll
-    for (int i = 0; i < C; ++i) mma16816(acc2[i], a_l[i], bh[0], bh[1]);
+    for (int i = 0; i < U; ++i)
+      if (tc_unit_exists<C, NW>(warp, i)) mma16816(acc2[i], a_l[i], bh[0], bh[1]);
   }
   {
     const int pr = it.EW - 1 - P0;  // folded right column after the last slab's products
     if (it.foldR && pr >= 0 && pr < npx) {
       #pragma unroll
-      for (int i = 0; i < C; ++i) {
-        const int u = warp + 8 * i;
+      for (int i = 0; i < U; ++i) {
+        if (!tc_unit_exists<C, NW>(warp, i)) continue;
+        const int u = warp + NW * i;
         const int mt2 = u >> 2, nt2 = u & 3;
         #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int row = 16 * mt2 + g + 8 * h;
-          const size_t o = v_index<C, VT>(row >> 5, row & 31, pr);
+          const size_t o = v_index<C, VT, NW>(row >> 5, row & 31, pr);
           const float v = __half2float(Vh[o]) + __half2float(Vl[o]);
           #pragma unroll
           for (int cc = 0; cc < 2; ++cc) {
@@ -302,14 +339,17 @@ __device__ __forceinline__ void tc_pass2_slab(const Item& it, const Slab& sl, co
 // Rounds the item's outputs (acc2, scaled by 2^12) to uint8, stages them in
 // ost (32 rows of 32 C bytes) and writes the block's rows with 16-byte
 // stores where the frame's alignment allows.
-template <int C>
-__device__ __forceinline__ void tc_write_output(const Item& it, unsigned char* ost, const float (&acc2)[C][4]) {
+template <int C, int NW = 8>
+__device__ __forceinline__ void tc_write_output(const Item& it, unsigned char* ost,
+                                                const float (&acc2)[tc_units(C, NW)][4]) {
+  constexpr int NT = TcDims<NW>::NT;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
   constexpr int opitch = 32 * C;
   #pragma unroll
-  for (int i = 0; i < C; ++i) {
-    const int u = warp + 8 * i;
+  for (int i = 0; i < tc_units(C, NW); ++i) {
+    const int u = warp + NW * i;
+    if (u >= 8 * C) continue;
     const int mt2 = u >> 2, nt2 = u & 3;
     #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -324,13 +364,13 @@ __device__ __forceinline__ void tc_write_output(const Item& it, unsigned char* o
   unsigned char* out = it.out + (size_t)it.y0 * it.pitch + (size_t)it.x0 * C;
   if (((((size_t)out) | it.pitch | (size_t)rowBytes) & 15) == 0) {
     const int nv = rowBytes >> 4;  // 16-byte pieces per row
-    for (int idx = tid; idx < it.bh * nv; idx += kThreads) {
+    for (int idx = tid; idx < it.bh * nv; idx += NT) {
       const int yo = idx / nv, v = idx - yo * nv;
       *reinterpret_cast<uint4*>(out + (size_t)yo * it.pitch + 16 * v) =
           *reinterpret_cast<const uint4*>(ost + yo * opitch + 16 * v);
     }
   } else {
-    for (int idx = tid; idx < it.bh * rowBytes; idx += kThreads) {
+    for (int idx = tid; idx < it.bh * rowBytes; idx += NT) {
       const int yo = idx / rowBytes, rem = idx - yo * rowBytes;
       out[(size_t)yo * it.pitch + rem] = ost[yo * opitch + rem];
     }
@@ -347,20 +387,21 @@ __device__ __forceinline__ void tc_write_output(const Item& it, unsigned char* o
 // the next item's index and record, so the work list's dependent loads
 // overlap the current item. Ends with the single-frame counter reset.
 // s_start: shared memory for rmax + 1 bucket starts (single frames).
-template <int RB, int C, bool FULL_SLABS = false, typename ItemFn>
+template <int RB, int C, bool FULL_SLABS = false, int NW = 8, typename ItemFn>
 __device__ __forceinline__ void tc_item_loop(const FrameSource& src, const CUtensorMap& tmap1, const Workspace& ws,
                                              int rmax, const BucketList& bl, int* s_start, ItemFn&& item_fn) {
+  constexpr int NT = TcDims<NW>::NT;
   __shared__ int s_state;
   __shared__ Item s_it;
   __shared__ float s_c;
   __shared__ const void* s_map;
-  __shared__ int s_wsum[kThreads / 32];
+  __shared__ int s_wsum[NW];
   const int tid = threadIdx.x;
 
   asm volatile("griddepcontrol.wait;" ::: "memory");
   const bool own_order = bl.list != nullptr;
   const int n_items = own_order ? (int)src.one_total : (int)ws.counters[CNT_NITEMS];
-  if (own_order) bucket_starts(ws.counters + CNT_HIST, bl.nb, s_start, s_wsum);
+  if (own_order) bucket_starts<NT>(ws.counters + CNT_HIST, bl.nb, s_start, s_wsum);
   const CUtensorMap* batch_maps =
       src.hdr ? reinterpret_cast<const CUtensorMap*>(reinterpret_cast<const char*>(src.hdr) + src.hdr->maps_offset)
               : nullptr;
@@ -411,7 +452,7 @@ __device__ __forceinline__ void tc_item_loop(const FrameSource& src, const CUten
             atomicOr(&ws.counters[CNT_ERROR], kFaultRadiusBound);
             state = 1;
           } else {
-            item_geometry(s_it, inf, fd, RB, FULL_SLABS);
+            item_geometry(s_it, inf, fd, RB, FULL_SLABS, TcDims<NW>::SLAB);
             s_c = inf.neg_half_inv_s2;
             s_map = !fd.tma ? nullptr : (batch_maps ? static_cast<const void*>(batch_maps + inf.frame)
                                                     : static_cast<const void*>(&tmap1));
@@ -432,7 +473,7 @@ __device__ __forceinline__ void tc_item_loop(const FrameSource& src, const CUten
     if (tid == 0) s_state = atomicAdd(&ws.counters[CNT_DONE_SIGMA], 1u) == gridDim.x - 1 ? 3 : 0;
     __syncthreads();
     if (s_state == 3) {
-      for (int j = tid; j < kBuckets; j += kThreads) ws.counters[CNT_HIST + j] = 0u;
+      for (int j = tid; j < kBuckets; j += NT) ws.counters[CNT_HIST + j] = 0u;
       if (tid == 0) {
         ws.counters[CNT_TICKET] = 0u;
         ws.counters[CNT_DONE_SIGMA] = 0u;

@@ -39,13 +39,14 @@ struct TcLayout {
 };
 
 // Offsets from the 1024-byte aligned start of the dynamic shared memory (the
-// 128-byte swizzle pattern repeats every 1024 bytes).
-__host__ __device__ inline TcLayout tc_layout(int rb, int rmax) {
+// 128-byte swizzle pattern repeats every 1024 bytes), for nw warps.
+__host__ __device__ inline TcLayout tc_layout(int rb, int rmax, int nw) {
   TcLayout L;
-  L.ring = 0;                                                  // u8 [stages][2][rb][128] (swizzled)
-  L.vh = L.ring + (size_t)tc_stages(rb) * rb * kRingRow;       // half [kVHalves]
-  L.vl = L.vh + (size_t)kVHalves * 2;                          // half [kVHalves]
-  L.cum = L.vl + (size_t)kVHalves * 2;                         // float [cum_len]
+  const size_t vh = (size_t)tc_vhalves(nw);
+  L.ring = 0;                                                  // u8 [stages][nw/4][rb][128] (swizzled)
+  L.vh = L.ring + (size_t)tc_stages(rb) * rb * (32 * nw);      // half [vh]
+  L.vl = L.vh + vh * 2;                                        // half [vh]
+  L.cum = L.vl + vh * 2;                                       // float [cum_len]
   L.pairs = L.cum + (size_t)((cum_len(rmax) + 3) & ~3) * 4;    // uint32 [4][npair]
   L.starts = L.pairs + (size_t)4 * npair(rmax) * 4;           // int [rmax + 1] bucket starts
   L.total = L.starts + (size_t)(rmax + 1) * 4 + 1024;          // + alignment slack
@@ -57,13 +58,15 @@ __host__ __device__ inline TcLayout tc_layout(int rb, int rmax) {
 // 0 at two points of the item (step 0 once the tables are built, step 1 once
 // the first chunk has arrived) to fetch the next item's record in the
 // background.
-template <int RB, int C, typename LookAhead>
+template <int RB, int C, int NW, typename LookAhead>
 __device__ __forceinline__ bool tc_item(const Item& it, float c_tap, unsigned char* ring, __half* Vh, __half* Vl,
                                         float* CU, unsigned int* P, int np,
                                         unsigned long long* bars, const void* map, bool map_in_global,
                                         int& gq0, unsigned int* err, LookAhead&& lookahead) {
-  constexpr int VP = TcGeo<C>::VP;
-  constexpr size_t stage_bytes = (size_t)RB * kRingRow;
+  using D = TcDims<NW>;
+  constexpr int VP = tc_vp(C, NW);
+  constexpr int NT = D::NT;
+  constexpr size_t stage_bytes = (size_t)RB * D::ROW;
   constexpr int kStagesTc = tc_stages(RB);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
@@ -73,23 +76,23 @@ __device__ __forceinline__ bool tc_item(const Item& it, float c_tap, unsigned ch
   // Raw uint8 chunks (slab s, rows k*RB ..) stream through the ring stages:
   // global chunk number gq0 + q uses stage (gq0 + q) % stages, and its
   // mbarrier completes for the ((gq0 + q) / stages)-th time.
-  auto issue = [&](int qq) {  // one thread: the chunk's two TMA boxes
+  auto issue = [&](int qq) {  // one thread: the chunk's NW / 4 TMA boxes
     const Slab cs = slab_of<true>(it, qq / it.nchunks);
     const int gq = gq0 + qq, stg = gq % kStagesTc;
     unsigned char* dst = ring + (size_t)stg * stage_bytes;
     const int x = (int)cs.src - cs.ph;  // 16-byte aligned byte column
     const int y = it.gy0 - it.ph + (qq % it.nchunks) * RB;
-    mbar_expect_tx(bars + stg, 2u * 128u * RB);
-    tma_load_2d(dst, map, x, y, bars + stg);
-    tma_load_2d(dst + 128 * RB, map, x + 128, y, bars + stg);
+    mbar_expect_tx(bars + stg, (unsigned int)D::BOXES * 128u * RB);
+    #pragma unroll
+    for (int bx = 0; bx < D::BOXES; ++bx) tma_load_2d(dst + 128 * RB * bx, map, x + 128 * bx, y, bars + stg);
   };
   auto load_plain = [&](int qq) {  // all threads: rows that TMA cannot load
     const Slab cs = slab_of<true>(it, qq / it.nchunks);
     unsigned char* dst = ring + (size_t)((gq0 + qq) % kStagesTc) * stage_bytes;
     const long long x0 = (long long)cs.src - cs.ph;
-    const int nb = min(256, (cs.ph + cs.sws + 31) & ~31);
+    const int nb = min(D::ROW, (cs.ph + cs.sws + 31) & ~31);
     const int y0 = it.gy0 - it.ph + (qq % it.nchunks) * RB;
-    for (int idx = threadIdx.x; idx < RB * nb; idx += kThreads) {
+    for (int idx = threadIdx.x; idx < RB * nb; idx += NT) {
       const int rho = idx / nb, b = idx - rho * nb;
       const int y = y0 + rho;
       const long long xb = x0 + b;
@@ -107,8 +110,8 @@ __device__ __forceinline__ bool tc_item(const Item& it, float c_tap, unsigned ch
   // publishes them).
   {
     const float S = warp_tap_sum(r, c_tap);
-    make_pairs(P, r, c_tap, S, np);
-    if ((it.foldT || it.foldB || it.foldL || it.foldR) && warp == kThreads / 32 - 1)
+    make_pairs<NT>(P, r, c_tap, S, np);
+    if ((it.foldT || it.foldB || it.foldL || it.foldR) && warp == NW - 1)
       make_cumulative_tc(CU, r, c_tap, S);
   }
   if (tid == 0) lookahead(0);
@@ -127,9 +130,9 @@ __device__ __forceinline__ bool tc_item(const Item& it, float c_tap, unsigned ch
   const int colw = 32 * warp;
 
   float acc1[2][4][4];
-  float acc2[C][4];
+  float acc2[tc_units(C, NW)][4];
   #pragma unroll
-  for (int i = 0; i < C; ++i)
+  for (int i = 0; i < tc_units(C, NW); ++i)
     #pragma unroll
     for (int k = 0; k < 4; ++k) acc2[i][k] = 0.f;
 
@@ -281,7 +284,7 @@ __device__ __forceinline__ bool tc_item(const Item& it, float c_tap, unsigned ch
       }
       // zero the columns px in [npx, npx16) that pass 2 reads
       const int zc = npx16 - npx;
-      for (int idx = tid; idx < C * 32 * zc; idx += kThreads) {
+      for (int idx = tid; idx < C * 32 * zc; idx += NT) {
         const int row = idx / zc, px = npx + (idx - row * zc);
         Vh[(size_t)row * VP + px] = __ushort_as_half(0);
         Vl[(size_t)row * VP + px] = __ushort_as_half(0);
@@ -289,7 +292,7 @@ __device__ __forceinline__ bool tc_item(const Item& it, float c_tap, unsigned ch
     }
     __syncthreads();
 
-    tc_pass2_slab<C>(it, sl, Vh, Vl, CU, P, np, acc2);
+    tc_pass2_slab<C, false, NW>(it, sl, Vh, Vl, CU, P, np, acc2);
   }
   if (!ok) {
     // a chunk never arrived: flag it, let the chunks still in flight land
@@ -307,19 +310,22 @@ __device__ __forceinline__ bool tc_item(const Item& it, float c_tap, unsigned ch
   gq0 += Q;
   __syncthreads();  // the ring is no longer read: it becomes the output stage
 
-  tc_write_output<C>(it, ring, acc2);
+  tc_write_output<C, NW>(it, ring, acc2);
   fence_proxy_async();  // the next item's TMA boxes overwrite the output stage
   return true;
 }
 
-template <int RB, int C>
-__global__ void __launch_bounds__(kThreads, 2)
+// Resident CTAs the register budget is set for: 4 warps x 4, 8 x 2, 16 x 1.
+__host__ __device__ constexpr int tc_min_blocks(int nw) { return nw == 4 ? 4 : (nw == 8 ? 2 : 1); }
+
+template <int RB, int C, int NW>
+__global__ void __launch_bounds__(32 * NW, tc_min_blocks(NW))
 tc_forward_kernel(const __grid_constant__ FrameSource src, Workspace ws, int rmax, BucketList bl,
                   const __grid_constant__ CUtensorMap tmap1) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  const TcLayout L = tc_layout(RB, rmax);
+  const TcLayout L = tc_layout(RB, rmax, NW);
   unsigned char* ring = smem + L.ring;
   __half* Vh = reinterpret_cast<__half*>(smem + L.vh);
   __half* Vl = reinterpret_cast<__half*>(smem + L.vl);
@@ -333,47 +339,62 @@ tc_forward_kernel(const __grid_constant__ FrameSource src, Workspace ws, int rma
     fence_proxy_async();
   }
   int gq0 = 0;  // chunks staged by this CTA so far (identical in every thread)
-  tc_item_loop<RB, C, true>(src, tmap1, ws, rmax, bl, reinterpret_cast<int*>(smem + L.starts),
+  tc_item_loop<RB, C, true, NW>(src, tmap1, ws, rmax, bl, reinterpret_cast<int*>(smem + L.starts),
                       [&](const Item& it, float c, const void* map, bool map_global, auto& lookahead) {
-                        return tc_item<RB, C>(it, c, ring, Vh, Vl, CU, P, np, s_bar, map, map_global, gq0,
-                                              ws.counters + CNT_ERROR, lookahead);
+                        return tc_item<RB, C, NW>(it, c, ring, Vh, Vl, CU, P, np, s_bar, map, map_global, gq0,
+                                                  ws.counters + CNT_ERROR, lookahead);
                       });
 }
 
-template <int RB, int C>
-void* tc_kernel_ptr() { return reinterpret_cast<void*>(&tc_forward_kernel<RB, C>); }
+template <int RB, int C, int NW>
+void* tc_kernel_ptr() { return reinterpret_cast<void*>(&tc_forward_kernel<RB, C, NW>); }
 
-template <int C>
+template <int C, int NW>
 void* pick_tc_rb(int rb) {
   switch (rb) {
-    case 16: return tc_kernel_ptr<16, C>();
-    case 64: return tc_kernel_ptr<64, C>();
-    default: return tc_kernel_ptr<32, C>();
+    case 16: return tc_kernel_ptr<16, C, NW>();
+    case 64: return tc_kernel_ptr<64, C, NW>();
+    default: return tc_kernel_ptr<32, C, NW>();
   }
 }
 
-void* pick_tc(int rb, int C) {
+template <int NW>
+void* pick_tc_c(int rb, int C) {
   switch (C) {
-    case 1: return pick_tc_rb<1>(rb);
-    case 2: return pick_tc_rb<2>(rb);
-    case 3: return pick_tc_rb<3>(rb);
-    default: return pick_tc_rb<4>(rb);
+    case 1: return pick_tc_rb<1, NW>(rb);
+    case 2: return pick_tc_rb<2, NW>(rb);
+    case 3: return pick_tc_rb<3, NW>(rb);
+    default: return pick_tc_rb<4, NW>(rb);
+  }
+}
+
+// Warps of the kernel a configuration runs: threads / 32 (128, 256 or 512
+// threads; anything else runs 256).
+int tc_warps(const FwdConfig& cfg) { return cfg.threads == 128 ? 4 : (cfg.threads == 512 ? 16 : 8); }
+
+void* pick_tc(const FwdConfig& cfg, int C) {
+  switch (tc_warps(cfg)) {
+    case 4: return pick_tc_c<4>(cfg.rows_per_chunk, C);
+    case 16: return pick_tc_c<16>(cfg.rows_per_chunk, C);
+    default: return pick_tc_c<8>(cfg.rows_per_chunk, C);
   }
 }
 
 }  // namespace
 
-size_t tc_forward_smem_bytes(const FwdConfig& cfg, int rmax) { return tc_layout(cfg.rows_per_chunk, rmax).total; }
+size_t tc_forward_smem_bytes(const FwdConfig& cfg, int rmax) {
+  return tc_layout(cfg.rows_per_chunk, rmax, tc_warps(cfg)).total;
+}
 
 int tc_forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int C) {
   const size_t smem = tc_forward_smem_bytes(cfg, rmax);
-  void* k = pick_tc(cfg.rows_per_chunk, C);
+  void* k = pick_tc(cfg, C);
   if (set_smem_attrs(reinterpret_cast<const void*>(k), smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kThreads, smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 32 * tc_warps(cfg), smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -383,7 +404,7 @@ int tc_forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int C) {
 cudaError_t launch_tc_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg, int rmax, int C,
                               int grid, cudaStream_t s, const BucketList& bl, bool pdl, const void* tmap_one) {
   const size_t smem = tc_forward_smem_bytes(cfg, rmax);
-  void* k = pick_tc(cfg.rows_per_chunk, C);
+  void* k = pick_tc(cfg, C);
   cudaError_t e = set_smem_attrs(reinterpret_cast<const void*>(k), smem);
   if (e != cudaSuccess) return e;
   BucketList b = bl;
@@ -393,7 +414,7 @@ cudaError_t launch_tc_forward(const FrameSource& src, const Workspace& ws, const
   void* args[] = {const_cast<FrameSource*>(&src), const_cast<Workspace*>(&ws), &rmax, &b, &map};
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(grid);
-  lc.blockDim = dim3(kThreads);
+  lc.blockDim = dim3(32 * tc_warps(cfg));
   lc.dynamicSmemBytes = smem;
   lc.stream = s;
   cudaLaunchAttribute attr[1];

@@ -88,6 +88,7 @@ _sig = {
     "fovea_get_config": (_i, [_vp, ctypes.POINTER(Config)]),
     "fovea_set_config": (_i, [_vp, ctypes.POINTER(Config)]),
     "fovea_autotune": (_i, [_vp, _i, ctypes.c_char_p]),
+    "fovea_autotune_batch": (_i, [_vp, ctypes.POINTER(Frame), _i, _i, ctypes.c_char_p, ctypes.POINTER(Config)]),
     "fovea_set_kernel_events": (_i, [_vp, _vp, _vp]),
     "fovea_destroy": (None, [_vp]),
     "fovea_render_noalloc": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _d, _d, _f, _f, _vp]),
@@ -363,6 +364,17 @@ class Context:
         _check(_lib.fovea_autotune(self._h, int(iters), p), "fovea_autotune")
         return self.get_config()
 
+    def autotune_batch(self, frames: Sequence["BatchFrame"], iters: int = 3, cache_path: Optional[str] = None) -> dict:
+        """Time the configurations on this batch (``fovea_autotune_batch``);
+        later batches like it render with the fastest. Returns it."""
+        arr = _frames_array(frames, self.device)
+        c = Config()
+        p = cache_path.encode() if cache_path else None
+        _check(_lib.fovea_autotune_batch(self._h, arr, len(frames), int(iters), p, ctypes.byref(c)),
+               "fovea_autotune_batch")
+        return {"threads": c.threads, "ctas_per_sm": c.ctas_per_sm, "rows_per_chunk": c.rows_per_chunk,
+                "tensor_cores": c.tensor_cores}
+
 
 def batch_context(block: int = 32) -> Context:
     """A batch-only context (``fovea_create`` with width = height = 0)."""
@@ -549,6 +561,11 @@ def _batch_ctx(block: int) -> Context:
 def foveate_batch(frames: Sequence[BatchFrame], block: int = 32, stream=None):
     """Render frames of mixed sizes in one batched launch sequence."""
     _batch_ctx(block).render_batch(frames, stream)
+
+
+def autotune_batch(frames: Sequence[BatchFrame], block: int = 32, iters: int = 3) -> dict:
+    """Autotune :func:`foveate_batch` for batches like this one."""
+    return _batch_ctx(block).autotune_batch(frames, iters)
 
 
 class FoveaFunction(torch.autograd.Function):

@@ -232,8 +232,24 @@ def test_every_config_gives_identical_output(fv, tc):
     torch.cuda.synchronize()
     for y in outs[1:]:
         assert torch.equal(y, outs[0])
+    if tc == 1:
+        # 128 and 512 threads cut the halo tile into narrower / wider column
+        # slabs, which regroups pass 2's fp32 sums: within 1 LSB, nearly all
+        # equal; within one thread count the chunk and CTA count change nothing
+        for nt in (128, 512):
+            outs_nt = []
+            for rb in (16, 64):
+                for ctas in (1, 0):
+                    ctx.set_config(nt, ctas, rb, tensor_cores=1)
+                    y = torch.empty_like(x)
+                    ctx.render(x, y, s.fix_x, s.fix_y)
+                    outs_nt.append(y)
+            torch.cuda.synchronize()
+            for y in outs_nt[1:]:
+                assert torch.equal(y, outs_nt[0])
+            assert_u8_close(outs_nt[0].cpu().numpy(), outs[0].cpu().numpy(), min_equal=0.999)
     cfg = ctx.autotune(iters=3)
-    assert cfg["rows_per_chunk"] in (16, 32, 64)
+    assert cfg["rows_per_chunk"] in (16, 32, 64) and cfg["threads"] in (128, 256, 512)
 
 
 # ---------------------------------------------------------------- argument errors
@@ -255,7 +271,7 @@ def test_argument_errors(fv):
 
 # ---------------------------------------------------------------- tensor-core kernel vs fp32 kernel
 
-@pytest.mark.parametrize("tc", [1, 2])
+@pytest.mark.parametrize("tc,threads", [(1, 256), (2, 256), (1, 128), (1, 512)])
 @pytest.mark.parametrize("W,H,C,B,fx,fy,k", [
     (1920, 1080, 3, 32, 960.0, 540.0, 0.02),
     (333, 221, 1, 32, 10.0, 200.0, 0.1),
@@ -263,17 +279,18 @@ def test_argument_errors(fv):
     (129, 77, 2, 8, 64.0, 38.0, 0.05),
     (256, 200, 3, 32, 250.0, 10.0, 0.7),
 ])
-def test_tensor_core_kernel_matches_fp32_kernel(fv, W, H, C, B, fx, fy, k, tc):
-    """Both tensor-core kernels (1: mma.sync; 2: vertical pass on tcgen05)
-    against the fp32 FMA kernel and the oracle; the last case has radii
-    above the tcgen05 kernel's bound, which falls back to mma.sync."""
+def test_tensor_core_kernel_matches_fp32_kernel(fv, W, H, C, B, fx, fy, k, tc, threads):
+    """Both tensor-core kernels (1: mma.sync with 128, 256 or 512 threads;
+    2: vertical pass on tcgen05) against the fp32 FMA kernel and the oracle;
+    the last case has radii above the tcgen05 kernel's bound, which falls
+    back to mma.sync."""
     img = wl.grating_frame(H, W, C, seed=W + C)
     x = to_dev(img)
     ctx = fv.Context(W, H, C, B, 0.5, k, fv.U8_HWC)
     ctx.set_config(256, 0, 32, tensor_cores=0)
     y32 = torch.empty_like(x)
     ctx.render(x, y32, fx, fy)
-    ctx.set_config(256, 0, 32, tensor_cores=tc)
+    ctx.set_config(threads, 0, 32, tensor_cores=tc)
     ytc = torch.empty_like(x)
     ctx.render(x, ytc, fx, fy)
     torch.cuda.synchronize()
