@@ -386,13 +386,15 @@ int fovea_render_noalloc(const void* in_dev, void* out_dev, int width, int heigh
                                           commit) ran out: the item was abandoned */
 #define FOVEA_FAULT_PIXEL_RADIUS 0x80u /* per-pixel path: a pixel's radius exceeded the launch's bound
                                           (internal); the pixel is written unblurred */
+#define FOVEA_FAULT_BOUNDS      0x100u /* bounds-checked builds (-DFOVEA_BOUNDS) only: a store fell outside
+                                          the buffer it belongs to and was skipped (internal) */
 
 /* Waits for `stream` (a cudaStream_t; the stream the context's calls were
  * ordered on), then reads and clears the context's device fault word. Stores
  * the word in *faults when faults is not NULL. Returns FOVEA_OK when no bit
  * was set; otherwise FOVEA_ETIMEOUT if FOVEA_FAULT_WAIT is set, else
  * FOVEA_ECUDA if an internal bit (ORDER, WORKLIST, BUCKETS, PIXEL_RADIUS,
- * RADIUS_BOUND, ADJ_BOUND) is set, else FOVEA_EINVAL (the caller's sigma map
+ * RADIUS_BOUND, ADJ_BOUND, BOUNDS) is set, else FOVEA_EINVAL (the caller's sigma map
  * was out of its declared range). FOVEA_ECUDA also when the stream or the
  * copy fails. The word accumulates over every call made since the last
  * check, so one check after a sequence of calls covers all of them. Not in

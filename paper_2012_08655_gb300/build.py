@@ -18,6 +18,12 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfovea.so")
+# Bounds-checked variant (-DFOVEA_BOUNDS): every global store and the tensor-
+# core kernels' shared-memory stores check their address against the buffer
+# they belong to, record FOVEA_FAULT_BOUNDS and skip the access instead of
+# writing out of bounds. A debugging aid, loaded through FOVEA_LIBRARY.
+BUILD_BOUNDS = os.path.join(HERE, "_build_bounds")
+LIB_BOUNDS = os.path.join(HERE, "libfovea_bounds.so")
 
 SOURCES = ["sigma.cu", "forward.cu", "tc_forward.cu", "umma_forward.cu", "pixel_forward.cu", "pyramid.cu", "ssim.cu", "adjoint.cu", "noalloc.cu", "peak.cu",
            "api.cu", "tune.cpp", "server.cpp"]
@@ -44,15 +50,19 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile (if out of date) and return the path of libfovea.so."""
+def build(force: bool = False, verbose: bool = False, extra_flags=(), bounds: bool = False) -> str:
+    """Compile (if out of date) and return the path of libfovea.so (or, with
+    ``bounds``, of the bounds-checked libfovea_bounds.so)."""
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    build_dir, lib = (BUILD_BOUNDS, LIB_BOUNDS) if bounds else (BUILD, LIB)
+    if bounds:
+        extra_flags = (*extra_flags, "-DFOVEA_BOUNDS")
+    os.makedirs(build_dir, exist_ok=True)
     common = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "fovea.h")]
     procs, objs = [], []
     for src in SOURCES:
         path = os.path.join(CSRC, src)
-        obj = os.path.join(BUILD, src + ".o")
+        obj = os.path.join(build_dir, src + ".o")
         objs.append(obj)
         if force or _stale(obj, [path, *common, __file__]):
             cmd = [nvcc, *_flags(extra_flags), "-c", path, "-o", obj]
@@ -71,15 +81,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if failed:
         msg = "\n".join(f"--- {s}\n{o}" for s, o in failed)
         raise RuntimeError(f"libfovea build failed:\n{msg}")
-    if force or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread", "-ldl", "-lrt"]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         subprocess.check_call(cmd)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, bounds="--bounds" in sys.argv))

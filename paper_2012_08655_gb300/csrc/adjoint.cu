@@ -212,7 +212,9 @@ adjoint_kernel(FrameSource src, Workspace ws, int rmax) {
             #pragma unroll
             for (int e = 0; e < 4; ++e) {
               const int col = 4 * q + e;
-              if (col < SWx && v[e] != 0.f) atomicAdd(rowp + col, v[e]);
+              if (col < SWx && v[e] != 0.f &&
+                  in_bounds(rowp + col, 4, gin, planePitch * C * 4, ws.counters + CNT_ERROR))
+                atomicAdd(rowp + col, v[e]);
             }
           }
         }

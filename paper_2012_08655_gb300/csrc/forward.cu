@@ -332,8 +332,10 @@ forward_kernel(FrameSource src, Workspace ws, int rmax, int row_bytes, BucketLis
         for (int j = 0; j < 8; ++j) {
           const int x = xg + j;
           if (x < it.bw) {
-            out[x] = acc2[j].x;
-            if (second) out[it.W + x] = acc2[j].y;
+            const size_t plane_bytes = (size_t)it.W * it.H * it.C * 4;
+            if (in_bounds(out + x, 4, it.out, plane_bytes, ws.counters + CNT_ERROR)) out[x] = acc2[j].x;
+            if (second && in_bounds(out + it.W + x, 4, it.out, plane_bytes, ws.counters + CNT_ERROR))
+              out[it.W + x] = acc2[j].y;
           }
         }
       }
@@ -353,7 +355,8 @@ forward_kernel(FrameSource src, Workspace ws, int rmax, int row_bytes, BucketLis
       unsigned char* out = it.out + (size_t)it.y0 * it.pitch + (size_t)it.x0 * it.C;
       for (int idx = tid; idx < it.bh * rowBytes; idx += kThreads) {
         const int yo = idx / rowBytes, rem = idx - yo * rowBytes;
-        out[(size_t)yo * it.pitch + rem] = ost[yo * opitch + rem];
+        unsigned char* o = out + (size_t)yo * it.pitch + rem;
+        if (in_bounds(o, 1, it.out, (size_t)it.H * it.pitch, ws.counters + CNT_ERROR)) *o = ost[yo * opitch + rem];
       }
     }
   }

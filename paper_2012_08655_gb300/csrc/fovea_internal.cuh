@@ -124,6 +124,36 @@ constexpr unsigned int kFaultWorklist = FOVEA_FAULT_WORKLIST;
 constexpr unsigned int kFaultBuckets = FOVEA_FAULT_BUCKETS;
 constexpr unsigned int kFaultWait = FOVEA_FAULT_WAIT;
 constexpr unsigned int kFaultPixelRadius = FOVEA_FAULT_PIXEL_RADIUS;
+constexpr unsigned int kFaultBounds = FOVEA_FAULT_BOUNDS;
+
+// Bounds-checked builds (-DFOVEA_BOUNDS): stores check their address first.
+#if defined(FOVEA_BOUNDS)
+constexpr bool kBoundsChecks = true;
+#else
+constexpr bool kBoundsChecks = false;
+#endif
+
+// True when [p, p + n) lies inside [base, base + bytes). Otherwise (bounds-
+// checked builds only) records kFaultBounds in *fault (if not null) and
+// returns false, and the caller skips the access. Always true, and free, in
+// ordinary builds.
+__device__ __forceinline__ bool in_bounds(const void* p, size_t n, const void* base, size_t bytes,
+                                          unsigned int* fault) {
+  if (!kBoundsChecks) return true;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p), b = reinterpret_cast<uintptr_t>(base);
+  if (a >= b && a - b <= bytes && n <= bytes - (a - b)) return true;
+  if (fault) atomicOr(fault, kFaultBounds);
+  return false;
+}
+
+// The same for shared memory, against the CTA's dynamic shared memory.
+extern __shared__ __align__(16) unsigned char fovea_dyn_smem[];
+__device__ __forceinline__ bool smem_in_bounds(const void* p, size_t n, unsigned int* fault) {
+  if (!kBoundsChecks) return true;
+  unsigned int dyn;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+  return in_bounds(p, n, fovea_dyn_smem, dyn, fault);
+}
 
 // Sigma and radius of block (bx, by) of a frame: the sigma law at the
 // block's nominal centre, or the frame's per-block map (r = ceil(3 sigma) of

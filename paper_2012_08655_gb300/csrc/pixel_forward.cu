@@ -274,7 +274,8 @@ pixel_tc_kernel(PixelParams pp) {
         if (y >= H) continue;
         unsigned char* op = out + ((size_t)y * W + x) * C;
         #pragma unroll
-        for (int c = 0; c < C; ++c) op[c] = quant_u8(o[rh][c]);
+        for (int c = 0; c < C; ++c)
+          if (in_bounds(op + c, 1, out, (size_t)W * H * C, pp.err)) op[c] = quant_u8(o[rh][c]);
       }
     }
   }
@@ -361,9 +362,11 @@ pixel_fp32_kernel(PixelParams pp, int rb) {
   #pragma unroll
   for (int ch = 0; ch < C; ++ch) {
     if (U8) {
-      static_cast<unsigned char*>(pp.out)[((size_t)y * W + x) * C + ch] = quant_u8(acc[ch]);
+      unsigned char* o = static_cast<unsigned char*>(pp.out) + ((size_t)y * W + x) * C + ch;
+      if (in_bounds(o, 1, pp.out, (size_t)W * H * C, pp.err)) *o = quant_u8(acc[ch]);
     } else {
-      static_cast<float*>(pp.out)[((size_t)ch * H + y) * W + x] = acc[ch];
+      float* o = static_cast<float*>(pp.out) + ((size_t)ch * H + y) * W + x;
+      if (in_bounds(o, 4, pp.out, (size_t)W * H * C * 4, pp.err)) *o = acc[ch];
     }
   }
 }

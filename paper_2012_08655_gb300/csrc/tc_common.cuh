@@ -338,10 +338,11 @@ __device__ __forceinline__ void tc_pass2_slab(const Item& it, const Slab& sl, co
 
 // Rounds the item's outputs (acc2, scaled by 2^12) to uint8, stages them in
 // ost (32 rows of 32 C bytes) and writes the block's rows with 16-byte
-// stores where the frame's alignment allows.
+// stores where the frame's alignment allows. fault: the fault word that
+// bounds-checked builds report stray stores in.
 template <int C, int NW = 8>
 __device__ __forceinline__ void tc_write_output(const Item& it, unsigned char* ost,
-                                                const float (&acc2)[tc_units(C, NW)][4]) {
+                                                const float (&acc2)[tc_units(C, NW)][4], unsigned int* fault) {
   constexpr int NT = TcDims<NW>::NT;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
@@ -356,23 +357,26 @@ __device__ __forceinline__ void tc_write_output(const Item& it, unsigned char* o
       const int row = 16 * mt2 + g + ((e >> 1) << 3);
       const int c = row >> 5, yo = row & 31;
       const int x = 8 * nt2 + 2 * t + (e & 1);
-      ost[yo * opitch + x * C + c] = quant_u8(acc2[i][e] * kWInv);
+      unsigned char* o = ost + yo * opitch + x * C + c;
+      if (smem_in_bounds(o, 1, fault)) *o = quant_u8(acc2[i][e] * kWInv);
     }
   }
   __syncthreads();
   const int rowBytes = it.bw * C;
+  const size_t frame_bytes = (size_t)it.H * it.pitch;
   unsigned char* out = it.out + (size_t)it.y0 * it.pitch + (size_t)it.x0 * C;
   if (((((size_t)out) | it.pitch | (size_t)rowBytes) & 15) == 0) {
     const int nv = rowBytes >> 4;  // 16-byte pieces per row
     for (int idx = tid; idx < it.bh * nv; idx += NT) {
       const int yo = idx / nv, v = idx - yo * nv;
-      *reinterpret_cast<uint4*>(out + (size_t)yo * it.pitch + 16 * v) =
-          *reinterpret_cast<const uint4*>(ost + yo * opitch + 16 * v);
+      uint4* o = reinterpret_cast<uint4*>(out + (size_t)yo * it.pitch + 16 * v);
+      if (in_bounds(o, 16, it.out, frame_bytes, fault)) *o = *reinterpret_cast<const uint4*>(ost + yo * opitch + 16 * v);
     }
   } else {
     for (int idx = tid; idx < it.bh * rowBytes; idx += NT) {
       const int yo = idx / rowBytes, rem = idx - yo * rowBytes;
-      out[(size_t)yo * it.pitch + rem] = ost[yo * opitch + rem];
+      unsigned char* o = out + (size_t)yo * it.pitch + rem;
+      if (in_bounds(o, 1, it.out, frame_bytes, fault)) *o = ost[yo * opitch + rem];
     }
   }
 }

@@ -75,7 +75,11 @@ __device__ __forceinline__ bool tc_item(const Item& it, float c_tap, unsigned ch
 
   // Raw uint8 chunks (slab s, rows k*RB ..) stream through the ring stages:
   // global chunk number gq0 + q uses stage (gq0 + q) % stages, and its
-  // mbarrier completes for the ((gq0 + q) / stages)-th time.
+  // mbarrier completes for the ((gq0 + q) / stages)-th time. gq0 counts the
+  // chunks loaded by TMA only: chunks of an item staged with plain loads
+  // (a frame whose rows TMA cannot address) complete no barrier phase, so
+  // they must not advance it, or a later item of the same launch would wait
+  // for the wrong phase parity.
   auto issue = [&](int qq) {  // one thread: the chunk's NW / 4 TMA boxes
     const Slab cs = slab_of<true>(it, qq / it.nchunks);
     const int gq = gq0 + qq, stg = gq % kStagesTc;
@@ -98,7 +102,8 @@ __device__ __forceinline__ bool tc_item(const Item& it, float c_tap, unsigned ch
       const long long xb = x0 + b;
       unsigned char v = 0;
       if (y >= 0 && y < it.H && xb < (long long)it.pitch) v = it.in[(size_t)y * it.pitch + (size_t)xb];
-      dst[ring_off<RB>(rho, b)] = v;
+      unsigned char* o = dst + ring_off<RB>(rho, b);
+      if (smem_in_bounds(o, 1, err)) *o = v;
     }
   };
   if (map && tid == 0) {
@@ -276,8 +281,10 @@ __device__ __forceinline__ bool tc_item(const Item& it, float c_tap, unsigned ch
               const __half h = __float2half_rn(v);
               const __half l = __float2half_rn(v - __half2float(h));
               const size_t o = (size_t)(c * 32 + 16 * mt + g + 8 * hh) * VP + px;
-              Vh[o] = h;
-              Vl[o] = l;
+              if (smem_in_bounds(Vh + o, 2, err) && smem_in_bounds(Vl + o, 2, err)) {
+                Vh[o] = h;
+                Vl[o] = l;
+              }
             }
           }
         }
@@ -286,8 +293,11 @@ __device__ __forceinline__ bool tc_item(const Item& it, float c_tap, unsigned ch
       const int zc = npx16 - npx;
       for (int idx = tid; idx < C * 32 * zc; idx += NT) {
         const int row = idx / zc, px = npx + (idx - row * zc);
-        Vh[(size_t)row * VP + px] = __ushort_as_half(0);
-        Vl[(size_t)row * VP + px] = __ushort_as_half(0);
+        const size_t o = (size_t)row * VP + px;
+        if (smem_in_bounds(Vh + o, 2, err) && smem_in_bounds(Vl + o, 2, err)) {
+          Vh[o] = __ushort_as_half(0);
+          Vl[o] = __ushort_as_half(0);
+        }
       }
     }
     __syncthreads();
@@ -307,10 +317,10 @@ __device__ __forceinline__ bool tc_item(const Item& it, float c_tap, unsigned ch
     __syncthreads();
     return false;
   }
-  gq0 += Q;
+  if (map) gq0 += Q;
   __syncthreads();  // the ring is no longer read: it becomes the output stage
 
-  tc_write_output<C, NW>(it, ring, acc2);
+  tc_write_output<C, NW>(it, ring, acc2, err);
   fence_proxy_async();  // the next item's TMA boxes overwrite the output stage
   return true;
 }
@@ -338,7 +348,7 @@ tc_forward_kernel(const __grid_constant__ FrameSource src, Workspace ws, int rma
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     fence_proxy_async();
   }
-  int gq0 = 0;  // chunks staged by this CTA so far (identical in every thread)
+  int gq0 = 0;  // chunks this CTA has loaded by TMA so far (identical in every thread)
   tc_item_loop<RB, C, true, NW>(src, tmap1, ws, rmax, bl, reinterpret_cast<int*>(smem + L.starts),
                       [&](const Item& it, float c, const void* map, bool map_global, auto& lookahead) {
                         return tc_item<RB, C, NW>(it, c, ring, Vh, Vl, CU, P, np, s_bar, map, map_global, gq0,

@@ -152,7 +152,12 @@ __device__ __forceinline__ void make_strips(__half* S2, int nent, int r, float c
 }
 
 // One item. bars: TMA ring stages; mbar_mma / conv_full[kA1Bufs]: MMA
-// completion and conversion completion per A1 buffer. gq0: chunks this CTA has staged so far (identical in all threads).
+// completion and conversion completion per A1 buffer. gq0: chunks this CTA
+// has staged so far, gt0: those of them loaded by TMA (identical in all
+// threads). The conversion and MMA barriers complete a phase for every
+// chunk; a ring stage's barrier only for chunks loaded by TMA, so its phase
+// parity follows gt0 (items of frames that TMA cannot address stage their
+// rows with plain loads).
 template <int RB, int C, typename LookAhead>
 __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned char* ring, __half* A1, __half* Vh,
                                         __half* Vl, __half* Sh, float* CU, unsigned int* P,
@@ -160,7 +165,8 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
                                         int* s_tile_has, volatile int* s_abort,
                                         unsigned long long* bars, unsigned long long* mbar_mma,
                                         unsigned long long* conv_full, const void* map,
-                                        bool map_in_global, int& gq0, unsigned int* err, LookAhead&& lookahead) {
+                                        bool map_in_global, int& gq0, int& gt0, unsigned int* err,
+                                        LookAhead&& lookahead) {
   constexpr size_t stage_bytes = (size_t)RB * kRingRow;
   constexpr int kStages = um_stages(RB);
   constexpr int kTileBytes = a1_tile_bytes(RB);
@@ -172,7 +178,7 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
 
   auto issue = [&](int qq) {  // one thread: the chunk's two TMA boxes
     const Slab cs = slab_of<true>(it, qq / it.nchunks);
-    const int gq = gq0 + qq, stg = gq % kStages;
+    const int gt = gt0 + qq, stg = gt % kStages;
     unsigned char* dst = ring + (size_t)stg * stage_bytes;
     const int x = (int)cs.src - cs.ph;
     const int y = it.gy0 - it.ph + (qq % it.nchunks) * RB;
@@ -276,7 +282,8 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
         const int qq = qs + k, gq = gq0 + qq;
         const int R0 = k * RB;
         if (map) {
-          if (!mbar_wait(bars + gq % kStages, (unsigned int)(gq / kStages) & 1u)) *s_abort = 1;
+          const int gt = gt0 + qq;
+          if (!mbar_wait(bars + gt % kStages, (unsigned int)(gt / kStages) & 1u)) *s_abort = 1;
         } else {
           asm volatile("bar.sync 1, 224;" ::: "memory");  // converters done with this stage's old rows
           load_plain_conv(qq, ct);
@@ -285,7 +292,7 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
         // the MMAs of chunk gq - kA1Bufs read the A1 buffer this chunk is converted into
         if (gq >= kA1Bufs && !mbar_wait(&mbar_mma[gq % kA1Bufs], (unsigned int)((gq - kA1Bufs) / kA1Bufs) & 1u))
           *s_abort = 1;
-        const unsigned char* st = ring + (size_t)(gq % kStages) * stage_bytes;
+        const unsigned char* st = ring + (size_t)(((map ? gt0 : gq0) + qq) % kStages) * stage_bytes;
         __half* a1b = A1 + (size_t)(gq % kA1Bufs) * kTileBytes;
         // ---- convert: 8 columns x 4 rows per work unit, transposed into
         // K-major core matrices; stash the folded edge rows as floats
@@ -425,7 +432,7 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
     if (tid == 0) {
       atomicOr(err, kFaultWait);
       for (int qq = q + 1; qq < issued; ++qq) {
-        const int g2 = gq0 + qq;
+        const int g2 = gt0 + qq;
         mbar_wait(bars + g2 % kStages, (unsigned int)(g2 / kStages) & 1u);
       }
     }
@@ -433,8 +440,9 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
     return false;
   }
   gq0 += Q;
+  if (map) gt0 += Q;
   __syncthreads();  // the ring is no longer read: it becomes the output stage
-  tc_write_output<C>(it, ring, acc2);
+  tc_write_output<C>(it, ring, acc2, err);
   fence_proxy_async();  // the next item's TMA boxes overwrite the output stage
   return true;
 }
@@ -485,12 +493,12 @@ umma_forward_kernel(const __grid_constant__ FrameSource src, Workspace ws, int r
   __syncthreads();
   tc05_fence_after();
   const unsigned int tmem = s_tmem;
-  int gq0 = 0;
+  int gq0 = 0, gt0 = 0;
   tc_item_loop<RB, C>(src, tmap1, ws, rmax, bl, reinterpret_cast<int*>(smem + L.starts),
                       [&](const Item& it, float c, const void* map, bool map_global, auto& lookahead) {
                         return um_item<RB, C>(it, c, ring, A1, Vh, Vl, Sh, CU, P, edge, foldw, np, nent, tmem,
                                               s_tile_has, &s_abort, s_bar, s_mma, s_conv, map, map_global, gq0,
-                                              ws.counters + CNT_ERROR, lookahead);
+                                              gt0, ws.counters + CNT_ERROR, lookahead);
                       });
   tc05_fence_before();
   __syncthreads();  // every MMA was waited for before its accumulator was read

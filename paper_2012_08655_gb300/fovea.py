@@ -20,7 +20,9 @@ from typing import Optional, Sequence
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfovea.so")
+# FOVEA_LIBRARY may name another build of the library (the bounds-checked
+# libfovea_bounds.so); by default the package's own libfovea.so.
+LIB_PATH = os.environ.get("FOVEA_LIBRARY") or os.path.join(_HERE, "libfovea.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
@@ -36,6 +38,7 @@ MAX_BLOCK = 256
 # device fault bits (FOVEA_FAULT_* of include/fovea.h), reported by Context.check()
 FAULT_SIGMA_RANGE, FAULT_RADIUS_BOUND, FAULT_ADJ_BOUND, FAULT_ORDER = 0x01, 0x02, 0x04, 0x08
 FAULT_WORKLIST, FAULT_BUCKETS, FAULT_WAIT, FAULT_PIXEL_RADIUS = 0x10, 0x20, 0x40, 0x80
+FAULT_BOUNDS = 0x100
 
 
 LAW_LINEAR, LAW_GEISLER_PERRY, LAW_MAP = 0, 1, 2

@@ -45,6 +45,37 @@ def test_mixed_batch_full_size(fv):
                         min_equal=0.99)
 
 
+@pytest.mark.parametrize("tc,threads", [(1, 256), (1, 128), (1, 512), (2, 256)])
+def test_batch_mixing_tma_and_plain_frames(fv, tc, threads):
+    """uint8 RGB frames of one batch whose rows TMA can load (16-byte
+    aligned pitch) and whose rows it cannot (odd pitch: plain loads), in
+    alternation, on both tensor-core kernels and every thread count: every
+    frame within 1 LSB of the oracle and no device fault. (Plain-loaded items
+    must not advance the TMA ring's phase count.)"""
+    sizes = [(640, 480), (33, 65), (480, 320), (101, 77), (1280, 720), (7, 300), (224, 224)]
+    g = wl.rng(77)
+    frames, imgs = [], []
+    for i, (w, h) in enumerate(sizes):
+        img = wl.grating_frame(h, w, 3, seed=90 + i)
+        x = to_dev(img)
+        fx, fy = float(np.float32(g.uniform(0, w))), float(np.float32(g.uniform(0, h)))
+        frames.append(fv.BatchFrame(x, torch.empty_like(x), fx, fy, 0.5, 0.03))
+        imgs.append(img)
+    ctx = fv.batch_context(32)
+    ctx.set_config(threads, 0, 32, tensor_cores=tc)
+    for rep in range(2):  # the second launch starts from the barrier phases the first one left
+        for f in frames:
+            f.out.zero_()
+        ctx.render_batch(frames)
+        assert ctx.check() == 0
+    torch.cuda.synchronize()
+    for i, (f, img) in enumerate(zip(frames, imgs)):
+        h, w = img.shape[:2]
+        blocks = sample_blocks(w, h, 32, f.fix_x, f.fix_y, n_random=8, seed=i)
+        ref = oracle.forward_u8(img, 32, f.fix_x, f.fix_y, 0.5, 0.03, "hwc", blocks=blocks)
+        assert_u8_close(f.out.cpu().numpy(), ref, mask=block_mask(w, h, 32, blocks, "hwc", 3), min_equal=0.99)
+
+
 def test_batch_of_mixed_formats_and_channels(fv):
     """A batch mixing uint8 HWC (1 and 3 channels) and float32 CHW frames of
     ragged sizes, checked frame by frame against the oracle."""
