@@ -396,6 +396,43 @@ def batched_leg(fv, torch):
                     "kernel does the work as fp16 MMAs, so the figure can exceed the FP32 peak"}
 
 
+def sharded_batched_leg(fv, torch, world: int, rank: int, reps: int = 10):
+    """The 64-frame mixed batch split over the ranks by estimated cost (LPT,
+    the same assignment on every rank): each rank renders its frames as one
+    autotuned batch on its GPU; time = max over ranks. Whole-job Mpix/s."""
+    from paper_2012_08655_gb300 import replicas
+    from paper_2012_08655_gb300 import workloads as wl
+    params = wl.mixed_batch_params(seed=0)
+    costs = [replicas.frame_cost(w, h, 3, replicas.frame_rmax(w, h, fx, fy, 0.5, k)) for (w, h, fx, fy, k) in params]
+    mine = replicas.shard_frames(costs, world, rank)
+    frames = []
+    for i in mine:
+        w, h, fx, fy, k = params[i]
+        x = torch.from_numpy(wl.grating_frame(h, w, 3, seed=w)).cuda()
+        frames.append(fv.BatchFrame(x, torch.empty_like(x), fx, fy, 0.5, k))
+    cfg = fv.autotune_batch(frames, iters=3) if frames else None
+    for _ in range(3):
+        if frames:
+            fv.foveate_batch(frames)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        if frames:
+            fv.foveate_batch(frames)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(e0.elapsed_time(e1) / reps, world)
+    px = sum(w * h for (w, h, _, _, _) in params)
+    return {"workload": "the 64-frame mixed batch split over the ranks", "ms": ms, "mpix_s": px / ms / 1e3,
+            "frames_per_rank": [len(replicas.shard_frames(costs, world, r)) for r in range(world)],
+            "rank0_config": cfg,
+            "parallelism": f"frames sharded over {world} ranks by estimated cost (LPT), one batched launch per "
+                           "GPU, max over ranks; no collective on the data path"}
+
+
 def train_leg(fv, torch, reps: int = 20):
     """32x3x224x224 float32 batch (sigma = 0.5 + 0.08 e, random fixations):
     forward and backward through the autograd function (batched render and
@@ -622,13 +659,17 @@ def pixelwise_leg(fv, torch, reps: int = 20):
     return res
 
 
-def served_leg(fv, torch, seconds: float, max_batch: int):
-    """Replay the Poisson request stream through the serving loop."""
+def served_leg(fv, torch, seconds: float, max_batch: int, world: int = 1, rank: int = 0):
+    """Replay the Poisson request stream through the serving loop. With
+    world > 1 each rank serves the requests of its streams (stream s on rank
+    s mod world) on its own GPU and rank 0 merges the latencies."""
     import numpy as np
 
+    from paper_2012_08655_gb300 import replicas
     from paper_2012_08655_gb300 import workloads as wl
     stream = wl.served_stream(seed=0, duration_s=seconds)
-    reqs = stream.requests
+    mine = set(replicas.shard_streams(len(stream.stream_shapes), world, rank))
+    reqs = [r for r in stream.requests if r.stream in mine]
     src, rings = {}, {}
     for s, (w, h, c) in enumerate(stream.stream_shapes):
         src[s] = torch.from_numpy(wl.grating_frame(h, w, c, seed=100 + s)).pin_memory()
@@ -684,6 +725,17 @@ def served_leg(fv, torch, seconds: float, max_batch: int):
     # Where the slowest 1 % of requests spend their time: waiting for
     # admission, waiting for their input copy and batch launch, and from the
     # batch launch until the worker saw their output copy finish.
+    if world > 1:
+        parts = replicas.gather_to_rank0({"lat": lat.tolist(), "px": px, "span": span, "n": len(reqs),
+                                          "bs": bs.tolist(), "errors": int(sum(1 for _, t in done if t["status"]))})
+        if parts is None:
+            return None
+        p50, p99 = replicas.merged_percentiles([p["lat"] for p in parts])
+        return {"p50_ms": p50, "p99_ms": p99, "mpix_s": sum(p["px"] for p in parts) / max(p["span"] for p in parts) / 1e6,
+                "requests": sum(p["n"] for p in parts), "errors": sum(p["errors"] for p in parts),
+                "mean_batch": float(np.mean(np.concatenate([np.asarray(p["bs"]) for p in parts]))),
+                "parallelism": f"streams sharded over {world} ranks (stream s on rank s mod {world}), one serving "
+                               "loop per GPU, latencies merged on rank 0; no collective on the data path"}
     tail = lat >= np.percentile(lat, 99)
     ph = np.array([[t["admit_us"] - t["arrival_us"], t["start_us"] - t["admit_us"], t["done_us"] - t["start_us"]]
                    for _, t in done]) * 1e-3
@@ -930,6 +982,12 @@ def run_ours(args):
         served["device_only"] = served_device_only(fv, torch)
         extras["served"] = served
         extras["saturated"] = saturated_leg(fv, torch, args.served_seconds)
+
+    if world > 1 and not args.no_extras:
+        extras["sharded_batch"] = sharded_batched_leg(fv, torch, world, rank)
+        served = served_leg(fv, torch, args.served_seconds, 64, world, rank)
+        if rank == 0:
+            extras["served_sharded"] = served
 
     cpu = cpu_oracle_sample() if (rank == 0 and world == 1 and not args.no_cpu) else None
     if rank == 0:
