@@ -276,7 +276,9 @@ typedef struct {
                          fp32 accumulation): 1 both passes on mma.sync; 2 the
                          vertical pass on tcgen05 with its accumulator in tensor
                          memory (radius bound <= 255 and 16 or 32 rows per chunk,
-                         else as 1); 0: fp32 FMA kernel */
+                         else as 1); 3 both passes on tcgen05, accumulators in
+                         tensor memory (RGB frames, radius bound <= 511, 16 or
+                         32 rows per chunk, else as 1); 0: fp32 FMA kernel */
 } fovea_config;
 
 /* Copy the context's current configuration into *cfg. FOVEA_EINVAL for a
@@ -287,7 +289,7 @@ int fovea_get_config(const fovea_ctx* ctx, fovea_config* cfg);
  * fixes one CUDA block per fragment). FOVEA_EUNSUPPORTED for threads other
  * than 128, 256 or 512 or rows_per_chunk other than 16, 32 or 64;
  * FOVEA_EINVAL for a null argument, ctas_per_sm outside 0..8 or tensor_cores
- * outside 0..2. A CTA count above what fits is reduced to what fits at
+ * outside 0..3. A CTA count above what fits is reduced to what fits at
  * launch. Output does not depend on ctas_per_sm or rows_per_chunk, only on
  * the kernel (tensor_cores and, for the mma.sync kernel, threads, which sets
  * where a wide halo tile is cut into column slabs and so the fp32 summation

@@ -285,17 +285,20 @@ int sigma_grid(long long items, int num_sms) {
 // The tensor-core kernels serve launches whose frames are all uint8 with one
 // channel count (tc_c = that count, 0 otherwise). Returns the kernel a
 // launch runs on: 0 the fp32 FMA kernel, 1 the mma.sync kernel, 2 the
-// kernel with pass 1 on tcgen05 (radius bound and row chunk permitting,
-// else the mma.sync kernel).
+// kernel with pass 1 on tcgen05, 3 the kernel with both passes on tcgen05
+// (2 and 3 where the radius bound, row chunk and channel count permit, else
+// the mma.sync kernel).
 int tc_kind(const FwdConfig& cfg, int fmt_mask, int tc_c, int rmax) {
   if (!cfg.tc || fmt_mask != 1 || tc_c <= 0) return 0;
   if (cfg.tc == 2 && rmax <= kUmmaMaxRadius && cfg.rows_per_chunk <= 32) return 2;
+  if (cfg.tc == 3 && tc05_supports(rmax, tc_c) && cfg.rows_per_chunk <= 32) return 3;
   return 1;
 }
 
 int forward_grid(const fovea_ctx* ctx, const FwdConfig& cfg, int rmax, int fmt_mask, int tc_c) {
   const int kind = tc_kind(cfg, fmt_mask, tc_c, rmax);
-  int per = kind == 2   ? umma_forward_max_ctas_per_sm(cfg, rmax, tc_c)
+  int per = kind == 3   ? tc05_forward_max_ctas_per_sm(cfg, rmax)
+            : kind == 2 ? umma_forward_max_ctas_per_sm(cfg, rmax, tc_c)
             : kind == 1 ? tc_forward_max_ctas_per_sm(cfg, rmax, tc_c)
                         : forward_max_ctas_per_sm(cfg, rmax, fmt_mask);
   if (per <= 0) return 0;
@@ -450,6 +453,9 @@ int enqueue_batch_kernels(fovea_ctx* ctx, const FwdConfig& cfg, bool adjoint, in
     int grid = forward_grid(ctx, cfg, rbound, fmt_mask, tc_c);
     if (grid <= 0) return FOVEA_EUNSUPPORTED;
     switch (tc_kind(cfg, fmt_mask, tc_c, rbound)) {
+      case 3:
+        e = launch_tc05_forward(src, ctx->ws, cfg, rbound, grid, s, BucketList{nullptr, 0, 0}, false, nullptr);
+        break;
       case 2:
         e = launch_umma_forward(src, ctx->ws, cfg, rbound, tc_c, grid, s, BucketList{nullptr, 0, 0}, false, nullptr);
         break;
@@ -622,8 +628,9 @@ static int render_one(fovea_ctx* ctx, const void* in_dev, void* out_dev, float f
   if (kind) {
     alignas(64) unsigned char map[kTensorMapBytes];
     src.one.tma = make_u8_tensor_map(map, src.one.in, src.one.W, src.one.H, src.one.C, ctx->cfg.rows_per_chunk) ? 1 : 0;
-    e = kind == 2 ? launch_umma_forward(src, ctx->ws, ctx->cfg, rmax, tc_c, grid, s, bl, pdl, map)
-                  : launch_tc_forward(src, ctx->ws, ctx->cfg, rmax, tc_c, grid, s, bl, pdl, map);
+    e = kind == 3   ? launch_tc05_forward(src, ctx->ws, ctx->cfg, rmax, grid, s, bl, pdl, map)
+        : kind == 2 ? launch_umma_forward(src, ctx->ws, ctx->cfg, rmax, tc_c, grid, s, bl, pdl, map)
+                    : launch_tc_forward(src, ctx->ws, ctx->cfg, rmax, tc_c, grid, s, bl, pdl, map);
   } else {
     e = launch_forward(src, ctx->ws, ctx->cfg, rmax, fmt_mask, grid, s, bl, pdl);
   }
@@ -1042,7 +1049,7 @@ int check_config(const fovea_config* cfg) {
   if (cfg->threads != 128 && cfg->threads != 256 && cfg->threads != 512) return FOVEA_EUNSUPPORTED;
   if (cfg->rows_per_chunk != 16 && cfg->rows_per_chunk != 32 && cfg->rows_per_chunk != 64) return FOVEA_EUNSUPPORTED;
   if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 8) return FOVEA_EINVAL;
-  if (cfg->tensor_cores < 0 || cfg->tensor_cores > 2) return FOVEA_EINVAL;
+  if (cfg->tensor_cores < 0 || cfg->tensor_cores > 3) return FOVEA_EINVAL;
   return FOVEA_OK;
 }
 

@@ -369,6 +369,13 @@ size_t umma_forward_smem_bytes(const FwdConfig& cfg, int rmax, int C);
 int umma_forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int C);
 cudaError_t launch_umma_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg, int rmax, int C,
                                 int grid, cudaStream_t s, const BucketList& bl, bool pdl, const void* tmap_one);
+// Both passes on tcgen05 (tc05_forward.cu): uint8 RGB frames (C = 3), radius
+// bound up to 511, row chunks of 16 or 32 rows.
+bool tc05_supports(int rmax, int C);
+size_t tc05_forward_smem_bytes(const FwdConfig& cfg, int rmax);
+int tc05_forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax);
+cudaError_t launch_tc05_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg, int rmax, int grid,
+                                cudaStream_t s, const BucketList& bl, bool pdl, const void* tmap_one);
 size_t adjoint_smem_bytes(int rmax);
 cudaError_t launch_adjoint(const FrameSource& src, const Workspace& ws, int rmax, int grid,
                            cudaStream_t s);

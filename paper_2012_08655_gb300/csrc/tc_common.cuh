@@ -391,7 +391,7 @@ __device__ __forceinline__ void tc_write_output(const Item& it, unsigned char* o
 // the next item's index and record, so the work list's dependent loads
 // overlap the current item. Ends with the single-frame counter reset.
 // s_start: shared memory for rmax + 1 bucket starts (single frames).
-template <int RB, int C, bool FULL_SLABS = false, int NW = 8, typename ItemFn>
+template <int RB, int C, bool FULL_SLABS = false, int NW = 8, int SLAB = TcDims<NW>::SLAB, typename ItemFn>
 __device__ __forceinline__ void tc_item_loop(const FrameSource& src, const CUtensorMap& tmap1, const Workspace& ws,
                                              int rmax, const BucketList& bl, int* s_start, ItemFn&& item_fn) {
   constexpr int NT = TcDims<NW>::NT;
@@ -456,7 +456,7 @@ __device__ __forceinline__ void tc_item_loop(const FrameSource& src, const CUten
             atomicOr(&ws.counters[CNT_ERROR], kFaultRadiusBound);
             state = 1;
           } else {
-            item_geometry(s_it, inf, fd, RB, FULL_SLABS, TcDims<NW>::SLAB);
+            item_geometry(s_it, inf, fd, RB, FULL_SLABS, SLAB);
             s_c = inf.neg_half_inv_s2;
             s_map = !fd.tma ? nullptr : (batch_maps ? static_cast<const void*>(batch_maps + inf.frame)
                                                     : static_cast<const void*>(&tmap1));

@@ -23,7 +23,7 @@
 #include <algorithm>
 #include <cstring>
 
-#include "tc_common.cuh"
+#include "tc05_common.cuh"
 
 namespace fovea {
 
@@ -33,7 +33,6 @@ using namespace fwd;
 using namespace tcc;
 
 constexpr int kTmemCols = 128;     // D1: two M tiles x 64 fp32 columns (hi and lo parts)
-constexpr int kXOff = 8;           // strip entry j holds Hankel index X = j - kXOff
 constexpr unsigned int kIdescM128N64 =
     (1u << 4)                      // D format: f32
     | (0u << 7) | (0u << 10)       // A, B format: f16
@@ -52,7 +51,6 @@ constexpr int kA1Bufs = 4;
 // stores free of bank conflicts).
 __host__ __device__ constexpr int a1_sbo(int rb) { return 16 * rb + 16; }
 __host__ __device__ constexpr int a1_tile_bytes(int rb) { return 16 * a1_sbo(rb); }
-__host__ __device__ inline int strip_entries(int rmax) { return rmax / 4 + 16; }
 
 struct UmLayout {
   size_t ring, a1, vh, vl, strip, cum, pairs, edge, foldw, starts, total;
@@ -83,72 +81,6 @@ __host__ __device__ inline UmLayout um_layout(int rb, int rmax, int C) {
   L.starts = L.foldw + (size_t)2 * 32 * 4;                           // int [rmax + 1]
   L.total = L.starts + (size_t)(rmax + 1) * 4 + 1024;                // + alignment slack
   return L;
-}
-
-// ---------------------------------------------------------------- tcgen05
-
-// Shared-memory matrix descriptor: no swizzle, K-major core matrices of 8
-// rows x 16 bytes; lbo / sbo = byte distance between core matrices adjacent
-// in K / in M (or N). Bits 46-48 hold the descriptor version 1.
-__device__ __forceinline__ unsigned long long umma_desc(const void* p, unsigned int lbo, unsigned int sbo) {
-  const unsigned int a = smem_u32(p);
-  return (unsigned long long)((a & 0x3FFFFu) >> 4) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-__device__ __forceinline__ void umma_f16(unsigned int d_tmem, unsigned long long a, unsigned long long b,
-                                         unsigned int idesc, unsigned int accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-// Arrives on `bar` once every tcgen05.mma issued so far by this thread is done.
-__device__ __forceinline__ void umma_commit(unsigned long long* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tc05_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
-__device__ __forceinline__ void tc05_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
-
-// 32 consecutive fp32 columns of this thread's tensor-memory lane.
-__device__ __forceinline__ void tmem_ld32(unsigned int taddr, float (&d)[32]) {
-  unsigned int u[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
-        "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]),
-        "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]),
-        "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-  #pragma unroll
-  for (int i = 0; i < 32; ++i) d[i] = __uint_as_float(u[i]);
-}
-
-// Hankel strip of one item for pass 1: entry j is two 128-byte core
-// matrices, hi then lo, whose row rho, column i holds the hi / lo fp16 part
-// of the scaled tap u(8 (j - kXOff) + rho + i + delta) * 2^12. Read with N
-// groups 128 bytes apart and K groups 256 bytes apart, N group 2a' + p of
-// the MMA's B is part p (hi, lo) of the Hankel core matrix a' + b: one
-// N = 64 instruction computes both products.
-__device__ __forceinline__ void make_strips(__half* S2, int nent, int r, float c, float S, int delta) {
-  for (int idx = threadIdx.x; idx < nent * 32; idx += kThreads) {
-    const int j = idx >> 5, rho = (idx >> 2) & 7, i0 = (idx & 3) * 2;
-    const int m0 = 8 * (j - kXOff) + rho + i0 + delta;
-    const float w0 = tap_u(m0, r, c, S) * kWScale, w1 = tap_u(m0 + 1, r, c, S) * kWScale;
-    const __half h0 = __float2half_rn(w0), h1 = __float2half_rn(w1);
-    const __half l0 = __float2half_rn(w0 - __half2float(h0)), l1 = __float2half_rn(w1 - __half2float(h1));
-    const int o = j * 128 + rho * 8 + i0;
-    *reinterpret_cast<unsigned int*>(S2 + o) = pack_half2(h0, h1);
-    *reinterpret_cast<unsigned int*>(S2 + o + 64) = pack_half2(l0, l1);
-  }
 }
 
 // One item. bars: TMA ring stages; mbar_mma / conv_full[kA1Bufs]: MMA
@@ -310,12 +242,16 @@ __device__ __forceinline__ bool um_item(const Item& it, float c_tap, unsigned ch
           #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const int vv = R0 + v0 + j;
-            if ((k == 0 && vv == it.ph) || vv == vb) {
-              float* ed = edge + (vv == vb ? 256 : 0) + b;
+            if ((k == 0 && vv == it.ph) || vv == vb) {  // both stashes when the tile is one row high
               #pragma unroll
-              for (int i = 0; i < 4; ++i) {
-                ed[i] = (float)((w[j].x >> (8 * i)) & 0xFFu);
-                ed[4 + i] = (float)((w[j].y >> (8 * i)) & 0xFFu);
+              for (int part = 0; part < 2; ++part) {
+                if (part == 0 ? !(k == 0 && vv == it.ph) : vv != vb) continue;
+                float* ed = edge + 256 * part + b;
+                #pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                  ed[i] = (float)((w[j].x >> (8 * i)) & 0xFFu);
+                  ed[4 + i] = (float)((w[j].y >> (8 * i)) & 0xFFu);
+                }
               }
             }
           }

@@ -63,7 +63,7 @@ def run_cases(fv, torch):
             wl.uniform_u8((h, w, c), seed=h + 3 * w)
         x = torch.from_numpy(img).to(dev)
         ctx = fv.Context(w, h, c, 32, 0.5, 0.04, fv.U8_HWC)
-        kinds = [(0, 256), (1, 128), (1, 256), (1, 512), (2, 256)]
+        kinds = [(0, 256), (1, 128), (1, 256), (1, 512), (2, 256), (3, 256)]
         for tc, nt in kinds:
             for skew in (0, 3):
                 if (h, w) == (2160, 3840) and skew:
@@ -95,7 +95,7 @@ def run_cases(fv, torch):
         frames.append(fv.BatchFrame(x, g.t, 0.9 * w, 0.1 * h, 0.5, 0.03))
         guards.append(g)
     bctx = fv.batch_context(32)
-    for tc, nt in [(0, 256), (1, 128), (1, 512), (2, 256)]:
+    for tc, nt in [(0, 256), (1, 128), (1, 512), (2, 256), (3, 256)]:
         bctx.set_config(nt, 0, 32, tensor_cores=tc)
         bctx.render_batch(frames)
         torch.cuda.synchronize()

@@ -45,7 +45,7 @@ def test_mixed_batch_full_size(fv):
                         min_equal=0.99)
 
 
-@pytest.mark.parametrize("tc,threads", [(1, 256), (1, 128), (1, 512), (2, 256)])
+@pytest.mark.parametrize("tc,threads", [(1, 256), (1, 128), (1, 512), (2, 256), (3, 256)])
 def test_batch_mixing_tma_and_plain_frames(fv, tc, threads):
     """uint8 RGB frames of one batch whose rows TMA can load (16-byte
     aligned pitch) and whose rows it cannot (odd pitch: plain loads), in

@@ -35,7 +35,7 @@ def render(fv, img, fmt, B, fx, fy, s0, k, tc):
     return y.cpu().numpy()
 
 
-@pytest.mark.parametrize("tc", [0, 1])
+@pytest.mark.parametrize("tc", [0, 1, 2, 3])
 def test_radius_near_the_maximum(fv, tc):
     """An 8 x 8 frame whose far corner block reaches r = 1013 (the library's
     bound is 1023): nearly every tap clamps onto the border."""
@@ -56,7 +56,7 @@ def test_radius_near_the_maximum_f32(fv):
 
 
 @pytest.mark.parametrize("shape", [(1, 1, 3), (1, 40, 1), (37, 1, 2)])
-@pytest.mark.parametrize("tc", [0, 1])
+@pytest.mark.parametrize("tc", [0, 1, 2, 3])
 def test_degenerate_frames(fv, shape, tc):
     H, W, C = shape
     img = wl.uniform_u8(shape, seed=H * W + C)
@@ -65,7 +65,7 @@ def test_degenerate_frames(fv, shape, tc):
     assert_u8_close(y, ref, min_equal=0.95)
 
 
-@pytest.mark.parametrize("tc", [0, 1])
+@pytest.mark.parametrize("tc", [0, 1, 2, 3])
 def test_one_pixel_blocks_equal_per_pixel_foveation(fv, tc):
     """With B = 1 every block is a pixel, so the block-wise map is the
     per-pixel map (the oracle's per-pixel function, a different code path)."""

@@ -216,14 +216,14 @@ def test_render_host_pipelined_calls(fv):
 
 # ---------------------------------------------------------------- configurations
 
-@pytest.mark.parametrize("tc", [0, 1, 2])
+@pytest.mark.parametrize("tc", [0, 1, 2, 3])
 def test_every_config_gives_identical_output(fv, tc):
     """Within one kernel, the row chunk and the CTA count change nothing."""
     s = wl.frame_1080p(seed=9)
     x = to_dev(s.image)
     ctx = fv.Context(1920, 1080, 3, 32, s.sigma0, s.k, fv.U8_HWC)
     outs = []
-    for rb in ((16, 32) if tc == 2 else (16, 32, 64)):
+    for rb in ((16, 32) if tc in (2, 3) else (16, 32, 64)):
         for ctas in (1, 2, 0):
             ctx.set_config(256, ctas, rb, tensor_cores=tc)
             y = torch.empty_like(x)
@@ -271,7 +271,7 @@ def test_argument_errors(fv):
 
 # ---------------------------------------------------------------- tensor-core kernel vs fp32 kernel
 
-@pytest.mark.parametrize("tc,threads", [(1, 256), (2, 256), (1, 128), (1, 512)])
+@pytest.mark.parametrize("tc,threads", [(1, 256), (2, 256), (3, 256), (1, 128), (1, 512)])
 @pytest.mark.parametrize("W,H,C,B,fx,fy,k", [
     (1920, 1080, 3, 32, 960.0, 540.0, 0.02),
     (333, 221, 1, 32, 10.0, 200.0, 0.1),
@@ -280,9 +280,10 @@ def test_argument_errors(fv):
     (256, 200, 3, 32, 250.0, 10.0, 0.7),
 ])
 def test_tensor_core_kernel_matches_fp32_kernel(fv, W, H, C, B, fx, fy, k, tc, threads):
-    """Both tensor-core kernels (1: mma.sync with 128, 256 or 512 threads;
-    2: vertical pass on tcgen05) against the fp32 FMA kernel and the oracle;
-    the last case has radii above the tcgen05 kernel's bound, which falls
+    """The tensor-core kernels (1: mma.sync with 128, 256 or 512 threads;
+    2: vertical pass on tcgen05; 3: both passes on tcgen05, RGB frames; the
+    other channel counts fall back to 1) against the fp32 FMA kernel and the
+    oracle; the last case has radii above the bound of kernel 2, which falls
     back to mma.sync."""
     img = wl.grating_frame(H, W, C, seed=W + C)
     x = to_dev(img)

@@ -51,7 +51,7 @@ def test_geisler_perry_sigma_table_bit_exact(fv):
         assert np.array_equal(sig.cpu().numpy(), osig.astype(np.float32))
 
 
-@pytest.mark.parametrize("tc", [0, 1, 2])
+@pytest.mark.parametrize("tc", [0, 1, 2, 3])
 @pytest.mark.parametrize("W,H,C,B,fx,fy,k", [
     (640, 360, 3, 32, 300.4, 170.6, 0.03),
     (129, 77, 1, 16, 64.0, 38.0, 0.05),
@@ -87,7 +87,7 @@ def test_centred_grid_f32_forward_and_backward(fv):
     np.testing.assert_allclose(gin.cpu().numpy(), ref, rtol=1e-5, atol=1e-5)
 
 
-@pytest.mark.parametrize("tc", [0, 1, 2])
+@pytest.mark.parametrize("tc", [0, 1, 2, 3])
 def test_geisler_perry_frame_matches_oracle(fv, tc):
     W, H, ec = 640, 480, 30.0
     img = wl.grating_frame(H, W, 3, seed=41)
@@ -101,7 +101,7 @@ def test_geisler_perry_frame_matches_oracle(fv, tc):
     assert_u8_close(y.cpu().numpy(), oracle.forward_u8(img, 32, 500.0, 100.0, s0, k, "hwc"), min_equal=0.99)
 
 
-@pytest.mark.parametrize("tc", [0, 1, 2])
+@pytest.mark.parametrize("tc", [0, 1, 2, 3])
 def test_sigma_map_matches_oracle(fv, tc):
     W, H, C, B = 300, 200, 3, 32
     g = wl.rng(51)
@@ -154,7 +154,7 @@ def test_batch_mixes_grids_laws_and_maps(fv):
 
 # ---------------------------------------------------------------- blocks larger than 32 (32 x 32 tiles sharing sigma)
 
-@pytest.mark.parametrize("tc", [0, 1, 2])
+@pytest.mark.parametrize("tc", [0, 1, 2, 3])
 @pytest.mark.parametrize("grid", [0, 1])
 def test_block_64_u8_matches_oracle(fv, tc, grid):
     W, H, C, B = 500, 300, 3, 64
