@@ -286,17 +286,18 @@ int sigma_grid(long long items, int num_sms) {
 // channel count (tc_c = that count, 0 otherwise). Returns the kernel a
 // launch runs on: 0 the fp32 FMA kernel, 1 the mma.sync kernel, 2 the
 // kernel with pass 1 on tcgen05, 3 the kernel with both passes on tcgen05
-// (2 and 3 where the radius bound, row chunk and channel count permit, else
-// the mma.sync kernel).
-int tc_kind(const FwdConfig& cfg, int fmt_mask, int tc_c, int rmax) {
+// (2 and 3 where the radius bound, row chunk and channel count permit, and
+// for 3 when every frame's rows can be loaded by TMA (all_tma); else the
+// mma.sync kernel).
+int tc_kind(const FwdConfig& cfg, int fmt_mask, int tc_c, int rmax, bool all_tma = true) {
   if (!cfg.tc || fmt_mask != 1 || tc_c <= 0) return 0;
   if (cfg.tc == 2 && rmax <= kUmmaMaxRadius && cfg.rows_per_chunk <= 32) return 2;
-  if (cfg.tc == 3 && tc05_supports(rmax, tc_c) && cfg.rows_per_chunk <= 32) return 3;
+  if (cfg.tc == 3 && all_tma && tc05_supports(rmax, tc_c) && cfg.rows_per_chunk <= 32) return 3;
   return 1;
 }
 
-int forward_grid(const fovea_ctx* ctx, const FwdConfig& cfg, int rmax, int fmt_mask, int tc_c) {
-  const int kind = tc_kind(cfg, fmt_mask, tc_c, rmax);
+int forward_grid(const fovea_ctx* ctx, const FwdConfig& cfg, int rmax, int fmt_mask, int tc_c, bool all_tma = true) {
+  const int kind = tc_kind(cfg, fmt_mask, tc_c, rmax, all_tma);
   int per = kind == 3   ? tc05_forward_max_ctas_per_sm(cfg, rmax)
             : kind == 2 ? umma_forward_max_ctas_per_sm(cfg, rmax, tc_c)
             : kind == 1 ? tc_forward_max_ctas_per_sm(cfg, rmax, tc_c)
@@ -368,7 +369,7 @@ FrameLaw law_of(const fovea_frame& f) {
 }
 
 int upload_batch(fovea_ctx* ctx, const FwdConfig& cfg, const fovea_frame* frames, int n, bool adjoint, cudaStream_t s,
-                 long long* total, int* rmax, int* fmt_mask, int* tc_c) {
+                 long long* total, int* rmax, int* fmt_mask, int* tc_c, bool* all_tma) {
   if (n <= 0 || !frames) return FOVEA_EINVAL;
   std::vector<FrameDesc> descs((size_t)n);
   long long item0 = 0;
@@ -407,13 +408,16 @@ int upload_batch(fovea_ctx* ctx, const FwdConfig& cfg, const fovea_frame* frames
   hdr.maps_offset = (int)maps_off;
   hdr.total_items = item0;
   char* hbuf = static_cast<char*>(ctx->batch_host[slot]);
+  bool every_tma = true;
   for (int i = 0; i < n; ++i) {
     FrameDesc& d = descs[(size_t)i];
     void* map = hbuf + maps_off + (size_t)i * kTensorMapBytes;
     d.tma = (!adjoint && d.fmt == FOVEA_U8_HWC &&
              make_u8_tensor_map(map, d.in, d.W, d.H, d.C, cfg.rows_per_chunk)) ? 1 : 0;
     if (!d.tma) std::memset(map, 0, kTensorMapBytes);
+    every_tma = every_tma && d.tma;
   }
+  *all_tma = every_tma;
   std::memcpy(hbuf, &hdr, sizeof(hdr));
   std::memcpy(hbuf + sizeof(hdr), descs.data(), (size_t)n * sizeof(FrameDesc));
   FOVEA_CUDA(cudaMemcpyAsync(ctx->batch_dev, hbuf, bytes, cudaMemcpyHostToDevice, s));
@@ -435,7 +439,7 @@ FrameSource batch_source(fovea_ctx* ctx) {
 
 // Enqueue (or capture) the batch launch sequence for the current batch buffer.
 int enqueue_batch_kernels(fovea_ctx* ctx, const FwdConfig& cfg, bool adjoint, int rbound, int fmt_mask, int tc_c,
-                          cudaStream_t s) {
+                          bool all_tma, cudaStream_t s) {
   const FrameSource src = batch_source(ctx);
   const int sg = 4 * ctx->num_sms;
   if (adjoint) {
@@ -450,9 +454,9 @@ int enqueue_batch_kernels(fovea_ctx* ctx, const FwdConfig& cfg, bool adjoint, in
     if (grid <= 0) return FOVEA_EUNSUPPORTED;
     e = launch_adjoint(src, ctx->ws, rbound, grid, s);
   } else {
-    int grid = forward_grid(ctx, cfg, rbound, fmt_mask, tc_c);
+    int grid = forward_grid(ctx, cfg, rbound, fmt_mask, tc_c, all_tma);
     if (grid <= 0) return FOVEA_EUNSUPPORTED;
-    switch (tc_kind(cfg, fmt_mask, tc_c, rbound)) {
+    switch (tc_kind(cfg, fmt_mask, tc_c, rbound, all_tma)) {
       case 3:
         e = launch_tc05_forward(src, ctx->ws, cfg, rbound, grid, s, BucketList{nullptr, 0, 0}, false, nullptr);
         break;
@@ -487,19 +491,21 @@ int run_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, bool adjoint, cu
   long long total = 0;
   int rmax = 0;
   int fmt_mask = 0, tc_c = 0;
-  int st = upload_batch(ctx, cfg, frames, n, adjoint, s, &total, &rmax, &fmt_mask, &tc_c);
+  bool all_tma = true;
+  int st = upload_batch(ctx, cfg, frames, n, adjoint, s, &total, &rmax, &fmt_mask, &tc_c, &all_tma);
   if (st != FOVEA_OK) return st;
   // Radius bound of the graph: next multiple of 64 (shared-memory size of
   // the persistent kernel depends on it).
   const int rbound = std::min(kMaxRadius, ((rmax + 63) / 64) * 64);
-  const auto key = std::make_pair((long long)((adjoint ? 1 : 0) + 2 * fmt_mask + 8 * tc_c) * 2048 + rbound,
+  const auto key = std::make_pair((long long)((adjoint ? 1 : 0) + 2 * fmt_mask + 8 * tc_c + 64 * (all_tma ? 1 : 0)) *
+                                      2048 + rbound,
                                   config_code(cfg));
   auto it = ctx->graphs.find(key);
   if (it == ctx->graphs.end()) {
     if (!ctx->capture_stream) FOVEA_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
     FOVEA_CUDA(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-    st = enqueue_batch_kernels(ctx, cfg, adjoint, rbound, fmt_mask, tc_c, ctx->capture_stream);
+    st = enqueue_batch_kernels(ctx, cfg, adjoint, rbound, fmt_mask, tc_c, all_tma, ctx->capture_stream);
     cudaError_t ee = cudaStreamEndCapture(ctx->capture_stream, &g);
     if (st != FOVEA_OK) {
       if (g) cudaGraphDestroy(g);
@@ -594,7 +600,11 @@ static int render_one(fovea_ctx* ctx, const void* in_dev, void* out_dev, float f
   const int rmax = radius_bound(ctx->W, ctx->H, ctx->B, fix_x, fix_y, ctx->law);
   const int fmt_mask = ctx->fmt == FOVEA_F32_CHW ? 2 : 1;
   const int tc_c = ctx->C;
-  int grid = forward_grid(ctx, ctx->cfg, rmax, fmt_mask, tc_c);
+  // the tensor map of the frame's rows (the tensor-core kernels load rows by TMA where it exists)
+  alignas(64) unsigned char map[kTensorMapBytes];
+  src.one.tma = (fmt_mask == 1 && ctx->cfg.tc &&
+                 make_u8_tensor_map(map, src.one.in, src.one.W, src.one.H, src.one.C, ctx->cfg.rows_per_chunk)) ? 1 : 0;
+  int grid = forward_grid(ctx, ctx->cfg, rmax, fmt_mask, tc_c, src.one.tma != 0);
   if (grid <= 0) return FOVEA_EUNSUPPORTED;
   // no more persistent CTAs than items (small frames start fewer CTAs)
   grid = (int)std::min<long long>(grid, src.one_total);
@@ -624,10 +634,8 @@ static int render_one(fovea_ctx* ctx, const void* in_dev, void* out_dev, float f
   // Programmatic dependent launch lets the blur kernel's prologue overlap the
   // sigma kernel (not when its launch is bracketed by timing events).
   const bool pdl = bl.list && !ctx->kev_start;
-  const int kind = tc_kind(ctx->cfg, fmt_mask, tc_c, rmax);
+  const int kind = tc_kind(ctx->cfg, fmt_mask, tc_c, rmax, src.one.tma != 0);
   if (kind) {
-    alignas(64) unsigned char map[kTensorMapBytes];
-    src.one.tma = make_u8_tensor_map(map, src.one.in, src.one.W, src.one.H, src.one.C, ctx->cfg.rows_per_chunk) ? 1 : 0;
     e = kind == 3   ? launch_tc05_forward(src, ctx->ws, ctx->cfg, rmax, grid, s, bl, pdl, map)
         : kind == 2 ? launch_umma_forward(src, ctx->ws, ctx->cfg, rmax, tc_c, grid, s, bl, pdl, map)
                     : launch_tc_forward(src, ctx->ws, ctx->cfg, rmax, tc_c, grid, s, bl, pdl, map);

@@ -23,24 +23,25 @@
 // instruction computes the hi and lo tap products), fp32 accumulation.
 //
 // Work split (one 32 x 32 block = one item; columns in slabs of 96 pixels =
-// three tiles of 32 pixels; rows in chunks of RB):
-//   warp 0, lane 0: the controller. It issues the TMA row boxes of each chunk
-//     into a 4-stage ring, waits for a chunk's conversion, refills its ring
-//     stage, issues the chunk's pass-1 MMAs (one per tile and K step) and
-//     commits them; after a slab, issues the pass-2 MMAs of each tile as its
-//     V operand becomes ready, accumulating the item's output in TMEM.
-//   warps 1..7: convert chunks (ring bytes -> fp16 A1 buffers, three of them,
-//     so conversion runs ahead of the tensor core), stash the folded edge
-//     rows. A converted row is indexed by staged byte, alignment padding
-//     included, so every 16-byte piece converts in place; the padding is
-//     skipped when the tile is read back (TMEM lane = staged byte).
+// three tiles of 32 pixels, each tile 128 staged bytes; rows in chunks of RB):
+//   warp 0, lane 0: the producer. It issues the TMA row boxes of each chunk
+//     into a 4-stage ring as stages are released, and, polling, the pass-2
+//     MMAs of each tile as its V operand becomes ready, accumulating the
+//     item's output in TMEM.
+//   warps 1..3, one per tile: convert the tile's 128 staged bytes of each
+//     chunk (ring bytes -> fp16 A1, two buffers per tile) and issue and commit
+//     the tile's own pass-1 MMAs, so a chunk needs no hand-over between warps.
+//     A converted row is indexed by staged byte, alignment padding included,
+//     so every 16-byte piece converts in place; the padding is skipped when
+//     the tile is read back (TMEM lane = staged byte).
 //   warps 4..7 (tensor-memory lane quarters 0..3): after a slab, read each
 //     tile's D1 back, add the folded top / bottom rows (clamp-to-edge, as in
 //     the other kernels), and write V as fp16 hi / lo into one of two A2
 //     buffers; warps 4..6, after the item, read D2, add the folded left /
 //     right columns, round to uint8 and stage the block by channel planes.
-// Every wait is bounded; a wait that gives up flags FOVEA_FAULT_WAIT, the
-// CTA drains what it issued and stops.
+// Every frame of a launch must be TMA-loadable (the host uses the mma.sync
+// kernel otherwise). Every wait is bounded; a wait that gives up flags
+// FOVEA_FAULT_WAIT, the CTA drains what it issued and stops.
 #include <algorithm>
 #include <cstring>
 
@@ -58,25 +59,23 @@ constexpr int kPxT = 32;                    // pixels per tile
 constexpr int kElT = kPxT * kC5;            // 96 element columns per tile
 constexpr int kTiles = 3;                   // tiles per slab
 constexpr int kSlabEl5 = kTiles * kElT;     // 288 elements per slab
-constexpr int kGroups = 20;                 // 16-element groups converted per row (elements 0..319)
 constexpr int kBoxes5 = 3;                  // 128-byte tensor-map boxes per staged row
 constexpr int kStages5 = 4;                 // ring stages
-constexpr int kA1Bufs5 = 3;                 // converted chunks in flight
-constexpr int kA1Cores = 40;                // 8-element M cores of a converted row (320 elements)
+constexpr int kA1Bufs5 = 2;                 // converted chunks in flight per tile
 constexpr int kA2Part = 16 * 4 * 128;       // one V part (hi or lo) of a tile: 16 M cores x 4 K groups
 constexpr int kThreads5 = 256;
-constexpr int kConv = 224;                  // converter threads (warps 1..7)
 constexpr unsigned int kTmemCols5 = 256;    // D1: 3 tiles x 64 columns; D2 at column 192
 constexpr int kMaxRadius5 = 511;            // tap strips grow with r
 // f32 accumulator, f16 A and B, A MN-major (bit 15), B K-major, N = 64, M = 128
 constexpr unsigned int kIdesc5 = (1u << 4) | (1u << 15) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
 
-// Converted chunk (pass-1 A operand, MN-major): core matrix (K group kg, M
-// core mg) at mg * RB * 16 + kg * 128 bytes, i.e. adjacent M cores RB * 16
-// bytes apart and adjacent K groups 128 bytes apart (the K groups of one M
-// core side by side, so either reading of the descriptor's two strides stays
-// inside the buffer).
-__host__ __device__ constexpr int a1_bytes5(int rb) { return kA1Cores * rb * 16; }
+// One tile's converted chunk (pass-1 A operand, MN-major, 128 staged bytes x
+// RB rows): core matrix (K group kg, M core mg) at mg * RB * 16 + kg * 128
+// bytes, i.e. adjacent K groups 128 bytes apart (the descriptor's leading
+// offset) and adjacent M cores RB * 16 bytes apart (its stride offset); the
+// K groups of one M core side by side, so either reading of the two strides
+// stays inside the buffer.
+__host__ __device__ constexpr int a1_tile_bytes5(int rb) { return 16 * rb * 16; }
 
 struct T5Layout {
   size_t ring, a1, a2, s1, s2, taps, cum, edge, foldw, vfold, ost, starts, total;
@@ -86,14 +85,14 @@ __host__ __device__ inline T5Layout t5_layout(int rb, int rmax) {
   T5Layout L;
   const size_t strip = (size_t)strip_entries(rmax) * 256;
   L.ring = 0;                                                        // u8 [stages][boxes][rb][128], swizzled
-  L.a1 = L.ring + (size_t)kStages5 * kBoxes5 * rb * 128;             // [3][a1_bytes5]
-  L.a2 = L.a1 + (size_t)kA1Bufs5 * a1_bytes5(rb);                    // [2 buffers][hi, lo][kA2Part]
+  L.a1 = L.ring + (size_t)kStages5 * kBoxes5 * rb * 128;             // [tile][buffer][a1_tile_bytes5]
+  L.a2 = L.a1 + (size_t)kTiles * kA1Bufs5 * a1_tile_bytes5(rb);      // [2 buffers][hi, lo][kA2Part]
   L.s1 = L.a2 + (size_t)2 * 2 * kA2Part;                             // pass-1 strip
   L.s2 = L.s1 + strip;                                               // pass-2 strip
   L.taps = L.s2 + strip;                                             // float [2 rmax + 1] normalised taps
   L.cum = L.taps + (size_t)((2 * rmax + 1 + 3) & ~3) * 4;            // float [cum_len]
-  L.edge = L.cum + (size_t)((cum_len(rmax) + 3) & ~3) * 4;           // u8 [2 slabs][top, bottom][320 staged bytes]
-  L.foldw = L.edge + (size_t)4 * 320;                                // float [top, bottom by yo; left, right by x][32]
+  L.edge = L.cum + (size_t)((cum_len(rmax) + 3) & ~3) * 4;           // u8 [3 slabs][top, bottom][320 staged bytes]
+  L.foldw = L.edge + (size_t)6 * 320;                                // float [top, bottom by yo; left, right by x][32]
   L.vfold = L.foldw + 128 * 4;                                       // float [2][96]
   L.ost = L.vfold + 2 * 96 * 4;                                      // u8 [C][32 rows][32 columns]
   L.starts = L.ost + 32 * 96;                                        // int [rmax + 1]
@@ -116,21 +115,20 @@ struct T5Smem {
 };
 
 struct T5Bars {
-  unsigned long long ring[kStages5];     // TMA bytes of a ring stage landed (count 1 + tx)
-  unsigned long long conv[kA1Bufs5];     // a chunk converted (7 converter warps)
-  unsigned long long a1free[kA1Bufs5];   // the MMAs that read an A1 buffer finished (commit)
-  unsigned long long slab;               // every pass-1 MMA of a slab finished (commit)
-  unsigned long long d1free;             // the epilogue warps read a slab's D1 (4 warps)
-  unsigned long long a2full[2];          // a tile's V written (4 warps)
-  unsigned long long a2free[2];          // the pass-2 MMAs that read an A2 buffer finished (commit)
-  unsigned long long d2;                 // every pass-2 MMA of an item finished (commit)
+  unsigned long long ring[kStages5];            // TMA bytes of a ring stage landed (count 1 + tx)
+  unsigned long long ringfree[kStages5];        // the three tile warps read a stage (3)
+  unsigned long long a1free[kTiles][kA1Bufs5];  // the MMAs that read a tile's A1 buffer finished (commit)
+  unsigned long long tdone[kTiles];             // a tile's pass-1 MMAs of a slab finished (commit + arrive; 2)
+  unsigned long long d1free[kTiles];            // the read-back warps read a tile's D1 (4)
+  unsigned long long a2full[2];                 // a tile's V written (4 warps)
+  unsigned long long a2free[2];                 // the pass-2 MMAs that read an A2 buffer finished (commit)
+  unsigned long long d2;                        // every pass-2 MMA of an item finished (commit)
 };
 
-// Phase counters (identical in every thread): chunks converted so far (A1
-// buffers), chunks loaded by TMA (ring stages), pass-2 tiles (A2 buffers),
-// slabs, items.
+// Phase counters (identical in every thread): ring chunks, A1 chunks (per
+// tile, all tiles alike), pass-2 tiles (A2 buffers), slabs, items.
 struct T5Count {
-  int gc, gt, gtile, gslab, gitem;
+  int gr, gc, gtile, gslab, gitem;
 };
 
 __device__ __forceinline__ bool t5_wait(unsigned long long* bar, int use, volatile int* abort, unsigned int* err) {
@@ -139,6 +137,19 @@ __device__ __forceinline__ bool t5_wait(unsigned long long* bar, int use, volati
   atomicOr(err, kFaultWait);
   *abort = 1;
   return false;
+}
+
+// Non-blocking: has the phase of the given use completed?
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, int use) {
+  unsigned int ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"((unsigned int)use & 1u)
+      : "memory");
+  return ok != 0;
 }
 
 __device__ __forceinline__ void tmem_ld64(unsigned int taddr, float (&d)[64]) {
@@ -157,32 +168,28 @@ __device__ __forceinline__ bool t5_item(const Item& it, float c_tap, const T5Sme
                                         unsigned int tmem, volatile int* abort, const void* map, bool map_in_global,
                                         T5Count& k, unsigned int* err, LookAhead&& lookahead) {
   constexpr size_t stage_bytes = (size_t)kBoxes5 * RB * 128;
-  constexpr int a1b = a1_bytes5(RB);
+  constexpr int a1t = a1_tile_bytes5(RB);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int r = it.r;
   const int Q = it.nsl * it.nchunks;
-  const int D0 = it.offy - it.ph;        // tap(v, yo) = v + D0 - yo
+  const int D0 = it.offy - it.ph;        // tap(v, yo) = v + D0 - yo; a multiple of 16, >= 0
   const int delta1 = (D0 + 1) & 7;       // (D0 - 31) mod 8
   const int delta2 = (it.offx + 1) & 7;  // (offx - 31) mod 8
-  const bool ctl = tid == 0;                  // MMA issuer
-  const bool prod = tid == 32;                // TMA producer (a converter thread)
-  const bool conv = warp >= 1;
-  const bool epi = warp >= 4;                 // tile read-back: TMEM lane quarters 0..3
-  const bool epi2 = warp >= 4 && warp <= 6;   // output: the channel quarters 0..2
+  const bool prod = tid == 0;            // TMA producer and pass-2 MMA issuer
+  const bool tilew = warp >= 1 && warp <= kTiles;
+  const bool epi = warp >= 4;            // tile read-back: TMEM lane quarters 0..3
+  const bool epi2 = warp >= 4 && warp <= 6;  // output: the channel quarters 0..2
+  const int gr_base = k.gr;
 
-  // The producer walks the item's chunks (slab by slab, RB rows each) with
-  // counters, so issuing a chunk costs no division.
-  int issued = 0;     // producer: chunks of this item whose rows were requested
-  int ring_seen = 0;  // producer: chunks whose rows it saw land (as a converter)
-  int is_slab = 0, is_chunk = 0, is_x = 0;  // producer: next chunk to issue, its slab's x
-  const int gt_base = k.gt;
+  // ---- producer state: it walks the item's chunks (slab by slab) with counters
+  int issued = 0, is_slab = 0, is_chunk = 0, is_x = 0;
   const int y_first = it.gy0 - it.ph;
-  auto issue = [&]() {  // producer: the next chunk's three TMA boxes
+  auto issue = [&]() {  // the next chunk's three TMA boxes into its ring stage
     if (is_chunk == 0) {
       const Slab cs = slab_of<true>(it, is_slab);
       is_x = (int)cs.src - cs.ph;  // 16-byte aligned byte column
     }
-    const int g = gt_base + issued, stg = g % kStages5;
+    const int g = gr_base + issued, stg = g % kStages5;
     unsigned char* dst = sm.ring + (size_t)stg * stage_bytes;
     const int y = y_first + is_chunk * RB;
     mbar_expect_tx(&bars->ring[stg], (unsigned int)kBoxes5 * 128u * RB);
@@ -194,10 +201,10 @@ __device__ __forceinline__ bool t5_item(const Item& it, float c_tap, const T5Sme
       ++is_slab;
     }
   };
-  if (map && prod) {
+  if (prod) {
     if (map_in_global) fence_tensormap_acquire(map);
     fence_proxy_async();
-    while (issued < kStages5 && issued < Q) issue();
+    while (issued < kStages5 && issued < Q) issue();  // the stages were released by the previous item
   }
   // ---- tables of the item: the taps once, then the two tap strips and the
   // folds' weights from them
@@ -221,156 +228,187 @@ __device__ __forceinline__ bool t5_item(const Item& it, float c_tap, const T5Sme
   }
   fence_proxy_async();  // the strips are read by the tensor cores
   __syncthreads();
-  if (ctl) lookahead(0);
-
   const int vb = it.ph + it.EH - 1;  // virtual row of the folded bottom row
-  int d2_started = 0;
-  int tile_base = 0;                  // pass-2 tiles of the item before this slab
-  for (int s = 0; s < it.nsl; ++s) {
-    const Slab sl = slab_of<true>(it, s);
-    const int npx = sl.sws / kC5;
-    const int ntiles = (npx + kPxT - 1) / kPxT;
-    const int P0 = sl.e0 / kC5;  // first folded pixel of the slab
-    const int qs = s * it.nchunks;
-    const int gs = k.gslab + s;
-    // edge rows of this slab (by staged byte): converters of the next slab
-    // (warps 1..3 run one slab ahead of the epilogue warps) write the other half
-    unsigned char* edge = sm.edge + (gs & 1) * 640;
-    // ------------------------------------------------------------ pass 1
-    if (ctl) {
-      // K steps (16 staged rows) with a tap of the 32 output rows: k0 <
-      // min(vrows, 32 - D0 + 2r) (D0 >= 0, so none lies above the band's
-      // start). Descriptors are the item's base descriptors plus offsets in
-      // 16-byte units: strip entry j0 = 2 kidx + D0 / 8 + 4 for K step kidx
-      // (D0 is a multiple of 16, so delta1 = 1); A1 tile t at 12 t M cores.
-      const int k_end = min(it.vrows, 32 - D0 + 2 * r);
-      const unsigned long long s1d = umma_desc(sm.s1, 256, 128) + (unsigned long long)(16 * (D0 / 8 + 4));
-      const unsigned long long a1d = umma_desc(sm.a1, 128, RB * 16);
-      int started[kTiles] = {0, 0, 0};
-      for (int kq = 0; kq < it.nchunks; ++kq) {
-        const int qq = qs + kq, g = k.gc + qq;
-        t5_wait(&bars->conv[g % kA1Bufs5], g / kA1Bufs5, abort, err);
-        tc05_fence_after();
-        if (qq == 0) lookahead(1);
-        if (kq == 0 && gs > 0) {  // D1 is free once the previous slab's tiles were read back
-          t5_wait(&bars->d1free, gs - 1, abort, err);
-          tc05_fence_after();
+
+  if (prod) {
+    // ------------------------------------------------------------ producer
+    lookahead(0);
+    int total_tiles = 0;
+    for (int s2 = 0; s2 < it.nsl; ++s2) total_tiles += (slab_of<true>(it, s2).sws / kC5 + kPxT - 1) / kPxT;
+    const unsigned long long a2d = umma_desc(sm.a2, 128, 512);
+    int done_tiles = 0, tslab = 0, ttile = 0, tslab_tiles = 0, tP0 = 0, tnpx = 0;
+    unsigned long long s2d = 0;
+    int d2_started = 0, idle = 0;
+    bool looked = false;
+    while ((issued < Q || done_tiles < total_tiles) && !*abort) {
+      bool progress = false;
+      if (issued < Q) {  // refill a released stage (its previous chunk, 4 back, was read by every tile warp)
+        const int g = gr_base + issued;
+        if (mbar_test(&bars->ringfree[g % kStages5], g / kStages5 - 1)) {
+          issue();
+          progress = true;
         }
-        const unsigned long long ab = a1d + (unsigned long long)((g % kA1Bufs5) * (a1b >> 4));
-        #pragma unroll
-        for (int ks = 0; ks < RB / 16; ++ks) {
-          const int k0 = kq * RB + 16 * ks;
-          if (k0 >= k_end || *abort) break;
-          const unsigned long long bd = s1d + (unsigned long long)(32 * (k0 >> 4));
-          #pragma unroll
-          for (int t = 0; t < kTiles; ++t) {
-            if (t >= ntiles) break;
-            umma_f16(tmem + 64 * t, ab + (unsigned long long)(t * (12 * RB) + 16 * ks), bd, kIdesc5, started[t]);
-            started[t] = 1;
-          }
-        }
-        umma_commit(&bars->a1free[g % kA1Bufs5]);
       }
-      umma_commit(&bars->slab);
-    } else if (conv) {
-      const int ct = tid - 32;
-      for (int kq = 0; kq < it.nchunks; ++kq) {
-        const int qq = qs + kq, g = k.gc + qq;
-        if (g >= kA1Bufs5) t5_wait(&bars->a1free[g % kA1Bufs5], g / kA1Bufs5 - 1, abort, err);
-        const unsigned char* st;
-        if (map) {
-          const int gt = k.gt + qq;
-          if (t5_wait(&bars->ring[gt % kStages5], gt / kStages5, abort, err) && prod) ring_seen = qq + 1;
-          st = sm.ring + (size_t)(gt % kStages5) * stage_bytes;
-        } else {
-          // rows that TMA cannot address: the converters stage them
-          unsigned char* dst = sm.ring + (size_t)((k.gc + qq) % kStages5) * stage_bytes;
-          const long long x0 = (long long)sl.src - sl.ph;
-          const int y0 = it.gy0 - it.ph + kq * RB;
-          for (int idx = ct; idx < RB * kBoxes5 * 128; idx += kConv) {
-            const int rho = idx / (kBoxes5 * 128), b = idx - rho * (kBoxes5 * 128);
-            const int y = y0 + rho;
-            const long long xb = x0 + b;
-            unsigned char v = 0;
-            if (y >= 0 && y < it.H && xb < (long long)it.pitch) v = it.in[(size_t)y * it.pitch + (size_t)xb];
-            unsigned char* o = dst + ring_off<RB>(rho, b);
-            if (smem_in_bounds(o, 1, err)) *o = v;
+      if (done_tiles < total_tiles) {
+        const int gtl = k.gtile + done_tiles, buf = gtl & 1;
+        if (mbar_test(&bars->a2full[buf], gtl >> 1)) {
+          if (ttile == 0) {  // first tile of a slab: its geometry and strip base
+            const Slab cs = slab_of<true>(it, tslab);
+            tnpx = cs.sws / kC5;
+            tslab_tiles = (tnpx + kPxT - 1) / kPxT;
+            tP0 = cs.e0 / kC5;
+            // strip entry of pixel p0 of the slab: (offx + P0 + p0 - 31 - delta2) / 8 + kXOff
+            s2d = umma_desc(sm.s2, 256, 128) + (unsigned long long)(16 * ((it.offx + tP0 - 31 - delta2) / 8 + kXOff));
           }
-          asm volatile("bar.sync 1, 224;" ::: "memory");
-          st = dst;
-        }
-        // convert: unit = (row rho, 16-element group ge); 8 consecutive
-        // threads take 8 rows of one group (conflict-free stores)
-        unsigned char* a1 = sm.a1 + (size_t)(g % kA1Bufs5) * a1b;
-        for (int u = ct; u < RB * kGroups; u += kConv) {
-          const int rho = u % RB, ge = u / RB;
-          const uint4 w = *reinterpret_cast<const uint4*>(st + ring_off<RB>(rho, 16 * ge));
-          const int vv = kq * RB + rho;
-          if ((kq == 0 && vv == it.ph) || vv == vb) {  // folded edge rows (both, if EH = 1)
+          tc05_fence_after();
+          #pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            const int p0 = kPxT * ttile + 16 * ks;
+            if (p0 >= tnpx) break;
+            const unsigned long long bd = s2d + (unsigned long long)(32 * (p0 >> 4));
             #pragma unroll
             for (int part = 0; part < 2; ++part) {
-              if (part == 0 ? !(kq == 0 && vv == it.ph) : vv != vb) continue;
-              *reinterpret_cast<uint4*>(edge + 320 * part + 16 * ge) = w;
+              umma_f16(tmem + 192, a2d + (unsigned long long)((buf * 2 + part) * (kA2Part >> 4) + 16 * ks), bd, kIdesc5,
+                       d2_started);
+              d2_started = 1;
             }
           }
-          const uint4 lo = make_uint4(__byte_perm(w.x, 0u, 0x4140), __byte_perm(w.x, 0u, 0x4342),
-                                      __byte_perm(w.y, 0u, 0x4140), __byte_perm(w.y, 0u, 0x4342));
-          const uint4 hi = make_uint4(__byte_perm(w.z, 0u, 0x4140), __byte_perm(w.z, 0u, 0x4342),
-                                      __byte_perm(w.w, 0u, 0x4140), __byte_perm(w.w, 0u, 0x4342));
-          unsigned char* o = a1 + (size_t)(2 * ge) * (RB * 16) + (rho >> 3) * 128 + (rho & 7) * 16;
-          if (smem_in_bounds(o, 16, err) && smem_in_bounds(o + RB * 16, 16, err)) {
-            *reinterpret_cast<uint4*>(o) = lo;
-            *reinterpret_cast<uint4*>(o + RB * 16) = hi;
+          umma_commit(&bars->a2free[buf]);
+          ++done_tiles;
+          if (++ttile == tslab_tiles) {
+            ttile = 0;
+            ++tslab;
           }
+          progress = true;
         }
-        fence_proxy_async();  // the converted chunk is read by the tensor cores
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&bars->conv[g % kA1Bufs5]);
-        if (map && prod && issued < Q) {  // every converter is done with this chunk's stage: refill it
-          if (t5_wait(&bars->conv[g % kA1Bufs5], g / kA1Bufs5, abort, err)) issue();
-        }
-        __syncwarp();
       }
-      asm volatile("bar.sync 1, 224;" ::: "memory");  // edge rows of the slab visible to the epilogue warps
+      if (!looked) {
+        lookahead(1);
+        looked = true;
+      }
+      if (progress) {
+        idle = 0;
+      } else if (++idle > kWaitLimit) {
+        atomicOr(err, kFaultWait);
+        *abort = 1;
+      } else {
+        __nanosleep(20);
+      }
     }
-    // ------------------------------------------------------------ V, pass 2
-    if (ctl) {
-      // strip entry of pixel p0 of the slab: (offx + P0 + p0 - 31 - delta2) / 8
-      // + kXOff (exact: delta2 = (offx - 31) mod 8, P0 and p0 multiples of 16)
-      const unsigned long long s2d =
-          umma_desc(sm.s2, 256, 128) + (unsigned long long)(16 * ((it.offx + P0 - 31 - delta2) / 8 + kXOff));
-      const unsigned long long a2d = umma_desc(sm.a2, 128, 512);
-      for (int t = 0; t < ntiles; ++t) {
-        const int gtl = k.gtile + tile_base + t, buf = gtl & 1;
-        t5_wait(&bars->a2full[buf], gtl >> 1, abort, err);
-        tc05_fence_after();
-        #pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {
-          const int p0 = kPxT * t + 16 * ks;
-          if (p0 >= npx || *abort) break;
-          const unsigned long long bd = s2d + (unsigned long long)(32 * (p0 >> 4));
+    umma_commit(&bars->d2);
+  } else if (tilew) {
+    // ------------------------------------------------------------ tile warps
+    const int t = warp - 1;
+    const int k_end = min(it.vrows, 32 - D0 + 2 * r);  // K steps with a tap of the 32 output rows
+    const unsigned long long s1d = umma_desc(sm.s1, 256, 128) + (unsigned long long)(16 * (D0 / 8 + 4));
+    const unsigned long long a1d = umma_desc(sm.a1 + (size_t)t * kA1Bufs5 * a1t, 128, RB * 16);
+    unsigned char* a1base = sm.a1 + (size_t)t * kA1Bufs5 * a1t;
+    int g = k.gc;  // this tile's A1 chunk counter (the same in every tile warp)
+    for (int s = 0; s < it.nsl; ++s) {
+      const Slab sl = slab_of<true>(it, s);
+      const int ntiles = (sl.sws / kC5 + kPxT - 1) / kPxT;
+      const bool active = t < ntiles;
+      const int gs = k.gslab + s;
+      unsigned char* edge = sm.edge + (gs % 3) * 640;
+      int started = 0;
+      for (int kq = 0; kq < it.nchunks; ++kq, ++g) {
+        const int gq = gr_base + s * it.nchunks + kq, stg = gq % kStages5;
+        t5_wait(&bars->ring[stg], gq / kStages5, abort, err);
+        const unsigned char* st = sm.ring + (size_t)stg * stage_bytes;
+        const int buf = g % kA1Bufs5;
+        // every tile warp commits once per chunk (an inactive tile with no
+        // MMA at all), so the buffers' phases stay in step
+        if (g >= kA1Bufs5) t5_wait(&bars->a1free[t][buf], g / kA1Bufs5 - 1, abort, err);
+        if (active) {
+          // convert: unit = (row rho, 16-byte group ge) of the tile's 128 staged bytes
+          unsigned char* a1 = a1base + (size_t)buf * a1t;
           #pragma unroll
-          for (int part = 0; part < 2; ++part) {
-            umma_f16(tmem + 192, a2d + (unsigned long long)((buf * 2 + part) * (kA2Part >> 4) + 16 * ks), bd, kIdesc5,
-                     d2_started);
-            d2_started = 1;
+          for (int i = 0; i < RB / 4; ++i) {
+            const int u = lane + 32 * i, rho = u % RB, ge = u / RB;
+            const int b = kElT * t + 16 * ge;  // staged byte
+            const uint4 w = *reinterpret_cast<const uint4*>(st + ring_off<RB>(rho, b));
+            const int vv = kq * RB + rho;
+            if ((kq == 0 && vv == it.ph) || vv == vb) {  // folded edge rows (both, if EH = 1)
+              #pragma unroll
+              for (int part = 0; part < 2; ++part) {
+                if (part == 0 ? !(kq == 0 && vv == it.ph) : vv != vb) continue;
+                *reinterpret_cast<uint4*>(edge + 320 * part + b) = w;
+              }
+            }
+            const uint4 lo = make_uint4(__byte_perm(w.x, 0u, 0x4140), __byte_perm(w.x, 0u, 0x4342),
+                                        __byte_perm(w.y, 0u, 0x4140), __byte_perm(w.y, 0u, 0x4342));
+            const uint4 hi = make_uint4(__byte_perm(w.z, 0u, 0x4140), __byte_perm(w.z, 0u, 0x4342),
+                                        __byte_perm(w.w, 0u, 0x4140), __byte_perm(w.w, 0u, 0x4342));
+            unsigned char* o = a1 + (size_t)(2 * ge) * (RB * 16) + (rho >> 3) * 128 + (rho & 7) * 16;
+            if (smem_in_bounds(o, 16, err) && smem_in_bounds(o + RB * 16, 16, err)) {
+              *reinterpret_cast<uint4*>(o) = lo;
+              *reinterpret_cast<uint4*>(o + RB * 16) = hi;
+            }
           }
+          fence_proxy_async();  // the converted chunk is read by the tensor cores
         }
-        umma_commit(&bars->a2free[buf]);
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&bars->ringfree[stg]);  // this warp is done with the stage
+          // the read-back of the tile's previous slab is done (also when the
+          // tile is inactive: otherwise its slab commits could run two phases
+          // ahead of the read-back warps' parity waits on tdone)
+          if (kq == 0 && gs > 0) t5_wait(&bars->d1free[t], gs - 1, abort, err);
+          if (active) {
+            tc05_fence_after();
+            #pragma unroll
+            for (int ks = 0; ks < RB / 16; ++ks) {
+              const int k0 = kq * RB + 16 * ks;
+              if (k0 >= k_end || *abort) break;
+              // strip entry 2 kidx + D0 / 8 + 4 for K step kidx = k0 / 16 (delta1 = 1)
+              umma_f16(tmem + 64 * t, a1d + (unsigned long long)(buf * (a1t >> 4) + 16 * ks),
+                       s1d + (unsigned long long)(32 * (k0 >> 4)), kIdesc5, started);
+              started = 1;
+            }
+          }
+          umma_commit(&bars->a1free[t][buf]);
+        }
+        __syncwarp();
       }
-    } else if (epi) {
-      t5_wait(&bars->slab, gs, abort, err);
-      tc05_fence_after();
-      const int q = warp - 4;  // TMEM lane quarter
-      const int lane_t = 32 * q + lane;        // TMEM lane = staged byte of the tile
-      const int el = lane_t - sl.ph;           // element of the tile (0 .. 95 for its 32 pixels)
+      __syncwarp();
+      if (lane == 0) {
+        umma_commit(&bars->tdone[t]);  // the tile's pass-1 MMAs of the slab (none if inactive)
+        mbar_arrive(&bars->tdone[t]);  // and (release) the warp's edge-row stash
+      }
+      __syncwarp();
+    }
+  }
+  // ------------------------------------------------------------ V (read-back warps)
+  int tile_base = 0;
+  if (epi) {
+    const int q = warp - 4;                  // TMEM lane quarter
+    const int lane_t = 32 * q + lane;        // TMEM lane = staged byte of the tile
+    for (int s = 0; s < it.nsl; ++s) {
+      const Slab sl = slab_of<true>(it, s);
+      const int npx = sl.sws / kC5;
+      const int ntiles = (npx + kPxT - 1) / kPxT;
+      const int P0 = sl.e0 / kC5;
+      const int gs = k.gslab + s;
+      const unsigned char* edge = sm.edge + (gs % 3) * 640;
+      const int el = lane_t - sl.ph;          // element of the tile (0 .. 95 for its 32 pixels)
       const bool mine = el >= 0 && el < kElT;
       const int px = mine ? el / kC5 : 0, c = mine ? el - px * kC5 : 0;
-      for (int t = 0; t < ntiles; ++t) {
+      for (int t = 0; t < kTiles; ++t) {
+        t5_wait(&bars->tdone[t], gs, abort, err);
+        if (t >= ntiles) {  // keep the tile's D1 phase in step
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bars->d1free[t]);
+          continue;
+        }
+        tc05_fence_after();
         const int gtl = k.gtile + tile_base + t, buf = gtl & 1;
         if (gtl >= 2) t5_wait(&bars->a2free[buf], (gtl >> 1) - 1, abort, err);
         float d[64];
+        __syncwarp();  // tcgen05.ld is warp-collective
         tmem_ld64(tmem + ((unsigned int)(32 * q) << 16) + 64 * t, d);
+        tc05_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars->d1free[t]);  // D1 of the tile is read: its next slab may start
         const int b = kElT * t + lane_t;      // staged byte
         const int spx = kPxT * t + px;        // slab pixel
         const int pg = P0 + spx;              // folded pixel
@@ -414,16 +452,14 @@ __device__ __forceinline__ bool t5_item(const Item& it, float c_tap, const T5Sme
           }
         }
         fence_proxy_async();  // V is read by the tensor cores
-        tc05_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars->a2full[buf]);
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&bars->d1free);  // this warp's reads of the slab's D1 are done
+      tile_base += ntiles;
     }
-    tile_base += ntiles;
+  } else {
+    for (int s = 0; s < it.nsl; ++s) tile_base += (slab_of<true>(it, s).sws / kC5 + kPxT - 1) / kPxT;
   }
-  if (ctl) umma_commit(&bars->d2);
   // ------------------------------------------------------------ output
   if (epi) asm volatile("bar.sync 2, 128;" ::: "memory");  // the folded V columns of every slab are visible
   if (epi2) {
@@ -431,6 +467,7 @@ __device__ __forceinline__ bool t5_item(const Item& it, float c_tap, const T5Sme
     tc05_fence_after();
     const int c = warp - 4, yo = lane;
     float d[64];
+    __syncwarp();
     tmem_ld64(tmem + ((unsigned int)(32 * c) << 16) + 192, d);
     const float vl = it.foldL ? sm.vfold[32 * c + yo] : 0.0f, vr = it.foldR ? sm.vfold[96 + 32 * c + yo] : 0.0f;
     // the row's 32 outputs of channel c, contiguous in a channel plane
@@ -441,8 +478,8 @@ __device__ __forceinline__ bool t5_item(const Item& it, float c_tap, const T5Sme
       float o = d[16 * a + i] + d[16 * a + 8 + i];
       if (it.foldL) o = fmaf(sm.foldw[64 + x], vl, o);
       if (it.foldR) o = fmaf(sm.foldw[96 + x], vr, o);
-      const unsigned int q = quant_u8(o * kWInv);
-      pk[x >> 2] = (x & 3) ? (pk[x >> 2] | (q << (8 * (x & 3)))) : q;
+      const unsigned int qv = quant_u8(o * kWInv);
+      pk[x >> 2] = (x & 3) ? (pk[x >> 2] | (qv << (8 * (x & 3)))) : qv;
     }
     unsigned char* orow = sm.ost + c * 1024 + yo * 32;
     if (smem_in_bounds(orow, 32, err)) {
@@ -451,8 +488,8 @@ __device__ __forceinline__ bool t5_item(const Item& it, float c_tap, const T5Sme
     }
     tc05_fence_before();
   }
-  k.gc += Q;
-  if (map) k.gt += Q;
+  k.gr += Q;
+  k.gc += it.nsl * it.nchunks;
   k.gtile += tile_base;
   k.gslab += it.nsl;
   k.gitem += 1;
@@ -460,13 +497,16 @@ __device__ __forceinline__ bool t5_item(const Item& it, float c_tap, const T5Sme
   if (*abort) {
     // a wait gave up: let the row loads still in flight land and every MMA
     // issued finish (bounded waits) before the CTA stops
-    if (prod) {  // at most kStages5 chunks were requested and not yet seen: one pending phase each
-      for (int qq = ring_seen; qq < issued; ++qq) {
-        const int g2 = gt_base + qq;
-        mbar_wait(&bars->ring[g2 % kStages5], (unsigned int)(g2 / kStages5) & 1u);
+    if (prod) {
+      // requested chunks whose stage was not released yet: one pending phase each
+      for (int qq = 0; qq < issued; ++qq) {
+        const int g2 = gr_base + qq;
+        if (!mbar_test(&bars->ringfree[g2 % kStages5], g2 / kStages5))
+          mbar_wait(&bars->ring[g2 % kStages5], (unsigned int)(g2 / kStages5) & 1u);
       }
+      mbar_wait(&bars->d2, (unsigned int)(k.gitem - 1) & 1u);  // the item's commit follows its pass-2 MMAs
     }
-    if (ctl) mbar_wait(&bars->d2, (unsigned int)(k.gitem - 1) & 1u);  // the item's commit follows all its MMAs
+    if (tilew && lane == 0) mbar_wait(&bars->tdone[warp - 1], (unsigned int)(k.gslab - 1) & 1u);
     __syncthreads();
     return false;
   }
@@ -525,13 +565,15 @@ tc05_forward_kernel(const __grid_constant__ FrameSource src, Workspace ws, int r
   __shared__ unsigned int s_tmem;
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kStages5; ++i) mbar_init(&bars.ring[i], 1);
-    for (int i = 0; i < kA1Bufs5; ++i) {
-      mbar_init(&bars.conv[i], 7);
-      mbar_init(&bars.a1free[i], 1);
+    for (int i = 0; i < kStages5; ++i) {
+      mbar_init(&bars.ring[i], 1);
+      mbar_init(&bars.ringfree[i], kTiles);
     }
-    mbar_init(&bars.slab, 1);
-    mbar_init(&bars.d1free, 4);
+    for (int t = 0; t < kTiles; ++t) {
+      for (int i = 0; i < kA1Bufs5; ++i) mbar_init(&bars.a1free[t][i], 1);
+      mbar_init(&bars.tdone[t], 2);
+      mbar_init(&bars.d1free[t], 4);
+    }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&bars.a2full[i], 4);
       mbar_init(&bars.a2free[i], 1);
@@ -556,6 +598,10 @@ tc05_forward_kernel(const __grid_constant__ FrameSource src, Workspace ws, int r
   tc_item_loop<RB, kC5, true, 8, kSlabEl5>(
       src, tmap1, ws, rmax, bl, reinterpret_cast<int*>(smem + L.starts),
       [&](const Item& it, float c, const void* map, bool map_global, auto& lookahead) {
+        if (!map) {  // rows TMA cannot address: the host runs the mma.sync kernel for such launches
+          if (threadIdx.x == 0) atomicOr(ws.counters + CNT_ERROR, kFaultRadiusBound);
+          return true;
+        }
         return t5_item<RB>(it, c, sm, &bars, nent, tmem, &s_abort, map, map_global, k, ws.counters + CNT_ERROR,
                            lookahead);
       });
