@@ -277,8 +277,9 @@ typedef struct {
                          vertical pass on tcgen05 with its accumulator in tensor
                          memory (radius bound <= 255 and 16 or 32 rows per chunk,
                          else as 1); 3 both passes on tcgen05, accumulators in
-                         tensor memory (RGB frames, radius bound <= 511, 16 or
-                         32 rows per chunk, else as 1); 0: fp32 FMA kernel */
+                         tensor memory, one CTA per SM (RGB frames whose rows
+                         TMA can load, radius bound <= 256, 16 rows per
+                         chunk, else as 1); 0: fp32 FMA kernel */
 } fovea_config;
 
 /* Copy the context's current configuration into *cfg. FOVEA_EINVAL for a

@@ -292,7 +292,7 @@ int sigma_grid(long long items, int num_sms) {
 int tc_kind(const FwdConfig& cfg, int fmt_mask, int tc_c, int rmax, bool all_tma = true) {
   if (!cfg.tc || fmt_mask != 1 || tc_c <= 0) return 0;
   if (cfg.tc == 2 && rmax <= kUmmaMaxRadius && cfg.rows_per_chunk <= 32) return 2;
-  if (cfg.tc == 3 && all_tma && tc05_supports(rmax, tc_c) && cfg.rows_per_chunk <= 32) return 3;
+  if (cfg.tc == 3 && all_tma && tc05_supports(rmax, tc_c) && cfg.rows_per_chunk == 16) return 3;
   return 1;
 }
 

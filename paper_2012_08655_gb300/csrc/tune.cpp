@@ -133,7 +133,7 @@ std::vector<fovea_config> candidates(int fmt_mask, int channels) {
       for (int rb : rbs) v.push_back(fovea_config{nt, 0, rb, 1});
     for (int rb : {16, 32}) v.push_back(fovea_config{256, 0, rb, 2});
     if (channels == 3)
-      for (int rb : {16, 32}) v.push_back(fovea_config{256, 0, rb, 3});
+      v.push_back(fovea_config{256, 0, 16, 3});
   }
   return v;
 }

@@ -69,7 +69,7 @@ def run_cases(fv, torch):
                 if (h, w) == (2160, 3840) and skew:
                     continue
                 g = Guarded(torch, (h, w, c), torch.uint8, skew)
-                ctx.set_config(nt, 0, 32, tensor_cores=tc)
+                ctx.set_config(nt, 0, 16 if tc == 3 else 32, tensor_cores=tc)
                 ctx.render(x, g.t, 0.3 * w, 0.6 * h)
                 torch.cuda.synchronize()
                 expect(g.intact(), f"render u8 {h}x{w}x{c} tc={tc} threads={nt} skew={skew}")
@@ -96,7 +96,7 @@ def run_cases(fv, torch):
         guards.append(g)
     bctx = fv.batch_context(32)
     for tc, nt in [(0, 256), (1, 128), (1, 512), (2, 256), (3, 256)]:
-        bctx.set_config(nt, 0, 32, tensor_cores=tc)
+        bctx.set_config(nt, 0, 16 if tc == 3 else 32, tensor_cores=tc)
         bctx.render_batch(frames)
         torch.cuda.synchronize()
         for i, g in enumerate(guards):
@@ -131,7 +131,7 @@ def run_cases(fv, torch):
         x = torch.from_numpy(img).to(dev)
         ctx = fv.Context(w, h, c, 32, 0.5, 0.05, fv.U8_HWC)
         for tc in (0, 1):
-            ctx.set_config(256, 0, 32, tensor_cores=tc)
+            ctx.set_config(256, 0, 16 if tc == 3 else 32, tensor_cores=tc)
             g = Guarded(torch, (h, w, c), torch.uint8, 3)
             ctx.render_pixelwise(x, g.t, 10.0, 20.0)
             torch.cuda.synchronize()

@@ -62,7 +62,7 @@ def test_batch_mixing_tma_and_plain_frames(fv, tc, threads):
         frames.append(fv.BatchFrame(x, torch.empty_like(x), fx, fy, 0.5, 0.03))
         imgs.append(img)
     ctx = fv.batch_context(32)
-    ctx.set_config(threads, 0, 32, tensor_cores=tc)
+    ctx.set_config(threads, 0, 16 if tc == 3 else 32, tensor_cores=tc)
     for rep in range(2):  # the second launch starts from the barrier phases the first one left
         for f in frames:
             f.out.zero_()

@@ -28,7 +28,7 @@ def render(fv, img, fmt, B, fx, fy, s0, k, tc):
     x = to_dev(img)
     w, h, c = fv._shape_of(x, fmt)
     ctx = fv.Context(w, h, c, B, s0, k, fmt)
-    ctx.set_config(256, 0, 32, tensor_cores=tc)
+    ctx.set_config(256, 0, 16 if tc == 3 else 32, tensor_cores=tc)
     y = torch.empty_like(x)
     ctx.render(x, y, fx, fy)
     torch.cuda.synchronize()

@@ -218,12 +218,14 @@ def test_render_host_pipelined_calls(fv):
 
 @pytest.mark.parametrize("tc", [0, 1, 2, 3])
 def test_every_config_gives_identical_output(fv, tc):
-    """Within one kernel, the row chunk and the CTA count change nothing."""
+    """Within one kernel, the row chunk and the CTA count change nothing
+    (kernel 3 stages 16-row chunks only and runs one CTA per SM whatever the
+    requested count)."""
     s = wl.frame_1080p(seed=9)
     x = to_dev(s.image)
     ctx = fv.Context(1920, 1080, 3, 32, s.sigma0, s.k, fv.U8_HWC)
     outs = []
-    for rb in ((16, 32) if tc in (2, 3) else (16, 32, 64)):
+    for rb in ((16,) if tc == 3 else (16, 32) if tc == 2 else (16, 32, 64)):
         for ctas in (1, 2, 0):
             ctx.set_config(256, ctas, rb, tensor_cores=tc)
             y = torch.empty_like(x)
@@ -291,7 +293,7 @@ def test_tensor_core_kernel_matches_fp32_kernel(fv, W, H, C, B, fx, fy, k, tc, t
     ctx.set_config(256, 0, 32, tensor_cores=0)
     y32 = torch.empty_like(x)
     ctx.render(x, y32, fx, fy)
-    ctx.set_config(threads, 0, 32, tensor_cores=tc)
+    ctx.set_config(threads, 0, 16 if tc == 3 else 32, tensor_cores=tc)
     ytc = torch.empty_like(x)
     ctx.render(x, ytc, fx, fy)
     torch.cuda.synchronize()

@@ -60,7 +60,7 @@ def test_geisler_perry_sigma_table_bit_exact(fv):
 def test_centred_grid_u8_matches_oracle(fv, tc, W, H, C, B, fx, fy, k):
     img = wl.grating_frame(H, W, C, seed=W + B)
     ctx = fv.Context(W, H, C, B, 0.5, k, fv.U8_HWC, grid=fv.GRID_CENTRED)
-    ctx.set_config(256, 0, 32, tensor_cores=tc)
+    ctx.set_config(256, 0, 16 if tc == 3 else 32, tensor_cores=tc)
     x = to_dev(img)
     y = torch.empty_like(x)
     ctx.render(x, y, fx, fy)
@@ -92,7 +92,7 @@ def test_geisler_perry_frame_matches_oracle(fv, tc):
     W, H, ec = 640, 480, 30.0
     img = wl.grating_frame(H, W, 3, seed=41)
     ctx = fv.Context(W, H, 3, 32, fmt=fv.U8_HWC, law=fv.LAW_GEISLER_PERRY, e_corner=ec)
-    ctx.set_config(256, 0, 32, tensor_cores=tc)
+    ctx.set_config(256, 0, 16 if tc == 3 else 32, tensor_cores=tc)
     x = to_dev(img)
     y = torch.empty_like(x)
     ctx.render(x, y, 500.0, 100.0)
@@ -110,7 +110,7 @@ def test_sigma_map_matches_oracle(fv, tc):
     smap[0, 0] = 0.0                      # identity block
     img = wl.grating_frame(H, W, C, seed=52)
     ctx = fv.Context(W, H, C, B, fmt=fv.U8_HWC, law=fv.LAW_MAP, sigma_map=to_dev(smap))
-    ctx.set_config(256, 0, 32, tensor_cores=tc)
+    ctx.set_config(256, 0, 16 if tc == 3 else 32, tensor_cores=tc)
     x = to_dev(img)
     y = torch.empty_like(x)
     ctx.render(x, y, 0.0, 0.0)
@@ -161,7 +161,7 @@ def test_block_64_u8_matches_oracle(fv, tc, grid):
     img = wl.grating_frame(H, W, C, seed=81)
     fx, fy = 210.7, 140.2
     ctx = fv.Context(W, H, C, B, 0.5, 0.02, fv.U8_HWC, grid=grid)
-    ctx.set_config(256, 0, 32, tensor_cores=tc)
+    ctx.set_config(256, 0, 16 if tc == 3 else 32, tensor_cores=tc)
     x = to_dev(img)
     y = torch.empty_like(x)
     ctx.render(x, y, fx, fy)
