@@ -61,7 +61,10 @@ KERNELS = {
         ("tc_forward.cu", "tc_common.cuh", "fwd_common.cuh", "fovea_internal.cuh")),
     2: ("umma_forward_kernel (vertical pass tcgen05 + TMEM, horizontal pass mma.sync)",
         os.path.join(ROOT, "profiles", "umma_forward_kernel_1080p_u8.txt"),
-        ("umma_forward.cu", "tc_common.cuh", "fwd_common.cuh", "fovea_internal.cuh")),
+        ("umma_forward.cu", "tc05_common.cuh", "tc_common.cuh", "fwd_common.cuh", "fovea_internal.cuh")),
+    3: ("tc05_forward_kernel (both passes tcgen05 + TMEM, warp-specialised pipeline)",
+        os.path.join(ROOT, "profiles", "tc05_forward_kernel_1080p_u8.txt"),
+        ("tc05_forward.cu", "tc05_common.cuh", "tc_common.cuh", "fwd_common.cuh", "fovea_internal.cuh")),
 }
 
 
@@ -79,9 +82,9 @@ def parse_args():
     p.add_argument("--train-only", action="store_true",
                    help="run only the float32 training leg (forward and backward) and print it")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiling runs)")
-    p.add_argument("--tensor-cores", type=int, choices=[0, 1, 2], default=None,
-                   help="force the forward kernel (0: fp32 FMA, 1: mma.sync, 2: tcgen05 vertical pass) "
-                        "instead of autotuning")
+    p.add_argument("--tensor-cores", type=int, choices=[0, 1, 2, 3], default=None,
+                   help="force the forward kernel (0: fp32 FMA, 1: mma.sync, 2: tcgen05 vertical pass, "
+                        "3: both passes on tcgen05) instead of autotuning")
     p.add_argument("--rows-per-chunk", type=int, choices=[16, 32, 64], default=32,
                    help="row chunk of the forced kernel (with --tensor-cores)")
     return p.parse_args()

@@ -606,6 +606,16 @@ static int render_one(fovea_ctx* ctx, const void* in_dev, void* out_dev, float f
                  make_u8_tensor_map(map, src.one.in, src.one.W, src.one.H, src.one.C, ctx->cfg.rows_per_chunk)) ? 1 : 0;
   int grid = forward_grid(ctx, ctx->cfg, rmax, fmt_mask, tc_c, src.one.tma != 0);
   if (grid <= 0) return FOVEA_EUNSUPPORTED;
+  const int kind = tc_kind(ctx->cfg, fmt_mask, tc_c, rmax, src.one.tma != 0);
+  if (kind == 0 && src.one_total <= grid) {
+    // every block fits in one wave: one launch, one CTA per block, each
+    // evaluating its own sigma (no sigma kernel, no work list)
+    if (ctx->kev_start) FOVEA_CUDA(cudaEventRecord(ctx->kev_start, s));
+    cudaError_t e = launch_forward_direct(src.one, src.one_total, ctx->ws, ctx->cfg, rmax, fmt_mask, s, !ctx->kev_start);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (ctx->kev_stop) FOVEA_CUDA(cudaEventRecord(ctx->kev_stop, s));
+    return FOVEA_OK;
+  }
   // no more persistent CTAs than items (small frames start fewer CTAs)
   grid = (int)std::min<long long>(grid, src.one_total);
   // Single frame: the sigma kernel also files every block under its radius
@@ -634,7 +644,6 @@ static int render_one(fovea_ctx* ctx, const void* in_dev, void* out_dev, float f
   // Programmatic dependent launch lets the blur kernel's prologue overlap the
   // sigma kernel (not when its launch is bracketed by timing events).
   const bool pdl = bl.list && !ctx->kev_start;
-  const int kind = tc_kind(ctx->cfg, fmt_mask, tc_c, rmax, src.one.tma != 0);
   if (kind) {
     e = kind == 3   ? launch_tc05_forward(src, ctx->ws, ctx->cfg, rmax, grid, s, bl, pdl, map)
         : kind == 2 ? launch_umma_forward(src, ctx->ws, ctx->cfg, rmax, tc_c, grid, s, bl, pdl, map)

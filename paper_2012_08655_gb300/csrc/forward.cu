@@ -217,6 +217,88 @@ __device__ __forceinline__ void process_item(const Item& it, const Smem& sm, flo
   }
 }
 
+// One item (one block of one frame), start to finish: stage its folded halo
+// tile, build its taps, run both passes and store the block. Every thread of
+// the CTA calls it; `c` is -1 / (2 sigma^2). taps_ready: U and CU already
+// hold the item's taps and their prefix sums.
+template <int RB, int MODE>
+__device__ __forceinline__ void run_item(const Item& it, float c, const Smem& sm, float2* U, float* CU, float* red,
+                                         unsigned int* err, bool taps_ready = false) {
+  const int tid = threadIdx.x;
+  const int g2 = tid >> 6, c2 = (tid >> 4) & 3, p2 = tid & 15;
+  const bool u8 = MODE == 0 ? true : (MODE == 1 ? false : it.isu8);
+  const int r = it.r;
+
+  // Start staging before the taps are ready: the copies do not need them.
+  {
+    constexpr int rbu = kRowBytesU8, rbf = kRowBytesF32;
+    #pragma unroll
+    for (int q = 0; q < mode_stages(MODE) - 1; ++q) {
+      const int Q = (u8 ? it.nsl : it.nsl * it.C) * it.nchunks;
+      if (q < Q) {
+        if (MODE != 1 && u8) stage_rows<true, RB>(it, slab_of<true>(it, q / it.nchunks), q % it.nchunks,
+                                                  sm.ring + (size_t)q * RB * rbu, (size_t)it.H * it.pitch);
+        if (MODE != 0 && !u8) stage_rows<false, RB>(it, slab_of<false>(it, q / it.nchunks), q % it.nchunks,
+                                                    sm.ring + (size_t)q * RB * rbf, (size_t)it.H * it.pitch * it.C);
+      }
+      cp_async_commit();
+    }
+  }
+  if (!taps_ready) {
+    make_taps(U, tap_len(r), r, c, red);
+    make_cumulative(U, CU, r);
+  }
+  __syncthreads();
+
+  float2 acc2[8];
+  #pragma unroll
+  for (int j = 0; j < 8; ++j) acc2[j] = make_float2(0.f, 0.f);
+  if (MODE != 1 && u8) process_item<true, RB, mode_stages(MODE)>(it, sm, acc2);
+  if (MODE != 0 && !u8) process_item<false, RB, mode_stages(MODE)>(it, sm, acc2);
+
+  cp_async_wait<0>();
+  __syncthreads();  // ring no longer read; it becomes the output stage
+
+  const int groups2 = (it.bw + 7) >> 3, xg = 8 * g2;
+  const bool act2base = g2 < groups2 && c2 < it.C && 2 * p2 < it.bh;
+  if (!u8) {
+    if (act2base) {
+      float* out = reinterpret_cast<float*>(it.out) + (size_t)c2 * it.W * it.H +
+                   (size_t)(it.y0 + 2 * p2) * it.W + it.x0;
+      const bool second = 2 * p2 + 1 < it.bh;
+      #pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int x = xg + j;
+        if (x < it.bw) {
+          const size_t plane_bytes = (size_t)it.W * it.H * it.C * 4;
+          if (in_bounds(out + x, 4, it.out, plane_bytes, err)) out[x] = acc2[j].x;
+          if (second && in_bounds(out + it.W + x, 4, it.out, plane_bytes, err))
+            out[it.W + x] = acc2[j].y;
+        }
+      }
+    }
+  } else {
+    unsigned char* ost = sm.ring;
+    const int opitch = 32 * it.C;
+    if (act2base) {
+      #pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int x = xg + j;
+        ost[(2 * p2) * opitch + x * it.C + c2] = quant_u8(acc2[j].x);
+        ost[(2 * p2 + 1) * opitch + x * it.C + c2] = quant_u8(acc2[j].y);
+      }
+    }
+    __syncthreads();
+    const int rowBytes = it.bw * it.C;
+    unsigned char* out = it.out + (size_t)it.y0 * it.pitch + (size_t)it.x0 * it.C;
+    for (int idx = tid; idx < it.bh * rowBytes; idx += kThreads) {
+      const int yo = idx / rowBytes, rem = idx - yo * rowBytes;
+      unsigned char* o = out + (size_t)yo * it.pitch + rem;
+      if (in_bounds(o, 1, it.out, (size_t)it.H * it.pitch, err)) *o = ost[yo * opitch + rem];
+    }
+  }
+}
+
 // MODE 0: uint8 frames only; 1: float32 frames only; 2: both (batches).
 template <int RB, int MODE>
 __global__ void __launch_bounds__(kThreads, 2)
@@ -238,7 +320,6 @@ forward_kernel(FrameSource src, Workspace ws, int rmax, int row_bytes, BucketLis
   __shared__ int s_wsum[kThreads / 32];
 
   const int tid = threadIdx.x;
-  const int g2 = tid >> 6, c2 = (tid >> 4) & 3, p2 = tid & 15;
   // The VV pads must read as zeros: clear the whole buffer once.
   for (int i = tid; i < 16 * kVVPitch; i += kThreads) sm.VV[i] = make_float2(0.f, 0.f);
   // Launched as a programmatic dependent of the sigma kernel: wait for its
@@ -289,76 +370,7 @@ forward_kernel(FrameSource src, Workspace ws, int rmax, int row_bytes, BucketLis
     __syncthreads();
     if (s_state == 2) break;
     if (s_state == 1) continue;
-    const Item& it = s_it;
-    const bool u8 = MODE == 0 ? true : (MODE == 1 ? false : it.isu8);
-    const int r = it.r;
-
-    // Start staging before the taps are ready: the copies do not need them.
-    {
-      constexpr int rbu = kRowBytesU8, rbf = kRowBytesF32;
-      #pragma unroll
-      for (int q = 0; q < mode_stages(MODE) - 1; ++q) {
-        const int Q = (u8 ? it.nsl : it.nsl * it.C) * it.nchunks;
-        if (q < Q) {
-          if (MODE != 1 && u8) stage_rows<true, RB>(it, slab_of<true>(it, q / it.nchunks), q % it.nchunks,
-                                                    sm.ring + (size_t)q * RB * rbu, (size_t)it.H * it.pitch);
-          if (MODE != 0 && !u8) stage_rows<false, RB>(it, slab_of<false>(it, q / it.nchunks), q % it.nchunks,
-                                                      sm.ring + (size_t)q * RB * rbf, (size_t)it.H * it.pitch * it.C);
-        }
-        cp_async_commit();
-      }
-    }
-    make_taps(U, tap_len(r), r, s_c, red);
-    make_cumulative(U, CU, r);
-    __syncthreads();
-
-    float2 acc2[8];
-    #pragma unroll
-    for (int j = 0; j < 8; ++j) acc2[j] = make_float2(0.f, 0.f);
-    if (MODE != 1 && u8) process_item<true, RB, mode_stages(MODE)>(it, sm, acc2);
-    if (MODE != 0 && !u8) process_item<false, RB, mode_stages(MODE)>(it, sm, acc2);
-
-    cp_async_wait<0>();
-    __syncthreads();  // ring no longer read; it becomes the output stage
-
-    const int groups2 = (it.bw + 7) >> 3, xg = 8 * g2;
-    const bool act2base = g2 < groups2 && c2 < it.C && 2 * p2 < it.bh;
-    if (!u8) {
-      if (act2base) {
-        float* out = reinterpret_cast<float*>(it.out) + (size_t)c2 * it.W * it.H +
-                     (size_t)(it.y0 + 2 * p2) * it.W + it.x0;
-        const bool second = 2 * p2 + 1 < it.bh;
-        #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int x = xg + j;
-          if (x < it.bw) {
-            const size_t plane_bytes = (size_t)it.W * it.H * it.C * 4;
-            if (in_bounds(out + x, 4, it.out, plane_bytes, ws.counters + CNT_ERROR)) out[x] = acc2[j].x;
-            if (second && in_bounds(out + it.W + x, 4, it.out, plane_bytes, ws.counters + CNT_ERROR))
-              out[it.W + x] = acc2[j].y;
-          }
-        }
-      }
-    } else {
-      unsigned char* ost = sm.ring;
-      const int opitch = 32 * it.C;
-      if (act2base) {
-        #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int x = xg + j;
-          ost[(2 * p2) * opitch + x * it.C + c2] = quant_u8(acc2[j].x);
-          ost[(2 * p2 + 1) * opitch + x * it.C + c2] = quant_u8(acc2[j].y);
-        }
-      }
-      __syncthreads();
-      const int rowBytes = it.bw * it.C;
-      unsigned char* out = it.out + (size_t)it.y0 * it.pitch + (size_t)it.x0 * it.C;
-      for (int idx = tid; idx < it.bh * rowBytes; idx += kThreads) {
-        const int yo = idx / rowBytes, rem = idx - yo * rowBytes;
-        unsigned char* o = out + (size_t)yo * it.pitch + rem;
-        if (in_bounds(o, 1, it.out, (size_t)it.H * it.pitch, ws.counters + CNT_ERROR)) *o = ost[yo * opitch + rem];
-      }
-    }
+    run_item<RB, MODE>(s_it, s_c, sm, U, CU, red, ws.counters + CNT_ERROR);
   }
   cp_async_wait<0>();
   if (own_order) {
@@ -376,6 +388,73 @@ forward_kernel(FrameSource src, Workspace ws, int rmax, int row_bytes, BucketLis
       }
     }
   }
+}
+
+// Single-launch form for frames with no more blocks than one wave of CTAs:
+// CTA b serves tile b alone. It evaluates the block's sigma itself (the
+// sigma kernel's item_record, so the radius and taps are the same bit for
+// bit) and runs the same item body, so no sigma kernel, work list or ticket
+// precedes it: a small frame costs one launch and one CTA's latency. As a
+// programmatic dependent launch it builds the block's sigma and taps (kernel
+// arguments only) before it waits for the previous grid, and lets the next
+// launch start as soon as every CTA got that far; a sigma map, the frame and
+// the output are touched only after the wait.
+template <int RB, int MODE>
+__global__ void __launch_bounds__(kThreads, 2)
+direct_kernel(const __grid_constant__ FrameDesc fd, Workspace ws, int rmax, int row_bytes) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const SmemLayout L = smem_layout(RB, row_bytes, rmax, mode_stages(MODE));
+  Smem sm;
+  sm.ring = smem + L.ring;
+  sm.VV = reinterpret_cast<float2*>(smem + L.vv);
+  float2* U = reinterpret_cast<float2*>(smem + L.taps);
+  float* CU = reinterpret_cast<float*>(smem + L.cum);
+  sm.U = U;
+  sm.CU = CU;
+  float* red = reinterpret_cast<float*>(smem + L.red);
+  __shared__ int s_state;
+  __shared__ Item s_it;
+  __shared__ float s_c;
+  const int tid = threadIdx.x;
+  unsigned int* err = ws.counters + CNT_ERROR;
+  auto record = [&]() {  // thread 0: the block's item and geometry
+    const ItemInfo inf = item_record(fd, 0, (int)blockIdx.x, err);
+    const bool u8f = fd.fmt == FOVEA_U8_HWC;
+    if (inf.r > rmax || (MODE == 0 ? !u8f : u8f)) {
+      atomicOr(err, kFaultRadiusBound);
+      s_state = 1;
+    } else {
+      item_geometry(s_it, inf, fd, RB);
+      s_c = inf.neg_half_inv_s2;
+      s_state = 0;
+    }
+  };
+  for (int i = tid; i < 16 * kVVPitch; i += kThreads) sm.VV[i] = make_float2(0.f, 0.f);
+  const bool early = fd.smap == nullptr;  // the law reads no device memory
+  if (early) {
+    if (tid == 0) record();
+    __syncthreads();
+    if (s_state == 0) {
+      make_taps(U, tap_len(s_it.r), s_it.r, s_c, red);
+      make_cumulative(U, CU, s_it.r);
+    }
+  }
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (!early) {
+    if (tid == 0) record();
+    __syncthreads();
+  }
+  if (s_state == 0) run_item<RB, MODE>(s_it, s_c, sm, U, CU, red, err, early);
+  cp_async_wait<0>();
+}
+
+template <int RB, int MODE>
+void* direct_ptr() { return reinterpret_cast<void*>(&direct_kernel<RB, MODE>); }
+
+void* pick_direct(int rb, int mode) {
+  if (mode == 0) return rb == 16 ? direct_ptr<16, 0>() : (rb == 64 ? direct_ptr<64, 0>() : direct_ptr<32, 0>());
+  return rb == 16 ? direct_ptr<16, 1>() : (rb == 64 ? direct_ptr<64, 1>() : direct_ptr<32, 1>());
 }
 
 template <int RB, int MODE>
@@ -447,6 +526,40 @@ cudaError_t launch_forward(const FrameSource& src, const Workspace& ws, const Fw
   void* args[] = {const_cast<FrameSource*>(&src), const_cast<Workspace*>(&ws), &rmax, &row_bytes, &b};
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(grid);
+  lc.blockDim = dim3(kThreads);
+  lc.dynamicSmemBytes = smem;
+  lc.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = attr;
+  lc.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelExC(&lc, k, args);
+}
+
+cudaError_t launch_forward_direct(const FrameDesc& fd, long long items, const Workspace& ws, const FwdConfig& cfg,
+                                  int rmax, int fmt_mask, cudaStream_t s, bool pdl) {
+  if (fmt_mask != 1 && fmt_mask != 2) return cudaErrorInvalidValue;
+  int row_bytes = fmt_mask == 2 ? kRowBytesF32 : kRowBytesU8;
+  // 64-row chunks where they fit: a halo of up to 64 rows is then staged in
+  // one chunk, one global-memory round trip (a single wave needs no second
+  // CTA per SM); the chunk size does not change the result
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return cudaGetLastError();
+  const int st = mode_stages(mode_of(fmt_mask));
+  int rb = smem_layout(64, row_bytes, rmax, st).total + 2048 <= (size_t)optin ? 64 : effective_rb(cfg, rmax, fmt_mask);
+  (void)cfg;
+  const size_t smem = smem_layout(rb, row_bytes, rmax, st).total;
+  void* k = pick_direct(rb, mode_of(fmt_mask));
+  cudaError_t e = set_smem_attrs(reinterpret_cast<const void*>(k), smem);
+  if (e != cudaSuccess) return e;
+  FrameDesc d = fd;
+  Workspace w = ws;
+  void* args[] = {&d, &w, &rmax, &row_bytes};
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned int)items);
   lc.blockDim = dim3(kThreads);
   lc.dynamicSmemBytes = smem;
   lc.stream = s;

@@ -178,6 +178,32 @@ __device__ __forceinline__ bool item_sigma(const FrameDesc& fd, int bx, int by, 
   return clamped;
 }
 
+// The work record of tile b of frame f (frame descriptor fd): sigma from the
+// frame's law in binary64, its radius, and -1 / (2 sigma^2). Out-of-range
+// sigma-map values and radii are clamped and flagged in *err (the sigma
+// kernel and the single-launch small-frame kernel both build items here, so
+// they agree bit for bit).
+__device__ __forceinline__ ItemInfo item_record(const FrameDesc& fd, int f, int b, unsigned int* err) {
+  const int tpb = fd.B / fd.T;  // tiles per block side
+  const int bx = (b % fd.nbx) / tpb, by = (b / fd.nbx) / tpb;
+  double sigma;
+  int r;
+  if (item_sigma(fd, bx, by, sigma, r)) atomicOr(err, kFaultSigmaRange);
+  if (r > kMaxRadius || r < 0) {  // the host refuses such laws and map bounds: never expected
+    r = r < 0 ? 0 : kMaxRadius;
+    if (!(sigma >= 0.0)) sigma = 0.0;
+    atomicOr(err, kFaultSigmaRange);
+  }
+  ItemInfo inf;
+  inf.sigma = (float)sigma;
+  inf.neg_half_inv_s2 = sigma > 0.0 ? (float)__ddiv_rn(-0.5, __dmul_rn(sigma, sigma)) : -INFINITY;
+  inf.r = r;
+  inf.frame = f;
+  inf.block = b;
+  inf.pad = 0;
+  return inf;
+}
+
 // Packed two-lane FMA: d = a * b + c on both float lanes (one f32x2
 // instruction on sm_100-family GPUs).
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
@@ -350,6 +376,11 @@ size_t forward_smem_bytes(const FwdConfig& cfg, int rmax, int fmt_mask);
 // With bl.list set, the kernel orders its own work from the radius histogram
 // and bucket lists (single frame), and it may be launched as a programmatic
 // dependent of the sigma kernel (pdl).
+// One frame whose blocks all fit in one wave: one CTA per block, sigma
+// evaluated in the CTA (no sigma kernel before it). fmt_mask 1 or 2; pdl:
+// launch as a programmatic dependent of the stream's previous kernel.
+cudaError_t launch_forward_direct(const FrameDesc& fd, long long items, const Workspace& ws, const FwdConfig& cfg,
+                                  int rmax, int fmt_mask, cudaStream_t s, bool pdl);
 cudaError_t launch_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg,
                            int rmax, int fmt_mask, int grid, cudaStream_t s,
                            const BucketList& bl = BucketList{nullptr, 0, 0}, bool pdl = false);

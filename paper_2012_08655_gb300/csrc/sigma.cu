@@ -35,23 +35,8 @@ __global__ void __launch_bounds__(kSigmaThreads) sigma_kernel(FrameSource src, W
     const int f = frame_of_item(src, i);
     const FrameDesc fd = load_frame(src, f);
     const int b = (int)(i - fd.item0);        // tile index
-    const int tpb = fd.B / fd.T;              // tiles per block side
-    const int bx = (b % fd.nbx) / tpb, by = (b / fd.nbx) / tpb;
-    double sigma;
-    int r;
-    if (item_sigma(fd, bx, by, sigma, r)) atomicOr(&ws.counters[CNT_ERROR], kFaultSigmaRange);
-    if (r > kMaxRadius || r < 0) {  // the host refuses such laws and map bounds: never expected
-      r = r < 0 ? 0 : kMaxRadius;
-      if (!(sigma >= 0.0)) sigma = 0.0;
-      atomicOr(&ws.counters[CNT_ERROR], kFaultSigmaRange);
-    }
-    ItemInfo inf;
-    inf.sigma = (float)sigma;
-    inf.neg_half_inv_s2 = sigma > 0.0 ? (float)__ddiv_rn(-0.5, __dmul_rn(sigma, sigma)) : -INFINITY;
-    inf.r = r;
-    inf.frame = f;
-    inf.block = b;
-    inf.pad = 0;
+    const ItemInfo inf = item_record(fd, f, b, &ws.counters[CNT_ERROR]);
+    const int r = inf.r;
     ws.items[i] = inf;
     const int bucket = r < kBuckets ? r : kBuckets - 1;
     const int rank = (int)atomicAdd(&hist[bucket], 1u);
@@ -60,7 +45,7 @@ __global__ void __launch_bounds__(kSigmaThreads) sigma_kernel(FrameSource src, W
       if (bucket < bl.nb && rank < bl.cap) bl.list[(size_t)bucket * bl.cap + rank] = (int)i;
       else atomicOr(&ws.counters[CNT_ERROR], kFaultBuckets);
     }
-    if (sigma_out) sigma_out[i] = (float)sigma;
+    if (sigma_out) sigma_out[i] = inf.sigma;
     if (radius_out) radius_out[i] = r;
   }
   // Let a dependent launch (the blur kernel) start its prologue; it waits for

@@ -112,6 +112,32 @@ def test_forward_edge_cases(fv, W, H, C, dt, B, fx, fy, s0, k):
         assert torch.equal(y, x)
 
 
+@pytest.mark.parametrize("W,H,C,dt,B,fx,fy,s0,k", EDGE[:10] + [(256, 256, 1, "f32", 32, 128.0, 128.0, 0.5, 0.02)])
+def test_single_wave_frames_match_the_persistent_kernel(fv, W, H, C, dt, B, fx, fy, s0, k):
+    """A frame with no more blocks than one wave of CTAs runs as one launch
+    with one CTA per block (sigma evaluated in the CTA); the same frame in a
+    batch runs the persistent kernel behind the sigma kernel. Same item body,
+    same sigma: bit-equal outputs."""
+    if dt == "u8":
+        img = wl.uniform_u8((H, W, C), seed=W + 5 * H)
+        fmt = fv.U8_HWC
+    else:
+        img = wl.uniform_f32((C, H, W), seed=W + 5 * H)
+        fmt = fv.F32_CHW
+    x = to_dev(img)
+    ctx = fv.Context(W, H, C, B, s0, k, fmt)
+    ctx.set_config(256, 0, 32, tensor_cores=0)
+    y1 = torch.empty_like(x)
+    ctx.render(x, y1, fx, fy)
+    bctx = fv.batch_context(B)
+    bctx.set_config(256, 0, 32, tensor_cores=0)
+    y2 = torch.empty_like(x)
+    bctx.render_batch([fv.BatchFrame(x, y2, fx, fy, s0, k)])
+    torch.cuda.synchronize()
+    assert ctx.check() == 0 and bctx.check() == 0
+    assert torch.equal(y1, y2)
+
+
 def test_u8_uniform_bytes_1080p_sampled(fv):
     img = wl.uniform_u8((1080, 1920, 3), seed=3)
     y = fv.foveate(to_dev(img), 700.25, 300.5, 0.5, 0.02).cpu().numpy()
