@@ -368,6 +368,17 @@ FrameLaw law_of(const fovea_frame& f) {
   return fl;
 }
 
+// Whether p is device memory (not page-locked host memory mapped into the
+// device's address space, nor an address CUDA does not know).
+bool in_device_memory(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 int upload_batch(fovea_ctx* ctx, const FwdConfig& cfg, const fovea_frame* frames, int n, bool adjoint, cudaStream_t s,
                  long long* total, int* rmax, int* fmt_mask, int* tc_c, bool* all_tma) {
   if (n <= 0 || !frames) return FOVEA_EINVAL;
@@ -412,7 +423,9 @@ int upload_batch(fovea_ctx* ctx, const FwdConfig& cfg, const fovea_frame* frames
   for (int i = 0; i < n; ++i) {
     FrameDesc& d = descs[(size_t)i];
     void* map = hbuf + maps_off + (size_t)i * kTensorMapBytes;
-    d.tma = (!adjoint && d.fmt == FOVEA_U8_HWC &&
+    // rows are loaded by TMA only from device memory (a frame in mapped host
+    // memory is staged with plain loads)
+    d.tma = (!adjoint && d.fmt == FOVEA_U8_HWC && in_device_memory(d.in) &&
              make_u8_tensor_map(map, d.in, d.W, d.H, d.C, cfg.rows_per_chunk)) ? 1 : 0;
     if (!d.tma) std::memset(map, 0, kTensorMapBytes);
     every_tma = every_tma && d.tma;
