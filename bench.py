@@ -662,6 +662,46 @@ def pixelwise_leg(fv, torch, reps: int = 20):
     return res
 
 
+def noalloc_leg(fv, torch, reps: int = 200):
+    """fovea_render_noalloc (the entry point that allocates nothing: its
+    scratch is a fixed array inside the library, and it always runs the fp32
+    CUDA-core kernel) on the 1920x1080 RGB uint8 frame, against fovea_render
+    on a context configured for the same kernel and on the context's default
+    (tensor-core) configuration: ms per render, device-resident buffers, CUDA
+    events over `reps` back-to-back calls."""
+    from paper_2012_08655_gb300 import workloads as wl
+    frame = wl.frame_1080p(seed=0)
+    x = torch.from_numpy(frame.image).cuda()
+    y = torch.empty_like(x)
+    cur = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(10):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        for _ in range(reps):
+            fn()
+        e1.record(cur)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    res = {"workload": "1920x1080 RGB uint8 frame, sigma = 0.5 + 0.02 e, fixation (960, 540)"}
+    res["noalloc_ms"] = timed(lambda: fv.render_noalloc(x, y, *FIX, SIGMA0, K_SLOPE, block=B))
+    fv.noalloc_check()
+    ctx = fv.Context(W, H, C, B, SIGMA0, K_SLOPE, fv.U8_HWC)
+    ctx.set_config(256, 0, 32, tensor_cores=0)
+    res["render_fp32_kernel_ms"] = timed(lambda: ctx.render(x, y, *FIX))
+    ctx.set_config(256, 0, 64, tensor_cores=1)
+    res["render_tensor_core_ms"] = timed(lambda: ctx.render(x, y, *FIX))
+    ctx.check()
+    ctx.close()
+    res["note"] = ("the no-allocation call runs the fp32 kernel with a fixed configuration; "
+                   "render_fp32_kernel_ms is the regular entry point on that kernel")
+    return res
+
+
 def served_leg(fv, torch, seconds: float, max_batch: int, world: int = 1, rank: int = 0):
     """Replay the Poisson request stream through the serving loop. With
     world > 1 each rank serves the requests of its streams (stream s on rank
@@ -1000,6 +1040,7 @@ def run_ours(args):
         extras["block_sweep"] = block_sweep_leg(fv, torch)
         extras["pixelwise"] = pixelwise_leg(fv, torch)
         extras["plain_256"] = plain_leg(fv, torch)
+        extras["noalloc"] = noalloc_leg(fv, torch)
         served = served_leg(fv, torch, args.served_seconds, max_batch=64)
         plain = served_leg(fv, torch, args.served_seconds, max_batch=1)
         served["plain_per_frame"] = {k: plain[k] for k in ("p50_ms", "p99_ms", "mpix_s", "mean_batch")}

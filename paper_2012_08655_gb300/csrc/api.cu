@@ -670,18 +670,21 @@ static int render_one(fovea_ctx* ctx, const void* in_dev, void* out_dev, float f
 }
 
 int fovea_render(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x, float fix_y, void* stream) {
+  fovea::TraceRange trace("fovea_render");
   if (!ctx || !in_dev || !out_dev || ctx->batch_only) return FOVEA_EINVAL;
   ctx->caller_stream_used = true;
   return render_one(ctx, in_dev, out_dev, fix_x, fix_y, static_cast<cudaStream_t>(stream));
 }
 
 int fovea_render_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, void* stream) {
+  fovea::TraceRange trace("fovea_render_batch");
   if (!ctx) return FOVEA_EINVAL;
   ctx->caller_stream_used = true;
   return run_batch(ctx, frames, n, false, static_cast<cudaStream_t>(stream));
 }
 
 int fovea_backward_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, void* stream) {
+  fovea::TraceRange trace("fovea_backward_batch");
   if (!ctx) return FOVEA_EINVAL;
   ctx->caller_stream_used = true;
   return run_batch(ctx, frames, n, true, static_cast<cudaStream_t>(stream));
@@ -689,6 +692,7 @@ int fovea_backward_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, void*
 
 int fovea_render_host(fovea_ctx* ctx, const void* in_host, void* out_host, float fix_x, float fix_y,
                       void* stream) {
+  fovea::TraceRange trace("fovea_render_host");
   if (!ctx || !in_host || !out_host || ctx->batch_only) return FOVEA_EINVAL;
   int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->law, fix_x, fix_y);
   if (st != FOVEA_OK) return st;
@@ -751,6 +755,7 @@ int fovea_render_host(fovea_ctx* ctx, const void* in_host, void* out_host, float
 
 int fovea_backward(fovea_ctx* ctx, const float* grad_out_dev, float* grad_in_dev, float fix_x, float fix_y,
                    void* stream) {
+  fovea::TraceRange trace("fovea_backward");
   if (!ctx || !grad_out_dev || !grad_in_dev || ctx->batch_only) return FOVEA_EINVAL;
   if (ctx->fmt != FOVEA_F32_CHW) return FOVEA_EINVAL;
   int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->law, fix_x, fix_y);
@@ -776,6 +781,7 @@ int fovea_backward(fovea_ctx* ctx, const float* grad_out_dev, float* grad_in_dev
 }
 
 int fovea_sigma_table(fovea_ctx* ctx, float fix_x, float fix_y, float* sigma_dev, int* radius_dev, void* stream) {
+  fovea::TraceRange trace("fovea_sigma_table");
   if (!ctx || !sigma_dev || !radius_dev || ctx->batch_only) return FOVEA_EINVAL;
   int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->law, fix_x, fix_y);
   if (st != FOVEA_OK) return st;
@@ -820,6 +826,7 @@ int pixel_radius_bound(int W, int H, double fx, double fy, double sigma0, double
 
 int fovea_render_pixelwise(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x, float fix_y,
                            void* stream) {
+  fovea::TraceRange trace("fovea_render_pixelwise");
   if (!ctx || !in_dev || !out_dev || ctx->batch_only) return FOVEA_EINVAL;
   if (ctx->law.smap) return FOVEA_EINVAL;  // a per-block map gives no per-pixel law
   int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->law, fix_x, fix_y);
@@ -848,6 +855,7 @@ int fovea_render_pixelwise(fovea_ctx* ctx, const void* in_dev, void* out_dev, fl
 
 int fovea_render_pyramid(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x, float fix_y,
                          void* stream) {
+  fovea::TraceRange trace("fovea_render_pyramid");
   if (!ctx || !in_dev || !out_dev || ctx->batch_only) return FOVEA_EINVAL;
   if (ctx->law.smap) return FOVEA_EINVAL;
   int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->law, fix_x, fix_y);
@@ -901,6 +909,7 @@ int fovea_render_pyramid(fovea_ctx* ctx, const void* in_dev, void* out_dev, floa
 
 int fovea_ssim(int width, int height, int channels, int format, const void* a_dev, const void* b_dev,
                double data_range, float* map_dev, double* sum_dev, void* stream) {
+  fovea::TraceRange trace("fovea_ssim");
   if (!a_dev || !b_dev || width <= 0 || height <= 0) return FOVEA_EINVAL;
   if (channels < 1 || channels > 4) return FOVEA_EINVAL;
   if (format != FOVEA_U8_HWC && format != FOVEA_F32_CHW) return FOVEA_EINVAL;

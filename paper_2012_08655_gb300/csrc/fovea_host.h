@@ -3,9 +3,21 @@
 
 #include <stddef.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fovea.h"
 
 namespace fovea {
+
+// One NVTX range over a scope (the library's host phases as named ranges on
+// a profiler's timeline; a push and a pop of a few nanoseconds when no tool
+// is attached).
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Sigma law and block grid of one frame as the host sees it: the linear law
 // (sigma0, k), or a per-block device map with an upper bound of its values;

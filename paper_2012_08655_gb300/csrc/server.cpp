@@ -188,6 +188,7 @@ void fovea_server::run() {
         std::stable_sort(ready.begin(), ready.end(), [](const Request* a, const Request* b) {
           return a->f.format != b->f.format ? a->f.format < b->f.format : a->f.channels < b->f.channels;
         });
+        fovea::TraceRange trace("server batch");
         const double t0 = now_us();
         bool failed = false;
         for (size_t g0 = 0; g0 < ready.size();) {

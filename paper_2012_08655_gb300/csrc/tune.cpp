@@ -206,6 +206,7 @@ bool lookup_batch_config(const fovea_ctx* ctx, const BatchSummary& bs, fovea_con
 }  // namespace fovea
 
 extern "C" int fovea_autotune(fovea_ctx* ctx, int iters, const char* cache_path) {
+  fovea::TraceRange trace("fovea_autotune");
   if (!ctx || iters <= 0) return FOVEA_EINVAL;
   int W, H, C, fmt, B;
   if (fovea::ctx_shape(ctx, &W, &H, &C, &fmt, &B) != FOVEA_OK) return FOVEA_EINVAL;
@@ -256,6 +257,7 @@ extern "C" int fovea_autotune(fovea_ctx* ctx, int iters, const char* cache_path)
 
 extern "C" int fovea_autotune_batch(fovea_ctx* ctx, const fovea_frame* frames, int n, int iters,
                                     const char* cache_path, fovea_config* chosen) {
+  fovea::TraceRange trace("fovea_autotune_batch");
   if (!ctx || !frames || n <= 0 || iters <= 0) return FOVEA_EINVAL;
   fovea::BatchSummary bs;
   int status = fovea::summarize_batch(ctx, frames, n, &bs);
