@@ -13,6 +13,7 @@ law, here sigma = sigma0 + k * eccentricity in pixels).
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 from dataclasses import dataclass
 from typing import Optional, Sequence
@@ -620,16 +621,39 @@ def check_train(block: int = 32, stream=None) -> int:
 
 
 # ------------------------------------------------------------------ serving
+class RequestLog:
+    """Append-only JSON-lines file of served requests (one object per line,
+    keys in insertion order); flushed after every line."""
+
+    def __init__(self, path: str):
+        self._f = open(path, "a", encoding="utf-8")
+
+    def append(self, record: dict):
+        if self._f is None:
+            raise ValueError("request log is closed")
+        self._f.write(json.dumps(record, separators=(",", ":")) + "\n")
+        self._f.flush()
+
+    def close(self):
+        if self._f is not None:
+            self._f.close()
+            self._f = None
+
+
 class Server:
     """Continuous-batching request loop (``fovea_server_*``).
 
     The host tensors of a request are held by this object from ``submit``
     until ``wait`` reports the request done (or until ``close``), so the
-    library's copies never outlive them."""
+    library's copies never outlive them. With ``log_path`` every request
+    that ``wait`` sees finish is appended to that file as one JSON line (its
+    id, frame shape, fixation and the library's timestamps and status)."""
 
     def __init__(self, device_budget_bytes: int = 1 << 30, max_batch: int = 64, block: int = 32,
-                 max_inflight: int = 256):
+                 max_inflight: int = 256, log_path: Optional[str] = None):
         self._held = {}
+        self._log = RequestLog(log_path) if log_path else None
+        self._meta = {}
         cfg = ServerConfig(int(device_budget_bytes), int(max_batch), int(block), int(max_inflight))
         h = _vp()
         _check(_lib.fovea_server_create(ctypes.byref(cfg), ctypes.byref(h)), "fovea_server_create")
@@ -657,16 +681,24 @@ class Server:
         t = self.now_us() if arrival_us is None else float(arrival_us)
         rid = _check(int(_lib.fovea_server_submit(self._h, ctypes.byref(fr), t)), "fovea_server_submit")
         self._held[rid] = (inp, out, sigma_map)
+        if self._log:
+            self._meta[rid] = {"width": w, "height": h, "channels": c, "format": int(fmt),
+                               "fix_x": float(fix_x), "fix_y": float(fix_y)}
         return rid
 
     def wait(self, rid: int, timeout_ms: int = 10000) -> dict:
         t = RequestTimes()
         _check(_lib.fovea_server_wait(self._h, int(rid), int(timeout_ms), ctypes.byref(t)), "fovea_server_wait")
         self._held.pop(int(rid), None)
-        return {"arrival_us": t.arrival_us, "admit_us": t.admit_us, "start_us": t.start_us,
-                "done_us": t.done_us, "batch_size": t.batch_size, "status": t.status}
+        times = {"arrival_us": t.arrival_us, "admit_us": t.admit_us, "start_us": t.start_us,
+                 "done_us": t.done_us, "batch_size": t.batch_size, "status": t.status}
+        if self._log:
+            self._log.append({"id": int(rid), **self._meta.pop(int(rid), {}), **times})
+        return times
 
     def close(self):
+        if getattr(self, "_log", None):
+            self._log.close()
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib.fovea_server_destroy(self._h)  # finishes every admitted request first
             self._h = _vp()

@@ -102,3 +102,23 @@ def test_fault_error_carries_the_word():
     e = fv.FoveaError(fv.EINVAL, "fovea_check", fv.FAULT_SIGMA_RANGE)
     assert e.status == fv.EINVAL and e.faults == fv.FAULT_SIGMA_RANGE
     assert "0x01" in str(e)
+
+
+def test_request_log_writes_one_json_object_per_line(tmp_path):
+    """The serving loop's optional request log (Server(log_path=...)):
+    append-only JSON lines, readable back record for record."""
+    import json
+    from paper_2012_08655_gb300.fovea import RequestLog
+    path = tmp_path / "requests.jsonl"
+    log = RequestLog(str(path))
+    recs = [{"id": 0, "width": 84, "height": 84, "channels": 1, "arrival_us": 1.5, "done_us": 90.25, "status": 0},
+            {"id": 1, "width": 1920, "height": 1080, "channels": 3, "arrival_us": 2.0, "done_us": 310.0, "status": 0}]
+    for r in recs:
+        log.append(r)
+    log.close()
+    lines = path.read_text().splitlines()
+    assert [json.loads(l) for l in lines] == recs
+    log2 = RequestLog(str(path))      # appends, never truncates
+    log2.append({"id": 2})
+    log2.close()
+    assert len(path.read_text().splitlines()) == 3

@@ -314,3 +314,22 @@ def test_server_holds_request_tensors_until_waited(fv):
         assert not srv._held
     for out in held:
         assert torch.equal(out, ref)
+
+
+def test_server_request_log(fv, tmp_path):
+    """Server(log_path=...) appends one JSON line per finished request: id,
+    frame shape, fixation and the library's timestamps and status."""
+    import json
+    path = tmp_path / "served.jsonl"
+    specs = [(84, 84, 1), (224, 224, 3), (1280, 720, 3)]
+    with fv.Server(device_budget_bytes=64 << 20, max_batch=8, log_path=str(path)) as srv:
+        rids = []
+        for i, (W, H, C) in enumerate(specs):
+            inp = torch.from_numpy(wl.grating_frame(H, W, C, seed=70 + i)).pin_memory()
+            rids.append(srv.submit(inp, torch.empty_like(inp).pin_memory(), W / 2.0, H / 3.0, 0.5, 0.02))
+        times = [srv.wait(r) for r in rids]
+    recs = [json.loads(l) for l in path.read_text().splitlines()]
+    assert [r["id"] for r in recs] == rids
+    for rec, t, (W, H, C) in zip(recs, times, specs):
+        assert (rec["width"], rec["height"], rec["channels"]) == (W, H, C)
+        assert rec["status"] == 0 and rec["done_us"] == t["done_us"] >= rec["start_us"] >= rec["admit_us"]
