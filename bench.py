@@ -702,6 +702,40 @@ def noalloc_leg(fv, torch, reps: int = 200):
     return res
 
 
+def kernel_variants_leg(fv, torch, reps: int = 200):
+    """Every forward kernel on the 1920x1080 RGB uint8 frame, each with its
+    best row chunk: ms per render (sigma + blur, device-resident buffers,
+    CUDA events over `reps` back-to-back renders) and the output's agreement
+    with the mma.sync kernel's."""
+    from paper_2012_08655_gb300 import workloads as wl
+    frame = wl.frame_1080p(seed=0)
+    x = torch.from_numpy(frame.image).cuda()
+    cur = torch.cuda.current_stream()
+    ctx = fv.Context(W, H, C, B, SIGMA0, K_SLOPE, fv.U8_HWC)
+    outs, res = {}, {"workload": "1920x1080 RGB uint8 frame, sigma = 0.5 + 0.02 e, fixation (960, 540)"}
+    for tc, rb in ((0, 32), (1, 64), (2, 32), (3, 16)):
+        ctx.set_config(256, 0, rb, tensor_cores=tc)
+        y = torch.empty_like(x)
+        for _ in range(10):
+            ctx.render(x, y, *FIX)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        for _ in range(reps):
+            ctx.render(x, y, *FIX)
+        e1.record(cur)
+        torch.cuda.synchronize()
+        outs[tc] = y
+        res[KERNELS[tc][0]] = {"ms": e0.elapsed_time(e1) / reps, "rows_per_chunk": rb}
+    ctx.check()
+    ctx.close()
+    ref = outs[1].to(torch.int16)
+    for tc in (0, 2, 3):
+        d = (outs[tc].to(torch.int16) - ref).abs()
+        res[KERNELS[tc][0]]["vs_mma_sync"] = {"max_lsb": int(d.max()), "equal": float((d == 0).float().mean())}
+    return res
+
+
 def served_leg(fv, torch, seconds: float, max_batch: int, world: int = 1, rank: int = 0):
     """Replay the Poisson request stream through the serving loop. With
     world > 1 each rank serves the requests of its streams (stream s on rank
@@ -1041,6 +1075,7 @@ def run_ours(args):
         extras["pixelwise"] = pixelwise_leg(fv, torch)
         extras["plain_256"] = plain_leg(fv, torch)
         extras["noalloc"] = noalloc_leg(fv, torch)
+        extras["kernel_variants"] = kernel_variants_leg(fv, torch)
         served = served_leg(fv, torch, args.served_seconds, max_batch=64)
         plain = served_leg(fv, torch, args.served_seconds, max_batch=1)
         served["plain_per_frame"] = {k: plain[k] for k in ("p50_ms", "p99_ms", "mpix_s", "mean_batch")}
