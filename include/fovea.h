@@ -429,6 +429,13 @@ const char* fovea_strerror(int status);
 /* The cudaError_t of the last failed CUDA call in this thread (0 if none). */
 int fovea_last_cuda_error(void);
 
+#define FOVEA_BUILD_BOUNDS 1
+/* Build flags of the loaded library: FOVEA_BUILD_BOUNDS when it is the
+ * bounds-checked build (compiled with FOVEA_BOUNDS: every kernel store checks
+ * its address, skips one outside its buffer and records FOVEA_FAULT_BOUNDS in
+ * the context's fault word), 0 for the regular build. */
+int fovea_build_flags(void);
+
 /* Diagnostic (no counterpart in the paper): measures the current GPU's FP32
  * FMA throughput, the roof of the blur kernels' arithmetic. Runs a kernel of
  * independent packed two-lane FMA chains (fma.rn.f32x2) on every SM of the

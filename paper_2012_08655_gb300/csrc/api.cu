@@ -1069,6 +1069,14 @@ const char* fovea_strerror(int status) {
 
 int fovea_last_cuda_error(void) { return g_last_cuda_error; }
 
+int fovea_build_flags(void) {
+#if defined(FOVEA_BOUNDS)
+  return FOVEA_BUILD_BOUNDS;
+#else
+  return 0;
+#endif
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------- internals used by other units

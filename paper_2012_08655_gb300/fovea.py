@@ -101,6 +101,7 @@ _sig = {
     "fovea_noalloc_check": (_i, [_vp, ctypes.POINTER(ctypes.c_uint)]),
     "fovea_strerror": (ctypes.c_char_p, [_i]),
     "fovea_last_cuda_error": (_i, []),
+    "fovea_build_flags": (_i, []),
     "fovea_measure_fma_rate": (_i, [ctypes.POINTER(_d), _vp]),
     "fovea_gp_law": (_i, [_i, _i, _d, ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "fovea_grid": (_i, [_vp, _f, _f, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
@@ -115,6 +116,12 @@ for _name, (_res, _args) in _sig.items():
     _fn = getattr(_lib, _name)
     _fn.restype = _res
     _fn.argtypes = _args
+
+# The bounds-checked build (FOVEA_LIBRARY naming libfovea_bounds.so): every
+# Context reads its fault word when it closes, and bounds faults are kept in
+# BOUNDS_FAULTS for a test harness to report.
+BOUNDS_BUILD = bool(_lib.fovea_build_flags() & 1)
+BOUNDS_FAULTS: list = []
 
 
 class FoveaError(RuntimeError):
@@ -249,8 +256,18 @@ class Context:
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
+            if BOUNDS_BUILD:
+                self.record_bounds_faults()
             _lib.fovea_destroy(self._h)
             self._h = _vp()
+
+    def record_bounds_faults(self):
+        """Bounds-checked build only: read (and clear) the fault word and keep
+        a FOVEA_FAULT_BOUNDS in BOUNDS_FAULTS (other bits are left to check())."""
+        w = ctypes.c_uint(0)
+        _lib.fovea_check(self._h, None, ctypes.byref(w))
+        if w.value & FAULT_BOUNDS:
+            BOUNDS_FAULTS.append((self.width, self.height, self.channels, int(w.value)))
 
     def __del__(self):
         try:
@@ -551,6 +568,19 @@ def sigma_table(width: int, height: int, fix_x: float, fix_y: float, sigma0: flo
                 block: int = 32, *, grid: int = GRID_ANCHORED, e_corner: Optional[float] = None):
     """Per-block (sigma float32, radius int32) computed by the sigma-table kernel."""
     return _ctx_for(width, height, 1, block, sigma0, k, F32_CHW, grid, e_corner).sigma_table(fix_x, fix_y)
+
+
+def take_bounds_faults() -> list:
+    """Bounds-checked build: the bounds faults recorded so far (closed
+    contexts, and the module's cached contexts, read now), cleared on return.
+    Always empty for the regular build."""
+    if BOUNDS_BUILD:
+        for ctx in list(_ctx_cache.values()):
+            if ctx._h.value:
+                ctx.record_bounds_faults()
+    out = list(BOUNDS_FAULTS)
+    BOUNDS_FAULTS.clear()
+    return out
 
 
 def _batch_ctx(block: int) -> Context:

@@ -188,6 +188,8 @@ if __name__ == "__main__":
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import torch
     from paper_2012_08655_gb300 import fovea
+    # the library's own flag agrees with the build the environment names
+    assert fovea.BOUNDS_BUILD == ("bounds" in os.path.basename(fovea.LIB_PATH)), fovea.LIB_PATH
     problems = run_cases(fovea, torch)
     for p in problems:
         print("FAIL", p)

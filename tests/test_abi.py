@@ -131,3 +131,13 @@ def test_fault_bits_and_checks(lib):
 def test_python_binding_imports_without_gpu():
     from paper_2012_08655_gb300 import fovea
     assert fovea.MAX_RADIUS == 1023
+
+
+def test_regular_build_reports_no_bounds_checks():
+    """fovea_build_flags tells the bounds-checked build (FOVEA_BOUNDS) from the
+    regular one; the binding keys its bounds-fault bookkeeping on it."""
+    from paper_2012_08655_gb300 import fovea
+    expect = 1 if "bounds" in os.path.basename(fovea.LIB_PATH) else 0
+    assert fovea._lib.fovea_build_flags() == expect
+    assert fovea.BOUNDS_BUILD == bool(expect)
+    assert fovea.take_bounds_faults() == []
