@@ -461,6 +461,21 @@ def train_leg(fv, torch, reps: int = 20):
         e1.record()
         torch.cuda.synchronize()
         res[name] = e0.elapsed_time(e1) / reps
+    # the same forward on the fp32 CUDA-core kernel (tensor cores off)
+    b = fv._batch_ctx(32)
+    b.set_config(256, 0, 32, tensor_cores=0)
+    with torch.no_grad():
+        for _ in range(3):
+            fv.foveate_train(x, fix, s0, k)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fv.foveate_train(x, fix, s0, k)
+        e1.record()
+        torch.cuda.synchronize()
+    res["forward_fp32"] = e0.elapsed_time(e1) / reps
+    b.set_config(256, 0, 32, tensor_cores=1)
     px = x_np.shape[0] * x_np.shape[2] * x_np.shape[3]
     # algorithmic work of the forward (the method's separable FMAs, halo
     # rows included, clamping not folded) from each image's radius table
@@ -477,8 +492,11 @@ def train_leg(fv, torch, reps: int = 20):
             "forward_backward_mpix_s": px / res["forward_backward"] / 1e3,
             "forward_algorithmic_fmas": fmas,
             "forward_tflops": tflops,
+            "forward_fp32_kernel_ms": res["forward_fp32"],
             "forward_note": "whole forward call (sigma, order and blur kernels, Python autograd overhead) "
-                            "against the algorithmic FMAs; fp32 CUDA-core kernel (float32 frames)"}
+                            "against the algorithmic FMAs; default configuration: float32 frames on the "
+                            "mma.sync tensor-core kernel (fp16 hi + lo splits); forward_fp32_kernel_ms: the "
+                            "same call on the fp32 CUDA-core kernel"}
 
 
 def block_sweep_leg(fv, torch):

@@ -278,8 +278,15 @@ typedef struct {
                          memory (radius bound <= 255 and 16 or 32 rows per chunk,
                          else as 1); 3 both passes on tcgen05, accumulators in
                          tensor memory, one CTA per SM (RGB frames whose rows
-                         TMA can load, radius bound <= 256, 16 rows per
-                         chunk, else as 1); 0: fp32 FMA kernel */
+                         TMA can load, radius bound <= 192, 16 rows per
+                         chunk, else as 1); 0: fp32 FMA kernel.
+                         Any non-zero value also runs launches whose frames are
+                         all float32 on mma.sync (data and taps split into fp16
+                         hi + lo parts, about 2^-21 relative error) when every
+                         frame's rows TMA can load (16-byte aligned base, width
+                         a multiple of 4), except a single frame whose blocks
+                         fit one wave of the fp32 kernel; staged values must
+                         satisfy |x| < 2^15 (else FOVEA_FAULT_VALUE_RANGE) */
 } fovea_config;
 
 /* Copy the context's current configuration into *cfg. FOVEA_EINVAL for a
@@ -391,6 +398,9 @@ int fovea_render_noalloc(const void* in_dev, void* out_dev, int width, int heigh
                                           (internal); the pixel is written unblurred */
 #define FOVEA_FAULT_BOUNDS      0x100u /* bounds-checked builds (-DFOVEA_BOUNDS) only: a store fell outside
                                           the buffer it belongs to and was skipped (internal) */
+#define FOVEA_FAULT_VALUE_RANGE 0x200u /* float32 frames on the tensor cores: a staged value was not finite
+                                          or |x| >= 2^15, beyond the fp16 hi + lo split; the
+                                          blocks it fed are not trustworthy (caller's data) */
 
 /* Waits for `stream` (a cudaStream_t; the stream the context's calls were
  * ordered on), then reads and clears the context's device fault word. Stores

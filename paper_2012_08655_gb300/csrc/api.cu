@@ -42,7 +42,7 @@ namespace fovea {
 int fault_status(unsigned int word) {
   if (!word) return FOVEA_OK;
   if (word & kFaultWait) return FOVEA_ETIMEOUT;
-  if (word & ~kFaultSigmaRange) return FOVEA_ECUDA;
+  if (word & ~(kFaultSigmaRange | kFaultValueRange)) return FOVEA_ECUDA;
   return FOVEA_EINVAL;
 }
 
@@ -134,6 +134,16 @@ struct fovea_ctx {
   unsigned int* fault_host = nullptr;
   cudaEvent_t fault_ev = nullptr;
   bool fault_copy_pending = false;
+  // tensor maps of the last two input buffers of the single-frame path
+  // (fovea_render_host alternates two staging buffers); a map depends only on
+  // the buffer, the context's fixed frame shape and the rows per box
+  struct MapEntry {
+    alignas(kTensorMapAlign) unsigned char map[kTensorMapBytes] = {};
+    const void* in = nullptr;
+    int rows = 0;
+    bool ok = false;
+  } maps[2];
+  int map_next = 0;
 };
 
 namespace fovea {
@@ -288,8 +298,10 @@ int sigma_grid(long long items, int num_sms) {
 // kernel with pass 1 on tcgen05, 3 the kernel with both passes on tcgen05
 // (2 and 3 where the radius bound, row chunk and channel count permit, and
 // for 3 when every frame's rows can be loaded by TMA (all_tma); else the
-// mma.sync kernel).
+// mma.sync kernel); 4 float32-only launches on the tensor cores (every
+// frame TMA-loadable; else the fp32 kernel).
 int tc_kind(const FwdConfig& cfg, int fmt_mask, int tc_c, int rmax, bool all_tma = true) {
+  if (cfg.tc && fmt_mask == 2) return all_tma && tcf_supports(rmax) ? 4 : 0;  // float32 frames
   if (!cfg.tc || fmt_mask != 1 || tc_c <= 0) return 0;
   if (cfg.tc == 2 && rmax <= kUmmaMaxRadius && cfg.rows_per_chunk <= 32) return 2;
   if (cfg.tc == 3 && all_tma && tc05_supports(rmax, tc_c) && cfg.rows_per_chunk == 16) return 3;
@@ -298,7 +310,8 @@ int tc_kind(const FwdConfig& cfg, int fmt_mask, int tc_c, int rmax, bool all_tma
 
 int forward_grid(const fovea_ctx* ctx, const FwdConfig& cfg, int rmax, int fmt_mask, int tc_c, bool all_tma = true) {
   const int kind = tc_kind(cfg, fmt_mask, tc_c, rmax, all_tma);
-  int per = kind == 3   ? tc05_forward_max_ctas_per_sm(cfg, rmax)
+  int per = kind == 4   ? tcf_forward_max_ctas_per_sm(rmax)
+            : kind == 3 ? tc05_forward_max_ctas_per_sm(cfg, rmax)
             : kind == 2 ? umma_forward_max_ctas_per_sm(cfg, rmax, tc_c)
             : kind == 1 ? tc_forward_max_ctas_per_sm(cfg, rmax, tc_c)
                         : forward_max_ctas_per_sm(cfg, rmax, fmt_mask);
@@ -425,8 +438,11 @@ int upload_batch(fovea_ctx* ctx, const FwdConfig& cfg, const fovea_frame* frames
     void* map = hbuf + maps_off + (size_t)i * kTensorMapBytes;
     // rows are loaded by TMA only from device memory (a frame in mapped host
     // memory is staged with plain loads)
-    d.tma = (!adjoint && d.fmt == FOVEA_U8_HWC && in_device_memory(d.in) &&
-             make_u8_tensor_map(map, d.in, d.W, d.H, d.C, cfg.rows_per_chunk)) ? 1 : 0;
+    d.tma = 0;
+    if (!adjoint && in_device_memory(d.in)) {
+      if (d.fmt == FOVEA_U8_HWC) d.tma = make_u8_tensor_map(map, d.in, d.W, d.H, d.C, cfg.rows_per_chunk) ? 1 : 0;
+      else if (cfg.tc) d.tma = make_f32_tensor_map(map, d.in, d.W, d.H, d.C, 16) ? 1 : 0;
+    }
     if (!d.tma) std::memset(map, 0, kTensorMapBytes);
     every_tma = every_tma && d.tma;
   }
@@ -470,6 +486,9 @@ int enqueue_batch_kernels(fovea_ctx* ctx, const FwdConfig& cfg, bool adjoint, in
     int grid = forward_grid(ctx, cfg, rbound, fmt_mask, tc_c, all_tma);
     if (grid <= 0) return FOVEA_EUNSUPPORTED;
     switch (tc_kind(cfg, fmt_mask, tc_c, rbound, all_tma)) {
+      case 4:
+        e = launch_tcf_forward(src, ctx->ws, rbound, grid, s, BucketList{nullptr, 0, 0}, false, nullptr);
+        break;
       case 3:
         e = launch_tc05_forward(src, ctx->ws, cfg, rbound, grid, s, BucketList{nullptr, 0, 0}, false, nullptr);
         break;
@@ -600,6 +619,22 @@ int fovea_create(int width, int height, int channels, int block, const fovea_sig
   return FOVEA_OK;
 }
 
+// The tensor map of a single frame at in_dev (the context's shape and
+// format), from the context's two-entry cache; nullptr where TMA cannot load
+// the frame's rows.
+static const void* frame_tensor_map(fovea_ctx* ctx, const void* in_dev, int fmt_mask) {
+  const int rows = fmt_mask == 1 ? ctx->cfg.rows_per_chunk : 16;
+  for (const auto& m : ctx->maps)
+    if (m.in == in_dev && m.rows == rows) return m.ok ? m.map : nullptr;
+  auto& m = ctx->maps[ctx->map_next];
+  ctx->map_next ^= 1;
+  m.ok = fmt_mask == 1 ? make_u8_tensor_map(m.map, in_dev, ctx->W, ctx->H, ctx->C, rows)
+                       : make_f32_tensor_map(m.map, in_dev, ctx->W, ctx->H, ctx->C, rows);
+  m.in = in_dev;
+  m.rows = rows;
+  return m.ok ? m.map : nullptr;
+}
+
 static int render_one(fovea_ctx* ctx, const void* in_dev, void* out_dev, float fix_x, float fix_y,
                       cudaStream_t s) {
   int st = check_frame(ctx->W, ctx->H, ctx->C, ctx->fmt, ctx->B, ctx->law, fix_x, fix_y);
@@ -613,11 +648,20 @@ static int render_one(fovea_ctx* ctx, const void* in_dev, void* out_dev, float f
   const int rmax = radius_bound(ctx->W, ctx->H, ctx->B, fix_x, fix_y, ctx->law);
   const int fmt_mask = ctx->fmt == FOVEA_F32_CHW ? 2 : 1;
   const int tc_c = ctx->C;
+  // A float32 frame that fits one wave of the fp32 kernel takes its
+  // one-launch path (no sigma kernel) even with the tensor cores enabled.
+  bool f32_one_wave = false;
+  int grid = 0;
+  if (fmt_mask == 2 && ctx->cfg.tc) {
+    FwdConfig c0 = ctx->cfg;
+    c0.tc = 0;
+    grid = forward_grid(ctx, c0, rmax, fmt_mask, tc_c);
+    f32_one_wave = grid > 0 && src.one_total <= grid;
+  }
   // the tensor map of the frame's rows (the tensor-core kernels load rows by TMA where it exists)
-  alignas(64) unsigned char map[kTensorMapBytes];
-  src.one.tma = (fmt_mask == 1 && ctx->cfg.tc &&
-                 make_u8_tensor_map(map, src.one.in, src.one.W, src.one.H, src.one.C, ctx->cfg.rows_per_chunk)) ? 1 : 0;
-  int grid = forward_grid(ctx, ctx->cfg, rmax, fmt_mask, tc_c, src.one.tma != 0);
+  const void* map = ctx->cfg.tc && !f32_one_wave ? frame_tensor_map(ctx, src.one.in, fmt_mask) : nullptr;
+  src.one.tma = map ? 1 : 0;
+  if (!f32_one_wave) grid = forward_grid(ctx, ctx->cfg, rmax, fmt_mask, tc_c, src.one.tma != 0);
   if (grid <= 0) return FOVEA_EUNSUPPORTED;
   const int kind = tc_kind(ctx->cfg, fmt_mask, tc_c, rmax, src.one.tma != 0);
   if (kind == 0 && src.one_total <= grid) {
@@ -658,7 +702,8 @@ static int render_one(fovea_ctx* ctx, const void* in_dev, void* out_dev, float f
   // sigma kernel (not when its launch is bracketed by timing events).
   const bool pdl = bl.list && !ctx->kev_start;
   if (kind) {
-    e = kind == 3   ? launch_tc05_forward(src, ctx->ws, ctx->cfg, rmax, grid, s, bl, pdl, map)
+    e = kind == 4   ? launch_tcf_forward(src, ctx->ws, rmax, grid, s, bl, pdl, map)
+        : kind == 3 ? launch_tc05_forward(src, ctx->ws, ctx->cfg, rmax, grid, s, bl, pdl, map)
         : kind == 2 ? launch_umma_forward(src, ctx->ws, ctx->cfg, rmax, tc_c, grid, s, bl, pdl, map)
                     : launch_tc_forward(src, ctx->ws, ctx->cfg, rmax, tc_c, grid, s, bl, pdl, map);
   } else {
@@ -1146,10 +1191,9 @@ int ctx_device_info(const fovea_ctx* ctx, int* device, int* num_sms) {
 
 int record_cuda_failure(int cuda_error) { return cuda_fail((cudaError_t)cuda_error); }
 
-bool make_u8_tensor_map(void* map, const void* base, int W, int H, int C, int rows) {
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   static std::once_flag once;
-  std::memset(map, 0, kTensorMapBytes);
   std::call_once(once, [] {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
@@ -1158,6 +1202,37 @@ bool make_u8_tensor_map(void* map, const void* base, int W, int H, int C, int ro
       encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     cudaGetLastError();
   });
+  return encode;
+}
+
+// Float32 CHW frame as a 3D tensor (x, y, channel plane): boxes of 32
+// elements (128 bytes, 128-byte swizzle) x `rows` rows of one plane, zero
+// outside the frame, so a row above or below a plane reads zeros (never the
+// neighbouring plane). Needs a 16-byte aligned base and W a multiple of 4.
+bool make_f32_tensor_map(void* map, const void* base, int W, int H, int C, int rows) {
+  std::memset(map, 0, kTensorMapBytes);
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  const unsigned long long pitch = (unsigned long long)W * 4ull;
+  if (!encode || !base || ((uintptr_t)base & 15) || (pitch & 15) || W <= 0 || H <= 0 || C <= 0 || rows <= 0 ||
+      rows > 256)
+    return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)C};
+  const cuuint64_t strides[2] = {pitch, pitch * (cuuint64_t)H};
+  const cuuint32_t box[3] = {32, (cuuint32_t)rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = encode(static_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base),
+                            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    std::memset(map, 0, kTensorMapBytes);
+    return false;
+  }
+  return true;
+}
+
+bool make_u8_tensor_map(void* map, const void* base, int W, int H, int C, int rows) {
+  std::memset(map, 0, kTensorMapBytes);
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
   const unsigned long long pitch = (unsigned long long)W * (unsigned long long)C;
   if (!encode || !base || ((uintptr_t)base & 15) || (pitch & 15) || W <= 0 || H <= 0 || rows <= 0 || rows > 256)
     return false;

@@ -74,6 +74,9 @@ constexpr size_t kTensorMapAlign = 64;
 // kTensorMapAlign). Returns false, leaving map zeroed, when the frame's base
 // address or row pitch is not a multiple of 16 bytes or the driver refuses.
 bool make_u8_tensor_map(void* map, const void* base, int W, int H, int C, int rows);
+// The same for a float32 CHW frame: a 3D map (x, y, plane), boxes of 32
+// elements x `rows` rows of one plane (16-byte aligned base, W a multiple of 4).
+bool make_f32_tensor_map(void* map, const void* base, int W, int H, int C, int rows);
 // Status a device fault word maps to (see fovea_check): FOVEA_OK for 0,
 // FOVEA_ETIMEOUT when a wait ran out, FOVEA_ECUDA for an internal fault,
 // FOVEA_EINVAL when only a sigma-map value was out of range.

@@ -27,7 +27,7 @@ struct FrameDesc {
   const void* in;
   void* out;
   int W, H, C, fmt;        // fmt: FOVEA_U8_HWC or FOVEA_F32_CHW
-  int nbx, nby, B, tma;    // block grid and block side; tma: a tensor map is provided (uint8 HWC)
+  int nbx, nby, B, tma;    // block grid and block side; tma: a tensor map of the frame's rows is provided
   float fx, fy;            // fixation (pixels)
   double sigma0, k;        // sigma law
   long long item0;         // index of the frame's first item in a batch
@@ -125,6 +125,7 @@ constexpr unsigned int kFaultBuckets = FOVEA_FAULT_BUCKETS;
 constexpr unsigned int kFaultWait = FOVEA_FAULT_WAIT;
 constexpr unsigned int kFaultPixelRadius = FOVEA_FAULT_PIXEL_RADIUS;
 constexpr unsigned int kFaultBounds = FOVEA_FAULT_BOUNDS;
+constexpr unsigned int kFaultValueRange = FOVEA_FAULT_VALUE_RANGE;
 
 // Bounds-checked builds (-DFOVEA_BOUNDS): stores check their address first.
 #if defined(FOVEA_BOUNDS)
@@ -400,13 +401,20 @@ size_t umma_forward_smem_bytes(const FwdConfig& cfg, int rmax, int C);
 int umma_forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax, int C);
 cudaError_t launch_umma_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg, int rmax, int C,
                                 int grid, cudaStream_t s, const BucketList& bl, bool pdl, const void* tmap_one);
-// Both passes on tcgen05 (tc05_forward.cu): uint8 RGB frames (C = 3), radius
-// bound up to 511, row chunks of 16 or 32 rows.
+// Both passes on tcgen05 (tc05_forward.cu): uint8 RGB frames (C = 3) whose
+// rows TMA can load, radius bound up to 192, 16-row chunks.
 bool tc05_supports(int rmax, int C);
 size_t tc05_forward_smem_bytes(const FwdConfig& cfg, int rmax);
 int tc05_forward_max_ctas_per_sm(const FwdConfig& cfg, int rmax);
 cudaError_t launch_tc05_forward(const FrameSource& src, const Workspace& ws, const FwdConfig& cfg, int rmax, int grid,
                                 cudaStream_t s, const BucketList& bl, bool pdl, const void* tmap_one);
+// Float32 CHW frames on mma.sync (tcf_forward.cu): every frame's rows
+// TMA-loadable (W a multiple of 4, 16-byte aligned base), 16-row chunks.
+bool tcf_supports(int rmax);
+size_t tcf_forward_smem_bytes(int rmax);
+int tcf_forward_max_ctas_per_sm(int rmax);
+cudaError_t launch_tcf_forward(const FrameSource& src, const Workspace& ws, int rmax, int grid, cudaStream_t s,
+                               const BucketList& bl, bool pdl, const void* tmap_one);
 size_t adjoint_smem_bytes(int rmax);
 cudaError_t launch_adjoint(const FrameSource& src, const Workspace& ws, int rmax, int grid,
                            cudaStream_t s);

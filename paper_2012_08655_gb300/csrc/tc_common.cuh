@@ -238,7 +238,10 @@ __device__ __forceinline__ bool tc_unit_exists(int warp, int i) {
   return (8 * C) % NW == 0 ? true : warp + NW * i < 8 * C;
 }
 
-template <int C, bool VT = false, int NW = 8>
+// FLUSH: each k-step's products go into a zeroed fragment that is added to
+// acc2 in fp32 (round to nearest) instead of accumulating in the MMA, whose
+// adds truncate; needed where the result is not rounded to 8 bits.
+template <int C, bool VT = false, int NW = 8, bool FLUSH = false>
 __device__ __forceinline__ void tc_pass2_slab(const Item& it, const Slab& sl, const __half* Vh, const __half* Vl,
                                               const float* CU, const unsigned int* P, int np,
                                               float (&acc2)[tc_units(C, NW)][4]) {
@@ -301,6 +304,19 @@ __device__ __forceinline__ void tc_pass2_slab(const Item& it, const Slab& sl, co
         ldsm_x4(a_h[i], Vh + (size_t)arow * VP + acol);
         ldsm_x4(a_l[i], Vl + (size_t)arow * VP + acol);
       }
+    }
+    if (FLUSH) {
+      #pragma unroll
+      for (int i = 0; i < U; ++i) {
+        if (!tc_unit_exists<C, NW>(warp, i)) continue;
+        float tmp[4] = {0.f, 0.f, 0.f, 0.f};
+        mma16816(tmp, a_h[i], bh[0], bh[1]);
+        mma16816(tmp, a_h[i], bl[0], bl[1]);
+        mma16816(tmp, a_l[i], bh[0], bh[1]);
+        #pragma unroll
+        for (int e = 0; e < 4; ++e) acc2[i][e] += tmp[e];
+      }
+      continue;
     }
     #pragma unroll
     for (int i = 0; i < U; ++i)
@@ -391,7 +407,8 @@ __device__ __forceinline__ void tc_write_output(const Item& it, unsigned char* o
 // the next item's index and record, so the work list's dependent loads
 // overlap the current item. Ends with the single-frame counter reset.
 // s_start: shared memory for rmax + 1 bucket starts (single frames).
-template <int RB, int C, bool FULL_SLABS = false, int NW = 8, int SLAB = TcDims<NW>::SLAB, typename ItemFn>
+template <int RB, int C, bool FULL_SLABS = false, int NW = 8, int SLAB = TcDims<NW>::SLAB, bool F32 = false,
+          typename ItemFn>
 __device__ __forceinline__ void tc_item_loop(const FrameSource& src, const CUtensorMap& tmap1, const Workspace& ws,
                                              int rmax, const BucketList& bl, int* s_start, ItemFn&& item_fn) {
   constexpr int NT = TcDims<NW>::NT;
@@ -452,7 +469,8 @@ __device__ __forceinline__ void tc_item_loop(const FrameSource& src, const CUten
         } else {
           const ItemInfo inf = nx_have ? nx_inf : ws.items[item];
           const FrameDesc fd = load_frame(src, inf.frame);
-          if (inf.r > rmax || fd.fmt != FOVEA_U8_HWC || fd.C != C) {
+          const bool fmt_ok = F32 ? fd.fmt == FOVEA_F32_CHW : (fd.fmt == FOVEA_U8_HWC && fd.C == C);
+          if (inf.r > rmax || !fmt_ok) {
             atomicOr(&ws.counters[CNT_ERROR], kFaultRadiusBound);
             state = 1;
           } else {

@@ -121,13 +121,15 @@ void save_file(const char* path) {
 }
 
 // Candidate configurations for frames of the given formats (fmt_mask bit 0
-// uint8, bit 1 float32) and channel count (0: mixed): the tensor-core
-// kernels only serve launches whose frames are all uint8 with one channel
-// count.
+// uint8, bit 1 float32) and channel count (0: mixed): the uint8 tensor-core
+// kernels serve launches whose frames are all uint8 with one channel count,
+// the float32 one (16-row chunks whatever rows_per_chunk says) launches whose
+// frames are all float32.
 std::vector<fovea_config> candidates(int fmt_mask, int channels) {
   std::vector<fovea_config> v;
   const int rbs[3] = {16, 32, 64};
   for (int rb : rbs) v.push_back(fovea_config{256, 0, rb, 0});
+  if (fmt_mask == 2) v.push_back(fovea_config{256, 0, 16, 1});
   if (fmt_mask == 1 && channels > 0) {
     for (int nt : {128, 256, 512})
       for (int rb : rbs) v.push_back(fovea_config{nt, 0, rb, 1});

@@ -39,7 +39,7 @@ MAX_BLOCK = 256
 # device fault bits (FOVEA_FAULT_* of include/fovea.h), reported by Context.check()
 FAULT_SIGMA_RANGE, FAULT_RADIUS_BOUND, FAULT_ADJ_BOUND, FAULT_ORDER = 0x01, 0x02, 0x04, 0x08
 FAULT_WORKLIST, FAULT_BUCKETS, FAULT_WAIT, FAULT_PIXEL_RADIUS = 0x10, 0x20, 0x40, 0x80
-FAULT_BOUNDS = 0x100
+FAULT_BOUNDS, FAULT_VALUE_RANGE = 0x100, 0x200
 
 
 LAW_LINEAR, LAW_GEISLER_PERRY, LAW_MAP = 0, 1, 2

@@ -115,7 +115,7 @@ def test_fault_bits_and_checks(lib):
     the host (the status mapping itself needs a device: tests/test_gpu_faults.py)."""
     text = open(HEADER).read()
     bits = {n: int(v, 16) for n, v in re.findall(r"#define FOVEA_FAULT_(\w+)\s+(0x[0-9a-fA-F]+)u", text)}
-    assert len(bits) == 9 and len(set(bits.values())) == 9
+    assert len(bits) == 10 and len(set(bits.values())) == 10
     assert all(v & (v - 1) == 0 for v in bits.values())
     from paper_2012_08655_gb300 import fovea
     for n, v in bits.items():
