@@ -310,7 +310,7 @@ int tc_kind(const FwdConfig& cfg, int fmt_mask, int tc_c, int rmax, bool all_tma
 
 int forward_grid(const fovea_ctx* ctx, const FwdConfig& cfg, int rmax, int fmt_mask, int tc_c, bool all_tma = true) {
   const int kind = tc_kind(cfg, fmt_mask, tc_c, rmax, all_tma);
-  int per = kind == 4   ? tcf_forward_max_ctas_per_sm(rmax)
+  int per = kind == 4   ? tcf_forward_max_ctas_per_sm(rmax, tc_c)
             : kind == 3 ? tc05_forward_max_ctas_per_sm(cfg, rmax)
             : kind == 2 ? umma_forward_max_ctas_per_sm(cfg, rmax, tc_c)
             : kind == 1 ? tc_forward_max_ctas_per_sm(cfg, rmax, tc_c)
@@ -487,7 +487,7 @@ int enqueue_batch_kernels(fovea_ctx* ctx, const FwdConfig& cfg, bool adjoint, in
     if (grid <= 0) return FOVEA_EUNSUPPORTED;
     switch (tc_kind(cfg, fmt_mask, tc_c, rbound, all_tma)) {
       case 4:
-        e = launch_tcf_forward(src, ctx->ws, rbound, grid, s, BucketList{nullptr, 0, 0}, false, nullptr);
+        e = launch_tcf_forward(src, ctx->ws, rbound, tc_c, grid, s, BucketList{nullptr, 0, 0}, false, nullptr);
         break;
       case 3:
         e = launch_tc05_forward(src, ctx->ws, cfg, rbound, grid, s, BucketList{nullptr, 0, 0}, false, nullptr);
@@ -702,7 +702,7 @@ static int render_one(fovea_ctx* ctx, const void* in_dev, void* out_dev, float f
   // sigma kernel (not when its launch is bracketed by timing events).
   const bool pdl = bl.list && !ctx->kev_start;
   if (kind) {
-    e = kind == 4   ? launch_tcf_forward(src, ctx->ws, rmax, grid, s, bl, pdl, map)
+    e = kind == 4   ? launch_tcf_forward(src, ctx->ws, rmax, tc_c, grid, s, bl, pdl, map)
         : kind == 3 ? launch_tc05_forward(src, ctx->ws, ctx->cfg, rmax, grid, s, bl, pdl, map)
         : kind == 2 ? launch_umma_forward(src, ctx->ws, ctx->cfg, rmax, tc_c, grid, s, bl, pdl, map)
                     : launch_tc_forward(src, ctx->ws, ctx->cfg, rmax, tc_c, grid, s, bl, pdl, map);

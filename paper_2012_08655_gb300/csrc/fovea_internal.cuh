@@ -410,11 +410,14 @@ cudaError_t launch_tc05_forward(const FrameSource& src, const Workspace& ws, con
                                 cudaStream_t s, const BucketList& bl, bool pdl, const void* tmap_one);
 // Float32 CHW frames on mma.sync (tcf_forward.cu): every frame's rows
 // TMA-loadable (W a multiple of 4, 16-byte aligned base), 16-row chunks.
+// channels: the launch's common channel count (0: mixed); 2 to 4 with a
+// radius bound up to 128 process all planes of a tile in one pass, else
+// one plane at a time.
 bool tcf_supports(int rmax);
-size_t tcf_forward_smem_bytes(int rmax);
-int tcf_forward_max_ctas_per_sm(int rmax);
-cudaError_t launch_tcf_forward(const FrameSource& src, const Workspace& ws, int rmax, int grid, cudaStream_t s,
-                               const BucketList& bl, bool pdl, const void* tmap_one);
+size_t tcf_forward_smem_bytes(int rmax, int channels);
+int tcf_forward_max_ctas_per_sm(int rmax, int channels);
+cudaError_t launch_tcf_forward(const FrameSource& src, const Workspace& ws, int rmax, int channels, int grid,
+                               cudaStream_t s, const BucketList& bl, bool pdl, const void* tmap_one);
 size_t adjoint_smem_bytes(int rmax);
 cudaError_t launch_adjoint(const FrameSource& src, const Workspace& ws, int rmax, int grid,
                            cudaStream_t s);

@@ -316,17 +316,17 @@ __device__ __forceinline__ void tc_pass2_slab(const Item& it, const Slab& sl, co
         #pragma unroll
         for (int e = 0; e < 4; ++e) acc2[i][e] += tmp[e];
       }
-      continue;
+    } else {
+      #pragma unroll
+      for (int i = 0; i < U; ++i)
+        if (tc_unit_exists<C, NW>(warp, i)) mma16816(acc2[i], a_h[i], bh[0], bh[1]);
+      #pragma unroll
+      for (int i = 0; i < U; ++i)
+        if (tc_unit_exists<C, NW>(warp, i)) mma16816(acc2[i], a_h[i], bl[0], bl[1]);
+      #pragma unroll
+      for (int i = 0; i < U; ++i)
+        if (tc_unit_exists<C, NW>(warp, i)) mma16816(acc2[i], a_l[i], bh[0], bh[1]);
     }
-    #pragma unroll
-    for (int i = 0; i < U; ++i)
-      if (tc_unit_exists<C, NW>(warp, i)) mma16816(acc2[i], a_h[i], bh[0], bh[1]);
-    #pragma unroll
-    for (int i = 0; i < U; ++i)
-      if (tc_unit_exists<C, NW>(warp, i)) mma16816(acc2[i], a_h[i], bl[0], bl[1]);
-    #pragma unroll
-    for (int i = 0; i < U; ++i)
-      if (tc_unit_exists<C, NW>(warp, i)) mma16816(acc2[i], a_l[i], bh[0], bh[1]);
   }
   {
     const int pr = it.EW - 1 - P0;  // folded right column after the last slab's products
@@ -469,7 +469,7 @@ __device__ __forceinline__ void tc_item_loop(const FrameSource& src, const CUten
         } else {
           const ItemInfo inf = nx_have ? nx_inf : ws.items[item];
           const FrameDesc fd = load_frame(src, inf.frame);
-          const bool fmt_ok = F32 ? fd.fmt == FOVEA_F32_CHW : (fd.fmt == FOVEA_U8_HWC && fd.C == C);
+          const bool fmt_ok = F32 ? (fd.fmt == FOVEA_F32_CHW && (C == 1 || fd.C == C)) : (fd.fmt == FOVEA_U8_HWC && fd.C == C);
           if (inf.r > rmax || !fmt_ok) {
             atomicOr(&ws.counters[CNT_ERROR], kFaultRadiusBound);
             state = 1;

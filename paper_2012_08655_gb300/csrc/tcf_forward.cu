@@ -3,8 +3,8 @@
 //
 // The block-wise separable blur of paper Section 2 and Algorithm 1 (taps of
 // Eq. 1 truncated at r = ceil(3 sigma)) as the banded Toeplitz contractions
-// of tc_forward.cu, on mma.sync.m16n8k16 (fp16 x fp16 -> fp32), one channel
-// plane at a time:
+// of tc_forward.cu, on mma.sync.m16n8k16 (fp16 x fp16 -> fp32), per channel
+// plane:
 //   pass 1 (vertical):   V[yo][e] = sum_v Wv[yo][v] T[v][e]
 //   pass 2 (horizontal): O[yo][x] = sum_p V[yo][p] Wh[p][x]
 // Each float32 value x is split into fp16 parts x_hi = fp16(x) and x_lo =
@@ -23,16 +23,25 @@
 // their value at r ~ 100. So each k-step's products go into a zeroed
 // fragment, which is added to the running sums with a rounded fp32 add.
 //
-// Staging: per 16-row chunk of a column slab of one channel plane, one thread
-// issues one 32-element (128-byte) box per warp column of a 3D tensor map over
-// (x, y, plane) (128-byte swizzle; rows outside the plane read zeros) into a
-// four-stage ring, completing on the stage's mbarrier (bounded waits). Warp w
-// owns slab elements 32w .. 32w + 31 in pass 1; lane (g, t) reads the four
-// consecutive elements 32w + 4g .. 4g + 3 of staged rows 2t, 2t + 1, 2t + 8,
-// 2t + 9 as four 16-byte loads and feeds element 32w + 4g + j to n-tile j.
-// The folded edge rows and columns, the tap-pair tables, pass 2 and the work
-// list are those of the uint8 kernel (tc_common.cuh); the outputs of a plane
-// are stored once its last slab is done.
+// Planes per pass: a launch whose frames all have C = 2 to 4 planes and whose
+// radius bound is at most 128 takes all C planes of a tile in each slab
+// pass, each plane on 8 / C warps side by side (slabs of up to 112 columns
+// for two planes, 61 for three or four), so a narrow halo still keeps most
+// warps busy in pass 1; other launches take one plane per pass on all eight
+// warps (slabs of up to 240 columns). V holds the pass's planes one after
+// the other (32 rows each) and pass 2 takes them as the uint8 kernel takes
+// interleaved channels.
+//
+// Staging: per 16-row chunk of a slab, one thread issues one 32-element
+// (128-byte) box per warp column of a 3D tensor map over (x, y, plane)
+// (128-byte swizzle; rows outside the plane read zeros) into a four-stage
+// ring with a full and an empty mbarrier per stage (bounded waits). Warp w
+// owns staged elements 32 b .. 32 b + 31 of its plane (b = w mod warps per
+// plane); lane (g, t) reads the four consecutive elements 32 b + 4g .. 4g + 3
+// of staged rows 2t, 2t + 1, 2t + 8, 2t + 9 as four 16-byte loads and feeds
+// element 32 b + 4g + j to n-tile j. The folded edge rows and columns, the
+// tap-pair tables, pass 2 and the work list are those of the uint8 kernel
+// (tc_common.cuh); a plane's outputs are stored once its last slab is done.
 #include <cstring>
 
 #include "tc_common.cuh"
@@ -50,23 +59,37 @@ constexpr int kRBF = 16;                    // staged rows per chunk (one k-step
 constexpr int kStagesF = 4;                 // ring stages
 constexpr int kBoxesF = kNWF;               // one 32-element box per warp column
 constexpr int kStageBF = kBoxesF * kRBF * 128;
-constexpr int kSlabF = 32 * kNWF - 16;      // elements per slab (up to 3 of alignment padding before it)
 constexpr float kRangeF = 32768.0f;         // |x| from here on does not split into fp16 hi + lo
 constexpr float kVScaleF = 1.0f / 4096.0f;  // V = pass-1 accumulator * 2^-12 (taps x 2^12, data x 1)
-constexpr int kVPF = tc_vp(1, kNWF);        // V row pitch (halves), the one pass 2 addresses V with
-static_assert((kSlabF + 15) / 16 * 16 <= kVPF, "a slab's V row, rounded up to whole k-steps, fits the pitch");
-static_assert(kSlabF + 3 <= 32 * kNWF, "a slab and its alignment padding fit the warps' columns");
+
+// CP channel planes per slab pass: CP = 1 takes one plane at a time (any
+// channel count); CP = C (2 to 4, launches whose frames all have C planes)
+// gives each plane WPP warps side by side.
+__host__ __device__ constexpr int tcf_min(int a, int b) { return a < b ? a : b; }
+template <int CP>
+struct TcfDims {
+  static constexpr int WPP = kNWF / CP;    // warps (32-element boxes) per plane
+  static constexpr int VP = tc_vp(CP, kNWF);  // V row pitch (halves), the one pass 2 addresses V with
+  // elements per plane and slab: alignment padding (up to 3) and slab fit the
+  // plane's warps, and the slab rounded up to whole k-steps fits the pitch
+  static constexpr int SLAB = tcf_min(32 * WPP - 3, VP / 16 * 16);
+  static_assert((SLAB + 15) / 16 * 16 <= VP, "a slab's V row, rounded up to whole k-steps, fits the pitch");
+  static_assert(SLAB + 3 <= 32 * WPP, "a slab and its alignment padding fit the plane's warps");
+};
 
 struct TcfLayout {
   size_t ring, vh, vl, cum, pairs, starts, total;
 };
 
-__host__ __device__ inline TcfLayout tcf_layout(int rmax) {
+// V halves (per hi or lo array) of CP planes per pass
+__host__ __device__ constexpr int tcf_vhalves(int cp, int vp) { return 32 * cp * vp; }
+
+__host__ __device__ inline TcfLayout tcf_layout(int rmax, int vhalves) {
   TcfLayout L;
   L.ring = 0;                                                 // [stage][box][16 rows][128 B], swizzled
-  L.vh = L.ring + (size_t)kStagesF * kStageBF;                // half [32][kVPF]
-  L.vl = L.vh + (size_t)32 * kVPF * 2;                        // half [32][kVPF]
-  L.cum = L.vl + (size_t)32 * kVPF * 2;                       // float [cum_len]
+  L.vh = L.ring + (size_t)kStagesF * kStageBF;                // half [planes][32][pitch]
+  L.vl = L.vh + (size_t)vhalves * 2;                          // half [planes][32][pitch]
+  L.cum = L.vl + (size_t)vhalves * 2;                         // float [cum_len]
   L.pairs = L.cum + (size_t)((cum_len(rmax) + 3) & ~3) * 4;   // uint32 [4][npair]
   L.starts = L.pairs + (size_t)4 * npair(rmax) * 4;          // int [rmax + 1] bucket starts
   L.total = L.starts + (size_t)(rmax + 1) * 4 + 1024;         // + alignment slack
@@ -84,30 +107,53 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const void* map, int x, i
       : "memory");
 }
 
-__device__ __forceinline__ unsigned int pack2(float a, float b) {
-  return pack_half2(__float2half_rn(a), __float2half_rn(b));
+__device__ __forceinline__ unsigned int h2_bits(__half2 h) {
+  unsigned int u;
+  memcpy(&u, &h, sizeof(u));
+  return u;
 }
 
-template <typename LookAhead>
+// One item (a halo tile of all channel planes). Chunk gq of the CTA (counted
+// over its items) sits in ring stage gq mod 4: full[stage] completes when its
+// boxes land, empty[stage] when all eight warps have read it (one arrival per
+// warp per chunk, whatever the warp did with it). Thread 0 issues a chunk
+// once its stage's previous chunk is released, three chunks ahead of its own
+// warp, so warps are not held in step chunk by chunk; block-wide barriers
+// remain only where the warps share V (slab ends) and the tables (item start).
+// A wait that runs out marks the warp dead (warp-uniform): it stops waiting
+// but keeps arriving and passing the same barriers, so every thread leaves
+// the item together, which then reports FOVEA_FAULT_WAIT.
+template <int CP, typename LookAhead>
 __device__ __forceinline__ bool tcf_item(const Item& it, float c_tap, unsigned char* ring, __half* Vh, __half* Vl,
-                                         float* CU, unsigned int* P, int np, unsigned long long* bars,
-                                         const void* map, bool map_in_global, int& gq0, unsigned int* err,
-                                         LookAhead&& lookahead) {
+                                         float* CU, unsigned int* P, int np, unsigned long long* full,
+                                         unsigned long long* empty, const void* map, bool map_in_global, int& gq0,
+                                         unsigned int* err, LookAhead&& lookahead) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int r = it.r;
-  const int nslabs = it.nsl * it.C;  // slab s: plane s / nsl, columns of slab s % nsl
+  using D = TcfDims<CP>;
+  // CP = 1: slab s is plane s / nsl, columns of slab s % nsl; else slab s is
+  // columns of slab s in every plane
+  const int nslabs = CP == 1 ? it.nsl * it.C : it.nsl;
   const int Q = nslabs * it.nchunks;
 
-  auto issue = [&](int qq) {  // one thread: the chunk's boxes that hold slab elements
-    const Slab cs = slab_of<false>(it, qq / it.nchunks);
+  int issued = 0;      // thread 0: chunks of this item issued
+  bool pdead = false;  // thread 0: a wait for a stage to be released ran out
+  auto issue = [&](int qq) {  // thread 0: the chunk's boxes that hold slab elements
     const int gq = gq0 + qq, stg = gq % kStagesF;
+    if (!pdead && gq >= kStagesF && !mbar_wait(empty + stg, (unsigned int)((gq - kStagesF) / kStagesF) & 1u))
+      pdead = true;
+    if (pdead) return;
+    const Slab cs = slab_of<false>(it, qq / it.nchunks);
     unsigned char* dst = ring + (size_t)stg * kStageBF;
     const int x = it.gx0 + cs.e0 - cs.ph;  // element column, a multiple of 4
     const int y = it.gy0 - it.ph + (qq % it.nchunks) * kRBF;
-    const int nbox = (cs.ph + cs.sws + 31) >> 5;
-    mbar_expect_tx(bars + stg, (unsigned int)nbox * 128u * kRBF);
-    for (int bx = 0; bx < nbox; ++bx) tma_load_3d(dst + bx * kRBF * 128, map, x + 32 * bx, y, cs.c, bars + stg);
+    const int nbox = (cs.ph + cs.sws + 31) >> 5;  // per plane
+    mbar_expect_tx(full + stg, (unsigned int)(CP * nbox) * 128u * kRBF);
+    for (int p = 0; p < CP; ++p)  // plane p's boxes feed warps p WPP .. p WPP + nbox - 1
+      for (int bx = 0; bx < nbox; ++bx)
+        tma_load_3d(dst + (p * D::WPP + bx) * kRBF * 128, map, x + 32 * bx, y, CP == 1 ? cs.c : p, full + stg);
+    ++issued;
   };
   if (tid == 0) {
     if (map_in_global) fence_tensormap_acquire(map);
@@ -120,36 +166,38 @@ __device__ __forceinline__ bool tcf_item(const Item& it, float c_tap, unsigned c
     if ((it.foldT || it.foldB || it.foldL || it.foldR) && warp == kNWF - 1) make_cumulative_tc(CU, r, c_tap, S);
   }
   if (tid == 0) lookahead(0);
+  __syncthreads();  // tables ready
 
   const unsigned int* Ph = P + ((g & 1) ? np : 0);
   const unsigned int* Pl = P + 2 * np + ((g & 1) ? np : 0);
   const int D0 = it.offy - it.ph;  // tap(v, yo) = v + D0 - yo
-  const int colw = 32 * warp;
+  const int wplane = warp / D::WPP;           // this warp's plane within the pass
+  const int colw = 32 * (warp % D::WPP);      // and its first staged element
+  const bool inplane = warp < CP * D::WPP;
   float acc1[2][4][4];
-  float acc2[tc_units(1, kNWF)][4];
+  float acc2[tc_units(CP, kNWF)][4];
   #pragma unroll
-  for (int i = 0; i < tc_units(1, kNWF); ++i)
+  for (int i = 0; i < tc_units(CP, kNWF); ++i)
     #pragma unroll
     for (int k = 0; k < 4; ++k) acc2[i][k] = 0.f;
   float vmax = 0.0f;  // largest staged |x| this thread converted (NaN sticks)
+  bool dead = false;  // warp-uniform: a wait of this warp ran out
 
-  int q = 0;
-  bool ok = true;
-  for (; q < Q; ++q) {
+  for (int q = 0; q < Q; ++q) {
     const int gq = gq0 + q;
-    bool got = mbar_wait(bars + gq % kStagesF, (unsigned int)(gq / kStagesF) & 1u);
-    got = __syncthreads_and(got) != 0;  // chunk q visible to every thread; iteration q-1 finished everywhere
-    if (!got) {
-      ok = false;
-      break;
+    if (tid == 0) {
+      if (q + kStagesF - 1 < Q) issue(q + kStagesF - 1);
+      if (q == 0) lookahead(1);
     }
-    if (tid == 0 && q + kStagesF - 1 < Q) issue(q + kStagesF - 1);
-    if (q == 0 && tid == 0) lookahead(1);
     const int s = q / it.nchunks, k = q - s * it.nchunks;
     const Slab sl = slab_of<false>(it, s);
     const int R0 = k * kRBF;
     const unsigned char* st = ring + (size_t)(gq % kStagesF) * kStageBF;
-    const bool wact = colw < sl.ph + sl.sws && colw + 32 > sl.ph;  // warp holds slab elements
+    const bool wact = inplane && colw < sl.ph + sl.sws && colw + 32 > sl.ph;  // warp holds slab elements
+    // every warp waits for the chunk, also one that holds none of the slab's
+    // elements: a warp must not arrive for chunk gq + 4 (same stage) before
+    // the chunk is issued, or its arrival would count toward chunk gq's phase
+    if (!dead) dead = !__all_sync(0xffffffffu, mbar_wait(full + gq % kStagesF, (unsigned int)(gq / kStagesF) & 1u));
     if (k == 0) {
       #pragma unroll
       for (int mt = 0; mt < 2; ++mt)
@@ -176,7 +224,7 @@ __device__ __forceinline__ bool tcf_item(const Item& it, float c_tap, unsigned c
       }
     }
     // ---- pass 1 on the chunk (one 16-row k-step)
-    if (wact && R0 < it.vrows) {
+    if (wact) {
       const int k0 = R0;
       const bool on0 = k0 + 15 >= -D0 && k0 <= 15 - D0 + 2 * r;
       const bool on1 = k0 + 15 >= 16 - D0 && k0 <= 31 - D0 + 2 * r;
@@ -204,18 +252,16 @@ __device__ __forceinline__ bool tcf_item(const Item& it, float c_tap, unsigned c
         for (int j = 0; j < 4; ++j) {
           vmax = fmaxf(vmax, fmaxf(fmaxf(fabsf(v0[j]), fabsf(v1[j])), fmaxf(fabsf(v8[j]), fabsf(v9[j]))));
           if (!(fabsf(v0[j]) + fabsf(v1[j]) + fabsf(v8[j]) + fabsf(v9[j]) < 4.0f * kRangeF)) vmax = kRangeF * 2.0f;
-          const __half h0 = __float2half_rn(v0[j]), h1 = __float2half_rn(v1[j]);
-          const __half h8 = __float2half_rn(v8[j]), h9 = __float2half_rn(v9[j]);
-          bh[j][0] = pack_half2(h0, h1);
-          bh[j][1] = pack_half2(h8, h9);
-          bl[j][0] = pack2(v0[j] - __half2float(h0), v1[j] - __half2float(h1));
-          bl[j][1] = pack2(v8[j] - __half2float(h8), v9[j] - __half2float(h9));
+          const __half2 h01 = __floats2half2_rn(v0[j], v1[j]), h89 = __floats2half2_rn(v8[j], v9[j]);
+          const float2 f01 = __half22float2(h01), f89 = __half22float2(h89);
+          bh[j][0] = h2_bits(h01);
+          bh[j][1] = h2_bits(h89);
+          bl[j][0] = h2_bits(__floats2half2_rn(v0[j] - f01.x, v1[j] - f01.y));
+          bl[j][1] = h2_bits(__floats2half2_rn(v8[j] - f89.x, v9[j] - f89.y));
         }
         // W_hi X_hi, W_lo X_hi and W_hi X_lo of the k-step go into a zeroed
-        // fragment that is then added to acc1 in fp32: the tensor cores
-        // truncate when they add products into an accumulator, so summing
-        // every k-step in the MMA accumulator would bias the result toward
-        // zero by about an ulp per k-step
+        // fragment that is then added to acc1 in fp32 (the MMA's own adds
+        // truncate)
         #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
           if (!(mt == 0 ? on0 : on1)) continue;
@@ -237,80 +283,91 @@ __device__ __forceinline__ bool tcf_item(const Item& it, float c_tap, unsigned c
         }
       }
     }
-    if (k != it.nchunks - 1) continue;
-
-    // ---- slab complete: folded bottom row, then V -> hi/lo fp16 for pass 2
-    const int npx = sl.sws;
-    const int npx16 = (npx + 15) & ~15;
-    {
-      const int vb = it.ph + it.EH - 1;
-      if (it.foldB && vb >= R0 && vb < R0 + kRBF && wact) {
-        const float4 a = *reinterpret_cast<const float4*>(st + fpiece(warp, vb - R0, 2 * t));
-        const float4 b = *reinterpret_cast<const float4*>(st + fpiece(warp, vb - R0, 2 * t + 1));
-        const float d0[4] = {a.x, a.y, a.z, a.w}, d1[4] = {b.x, b.y, b.z, b.w};
+    const bool last = k == it.nchunks - 1;
+    // folded bottom row (in the slab's last chunk), the stage's last read
+    const int vb = it.ph + it.EH - 1;
+    if (last && it.foldB && vb >= R0 && vb < R0 + kRBF && wact) {
+      const float4 a = *reinterpret_cast<const float4*>(st + fpiece(warp, vb - R0, 2 * t));
+      const float4 b = *reinterpret_cast<const float4*>(st + fpiece(warp, vb - R0, 2 * t + 1));
+      const float d0[4] = {a.x, a.y, a.z, a.w}, d1[4] = {b.x, b.y, b.z, b.w};
+      #pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const float c0 = cum_at(CU, 2 * r + 1 - (it.offy + it.EH - (16 * mt + g)), r) * kWScale;
+        const float c1 = cum_at(CU, 2 * r + 1 - (it.offy + it.EH - (16 * mt + g + 8)), r) * kWScale;
         #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-          const float c0 = cum_at(CU, 2 * r + 1 - (it.offy + it.EH - (16 * mt + g)), r) * kWScale;
-          const float c1 = cum_at(CU, 2 * r + 1 - (it.offy + it.EH - (16 * mt + g + 8)), r) * kWScale;
-          #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            acc1[mt][j][0] = fmaf(c0, d0[j], acc1[mt][j][0]);
-            acc1[mt][j][1] = fmaf(c0, d1[j], acc1[mt][j][1]);
-            acc1[mt][j][2] = fmaf(c1, d0[j], acc1[mt][j][2]);
-            acc1[mt][j][3] = fmaf(c1, d1[j], acc1[mt][j][3]);
-          }
+        for (int j = 0; j < 4; ++j) {
+          acc1[mt][j][0] = fmaf(c0, d0[j], acc1[mt][j][0]);
+          acc1[mt][j][1] = fmaf(c0, d1[j], acc1[mt][j][1]);
+          acc1[mt][j][2] = fmaf(c1, d0[j], acc1[mt][j][2]);
+          acc1[mt][j][3] = fmaf(c1, d1[j], acc1[mt][j][3]);
         }
       }
-      // V[yo][px] = acc * 2^-12 as hi + lo fp16; staged element 32w + 8t + e8
-      // is slab pixel 32w + 8t + e8 - ph
-      if (wact) {
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty + gq % kStagesF);  // this warp is done with the stage
+    if (!last) continue;
+
+    // ---- slab complete: V -> hi/lo fp16 for pass 2
+    const int npx = sl.sws;
+    const int npx16 = (npx + 15) & ~15;
+    __syncthreads();  // every warp is done with the previous slab's V
+    // V[yo][px] = acc * 2^-12 as hi + lo fp16; staged element 32w + 8t + e8
+    // is slab pixel 32w + 8t + e8 - ph
+    if (wact) {
+      #pragma unroll
+      for (int e8 = 0; e8 < 8; ++e8) {
+        const int e = colw + 8 * t + e8 - sl.ph;
+        if (e < 0 || e >= npx) continue;
         #pragma unroll
-        for (int e8 = 0; e8 < 8; ++e8) {
-          const int e = colw + 8 * t + e8 - sl.ph;
-          if (e < 0 || e >= npx) continue;
+        for (int mt = 0; mt < 2; ++mt) {
           #pragma unroll
-          for (int mt = 0; mt < 2; ++mt) {
-            #pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-              const float v = acc1[mt][e8 & 3][2 * hh + (e8 >> 2)] * kVScaleF;
-              const __half h = __float2half_rn(v);
-              const __half l = __float2half_rn(v - __half2float(h));
-              const size_t o = (size_t)(16 * mt + g + 8 * hh) * kVPF + e;
-              if (smem_in_bounds(Vh + o, 2, err) && smem_in_bounds(Vl + o, 2, err)) {
-                Vh[o] = h;
-                Vl[o] = l;
-              }
+          for (int hh = 0; hh < 2; ++hh) {
+            const float v = acc1[mt][e8 & 3][2 * hh + (e8 >> 2)] * kVScaleF;
+            const __half h = __float2half_rn(v);
+            const __half l = __float2half_rn(v - __half2float(h));
+            const size_t o = (size_t)(32 * wplane + 16 * mt + g + 8 * hh) * D::VP + e;
+            if (smem_in_bounds(Vh + o, 2, err) && smem_in_bounds(Vl + o, 2, err)) {
+              Vh[o] = h;
+              Vl[o] = l;
             }
           }
         }
       }
-      // zero the columns px in [npx, npx16) that pass 2 reads
-      const int zc = npx16 - npx;
-      for (int idx = tid; idx < 32 * zc; idx += kNTF) {
-        const int row = idx / zc, px = npx + (idx - row * zc);
-        const size_t o = (size_t)row * kVPF + px;
-        if (smem_in_bounds(Vh + o, 2, err) && smem_in_bounds(Vl + o, 2, err)) {
-          Vh[o] = __ushort_as_half(0);
-          Vl[o] = __ushort_as_half(0);
-        }
+    }
+    // zero the columns px in [npx, npx16) that pass 2 reads
+    const int zc = npx16 - npx;
+    for (int idx = tid; idx < 32 * CP * zc; idx += kNTF) {
+      const int row = idx / zc, px = npx + (idx - row * zc);
+      const size_t o = (size_t)row * D::VP + px;
+      if (smem_in_bounds(Vh + o, 2, err) && smem_in_bounds(Vl + o, 2, err)) {
+        Vh[o] = __ushort_as_half(0);
+        Vl[o] = __ushort_as_half(0);
       }
     }
-    __syncthreads();
-    tc_pass2_slab<1, false, kNWF, true>(it, sl, Vh, Vl, CU, P, np, acc2);
+    __syncthreads();  // V complete
+    {
+      // pass 2 counts a slab in interleaved elements: pixels x planes
+      Slab s2 = sl;
+      s2.e0 = sl.e0 * CP;
+      s2.sws = sl.sws * CP;
+      tc_pass2_slab<CP, false, kNWF, true>(it, s2, Vh, Vl, CU, P, np, acc2);
+    }
 
     if (s % it.nsl == it.nsl - 1) {
-      // the plane's last slab: its outputs (x 2^-12) go straight to the frame
+      // the last slab of the pass's planes: their outputs (x 2^-12) go
+      // straight to the frame; unit u holds rows of m-tile u / 4 of V, whose
+      // plane is (u / 4) / 2 (the slab's plane when CP = 1)
       const size_t plane = (size_t)it.W * it.H;
-      float* outp = reinterpret_cast<float*>(it.out) + (size_t)sl.c * plane;
       const size_t frame_bytes = plane * it.C * 4;
       #pragma unroll
-      for (int i = 0; i < tc_units(1, kNWF); ++i) {
+      for (int i = 0; i < tc_units(CP, kNWF); ++i) {
         const int u = warp + kNWF * i;
-        if (u >= 8) continue;
+        if (u >= 8 * CP) continue;
         const int mt2 = u >> 2, nt2 = u & 3;
+        float* outp = reinterpret_cast<float*>(it.out) + (size_t)(CP == 1 ? sl.c : mt2 >> 1) * plane;
         #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const int yo = 16 * mt2 + g + ((e >> 1) << 3), x = 8 * nt2 + 2 * t + (e & 1);
+          const int yo = 16 * (mt2 & 1) + g + ((e >> 1) << 3), x = 8 * nt2 + 2 * t + (e & 1);
           if (yo < it.bh && x < it.bw) {
             float* o = outp + (size_t)(it.y0 + yo) * it.W + it.x0 + x;
             if (in_bounds(o, 4, it.out, frame_bytes, err)) *o = acc2[i][e] * kWInv;
@@ -320,66 +377,99 @@ __device__ __forceinline__ bool tcf_item(const Item& it, float c_tap, unsigned c
       }
     }
   }
-  if (!ok) {
-    // a chunk never arrived: flag it, let the chunks still in flight land
-    // (bounded) and give up on the item
+  gq0 += Q;
+  const bool fail = __syncthreads_or(dead || pdead) != 0;
+  if (fail) {
+    // a wait ran out: flag it, let this item's boxes still in flight land
+    // (bounded) and give up
     if (tid == 0) {
       atomicOr(err, kFaultWait);
-      for (int qq = q; qq < Q && qq < q + kStagesF - 1; ++qq) {
-        const int gq = gq0 + qq;
-        mbar_wait(bars + gq % kStagesF, (unsigned int)(gq / kStagesF) & 1u);
+      const int first = gq0 - Q;
+      for (int qq = issued > kStagesF ? issued - kStagesF : 0; qq < issued; ++qq) {
+        const int c = first + qq;
+        mbar_wait(full + c % kStagesF, (unsigned int)(c / kStagesF) & 1u);
       }
     }
     __syncthreads();
     return false;
   }
-  gq0 += Q;
   if (__syncthreads_or(!(vmax < kRangeF)) && tid == 0) atomicOr(err, kFaultValueRange);
   fence_proxy_async();  // the next item's TMA boxes overwrite the ring
   return true;
 }
 
+template <int CP>
 __global__ void __launch_bounds__(kNTF, 2)
 tcf_forward_kernel(const __grid_constant__ FrameSource src, Workspace ws, int rmax, BucketList bl,
                    const __grid_constant__ CUtensorMap tmap1) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  const TcfLayout L = tcf_layout(rmax);
+  const TcfLayout L = tcf_layout(rmax, tcf_vhalves(CP, TcfDims<CP>::VP));
   unsigned char* ring = smem + L.ring;
   __half* Vh = reinterpret_cast<__half*>(smem + L.vh);
   __half* Vl = reinterpret_cast<__half*>(smem + L.vl);
   float* CU = reinterpret_cast<float*>(smem + L.cum);
   unsigned int* P = reinterpret_cast<unsigned int*>(smem + L.pairs);
-  __shared__ __align__(8) unsigned long long s_bar[kStagesF];
+  __shared__ __align__(8) unsigned long long s_full[kStagesF], s_empty[kStagesF];
   const int np = npair(rmax);
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kStagesF; ++i) mbar_init(&s_bar[i], 1);
+    for (int i = 0; i < kStagesF; ++i) {
+      mbar_init(&s_full[i], 1);
+      mbar_init(&s_empty[i], kNWF);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     fence_proxy_async();
   }
   int gq0 = 0;  // chunks this CTA has loaded so far (identical in every thread)
-  tc_item_loop<kRBF, 1, true, kNWF, kSlabF, true>(
+  tc_item_loop<kRBF, CP, true, kNWF, TcfDims<CP>::SLAB, true>(
       src, tmap1, ws, rmax, bl, reinterpret_cast<int*>(smem + L.starts),
       [&](const Item& it, float c, const void* map, bool map_global, auto& lookahead) {
         if (!map) {  // rows TMA cannot address: the host runs the fp32 kernel for such launches
           if (threadIdx.x == 0) atomicOr(ws.counters + CNT_ERROR, kFaultRadiusBound);
           return true;
         }
-        return tcf_item(it, c, ring, Vh, Vl, CU, P, np, s_bar, map, map_global, gq0, ws.counters + CNT_ERROR,
-                        lookahead);
+        return tcf_item<CP>(it, c, ring, Vh, Vl, CU, P, np, s_full, s_empty, map, map_global, gq0,
+                            ws.counters + CNT_ERROR, lookahead);
       });
+}
+
+// Planes per pass for a launch whose frames all have `channels` planes (0:
+// mixed counts) and whose radius bound is rmax. Packed passes pay off while
+// halos are narrow; from a radius bound of 129 on (halos beyond 290 columns)
+// one plane per pass on all eight warps measured faster (1920 x 1080 x 3
+// float32, sigma = 0.5 + 0.08 e, radii up to 262: 1.24 ms against 1.34 ms
+// packed; at radii up to 67, 0.248 ms packed against 0.267 ms).
+constexpr int kTcfPackedRadius = 128;
+int tcf_planes(int channels, int rmax) {
+  return channels >= 2 && channels <= 4 && rmax <= kTcfPackedRadius ? channels : 1;
+}
+
+const void* tcf_kernel_fn(int channels, int rmax) {
+  switch (tcf_planes(channels, rmax)) {
+    case 2: return reinterpret_cast<const void*>(&tcf_forward_kernel<2>);
+    case 3: return reinterpret_cast<const void*>(&tcf_forward_kernel<3>);
+    case 4: return reinterpret_cast<const void*>(&tcf_forward_kernel<4>);
+    default: return reinterpret_cast<const void*>(&tcf_forward_kernel<1>);
+  }
+}
+
+int tcf_vpitch(int cp) {
+  return cp == 2 ? TcfDims<2>::VP : cp == 3 ? TcfDims<3>::VP : cp == 4 ? TcfDims<4>::VP : TcfDims<1>::VP;
 }
 
 }  // namespace
 
 bool tcf_supports(int rmax) { return rmax <= kMaxRadius; }
 
-size_t tcf_forward_smem_bytes(int rmax) { return tcf_layout(rmax).total; }
+size_t tcf_forward_smem_bytes(int rmax, int channels) {
+  const int cp = tcf_planes(channels, rmax);
+  return tcf_layout(rmax, tcf_vhalves(cp, tcf_vpitch(cp))).total;
+}
 
-int tcf_forward_max_ctas_per_sm(int rmax) {
-  const size_t smem = tcf_forward_smem_bytes(rmax);
-  const void* k = reinterpret_cast<const void*>(&tcf_forward_kernel);
+int tcf_forward_max_ctas_per_sm(int rmax, int channels) {
+  const size_t smem = tcf_forward_smem_bytes(rmax, channels);
+  const void* k = tcf_kernel_fn(channels, rmax);
   if (set_smem_attrs(k, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -392,10 +482,10 @@ int tcf_forward_max_ctas_per_sm(int rmax) {
   return n;
 }
 
-cudaError_t launch_tcf_forward(const FrameSource& src, const Workspace& ws, int rmax, int grid, cudaStream_t s,
-                               const BucketList& bl, bool pdl, const void* tmap_one) {
-  const size_t smem = tcf_forward_smem_bytes(rmax);
-  void* k = reinterpret_cast<void*>(&tcf_forward_kernel);
+cudaError_t launch_tcf_forward(const FrameSource& src, const Workspace& ws, int rmax, int channels, int grid,
+                               cudaStream_t s, const BucketList& bl, bool pdl, const void* tmap_one) {
+  const size_t smem = tcf_forward_smem_bytes(rmax, channels);
+  void* k = const_cast<void*>(tcf_kernel_fn(channels, rmax));
   cudaError_t e = set_smem_attrs(reinterpret_cast<const void*>(k), smem);
   if (e != cudaSuccess) return e;
   BucketList b = bl;

@@ -51,6 +51,8 @@ CASES = [
     (1000, 60, 1, 32, 0.0, 30.0, 0.5, 0.3),       # wide halos: several column slabs
     (640, 40, 2, 32, 600.0, 20.0, 0.5, 0.4),      # several slabs in each of two planes
     (128, 96, 4, 8, 64.0, 48.0, 0.0, 0.15),       # sigma0 = 0, B = 8, four channels
+    (400, 120, 3, 32, 380.0, 60.0, 0.5, 0.25),    # three planes per pass, several slabs
+    (200, 64, 4, 32, 0.0, 32.0, 0.5, 0.3),        # four planes per pass, several slabs
     (4, 1, 1, 32, 2.0, 0.5, 1.0, 0.0),            # one row of four
     (8, 300, 1, 32, 4.0, 0.0, 0.5, 0.05),         # narrow column
     (37, 29, 1, 32, 10.0, 10.0, 0.5, 0.1),        # W not a multiple of 4: the fp32 kernel
@@ -82,9 +84,12 @@ def test_tcf_signed_data_of_larger_magnitude(fv):
 
 
 def test_tcf_mixed_batch_and_single_frame_agree(fv):
-    """Frames of several sizes in one tensor-core launch; a frame too large
-    for one wave also renders alone through fovea_render on the same kernel,
-    bit for bit equal to its batch output (same item body, same sigma)."""
+    """Frames of several sizes and channel counts in one tensor-core launch
+    (one plane per slab pass); a frame too large for one wave also renders
+    alone through fovea_render (its three planes together in each pass), bit
+    for bit equal to a batch of that frame alone (same kernel, same sigma)
+    and within 2e-6 of its output in the mixed batch (other slab widths
+    regroup the fp32 sums)."""
     frames = [(wl.uniform_f32((3, 1080, 1920), seed=1), 700.5, 300.25, 0.5, 0.02),
               (wl.uniform_f32((1, 256, 256), seed=2), 128.0, 128.0, 0.5, 0.02),
               (wl.uniform_f32((3, 224, 224), seed=3), 200.0, 15.0, 0.5, 0.08),
@@ -103,7 +108,9 @@ def test_tcf_mixed_batch_and_single_frame_agree(fv):
     ctx.render(x, y, fx, fy)
     torch.cuda.synchronize()
     assert ctx.check() == 0
-    assert torch.equal(y, outs[0])
+    alone, = render_batch_with(fv, frames[:1], 1)
+    assert torch.equal(y, alone)
+    assert float((y - outs[0]).abs().max()) <= 2e-6
 
 
 def test_tcf_value_out_of_range_is_reported(fv):
