@@ -286,7 +286,11 @@ typedef struct {
                          frame's rows TMA can load (16-byte aligned base, width
                          a multiple of 4), except a single frame whose blocks
                          fit one wave of the fp32 kernel; staged values must
-                         satisfy |x| < 2^15 (else FOVEA_FAULT_VALUE_RANGE) */
+                         satisfy |x| < 2^15 (else FOVEA_FAULT_VALUE_RANGE).
+                         The adjoint (fovea_backward*) runs on the fp32 kernel,
+                         except with 2: on mma.sync with a power-of-two scale
+                         per block plane (measured slower; error about 2^-21
+                         of the block's largest |gradient|) */
 } fovea_config;
 
 /* Copy the context's current configuration into *cfg. FOVEA_EINVAL for a

@@ -25,7 +25,7 @@ LIB = os.path.join(HERE, "libfovea.so")
 BUILD_BOUNDS = os.path.join(HERE, "_build_bounds")
 LIB_BOUNDS = os.path.join(HERE, "libfovea_bounds.so")
 
-SOURCES = ["sigma.cu", "forward.cu", "tc_forward.cu", "umma_forward.cu", "tc05_forward.cu", "tcf_forward.cu", "pixel_forward.cu", "pyramid.cu", "ssim.cu", "adjoint.cu", "noalloc.cu", "peak.cu",
+SOURCES = ["sigma.cu", "forward.cu", "tc_forward.cu", "umma_forward.cu", "tc05_forward.cu", "tcf_forward.cu", "tca_adjoint.cu", "pixel_forward.cu", "pyramid.cu", "ssim.cu", "adjoint.cu", "noalloc.cu", "peak.cu",
            "api.cu", "tune.cpp", "server.cpp"]
 HEADERS = ["fovea_internal.cuh", "fovea_host.h", "fwd_common.cuh", "tc_common.cuh", "tc05_common.cuh", "arena.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

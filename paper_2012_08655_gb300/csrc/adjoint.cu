@@ -87,6 +87,9 @@ adjoint_kernel(FrameSource src, Workspace ws, int rmax) {
     const size_t planePitch = (size_t)W * H;
     const float* gout = static_cast<const float*>(fd.in);
     float* gin = static_cast<float*>(fd.out);
+    // rows of grad_in start on 16-byte boundaries: four consecutive columns
+    // from a multiple of 4 take one vector reduction
+    const bool vec_ok = (((uintptr_t)gin) & 15) == 0 && (W & 3) == 0;
 
     make_taps(U, tap_len(r), r, inf.neg_half_inv_s2, red);
     make_cumulative(U, CU, r);
@@ -105,6 +108,9 @@ adjoint_kernel(FrameSource src, Workspace ws, int rmax) {
     for (int c = 0; c < C; ++c) {
       for (int X0 = 0; X0 < EW; X0 += kSlabPx) {
         const int SWx = min(kSlabPx, EW - X0);
+        // Z column of slab column col is col + sh: pass B's groups of four Z
+        // columns then cover frame columns from a multiple of 4
+        const int sh = (gx0 + X0) & 3;
         // ---- pass A: Z[yo][ex - X0] = sum_xo w(ex, xo) g[yo][xo]
         const int ngA = (SWx + 7) >> 3;
         for (int it = tid; it < 16 * ngA; it += kThreads) {
@@ -150,14 +156,14 @@ adjoint_kernel(FrameSource src, Workspace ws, int rmax) {
           for (int j = 0; j < 8; ++j) {
             const int col = 8 * g + j;
             if (col < SWx) {
-              Z[(2 * p) * kZPitch + col] = acc[j].x;
-              Z[(2 * p + 1) * kZPitch + col] = acc[j].y;
+              Z[(2 * p) * kZPitch + col + sh] = acc[j].x;
+              Z[(2 * p + 1) * kZPitch + col + sh] = acc[j].y;
             }
           }
         }
         __syncthreads();
         // ---- pass B: g_in[gy0 + ey][gx0 + ex] += sum_yo w(ey, yo) Z[yo][ex]
-        const int nq = (SWx + 3) >> 2;
+        const int nq = (SWx + sh + 3) >> 2;  // groups of four Z columns (slab columns 4q - sh ..)
         for (int it = tid; it < nq * nh; it += kThreads) {
           const int q = it % nq, h = it / nq;
           const int tg = offy + 8 * h;        // tap index of (ey = 8h, yo = 0)
@@ -203,18 +209,24 @@ adjoint_kernel(FrameSource src, Workspace ws, int rmax) {
             }
           }
           float* plane = gin + (size_t)c * planePitch;
+          const int col0 = 4 * q - sh;  // slab column of the group's first value
           #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int ey = 8 * h + j;
             if (ey >= EH) break;
             float* rowp = plane + (size_t)(gy0 + ey) * W + gx0 + X0;
             const float v[4] = {acc[j][0].x, acc[j][0].y, acc[j][1].x, acc[j][1].y};
-            #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int col = 4 * q + e;
-              if (col < SWx && v[e] != 0.f &&
-                  in_bounds(rowp + col, 4, gin, planePitch * C * 4, ws.counters + CNT_ERROR))
-                atomicAdd(rowp + col, v[e]);
+            if (vec_ok && col0 >= 0 && col0 + 3 < SWx) {
+              if (in_bounds(rowp + col0, 16, gin, planePitch * C * 4, ws.counters + CNT_ERROR))
+                red_add_f32x4(rowp + col0, v[0], v[1], v[2], v[3]);
+            } else {
+              #pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const int col = col0 + e;
+                if (col >= 0 && col < SWx && v[e] != 0.f &&
+                    in_bounds(rowp + col, 4, gin, planePitch * C * 4, ws.counters + CNT_ERROR))
+                  red_add_f32(rowp + col, v[e]);
+              }
             }
           }
         }

@@ -329,8 +329,10 @@ long long config_code(const FwdConfig& c) {
   return (((long long)c.threads * 128 + c.rows_per_chunk) * 4 + c.tc) * 16 + c.ctas_per_sm;
 }
 
-int adjoint_grid(fovea_ctx* ctx, int rmax) {
-  int per = adjoint_max_ctas_per_sm(rmax);
+// tc: the tensor-core adjoint (tensor_cores = 2; measured slower than the
+// fp32 adjoint, which every other setting runs), else the fp32 one
+int adjoint_grid(fovea_ctx* ctx, int rmax, bool tc) {
+  int per = tc ? tca_adjoint_max_ctas_per_sm(rmax) : adjoint_max_ctas_per_sm(rmax);
   if (per <= 0) return 0;
   return per * ctx->num_sms;
 }
@@ -479,9 +481,10 @@ int enqueue_batch_kernels(fovea_ctx* ctx, const FwdConfig& cfg, bool adjoint, in
   cudaError_t e = launch_sigma_order(src, ctx->ws, sg, nullptr, nullptr, s);
   if (e != cudaSuccess) return cuda_fail(e);
   if (adjoint) {
-    int grid = adjoint_grid(ctx, rbound);
+    const bool tca = cfg.tc == 2;
+    int grid = adjoint_grid(ctx, rbound, tca);
     if (grid <= 0) return FOVEA_EUNSUPPORTED;
-    e = launch_adjoint(src, ctx->ws, rbound, grid, s);
+    e = tca ? launch_tca_adjoint(src, ctx->ws, rbound, grid, s) : launch_adjoint(src, ctx->ws, rbound, grid, s);
   } else {
     int grid = forward_grid(ctx, cfg, rbound, fmt_mask, tc_c, all_tma);
     if (grid <= 0) return FOVEA_EUNSUPPORTED;
@@ -818,9 +821,10 @@ int fovea_backward(fovea_ctx* ctx, const float* grad_out_dev, float* grad_in_dev
   FOVEA_CUDA(cudaMemsetAsync(grad_in_dev, 0, nb, s));
   cudaError_t e = launch_sigma_order(src, ctx->ws, sigma_grid(src.one_total, ctx->num_sms), nullptr, nullptr, s);
   if (e != cudaSuccess) return cuda_fail(e);
-  const int grid = adjoint_grid(ctx, rmax);
+  const bool tc = ctx->cfg.tc == 2;
+  const int grid = adjoint_grid(ctx, rmax, tc);
   if (grid <= 0) return FOVEA_EUNSUPPORTED;
-  e = launch_adjoint(src, ctx->ws, rmax, grid, s);
+  e = tc ? launch_tca_adjoint(src, ctx->ws, rmax, grid, s) : launch_adjoint(src, ctx->ws, rmax, grid, s);
   if (e != cudaSuccess) return cuda_fail(e);
   return FOVEA_OK;
 }

@@ -304,6 +304,22 @@ __device__ __forceinline__ float cum_at(const float* CU, int m, int r) {
   return CU[m < 0 ? 0 : (m > 2 * r + 1 ? 2 * r + 1 : m)];
 }
 
+// Fire-and-forget fp32 add into global memory (red.global: no value comes
+// back, the issuing warp does not wait). atomicAdd through a generic pointer
+// with its result unused compiled to a generic atomic that returns the old
+// value (one read-back sector per update and a scoreboard wait).
+__device__ __forceinline__ void red_add_f32(float* p, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;\n" ::"l"(__cvta_generic_to_global(p)), "f"(v) : "memory");
+}
+
+// Four consecutive floats at a 16-byte aligned address, one vector reduction
+// (sm_90 and later).
+__device__ __forceinline__ void red_add_f32x4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(__cvta_generic_to_global(p)), "f"(a), "f"(b),
+               "f"(c), "f"(d)
+               : "memory");
+}
+
 // Packed two-lane add.
 __device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
 #if defined(FOVEA_SCALAR_FMA)
@@ -421,6 +437,12 @@ cudaError_t launch_tcf_forward(const FrameSource& src, const Workspace& ws, int 
 size_t adjoint_smem_bytes(int rmax);
 cudaError_t launch_adjoint(const FrameSource& src, const Workspace& ws, int rmax, int grid,
                            cudaStream_t s);
+// The adjoint on mma.sync (tca_adjoint.cu): per block plane a power-of-two
+// scale, fp16 hi + lo splits of the gradient and of Z, the forward kernel's
+// tap-pair tables; any radius bound.
+size_t tca_adjoint_smem_bytes(int rmax);
+int tca_adjoint_max_ctas_per_sm(int rmax);
+cudaError_t launch_tca_adjoint(const FrameSource& src, const Workspace& ws, int rmax, int grid, cudaStream_t s);
 int adjoint_max_ctas_per_sm(int rmax);
 
 // ------------------------------------------------------------------ per-pixel foveation
