@@ -18,6 +18,7 @@ import os
 from dataclasses import dataclass
 from typing import Optional, Sequence
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -435,16 +436,42 @@ def _frames_array(frames: Sequence[BatchFrame], device: Optional[int] = None):
     return arr
 
 
-def _frames_of_nchw(x: torch.Tensor, y: torch.Tensor, fixes, sigma0: float, k: float):
-    """Frame array of a contiguous float32 [N, C, H, W] batch (input x,
-    output y) from the base pointers, without a tensor view per image."""
+# numpy mirror of the Frame struct (same field offsets and size), so a batch's
+# frame records are filled by vectorised assignments instead of one ctypes
+# constructor per frame
+_FRAME_NP = np.dtype({
+    "names": [name for name, _ in Frame._fields_],
+    "formats": [{ctypes.c_int: np.int32, ctypes.c_void_p: np.uint64, ctypes.c_float: np.float32,
+                 ctypes.c_double: np.float64}[typ] for _, typ in Frame._fields_],
+    "offsets": [getattr(Frame, name).offset for name, _ in Frame._fields_],
+    "itemsize": ctypes.sizeof(Frame)})
+
+
+class _FrameRecords:
+    """Frame records in a numpy array, passed to the C calls as Frame*."""
+
+    def __init__(self, recs: np.ndarray):
+        self.recs = recs
+        self.ptr = recs.ctypes.data_as(ctypes.POINTER(Frame))
+
+    def __len__(self):
+        return len(self.recs)
+
+
+def _frames_of_nchw(x: torch.Tensor, y: torch.Tensor, fixes: np.ndarray, sigma0: float, k: float):
+    """Frame records of a contiguous float32 [N, C, H, W] batch (input x,
+    output y) from the base pointers, without a tensor view per image;
+    fixes: float32 [N, 2] (x, y)."""
     n, c, h, w = x.shape
-    step = c * h * w * 4
-    xi, yo = x.data_ptr(), y.data_ptr()
-    arr = (Frame * n)()
-    for i, (fx, fy) in enumerate(fixes):
-        arr[i] = Frame(w, h, c, F32_CHW, xi + i * step, yo + i * step, fx, fy, sigma0, k, GRID_ANCHORED, None, 0.0)
-    return arr
+    step = np.uint64(c * h * w * 4)
+    idx = np.arange(n, dtype=np.uint64)
+    recs = np.zeros(n, dtype=_FRAME_NP)
+    recs["width"], recs["height"], recs["channels"], recs["format"] = w, h, c, F32_CHW
+    recs["in_"] = np.uint64(x.data_ptr()) + idx * step
+    recs["out"] = np.uint64(y.data_ptr()) + idx * step
+    recs["fix_x"], recs["fix_y"] = fixes[:, 0], fixes[:, 1]
+    recs["sigma0"], recs["k"], recs["grid"] = sigma0, k, GRID_ANCHORED
+    return _FrameRecords(recs)
 
 
 # ------------------------------------------------------------------ functional API
@@ -616,12 +643,14 @@ class FoveaFunction(torch.autograd.Function):
             raise ValueError("FoveaFunction takes float32 [N, C, H, W]")
         x = x.contiguous()
         _require_device_frame(x, "x")
-        fixes = [(float(a), float(b)) for a, b in fix.detach().cpu().tolist()]
+        fixes = np.ascontiguousarray(fix.detach().cpu().numpy(), dtype=np.float32).reshape(-1, 2)
+        if len(fixes) != x.shape[0]:
+            raise ValueError("one fixation per image")
         y = torch.empty_like(x)
         bctx = _batch_ctx(block)
         arr = _frames_of_nchw(x, y, fixes, float(sigma0), float(k))
         st = _stream_handle(None)
-        _check(_lib.fovea_render_batch(bctx._h, arr, len(fixes), st), "fovea_render_batch")
+        _check(_lib.fovea_render_batch(bctx._h, arr.ptr, len(arr), st), "fovea_render_batch")
         bctx.check_async()  # faults of earlier launches surface here without a wait
         ctx.fixes, ctx.sigma0, ctx.k, ctx.block = fixes, sigma0, k, block
         return y
@@ -633,7 +662,7 @@ class FoveaFunction(torch.autograd.Function):
         gx = torch.empty_like(gy)
         bctx = _batch_ctx(ctx.block)
         arr = _frames_of_nchw(gy, gx, ctx.fixes, float(ctx.sigma0), float(ctx.k))
-        _check(_lib.fovea_backward_batch(bctx._h, arr, len(ctx.fixes), _stream_handle(None)), "fovea_backward_batch")
+        _check(_lib.fovea_backward_batch(bctx._h, arr.ptr, len(arr), _stream_handle(None)), "fovea_backward_batch")
         bctx.check_async()
         return gx, None, None, None, None
 

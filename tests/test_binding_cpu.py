@@ -122,3 +122,24 @@ def test_request_log_writes_one_json_object_per_line(tmp_path):
     log2.append({"id": 2})
     log2.close()
     assert len(path.read_text().splitlines()) == 3
+
+
+def test_frame_records_match_the_ctypes_struct():
+    """The numpy frame records of the autograd path have the C struct's
+    layout: each record's bytes equal a ctypes Frame built field by field."""
+    import ctypes
+    import numpy as np
+    import torch
+    from paper_2012_08655_gb300 import fovea as fv
+    x = torch.zeros((3, 2, 5, 8), dtype=torch.float32)
+    y = torch.zeros_like(x)
+    fixes = np.array([[1.5, 2.25], [-3.0, 7.125], [100.0, 0.5]], np.float32)
+    recs = fv._frames_of_nchw(x, y, fixes, 0.5, 0.08)
+    assert len(recs) == 3 and recs.recs.itemsize == ctypes.sizeof(fv.Frame)
+    step = 2 * 5 * 8 * 4
+    for i in range(3):
+        want = fv.Frame(8, 5, 2, fv.F32_CHW, x.data_ptr() + i * step, y.data_ptr() + i * step,
+                        float(fixes[i, 0]), float(fixes[i, 1]), 0.5, 0.08, fv.GRID_ANCHORED, None, 0.0)
+        assert recs.recs[i].tobytes() == bytes(want)
+    # and the pointer handed to the C calls is the array's first record
+    assert ctypes.addressof(recs.ptr.contents) == recs.recs.ctypes.data
