@@ -22,9 +22,17 @@ namespace fovea {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kSlabPx = 256;           // tile pixel columns per slab (one channel at a time)
-constexpr int kZPitch = kSlabPx + 4;   // float pitch of Z (multiple of 4 for float4 reads)
 constexpr int kGPitch = 33;            // float2 pitch of the row-pair gradient block (odd)
+// Every plane of the tile goes through each pass together (more independent
+// work per phase, one pair of barriers per slab instead of per plane): Z
+// holds the planes one after the other, slabs of 256 tile columns for one
+// or two planes, 128 for three or four; a Z row has 4 spare floats (the
+// column shift of the vector reductions, float4 reads).
+__host__ __device__ constexpr int adj_slab(int C) { return C <= 2 ? 256 : 128; }
+__host__ __device__ constexpr int adj_zpitch(int C) { return adj_slab(C) + 4; }
+constexpr int kZFloats = 4 * 32 * (128 + 4);  // the largest C x 32 x pitch (C = 4; C = 2 needs 16,640)
+static_assert(2 * 32 * (256 + 4) <= kZFloats && 1 * 32 * (256 + 4) <= kZFloats && 3 * 32 * (128 + 4) <= kZFloats,
+              "every channel count's Z fits");
 
 struct SmemLayout {
   size_t gg, z, taps, cum, red, total;
@@ -33,8 +41,8 @@ struct SmemLayout {
 __host__ __device__ inline SmemLayout smem_layout(int rmax) {
   SmemLayout L;
   L.gg = 0;                                                // float2 [4][16][kGPitch]
-  L.z = L.gg + (size_t)4 * 16 * kGPitch * sizeof(float2);  // float [32][kZPitch]
-  L.taps = L.z + (size_t)32 * kZPitch * sizeof(float);     // float2 [tap_len]
+  L.z = L.gg + (size_t)4 * 16 * kGPitch * sizeof(float2);  // float [C][32][zpitch]
+  L.taps = L.z + (size_t)kZFloats * sizeof(float);         // float2 [tap_len]
   L.cum = L.taps + (size_t)tap_len(rmax) * sizeof(float2); // float [cum_len]
   L.red = L.cum + (size_t)cum_len(rmax) * sizeof(float);   // float [32]
   L.total = L.red + 32 * sizeof(float);
@@ -105,16 +113,19 @@ adjoint_kernel(FrameSource src, Workspace ws, int rmax) {
     __syncthreads();
 
     const int nh = (EH + 7) >> 3;
-    for (int c = 0; c < C; ++c) {
-      for (int X0 = 0; X0 < EW; X0 += kSlabPx) {
-        const int SWx = min(kSlabPx, EW - X0);
+    const int slab = adj_slab(C), kZPitch = adj_zpitch(C);
+    {
+      for (int X0 = 0; X0 < EW; X0 += slab) {
+        const int SWx = min(slab, EW - X0);
         // Z column of slab column col is col + sh: pass B's groups of four Z
         // columns then cover frame columns from a multiple of 4
         const int sh = (gx0 + X0) & 3;
-        // ---- pass A: Z[yo][ex - X0] = sum_xo w(ex, xo) g[yo][xo]
+        // ---- pass A: Z[c][yo][ex - X0] = sum_xo w(ex, xo) g[c][yo][xo], every plane
         const int ngA = (SWx + 7) >> 3;
-        for (int it = tid; it < 16 * ngA; it += kThreads) {
-          const int p = it & 15, g = it >> 4;
+        for (int it = tid; it < C * 16 * ngA; it += kThreads) {
+          const int c = it / (16 * ngA), rem = it - c * 16 * ngA;
+          const int p = rem & 15, g = rem >> 4;
+          float* Zc = Z + (size_t)c * 32 * kZPitch;
           const int tg = offx + X0 + 8 * g;   // tap index of (ex = X0 + 8g, xo = 0)
           const int klo = max(tg - bw + 1, -7), khi = min(tg, 2 * r);
           float2 acc[8];
@@ -156,16 +167,18 @@ adjoint_kernel(FrameSource src, Workspace ws, int rmax) {
           for (int j = 0; j < 8; ++j) {
             const int col = 8 * g + j;
             if (col < SWx) {
-              Z[(2 * p) * kZPitch + col + sh] = acc[j].x;
-              Z[(2 * p + 1) * kZPitch + col + sh] = acc[j].y;
+              Zc[(2 * p) * kZPitch + col + sh] = acc[j].x;
+              Zc[(2 * p + 1) * kZPitch + col + sh] = acc[j].y;
             }
           }
         }
         __syncthreads();
         // ---- pass B: g_in[gy0 + ey][gx0 + ex] += sum_yo w(ey, yo) Z[yo][ex]
         const int nq = (SWx + sh + 3) >> 2;  // groups of four Z columns (slab columns 4q - sh ..)
-        for (int it = tid; it < nq * nh; it += kThreads) {
-          const int q = it % nq, h = it / nq;
+        for (int it = tid; it < C * nq * nh; it += kThreads) {
+          const int c = it / (nq * nh), rem = it - c * nq * nh;
+          const int q = rem % nq, h = rem / nq;
+          const float* Zc = Z + (size_t)c * 32 * kZPitch;
           const int tg = offy + 8 * h;        // tap index of (ey = 8h, yo = 0)
           const int klo = max(tg - bh + 1, -7), khi = min(tg, 2 * r);
           float2 acc[8][2];
@@ -182,7 +195,7 @@ adjoint_kernel(FrameSource src, Workspace ws, int rmax) {
                 const int kk = kb + s;
                 w[(s + 7) & 7] = U[kTapPad + kk + 7];
                 float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (kk >= klo && kk <= khi) d = *reinterpret_cast<const float4*>(Z + (tg - kk) * kZPitch + 4 * q);
+                if (kk >= klo && kk <= khi) d = *reinterpret_cast<const float4*>(Zc + (tg - kk) * kZPitch + 4 * q);
                 const float2 dlo = make_float2(d.x, d.y), dhi = make_float2(d.z, d.w);
                 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
@@ -202,7 +215,7 @@ adjoint_kernel(FrameSource src, Workspace ws, int rmax) {
                 float cw = 0.f;
                 if (ft) cw += cum_at(CU, offy - yo, r);
                 if (fb) cw += cum_at(CU, 2 * r + 1 - (offy + EH - yo), r);
-                const float4 d = *reinterpret_cast<const float4*>(Z + yo * kZPitch + 4 * q);
+                const float4 d = *reinterpret_cast<const float4*>(Zc + yo * kZPitch + 4 * q);
                 acc[j][0] = ffma2(make_float2(cw, cw), make_float2(d.x, d.y), acc[j][0]);
                 acc[j][1] = ffma2(make_float2(cw, cw), make_float2(d.z, d.w), acc[j][1]);
               }
