@@ -286,7 +286,8 @@ typedef struct {
                          frame's rows TMA can load (16-byte aligned base, width
                          a multiple of 4), except a single frame whose blocks
                          fit one wave of the fp32 kernel; staged values must
-                         satisfy |x| < 2^15 (else FOVEA_FAULT_VALUE_RANGE).
+                         satisfy |x| < 32760 = 2^15 - 8, below what fp16
+                         rounds to 2^15 (else FOVEA_FAULT_VALUE_RANGE).
                          The adjoint (fovea_backward*) runs on the fp32 kernel,
                          except with 2: on mma.sync with a power-of-two scale
                          per block plane (measured slower; error about 2^-21
@@ -403,7 +404,8 @@ int fovea_render_noalloc(const void* in_dev, void* out_dev, int width, int heigh
 #define FOVEA_FAULT_BOUNDS      0x100u /* bounds-checked builds (-DFOVEA_BOUNDS) only: a store fell outside
                                           the buffer it belongs to and was skipped (internal) */
 #define FOVEA_FAULT_VALUE_RANGE 0x200u /* float32 frames on the tensor cores: a staged value was not finite
-                                          or |x| >= 2^15, beyond the fp16 hi + lo split; the
+                                          or |x| >= 32760 (fp16 rounds it to 2^15 or more),
+                                          beyond the fp16 hi + lo split; the
                                           blocks it fed are not trustworthy (caller's data) */
 
 /* Waits for `stream` (a cudaStream_t; the stream the context's calls were

@@ -14,7 +14,8 @@
 // product of two fp16 values is exact in fp32, so the result carries fp32
 // accumulation error plus a representation error of about 2^-21 of |x| (for
 // |x| >= 2^-14; an absolute 2^-25 below, where the parts are fp16
-// subnormals). The split needs |x| < 2^15: a staged value beyond that, or
+// subnormals). The split needs |x| < 32760 (fp16 rounds larger values to
+// 2^15 or more): a staged value beyond that, or
 // one that is not finite, is recorded as FOVEA_FAULT_VALUE_RANGE and its
 // block is not trustworthy.
 // The tensor cores truncate (round toward zero) when they add products into
@@ -180,7 +181,9 @@ __device__ __forceinline__ bool tcf_item(const Item& it, float c_tap, unsigned c
   for (int i = 0; i < tc_units(CP, kNWF); ++i)
     #pragma unroll
     for (int k = 0; k < 4; ++k) acc2[i][k] = 0.f;
-  float vmax = 0.0f;  // largest staged |x| this thread converted (NaN sticks)
+  // largest |x_hi| this thread converted, NaN sticking: x_hi = fp16(x) is
+  // at least 2^15 (or infinite) for every |x| >= 32760
+  __half2 hmax = __float2half2_rn(0.0f);
   bool dead = false;  // warp-uniform: a wait of this warp ran out
 
   for (int q = 0; q < Q; ++q) {
@@ -250,9 +253,8 @@ __device__ __forceinline__ bool tcf_item(const Item& it, float c_tap, unsigned c
         unsigned int bh[4][2], bl[4][2];
         #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          vmax = fmaxf(vmax, fmaxf(fmaxf(fabsf(v0[j]), fabsf(v1[j])), fmaxf(fabsf(v8[j]), fabsf(v9[j]))));
-          if (!(fabsf(v0[j]) + fabsf(v1[j]) + fabsf(v8[j]) + fabsf(v9[j]) < 4.0f * kRangeF)) vmax = kRangeF * 2.0f;
           const __half2 h01 = __floats2half2_rn(v0[j], v1[j]), h89 = __floats2half2_rn(v8[j], v9[j]);
+          hmax = __hmax2_nan(hmax, __hmax2_nan(__habs2(h01), __habs2(h89)));
           const float2 f01 = __half22float2(h01), f89 = __half22float2(h89);
           bh[j][0] = h2_bits(h01);
           bh[j][1] = h2_bits(h89);
@@ -393,7 +395,8 @@ __device__ __forceinline__ bool tcf_item(const Item& it, float c_tap, unsigned c
     __syncthreads();
     return false;
   }
-  if (__syncthreads_or(!(vmax < kRangeF)) && tid == 0) atomicOr(err, kFaultValueRange);
+  const float2 hm = __half22float2(hmax);
+  if (__syncthreads_or(!(hm.x < kRangeF && hm.y < kRangeF)) && tid == 0) atomicOr(err, kFaultValueRange);
   fence_proxy_async();  // the next item's TMA boxes overwrite the ring
   return true;
 }

@@ -113,16 +113,24 @@ def test_tcf_mixed_batch_and_single_frame_agree(fv):
     assert float((y - outs[0]).abs().max()) <= 2e-6
 
 
-def test_tcf_value_out_of_range_is_reported(fv):
-    """A staged value the fp16 split cannot carry (|x| >= 2^15, or not
-    finite) sets FOVEA_FAULT_VALUE_RANGE: fovea_check reports EINVAL (the
-    caller's data) and the context stays usable."""
+@pytest.mark.parametrize("bad", [32760.0, -40000.0, float("nan"), float("-inf")])
+def test_tcf_value_out_of_range_is_reported(fv, bad):
+    """A staged value the fp16 split cannot carry (|x| >= 32760, which fp16
+    rounds to 2^15 or more, or not finite) sets FOVEA_FAULT_VALUE_RANGE:
+    fovea_check reports EINVAL (the caller's data); 32759 does not, and the
+    context stays usable."""
     img = wl.uniform_f32((1, 64, 64), seed=5)
-    img[0, 10, 20] = 40000.0
     ctx = fv.batch_context(32)
     ctx.set_config(256, 0, 32, tensor_cores=1)
     x = to_dev(img)
     y = torch.empty_like(x)
+    img[0, 10, 20] = -32759.0
+    x.copy_(torch.from_numpy(img))
+    ctx.render_batch([fv.BatchFrame(x, y, 32.0, 32.0, 0.5, 0.1)])
+    torch.cuda.synchronize()
+    assert ctx.check() == 0
+    img[0, 10, 20] = bad
+    x.copy_(torch.from_numpy(img))
     ctx.render_batch([fv.BatchFrame(x, y, 32.0, 32.0, 0.5, 0.1)])
     with pytest.raises(fv.FoveaError) as e:
         ctx.check()
