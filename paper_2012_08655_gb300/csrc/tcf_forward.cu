@@ -60,7 +60,7 @@ constexpr int kRBF = 16;                    // staged rows per chunk (one k-step
 constexpr int kStagesF = 4;                 // ring stages
 constexpr int kBoxesF = kNWF;               // one 32-element box per warp column
 constexpr int kStageBF = kBoxesF * kRBF * 128;
-constexpr float kRangeF = 32768.0f;         // |x| from here on does not split into fp16 hi + lo
+constexpr float kRangeF = 32768.0f;         // an fp16 hi part this large (or not finite) flags the value range
 constexpr float kVScaleF = 1.0f / 4096.0f;  // V = pass-1 accumulator * 2^-12 (taps x 2^12, data x 1)
 
 // CP channel planes per slab pass: CP = 1 takes one plane at a time (any
