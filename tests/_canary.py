@@ -124,7 +124,44 @@ def run_cases(fv, torch):
         expect(g.intact(), f"mixed batch frame {i}")
     for i, g in enumerate(aguards):
         expect(g.intact(), f"adjoint batch frame {i}")
+    # the adjoint on the tensor cores (tensor_cores = 2), same frames
+    bctx.set_config(256, 0, 32, tensor_cores=2)
+    aguards2 = []
+    for i, f in enumerate(adj):
+        g = Guarded(torch, tuple(f.inp.shape), torch.float32, 4 * ((i + 1) % 3))
+        aguards2.append(g)
+        adj[i] = fv.BatchFrame(f.inp, g.t, f.fix_x, f.fix_y, f.sigma0, f.k)
+    bctx.backward_batch(adj)
+    torch.cuda.synchronize()
+    for i, g in enumerate(aguards2):
+        expect(g.intact(), f"tensor-core adjoint batch frame {i}")
+    # float32 batches on the tensor cores: three planes per pass (uniform
+    # channel count), one plane per pass (mixed counts); widths a multiple of
+    # 4 and frames at least one TMA box (32 x 16), so every frame of a batch
+    # is TMA-loadable and the batch runs on the tensor-core kernel
+    bctx.set_config(256, 0, 32, tensor_cores=1)
+    for label, shapes in (("f32 tc batch, 3 planes", [(3, 33, 64), (3, 300, 32), (3, 96, 512), (3, 16, 36)]),
+                          ("f32 tc batch, mixed planes", [(1, 70, 1000), (2, 45, 36), (4, 129, 100)])):
+        fr, gs = [], []
+        for i, shape in enumerate(shapes):
+            x = torch.from_numpy(wl.uniform_f32(shape, seed=40 + i)).to(dev)
+            g = Guarded(torch, shape, torch.float32, 4 * (i % 4))
+            fr.append(fv.BatchFrame(x, g.t, 0.25 * shape[2], 0.75 * shape[1], 0.5, 0.3))
+            gs.append(g)
+        bctx.render_batch(fr)
+        torch.cuda.synchronize()
+        for i, g in enumerate(gs):
+            expect(g.intact(), f"{label} frame {i}")
     check_ctx(bctx, "batches")
+    # a float32 frame beyond one wave: the tensor-core kernel on the single-frame path
+    x = torch.from_numpy(wl.uniform_f32((3, 512, 800), seed=77)).to(dev)
+    ctx = fv.Context(800, 512, 3, 32, 0.5, 0.02, fv.F32_CHW)
+    for skew in (0, 4):
+        g = Guarded(torch, (3, 512, 800), torch.float32, skew)
+        ctx.render(x, g.t, 700.0, 30.0)
+        torch.cuda.synchronize()
+        expect(g.intact(), f"render f32 3x512x800 (tensor cores) skew={skew}")
+    check_ctx(ctx, "f32 3x512x800")
     # ---- per-pixel foveation, pyramid and SSIM map
     for (h, w, c) in [(65, 33, 3), (1, 300, 1), (120, 200, 4)]:
         img = wl.uniform_u8((h, w, c), seed=h * w)
