@@ -1,5 +1,6 @@
-// Tensor-core forward kernel for float32 CHW frames (tensor_cores = 1 on a
-// float32 launch; the fp32 CUDA-core kernel otherwise).
+// Tensor-core forward kernel for float32 CHW frames (any non-zero
+// tensor_cores on a launch of float32 frames whose rows TMA can load; the
+// fp32 CUDA-core kernel otherwise).
 //
 // The block-wise separable blur of paper Section 2 and Algorithm 1 (taps of
 // Eq. 1 truncated at r = ceil(3 sigma)) as the banded Toeplitz contractions
@@ -15,9 +16,8 @@
 // accumulation error plus a representation error of about 2^-21 of |x| (for
 // |x| >= 2^-14; an absolute 2^-25 below, where the parts are fp16
 // subnormals). The split needs |x| < 32760 (fp16 rounds larger values to
-// 2^15 or more): a staged value beyond that, or
-// one that is not finite, is recorded as FOVEA_FAULT_VALUE_RANGE and its
-// block is not trustworthy.
+// 2^15 or more): a staged value beyond that, or one that is not finite, is
+// recorded as FOVEA_FAULT_VALUE_RANGE and its block is not trustworthy.
 // The tensor cores truncate (round toward zero) when they add products into
 // an accumulator, about an ulp of the accumulator per MMA; summing a whole
 // window in the MMA accumulators biased outputs toward zero by ~2e-6 of
