@@ -445,6 +445,7 @@ def train_leg(fv, torch, reps: int = 20):
     x = torch.from_numpy(x_np).cuda().requires_grad_(True)
     fix = torch.from_numpy(fix_np)
     g = torch.rand_like(x)
+    n_img = x_np.shape[0]
     res = {}
     for name in ("forward", "forward_backward"):
         def step():
@@ -475,6 +476,23 @@ def train_leg(fv, torch, reps: int = 20):
         e1.record()
         torch.cuda.synchronize()
     res["forward_fp32"] = e0.elapsed_time(e1) / reps
+    # the backward alone (one batched adjoint launch per call): the fp32
+    # adjoint every configuration but tensor_cores = 2 runs, then that one
+    gi = torch.empty_like(g)
+    frames = [fv.BatchFrame(g[i], gi[i], float(fix_np[i, 0]), float(fix_np[i, 1]), s0, k) for i in range(n_img)]
+    for key, tc in (("backward", 1), ("backward_tensor_cores", 2)):
+        b.set_config(256, 0, 32, tensor_cores=tc)
+        for _ in range(3):
+            b.backward_batch(frames)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            b.backward_batch(frames)
+        e1.record()
+        torch.cuda.synchronize()
+        b.check()
+        res[key] = e0.elapsed_time(e1) / reps
     b.set_config(256, 0, 32, tensor_cores=1)
     px = x_np.shape[0] * x_np.shape[2] * x_np.shape[3]
     # algorithmic work of the forward (the method's separable FMAs, halo
@@ -493,10 +511,14 @@ def train_leg(fv, torch, reps: int = 20):
             "forward_algorithmic_fmas": fmas,
             "forward_tflops": tflops,
             "forward_fp32_kernel_ms": res["forward_fp32"],
+            "backward_ms": res["backward"],
+            "backward_tensor_cores_ms": res["backward_tensor_cores"],
             "forward_note": "whole forward call (sigma, order and blur kernels, Python autograd overhead) "
                             "against the algorithmic FMAs; default configuration: float32 frames on the "
                             "mma.sync tensor-core kernel (fp16 hi + lo splits); forward_fp32_kernel_ms: the "
-                            "same call on the fp32 CUDA-core kernel"}
+                            "same call on the fp32 CUDA-core kernel; backward_ms: one batched adjoint launch "
+                            "(fovea_backward_batch) on the default fp32 adjoint, backward_tensor_cores_ms: the "
+                            "same on the tensor-core adjoint (tensor_cores = 2)"}
 
 
 def block_sweep_leg(fv, torch):
