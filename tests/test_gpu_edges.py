@@ -45,7 +45,10 @@ def test_radius_near_the_maximum(fv, tc):
     assert 1000 < rad.max() <= 1023
     y = render(fv, img, fv.U8_HWC, 4, 0.0, 0.0, s0, k, tc)
     ref = oracle.forward_u8(img, 4, 0.0, 0.0, s0, k, "hwc")
-    assert_u8_close(y, ref, min_equal=0.95)
+    # 192 values: every one within 1 LSB, at most two of them off (a rounding
+    # tie of the fp32 or fp16-split sums against the binary64 oracle)
+    assert_u8_close(y, ref, min_equal=0.0)
+    assert int((y.astype(int) != ref.astype(int)).sum()) <= 2
 
 
 def test_radius_near_the_maximum_f32(fv):
@@ -62,7 +65,9 @@ def test_degenerate_frames(fv, shape, tc):
     img = wl.uniform_u8(shape, seed=H * W + C)
     y = render(fv, img, fv.U8_HWC, 32, W / 3.0, H / 2.0, 0.8, 0.3, tc)
     ref = oracle.forward_u8(img, 32, W / 3.0, H / 2.0, 0.8, 0.3, "hwc")
-    assert_u8_close(y, ref, min_equal=0.95)
+    # 3 to 74 values: every one within 1 LSB, at most two of them off
+    assert_u8_close(y, ref, min_equal=0.0)
+    assert int((y.astype(int) != ref.astype(int)).sum()) <= 2
 
 
 @pytest.mark.parametrize("tc", [0, 1, 2, 3])
