@@ -131,3 +131,16 @@ def test_the_check_catches_a_parity_slip():
     except AssertionError:
         return
     raise AssertionError("a wrong parity table went unnoticed")
+
+
+def test_the_check_catches_a_short_table(monkeypatch):
+    """The check is live on extents too: the forward passes read up to entry
+    r + 38 (and down to entry 0), so a table of r + 37 entries fails."""
+    import sys
+    mod = sys.modules[__name__]
+    monkeypatch.setattr(mod, "npair", lambda rmax: rmax + 37)
+    try:
+        test_forward_pass1_reads_stay_in_the_tables()
+    except AssertionError:
+        return
+    raise AssertionError("a table too short for the reads went unnoticed")
