@@ -26,7 +26,7 @@
 //
 // Planes per pass: a launch whose frames all have C = 2 to 4 planes and whose
 // radius bound is at most 128 takes all C planes of a tile in each slab
-// pass, each plane on 8 / C warps side by side (slabs of up to 112 columns
+// pass, each plane on 8 / C warps side by side (slabs of up to 125 columns
 // for two planes, 61 for three or four), so a narrow halo still keeps most
 // warps busy in pass 1; other launches take one plane per pass on all eight
 // warps (slabs of up to 240 columns). V holds the pass's planes one after

@@ -74,7 +74,7 @@ def test_forward_pass2_reads_stay_in_the_tables():
     for r in RADII:
         for offx in offsets(r):
             EW = 32 + 2 * r - offx  # largest folded halo for this offset
-            for slab in (240, 112, 61):  # one plane per pass; two; three or four (packed)
+            for slab in (240, 125, 61):  # one plane per pass; two; three or four (packed)
                 for P0 in range(0, EW, slab):
                     npx = min(slab, EW - P0)
                     npx16 = (npx + 15) & ~15
