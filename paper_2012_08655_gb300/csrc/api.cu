@@ -624,15 +624,16 @@ int fovea_create(int width, int height, int channels, int block, const fovea_sig
 
 // The tensor map of a single frame at in_dev (the context's shape and
 // format), from the context's two-entry cache; nullptr where TMA cannot load
-// the frame's rows.
+// the frame's rows (as in batches, only device memory is loaded by TMA).
 static const void* frame_tensor_map(fovea_ctx* ctx, const void* in_dev, int fmt_mask) {
   const int rows = fmt_mask == 1 ? ctx->cfg.rows_per_chunk : 16;
   for (const auto& m : ctx->maps)
     if (m.in == in_dev && m.rows == rows) return m.ok ? m.map : nullptr;
   auto& m = ctx->maps[ctx->map_next];
   ctx->map_next ^= 1;
-  m.ok = fmt_mask == 1 ? make_u8_tensor_map(m.map, in_dev, ctx->W, ctx->H, ctx->C, rows)
-                       : make_f32_tensor_map(m.map, in_dev, ctx->W, ctx->H, ctx->C, rows);
+  m.ok = in_device_memory(in_dev) &&
+         (fmt_mask == 1 ? make_u8_tensor_map(m.map, in_dev, ctx->W, ctx->H, ctx->C, rows)
+                        : make_f32_tensor_map(m.map, in_dev, ctx->W, ctx->H, ctx->C, rows));
   m.in = in_dev;
   m.rows = rows;
   return m.ok ? m.map : nullptr;
